@@ -1,0 +1,172 @@
+/*
+ * cfust.h - C ABI of the GB300 CFUST-mixture EM library (libcfust.so).
+ *
+ * The library fits finite mixtures of canonical fundamental skew t (CFUST)
+ * distributions by EM, the model of Eq. 1 and Eq. 2 of Lee, McLachlan and
+ * Leemaqz, "Multi-Node EM Algorithm for Finite Mixture Models"
+ * (arXiv:2005.06848):
+ *
+ *   f(y; Psi)   = sum_i pi_i f_i(y; theta_i)                       (Eq. 1)
+ *   f_i(y)      = 2^r t_p(y; mu, Omega, nu)
+ *                 T_r(Delta^T Omega^{-1}(y - mu) sqrt((nu+p)/(nu+d)); 0, Lambda, nu+p)  (Eq. 2)
+ *   Omega = Sigma + Delta Delta^T,  Lambda = I_r - Delta^T Omega^{-1} Delta,
+ *   d = (y-mu)^T Omega^{-1} (y-mu).
+ *
+ * The paper writes the skew dimension as q; it is r here.  Every call runs its
+ * arithmetic in this library's CUDA kernels (sm_103a); nothing falls back to
+ * the host.
+ *
+ * Conventions
+ *  - The caller owns every buffer.  Y and the per-pair E-step arrays are DEVICE
+ *    pointers on the context's stream; cfust_params and the scalar outputs
+ *    (log-likelihood, traces) are HOST memory.
+ *  - Y is row-major [n][p] double, 8-byte aligned.
+ *  - Per-pair arrays are component-major and coalesced in the observation
+ *    index j: tau[g][n], logf[g][n], e1[g][n], e2[g][n], e3[g][r][n],
+ *    e4[g][r(r+1)/2][n] with e4 packed as the lower triangle row by row
+ *    (entry (t, h), h <= t, at t(t+1)/2 + h).  Their element type is double in
+ *    CFUST_FP64 mode and float in CFUST_FP32 mode.
+ *  - Calls that return host scalars synchronise the context's stream; the
+ *    others are stream-ordered.  No call aborts: errors come back as a
+ *    negative cfust_status, and cfust_last_error() gives a message.
+ *  - Limits: 1 <= p <= CFUST_PMAX, 1 <= r <= CFUST_RMAX, 1 <= g <= CFUST_GMAX,
+ *    32 <= lattice points <= CFUST_NMAX with the count a multiple of 32.
+ */
+#ifndef CFUST_H
+#define CFUST_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define CFUST_PMAX 16
+#define CFUST_RMAX 6
+#define CFUST_GMAX 64
+#define CFUST_NMAX 65536
+
+typedef int cfust_status;
+#define CFUST_OK           0
+#define CFUST_EINVAL      -1   /* bad argument or parameter (message says which) */
+#define CFUST_ENOTPD      -2   /* Omega, Lambda, S6 or an updated Sigma not positive definite */
+#define CFUST_ENUMERIC    -3   /* NaN/Inf, or an observation with zero density under every component */
+#define CFUST_EDEGENERATE -4   /* a component's sum of tau fell below 1e-10 n */
+#define CFUST_ETIMEOUT    -5   /* a bounded device wait ran out (no fault is raised) */
+#define CFUST_ECUDA       -6   /* a CUDA runtime call failed */
+#define CFUST_ENOMEM      -7   /* device allocation failed */
+
+#define CFUST_FP64 0   /* every step in double precision (parity mode) */
+#define CFUST_FP32 1   /* lattice sweeps in float; factorisations, log-likelihood and M-step sums in double */
+
+/* Mixture parameters Psi = (pi_1..pi_g, theta_1..theta_g), theta_i = (mu_i, Sigma_i, Delta_i, nu_i)
+ * (Section 2).  Host memory, row-major:
+ *   pi[g], mu[g][p], Sigma[g][p][p] (full symmetric), Delta[g][p][r], nu[g]. */
+typedef struct {
+  int g, p, r;
+  double *pi;
+  double *mu;
+  double *Sigma;
+  double *Delta;
+  double *nu;
+} cfust_params;
+
+/* Shifted rank-1 lattice rule used for every r-variate t integral: point k
+ * (k = 0..n-1) is u_k = frac(((k z) mod n)/n + shift), then the baker's
+ * transform u <- 1 - |2u - 1| is applied.  dim must be r + 1: coordinate 0
+ * drives the chi-square mixing variable, 1..r the normal variables.
+ * z and shift are host arrays of length dim, read at cfust_create. */
+typedef struct {
+  int n;
+  int dim;
+  const int64_t *z;
+  const double *shift;
+} cfust_lattice;
+
+typedef struct {
+  int precision;          /* CFUST_FP64 or CFUST_FP32 */
+  cfust_lattice lattice;
+  int e2_mode;            /* 0: e2 = e1 - log((nu+d)/2) - (nu+p)/(nu+d) + psi((nu+p)/2);
+                             1: lattice estimate of E[log W | y] from the density sweep */
+  double nu_min, nu_max;  /* bracket of the nu update; 0, 0 selects [1, 200] */
+  int max_iter;           /* EM iterations run by cfust_fit */
+  double tol;             /* Aitken stopping threshold (Algorithm 4); 0 disables it */
+  int use_graph;          /* 1: cfust_fit replays one CUDA graph per EM iteration */
+  int timing;             /* 1: bracket every lattice-sweep kernel launch with CUDA events */
+} cfust_opts;
+
+typedef struct cfust_ctx cfust_ctx;
+
+/* Create a context bound to the current CUDA device and to cuda_stream (a
+ * cudaStream_t; NULL means the legacy default stream).  Copies opts and the
+ * lattice spec.  Allocates per-context device scratch lazily on first use. */
+cfust_status cfust_create(cfust_ctx **ctx, const cfust_opts *opts, void *cuda_stream);
+
+/* Free the context and its device scratch.  NULL is accepted. */
+cfust_status cfust_destroy(cfust_ctx *ctx);
+
+/* l(Psi) = sum_j log sum_i pi_i f_i(y_j) (Eq. 1, Eq. 3), one density sweep per pair.
+ * Y: device [n][p].  loglik: host, written on success.  Synchronises. */
+cfust_status cfust_loglik(cfust_ctx *ctx, const double *Y, int64_t n,
+                          const cfust_params *params, double *loglik);
+
+/* E-step of Section 2 (Algorithm 2's per-pair work): for every (i, j),
+ * tau_ij = pi_i f_ij / f_j (Eq. 4) and the conditional expectations
+ * e1 = E[W|y], e2 = E[log W|y], e3 = E[W U|y], e4 = E[W U U^T|y] of the latent
+ * gamma W and truncated-normal U.  logf (log f_i(y_j)) may be NULL; the
+ * others must be device arrays in the layout above.  loglik (host, may be
+ * NULL) receives l(Psi).  Synchronises when loglik is not NULL. */
+cfust_status cfust_estep(cfust_ctx *ctx, const double *Y, int64_t n,
+                         const cfust_params *params,
+                         void *logf, void *tau, void *e1, void *e2, void *e3, void *e4,
+                         double *loglik);
+
+/* M-step of Algorithm 3: accumulates the eight per-component sums of
+ * Section 3.2 from tau, e1..e4 (device, same layout and element type as
+ * cfust_estep's outputs) and Y, then updates params in place (host) by
+ * conditional maximisation: pi, mu, Delta, Sigma, nu.  Synchronises. */
+cfust_status cfust_mstep(cfust_ctx *ctx, const double *Y, int64_t n,
+                         const void *tau, const void *e1, const void *e2,
+                         const void *e3, const void *e4, cfust_params *params);
+
+/* Full EM (Section 2 outline) from params (updated in place): at most
+ * opts.max_iter iterations, stopping early by Algorithm 4 when opts.tol > 0.
+ * loglik_trace (host, length max_iter + 1, may be NULL) receives
+ * l(Psi^(0)) .. l(Psi^(k)), each E-step yielding the log-likelihood of the
+ * parameters it starts from.  iters_done (may be NULL) receives k. */
+cfust_status cfust_fit(cfust_ctx *ctx, const double *Y, int64_t n,
+                       cfust_params *params, double *loglik_trace, int *iters_done);
+
+/* Stepwise form of cfust_fit for callers that drive the iterations themselves.
+ * cfust_fit_begin uploads params and binds Y (device [n][p], kept until
+ * cfust_fit_end) and resets the trace.  cfust_fit_step enqueues `iters` EM
+ * iterations on the context's stream without synchronising (each a replay of
+ * one CUDA graph when opts.use_graph is 1); at most opts.max_iter iterations
+ * in total.  cfust_fit_end runs the final density sweep, synchronises, and
+ * returns the parameters, the trace l(Psi^(0)) .. l(Psi^(k)) (host, k + 1
+ * entries, may be NULL) and k (may be NULL). */
+cfust_status cfust_fit_begin(cfust_ctx *ctx, const double *Y, int64_t n,
+                             const cfust_params *params);
+cfust_status cfust_fit_step(cfust_ctx *ctx, int iters);
+cfust_status cfust_fit_end(cfust_ctx *ctx, cfust_params *params, double *loglik_trace,
+                           int *iters_done);
+
+/* Number of (i, j) pairs whose single-precision lattice sweep fell below the
+ * underflow guard in the last E-step and were recomputed in double precision
+ * on the GPU (always 0 in CFUST_FP64 mode). */
+cfust_status cfust_last_rescued(cfust_ctx *ctx, int64_t *count);
+
+/* Device time (ms) of the last lattice-sweep kernel launch (the E-step's
+ * dominant kernel), from the CUDA events recorded around it on the launching
+ * stream when opts.timing is 1.  Synchronises on the stop event.
+ * CFUST_EINVAL when timing is off or nothing has run yet. */
+cfust_status cfust_last_sweep_ms(cfust_ctx *ctx, float *ms);
+
+/* Message for the last error on ctx (or on context creation when ctx is NULL). */
+const char *cfust_last_error(cfust_ctx *ctx);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* CFUST_H */

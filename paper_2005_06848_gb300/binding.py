@@ -1,0 +1,245 @@
+"""Thin ctypes binding of libcfust (include/cfust.h).
+
+Argument marshalling only: every step of the E-step, M-step and fit runs in
+the library's CUDA kernels.  PyTorch supplies device memory and the stream.
+Loading fails loudly when the library is missing and cannot be built.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+from . import build as _build
+
+CFUST_FP64 = 0
+CFUST_FP32 = 1
+STATUS = {0: "CFUST_OK", -1: "CFUST_EINVAL", -2: "CFUST_ENOTPD", -3: "CFUST_ENUMERIC",
+          -4: "CFUST_EDEGENERATE", -5: "CFUST_ETIMEOUT", -6: "CFUST_ECUDA", -7: "CFUST_ENOMEM"}
+
+EXPORTED = ["cfust_create", "cfust_destroy", "cfust_loglik", "cfust_estep", "cfust_mstep",
+            "cfust_fit", "cfust_fit_begin", "cfust_fit_step", "cfust_fit_end",
+            "cfust_last_rescued", "cfust_last_sweep_ms", "cfust_last_error"]
+
+
+class CfustError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"{STATUS.get(status, status)}: {msg}")
+        self.status = status
+
+
+class cfust_params(ctypes.Structure):
+    _fields_ = [("g", ctypes.c_int), ("p", ctypes.c_int), ("r", ctypes.c_int),
+                ("pi", ctypes.POINTER(ctypes.c_double)), ("mu", ctypes.POINTER(ctypes.c_double)),
+                ("Sigma", ctypes.POINTER(ctypes.c_double)), ("Delta", ctypes.POINTER(ctypes.c_double)),
+                ("nu", ctypes.POINTER(ctypes.c_double))]
+
+
+class cfust_lattice(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_int), ("dim", ctypes.c_int),
+                ("z", ctypes.POINTER(ctypes.c_int64)), ("shift", ctypes.POINTER(ctypes.c_double))]
+
+
+class cfust_opts(ctypes.Structure):
+    _fields_ = [("precision", ctypes.c_int), ("lattice", cfust_lattice), ("e2_mode", ctypes.c_int),
+                ("nu_min", ctypes.c_double), ("nu_max", ctypes.c_double),
+                ("max_iter", ctypes.c_int), ("tol", ctypes.c_double), ("use_graph", ctypes.c_int),
+                ("timing", ctypes.c_int)]
+
+
+_LIB = None
+
+
+def load(build_if_missing: bool = True) -> ctypes.CDLL:
+    """Load libcfust.so (building it in-tree with nvcc when absent or stale)."""
+    global _LIB
+    if _LIB is not None:
+        return _LIB
+    path = _build.build() if build_if_missing else _build.LIB
+    if not os.path.exists(path):
+        raise RuntimeError(f"libcfust.so not found at {path}")
+    lib = ctypes.CDLL(path)
+    vp, i64, dp = ctypes.c_void_p, ctypes.c_int64, ctypes.POINTER(ctypes.c_double)
+    P = ctypes.POINTER(cfust_params)
+    sig = {
+        "cfust_create": ([ctypes.POINTER(vp), ctypes.POINTER(cfust_opts), vp], ctypes.c_int),
+        "cfust_destroy": ([vp], ctypes.c_int),
+        "cfust_loglik": ([vp, vp, i64, P, dp], ctypes.c_int),
+        "cfust_estep": ([vp, vp, i64, P, vp, vp, vp, vp, vp, vp, dp], ctypes.c_int),
+        "cfust_mstep": ([vp, vp, i64, vp, vp, vp, vp, vp, P], ctypes.c_int),
+        "cfust_fit": ([vp, vp, i64, P, dp, ctypes.POINTER(ctypes.c_int)], ctypes.c_int),
+        "cfust_fit_begin": ([vp, vp, i64, P], ctypes.c_int),
+        "cfust_fit_step": ([vp, ctypes.c_int], ctypes.c_int),
+        "cfust_fit_end": ([vp, P, dp, ctypes.POINTER(ctypes.c_int)], ctypes.c_int),
+        "cfust_last_rescued": ([vp, ctypes.POINTER(i64)], ctypes.c_int),
+        "cfust_last_sweep_ms": ([vp, ctypes.POINTER(ctypes.c_float)], ctypes.c_int),
+        "cfust_last_error": ([vp], ctypes.c_char_p),
+    }
+    for name, (args, res) in sig.items():
+        fn = getattr(lib, name)
+        fn.argtypes = args
+        fn.restype = res
+    _LIB = lib
+    return lib
+
+
+class _HostParams:
+    """cfust_params view over contiguous float64 numpy copies (kept alive here)."""
+
+    def __init__(self, params):
+        self.arrays = [np.ascontiguousarray(a, dtype=np.float64).copy() for a in params.as_arrays()]
+        pi, mu, Sigma, Delta, nu = self.arrays
+        dp = ctypes.POINTER(ctypes.c_double)
+        self.c = cfust_params(int(pi.shape[0]), int(mu.shape[1]), int(Delta.shape[2]),
+                              pi.ctypes.data_as(dp), mu.ctypes.data_as(dp), Sigma.ctypes.data_as(dp),
+                              Delta.ctypes.data_as(dp), nu.ctypes.data_as(dp))
+
+    def to_params(self):
+        from .synth import Params
+        return Params(*(a.copy() for a in self.arrays))
+
+
+def _ptr(t):
+    return ctypes.c_void_p(0 if t is None else t.data_ptr())
+
+
+class Context:
+    """A cfust_ctx bound to the current CUDA device and a torch stream."""
+
+    def __init__(self, lattice, precision=CFUST_FP32, e2_mode=0, nu_min=0.0, nu_max=0.0,
+                 max_iter=0, tol=0.0, use_graph=True, timing=False, stream=None):
+        import torch
+        self.lib = load()
+        self._z = np.ascontiguousarray(lattice.z, dtype=np.int64)
+        self._shift = np.ascontiguousarray(lattice.shift, dtype=np.float64)
+        lat = cfust_lattice(int(lattice.n), int(self._z.shape[0]),
+                            self._z.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)),
+                            self._shift.ctypes.data_as(ctypes.POINTER(ctypes.c_double)))
+        self.opts = cfust_opts(int(precision), lat, int(e2_mode), float(nu_min), float(nu_max),
+                               int(max_iter), float(tol), 1 if use_graph else 0, 1 if timing else 0)
+        self.precision = int(precision)
+        self.stream = stream if stream is not None else torch.cuda.current_stream()
+        self.lattice_n = int(lattice.n)
+        h = ctypes.c_void_p()
+        st = self.lib.cfust_create(ctypes.byref(h), ctypes.byref(self.opts),
+                                   ctypes.c_void_p(self.stream.cuda_stream))
+        if st != 0:
+            raise CfustError(st, self.lib.cfust_last_error(None).decode())
+        self.h = h
+
+    # -- helpers ---------------------------------------------------------
+    @property
+    def dtype(self):
+        import torch
+        return torch.float64 if self.precision == CFUST_FP64 else torch.float32
+
+    def _check(self, st):
+        if st != 0:
+            raise CfustError(st, self.lib.cfust_last_error(self.h).decode())
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.lib.cfust_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    # -- ABI calls (same names as the C entry points) ----------------------
+    def cfust_loglik(self, Y, params) -> float:
+        hp = _HostParams(params)
+        out = ctypes.c_double()
+        self._check(self.lib.cfust_loglik(self.h, _ptr(Y), Y.shape[0], ctypes.byref(hp.c), ctypes.byref(out)))
+        return out.value
+
+    def alloc_estep(self, n, g, r, device=None):
+        import torch
+        dev = device or torch.device("cuda", torch.cuda.current_device())
+        kw = dict(dtype=self.dtype, device=dev)
+        rp = r * (r + 1) // 2
+        return dict(logf=torch.empty((g, n), **kw), tau=torch.empty((g, n), **kw),
+                    e1=torch.empty((g, n), **kw), e2=torch.empty((g, n), **kw),
+                    e3=torch.empty((g, r, n), **kw), e4=torch.empty((g, rp, n), **kw))
+
+    def cfust_estep(self, Y, params, out=None):
+        """Returns dict(logf, tau, e1, e2, e3[g,r,n], e4[g,r(r+1)/2,n], loglik)."""
+        n = Y.shape[0]
+        if out is None:
+            out = self.alloc_estep(n, params.g, params.r, Y.device)
+        hp = _HostParams(params)
+        ll = ctypes.c_double()
+        self._check(self.lib.cfust_estep(self.h, _ptr(Y), n, ctypes.byref(hp.c), _ptr(out["logf"]),
+                                         _ptr(out["tau"]), _ptr(out["e1"]), _ptr(out["e2"]),
+                                         _ptr(out["e3"]), _ptr(out["e4"]), ctypes.byref(ll)))
+        out = dict(out)
+        out["loglik"] = ll.value
+        return out
+
+    def cfust_mstep(self, Y, E, params):
+        hp = _HostParams(params)
+        self._check(self.lib.cfust_mstep(self.h, _ptr(Y), Y.shape[0], _ptr(E["tau"]), _ptr(E["e1"]),
+                                         _ptr(E["e2"]), _ptr(E["e3"]), _ptr(E["e4"]), ctypes.byref(hp.c)))
+        return hp.to_params()
+
+    def cfust_fit(self, Y, params, max_iter=None):
+        if max_iter is not None and max_iter != self.opts.max_iter:
+            raise ValueError("max_iter is fixed at context creation")
+        hp = _HostParams(params)
+        trace = np.zeros(self.opts.max_iter + 1)
+        done = ctypes.c_int()
+        self._check(self.lib.cfust_fit(self.h, _ptr(Y), Y.shape[0], ctypes.byref(hp.c),
+                                       trace.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
+                                       ctypes.byref(done)))
+        return hp.to_params(), trace[:done.value + 1], done.value
+
+    def cfust_fit_begin(self, Y, params):
+        self._fit_hp = _HostParams(params)
+        self._fit_Y = Y  # keep the device buffer alive until cfust_fit_end
+        self._check(self.lib.cfust_fit_begin(self.h, _ptr(Y), Y.shape[0], ctypes.byref(self._fit_hp.c)))
+
+    def cfust_fit_step(self, iters=1):
+        self._check(self.lib.cfust_fit_step(self.h, int(iters)))
+
+    def cfust_fit_end(self):
+        hp = self._fit_hp
+        trace = np.zeros(self.opts.max_iter + 1)
+        done = ctypes.c_int()
+        self._check(self.lib.cfust_fit_end(self.h, ctypes.byref(hp.c),
+                                           trace.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
+                                           ctypes.byref(done)))
+        self._fit_Y = None
+        return hp.to_params(), trace[:done.value + 1], done.value
+
+    def cfust_last_sweep_ms(self) -> float:
+        v = ctypes.c_float()
+        self._check(self.lib.cfust_last_sweep_ms(self.h, ctypes.byref(v)))
+        return v.value
+
+    def cfust_last_rescued(self) -> int:
+        v = ctypes.c_int64()
+        self._check(self.lib.cfust_last_rescued(self.h, ctypes.byref(v)))
+        return v.value
+
+
+def unpack_e4(e4, r):
+    """[.., r(r+1)/2, n] packed lower triangle -> [.., n, r, r] symmetric (numpy)."""
+    e4 = np.asarray(e4)
+    lead = e4.shape[:-2]
+    n = e4.shape[-1]
+    full = np.zeros(lead + (n, r, r))
+    for t in range(r):
+        for h in range(t + 1):
+            v = e4[..., t * (t + 1) // 2 + h, :]
+            full[..., :, t, h] = v
+            full[..., :, h, t] = v
+    return full

@@ -1,0 +1,646 @@
+// Host side of the C ABI declared in include/cfust.h: context, argument
+// checks, device buffers, and the EM driver (Section 2 outline; Algorithms
+// 2-4) that chains the kernels on the context's stream.
+#include <math.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <string>
+#include <vector>
+
+#include "cfust_internal.cuh"
+
+using namespace cfust;
+
+struct cfust_ctx {
+  int device = 0;
+  cudaStream_t stream = nullptr;
+  cfust_opts opts{};
+  LatticeDev lat{};
+  std::string err;
+
+  int g = 0, p = 0, r = 0;
+  int64_t n_cap = 0;       // observations the pair buffers hold
+  int nb_cap = 0;          // posterior blocks the partial buffers hold
+
+  double *d_params = nullptr;
+  CompT<double> *d_c64 = nullptr;
+  CompT<float> *d_c32 = nullptr;
+  double *d_chi64 = nullptr;
+  float *d_chi32 = nullptr;
+  int *d_status = nullptr;      // [0] error bits, [1] EM iteration counter
+  unsigned *d_rescue_cnt = nullptr;
+  double *d_ll = nullptr;
+  double *d_trace = nullptr;
+  int trace_cap = 0;
+  unsigned long long *d_rescue = nullptr;
+  double *d_partials = nullptr;
+  double *d_llpart = nullptr;
+  void *d_logf = nullptr, *d_e1 = nullptr, *d_e2 = nullptr, *d_e3 = nullptr, *d_e4 = nullptr;
+
+  cudaStream_t cap_stream = nullptr;  // private stream for graph capture
+  cudaEvent_t ev_sweep[2] = {nullptr, nullptr};
+  bool sweep_recorded = false;
+  cudaGraphExec_t gexec = nullptr;
+  const double *graph_Y = nullptr;
+  int64_t graph_n = 0;
+
+  // stepwise fit state
+  const double *fit_Y = nullptr;
+  int64_t fit_n = 0;
+  int fit_done = 0;
+  bool fit_open = false;
+};
+
+namespace {
+
+thread_local std::string g_create_error;
+
+struct DeviceGuard {
+  int prev = -1;
+  explicit DeviceGuard(int dev) {
+    if (cudaGetDevice(&prev) != cudaSuccess) prev = -1;
+    if (prev != dev) cudaSetDevice(dev);
+  }
+  ~DeviceGuard() {
+    int cur = -1;
+    if (prev >= 0 && cudaGetDevice(&cur) == cudaSuccess && cur != prev) cudaSetDevice(prev);
+  }
+};
+
+cfust_status fail(cfust_ctx *c, cfust_status s, const std::string &msg) {
+  if (c) c->err = msg;
+  return s;
+}
+
+cfust_status cuda_fail(cfust_ctx *c, cudaError_t e, const char *where) {
+  return fail(c, e == cudaErrorMemoryAllocation ? CFUST_ENOMEM : CFUST_ECUDA,
+              std::string(where) + ": " + cudaGetErrorString(e));
+}
+
+#define CF_CUDA(c, call)                                    \
+  do {                                                      \
+    cudaError_t e_ = (call);                                \
+    if (e_ != cudaSuccess) return cuda_fail((c), e_, #call); \
+  } while (0)
+
+template <typename P>
+cudaError_t realloc_dev(P **ptr, size_t bytes) {
+  if (*ptr) cudaFree(*ptr);
+  *ptr = nullptr;
+  if (bytes == 0) return cudaSuccess;
+  return cudaMalloc(reinterpret_cast<void **>(ptr), bytes);
+}
+
+size_t elem_size(const cfust_ctx *c) { return c->opts.precision == CFUST_FP64 ? 8 : 4; }
+
+void drop_graph(cfust_ctx *c) {
+  if (c->gexec) cudaGraphExecDestroy(c->gexec);
+  c->gexec = nullptr;
+  c->graph_Y = nullptr;
+  c->graph_n = 0;
+}
+
+// (Re)allocate every device buffer for shapes (g, p, r) and n observations.
+cfust_status ensure(cfust_ctx *c, int g, int p, int r, int64_t n) {
+  const int N = c->lat.n;
+  if (g != c->g || p != c->p || r != c->r) {
+    drop_graph(c);
+    CF_CUDA(c, realloc_dev(&c->d_params, sizeof(double) * param_block_size(g, p, r)));
+    CF_CUDA(c, realloc_dev(&c->d_c64, sizeof(CompT<double>) * g));
+    CF_CUDA(c, realloc_dev(&c->d_c32, sizeof(CompT<float>) * g));
+    CF_CUDA(c, realloc_dev(&c->d_chi64, sizeof(double) * 2 * (size_t)N * g));
+    CF_CUDA(c, realloc_dev(&c->d_chi32, sizeof(float) * 2 * (size_t)N * g));
+    c->g = g;
+    c->p = p;
+    c->r = r;
+    c->n_cap = 0;
+    c->nb_cap = 0;
+  }
+  if (!c->d_status) {
+    CF_CUDA(c, cudaMalloc(&c->d_status, 2 * sizeof(int)));
+    CF_CUDA(c, cudaMalloc(&c->d_rescue_cnt, sizeof(unsigned)));
+    CF_CUDA(c, cudaMalloc(&c->d_ll, sizeof(double)));
+    CF_CUDA(c, cudaMemset(c->d_rescue_cnt, 0, sizeof(unsigned)));
+  }
+  const int nb = posterior_nblocks(n);
+  if (nb > c->nb_cap) {
+    drop_graph(c);
+    CF_CUDA(c, realloc_dev(&c->d_partials, sizeof(double) * (size_t)nb * g * sums_width(p, r)));
+    CF_CUDA(c, realloc_dev(&c->d_llpart, sizeof(double) * (size_t)nb));
+    c->nb_cap = nb;
+  }
+  if (n > c->n_cap) {
+    drop_graph(c);
+    const size_t es = elem_size(c);
+    const size_t gn = (size_t)g * (size_t)n;
+    const int rp = r * (r + 1) / 2;
+    CF_CUDA(c, realloc_dev(&c->d_rescue, sizeof(unsigned long long) * gn));
+    CF_CUDA(c, realloc_dev(&c->d_logf, es * gn));
+    CF_CUDA(c, realloc_dev(&c->d_e1, es * gn));
+    CF_CUDA(c, realloc_dev(&c->d_e2, es * gn));
+    CF_CUDA(c, realloc_dev(&c->d_e3, es * gn * r));
+    CF_CUDA(c, realloc_dev(&c->d_e4, es * gn * rp));
+    c->n_cap = n;
+  }
+  return CFUST_OK;
+}
+
+cfust_status check_params(cfust_ctx *c, const cfust_params *P) {
+  if (!P) return fail(c, CFUST_EINVAL, "params is NULL");
+  const int g = P->g, p = P->p, r = P->r;
+  if (g < 1 || g > CFUST_GMAX) return fail(c, CFUST_EINVAL, "g out of range");
+  if (p < 1 || p > CFUST_PMAX) return fail(c, CFUST_EINVAL, "p out of range");
+  if (r < 1 || r > CFUST_RMAX) return fail(c, CFUST_EINVAL, "r out of range");
+  if (r + 1 != c->opts.lattice.dim)
+    return fail(c, CFUST_EINVAL, "lattice dimension must equal r + 1");
+  if (!P->pi || !P->mu || !P->Sigma || !P->Delta || !P->nu)
+    return fail(c, CFUST_EINVAL, "a parameter array is NULL");
+  double spi = 0.0;
+  for (int i = 0; i < g; ++i) {
+    if (!(P->pi[i] > 0.0) || !isfinite(P->pi[i])) return fail(c, CFUST_EINVAL, "pi_i must be > 0");
+    spi += P->pi[i];
+    if (!(P->nu[i] > 0.0) || !isfinite(P->nu[i])) return fail(c, CFUST_EINVAL, "nu_i must be > 0");
+    for (int a = 0; a < p; ++a)
+      if (!isfinite(P->mu[i * p + a])) return fail(c, CFUST_EINVAL, "mu not finite");
+    for (int a = 0; a < p * r; ++a)
+      if (!isfinite(P->Delta[(size_t)i * p * r + a])) return fail(c, CFUST_EINVAL, "Delta not finite");
+    const double *S = P->Sigma + (size_t)i * p * p;
+    double L[CFUST_PMAX * CFUST_PMAX];
+    for (int a = 0; a < p; ++a)
+      for (int b = 0; b < p; ++b) {
+        const double v = S[a * p + b], w = S[b * p + a];
+        if (!isfinite(v)) return fail(c, CFUST_EINVAL, "Sigma not finite");
+        if (fabs(v - w) > 1e-12 * (fabs(v) + fabs(w)) + 1e-300)
+          return fail(c, CFUST_EINVAL, "Sigma not symmetric");
+      }
+    for (int j = 0; j < p; ++j) {
+      double s = S[j * p + j];
+      for (int k = 0; k < j; ++k) s -= L[j * p + k] * L[j * p + k];
+      if (!(s > 0.0)) return fail(c, CFUST_ENOTPD, "Sigma not positive definite");
+      L[j * p + j] = sqrt(s);
+      for (int i2 = j + 1; i2 < p; ++i2) {
+        double t = S[i2 * p + j];
+        for (int k = 0; k < j; ++k) t -= L[i2 * p + k] * L[j * p + k];
+        L[i2 * p + j] = t / L[j * p + j];
+      }
+    }
+  }
+  if (fabs(spi - 1.0) > 1e-10) return fail(c, CFUST_EINVAL, "pi must sum to 1");
+  return CFUST_OK;
+}
+
+cfust_status upload_params(cfust_ctx *c, const cfust_params *P) {
+  const int g = P->g, p = P->p, r = P->r;
+  ParamView v = param_view(c->d_params, g, p, r);
+  CF_CUDA(c, cudaMemcpyAsync(v.pi, P->pi, sizeof(double) * g, cudaMemcpyHostToDevice, c->stream));
+  CF_CUDA(c, cudaMemcpyAsync(v.mu, P->mu, sizeof(double) * g * p, cudaMemcpyHostToDevice, c->stream));
+  CF_CUDA(c, cudaMemcpyAsync(v.Sigma, P->Sigma, sizeof(double) * g * p * p, cudaMemcpyHostToDevice,
+                             c->stream));
+  CF_CUDA(c, cudaMemcpyAsync(v.Delta, P->Delta, sizeof(double) * g * p * r, cudaMemcpyHostToDevice,
+                             c->stream));
+  CF_CUDA(c, cudaMemcpyAsync(v.nu, P->nu, sizeof(double) * g, cudaMemcpyHostToDevice, c->stream));
+  return CFUST_OK;
+}
+
+cfust_status download_params(cfust_ctx *c, cfust_params *P) {
+  const int g = P->g, p = P->p, r = P->r;
+  ParamView v = param_view(c->d_params, g, p, r);
+  CF_CUDA(c, cudaMemcpyAsync(P->pi, v.pi, sizeof(double) * g, cudaMemcpyDeviceToHost, c->stream));
+  CF_CUDA(c, cudaMemcpyAsync(P->mu, v.mu, sizeof(double) * g * p, cudaMemcpyDeviceToHost, c->stream));
+  CF_CUDA(c, cudaMemcpyAsync(P->Sigma, v.Sigma, sizeof(double) * g * p * p, cudaMemcpyDeviceToHost,
+                             c->stream));
+  CF_CUDA(c, cudaMemcpyAsync(P->Delta, v.Delta, sizeof(double) * g * p * r, cudaMemcpyDeviceToHost,
+                             c->stream));
+  CF_CUDA(c, cudaMemcpyAsync(P->nu, v.nu, sizeof(double) * g, cudaMemcpyDeviceToHost, c->stream));
+  return CFUST_OK;
+}
+
+cfust_status status_from_bits(cfust_ctx *c, int bits) {
+  if (bits == 0) return CFUST_OK;
+  if (bits & ERR_TIMEOUT) return fail(c, CFUST_ETIMEOUT, "a bounded device wait ran out");
+  if (bits & ERR_NOTPD_OMEGA) return fail(c, CFUST_ENOTPD, "Omega = Sigma + Delta Delta^T not positive definite");
+  if (bits & ERR_NOTPD_LAMBDA) return fail(c, CFUST_ENOTPD, "Lambda = I - Delta^T Omega^-1 Delta not positive definite");
+  if (bits & ERR_NOTPD_S6) return fail(c, CFUST_ENOTPD, "sum of tau e4 not positive definite");
+  if (bits & ERR_NOTPD_SIGMA) return fail(c, CFUST_ENOTPD, "updated Sigma not positive definite");
+  if (bits & ERR_DEGENERATE) return fail(c, CFUST_EDEGENERATE, "a component lost its posterior weight");
+  if (bits & ERR_ZERO_DENSITY) return fail(c, CFUST_ENUMERIC, "an observation has zero density under every component");
+  return fail(c, CFUST_ENUMERIC, "non-finite value in the E-step");
+}
+
+// Read the status word (synchronises) and the rescue count.
+cfust_status finish(cfust_ctx *c) {
+  int bits = 0;
+  CF_CUDA(c, cudaMemcpyAsync(&bits, c->d_status, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+  CF_CUDA(c, cudaStreamSynchronize(c->stream));
+  return status_from_bits(c, bits);
+}
+
+cfust_status check_common(cfust_ctx *c, const double *Y, int64_t n, const cfust_params *P) {
+  if (!c) return CFUST_EINVAL;
+  if (!Y) return fail(c, CFUST_EINVAL, "Y is NULL");
+  if (n < 1) return fail(c, CFUST_EINVAL, "n must be >= 1");
+  if ((uint64_t)n * (uint64_t)(P ? P->g : 1) >= (1ull << 40)) return fail(c, CFUST_EINVAL, "n too large");
+  if (reinterpret_cast<uintptr_t>(Y) % 8 != 0) return fail(c, CFUST_EINVAL, "Y must be 8-byte aligned");
+  return check_params(c, P);
+}
+
+EstepOut ctx_out(cfust_ctx *c) {
+  EstepOut o;
+  o.logf = c->d_logf;
+  o.e1 = c->d_e1;
+  o.e2 = c->d_e2;
+  o.e3 = c->d_e3;
+  o.e4 = c->d_e4;
+  return o;
+}
+
+PosteriorArgs post_args(cfust_ctx *c, const double *Y, int64_t n) {
+  PosteriorArgs a{};
+  a.Y = Y;
+  a.n = n;
+  a.g = c->g;
+  a.p = c->p;
+  a.r = c->r;
+  a.pi = param_view(c->d_params, c->g, c->p, c->r).pi;
+  a.partials = c->d_partials;
+  a.ll_partials = c->d_llpart;
+  a.d_status = c->d_status;
+  a.nblocks = posterior_nblocks(n);
+  return a;
+}
+
+double nu_lo(const cfust_ctx *c) { return c->opts.nu_min > 0 ? c->opts.nu_min : 1.0; }
+double nu_hi(const cfust_ctx *c) { return c->opts.nu_max > 0 ? c->opts.nu_max : 200.0; }
+
+SweepTiming sweep_timing(cfust_ctx *c, bool capturing) {
+  SweepTiming tm;
+  if (c->opts.timing && c->ev_sweep[0]) {
+    tm.start = c->ev_sweep[0];
+    tm.stop = c->ev_sweep[1];
+    tm.capturing = capturing;
+    c->sweep_recorded = true;
+  }
+  return tm;
+}
+
+// One EM iteration on the stream: E-step at the device parameters (yielding
+// their log-likelihood into trace[iter]), then the M-step in place.
+cfust_status enqueue_iteration(cfust_ctx *c, const double *Y, int64_t n, cudaStream_t st) {
+  CF_CUDA(c, launch_precompute(c->d_params, c->g, c->p, c->r, c->lat, c->d_c64, c->d_c32, c->d_chi64,
+                               c->d_chi32, c->d_status, st));
+  CF_CUDA(c, launch_estep(c->opts.precision, Y, n, c->g, c->p, c->r, c->lat, c->d_c64, c->d_c32,
+                          c->d_chi64, c->d_chi32, ctx_out(c), false, c->opts.e2_mode,
+                          c->d_rescue, c->d_rescue_cnt, c->d_status, 0, st,
+                          sweep_timing(c, st == c->cap_stream)));
+  PosteriorArgs a = post_args(c, Y, n);
+  a.logf = c->d_logf;
+  a.e1 = c->d_e1;
+  a.e2 = c->d_e2;
+  a.e3 = c->d_e3;
+  a.e4 = c->d_e4;
+  a.want_sums = true;
+  a.want_ll = true;
+  CF_CUDA(c, launch_posterior(c->opts.precision, a, st));
+  CF_CUDA(c, launch_reduce_ll(c->d_llpart, a.nblocks, c->d_ll, c->d_trace, c->d_status + 1, st));
+  CF_CUDA(c, launch_mstep_finalize(c->d_partials, a.nblocks, c->g, c->p, c->r, n, nu_lo(c), nu_hi(c),
+                                   c->d_params, c->d_status, st));
+  return CFUST_OK;
+}
+
+// Density-only pass: log-likelihood of the device parameters into *d_ll
+// (and trace[iter] when trace is set).
+cfust_status enqueue_loglik(cfust_ctx *c, const double *Y, int64_t n, double *trace) {
+  CF_CUDA(c, launch_precompute(c->d_params, c->g, c->p, c->r, c->lat, c->d_c64, c->d_c32, c->d_chi64,
+                               c->d_chi32, c->d_status, c->stream));
+  EstepOut o{};
+  o.logf = c->d_logf;
+  CF_CUDA(c, launch_estep(c->opts.precision, Y, n, c->g, c->p, c->r, c->lat, c->d_c64, c->d_c32,
+                          c->d_chi64, c->d_chi32, o, true, c->opts.e2_mode,
+                          c->d_rescue, c->d_rescue_cnt, c->d_status, 0, c->stream,
+                          sweep_timing(c, false)));
+  PosteriorArgs a = post_args(c, Y, n);
+  a.logf = c->d_logf;
+  a.want_ll = true;
+  CF_CUDA(c, launch_posterior(c->opts.precision, a, c->stream));
+  CF_CUDA(c, launch_reduce_ll(c->d_llpart, a.nblocks, c->d_ll, trace, c->d_status + 1, c->stream));
+  return CFUST_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+cfust_status cfust_create(cfust_ctx **out, const cfust_opts *o, void *cuda_stream) {
+  g_create_error.clear();
+  if (!out || !o) {
+    g_create_error = "ctx or opts is NULL";
+    return CFUST_EINVAL;
+  }
+  *out = nullptr;
+  const cfust_lattice &L = o->lattice;
+  if (o->precision != CFUST_FP64 && o->precision != CFUST_FP32) {
+    g_create_error = "precision must be CFUST_FP64 or CFUST_FP32";
+    return CFUST_EINVAL;
+  }
+  if (L.n < 32 || L.n > CFUST_NMAX || L.n % 32 != 0) {
+    g_create_error = "lattice points must be a multiple of 32 in [32, CFUST_NMAX]";
+    return CFUST_EINVAL;
+  }
+  if (L.dim < 2 || L.dim > CFUST_RMAX + 1 || !L.z || !L.shift) {
+    g_create_error = "lattice dim must be in [2, CFUST_RMAX + 1] with z and shift given";
+    return CFUST_EINVAL;
+  }
+  if (o->e2_mode != 0 && o->e2_mode != 1) {
+    g_create_error = "e2_mode must be 0 or 1";
+    return CFUST_EINVAL;
+  }
+  if (o->max_iter < 0 || !(o->tol >= 0.0)) {
+    g_create_error = "max_iter must be >= 0 and tol >= 0";
+    return CFUST_EINVAL;
+  }
+  if ((o->nu_min != 0.0 || o->nu_max != 0.0) && !(o->nu_min > 0.0 && o->nu_max > o->nu_min)) {
+    g_create_error = "need 0 < nu_min < nu_max";
+    return CFUST_EINVAL;
+  }
+  cfust_ctx *c = new cfust_ctx();
+  c->opts = *o;
+  c->opts.lattice.z = nullptr;
+  c->opts.lattice.shift = nullptr;
+  c->stream = static_cast<cudaStream_t>(cuda_stream);
+  if (cudaGetDevice(&c->device) != cudaSuccess) {
+    g_create_error = "no CUDA device";
+    delete c;
+    return CFUST_ECUDA;
+  }
+  if (o->timing) {
+    if (cudaEventCreate(&c->ev_sweep[0]) != cudaSuccess || cudaEventCreate(&c->ev_sweep[1]) != cudaSuccess) {
+      g_create_error = "cudaEventCreate failed";
+      delete c;
+      return CFUST_ECUDA;
+    }
+  }
+  c->lat.n = L.n;
+  for (int t = 0; t <= CFUST_RMAX; ++t) {
+    if (t < L.dim) {
+      if (!(L.shift[t] >= 0.0 && L.shift[t] < 1.0)) {
+        g_create_error = "lattice shift must lie in [0, 1)";
+        delete c;
+        return CFUST_EINVAL;
+      }
+      int64_t zz = L.z[t] % L.n;
+      if (zz < 0) zz += L.n;
+      c->lat.z[t] = (int)zz;
+      c->lat.step[t] = (int)((32 * zz) % L.n);
+      c->lat.shift[t] = L.shift[t];
+      const double sn = L.shift[t] * (double)L.n;
+      c->lat.sint[t] = (int)floor(sn);
+      c->lat.sfrac[t] = sn - floor(sn);
+    } else {
+      c->lat.z[t] = 0;
+      c->lat.step[t] = 0;
+      c->lat.shift[t] = 0.0;
+      c->lat.sint[t] = 0;
+      c->lat.sfrac[t] = 0.0;
+    }
+  }
+  *out = c;
+  return CFUST_OK;
+}
+
+cfust_status cfust_destroy(cfust_ctx *c) {
+  if (!c) return CFUST_OK;
+  DeviceGuard dg(c->device);
+  drop_graph(c);
+  if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
+  for (cudaEvent_t ev : c->ev_sweep)
+    if (ev) cudaEventDestroy(ev);
+  void *bufs[] = {c->d_params, c->d_c64, c->d_c32, c->d_chi64, c->d_chi32, c->d_status,
+                  c->d_rescue_cnt, c->d_ll, c->d_trace, c->d_rescue, c->d_partials, c->d_llpart,
+                  c->d_logf, c->d_e1, c->d_e2, c->d_e3, c->d_e4};
+  for (void *b : bufs)
+    if (b) cudaFree(b);
+  delete c;
+  return CFUST_OK;
+}
+
+const char *cfust_last_error(cfust_ctx *c) {
+  if (!c) return g_create_error.c_str();
+  return c->err.c_str();
+}
+
+cfust_status cfust_last_rescued(cfust_ctx *c, int64_t *count) {
+  if (!c || !count) return CFUST_EINVAL;
+  DeviceGuard dg(c->device);
+  if (!c->d_rescue_cnt) {
+    *count = 0;
+    return CFUST_OK;
+  }
+  unsigned v = 0;
+  CF_CUDA(c, cudaMemcpyAsync(&v, c->d_rescue_cnt, sizeof(unsigned), cudaMemcpyDeviceToHost, c->stream));
+  CF_CUDA(c, cudaStreamSynchronize(c->stream));
+  *count = (c->opts.precision == CFUST_FP32) ? (int64_t)v : 0;
+  return CFUST_OK;
+}
+
+cfust_status cfust_last_sweep_ms(cfust_ctx *c, float *ms) {
+  if (!c || !ms) return CFUST_EINVAL;
+  if (!c->opts.timing || !c->sweep_recorded) return fail(c, CFUST_EINVAL, "no timed sweep recorded");
+  DeviceGuard dg(c->device);
+  CF_CUDA(c, cudaEventSynchronize(c->ev_sweep[1]));
+  CF_CUDA(c, cudaEventElapsedTime(ms, c->ev_sweep[0], c->ev_sweep[1]));
+  return CFUST_OK;
+}
+
+cfust_status cfust_loglik(cfust_ctx *c, const double *Y, int64_t n, const cfust_params *P,
+                          double *loglik) {
+  cfust_status s = check_common(c, Y, n, P);
+  if (s != CFUST_OK) return s;
+  if (!loglik) return fail(c, CFUST_EINVAL, "loglik is NULL");
+  DeviceGuard dg(c->device);
+  if ((s = ensure(c, P->g, P->p, P->r, n)) != CFUST_OK) return s;
+  if ((s = upload_params(c, P)) != CFUST_OK) return s;
+  CF_CUDA(c, cudaMemsetAsync(c->d_status, 0, 2 * sizeof(int), c->stream));
+  if ((s = enqueue_loglik(c, Y, n, nullptr)) != CFUST_OK) return s;
+  double ll = 0.0;
+  CF_CUDA(c, cudaMemcpyAsync(&ll, c->d_ll, sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+  if ((s = finish(c)) != CFUST_OK) return s;
+  *loglik = ll;
+  return CFUST_OK;
+}
+
+cfust_status cfust_estep(cfust_ctx *c, const double *Y, int64_t n, const cfust_params *P, void *logf,
+                         void *tau, void *e1, void *e2, void *e3, void *e4, double *loglik) {
+  cfust_status s = check_common(c, Y, n, P);
+  if (s != CFUST_OK) return s;
+  if (!tau || !e1 || !e2 || !e3 || !e4) return fail(c, CFUST_EINVAL, "an E-step output is NULL");
+  DeviceGuard dg(c->device);
+  if ((s = ensure(c, P->g, P->p, P->r, n)) != CFUST_OK) return s;
+  if ((s = upload_params(c, P)) != CFUST_OK) return s;
+  CF_CUDA(c, cudaMemsetAsync(c->d_status, 0, 2 * sizeof(int), c->stream));
+  CF_CUDA(c, launch_precompute(c->d_params, c->g, c->p, c->r, c->lat, c->d_c64, c->d_c32, c->d_chi64,
+                               c->d_chi32, c->d_status, c->stream));
+  EstepOut o;
+  o.logf = logf ? logf : c->d_logf;
+  o.e1 = e1;
+  o.e2 = e2;
+  o.e3 = e3;
+  o.e4 = e4;
+  CF_CUDA(c, launch_estep(c->opts.precision, Y, n, c->g, c->p, c->r, c->lat, c->d_c64, c->d_c32,
+                          c->d_chi64, c->d_chi32, o, false, c->opts.e2_mode,
+                          c->d_rescue, c->d_rescue_cnt, c->d_status, 0, c->stream,
+                          sweep_timing(c, false)));
+  PosteriorArgs a = post_args(c, Y, n);
+  a.logf = o.logf;
+  a.tau_out = tau;
+  a.want_ll = true;
+  CF_CUDA(c, launch_posterior(c->opts.precision, a, c->stream));
+  CF_CUDA(c, launch_reduce_ll(c->d_llpart, a.nblocks, c->d_ll, nullptr, nullptr, c->stream));
+  double ll = 0.0;
+  CF_CUDA(c, cudaMemcpyAsync(&ll, c->d_ll, sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+  if ((s = finish(c)) != CFUST_OK) return s;
+  if (loglik) *loglik = ll;
+  return CFUST_OK;
+}
+
+cfust_status cfust_mstep(cfust_ctx *c, const double *Y, int64_t n, const void *tau, const void *e1,
+                         const void *e2, const void *e3, const void *e4, cfust_params *P) {
+  cfust_status s = check_common(c, Y, n, P);
+  if (s != CFUST_OK) return s;
+  if (!tau || !e1 || !e2 || !e3 || !e4) return fail(c, CFUST_EINVAL, "an E-step input is NULL");
+  DeviceGuard dg(c->device);
+  if ((s = ensure(c, P->g, P->p, P->r, n)) != CFUST_OK) return s;
+  if ((s = upload_params(c, P)) != CFUST_OK) return s;
+  CF_CUDA(c, cudaMemsetAsync(c->d_status, 0, 2 * sizeof(int), c->stream));
+  PosteriorArgs a = post_args(c, Y, n);
+  a.tau_in = tau;
+  a.e1 = e1;
+  a.e2 = e2;
+  a.e3 = e3;
+  a.e4 = e4;
+  a.want_sums = true;
+  CF_CUDA(c, launch_posterior(c->opts.precision, a, c->stream));
+  CF_CUDA(c, launch_mstep_finalize(c->d_partials, a.nblocks, c->g, c->p, c->r, n, nu_lo(c), nu_hi(c),
+                                   c->d_params, c->d_status, c->stream));
+  if ((s = finish(c)) != CFUST_OK) return s;
+  if ((s = download_params(c, P)) != CFUST_OK) return s;
+  CF_CUDA(c, cudaStreamSynchronize(c->stream));
+  return CFUST_OK;
+}
+
+cfust_status cfust_fit_begin(cfust_ctx *c, const double *Y, int64_t n, const cfust_params *P) {
+  cfust_status s = check_common(c, Y, n, P);
+  if (s != CFUST_OK) return s;
+  DeviceGuard dg(c->device);
+  if ((s = ensure(c, P->g, P->p, P->r, n)) != CFUST_OK) return s;
+  const int K = c->opts.max_iter;
+  if (K + 1 > c->trace_cap) {
+    CF_CUDA(c, realloc_dev(&c->d_trace, sizeof(double) * (K + 1)));
+    c->trace_cap = K + 1;
+    drop_graph(c);
+  }
+  if ((s = upload_params(c, P)) != CFUST_OK) return s;
+  CF_CUDA(c, cudaMemsetAsync(c->d_status, 0, 2 * sizeof(int), c->stream));
+  if (c->opts.use_graph && (c->graph_Y != Y || c->graph_n != n)) drop_graph(c);
+  if (c->opts.use_graph && !c->gexec && K > 0) {
+    cudaGraph_t gr = nullptr;
+    if (!c->cap_stream) CF_CUDA(c, cudaStreamCreateWithFlags(&c->cap_stream, cudaStreamNonBlocking));
+    CF_CUDA(c, cudaStreamBeginCapture(c->cap_stream, cudaStreamCaptureModeRelaxed));
+    cfust_status cs = enqueue_iteration(c, Y, n, c->cap_stream);
+    cudaError_t ce = cudaStreamEndCapture(c->cap_stream, &gr);
+    if (cs != CFUST_OK) {
+      if (gr) cudaGraphDestroy(gr);
+      return cs;
+    }
+    if (ce != cudaSuccess) return cuda_fail(c, ce, "cudaStreamEndCapture");
+    ce = cudaGraphInstantiate(&c->gexec, gr, 0);
+    cudaGraphDestroy(gr);
+    if (ce != cudaSuccess) {
+      c->gexec = nullptr;
+      return cuda_fail(c, ce, "cudaGraphInstantiate");
+    }
+    c->graph_Y = Y;
+    c->graph_n = n;
+  }
+  c->fit_Y = Y;
+  c->fit_n = n;
+  c->fit_done = 0;
+  c->fit_open = true;
+  return CFUST_OK;
+}
+
+cfust_status cfust_fit_step(cfust_ctx *c, int iters) {
+  if (!c) return CFUST_EINVAL;
+  if (!c->fit_open) return fail(c, CFUST_EINVAL, "cfust_fit_begin has not been called");
+  if (iters < 0 || c->fit_done + iters > c->opts.max_iter)
+    return fail(c, CFUST_EINVAL, "more iterations than opts.max_iter");
+  DeviceGuard dg(c->device);
+  for (int k = 0; k < iters; ++k) {
+    if (c->opts.use_graph) {
+      CF_CUDA(c, cudaGraphLaunch(c->gexec, c->stream));
+    } else {
+      cfust_status s = enqueue_iteration(c, c->fit_Y, c->fit_n, c->stream);
+      if (s != CFUST_OK) return s;
+    }
+    ++c->fit_done;
+  }
+  return CFUST_OK;
+}
+
+cfust_status cfust_fit_end(cfust_ctx *c, cfust_params *P, double *trace, int *iters_done) {
+  if (!c) return CFUST_EINVAL;
+  if (!c->fit_open) return fail(c, CFUST_EINVAL, "cfust_fit_begin has not been called");
+  if (!P || P->g != c->g || P->p != c->p || P->r != c->r)
+    return fail(c, CFUST_EINVAL, "params shape differs from cfust_fit_begin");
+  DeviceGuard dg(c->device);
+  c->fit_open = false;
+  cfust_status s;
+  if ((s = enqueue_loglik(c, c->fit_Y, c->fit_n, c->d_trace)) != CFUST_OK) return s;
+  if ((s = finish(c)) != CFUST_OK) return s;
+  if (trace)
+    CF_CUDA(c, cudaMemcpyAsync(trace, c->d_trace, sizeof(double) * (c->fit_done + 1),
+                               cudaMemcpyDeviceToHost, c->stream));
+  if ((s = download_params(c, P)) != CFUST_OK) return s;
+  CF_CUDA(c, cudaStreamSynchronize(c->stream));
+  if (iters_done) *iters_done = c->fit_done;
+  return CFUST_OK;
+}
+
+cfust_status cfust_fit(cfust_ctx *c, const double *Y, int64_t n, cfust_params *P, double *trace,
+                       int *iters_done) {
+  cfust_status s = cfust_fit_begin(c, Y, n, P);
+  if (s != CFUST_OK) return s;
+  DeviceGuard dg(c->device);
+  const int K = c->opts.max_iter;
+  std::vector<double> hist;
+  for (int k = 0; k < K; ++k) {
+    if ((s = cfust_fit_step(c, 1)) != CFUST_OK) {
+      c->fit_open = false;
+      return s;
+    }
+    if (c->opts.tol > 0.0) {
+      double lk = 0.0;
+      CF_CUDA(c, cudaMemcpyAsync(&lk, c->d_trace + k, sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+      CF_CUDA(c, cudaStreamSynchronize(c->stream));
+      hist.push_back(lk);
+      const size_t m = hist.size();
+      if (m >= 3) {
+        // Algorithm 4 with the standard Aitken asymptote
+        const double l2 = hist[m - 3], l1 = hist[m - 2], l0 = hist[m - 1];
+        const double den = l1 - l2;
+        bool stop = (den == 0.0);
+        if (!stop) {
+          const double acc = (l0 - l1) / den;
+          if (acc != 1.0) {
+            const double linf = l1 + (l0 - l1) / (1.0 - acc);
+            stop = fabs(linf - l0) < c->opts.tol;
+          }
+        }
+        if (stop) break;
+      }
+    }
+  }
+  return cfust_fit_end(c, P, trace, iters_done);
+}
+
+}  // extern "C"

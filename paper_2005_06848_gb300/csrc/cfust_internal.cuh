@@ -1,0 +1,146 @@
+// Internal declarations shared by the CUDA translation units of libcfust.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "cfust.h"
+
+namespace cfust {
+
+constexpr int PMAX = CFUST_PMAX;
+constexpr int RMAX = CFUST_RMAX;
+constexpr int WARP = 32;
+
+// Device-side error bits (OR-ed into the context's status word).
+enum : int {
+  ERR_NOTPD_OMEGA = 1 << 0,
+  ERR_NOTPD_LAMBDA = 1 << 1,
+  ERR_NOTPD_S6 = 1 << 2,
+  ERR_NOTPD_SIGMA = 1 << 3,
+  ERR_NUMERIC = 1 << 4,
+  ERR_DEGENERATE = 1 << 5,
+  ERR_TIMEOUT = 1 << 6,
+  ERR_ZERO_DENSITY = 1 << 7,
+};
+
+// Per-component constants of Eq. 2, produced in double by the precompute
+// kernel and read by the E-step.  The per-pair prologue (z, d, q) always runs
+// in double; the lattice sweep reads L and 1/L_tt in its own precision T.
+//   A = chol(Omega)^{-1} (lower), B = (A Delta)^T, L = chol(Lambda) with
+//   Lambda = I - B B^T = I - Delta^T Omega^{-1} Delta,
+//   c0 = r log 2 + lgamma((nu+p)/2) - lgamma(nu/2) - (p/2) log(nu pi) - (1/2) log|Omega|.
+template <typename T>
+struct CompT {
+  double mu[PMAX];
+  double A[PMAX * PMAX];  // row-major, stride PMAX, lower triangle used
+  double B[RMAX * PMAX];  // r x p, stride PMAX
+  double c0;
+  double nu, mA, mB;      // nu, nu + p, nu + p + 2
+  double psiA;            // digamma((nu + p) / 2)
+  double logmA;           // log(nu + p)
+  T L[RMAX * RMAX];       // r x r, stride RMAX, lower triangle used
+  T Linv[RMAX];           // 1 / L_tt
+};
+
+// Layout of the device parameter block (doubles): pi[g] mu[g][p] Sigma[g][p][p]
+// Delta[g][p][r] nu[g], exactly the host cfust_params arrays back to back.
+struct ParamView {
+  double *pi, *mu, *Sigma, *Delta, *nu;
+};
+
+__host__ __device__ inline int64_t param_block_size(int g, int p, int r) {
+  return (int64_t)g * (2 + p + p * p + p * r);
+}
+
+__host__ __device__ inline ParamView param_view(double *base, int g, int p, int r) {
+  ParamView v;
+  v.pi = base;
+  v.mu = v.pi + g;
+  v.Sigma = v.mu + (int64_t)g * p;
+  v.Delta = v.Sigma + (int64_t)g * p * p;
+  v.nu = v.Delta + (int64_t)g * p * r;
+  return v;
+}
+
+// Number of doubles in one component's M-step sum vector:
+// S1, S2, S3[p], S4[r], S5[p][r], S6[r(r+1)/2], S7[p(p+1)/2], S8.
+__host__ __device__ inline int sums_width(int p, int r) {
+  return 3 + p + r + p * r + r * (r + 1) / 2 + p * (p + 1) / 2;
+}
+
+// ---------------------------------------------------------------------------
+// Launchers (one translation unit each)
+// ---------------------------------------------------------------------------
+
+// Lattice rule on the device.  For coordinate t, frac(k z_t / n + shift_t) * n
+// = m + sfrac_t with the integer m = (k z_t + sint_t) mod n, sint_t = floor(shift_t n)
+// and sfrac_t = shift_t n - sint_t in [0, 1).  The baker-transformed point is
+// u = 1 - |2 (m + sfrac_t)/n - 1|; the sweep needs 1 - u = |2m - n + 2 sfrac_t| / n,
+// which this integer/fraction split keeps accurate in single precision.
+struct LatticeDev {
+  int n;                 // points
+  int z[RMAX + 1];       // generator vector mod n
+  int step[RMAX + 1];    // (32 z) mod n: advance of one lane between its points
+  int sint[RMAX + 1];
+  double sfrac[RMAX + 1];
+  double shift[RMAX + 1];
+};
+
+// Precompute: factorisations, constants and chi-scale tables for every component.
+cudaError_t launch_precompute(const double *d_params, int g, int p, int r, const LatticeDev &lat,
+                              CompT<double> *c64, CompT<float> *c32, double *chi64, float *chi32,
+                              int *d_status, cudaStream_t st);
+
+struct EstepOut {
+  void *logf, *e1, *e2, *e3, *e4;
+};
+
+// Optional CUDA events recorded right before and after the sweep kernel;
+// `capturing` selects external event-record nodes inside a stream capture.
+struct SweepTiming {
+  cudaEvent_t start = nullptr, stop = nullptr;
+  bool capturing = false;
+};
+
+// E-step lattice sweeps for all (i, j).  precision: CFUST_FP64 / CFUST_FP32.
+// In FP32 mode, pairs whose sweep underflows are appended to rescue_list and
+// recomputed in double by the rescue pass (both launched here).
+cudaError_t launch_estep(int precision, const double *Y, int64_t n, int g, int p, int r,
+                         const LatticeDev &lat, const CompT<double> *c64, const CompT<float> *c32,
+                         const double *chi64, const float *chi32, EstepOut out, bool density_only,
+                         int e2_mode, unsigned long long *rescue_list, unsigned *rescue_count, int *d_status,
+                         int pairs_per_warp, cudaStream_t st, SweepTiming tm = SweepTiming());
+
+// Posterior memberships (Eq. 4), log-likelihood partials (Eq. 3) and the
+// M-step sum partials of Section 3.2 for components [0, g).
+struct PosteriorArgs {
+  const double *Y;
+  int64_t n;
+  int g, p, r;
+  const double *pi;       // device, [g]
+  const void *logf;       // [g][n] or NULL when tau_in is given
+  const void *tau_in;     // [g][n] or NULL
+  const void *e1, *e2, *e3, *e4;
+  void *tau_out;          // may be NULL
+  bool want_sums;
+  bool want_ll;
+  double *partials;       // [nblocks][g * K]
+  double *ll_partials;    // [nblocks]
+  int *d_status;
+  int nblocks;
+};
+cudaError_t launch_posterior(int precision, const PosteriorArgs &a, cudaStream_t st);
+int posterior_nblocks(int64_t n);
+
+// Sum the per-block log-likelihood partials in a fixed order: *ll_out = sum,
+// and when trace != NULL also trace[*iter] = sum and ++*iter.
+cudaError_t launch_reduce_ll(const double *ll_partials, int nblocks, double *ll_out,
+                             double *trace, int *iter, cudaStream_t st);
+
+// Algorithm 3: per-component conditional-maximisation update from the sums.
+cudaError_t launch_mstep_finalize(const double *partials, int nblocks, int g, int p, int r,
+                                  int64_t n, double nu_min, double nu_max, double *d_params,
+                                  int *d_status, cudaStream_t st);
+
+}  // namespace cfust

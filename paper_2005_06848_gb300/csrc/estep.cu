@@ -1,0 +1,518 @@
+// E-step lattice sweeps: one warp per (observation j, component i) pair, the
+// lattice points spread over the 32 lanes, warp-shuffle reductions.
+//
+// For pair (i, j), with z = A (y_j - mu_i), d = z^T z, q = B z (Eq. 2; this
+// prologue always in double, one lane per pair, broadcast by shuffles):
+//   log f_ij = c0 - ((nu+p)/2) log(1 + d/nu) + log T_A
+//   pass A: T_A = P(L V > a_A), V ~ t_r(0, I, nu+p),   a_A = -q sqrt((nu+p)/(nu+d))
+//   pass B: T_B, E[V], E[V V^T] for V ~ t_r(0, I, nu+p+2), a_B = -q sqrt((nu+p+2)/(nu+d))
+// each probability by Genz's separation of variables over the shifted lattice:
+//   lim_t = (a_t s - sum_{h<t} L_th z_h) / L_tt,  p_t = Phi(-lim_t),
+//   z_t = -Phi^{-1}(max((1 - u_t) p_t, tiny)),   weight w = prod_t p_t,  V = z / s,
+// s the chi scale of the point (a per-component table).  Both passes share
+// the lattice point and run interleaved in one sweep.  The per-pair outputs
+// are the E-step expectations of the latent gamma W and truncated normal U:
+//   e1 = (nu+p)/(nu+d) T_B/T_A,  sigma = sqrt((nu+d)/(nu+p+2)),
+//   e3 = e1 (q + sigma L E[V]),
+//   e4 = e1 (q q^T + sigma (q (L E[V])^T + (L E[V]) q^T) + sigma^2 L E[V V^T] L^T),
+//   e2 = e1 - log((nu+d)/2) - (nu+p)/(nu+d) + psi((nu+p)/2)     (e2_mode 0)
+//      = E_w[log chi^2_{nu+p}] - log(nu+d)                         (e2_mode 1).
+// Where T_A or T_B is 0, e1..e4 are 0 (their posterior weight is 0).
+//
+// Single precision: the sweep runs in float; a pair whose lattice sum falls
+// below 1e-25 N in either pass (float products near underflow) or whose result
+// is not finite is queued and recomputed in double by rescue_kernel.
+#include <math.h>
+
+#include "cfust_internal.cuh"
+
+namespace cfust {
+
+namespace {
+
+template <typename T>
+struct Num;
+
+template <>
+struct Num<float> {
+  __device__ static float cdf(float x) { return normcdff(x); }
+  __device__ static float icdf(float x) { return normcdfinvf(x); }
+  __device__ static constexpr float tiny() { return 1.17549435e-38f; }
+  __device__ static constexpr float umin() { return 5.9604644775390625e-08f; }  // 2^-24
+  __device__ static float lg(float x) { return logf(x); }
+  __device__ static float lg1p(float x) { return log1pf(x); }
+  __device__ static float sq(float x) { return sqrtf(x); }
+  __device__ static float ab(float x) { return fabsf(x); }
+  __device__ static float mn(float x, float y) { return fminf(x, y); }
+  __device__ static float mx(float x, float y) { return fmaxf(x, y); }
+};
+
+template <>
+struct Num<double> {
+  __device__ static double cdf(double x) { return normcdf(x); }
+  __device__ static double icdf(double x) { return normcdfinv(x); }
+  __device__ static constexpr double tiny() { return 2.2250738585072014e-308; }
+  __device__ static constexpr double umin() { return 1.1102230246251565e-16; }  // 2^-53
+  __device__ static double lg(double x) { return log(x); }
+  __device__ static double lg1p(double x) { return log1p(x); }
+  __device__ static double sq(double x) { return sqrt(x); }
+  __device__ static double ab(double x) { return fabs(x); }
+  __device__ static double mn(double x, double y) { return fmin(x, y); }
+  __device__ static double mx(double x, double y) { return fmax(x, y); }
+};
+
+struct EArgs {
+  const double *Y;
+  int64_t n;
+  int g, p, N;
+  int z[RMAX + 1];
+  int step[RMAX + 1];
+  int sint[RMAX + 1];
+  double sfrac[RMAX + 1];
+  const void *comp;  // CompT<T>[g]
+  const void *chi;   // T[g][2][N]
+  EstepOut out;
+  int e2_mode;
+  int ppw;           // pairs per warp (observations of one component)
+  int staged;
+  unsigned long long *rescue_list;
+  unsigned *rescue_count;
+  int *status;
+};
+
+__host__ __device__ constexpr size_t align16(size_t x) { return (x + 15) & ~size_t(15); }
+
+// ---- bulk async copy global -> shared, completion on an mbarrier ---------
+__device__ __forceinline__ uint32_t smem_addr(const void *p) {
+  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+__device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(count)
+               : "memory");
+  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint64_t *bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)),
+               "r"(bytes)
+               : "memory");
+}
+__device__ __forceinline__ void bulk_copy_g2s(void *dst, const void *src, uint32_t bytes,
+                                              uint64_t *bar) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+          smem_addr(dst)),
+      "l"(src), "r"(bytes), "r"(smem_addr(bar))
+      : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity) {
+  uint32_t done;
+  asm volatile(
+      "{\n .reg .pred P;\n mbarrier.try_wait.parity.shared::cta.b64 P, [%1], %2;\n selp.u32 %0, 1, 0, "
+      "P;\n}\n"
+      : "=r"(done)
+      : "r"(smem_addr(bar)), "r"(parity)
+      : "memory");
+  return done != 0;
+}
+// Bounded wait: gives up after `limit` polls (each poll itself blocks for a
+// hardware-chosen interval), so a lost completion can never hang the GPU.
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, uint32_t parity, int limit) {
+  for (int it = 0; it < limit; ++it)
+    if (mbar_try_wait(bar, parity)) return true;
+  return false;
+}
+
+template <typename T>
+__device__ __forceinline__ T warp_sum(T v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+template <typename OT, typename T>
+__device__ __forceinline__ void store(void *base, int64_t idx, T v) {
+  reinterpret_cast<OT *>(base)[idx] = static_cast<OT>(v);
+}
+
+// Per-pair prologue in double precision: z = A (y - mu), d = z^T z, q = B z and
+// the log of the t_p factor with the constant c0 of Eq. 2.
+template <int R>
+struct Prologue {
+  double d, logt;
+  double q[R];
+};
+
+template <typename T, int R>
+__device__ __forceinline__ Prologue<R> prologue(const EArgs &a, const CompT<T> &c, int64_t j) {
+  Prologue<R> pr;
+  const int p = a.p;
+  const double *yj = a.Y + j * (int64_t)p;
+  double yc[PMAX];
+#pragma unroll
+  for (int k = 0; k < PMAX; ++k) yc[k] = (k < p) ? yj[k] - c.mu[k] : 0.0;
+#pragma unroll
+  for (int t = 0; t < R; ++t) pr.q[t] = 0.0;
+  double d = 0.0;
+#pragma unroll
+  for (int k = 0; k < PMAX; ++k) {
+    if (k < p) {
+      double acc = 0.0;
+#pragma unroll
+      for (int l = 0; l <= k; ++l) acc += c.A[k * PMAX + l] * yc[l];
+      d += acc * acc;
+#pragma unroll
+      for (int t = 0; t < R; ++t) pr.q[t] += c.B[t * PMAX + k] * acc;
+    }
+  }
+  pr.d = d;
+  pr.logt = c.c0 - 0.5 * c.mA * log1p(d / c.nu);
+  return pr;
+}
+
+template <int R>
+__device__ __forceinline__ Prologue<R> shfl_prologue(const Prologue<R> &mine, int src) {
+  Prologue<R> o;
+  o.d = __shfl_sync(0xffffffffu, mine.d, src);
+  o.logt = __shfl_sync(0xffffffffu, mine.logt, src);
+#pragma unroll
+  for (int t = 0; t < R; ++t) o.q[t] = __shfl_sync(0xffffffffu, mine.q[t], src);
+  return o;
+}
+
+// One (i, j) pair on one warp, its prologue given.  Returns true (uniformly
+// over the warp) when `check` is set and the single-precision sweep needs the
+// double rescue; in that case nothing is written.
+template <typename T, typename OT, int R, bool DENS>
+__device__ __forceinline__ bool pair_sweep(const EArgs &a, const CompT<T> &c, const Prologue<R> &pr,
+                                           const T *__restrict__ tA, const T *__restrict__ tB,
+                                           int i, int64_t j, int lane, bool check) {
+  using M = Num<T>;
+  constexpr int RP = R * (R + 1) / 2;
+  const int N = a.N;
+  const double nud64 = c.nu + pr.d;
+  const double fA = sqrt(c.mA / nud64), fB = sqrt(c.mB / nud64);
+  T q[R], aA[R], aB[R];
+#pragma unroll
+  for (int t = 0; t < R; ++t) {
+    q[t] = static_cast<T>(pr.q[t]);
+    aA[t] = static_cast<T>(-pr.q[t] * fA);
+    aB[t] = static_cast<T>(-pr.q[t] * fB);
+  }
+  T Lc[RP], Li[R];
+#pragma unroll
+  for (int t = 0; t < R; ++t) {
+    Li[t] = c.Linv[t];
+#pragma unroll
+    for (int h = 0; h <= t; ++h) Lc[t * (t + 1) / 2 + h] = c.L[t * RMAX + h];
+  }
+
+  // lattice state: m_t = (k z_t + sint_t) mod N for this lane's first point
+  int m[R], stp[R];
+  T two_sf[R];
+#pragma unroll
+  for (int t = 0; t < R; ++t) {
+    m[t] = static_cast<int>(((int64_t)lane * a.z[t + 1] + a.sint[t + 1]) % N);
+    stp[t] = a.step[t + 1];
+    two_sf[t] = static_cast<T>(2.0 * a.sfrac[t + 1]);
+  }
+  const T invN = T(1) / static_cast<T>(N);
+  const T umin = M::umin();
+  const T umax = T(1) - umin;
+  const bool e2lat = (a.e2_mode == 1);
+  const T logmA = static_cast<T>(c.logmA);
+
+  T SA = T(0), SL = T(0), SB = T(0);
+  T M1[R], M2[RP];
+#pragma unroll
+  for (int t = 0; t < R; ++t) M1[t] = T(0);
+#pragma unroll
+  for (int t = 0; t < RP; ++t) M2[t] = T(0);
+
+  for (int k = lane; k < N; k += WARP) {
+    T um[R];  // 1 - u_t of this point: |2 m - N + 2 sfrac| / N, clamped
+#pragma unroll
+    for (int t = 0; t < R; ++t) {
+      const T v = M::ab(static_cast<T>(2 * m[t] - N) + two_sf[t]) * invN;
+      um[t] = M::mn(M::mx(v, umin), umax);
+      m[t] += stp[t];
+      if (m[t] >= N) m[t] -= N;
+    }
+    // pass A: density integral
+    const T sA = tA[k];
+    T wA = T(1);
+    T zA[R];
+#pragma unroll
+    for (int t = 0; t < R; ++t) {
+      T acc = aA[t] * sA;
+#pragma unroll
+      for (int h = 0; h < t; ++h) acc -= Lc[t * (t + 1) / 2 + h] * zA[h];
+      const T pt = M::cdf(-acc * Li[t]);
+      wA *= pt;
+      if (t + 1 < R) zA[t] = -M::icdf(M::mx(um[t] * pt, M::tiny()));
+    }
+    SA += wA;
+    if (e2lat) SL += wA * (logmA + T(2) * M::lg(sA));
+    if (!DENS) {
+      // pass B: the e1 numerator and the truncated moments
+      const T sB = tB[k];
+      const T isB = T(1) / sB;
+      T wB = T(1);
+      T zB[R];
+#pragma unroll
+      for (int t = 0; t < R; ++t) {
+        T acc = aB[t] * sB;
+#pragma unroll
+        for (int h = 0; h < t; ++h) acc -= Lc[t * (t + 1) / 2 + h] * zB[h];
+        const T pt = M::cdf(-acc * Li[t]);
+        wB *= pt;
+        zB[t] = -M::icdf(M::mx(um[t] * pt, M::tiny()));
+      }
+      SB += wB;
+#pragma unroll
+      for (int t = 0; t < R; ++t) {
+        const T wv = wB * (zB[t] * isB);
+#pragma unroll
+        for (int h = 0; h <= t; ++h) M2[t * (t + 1) / 2 + h] += wv * (zB[h] * isB);
+        M1[t] += wv;
+      }
+    }
+  }
+
+  SA = warp_sum(SA);
+  if (e2lat) SL = warp_sum(SL);
+  if (!DENS) {
+    SB = warp_sum(SB);
+#pragma unroll
+    for (int t = 0; t < R; ++t) M1[t] = warp_sum(M1[t]);
+#pragma unroll
+    for (int t = 0; t < RP; ++t) M2[t] = warp_sum(M2[t]);
+  }
+
+  const T logf = static_cast<T>(pr.logt) + M::lg(SA) - M::lg(static_cast<T>(N));
+  if (check) {
+    const T thr = T(1e-25) * static_cast<T>(N);
+    bool need = !(SA >= thr) || !isfinite(logf);
+    if (!DENS) need = need || !(SB >= thr);
+    if (need) return true;
+  }
+  const int64_t n = a.n;
+  const int64_t ij = (int64_t)i * n + j;
+  if (a.out.logf != nullptr && lane == 0) store<OT>(a.out.logf, ij, logf);
+  if (DENS) return false;
+
+  const bool ok = (SA > T(0)) && (SB > T(0));
+  const T ratio = static_cast<T>(c.mA / nud64);
+  const T e1 = ok ? ratio * (SB / SA) : T(0);
+  const T sig = static_cast<T>(sqrt(nud64 / c.mB));
+  const T iSB = ok ? T(1) / SB : T(0);
+  T LEV[R];
+#pragma unroll
+  for (int t = 0; t < R; ++t) {
+    T s = T(0);
+#pragma unroll
+    for (int h = 0; h <= t; ++h) s += Lc[t * (t + 1) / 2 + h] * (M1[h] * iSB);
+    LEV[t] = s;
+  }
+  T e2;
+  if (e2lat)
+    e2 = ok ? SL / SA - static_cast<T>(log(nud64)) : T(0);
+  else
+    e2 = ok ? e1 - static_cast<T>(log(0.5 * nud64) + c.mA / nud64 - c.psiA) : T(0);
+
+  // lane-parallel stores: lane 0 wrote logf; lane 1 e1, lane 2 e2, lanes 3.. e3 then e4
+  if (lane == 1) store<OT>(a.out.e1, ij, e1);
+  if (lane == 2) store<OT>(a.out.e2, ij, e2);
+#pragma unroll
+  for (int t = 0; t < R; ++t) {
+    if (lane == 3 + t) store<OT>(a.out.e3, ((int64_t)i * R + t) * n + j, e1 * (q[t] + sig * LEV[t]));
+  }
+  // E[V V^T] in the L basis: (L EVV L^T)_th = sum_{a<=t} sum_{b<=h} L_ta EVV_ab L_hb
+#pragma unroll
+  for (int t = 0; t < R; ++t) {
+#pragma unroll
+    for (int h = 0; h <= t; ++h) {
+      const int o = 3 + R + t * (t + 1) / 2 + h;
+      if (lane == (o & 31)) {
+        T s = T(0);
+#pragma unroll
+        for (int aa = 0; aa <= t; ++aa) {
+#pragma unroll
+          for (int bb = 0; bb <= h; ++bb) {
+            const T evv = (aa >= bb ? M2[aa * (aa + 1) / 2 + bb] : M2[bb * (bb + 1) / 2 + aa]) * iSB;
+            s += Lc[t * (t + 1) / 2 + aa] * evv * Lc[h * (h + 1) / 2 + bb];
+          }
+        }
+        const T exx = q[t] * q[h] + sig * (q[t] * LEV[h] + LEV[t] * q[h]) + sig * sig * s;
+        store<OT>(a.out.e4, ((int64_t)i * RP + t * (t + 1) / 2 + h) * n + j, e1 * exx);
+      }
+    }
+  }
+  return false;
+}
+
+template <typename T, int R, bool DENS>
+__global__ void __launch_bounds__(256) estep_kernel(EArgs a) {
+  extern __shared__ __align__(128) unsigned char smem[];
+  const int i = blockIdx.y;
+  const int N = a.N;
+  const size_t tab_bytes = a.staged ? (size_t)(DENS ? 1 : 2) * N * sizeof(T) : 0;
+  T *tab = reinterpret_cast<T *>(smem);
+  CompT<T> *cs = reinterpret_cast<CompT<T> *>(smem + align16(tab_bytes));
+  uint64_t *bar = reinterpret_cast<uint64_t *>(smem + align16(tab_bytes) + align16(sizeof(CompT<T>)));
+  const T *gtab = reinterpret_cast<const T *>(a.chi) + (int64_t)i * 2 * N;
+
+  if (a.staged && threadIdx.x == 0) {
+    mbar_init(bar, 1);
+    mbar_expect_tx(bar, static_cast<uint32_t>(tab_bytes));
+    bulk_copy_g2s(tab, gtab, static_cast<uint32_t>(tab_bytes), bar);
+  }
+  const uint32_t *src = reinterpret_cast<const uint32_t *>(reinterpret_cast<const CompT<T> *>(a.comp) + i);
+  uint32_t *dst = reinterpret_cast<uint32_t *>(cs);
+  for (int w = threadIdx.x; w < (int)(sizeof(CompT<T>) / 4); w += blockDim.x) dst[w] = src[w];
+  __syncthreads();
+  if (a.staged) {
+    if (!mbar_wait_bounded(bar, 0, 1 << 22)) {
+      if (threadIdx.x == 0) atomicOr(a.status, ERR_TIMEOUT);
+      return;
+    }
+  }
+  const T *tA = a.staged ? tab : gtab;
+  const T *tB = tA + N;
+
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+  // this warp's observations: ppw consecutive j; lane b computes the double
+  // prologue of the b-th of them, then the warp sweeps them one at a time
+  const int64_t jw0 = ((int64_t)blockIdx.x * nw + warp) * a.ppw;
+  int cnt = 0;
+  if (jw0 < a.n) cnt = (int)((a.n - jw0) < a.ppw ? (a.n - jw0) : a.ppw);
+  Prologue<R> mine;
+  if (lane < cnt) mine = prologue<T, R>(a, *cs, jw0 + lane);
+  const bool check = (sizeof(T) == 4);
+  for (int b = 0; b < cnt; ++b) {
+    const Prologue<R> pr = shfl_prologue<R>(mine, b);
+    const int64_t j = jw0 + b;
+    const bool need = pair_sweep<T, T, R, DENS>(a, *cs, pr, tA, tB, i, j, lane, check);
+    if (need && lane == 0) {
+      const unsigned slot = atomicAdd(a.rescue_count, 1u);
+      a.rescue_list[slot] = (unsigned long long)i * (unsigned long long)a.n + (unsigned long long)j;
+    }
+  }
+}
+
+// Double-precision recomputation of the queued pairs, float outputs.
+template <int R, bool DENS>
+__global__ void __launch_bounds__(256) rescue_kernel(EArgs a) {
+  const unsigned cnt = *a.rescue_count;
+  const int lane = threadIdx.x & 31;
+  const unsigned gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const unsigned nwarps = (gridDim.x * blockDim.x) >> 5;
+  const CompT<double> *comp = reinterpret_cast<const CompT<double> *>(a.comp);
+  const double *chi = reinterpret_cast<const double *>(a.chi);
+  for (unsigned w = gw; w < cnt; w += nwarps) {
+    const unsigned long long id = a.rescue_list[w];
+    const int i = static_cast<int>(id / (unsigned long long)a.n);
+    const int64_t j = static_cast<int64_t>(id % (unsigned long long)a.n);
+    const double *tA = chi + (int64_t)i * 2 * a.N;
+    const Prologue<R> pr = prologue<double, R>(a, comp[i], j);
+    pair_sweep<double, float, R, DENS>(a, comp[i], pr, tA, tA + a.N, i, j, lane, false);
+  }
+}
+
+template <typename T, int R, bool DENS>
+cudaError_t launch_r(EArgs a, int g, int64_t n, cudaStream_t st, bool fp32,
+                     const CompT<double> *c64, const double *chi64, SweepTiming tm) {
+  const size_t tab_bytes = (size_t)(DENS ? 1 : 2) * a.N * sizeof(T);
+  a.staged = tab_bytes <= 160u * 1024u ? 1 : 0;
+  const size_t smem = (a.staged ? align16(tab_bytes) : 0) + align16(sizeof(CompT<T>)) + 16;
+  cudaError_t e = cudaFuncSetAttribute(estep_kernel<T, R, DENS>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  const int64_t per_cta = (int64_t)a.ppw * 8;
+  const int64_t bx = (n + per_cta - 1) / per_cta;
+  if (bx > 0x7fffffff) return cudaErrorInvalidValue;
+  dim3 grid((unsigned)bx, g);
+  if (fp32) {
+    e = cudaMemsetAsync(a.rescue_count, 0, sizeof(unsigned), st);
+    if (e != cudaSuccess) return e;
+  }
+  const unsigned evflag = tm.capturing ? cudaEventRecordExternal : cudaEventRecordDefault;
+  if (tm.start) {
+    e = cudaEventRecordWithFlags(tm.start, st, evflag);
+    if (e != cudaSuccess) return e;
+  }
+  estep_kernel<T, R, DENS><<<grid, 256, smem, st>>>(a);
+  e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  if (tm.stop) {
+    e = cudaEventRecordWithFlags(tm.stop, st, evflag);
+    if (e != cudaSuccess) return e;
+  }
+  if (!fp32) return e;
+  EArgs b = a;
+  b.comp = c64;
+  b.chi = chi64;
+  rescue_kernel<R, DENS><<<152 * 2, 256, 0, st>>>(b);
+  return cudaGetLastError();
+}
+
+template <typename T, bool DENS>
+cudaError_t dispatch_r(int r, EArgs a, int g, int64_t n, cudaStream_t st, bool fp32,
+                       const CompT<double> *c64, const double *chi64, SweepTiming tm) {
+  switch (r) {
+    case 1: return launch_r<T, 1, DENS>(a, g, n, st, fp32, c64, chi64, tm);
+    case 2: return launch_r<T, 2, DENS>(a, g, n, st, fp32, c64, chi64, tm);
+    case 3: return launch_r<T, 3, DENS>(a, g, n, st, fp32, c64, chi64, tm);
+    case 4: return launch_r<T, 4, DENS>(a, g, n, st, fp32, c64, chi64, tm);
+    case 5: return launch_r<T, 5, DENS>(a, g, n, st, fp32, c64, chi64, tm);
+    case 6: return launch_r<T, 6, DENS>(a, g, n, st, fp32, c64, chi64, tm);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+}  // namespace
+
+cudaError_t launch_estep(int precision, const double *Y, int64_t n, int g, int p, int r,
+                         const LatticeDev &lat, const CompT<double> *c64, const CompT<float> *c32,
+                         const double *chi64, const float *chi32, EstepOut out, bool density_only,
+                         int e2_mode, unsigned long long *rescue_list, unsigned *rescue_count, int *d_status,
+                         int pairs_per_warp, cudaStream_t st, SweepTiming tm) {
+  if (n <= 0) return cudaSuccess;
+  EArgs a;
+  a.Y = Y;
+  a.n = n;
+  a.g = g;
+  a.p = p;
+  a.N = lat.n;
+  for (int t = 0; t <= RMAX; ++t) {
+    a.z[t] = lat.z[t];
+    a.step[t] = lat.step[t];
+    a.sint[t] = lat.sint[t];
+    a.sfrac[t] = lat.sfrac[t];
+  }
+  a.out = out;
+  a.e2_mode = e2_mode;
+  if (pairs_per_warp <= 0) {
+    // enough CTAs for about four waves of two CTAs per SM, at most 32 pairs per warp
+    const int64_t target_ctas = 152 * 2 * 4;
+    int64_t ppw = ((int64_t)g * n) / (target_ctas * 8);
+    pairs_per_warp = (int)(ppw < 1 ? 1 : (ppw > 32 ? 32 : ppw));
+  }
+  a.ppw = pairs_per_warp > 32 ? 32 : pairs_per_warp;
+  a.staged = 1;
+  a.rescue_list = rescue_list;
+  a.rescue_count = rescue_count;
+  a.status = d_status;
+  if (precision == CFUST_FP64) {
+    a.comp = c64;
+    a.chi = chi64;
+    return density_only ? dispatch_r<double, true>(r, a, g, n, st, false, c64, chi64, tm)
+                        : dispatch_r<double, false>(r, a, g, n, st, false, c64, chi64, tm);
+  }
+  a.comp = c32;
+  a.chi = chi32;
+  return density_only ? dispatch_r<float, true>(r, a, g, n, st, true, c64, chi64, tm)
+                      : dispatch_r<float, false>(r, a, g, n, st, true, c64, chi64, tm);
+}
+
+}  // namespace cfust

@@ -1,0 +1,372 @@
+// Posterior memberships, log-likelihood and the M-step (Algorithms 2 and 3).
+//
+// posterior_kernel: for every observation j, tau_ij = exp(log pi_i + log f_ij
+// - LSE_i(...)) (Eq. 4) and log f_j = LSE (Eq. 3), then per component the
+// eight sums of Section 3.2 (derived from the expected complete-data
+// log-likelihood):
+//   S1 = sum tau, S2 = sum tau e1, S3 = sum tau e1 y, S4 = sum tau e3,
+//   S5 = sum tau y e3^T, S6 = sum tau e4, S7 = sum tau e1 y y^T, S8 = sum tau (e2 - e1)
+// as block-level segmented reductions in double precision: each block walks
+// its tiles of 64 observations, stages per-observation weight rows and y in
+// shared memory, and every thread owns fixed entries of the sum vectors.  The
+// per-block partials are reduced in a fixed order, so results do not depend
+// on scheduling.
+//
+// mstep_finalize_kernel: one block per component, conditional maximisation
+// (pi, then mu with the old Delta, then Delta, then Sigma, then nu).
+#include <math.h>
+
+#include "cfust_internal.cuh"
+#include "special.cuh"
+
+namespace cfust {
+
+namespace {
+
+constexpr int TJ = 64;       // observations per tile
+constexpr int MAXOWN = 8;    // sum entries per thread
+constexpr int THREADS = 256;
+
+__device__ inline void entry_desc(int ent, int p, int r, int *w, int *y1, int *y2) {
+  const int rp = r * (r + 1) / 2;
+  *y1 = -1;
+  *y2 = -1;
+  if (ent == 0) { *w = 0; return; }                 // S1
+  if (ent == 1) { *w = 1; return; }                 // S2
+  ent -= 2;
+  if (ent < p) { *w = 1; *y1 = ent; return; }       // S3[a]
+  ent -= p;
+  if (ent < r) { *w = 2 + ent; return; }            // S4[t]
+  ent -= r;
+  if (ent < p * r) { *w = 2 + ent % r; *y1 = ent / r; return; }  // S5[a][t]
+  ent -= p * r;
+  if (ent < rp) { *w = 2 + r + ent; return; }       // S6 packed
+  ent -= rp;
+  if (ent < p * (p + 1) / 2) {                      // S7 packed (a, b), b <= a
+    int a = 0;
+    while ((a + 1) * (a + 2) / 2 <= ent) ++a;
+    *w = 1;
+    *y1 = a;
+    *y2 = ent - a * (a + 1) / 2;
+    return;
+  }
+  *w = 2 + r + rp;                                  // S8
+}
+
+template <typename ET>
+__global__ void __launch_bounds__(THREADS) posterior_kernel(PosteriorArgs a, int c0, int c1) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  double *smem = reinterpret_cast<double *>(smem_raw);
+  const int p = a.p, r = a.r, g = a.g;
+  const int rp = r * (r + 1) / 2;
+  const int K = sums_width(p, r);
+  const int WR = 3 + r + rp;
+  const int gc = c1 - c0;
+  const int64_t n = a.n;
+  double *ys = smem;                     // [TJ][p]
+  double *ws = ys + TJ * p;              // [gc][TJ][WR]
+  __shared__ double red[THREADS];
+
+  const ET *logf = reinterpret_cast<const ET *>(a.logf);
+  const ET *tau_in = reinterpret_cast<const ET *>(a.tau_in);
+  const ET *e1 = reinterpret_cast<const ET *>(a.e1);
+  const ET *e2 = reinterpret_cast<const ET *>(a.e2);
+  const ET *e3 = reinterpret_cast<const ET *>(a.e3);
+  const ET *e4 = reinterpret_cast<const ET *>(a.e4);
+  ET *tau_out = reinterpret_cast<ET *>(a.tau_out);
+
+  int own_w[MAXOWN], own_y1[MAXOWN], own_y2[MAXOWN], own_c[MAXOWN];
+  double acc[MAXOWN];
+  const int E = a.want_sums ? gc * K : 0;
+#pragma unroll
+  for (int k = 0; k < MAXOWN; ++k) {
+    const int e = threadIdx.x + k * THREADS;
+    acc[k] = 0.0;
+    own_c[k] = -1;
+    own_w[k] = 0;
+    own_y1[k] = own_y2[k] = -1;
+    if (e < E) {
+      own_c[k] = e / K;
+      entry_desc(e % K, p, r, &own_w[k], &own_y1[k], &own_y2[k]);
+    }
+  }
+  double llacc = 0.0;
+  int bad = 0;
+  const int64_t ntiles = (n + TJ - 1) / TJ;
+  const bool first_chunk = (c0 == 0);
+
+  for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+    const int64_t j0 = tile * TJ;
+    const int nt = (int)((n - j0) < TJ ? (n - j0) : TJ);
+    if (a.want_sums)
+      for (int idx = threadIdx.x; idx < nt * p; idx += THREADS) ys[idx] = a.Y[j0 * p + idx];
+    if (threadIdx.x < nt) {
+      const int jj = threadIdx.x;
+      const int64_t j = j0 + jj;
+      if (logf != nullptr) {
+        double mx = -INFINITY;
+        for (int i = 0; i < g; ++i) mx = fmax(mx, log(a.pi[i]) + (double)logf[(int64_t)i * n + j]);
+        double s = 0.0;
+        for (int i = 0; i < g; ++i) s += exp(log(a.pi[i]) + (double)logf[(int64_t)i * n + j] - mx);
+        const double lse = mx + log(s);
+        if (!isfinite(lse)) bad = 1;
+        llacc += lse;
+        for (int i = 0; i < g; ++i) {
+          const double t = exp(log(a.pi[i]) + (double)logf[(int64_t)i * n + j] - lse);
+          if (tau_out != nullptr && first_chunk) tau_out[(int64_t)i * n + j] = (ET)t;
+          if (a.want_sums && i >= c0 && i < c1) ws[((i - c0) * TJ + jj) * WR] = t;
+        }
+      } else if (a.want_sums) {
+        for (int i = c0; i < c1; ++i) ws[((i - c0) * TJ + jj) * WR] = (double)tau_in[(int64_t)i * n + j];
+      }
+    }
+    __syncthreads();
+    if (a.want_sums) {
+      for (int idx = threadIdx.x; idx < gc * nt; idx += THREADS) {
+        const int ic = idx / nt, jj = idx % nt;
+        const int i = c0 + ic;
+        const int64_t j = j0 + jj;
+        double *row = ws + (ic * TJ + jj) * WR;
+        const double t = row[0];
+        const double v1 = (double)e1[(int64_t)i * n + j];
+        row[1] = t * v1;
+        for (int q = 0; q < r; ++q) row[2 + q] = t * (double)e3[((int64_t)i * r + q) * n + j];
+        for (int q = 0; q < rp; ++q) row[2 + r + q] = t * (double)e4[((int64_t)i * rp + q) * n + j];
+        row[2 + r + rp] = t * ((double)e2[(int64_t)i * n + j] - v1);
+      }
+      __syncthreads();
+#pragma unroll
+      for (int k = 0; k < MAXOWN; ++k) {
+        if (own_c[k] >= 0) {
+          const double *col = ws + own_c[k] * TJ * WR + own_w[k];
+          const int y1 = own_y1[k], y2 = own_y2[k];
+          double s = 0.0;
+          if (y1 < 0) {
+            for (int jj = 0; jj < nt; ++jj) s += col[jj * WR];
+          } else if (y2 < 0) {
+            for (int jj = 0; jj < nt; ++jj) s += col[jj * WR] * ys[jj * p + y1];
+          } else {
+            for (int jj = 0; jj < nt; ++jj) s += col[jj * WR] * ys[jj * p + y1] * ys[jj * p + y2];
+          }
+          acc[k] += s;
+        }
+      }
+    }
+    __syncthreads();
+  }
+
+  if (a.want_sums) {
+    double *dst = a.partials + (int64_t)blockIdx.x * g * K;
+#pragma unroll
+    for (int k = 0; k < MAXOWN; ++k) {
+      const int e = threadIdx.x + k * THREADS;
+      if (e < E) dst[(int64_t)c0 * K + e] = acc[k];
+    }
+  }
+  if (a.want_ll && first_chunk) {
+    red[threadIdx.x] = llacc;
+    __syncthreads();
+    for (int s = THREADS / 2; s > 0; s >>= 1) {
+      if (threadIdx.x < s) red[threadIdx.x] += red[threadIdx.x + s];
+      __syncthreads();
+    }
+    if (threadIdx.x == 0) a.ll_partials[blockIdx.x] = red[0];
+  }
+  if (bad) atomicOr(a.d_status, ERR_ZERO_DENSITY);
+}
+
+__global__ void reduce_ll_kernel(const double *part, int nb, double *out, double *trace, int *iter) {
+  __shared__ double red[256];
+  double s = 0.0;
+  for (int b = threadIdx.x; b < nb; b += 256) s += part[b];
+  red[threadIdx.x] = s;
+  __syncthreads();
+  for (int h = 128; h > 0; h >>= 1) {
+    if (threadIdx.x < h) red[threadIdx.x] += red[threadIdx.x + h];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    *out = red[0];
+    if (trace != nullptr) {
+      trace[*iter] = red[0];
+      *iter += 1;
+    }
+  }
+}
+
+__device__ bool chol_inplace(double *S, int n, int ld) {
+  for (int j = 0; j < n; ++j) {
+    double s = S[j * ld + j];
+    for (int k = 0; k < j; ++k) s -= S[j * ld + k] * S[j * ld + k];
+    if (!(s > 0.0) || !isfinite(s)) return false;
+    const double d = sqrt(s);
+    S[j * ld + j] = d;
+    for (int i = j + 1; i < n; ++i) {
+      double t = S[i * ld + j];
+      for (int k = 0; k < j; ++k) t -= S[i * ld + k] * S[j * ld + k];
+      S[i * ld + j] = t / d;
+    }
+  }
+  return true;
+}
+
+__device__ double nu_equation(double nu, double c) {
+  return log(0.5 * nu) - digamma(0.5 * nu) + 1.0 + c;
+}
+
+// Root of log(nu/2) - psi(nu/2) + 1 + c = 0 in [lo, hi] by bisection; the
+// left side decreases in nu, so the bound is returned when there is no sign change.
+__device__ double solve_nu(double c, double lo, double hi) {
+  if (nu_equation(hi, c) >= 0.0) return hi;
+  if (nu_equation(lo, c) <= 0.0) return lo;
+  for (int it = 0; it < 200; ++it) {
+    const double mid = 0.5 * (lo + hi);
+    if (mid <= lo || mid >= hi) break;
+    if (nu_equation(mid, c) > 0.0) lo = mid; else hi = mid;
+    if (hi - lo <= 2e-16 * hi) break;
+  }
+  return 0.5 * (lo + hi);
+}
+
+__global__ void mstep_finalize_kernel(const double *partials, int nb, int g, int p, int r, int64_t n,
+                                      double nu_min, double nu_max, double *params, int *status) {
+  __shared__ double S[3 + PMAX + RMAX + PMAX * RMAX + RMAX * (RMAX + 1) / 2 + PMAX * (PMAX + 1) / 2];
+  const int i = blockIdx.x;
+  const int K = sums_width(p, r);
+  for (int e = threadIdx.x; e < K; e += blockDim.x) {
+    double s = 0.0;
+    for (int b = 0; b < nb; ++b) s += partials[(int64_t)b * g * K + (int64_t)i * K + e];
+    S[e] = s;
+  }
+  __syncthreads();
+  if (threadIdx.x != 0) return;
+
+  const int rp = r * (r + 1) / 2;
+  const double S1 = S[0], S2 = S[1];
+  const double *S3 = S + 2;
+  const double *S4 = S3 + p;
+  const double *S5 = S4 + r;          // [p][r]
+  const double *S6p = S5 + p * r;     // packed lower
+  const double *S7p = S6p + rp;       // packed lower
+  const double S8 = S7p[p * (p + 1) / 2];
+  if (!(S1 > 1e-10 * (double)n) || !(S2 > 0.0)) {
+    atomicOr(status, ERR_DEGENERATE);
+    return;
+  }
+  ParamView pv = param_view(params, g, p, r);
+  double *mu = pv.mu + (int64_t)i * p;
+  double *Sig = pv.Sigma + (int64_t)i * p * p;
+  double *Del = pv.Delta + (int64_t)i * p * r;
+
+  double m[PMAX], C[PMAX * RMAX], D[PMAX * RMAX], S6[RMAX * RMAX], Lc[RMAX * RMAX];
+  for (int a = 0; a < p; ++a) {
+    double s = S3[a];
+    for (int t = 0; t < r; ++t) s -= Del[a * r + t] * S4[t];
+    m[a] = s / S2;
+  }
+  for (int a = 0; a < p; ++a)
+    for (int t = 0; t < r; ++t) C[a * RMAX + t] = S5[a * r + t] - m[a] * S4[t];
+  for (int t = 0; t < r; ++t)
+    for (int h = 0; h <= t; ++h) S6[t * RMAX + h] = S6[h * RMAX + t] = S6p[t * (t + 1) / 2 + h];
+  for (int t = 0; t < r; ++t)
+    for (int h = 0; h < r; ++h) Lc[t * RMAX + h] = S6[t * RMAX + h];
+  if (!chol_inplace(Lc, r, RMAX)) {
+    atomicOr(status, ERR_NOTPD_S6);
+    return;
+  }
+  // Delta row a solves S6 x = C[a, :]^T
+  for (int a = 0; a < p; ++a) {
+    double x[RMAX];
+    for (int t = 0; t < r; ++t) {
+      double s = C[a * RMAX + t];
+      for (int k = 0; k < t; ++k) s -= Lc[t * RMAX + k] * x[k];
+      x[t] = s / Lc[t * RMAX + t];
+    }
+    for (int t = r - 1; t >= 0; --t) {
+      double s = x[t];
+      for (int k = t + 1; k < r; ++k) s -= Lc[k * RMAX + t] * x[k];
+      x[t] = s / Lc[t * RMAX + t];
+    }
+    for (int t = 0; t < r; ++t) D[a * RMAX + t] = x[t];
+  }
+  double Sn[PMAX * PMAX];
+  for (int a = 0; a < p; ++a)
+    for (int b = 0; b <= a; ++b) {
+      double s = S7p[a * (a + 1) / 2 + b] - S3[a] * m[b] - m[a] * S3[b] + S2 * m[a] * m[b];
+      for (int t = 0; t < r; ++t) s -= C[a * RMAX + t] * D[b * RMAX + t] + D[a * RMAX + t] * C[b * RMAX + t];
+      for (int t = 0; t < r; ++t)
+        for (int h = 0; h < r; ++h) s += D[a * RMAX + t] * S6[t * RMAX + h] * D[b * RMAX + h];
+      Sn[a * PMAX + b] = Sn[b * PMAX + a] = s / S1;
+    }
+  double Lt[PMAX * PMAX];
+  for (int a = 0; a < p * PMAX; ++a) Lt[a] = Sn[a];
+  if (!chol_inplace(Lt, p, PMAX)) {
+    atomicOr(status, ERR_NOTPD_SIGMA);
+    return;
+  }
+  pv.pi[i] = S1 / (double)n;
+  for (int a = 0; a < p; ++a) {
+    mu[a] = m[a];
+    for (int t = 0; t < r; ++t) Del[a * r + t] = D[a * RMAX + t];
+    for (int b = 0; b < p; ++b) Sig[a * p + b] = Sn[a * PMAX + b];
+  }
+  pv.nu[i] = solve_nu(S8 / S1, nu_min, nu_max);
+}
+
+}  // namespace
+
+int posterior_nblocks(int64_t n) {
+  const int64_t ntiles = (n + TJ - 1) / TJ;
+  const int64_t cap = 152 * 4;
+  return (int)(ntiles < cap ? (ntiles > 0 ? ntiles : 1) : cap);
+}
+
+cudaError_t launch_posterior(int precision, const PosteriorArgs &a, cudaStream_t st) {
+  const int K = sums_width(a.p, a.r);
+  const int WR = 3 + a.r + a.r * (a.r + 1) / 2;
+  // components per launch: bounded by the per-thread entries and by shared memory
+  int gc = a.g;
+  if (a.want_sums) {
+    const int by_entries = (MAXOWN * THREADS) / K;
+    const int by_smem = (int)((96 * 1024 - (size_t)TJ * a.p * 8) / ((size_t)TJ * WR * 8));
+    gc = a.g < by_entries ? a.g : by_entries;
+    gc = gc < by_smem ? gc : by_smem;
+    if (gc < 1) return cudaErrorInvalidValue;
+  }
+  for (int c0 = 0; c0 < a.g; c0 += gc) {
+    const int c1 = (c0 + gc < a.g) ? c0 + gc : a.g;
+    const size_t smem = a.want_sums ? ((size_t)TJ * a.p + (size_t)(c1 - c0) * TJ * WR) * 8 : 16;
+    cudaError_t e;
+    if (precision == CFUST_FP64) {
+      e = cudaFuncSetAttribute(posterior_kernel<double>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                               (int)smem);
+      if (e != cudaSuccess) return e;
+      posterior_kernel<double><<<a.nblocks, THREADS, smem, st>>>(a, c0, c1);
+    } else {
+      e = cudaFuncSetAttribute(posterior_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                               (int)smem);
+      if (e != cudaSuccess) return e;
+      posterior_kernel<float><<<a.nblocks, THREADS, smem, st>>>(a, c0, c1);
+    }
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    if (!a.want_sums) break;
+  }
+  return cudaSuccess;
+}
+
+cudaError_t launch_reduce_ll(const double *ll_partials, int nblocks, double *ll_out, double *trace,
+                             int *iter, cudaStream_t st) {
+  reduce_ll_kernel<<<1, 256, 0, st>>>(ll_partials, nblocks, ll_out, trace, iter);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_mstep_finalize(const double *partials, int nblocks, int g, int p, int r, int64_t n,
+                                  double nu_min, double nu_max, double *d_params, int *d_status,
+                                  cudaStream_t st) {
+  mstep_finalize_kernel<<<g, 128, 0, st>>>(partials, nblocks, g, p, r, n, nu_min, nu_max, d_params,
+                                           d_status);
+  return cudaGetLastError();
+}
+
+}  // namespace cfust

@@ -1,0 +1,264 @@
+"""Parity of the CUDA path (through the C ABI) with the FP64 oracle.
+
+Same seeded inputs and the same lattice on both sides.  Tolerances:
+FP64 mode: log f_ij and l(Psi) to 1e-10 relative (|a - b| <= 1e-10 max(1, |b|)),
+tau and e1..e4 to 1e-9; FP32 mode: log f_ij to 1e-4 absolute, tau to 1e-5,
+l(Psi) to 1e-6 relative, parameters after 50 EM iterations to 1e-3 relative.
+"""
+import json
+import os
+
+import numpy as np
+import pytest
+
+from oracle import cfust_oracle as O
+from paper_2005_06848_gb300 import binding, synth
+
+pytestmark = [pytest.mark.gpu, pytest.mark.filterwarnings("ignore::RuntimeWarning")]
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+
+
+def _torch():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    return torch
+
+
+def _problem(workload, n, N, seed=0):
+    Y, labels, truth, init, _, meta = synth.workload(workload, n=n, seed=seed)
+    lat = synth.make_lattice(N, meta["r"] + 1, seed)
+    return Y, truth, init, lat
+
+
+def _gpu_estep(Y, params, lat, precision, e2_mode=0):
+    torch = _torch()
+    with binding.Context(lat, precision=precision, e2_mode=e2_mode) as ctx:
+        Yd = torch.from_numpy(Y).cuda()
+        out = ctx.cfust_estep(Yd, params)
+        res = {k: (v.double().cpu().numpy() if hasattr(v, "cpu") else v) for k, v in out.items()}
+        res["rescued"] = ctx.cfust_last_rescued()
+    return res
+
+
+def _oracle_estep(Y, params, lat, e2_mode=0):
+    U = O.lattice_points(lat.n, lat.z, lat.shift)
+    return O.estep(Y, params, U, e2_mode)
+
+
+def _cmp(name, got, ref, rtol, atol=0.0):
+    got = np.asarray(got, dtype=np.float64)
+    ref = np.asarray(ref, dtype=np.float64)
+    assert got.shape == ref.shape, (name, got.shape, ref.shape)
+    both_inf = np.isinf(got) & np.isinf(ref) & (np.sign(got) == np.sign(ref))
+    err = np.where(both_inf, 0.0, np.abs(got - ref))
+    tol = atol + rtol * np.maximum(1.0, np.abs(np.where(both_inf, 0.0, ref)))
+    worst = float(np.max(err / tol)) if err.size else 0.0
+    assert np.all(err <= tol), f"{name}: worst error / tolerance = {worst:.3g}, max abs err {err.max():.3g}"
+    return float(err.max()) if err.size else 0.0
+
+
+def _compare_estep(G, R, r, fp64):
+    g, n = R["logf"].shape
+    e4_ref = np.stack([R["e4"][:, :, t, h] for t in range(r) for h in range(t + 1)], axis=1)
+    e3_ref = np.transpose(R["e3"], (0, 2, 1))
+    if fp64:
+        _cmp("logf", G["logf"], R["logf"], 1e-10)
+        _cmp("tau", G["tau"], R["tau"], 0, 1e-11)
+        for k in ("e1", "e2"):
+            _cmp(k, G[k], R[k], 1e-9)
+        _cmp("e3", G["e3"], e3_ref, 1e-9)
+        _cmp("e4", G["e4"], e4_ref, 1e-9)
+        assert abs(G["loglik"] - R["loglik"]) <= 1e-10 * abs(R["loglik"])
+    else:
+        _cmp("logf", G["logf"], R["logf"], 0, 1e-4)
+        _cmp("tau", G["tau"], R["tau"], 0, 1e-5)
+        for k in ("e1", "e2"):
+            _cmp(k, G[k], R[k], 2e-4)
+        _cmp("e3", G["e3"], e3_ref, 2e-4)
+        _cmp("e4", G["e4"], e4_ref, 2e-4)
+        assert abs(G["loglik"] - R["loglik"]) <= 1e-6 * abs(R["loglik"])
+
+
+CASES = [
+    # (workload, n, lattice points)
+    ("cfust_p2r2g2_n2000_N1024", 200, 1024),
+    ("cfust_p4r4g3_n100000_N4096", 333, 1024),
+    ("cfust_p3r3g4_n1000000_N2048", 150, 2048),
+    ("cfust_p8r4g6_n1000000_N8192", 70, 1024),
+]
+
+
+@pytest.mark.parametrize("precision", [binding.CFUST_FP64, binding.CFUST_FP32])
+@pytest.mark.parametrize("case", CASES, ids=[c[0].split("_n")[0] for c in CASES])
+def test_estep_matches_oracle(case, precision):
+    wl, n, N = case
+    Y, truth, init, lat = _problem(wl, n, N)
+    R = _oracle_estep(Y, init, lat)
+    G = _gpu_estep(Y, init, lat, precision)
+    _compare_estep(G, R, init.r, precision == binding.CFUST_FP64)
+    assert np.allclose(G["tau"].sum(axis=0), 1.0, atol=1e-12 if precision == 0 else 1e-5)
+
+
+@pytest.mark.parametrize("precision", [binding.CFUST_FP64, binding.CFUST_FP32])
+def test_estep_lattice_e2_mode(precision):
+    Y, truth, init, lat = _problem("cfust_p3r3g4_n1000000_N2048", 90, 1024)
+    R = _oracle_estep(Y, init, lat, e2_mode=1)
+    G = _gpu_estep(Y, init, lat, precision, e2_mode=1)
+    _compare_estep(G, R, init.r, precision == binding.CFUST_FP64)
+
+
+def _edge_params(rng, g, p, r, spread=3.0):
+    P = synth.random_params(rng, g, p, r, spread ** 2, 2, 1.5, 3.0, 12.0)
+    return P
+
+
+@pytest.mark.parametrize("g,p,r,n,N", [
+    (1, 1, 1, 1, 32),        # a single pair, the smallest lattice
+    (1, 1, 1, 37, 64),       # fewer observations than one CTA tile, ragged
+    (2, 16, 6, 40, 256),     # the largest p and r the library takes
+    (3, 5, 2, 129, 96),      # lattice size not a power of two
+    (5, 3, 3, 64, 128),      # exactly one tile
+])
+def test_estep_edge_shapes_fp64(g, p, r, n, N):
+    rng = np.random.default_rng(100 + g * 7 + p)
+    P = _edge_params(rng, g, p, r)
+    Y, _ = synth.sample_cfust(P, n, rng)
+    lat = synth.make_lattice(N, r + 1, 5)
+    R = _oracle_estep(Y, P, lat)
+    G = _gpu_estep(Y, P, lat, binding.CFUST_FP64)
+    _compare_estep(G, R, r, True)
+
+
+def test_estep_full_size_sampled_fp32():
+    """The p=4, r=4, g=3, n=100000, N=4096 workload in the bench's launch
+    configuration; the oracle recomputes 48 sampled observations."""
+    Y, truth, init, lat = _problem("cfust_p4r4g3_n100000_N4096", None, 4096)
+    G = _gpu_estep(Y, init, lat, binding.CFUST_FP32)
+    idx = np.sort(np.random.default_rng(7).choice(Y.shape[0], 48, replace=False))
+    R = _oracle_estep(Y[idx], init, lat)
+    sub = {k: (v[:, idx] if k in ("logf", "tau", "e1", "e2") else v[..., idx]) for k, v in G.items()
+           if k not in ("loglik", "rescued")}
+    _cmp("logf", sub["logf"], R["logf"], 0, 1e-4)
+    _cmp("tau", sub["tau"], R["tau"], 0, 1e-5)
+    _cmp("e1", sub["e1"], R["e1"], 2e-4)
+    assert np.allclose(G["tau"].sum(axis=0), 1.0, atol=1e-5)
+    assert np.all(np.isfinite(G["logf"]))
+
+
+def test_loglik_matches_oracle_fp64():
+    torch = _torch()
+    Y, truth, init, lat = _problem("cfust_p4r4g3_n100000_N4096", 257, 1024)
+    U = O.lattice_points(lat.n, lat.z, lat.shift)
+    ref = O.loglik(Y, init, U)
+    with binding.Context(lat, precision=binding.CFUST_FP64) as ctx:
+        got = ctx.cfust_loglik(torch.from_numpy(Y).cuda(), init)
+    assert abs(got - ref) <= 1e-10 * abs(ref)
+
+
+def test_mstep_matches_oracle_fp64():
+    torch = _torch()
+    Y, truth, init, lat = _problem("cfust_p4r4g3_n100000_N4096", 300, 1024)
+    R = _oracle_estep(Y, init, lat)
+    ref = O.mstep_update(O.mstep_sums(Y, R["tau"], R["e1"], R["e2"], R["e3"], R["e4"]), init, Y.shape[0])
+    r = init.r
+    dev = lambda a: torch.from_numpy(np.ascontiguousarray(a)).cuda()
+    E = dict(tau=dev(R["tau"]), e1=dev(R["e1"]), e2=dev(R["e2"]),
+             e3=dev(np.transpose(R["e3"], (0, 2, 1))),
+             e4=dev(np.stack([R["e4"][:, :, t, h] for t in range(r) for h in range(t + 1)], axis=1)))
+    with binding.Context(lat, precision=binding.CFUST_FP64) as ctx:
+        got = ctx.cfust_mstep(dev(Y), E, init)
+    for a, b, name in zip(got.as_arrays(), ref.as_arrays(), ("pi", "mu", "Sigma", "Delta", "nu")):
+        _cmp(name, a, b, 1e-10)
+
+
+def _fit_gpu(Y, params, lat, precision, iters, use_graph=True):
+    torch = _torch()
+    with binding.Context(lat, precision=precision, max_iter=iters, use_graph=use_graph) as ctx:
+        return ctx.cfust_fit(torch.from_numpy(Y).cuda(), params)
+
+
+def test_fit_fp64_matches_oracle_and_graph_replay_is_bitwise_equal():
+    Y, truth, init, lat = _problem("cfust_p2r2g2_n2000_N1024", 300, 1024)
+    U = O.lattice_points(lat.n, lat.z, lat.shift)
+    ref, ref_trace = O.fit(Y, init, U, 5)
+    got, trace, done = _fit_gpu(Y, init, lat, binding.CFUST_FP64, 5)
+    assert done == 5
+    _cmp("trace", trace, ref_trace, 1e-10)
+    for a, b, name in zip(got.as_arrays(), ref.as_arrays(), ("pi", "mu", "Sigma", "Delta", "nu")):
+        _cmp(name, a, b, 1e-8)
+    got2, trace2, _ = _fit_gpu(Y, init, lat, binding.CFUST_FP64, 5, use_graph=False)
+    assert np.array_equal(trace, trace2)
+    for a, b in zip(got.as_arrays(), got2.as_arrays()):
+        assert np.array_equal(a, b)
+
+
+def _load_golden(name):
+    with open(os.path.join(HERE, "golden", name)) as f:
+        return json.load(f)
+
+
+@pytest.mark.parametrize("golden", ["fit_cfust_p4r4g3_n1500_N1024_it50.json",
+                                    "fit_cfust_p2r2g2_n2000_N1024_it20.json"])
+def test_fit_fp32_parameters_match_oracle_golden(golden):
+    G = _load_golden(golden)
+    Y, truth, init, _, _, meta = synth.workload(G["workload"], n=G["n"])
+    assert np.allclose(Y[:4], G["y_head"], rtol=1e-10, atol=0) and \
+        np.allclose(Y.sum(axis=0), G["y_colsum"], rtol=1e-10, atol=1e-9), "input generator drifted"
+    lat = synth.make_lattice(G["lattice_n"], meta["r"] + 1, G["lattice_seed"])
+    got, trace, done = _fit_gpu(Y, init, lat, binding.CFUST_FP32, G["iters"])
+    assert done == G["iters"]
+    ref_trace = np.array(G["trace"])
+    assert np.all(np.abs(trace - ref_trace) <= 1e-6 * np.abs(ref_trace))
+    for name, a in zip(("pi", "mu", "Sigma", "Delta", "nu"), got.as_arrays()):
+        b = np.array(G["params"][name])
+        scale = np.maximum(np.abs(b), np.max(np.abs(b)) * 1e-2)
+        rel = np.max(np.abs(a - b) / scale)
+        assert rel <= 1e-3, f"{name}: relative error {rel:.3g}"
+    # the same fit in FP64 mode reproduces the oracle far more tightly
+    got64, trace64, _ = _fit_gpu(Y, init, lat, binding.CFUST_FP64, G["iters"])
+    assert np.all(np.abs(trace64 - ref_trace) <= 1e-9 * np.abs(ref_trace))
+
+
+def test_repeat_runs_are_bitwise_identical_fp32():
+    Y, truth, init, lat = _problem("cfust_p3r3g4_n1000000_N2048", 5000, 2048)
+    a = _gpu_estep(Y, init, lat, binding.CFUST_FP32)
+    b = _gpu_estep(Y, init, lat, binding.CFUST_FP32)
+    for k in ("logf", "tau", "e1", "e2", "e3", "e4"):
+        assert np.array_equal(a[k], b[k]), k
+    assert a["loglik"] == b["loglik"]
+
+
+def test_invalid_parameters_are_rejected():
+    torch = _torch()
+    Y, truth, init, lat = _problem("cfust_p2r2g2_n2000_N1024", 50, 1024)
+    Yd = torch.from_numpy(Y).cuda()
+    with binding.Context(lat, precision=binding.CFUST_FP64) as ctx:
+        bad = init.copy(); bad.Sigma[0] = np.array([[1.0, 2.0], [2.0, 1.0]])
+        with pytest.raises(binding.CfustError) as ei:
+            ctx.cfust_loglik(Yd, bad)
+        assert ei.value.status == -2
+        bad = init.copy(); bad.pi[0] += 0.1
+        with pytest.raises(binding.CfustError) as ei:
+            ctx.cfust_loglik(Yd, bad)
+        assert ei.value.status == -1
+        bad = init.copy(); bad.nu[1] = -1.0
+        with pytest.raises(binding.CfustError) as ei:
+            ctx.cfust_loglik(Yd, bad)
+        assert ei.value.status == -1
+        # the context stays usable after errors
+        assert np.isfinite(ctx.cfust_loglik(Yd, init))
+
+
+def test_degenerate_component_is_reported():
+    torch = _torch()
+    Y, truth, init, lat = _problem("cfust_p2r2g2_n2000_N1024", 200, 1024)
+    P = init.copy()
+    P.mu[1] = np.array([1e4, -1e4])     # no observation near component 2
+    P.Delta[1] = 0.0
+    P.nu[1] = 30.0
+    with binding.Context(lat, precision=binding.CFUST_FP64, max_iter=2) as ctx:
+        with pytest.raises(binding.CfustError) as ei:
+            ctx.cfust_fit(torch.from_numpy(Y).cuda(), P)
+        assert ei.value.status == -4
