@@ -203,7 +203,7 @@ def _load_golden(name):
                                     "fit_cfust_p2r2g2_n2000_N1024_it20.json"])
 def test_fit_fp32_parameters_match_oracle_golden(golden):
     G = _load_golden(golden)
-    Y, truth, init, _, _, meta = synth.workload(G["workload"], n=G["n"])
+    Y, _, truth, init, _, meta = synth.workload(G["workload"], n=G["n"])
     assert np.allclose(Y[:4], G["y_head"], rtol=1e-10, atol=0) and \
         np.allclose(Y.sum(axis=0), G["y_colsum"], rtol=1e-10, atol=1e-9), "input generator drifted"
     lat = synth.make_lattice(G["lattice_n"], meta["r"] + 1, G["lattice_seed"])
