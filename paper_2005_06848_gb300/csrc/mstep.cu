@@ -231,6 +231,7 @@ __device__ double solve_nu(double c, double lo, double hi) {
 __global__ void mstep_finalize_kernel(const double *partials, int nb, int g, int p, int r, int64_t n,
                                       double nu_min, double nu_max, double *params, int *status) {
   __shared__ double S[3 + PMAX + RMAX + PMAX * RMAX + RMAX * (RMAX + 1) / 2 + PMAX * (PMAX + 1) / 2];
+  __shared__ double red[128];
   const int i = blockIdx.x;
   const int K = sums_width(p, r);
   for (int e = threadIdx.x; e < K; e += blockDim.x) {
@@ -238,8 +239,20 @@ __global__ void mstep_finalize_kernel(const double *partials, int nb, int g, int
     for (int b = 0; b < nb; ++b) s += partials[(int64_t)b * g * K + (int64_t)i * K + e];
     S[e] = s;
   }
+  // total posterior weight over all components (= n when every tau row sums to 1)
+  double tw = 0.0;
+  for (int q = threadIdx.x; q < g * nb; q += blockDim.x) {
+    const int ic = q / nb, b = q % nb;
+    tw += partials[(int64_t)b * g * K + (int64_t)ic * K];
+  }
+  red[threadIdx.x] = tw;
   __syncthreads();
+  for (int h = 64; h > 0; h >>= 1) {
+    if (threadIdx.x < h) red[threadIdx.x] += red[threadIdx.x + h];
+    __syncthreads();
+  }
   if (threadIdx.x != 0) return;
+  const double total_weight = red[0];
 
   const int rp = r * (r + 1) / 2;
   const double S1 = S[0], S2 = S[1];
@@ -304,7 +317,8 @@ __global__ void mstep_finalize_kernel(const double *partials, int nb, int g, int
     atomicOr(status, ERR_NOTPD_SIGMA);
     return;
   }
-  pv.pi[i] = S1 / (double)n;
+  // pi_i maximises sum_i S1_i log pi_i subject to sum_i pi_i = 1
+  pv.pi[i] = S1 / total_weight;
   for (int a = 0; a < p; ++a) {
     mu[a] = m[a];
     for (int t = 0; t < r; ++t) Del[a * r + t] = D[a * RMAX + t];
