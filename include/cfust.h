@@ -162,6 +162,14 @@ cfust_status cfust_last_rescued(cfust_ctx *ctx, int64_t *count);
  * CFUST_EINVAL when timing is off or nothing has run yet. */
 cfust_status cfust_last_sweep_ms(cfust_ctx *ctx, float *ms);
 
+/* Single-precision normal functions of the lattice sweep, exposed for
+ * verification.  x, out: device float arrays of n elements; stream: a
+ * cudaStream_t (NULL = legacy default stream); stream-ordered.
+ *   which 0: Phi(-x) (this library)      1: Phi^{-1}(x) (this library)
+ *         2: normcdff(-x) (CUDA)          3: normcdfinvf(x) (CUDA)
+ *         4: log Phi(-x) (this library)   5: -Phi^{-1}(exp(x)) (this library, x <= 0) */
+cfust_status cfust_normal_f32(const float *x, float *out, int64_t n, int which, void *stream);
+
 /* Message for the last error on ctx (or on context creation when ctx is NULL). */
 const char *cfust_last_error(cfust_ctx *ctx);
 

@@ -20,7 +20,7 @@ STATUS = {0: "CFUST_OK", -1: "CFUST_EINVAL", -2: "CFUST_ENOTPD", -3: "CFUST_ENUM
 
 EXPORTED = ["cfust_create", "cfust_destroy", "cfust_loglik", "cfust_estep", "cfust_mstep",
             "cfust_fit", "cfust_fit_begin", "cfust_fit_step", "cfust_fit_end",
-            "cfust_last_rescued", "cfust_last_sweep_ms", "cfust_last_error"]
+            "cfust_last_rescued", "cfust_last_sweep_ms", "cfust_normal_f32", "cfust_last_error"]
 
 
 class CfustError(RuntimeError):
@@ -75,6 +75,7 @@ def load(build_if_missing: bool = True) -> ctypes.CDLL:
         "cfust_last_rescued": ([vp, ctypes.POINTER(i64)], ctypes.c_int),
         "cfust_last_sweep_ms": ([vp, ctypes.POINTER(ctypes.c_float)], ctypes.c_int),
         "cfust_last_error": ([vp], ctypes.c_char_p),
+        "cfust_normal_f32": ([vp, vp, i64, ctypes.c_int, vp], ctypes.c_int),
     }
     for name, (args, res) in sig.items():
         fn = getattr(lib, name)
@@ -229,6 +230,21 @@ class Context:
         v = ctypes.c_int64()
         self._check(self.lib.cfust_last_rescued(self.h, ctypes.byref(v)))
         return v.value
+
+
+def cfust_normal_f32(x, which, stream=None):
+    """Evaluate one of the library's single-precision normal functions on a
+    float32 CUDA tensor (see include/cfust.h for `which`)."""
+    import torch
+    lib = load()
+    out = torch.empty_like(x)
+    st = stream if stream is not None else torch.cuda.current_stream()
+    rc = lib.cfust_normal_f32(ctypes.c_void_p(x.data_ptr()), ctypes.c_void_p(out.data_ptr()), x.numel(),
+                              int(which), ctypes.c_void_p(st.cuda_stream))
+    if rc != 0:
+        raise CfustError(rc, "cfust_normal_f32 failed")
+    st.synchronize()
+    return out
 
 
 def unpack_e4(e4, r):

@@ -443,6 +443,13 @@ cfust_status cfust_last_rescued(cfust_ctx *c, int64_t *count) {
   return CFUST_OK;
 }
 
+cfust_status cfust_normal_f32(const float *x, float *out, int64_t n, int which, void *stream) {
+  if (n < 0 || (n > 0 && (!x || !out)) || which < 0 || which > 5) return CFUST_EINVAL;
+  if (launch_normal_f32(x, out, n, which, static_cast<cudaStream_t>(stream)) != cudaSuccess)
+    return CFUST_ECUDA;
+  return CFUST_OK;
+}
+
 cfust_status cfust_last_sweep_ms(cfust_ctx *c, float *ms) {
   if (!c || !ms) return CFUST_EINVAL;
   if (!c->opts.timing || !c->sweep_recorded) return fail(c, CFUST_EINVAL, "no timed sweep recorded");

@@ -112,6 +112,9 @@ cudaError_t launch_estep(int precision, const double *Y, int64_t n, int g, int p
                          int e2_mode, unsigned long long *rescue_list, unsigned *rescue_count, int *d_status,
                          int pairs_per_warp, cudaStream_t st, SweepTiming tm = SweepTiming());
 
+// Elementwise single-precision normal functions (see cfust_normal_f32).
+cudaError_t launch_normal_f32(const float *x, float *out, int64_t n, int which, cudaStream_t st);
+
 // Posterior memberships (Eq. 4), log-likelihood partials (Eq. 3) and the
 // M-step sum partials of Section 3.2 for components [0, g).
 struct PosteriorArgs {

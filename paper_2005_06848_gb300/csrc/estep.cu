@@ -19,12 +19,16 @@
 //      = E_w[log chi^2_{nu+p}] - log(nu+d)                         (e2_mode 1).
 // Where T_A or T_B is 0, e1..e4 are 0 (their posterior weight is 0).
 //
-// Single precision: the sweep runs in float; a pair whose lattice sum falls
-// below 1e-25 N in either pass (float products near underflow) or whose result
-// is not finite is queued and recomputed in double by rescue_kernel.
+// Single precision: the sweep runs in float with this library's normal tail
+// and quantile approximations (normal_f32.cuh); a pair whose lattice sum falls
+// below 1e-20 N in either pass (point weights near the float underflow) or whose
+// result is not finite is queued and recomputed by rescue_kernel, a float sweep
+// that carries every point weight as a logarithm and accumulates with a running
+// maximum.  Double precision calls CUDA's normcdf / normcdfinv.
 #include <math.h>
 
 #include "cfust_internal.cuh"
+#include "normal_f32.cuh"
 
 namespace cfust {
 
@@ -33,15 +37,14 @@ namespace {
 template <typename T>
 struct Num;
 
+// upper(y) = Phi(-y); icdf(x) = Phi^{-1}(x)
 template <>
 struct Num<float> {
-  __device__ static float cdf(float x) { return normcdff(x); }
-  __device__ static float icdf(float x) { return normcdfinvf(x); }
+  __device__ static float upper(float y) { return phi_upper_f32(y); }
+  __device__ static float icdf(float x) { return phi_inv_f32(x); }
   __device__ static constexpr float tiny() { return 1.17549435e-38f; }
   __device__ static constexpr float umin() { return 5.9604644775390625e-08f; }  // 2^-24
   __device__ static float lg(float x) { return logf(x); }
-  __device__ static float lg1p(float x) { return log1pf(x); }
-  __device__ static float sq(float x) { return sqrtf(x); }
   __device__ static float ab(float x) { return fabsf(x); }
   __device__ static float mn(float x, float y) { return fminf(x, y); }
   __device__ static float mx(float x, float y) { return fmaxf(x, y); }
@@ -49,13 +52,11 @@ struct Num<float> {
 
 template <>
 struct Num<double> {
-  __device__ static double cdf(double x) { return normcdf(x); }
+  __device__ static double upper(double y) { return normcdf(-y); }
   __device__ static double icdf(double x) { return normcdfinv(x); }
   __device__ static constexpr double tiny() { return 2.2250738585072014e-308; }
   __device__ static constexpr double umin() { return 1.1102230246251565e-16; }  // 2^-53
   __device__ static double lg(double x) { return log(x); }
-  __device__ static double lg1p(double x) { return log1p(x); }
-  __device__ static double sq(double x) { return sqrt(x); }
   __device__ static double ab(double x) { return fabs(x); }
   __device__ static double mn(double x, double y) { return fmin(x, y); }
   __device__ static double mx(double x, double y) { return fmax(x, y); }
@@ -207,16 +208,18 @@ __device__ __forceinline__ bool pair_sweep(const EArgs &a, const CompT<T> &c, co
     for (int h = 0; h <= t; ++h) Lc[t * (t + 1) / 2 + h] = c.L[t * RMAX + h];
   }
 
-  // lattice state: m_t = (k z_t + sint_t) mod N for this lane's first point
-  int m[R], stp[R];
-  T two_sf[R];
+  // lattice state: fm_t = 2 m_t - N with m_t = (k z_t + sint_t) mod N for this
+  // lane's point; integers below 2^17 are exact in float, so the update is exact
+  T fm[R], fstep[R], two_sf[R];
 #pragma unroll
   for (int t = 0; t < R; ++t) {
-    m[t] = static_cast<int>(((int64_t)lane * a.z[t + 1] + a.sint[t + 1]) % N);
-    stp[t] = a.step[t + 1];
+    const int m0 = static_cast<int>(((int64_t)lane * a.z[t + 1] + a.sint[t + 1]) % N);
+    fm[t] = static_cast<T>(2 * m0 - N);
+    fstep[t] = static_cast<T>(2 * a.step[t + 1]);
     two_sf[t] = static_cast<T>(2.0 * a.sfrac[t + 1]);
   }
-  const T invN = T(1) / static_cast<T>(N);
+  const T fN = static_cast<T>(N);
+  const T invN = T(1) / fN;
   const T umin = M::umin();
   const T umax = T(1) - umin;
   const bool e2lat = (a.e2_mode == 1);
@@ -233,10 +236,10 @@ __device__ __forceinline__ bool pair_sweep(const EArgs &a, const CompT<T> &c, co
     T um[R];  // 1 - u_t of this point: |2 m - N + 2 sfrac| / N, clamped
 #pragma unroll
     for (int t = 0; t < R; ++t) {
-      const T v = M::ab(static_cast<T>(2 * m[t] - N) + two_sf[t]) * invN;
+      const T v = M::ab(fm[t] + two_sf[t]) * invN;
       um[t] = M::mn(M::mx(v, umin), umax);
-      m[t] += stp[t];
-      if (m[t] >= N) m[t] -= N;
+      fm[t] += fstep[t];
+      if (fm[t] >= fN) fm[t] -= T(2) * fN;
     }
     // pass A: density integral
     const T sA = tA[k];
@@ -247,7 +250,7 @@ __device__ __forceinline__ bool pair_sweep(const EArgs &a, const CompT<T> &c, co
       T acc = aA[t] * sA;
 #pragma unroll
       for (int h = 0; h < t; ++h) acc -= Lc[t * (t + 1) / 2 + h] * zA[h];
-      const T pt = M::cdf(-acc * Li[t]);
+      const T pt = M::upper(acc * Li[t]);
       wA *= pt;
       if (t + 1 < R) zA[t] = -M::icdf(M::mx(um[t] * pt, M::tiny()));
     }
@@ -264,7 +267,7 @@ __device__ __forceinline__ bool pair_sweep(const EArgs &a, const CompT<T> &c, co
         T acc = aB[t] * sB;
 #pragma unroll
         for (int h = 0; h < t; ++h) acc -= Lc[t * (t + 1) / 2 + h] * zB[h];
-        const T pt = M::cdf(-acc * Li[t]);
+        const T pt = M::upper(acc * Li[t]);
         wB *= pt;
         zB[t] = -M::icdf(M::mx(um[t] * pt, M::tiny()));
       }
@@ -291,7 +294,7 @@ __device__ __forceinline__ bool pair_sweep(const EArgs &a, const CompT<T> &c, co
 
   const T logf = static_cast<T>(pr.logt) + M::lg(SA) - M::lg(static_cast<T>(N));
   if (check) {
-    const T thr = T(1e-25) * static_cast<T>(N);
+    const T thr = T(1e-20) * static_cast<T>(N);
     bool need = !(SA >= thr) || !isfinite(logf);
     if (!DENS) need = need || !(SB >= thr);
     if (need) return true;
@@ -400,22 +403,193 @@ __global__ void __launch_bounds__(256) estep_kernel(EArgs a) {
   }
 }
 
-// Double-precision recomputation of the queued pairs, float outputs.
+// Log-domain single-precision sweep for the queued pairs.  Each point weight
+// is carried as log w = sum_t log Phi(-lim_t) and accumulated against a
+// running maximum (per lane, then across the warp), so nothing underflows;
+// the conditional draws come from the quantile of exp(log(1 - u_t) + log p_t).
+template <int R, bool DENS>
+__device__ void pair_sweep_log(const EArgs &a, const CompT<float> &c, const Prologue<R> &pr,
+                               const float *__restrict__ tA, const float *__restrict__ tB, int i,
+                               int64_t j, int lane) {
+  constexpr int RP = R * (R + 1) / 2;
+  const int N = a.N;
+  const double nud64 = c.nu + pr.d;
+  const double fA = sqrt(c.mA / nud64), fB = sqrt(c.mB / nud64);
+  float q[R], aA[R], aB[R], Lc[RP], Li[R];
+#pragma unroll
+  for (int t = 0; t < R; ++t) {
+    q[t] = (float)pr.q[t];
+    aA[t] = (float)(-pr.q[t] * fA);
+    aB[t] = (float)(-pr.q[t] * fB);
+    Li[t] = c.Linv[t];
+#pragma unroll
+    for (int h = 0; h <= t; ++h) Lc[t * (t + 1) / 2 + h] = c.L[t * RMAX + h];
+  }
+  float fm[R], fstep[R], two_sf[R];
+#pragma unroll
+  for (int t = 0; t < R; ++t) {
+    const int m0 = (int)(((int64_t)lane * a.z[t + 1] + a.sint[t + 1]) % N);
+    fm[t] = (float)(2 * m0 - N);
+    fstep[t] = (float)(2 * a.step[t + 1]);
+    two_sf[t] = (float)(2.0 * a.sfrac[t + 1]);
+  }
+  const float fN = (float)N, invN = 1.0f / fN;
+  const float umin = 5.9604644775390625e-08f, umax = 1.0f - umin;
+  const bool e2lat = (a.e2_mode == 1);
+  const float logmA = (float)c.logmA;
+
+  float mAx = -INFINITY, SA = 0.f, SL = 0.f;
+  float mBx = -INFINITY, SB = 0.f, M1[R], M2[RP];
+#pragma unroll
+  for (int t = 0; t < R; ++t) M1[t] = 0.f;
+#pragma unroll
+  for (int t = 0; t < RP; ++t) M2[t] = 0.f;
+
+  for (int k = lane; k < N; k += WARP) {
+    float lum[R];
+#pragma unroll
+    for (int t = 0; t < R; ++t) {
+      const float v = fabsf(fm[t] + two_sf[t]) * invN;
+      lum[t] = logf(fminf(fmaxf(v, umin), umax));
+      fm[t] += fstep[t];
+      if (fm[t] >= fN) fm[t] -= 2.0f * fN;
+    }
+    const float sA = tA[k];
+    float lw = 0.f, z[R];
+#pragma unroll
+    for (int t = 0; t < R; ++t) {
+      float acc = aA[t] * sA;
+#pragma unroll
+      for (int h = 0; h < t; ++h) acc -= Lc[t * (t + 1) / 2 + h] * z[h];
+      const float lp = log_phi_upper_f32(acc * Li[t]);
+      lw += lp;
+      if (t + 1 < R) z[t] = neg_quantile_log_f32(lum[t] + lp);
+    }
+    const float lc = e2lat ? logmA + 2.0f * logf(sA) : 0.f;
+    if (lw > mAx) {
+      const float sc = expf(mAx - lw);
+      SA = fmaf(SA, sc, 1.0f);
+      SL = fmaf(SL, sc, lc);
+      mAx = lw;
+    } else {
+      const float e = expf(lw - mAx);
+      SA += e;
+      SL = fmaf(e, lc, SL);
+    }
+    if (!DENS) {
+      const float sB = tB[k];
+      const float isB = 1.0f / sB;
+      float lwb = 0.f;
+#pragma unroll
+      for (int t = 0; t < R; ++t) {
+        float acc = aB[t] * sB;
+#pragma unroll
+        for (int h = 0; h < t; ++h) acc -= Lc[t * (t + 1) / 2 + h] * z[h];
+        const float lp = log_phi_upper_f32(acc * Li[t]);
+        lwb += lp;
+        z[t] = neg_quantile_log_f32(lum[t] + lp);
+      }
+      float sc = 1.0f, e = 1.0f;
+      if (lwb > mBx) {
+        sc = expf(mBx - lwb);
+        mBx = lwb;
+      } else {
+        e = expf(lwb - mBx);
+      }
+      SB = fmaf(SB, sc, e);
+#pragma unroll
+      for (int t = 0; t < R; ++t) {
+        const float vt = z[t] * isB;
+        M1[t] = fmaf(M1[t], sc, e * vt);
+#pragma unroll
+        for (int h = 0; h <= t; ++h) M2[t * (t + 1) / 2 + h] = fmaf(M2[t * (t + 1) / 2 + h], sc, e * vt * (z[h] * isB));
+      }
+    }
+  }
+  // combine lanes against the warp-wide maximum
+  float wmA = mAx;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) wmA = fmaxf(wmA, __shfl_xor_sync(0xffffffffu, wmA, o));
+  const float scA = (mAx == -INFINITY) ? 0.f : expf(mAx - wmA);
+  SA = warp_sum(SA * scA);
+  SL = warp_sum(SL * scA);
+  float wmB = mBx;
+  if (!DENS) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) wmB = fmaxf(wmB, __shfl_xor_sync(0xffffffffu, wmB, o));
+    const float scB = (mBx == -INFINITY) ? 0.f : expf(mBx - wmB);
+    SB = warp_sum(SB * scB);
+#pragma unroll
+    for (int t = 0; t < R; ++t) M1[t] = warp_sum(M1[t] * scB);
+#pragma unroll
+    for (int t = 0; t < RP; ++t) M2[t] = warp_sum(M2[t] * scB);
+  }
+  const double logTA = (double)wmA + log((double)SA) - log((double)N);
+  const float logf_out = (float)(pr.logt + logTA);
+  const int64_t n = a.n;
+  const int64_t ij = (int64_t)i * n + j;
+  if (!isfinite(logf_out) && lane == 0) atomicOr(a.status, ERR_NUMERIC);
+  if (a.out.logf != nullptr && lane == 0) store<float>(a.out.logf, ij, logf_out);
+  if (DENS) return;
+  const double logTB = (double)wmB + log((double)SB) - log((double)N);
+  const bool ok = isfinite(logTA) && isfinite(logTB);
+  const float e1 = ok ? (float)(c.mA / nud64 * exp(logTB - logTA)) : 0.f;
+  const float sig = (float)sqrt(nud64 / c.mB);
+  const float iSB = ok ? 1.0f / SB : 0.f;
+  float LEV[R];
+#pragma unroll
+  for (int t = 0; t < R; ++t) {
+    float sacc = 0.f;
+#pragma unroll
+    for (int h = 0; h <= t; ++h) sacc += Lc[t * (t + 1) / 2 + h] * (M1[h] * iSB);
+    LEV[t] = sacc;
+  }
+  float e2;
+  if (e2lat)
+    e2 = ok ? SL / SA - (float)log(nud64) : 0.f;
+  else
+    e2 = ok ? e1 - (float)(log(0.5 * nud64) + c.mA / nud64 - c.psiA) : 0.f;
+  if (lane == 1) store<float>(a.out.e1, ij, e1);
+  if (lane == 2) store<float>(a.out.e2, ij, e2);
+#pragma unroll
+  for (int t = 0; t < R; ++t)
+    if (lane == 3 + t) store<float>(a.out.e3, ((int64_t)i * R + t) * n + j, e1 * (q[t] + sig * LEV[t]));
+#pragma unroll
+  for (int t = 0; t < R; ++t) {
+#pragma unroll
+    for (int h = 0; h <= t; ++h) {
+      const int o = 3 + R + t * (t + 1) / 2 + h;
+      if (lane == (o & 31)) {
+        float sacc = 0.f;
+#pragma unroll
+        for (int aa = 0; aa <= t; ++aa)
+#pragma unroll
+          for (int bb = 0; bb <= h; ++bb) {
+            const float evv = (aa >= bb ? M2[aa * (aa + 1) / 2 + bb] : M2[bb * (bb + 1) / 2 + aa]) * iSB;
+            sacc += Lc[t * (t + 1) / 2 + aa] * evv * Lc[h * (h + 1) / 2 + bb];
+          }
+        const float exx = q[t] * q[h] + sig * (q[t] * LEV[h] + LEV[t] * q[h]) + sig * sig * sacc;
+        store<float>(a.out.e4, ((int64_t)i * RP + t * (t + 1) / 2 + h) * n + j, e1 * exx);
+      }
+    }
+  }
+}
+
 template <int R, bool DENS>
 __global__ void __launch_bounds__(256) rescue_kernel(EArgs a) {
   const unsigned cnt = *a.rescue_count;
   const int lane = threadIdx.x & 31;
   const unsigned gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const unsigned nwarps = (gridDim.x * blockDim.x) >> 5;
-  const CompT<double> *comp = reinterpret_cast<const CompT<double> *>(a.comp);
-  const double *chi = reinterpret_cast<const double *>(a.chi);
+  const CompT<float> *comp = reinterpret_cast<const CompT<float> *>(a.comp);
+  const float *chi = reinterpret_cast<const float *>(a.chi);
   for (unsigned w = gw; w < cnt; w += nwarps) {
     const unsigned long long id = a.rescue_list[w];
     const int i = static_cast<int>(id / (unsigned long long)a.n);
     const int64_t j = static_cast<int64_t>(id % (unsigned long long)a.n);
-    const double *tA = chi + (int64_t)i * 2 * a.N;
-    const Prologue<R> pr = prologue<double, R>(a, comp[i], j);
-    pair_sweep<double, float, R, DENS>(a, comp[i], pr, tA, tA + a.N, i, j, lane, false);
+    const float *tA = chi + (int64_t)i * 2 * a.N;
+    const Prologue<R> pr = prologue<float, R>(a, comp[i], j);
+    pair_sweep_log<R, DENS>(a, comp[i], pr, tA, tA + a.N, i, j, lane);
   }
 }
 
@@ -449,10 +623,7 @@ cudaError_t launch_r(EArgs a, int g, int64_t n, cudaStream_t st, bool fp32,
     if (e != cudaSuccess) return e;
   }
   if (!fp32) return e;
-  EArgs b = a;
-  b.comp = c64;
-  b.chi = chi64;
-  rescue_kernel<R, DENS><<<152 * 2, 256, 0, st>>>(b);
+  rescue_kernel<R, DENS><<<152 * 2, 256, 0, st>>>(a);
   return cudaGetLastError();
 }
 
@@ -470,7 +641,30 @@ cudaError_t dispatch_r(int r, EArgs a, int g, int64_t n, cudaStream_t st, bool f
   }
 }
 
+__global__ void normal_f32_kernel(const float *x, float *out, int64_t n, int which) {
+  for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < n; k += (int64_t)gridDim.x * blockDim.x) {
+    const float v = x[k];
+    float r;
+    switch (which) {
+      case 0: r = phi_upper_f32(v); break;
+      case 1: r = phi_inv_f32(v); break;
+      case 2: r = normcdff(-v); break;
+      case 3: r = normcdfinvf(v); break;
+      case 4: r = log_phi_upper_f32(v); break;
+      default: r = neg_quantile_log_f32(v); break;
+    }
+    out[k] = r;
+  }
+}
+
 }  // namespace
+
+cudaError_t launch_normal_f32(const float *x, float *out, int64_t n, int which, cudaStream_t st) {
+  if (n <= 0) return cudaSuccess;
+  const int64_t blocks = (n + 255) / 256;
+  normal_f32_kernel<<<(unsigned)(blocks < 152 * 16 ? blocks : 152 * 16), 256, 0, st>>>(x, out, n, which);
+  return cudaGetLastError();
+}
 
 cudaError_t launch_estep(int precision, const double *Y, int64_t n, int g, int p, int r,
                          const LatticeDev &lat, const CompT<double> *c64, const CompT<float> *c32,

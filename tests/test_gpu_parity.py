@@ -262,3 +262,16 @@ def test_degenerate_component_is_reported():
         with pytest.raises(binding.CfustError) as ei:
             ctx.cfust_fit(torch.from_numpy(Y).cuda(), P)
         assert ei.value.status == -4
+
+
+def test_fp32_rescued_pairs_match_oracle():
+    """Pairs whose float lattice weights underflow go through the log-domain
+    rescue sweep; they must meet the same FP32 tolerances as the rest."""
+    Y, truth, init, lat = _problem("cfust_p4r4g3_n100000_N4096", 1200, 512)
+    R = _oracle_estep(Y, init, lat)
+    G = _gpu_estep(Y, init, lat, binding.CFUST_FP32)
+    assert G["rescued"] >= 1, "workload produced no rescued pairs"
+    _compare_estep(G, R, init.r, False)
+    # the rescued pairs are those with tiny T_A or T_B: check them explicitly
+    tiny = R["logf"] < np.percentile(R["logf"], 2)
+    _cmp("logf tail", G["logf"][tiny], R["logf"][tiny], 0, 1e-4)
