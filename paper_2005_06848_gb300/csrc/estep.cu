@@ -37,12 +37,16 @@ namespace {
 template <typename T>
 struct Num;
 
-// upper(y) = Phi(-y); icdf(x) = Phi^{-1}(x)
+// upper_pq(y): p = Phi(-y) and q = 1 - p; neg_quantile(um, u, p, q) =
+// -Phi^{-1}(um p) with u = 1 - um.  The float versions take the quantile on
+// the smaller side (normal_f32.cuh); the double versions follow the plain
+// definition, -Phi^{-1}(max(um p, tiny)).
 template <>
 struct Num<float> {
-  __device__ static float upper(float y) { return phi_upper_f32(y); }
-  __device__ static float icdf(float x) { return phi_inv_f32(x); }
-  __device__ static constexpr float tiny() { return 1.17549435e-38f; }
+  __device__ static void upper_pq(float y, float &p, float &q) { phi_upper_pq_f32(y, p, q); }
+  __device__ static float neg_quantile(float um, float u, float p, float q) {
+    return neg_quantile_f32(um, u, p, q);
+  }
   __device__ static constexpr float umin() { return 5.9604644775390625e-08f; }  // 2^-24
   __device__ static float lg(float x) { return logf(x); }
   __device__ static float ab(float x) { return fabsf(x); }
@@ -52,9 +56,13 @@ struct Num<float> {
 
 template <>
 struct Num<double> {
-  __device__ static double upper(double y) { return normcdf(-y); }
-  __device__ static double icdf(double x) { return normcdfinv(x); }
-  __device__ static constexpr double tiny() { return 2.2250738585072014e-308; }
+  __device__ static void upper_pq(double y, double &p, double &q) {
+    p = normcdf(-y);
+    q = 1.0 - p;
+  }
+  __device__ static double neg_quantile(double um, double, double p, double) {
+    return -normcdfinv(fmax(um * p, 2.2250738585072014e-308));
+  }
   __device__ static constexpr double umin() { return 1.1102230246251565e-16; }  // 2^-53
   __device__ static double lg(double x) { return log(x); }
   __device__ static double ab(double x) { return fabs(x); }
@@ -233,11 +241,12 @@ __device__ __forceinline__ bool pair_sweep(const EArgs &a, const CompT<T> &c, co
   for (int t = 0; t < RP; ++t) M2[t] = T(0);
 
   for (int k = lane; k < N; k += WARP) {
-    T um[R];  // 1 - u_t of this point: |2 m - N + 2 sfrac| / N, clamped
+    T um[R], uu[R];  // 1 - u_t = |2 m - N + 2 sfrac| / N and u_t, both clamped
 #pragma unroll
     for (int t = 0; t < R; ++t) {
-      const T v = M::ab(fm[t] + two_sf[t]) * invN;
-      um[t] = M::mn(M::mx(v, umin), umax);
+      const T av = M::ab(fm[t] + two_sf[t]);
+      um[t] = M::mn(M::mx(av * invN, umin), umax);
+      uu[t] = M::mx((fN - av) * invN, umin);
       fm[t] += fstep[t];
       if (fm[t] >= fN) fm[t] -= T(2) * fN;
     }
@@ -250,9 +259,10 @@ __device__ __forceinline__ bool pair_sweep(const EArgs &a, const CompT<T> &c, co
       T acc = aA[t] * sA;
 #pragma unroll
       for (int h = 0; h < t; ++h) acc -= Lc[t * (t + 1) / 2 + h] * zA[h];
-      const T pt = M::upper(acc * Li[t]);
+      T pt, qt;
+      M::upper_pq(acc * Li[t], pt, qt);
       wA *= pt;
-      if (t + 1 < R) zA[t] = -M::icdf(M::mx(um[t] * pt, M::tiny()));
+      if (t + 1 < R) zA[t] = M::neg_quantile(um[t], uu[t], pt, qt);
     }
     SA += wA;
     if (e2lat) SL += wA * (logmA + T(2) * M::lg(sA));
@@ -267,9 +277,10 @@ __device__ __forceinline__ bool pair_sweep(const EArgs &a, const CompT<T> &c, co
         T acc = aB[t] * sB;
 #pragma unroll
         for (int h = 0; h < t; ++h) acc -= Lc[t * (t + 1) / 2 + h] * zB[h];
-        const T pt = M::upper(acc * Li[t]);
+        T pt, qt;
+        M::upper_pq(acc * Li[t], pt, qt);
         wB *= pt;
-        zB[t] = -M::icdf(M::mx(um[t] * pt, M::tiny()));
+        zB[t] = M::neg_quantile(um[t], uu[t], pt, qt);
       }
       SB += wB;
 #pragma unroll
@@ -403,27 +414,55 @@ __global__ void __launch_bounds__(256) estep_kernel(EArgs a) {
   }
 }
 
-// Log-domain single-precision sweep for the queued pairs.  Each point weight
-// is carried as log w = sum_t log Phi(-lim_t) and accumulated against a
-// running maximum (per lane, then across the warp), so nothing underflows;
-// the conditional draws come from the quantile of exp(log(1 - u_t) + log p_t).
+// One coordinate of the log-domain sweep: log p for p = Phi(-lim) and the
+// conditional draw z = -Phi^{-1}((1 - u) p).  While p is a normal float the
+// direct single-precision forms are used; beyond, log p = log G(lim) - lim^2/2
+// with the square in double and z from the log-domain quantile.
+__device__ __forceinline__ void rescue_dim(double lim, float um, float u, double &lp, float &z) {
+  const float limf = (float)lim;
+  if (limf < 12.0f) {
+    float p, q;
+    phi_upper_pq_f32(limf, p, q);
+    lp = log((double)p);
+    z = neg_quantile_f32(um, u, p, q);
+  } else {
+    float G;
+    if (limf <= 40.0f) {
+      G = nf32::tail_factor(limf);
+    } else {
+      const float ia2 = 1.0f / (limf * limf);
+      G = 0.398942280f / limf * fmaf(ia2, fmaf(3.0f, ia2, -1.0f), 1.0f);
+    }
+    lp = (double)logf(G) - 0.5 * lim * lim;
+    z = neg_quantile_log_f32(logf(um) + (float)lp);
+  }
+}
+
+// Log-domain sweep for the queued pairs.  Each point weight is carried as
+// log w = sum_t log Phi(-lim_t) (limits and log weights in double, the normal
+// functions in float) and accumulated against a running maximum, per lane and
+// then across the warp, so nothing underflows.
 template <int R, bool DENS>
-__device__ void pair_sweep_log(const EArgs &a, const CompT<float> &c, const Prologue<R> &pr,
-                               const float *__restrict__ tA, const float *__restrict__ tB, int i,
+__device__ void pair_sweep_log(const EArgs &a, const CompT<double> &c, const Prologue<R> &pr,
+                               const double *__restrict__ tA, const double *__restrict__ tB, int i,
                                int64_t j, int lane) {
   constexpr int RP = R * (R + 1) / 2;
   const int N = a.N;
   const double nud64 = c.nu + pr.d;
   const double fA = sqrt(c.mA / nud64), fB = sqrt(c.mB / nud64);
-  float q[R], aA[R], aB[R], Lc[RP], Li[R];
+  double aA[R], aB[R], Lc[RP], Li[R];
+  float q[R], Lf[RP];
 #pragma unroll
   for (int t = 0; t < R; ++t) {
     q[t] = (float)pr.q[t];
-    aA[t] = (float)(-pr.q[t] * fA);
-    aB[t] = (float)(-pr.q[t] * fB);
+    aA[t] = -pr.q[t] * fA;
+    aB[t] = -pr.q[t] * fB;
     Li[t] = c.Linv[t];
 #pragma unroll
-    for (int h = 0; h <= t; ++h) Lc[t * (t + 1) / 2 + h] = c.L[t * RMAX + h];
+    for (int h = 0; h <= t; ++h) {
+      Lc[t * (t + 1) / 2 + h] = c.L[t * RMAX + h];
+      Lf[t * (t + 1) / 2 + h] = (float)c.L[t * RMAX + h];
+    }
   }
   float fm[R], fstep[R], two_sf[R];
 #pragma unroll
@@ -436,65 +475,66 @@ __device__ void pair_sweep_log(const EArgs &a, const CompT<float> &c, const Prol
   const float fN = (float)N, invN = 1.0f / fN;
   const float umin = 5.9604644775390625e-08f, umax = 1.0f - umin;
   const bool e2lat = (a.e2_mode == 1);
-  const float logmA = (float)c.logmA;
 
-  float mAx = -INFINITY, SA = 0.f, SL = 0.f;
-  float mBx = -INFINITY, SB = 0.f, M1[R], M2[RP];
+  double mAx = -INFINITY, mBx = -INFINITY;
+  float SA = 0.f, SL = 0.f, SB = 0.f, M1[R], M2[RP];
 #pragma unroll
   for (int t = 0; t < R; ++t) M1[t] = 0.f;
 #pragma unroll
   for (int t = 0; t < RP; ++t) M2[t] = 0.f;
 
   for (int k = lane; k < N; k += WARP) {
-    float lum[R];
+    float um[R], uu[R];
 #pragma unroll
     for (int t = 0; t < R; ++t) {
-      const float v = fabsf(fm[t] + two_sf[t]) * invN;
-      lum[t] = logf(fminf(fmaxf(v, umin), umax));
+      const float av = fabsf(fm[t] + two_sf[t]);
+      um[t] = fminf(fmaxf(av * invN, umin), umax);
+      uu[t] = fmaxf((fN - av) * invN, umin);
       fm[t] += fstep[t];
       if (fm[t] >= fN) fm[t] -= 2.0f * fN;
     }
-    const float sA = tA[k];
-    float lw = 0.f, z[R];
+    const double sA = tA[k];
+    double lw = 0.0;
+    float z[R];
 #pragma unroll
     for (int t = 0; t < R; ++t) {
-      float acc = aA[t] * sA;
+      double acc = aA[t] * sA;
 #pragma unroll
-      for (int h = 0; h < t; ++h) acc -= Lc[t * (t + 1) / 2 + h] * z[h];
-      const float lp = log_phi_upper_f32(acc * Li[t]);
+      for (int h = 0; h < t; ++h) acc -= Lc[t * (t + 1) / 2 + h] * (double)z[h];
+      double lp;
+      rescue_dim(acc * Li[t], um[t], uu[t], lp, z[t]);
       lw += lp;
-      if (t + 1 < R) z[t] = neg_quantile_log_f32(lum[t] + lp);
     }
-    const float lc = e2lat ? logmA + 2.0f * logf(sA) : 0.f;
+    const float lc = e2lat ? (float)(c.logmA + 2.0 * log(sA)) : 0.f;
     if (lw > mAx) {
-      const float sc = expf(mAx - lw);
+      const float sc = (float)exp(mAx - lw);
       SA = fmaf(SA, sc, 1.0f);
       SL = fmaf(SL, sc, lc);
       mAx = lw;
     } else {
-      const float e = expf(lw - mAx);
+      const float e = expf((float)(lw - mAx));
       SA += e;
       SL = fmaf(e, lc, SL);
     }
     if (!DENS) {
-      const float sB = tB[k];
-      const float isB = 1.0f / sB;
-      float lwb = 0.f;
+      const double sB = tB[k];
+      const float isB = (float)(1.0 / sB);
+      double lwb = 0.0;
 #pragma unroll
       for (int t = 0; t < R; ++t) {
-        float acc = aB[t] * sB;
+        double acc = aB[t] * sB;
 #pragma unroll
-        for (int h = 0; h < t; ++h) acc -= Lc[t * (t + 1) / 2 + h] * z[h];
-        const float lp = log_phi_upper_f32(acc * Li[t]);
+        for (int h = 0; h < t; ++h) acc -= Lc[t * (t + 1) / 2 + h] * (double)z[h];
+        double lp;
+        rescue_dim(acc * Li[t], um[t], uu[t], lp, z[t]);
         lwb += lp;
-        z[t] = neg_quantile_log_f32(lum[t] + lp);
       }
       float sc = 1.0f, e = 1.0f;
       if (lwb > mBx) {
-        sc = expf(mBx - lwb);
+        sc = (float)exp(mBx - lwb);
         mBx = lwb;
       } else {
-        e = expf(lwb - mBx);
+        e = expf((float)(lwb - mBx));
       }
       SB = fmaf(SB, sc, e);
 #pragma unroll
@@ -502,36 +542,37 @@ __device__ void pair_sweep_log(const EArgs &a, const CompT<float> &c, const Prol
         const float vt = z[t] * isB;
         M1[t] = fmaf(M1[t], sc, e * vt);
 #pragma unroll
-        for (int h = 0; h <= t; ++h) M2[t * (t + 1) / 2 + h] = fmaf(M2[t * (t + 1) / 2 + h], sc, e * vt * (z[h] * isB));
+        for (int h = 0; h <= t; ++h)
+          M2[t * (t + 1) / 2 + h] = fmaf(M2[t * (t + 1) / 2 + h], sc, e * vt * (z[h] * isB));
       }
     }
   }
   // combine lanes against the warp-wide maximum
-  float wmA = mAx;
+  double wmA = mAx;
 #pragma unroll
-  for (int o = 16; o > 0; o >>= 1) wmA = fmaxf(wmA, __shfl_xor_sync(0xffffffffu, wmA, o));
-  const float scA = (mAx == -INFINITY) ? 0.f : expf(mAx - wmA);
+  for (int o = 16; o > 0; o >>= 1) wmA = fmax(wmA, __shfl_xor_sync(0xffffffffu, wmA, o));
+  const float scA = (mAx == -INFINITY) ? 0.f : (float)exp(mAx - wmA);
   SA = warp_sum(SA * scA);
   SL = warp_sum(SL * scA);
-  float wmB = mBx;
+  double wmB = mBx;
   if (!DENS) {
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) wmB = fmaxf(wmB, __shfl_xor_sync(0xffffffffu, wmB, o));
-    const float scB = (mBx == -INFINITY) ? 0.f : expf(mBx - wmB);
+    for (int o = 16; o > 0; o >>= 1) wmB = fmax(wmB, __shfl_xor_sync(0xffffffffu, wmB, o));
+    const float scB = (mBx == -INFINITY) ? 0.f : (float)exp(mBx - wmB);
     SB = warp_sum(SB * scB);
 #pragma unroll
     for (int t = 0; t < R; ++t) M1[t] = warp_sum(M1[t] * scB);
 #pragma unroll
     for (int t = 0; t < RP; ++t) M2[t] = warp_sum(M2[t] * scB);
   }
-  const double logTA = (double)wmA + log((double)SA) - log((double)N);
+  const double logTA = wmA + log((double)SA) - log((double)N);
   const float logf_out = (float)(pr.logt + logTA);
   const int64_t n = a.n;
   const int64_t ij = (int64_t)i * n + j;
   if (!isfinite(logf_out) && lane == 0) atomicOr(a.status, ERR_NUMERIC);
   if (a.out.logf != nullptr && lane == 0) store<float>(a.out.logf, ij, logf_out);
   if (DENS) return;
-  const double logTB = (double)wmB + log((double)SB) - log((double)N);
+  const double logTB = wmB + log((double)SB) - log((double)N);
   const bool ok = isfinite(logTA) && isfinite(logTB);
   const float e1 = ok ? (float)(c.mA / nud64 * exp(logTB - logTA)) : 0.f;
   const float sig = (float)sqrt(nud64 / c.mB);
@@ -541,7 +582,7 @@ __device__ void pair_sweep_log(const EArgs &a, const CompT<float> &c, const Prol
   for (int t = 0; t < R; ++t) {
     float sacc = 0.f;
 #pragma unroll
-    for (int h = 0; h <= t; ++h) sacc += Lc[t * (t + 1) / 2 + h] * (M1[h] * iSB);
+    for (int h = 0; h <= t; ++h) sacc += Lf[t * (t + 1) / 2 + h] * (M1[h] * iSB);
     LEV[t] = sacc;
   }
   float e2;
@@ -566,7 +607,7 @@ __device__ void pair_sweep_log(const EArgs &a, const CompT<float> &c, const Prol
 #pragma unroll
           for (int bb = 0; bb <= h; ++bb) {
             const float evv = (aa >= bb ? M2[aa * (aa + 1) / 2 + bb] : M2[bb * (bb + 1) / 2 + aa]) * iSB;
-            sacc += Lc[t * (t + 1) / 2 + aa] * evv * Lc[h * (h + 1) / 2 + bb];
+            sacc += Lf[t * (t + 1) / 2 + aa] * evv * Lf[h * (h + 1) / 2 + bb];
           }
         const float exx = q[t] * q[h] + sig * (q[t] * LEV[h] + LEV[t] * q[h]) + sig * sig * sacc;
         store<float>(a.out.e4, ((int64_t)i * RP + t * (t + 1) / 2 + h) * n + j, e1 * exx);
@@ -576,19 +617,18 @@ __device__ void pair_sweep_log(const EArgs &a, const CompT<float> &c, const Prol
 }
 
 template <int R, bool DENS>
-__global__ void __launch_bounds__(256) rescue_kernel(EArgs a) {
+__global__ void __launch_bounds__(256) rescue_kernel(EArgs a, const CompT<double> *comp,
+                                                      const double *chi) {
   const unsigned cnt = *a.rescue_count;
   const int lane = threadIdx.x & 31;
   const unsigned gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const unsigned nwarps = (gridDim.x * blockDim.x) >> 5;
-  const CompT<float> *comp = reinterpret_cast<const CompT<float> *>(a.comp);
-  const float *chi = reinterpret_cast<const float *>(a.chi);
   for (unsigned w = gw; w < cnt; w += nwarps) {
     const unsigned long long id = a.rescue_list[w];
     const int i = static_cast<int>(id / (unsigned long long)a.n);
     const int64_t j = static_cast<int64_t>(id % (unsigned long long)a.n);
-    const float *tA = chi + (int64_t)i * 2 * a.N;
-    const Prologue<R> pr = prologue<float, R>(a, comp[i], j);
+    const double *tA = chi + (int64_t)i * 2 * a.N;
+    const Prologue<R> pr = prologue<double, R>(a, comp[i], j);
     pair_sweep_log<R, DENS>(a, comp[i], pr, tA, tA + a.N, i, j, lane);
   }
 }
@@ -623,7 +663,7 @@ cudaError_t launch_r(EArgs a, int g, int64_t n, cudaStream_t st, bool fp32,
     if (e != cudaSuccess) return e;
   }
   if (!fp32) return e;
-  rescue_kernel<R, DENS><<<152 * 2, 256, 0, st>>>(a);
+  rescue_kernel<R, DENS><<<152 * 2, 256, 0, st>>>(a, c64, chi64);
   return cudaGetLastError();
 }
 

@@ -3,8 +3,9 @@
 // fit_normal_f32.py), plus log-domain variants for pairs whose lattice weights
 // fall below the float range.
 //
-//   phi_upper_f32(y)  = Phi(-y) = P(Z > y)
+//   phi_upper_f32(y)  = Phi(-y) = P(Z > y); phi_upper_pq_f32 also gives Phi(y)
 //   phi_inv_f32(x)    = Phi^{-1}(x), x in (0, 1)
+//   neg_quantile_f32  = -Phi^{-1}(um p), evaluated on the smaller of x, 1 - x
 //   log_phi_upper_f32(y) = log Phi(-y) for any finite y
 //   neg_quantile_log_f32(la) = -Phi^{-1}(exp(la)) for la <= 0, including
 //                              exp(la) far below the float range
@@ -37,13 +38,22 @@ __device__ __forceinline__ float tail_factor(float a) {
 
 }  // namespace nf32
 
-__device__ __forceinline__ float phi_upper_f32(float y) {
+// Phi(-y) and its complement 1 - Phi(-y) = Phi(y), each from the small side.
+__device__ __forceinline__ void phi_upper_pq_f32(float y, float &p, float &q) {
   const float a = fabsf(y);
   const float s = a * a;
   const float e = fmaf(a, a, -s);
   float tail = nf32::tail_factor(a) * expf(-0.5f * s);
   tail = fmaf(-0.5f * e, tail, tail);
-  return (y >= 0.0f) ? tail : 1.0f - tail;
+  const float big = 1.0f - tail;
+  p = (y >= 0.0f) ? tail : big;
+  q = (y >= 0.0f) ? big : tail;
+}
+
+__device__ __forceinline__ float phi_upper_f32(float y) {
+  float p, q;
+  phi_upper_pq_f32(y, p, q);
+  return p;
 }
 
 __device__ __forceinline__ float phi_inv_f32(float x) {
@@ -57,6 +67,15 @@ __device__ __forceinline__ float phi_inv_f32(float x) {
     p = (w < 16.0f) ? nf32::horner(nf32::Q_P1, sw - nf32::Q_S1) : nf32::horner(nf32::Q_P2, sw - nf32::Q_S2);
   }
   return 1.41421356237f * v * p;
+}
+
+// z = -Phi^{-1}(x) for x = um * p, given also u = 1 - um and q = 1 - p; when
+// x > 1/2 the quantile is taken of 1 - x = u + um q, which keeps full relative
+// precision where x itself is within rounding of 1.
+__device__ __forceinline__ float neg_quantile_f32(float um, float u, float p, float q) {
+  const float x = um * p;
+  if (x <= 0.5f) return -phi_inv_f32(fmaxf(x, 1.17549435e-38f));
+  return phi_inv_f32(fmaf(um, q, u));
 }
 
 __device__ __forceinline__ float log_phi_upper_f32(float y) {
@@ -76,7 +95,11 @@ __device__ __forceinline__ float log_phi_upper_f32(float y) {
 }
 
 __device__ __forceinline__ float neg_quantile_log_f32(float la) {
-  if (la > -80.0f) return -phi_inv_f32(fminf(expf(la), 0.99999994f));
+  if (la > -0.693147181f) {
+    // x = exp(la) > 1/2: use 1 - x = -expm1(la) from the small side
+    return phi_inv_f32(-expm1f(la));
+  }
+  if (la > -80.0f) return -phi_inv_f32(expf(la));
   // far tail: z solves log Phi(-z) = la; fixed-point start from
   // z^2 = -2 la - 2 log z - log(2 pi), then Newton steps on log Phi(-z) whose
   // derivative is -1 / (sqrt(2 pi) G(z))
