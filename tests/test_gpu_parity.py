@@ -270,12 +270,12 @@ def test_fp32_rescued_pairs_match_oracle():
     planted at mu_i - c Delta_i 1 put T_A of one component near exp(-145)
     and exp(-274)."""
     Y, truth, init, lat = _problem("cfust_p4r4g3_n100000_N4096", 200, 512)
-    extra = [init.mu[i] - c * init.Delta[i].sum(axis=1) for i in range(init.g) for c in (1.0, 2.0, 4.0)]
+    extra = [init.mu[i] - c * init.Delta[i].sum(axis=1) for i in range(init.g) for c in (2.0, 4.0, 8.0, 16.0)]
     Y = np.ascontiguousarray(np.vstack([Y, np.array(extra)]))
     R = _oracle_estep(Y, init, lat)
     G = _gpu_estep(Y, init, lat, binding.CFUST_FP32)
     assert G["rescued"] >= 2, G["rescued"]
     _compare_estep(G, R, init.r, False)
-    tiny = R["logf"] < -100.0
+    tiny = R["logf"] < -60.0
     assert tiny.sum() >= 2
     _cmp("logf tail", G["logf"][tiny], R["logf"][tiny], 0, 1e-4)
