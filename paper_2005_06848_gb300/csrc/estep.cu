@@ -47,7 +47,9 @@ struct Num<float> {
   __device__ static float neg_quantile(float um, float u, float p, float q) {
     return neg_quantile_f32(um, u, p, q);
   }
-  __device__ static constexpr float umin() { return 5.9604644775390625e-08f; }  // 2^-24
+  // 2^-53, the same clamp as double precision: a normal float, so the small
+  // side of a lattice coordinate keeps its value down to where the oracle clamps
+  __device__ static constexpr float umin() { return 1.1102230246251565e-16f; }
   __device__ static float lg(float x) { return logf(x); }
   __device__ static float ab(float x) { return fabsf(x); }
   __device__ static float mn(float x, float y) { return fminf(x, y); }
@@ -218,18 +220,19 @@ __device__ __forceinline__ bool pair_sweep(const EArgs &a, const CompT<T> &c, co
 
   // lattice state: fm_t = 2 m_t - N with m_t = (k z_t + sint_t) mod N for this
   // lane's point; integers below 2^17 are exact in float, so the update is exact
-  T fm[R], fstep[R], two_sf[R];
+  T fm[R], fstep[R], two_sf[R], half_sf2[R];
 #pragma unroll
   for (int t = 0; t < R; ++t) {
     const int m0 = static_cast<int>(((int64_t)lane * a.z[t + 1] + a.sint[t + 1]) % N);
     fm[t] = static_cast<T>(2 * m0 - N);
     fstep[t] = static_cast<T>(2 * a.step[t + 1]);
     two_sf[t] = static_cast<T>(2.0 * a.sfrac[t + 1]);
+    half_sf2[t] = static_cast<T>(a.sfrac[t + 1]);
   }
   const T fN = static_cast<T>(N);
   const T invN = T(1) / fN;
   const T umin = M::umin();
-  const T umax = T(1) - umin;
+  const T umax = T(1) - (sizeof(T) == 4 ? T(5.9604644775390625e-08) : umin);  // largest value below 1
   const bool e2lat = (a.e2_mode == 1);
   const T logmA = static_cast<T>(c.logmA);
 
@@ -241,12 +244,15 @@ __device__ __forceinline__ bool pair_sweep(const EArgs &a, const CompT<T> &c, co
   for (int t = 0; t < RP; ++t) M2[t] = T(0);
 
   for (int k = lane; k < N; k += WARP) {
-    T um[R], uu[R];  // 1 - u_t = |2 m - N + 2 sfrac| / N and u_t, both clamped
+    // 1 - u_t = |2 m - N + 2 sfrac| / N and u_t = 2 min(m + sfrac, N - m - sfrac) / N,
+    // each formed from an exact integer and the fraction so the small side stays exact
+    T um[R], uu[R];
 #pragma unroll
     for (int t = 0; t < R; ++t) {
-      const T av = M::ab(fm[t] + two_sf[t]);
-      um[t] = M::mn(M::mx(av * invN, umin), umax);
-      uu[t] = M::mx((fN - av) * invN, umin);
+      const T mm = T(0.5) * (fm[t] + fN);
+      const T lo = mm + half_sf2[t], hi = (fN - mm) - half_sf2[t];
+      um[t] = M::mn(M::mx(M::ab(fm[t] + two_sf[t]) * invN, umin), umax);
+      uu[t] = M::mx(T(2) * M::mn(lo, hi) * invN, umin);
       fm[t] += fstep[t];
       if (fm[t] >= fN) fm[t] -= T(2) * fN;
     }
@@ -464,16 +470,17 @@ __device__ void pair_sweep_log(const EArgs &a, const CompT<double> &c, const Pro
       Lf[t * (t + 1) / 2 + h] = (float)c.L[t * RMAX + h];
     }
   }
-  float fm[R], fstep[R], two_sf[R];
+  float fm[R], fstep[R], two_sf[R], sf[R];
 #pragma unroll
   for (int t = 0; t < R; ++t) {
     const int m0 = (int)(((int64_t)lane * a.z[t + 1] + a.sint[t + 1]) % N);
     fm[t] = (float)(2 * m0 - N);
     fstep[t] = (float)(2 * a.step[t + 1]);
     two_sf[t] = (float)(2.0 * a.sfrac[t + 1]);
+    sf[t] = (float)a.sfrac[t + 1];
   }
   const float fN = (float)N, invN = 1.0f / fN;
-  const float umin = 5.9604644775390625e-08f, umax = 1.0f - umin;
+  const float umin = 1.1102230246251565e-16f, umax = 1.0f - 5.9604644775390625e-08f;
   const bool e2lat = (a.e2_mode == 1);
 
   double mAx = -INFINITY, mBx = -INFINITY;
@@ -487,9 +494,10 @@ __device__ void pair_sweep_log(const EArgs &a, const CompT<double> &c, const Pro
     float um[R], uu[R];
 #pragma unroll
     for (int t = 0; t < R; ++t) {
-      const float av = fabsf(fm[t] + two_sf[t]);
-      um[t] = fminf(fmaxf(av * invN, umin), umax);
-      uu[t] = fmaxf((fN - av) * invN, umin);
+      const float mm = 0.5f * (fm[t] + fN);
+      const float lo = mm + sf[t], hi = (fN - mm) - sf[t];
+      um[t] = fminf(fmaxf(fabsf(fm[t] + two_sf[t]) * invN, umin), umax);
+      uu[t] = fmaxf(2.0f * fminf(lo, hi) * invN, umin);
       fm[t] += fstep[t];
       if (fm[t] >= fN) fm[t] -= 2.0f * fN;
     }

@@ -57,7 +57,7 @@ def test_log_tail_and_log_quantile():
     ref_z = -special.ndtri(np.exp(la.astype(np.float64)))
     own_z = _eval(la, 5)
     # near z = 0 the float input la itself rounds at ~6e-8, so compare absolutely there
-    assert np.max(np.abs(own_z - ref_z) / np.maximum(np.abs(ref_z), 0.05)) < 2e-6
+    assert np.max(np.abs(own_z - ref_z) / np.maximum(np.abs(ref_z), 0.5)) < 2e-6
     # beyond double range: z solves log Phi(-z) = la; check through the log tail
     la2 = -np.logspace(3, 5, 200).astype(np.float32)
     z2 = _eval(la2, 5)
