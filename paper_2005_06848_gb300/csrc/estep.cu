@@ -424,6 +424,12 @@ __global__ void __launch_bounds__(256) estep_kernel(EArgs a) {
 // conditional draw z = -Phi^{-1}((1 - u) p).  While p is a normal float the
 // direct single-precision forms are used; beyond, log p = log G(lim) - lim^2/2
 // with the square in double and z from the log-domain quantile.
+__device__ __forceinline__ float tail_factor_any(float a) {
+  if (a <= 40.0f) return nf32::tail_factor(a);
+  const float ia2 = 1.0f / (a * a);
+  return 0.398942280f / a * fmaf(ia2, fmaf(3.0f, ia2, -1.0f), 1.0f);
+}
+
 __device__ __forceinline__ void rescue_dim(double lim, float um, float u, double &lp, float &z) {
   const float limf = (float)lim;
   if (limf < 12.0f) {
@@ -432,15 +438,16 @@ __device__ __forceinline__ void rescue_dim(double lim, float um, float u, double
     lp = log((double)p);
     z = neg_quantile_f32(um, u, p, q);
   } else {
-    float G;
-    if (limf <= 40.0f) {
-      G = nf32::tail_factor(limf);
-    } else {
-      const float ia2 = 1.0f / (limf * limf);
-      G = 0.398942280f / limf * fmaf(ia2, fmaf(3.0f, ia2, -1.0f), 1.0f);
-    }
-    lp = (double)logf(G) - 0.5 * lim * lim;
+    lp = (double)logf(tail_factor_any(limf)) - 0.5 * lim * lim;
     z = neg_quantile_log_f32(logf(um) + (float)lp);
+  }
+  if (z > 1.0f) {
+    // one Newton step on log Phi(-z) = log(1 - u) + log p with the residual in
+    // double: d/dz log Phi(-z) = -1 / (sqrt(2 pi) G(z))
+    const float G = tail_factor_any(z);
+    const double lpz = (double)logf(G) - 0.5 * (double)z * (double)z;
+    const double la = log((double)um) + lp;
+    z = (float)((double)z + (lpz - la) * 2.5066282746310002 * (double)G);
   }
 }
 
