@@ -43,7 +43,7 @@ struct Num;
 // definition, -Phi^{-1}(max(um p, tiny)).
 template <>
 struct Num<float> {
-  __device__ static void upper_pq(float y, float &p, float &q) { phi_upper_pq_f32(y, p, q); }
+  __device__ static void upper_pq(float y, float &p, float &q) { phi_upper_pq_fast_f32(y, p, q); }
   __device__ static float neg_quantile(float um, float u, float p, float q) {
     return neg_quantile_f32(um, u, p, q);
   }
@@ -432,57 +432,70 @@ __device__ __forceinline__ float tail_factor_any(float a) {
 
 __device__ __forceinline__ void rescue_dim(double lim, float um, float u, double &lp, float &z) {
   const float limf = (float)lim;
+  const float lum = logf(um);
   if (limf < 12.0f) {
     float p, q;
     phi_upper_pq_f32(limf, p, q);
-    lp = log((double)p);
+    lp = (double)logf(p);
     z = neg_quantile_f32(um, u, p, q);
   } else {
     lp = (double)logf(tail_factor_any(limf)) - 0.5 * lim * lim;
-    z = neg_quantile_log_f32(logf(um) + (float)lp);
+    z = neg_quantile_log_f32(lum + (float)lp);
   }
   if (z > 1.0f) {
-    // one Newton step on log Phi(-z) = log(1 - u) + log p with the residual in
-    // double: d/dz log Phi(-z) = -1 / (sqrt(2 pi) G(z))
+    // one Newton step on log Phi(-z) = log(1 - u) + log p, the residual formed in
+    // double from float logarithms: d/dz log Phi(-z) = -1 / (sqrt(2 pi) G(z))
     const float G = tail_factor_any(z);
     const double lpz = (double)logf(G) - 0.5 * (double)z * (double)z;
-    const double la = log((double)um) + lp;
-    z = (float)((double)z + (lpz - la) * 2.5066282746310002 * (double)G);
+    const double h = lpz - ((double)lum + lp);
+    z = fmaf((float)h * 2.50662827f, G, z);
   }
 }
 
-// Log-domain sweep for the queued pairs.  Each point weight is carried as
-// log w = sum_t log Phi(-lim_t) (limits and log weights in double, the normal
-// functions in float) and accumulated against a running maximum, per lane and
-// then across the warp, so nothing underflows.
+// Running log-sum-exp accumulator: value = exp(m) * s.
+__device__ __forceinline__ void lse_add(double &m, float &s, double lw, float &scale_old, float &w_new) {
+  if (lw > m) {
+    scale_old = (m == -INFINITY) ? 0.f : expf((float)(m - lw));
+    w_new = 1.0f;
+    m = lw;
+  } else {
+    scale_old = 1.0f;
+    w_new = expf((float)(lw - m));
+  }
+  s = fmaf(s, scale_old, w_new);
+}
+
+// Log-domain sweep of one queued pair by a whole CTA: the warps split the
+// lattice points, each point weight is carried as log w = sum_t log Phi(-lim_t)
+// (limits and log weights in double arithmetic, every transcendental in float)
+// and accumulated against a running maximum, per lane, warp and CTA, so nothing
+// underflows.  `sm` is shared scratch of at least 8 * (4 + 3 + R + R(R+1)/2) words.
 template <int R, bool DENS>
-__device__ void pair_sweep_log(const EArgs &a, const CompT<double> &c, const Prologue<R> &pr,
-                               const double *__restrict__ tA, const double *__restrict__ tB, int i,
-                               int64_t j, int lane) {
+__device__ void pair_sweep_log_cta(const EArgs &a, const CompT<double> &c, const Prologue<R> &pr,
+                                   const double *__restrict__ tA, const double *__restrict__ tB, int i,
+                                   int64_t j, double *sm) {
   constexpr int RP = R * (R + 1) / 2;
+  constexpr int NV = 3 + R + RP;  // SA, SL, SB, M1, M2
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
   const int N = a.N;
   const double nud64 = c.nu + pr.d;
   const double fA = sqrt(c.mA / nud64), fB = sqrt(c.mB / nud64);
   double aA[R], aB[R], Lc[RP], Li[R];
-  float q[R], Lf[RP];
 #pragma unroll
   for (int t = 0; t < R; ++t) {
-    q[t] = (float)pr.q[t];
     aA[t] = -pr.q[t] * fA;
     aB[t] = -pr.q[t] * fB;
     Li[t] = c.Linv[t];
 #pragma unroll
-    for (int h = 0; h <= t; ++h) {
-      Lc[t * (t + 1) / 2 + h] = c.L[t * RMAX + h];
-      Lf[t * (t + 1) / 2 + h] = (float)c.L[t * RMAX + h];
-    }
+    for (int h = 0; h <= t; ++h) Lc[t * (t + 1) / 2 + h] = c.L[t * RMAX + h];
   }
+  const int k0 = warp * WARP + lane, kstride = nw * WARP;
   float fm[R], fstep[R], two_sf[R], sf[R];
 #pragma unroll
   for (int t = 0; t < R; ++t) {
-    const int m0 = (int)(((int64_t)lane * a.z[t + 1] + a.sint[t + 1]) % N);
+    const int m0 = (int)(((int64_t)k0 * a.z[t + 1] + a.sint[t + 1]) % N);
     fm[t] = (float)(2 * m0 - N);
-    fstep[t] = (float)(2 * a.step[t + 1]);
+    fstep[t] = (float)(2 * (int)(((int64_t)kstride * a.z[t + 1]) % N));
     two_sf[t] = (float)(2.0 * a.sfrac[t + 1]);
     sf[t] = (float)a.sfrac[t + 1];
   }
@@ -490,14 +503,12 @@ __device__ void pair_sweep_log(const EArgs &a, const CompT<double> &c, const Pro
   const float umin = 1.1102230246251565e-16f, umax = 1.0f - 5.9604644775390625e-08f;
   const bool e2lat = (a.e2_mode == 1);
 
-  double mAx = -INFINITY, mBx = -INFINITY;
-  float SA = 0.f, SL = 0.f, SB = 0.f, M1[R], M2[RP];
+  double mA = -INFINITY, mB = -INFINITY;
+  float v[NV];
 #pragma unroll
-  for (int t = 0; t < R; ++t) M1[t] = 0.f;
-#pragma unroll
-  for (int t = 0; t < RP; ++t) M2[t] = 0.f;
+  for (int t = 0; t < NV; ++t) v[t] = 0.f;
 
-  for (int k = lane; k < N; k += WARP) {
+  for (int k = k0; k < N; k += kstride) {
     float um[R], uu[R];
 #pragma unroll
     for (int t = 0; t < R; ++t) {
@@ -520,17 +531,9 @@ __device__ void pair_sweep_log(const EArgs &a, const CompT<double> &c, const Pro
       rescue_dim(acc * Li[t], um[t], uu[t], lp, z[t]);
       lw += lp;
     }
-    const float lc = e2lat ? (float)(c.logmA + 2.0 * log(sA)) : 0.f;
-    if (lw > mAx) {
-      const float sc = (float)exp(mAx - lw);
-      SA = fmaf(SA, sc, 1.0f);
-      SL = fmaf(SL, sc, lc);
-      mAx = lw;
-    } else {
-      const float e = expf((float)(lw - mAx));
-      SA += e;
-      SL = fmaf(e, lc, SL);
-    }
+    float so, wn;
+    lse_add(mA, v[0], lw, so, wn);
+    if (e2lat) v[1] = fmaf(v[1], so, wn * (float)(c.logmA + 2.0 * (double)logf((float)sA)));
     if (!DENS) {
       const double sB = tB[k];
       const float isB = (float)(1.0 / sB);
@@ -544,107 +547,112 @@ __device__ void pair_sweep_log(const EArgs &a, const CompT<double> &c, const Pro
         rescue_dim(acc * Li[t], um[t], uu[t], lp, z[t]);
         lwb += lp;
       }
-      float sc = 1.0f, e = 1.0f;
-      if (lwb > mBx) {
-        sc = (float)exp(mBx - lwb);
-        mBx = lwb;
-      } else {
-        e = expf((float)(lwb - mBx));
-      }
-      SB = fmaf(SB, sc, e);
+      lse_add(mB, v[2], lwb, so, wn);
 #pragma unroll
       for (int t = 0; t < R; ++t) {
         const float vt = z[t] * isB;
-        M1[t] = fmaf(M1[t], sc, e * vt);
+        v[3 + t] = fmaf(v[3 + t], so, wn * vt);
 #pragma unroll
         for (int h = 0; h <= t; ++h)
-          M2[t * (t + 1) / 2 + h] = fmaf(M2[t * (t + 1) / 2 + h], sc, e * vt * (z[h] * isB));
+          v[3 + R + t * (t + 1) / 2 + h] = fmaf(v[3 + R + t * (t + 1) / 2 + h], so, wn * vt * (z[h] * isB));
       }
     }
   }
-  // combine lanes against the warp-wide maximum
-  double wmA = mAx;
+  // combine: per warp against the warp maximum, then across warps in shared memory
+  double wmA = mA, wmB = mB;
 #pragma unroll
-  for (int o = 16; o > 0; o >>= 1) wmA = fmax(wmA, __shfl_xor_sync(0xffffffffu, wmA, o));
-  const float scA = (mAx == -INFINITY) ? 0.f : (float)exp(mAx - wmA);
-  SA = warp_sum(SA * scA);
-  SL = warp_sum(SL * scA);
-  double wmB = mBx;
-  if (!DENS) {
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) wmB = fmax(wmB, __shfl_xor_sync(0xffffffffu, wmB, o));
-    const float scB = (mBx == -INFINITY) ? 0.f : (float)exp(mBx - wmB);
-    SB = warp_sum(SB * scB);
-#pragma unroll
-    for (int t = 0; t < R; ++t) M1[t] = warp_sum(M1[t] * scB);
-#pragma unroll
-    for (int t = 0; t < RP; ++t) M2[t] = warp_sum(M2[t] * scB);
+  for (int o = 16; o > 0; o >>= 1) {
+    wmA = fmax(wmA, __shfl_xor_sync(0xffffffffu, wmA, o));
+    wmB = fmax(wmB, __shfl_xor_sync(0xffffffffu, wmB, o));
   }
-  const double logTA = wmA + log((double)SA) - log((double)N);
-  const float logf_out = (float)(pr.logt + logTA);
-  const int64_t n = a.n;
-  const int64_t ij = (int64_t)i * n + j;
-  if (!isfinite(logf_out) && lane == 0) atomicOr(a.status, ERR_NUMERIC);
-  if (a.out.logf != nullptr && lane == 0) store<float>(a.out.logf, ij, logf_out);
-  if (DENS) return;
-  const double logTB = wmB + log((double)SB) - log((double)N);
-  const bool ok = isfinite(logTA) && isfinite(logTB);
-  const float e1 = ok ? (float)(c.mA / nud64 * exp(logTB - logTA)) : 0.f;
-  const float sig = (float)sqrt(nud64 / c.mB);
-  const float iSB = ok ? 1.0f / SB : 0.f;
-  float LEV[R];
+  const float scA = (mA == -INFINITY) ? 0.f : expf((float)(mA - wmA));
+  const float scB = (mB == -INFINITY) ? 0.f : expf((float)(mB - wmB));
+  v[0] = warp_sum(v[0] * scA);
+  v[1] = warp_sum(v[1] * scA);
 #pragma unroll
-  for (int t = 0; t < R; ++t) {
-    float sacc = 0.f;
+  for (int t = 2; t < NV; ++t) v[t] = warp_sum(v[t] * scB);
+  double *row = sm + warp * (2 + NV);
+  if (lane == 0) {
+    row[0] = wmA;
+    row[1] = wmB;
 #pragma unroll
-    for (int h = 0; h <= t; ++h) sacc += Lf[t * (t + 1) / 2 + h] * (M1[h] * iSB);
-    LEV[t] = sacc;
+    for (int t = 0; t < NV; ++t) row[2 + t] = (double)v[t];
   }
-  float e2;
-  if (e2lat)
-    e2 = ok ? SL / SA - (float)log(nud64) : 0.f;
-  else
-    e2 = ok ? e1 - (float)(log(0.5 * nud64) + c.mA / nud64 - c.psiA) : 0.f;
-  if (lane == 1) store<float>(a.out.e1, ij, e1);
-  if (lane == 2) store<float>(a.out.e2, ij, e2);
-#pragma unroll
-  for (int t = 0; t < R; ++t)
-    if (lane == 3 + t) store<float>(a.out.e3, ((int64_t)i * R + t) * n + j, e1 * (q[t] + sig * LEV[t]));
-#pragma unroll
-  for (int t = 0; t < R; ++t) {
-#pragma unroll
-    for (int h = 0; h <= t; ++h) {
-      const int o = 3 + R + t * (t + 1) / 2 + h;
-      if (lane == (o & 31)) {
-        float sacc = 0.f;
-#pragma unroll
-        for (int aa = 0; aa <= t; ++aa)
-#pragma unroll
-          for (int bb = 0; bb <= h; ++bb) {
-            const float evv = (aa >= bb ? M2[aa * (aa + 1) / 2 + bb] : M2[bb * (bb + 1) / 2 + aa]) * iSB;
-            sacc += Lf[t * (t + 1) / 2 + aa] * evv * Lf[h * (h + 1) / 2 + bb];
-          }
-        const float exx = q[t] * q[h] + sig * (q[t] * LEV[h] + LEV[t] * q[h]) + sig * sig * sacc;
-        store<float>(a.out.e4, ((int64_t)i * RP + t * (t + 1) / 2 + h) * n + j, e1 * exx);
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double gA = -INFINITY, gB = -INFINITY;
+    for (int w = 0; w < nw; ++w) {
+      gA = fmax(gA, sm[w * (2 + NV)]);
+      gB = fmax(gB, sm[w * (2 + NV) + 1]);
+    }
+    double tot[NV];
+    for (int t = 0; t < NV; ++t) tot[t] = 0.0;
+    for (int w = 0; w < nw; ++w) {
+      const double *rw = sm + w * (2 + NV);
+      const double fa = (rw[0] == -INFINITY) ? 0.0 : exp(rw[0] - gA);
+      const double fb = (rw[1] == -INFINITY) ? 0.0 : exp(rw[1] - gB);
+      tot[0] += rw[2] * fa;
+      tot[1] += rw[3] * fa;
+      for (int t = 2; t < NV; ++t) tot[t] += rw[2 + t] * fb;
+    }
+    const int64_t n = a.n;
+    const int64_t ij = (int64_t)i * n + j;
+    const double logTA = gA + log(tot[0]) - log((double)N);
+    const double logf_out = pr.logt + logTA;
+    if (!isfinite(logf_out)) atomicOr(a.status, ERR_NUMERIC);
+    if (a.out.logf != nullptr) store<float>(a.out.logf, ij, logf_out);
+    if (!DENS) {
+      const double logTB = gB + log(tot[2]) - log((double)N);
+      const bool ok = isfinite(logTA) && isfinite(logTB);
+      const double e1 = ok ? c.mA / nud64 * exp(logTB - logTA) : 0.0;
+      const double sig = sqrt(nud64 / c.mB);
+      const double iSB = ok ? 1.0 / tot[2] : 0.0;
+      double LEV[R];
+      for (int t = 0; t < R; ++t) {
+        double sacc = 0.0;
+        for (int h = 0; h <= t; ++h) sacc += Lc[t * (t + 1) / 2 + h] * (tot[3 + h] * iSB);
+        LEV[t] = sacc;
       }
+      double e2;
+      if (e2lat)
+        e2 = ok ? tot[1] / tot[0] - log(nud64) : 0.0;
+      else
+        e2 = ok ? e1 - (log(0.5 * nud64) + c.mA / nud64 - c.psiA) : 0.0;
+      store<float>(a.out.e1, ij, e1);
+      store<float>(a.out.e2, ij, e2);
+      for (int t = 0; t < R; ++t) store<float>(a.out.e3, ((int64_t)i * R + t) * n + j, e1 * (pr.q[t] + sig * LEV[t]));
+      for (int t = 0; t < R; ++t)
+        for (int h = 0; h <= t; ++h) {
+          double sacc = 0.0;
+          for (int aa = 0; aa <= t; ++aa)
+            for (int bb = 0; bb <= h; ++bb) {
+              const double evv = (aa >= bb ? tot[3 + R + aa * (aa + 1) / 2 + bb] : tot[3 + R + bb * (bb + 1) / 2 + aa]) * iSB;
+              sacc += Lc[t * (t + 1) / 2 + aa] * evv * Lc[h * (h + 1) / 2 + bb];
+            }
+          const double exx = pr.q[t] * pr.q[h] + sig * (pr.q[t] * LEV[h] + LEV[t] * pr.q[h]) + sig * sig * sacc;
+          store<float>(a.out.e4, ((int64_t)i * RP + t * (t + 1) / 2 + h) * n + j, e1 * exx);
+        }
     }
   }
+  __syncthreads();
 }
 
 template <int R, bool DENS>
 __global__ void __launch_bounds__(256) rescue_kernel(EArgs a, const CompT<double> *comp,
                                                       const double *chi) {
+  constexpr int NV = 3 + R + R * (R + 1) / 2;
+  __shared__ double sm[8 * (2 + NV)];
+  __shared__ Prologue<R> spr;
   const unsigned cnt = *a.rescue_count;
-  const int lane = threadIdx.x & 31;
-  const unsigned gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-  const unsigned nwarps = (gridDim.x * blockDim.x) >> 5;
-  for (unsigned w = gw; w < cnt; w += nwarps) {
+  for (unsigned w = blockIdx.x; w < cnt; w += gridDim.x) {
     const unsigned long long id = a.rescue_list[w];
     const int i = static_cast<int>(id / (unsigned long long)a.n);
     const int64_t j = static_cast<int64_t>(id % (unsigned long long)a.n);
+    if (threadIdx.x == 0) spr = prologue<double, R>(a, comp[i], j);
+    __syncthreads();
+    const Prologue<R> pr = spr;
     const double *tA = chi + (int64_t)i * 2 * a.N;
-    const Prologue<R> pr = prologue<double, R>(a, comp[i], j);
-    pair_sweep_log<R, DENS>(a, comp[i], pr, tA, tA + a.N, i, j, lane);
+    pair_sweep_log_cta<R, DENS>(a, comp[i], pr, tA, tA + a.N, i, j, sm);
   }
 }
 
@@ -678,7 +686,7 @@ cudaError_t launch_r(EArgs a, int g, int64_t n, cudaStream_t st, bool fp32,
     if (e != cudaSuccess) return e;
   }
   if (!fp32) return e;
-  rescue_kernel<R, DENS><<<152 * 2, 256, 0, st>>>(a, c64, chi64);
+  rescue_kernel<R, DENS><<<152 * 4, 256, 0, st>>>(a, c64, chi64);
   return cudaGetLastError();
 }
 
