@@ -292,7 +292,8 @@ cfust_status enqueue_iteration(cfust_ctx *c, const double *Y, int64_t n, cudaStr
   CF_CUDA(c, launch_estep(c->opts.precision, Y, n, c->g, c->p, c->r, c->lat, c->d_c64, c->d_c32,
                           c->d_chi64, c->d_chi32, ctx_out(c), false, c->opts.e2_mode,
                           c->d_rescue, c->d_rescue_cnt, c->d_status, 0, st,
-                          sweep_timing(c, st == c->cap_stream)));
+                          sweep_timing(c, st == c->cap_stream), 1,
+                          param_view(c->d_params, c->g, c->p, c->r).pi));
   PosteriorArgs a = post_args(c, Y, n);
   a.logf = c->d_logf;
   a.e1 = c->d_e1;
@@ -318,7 +319,7 @@ cfust_status enqueue_loglik(cfust_ctx *c, const double *Y, int64_t n, double *tr
   CF_CUDA(c, launch_estep(c->opts.precision, Y, n, c->g, c->p, c->r, c->lat, c->d_c64, c->d_c32,
                           c->d_chi64, c->d_chi32, o, true, c->opts.e2_mode,
                           c->d_rescue, c->d_rescue_cnt, c->d_status, 0, c->stream,
-                          sweep_timing(c, false)));
+                          sweep_timing(c, false), 1, param_view(c->d_params, c->g, c->p, c->r).pi));
   PosteriorArgs a = post_args(c, Y, n);
   a.logf = c->d_logf;
   a.want_ll = true;

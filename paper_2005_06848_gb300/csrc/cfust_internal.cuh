@@ -105,12 +105,16 @@ struct SweepTiming {
 
 // E-step lattice sweeps for all (i, j).  precision: CFUST_FP64 / CFUST_FP32.
 // In FP32 mode, pairs whose sweep underflows are appended to rescue_list and
-// recomputed in double by the rescue pass (both launched here).
+// recomputed by the log-domain rescue pass (both launched here).  With
+// `triage`, a queued pair whose posterior weight is below exp(-50) of the
+// best component of its observation (judged from an upper bound of its
+// density) gets log f = -inf and e = 0 instead (fit and log-likelihood paths).
 cudaError_t launch_estep(int precision, const double *Y, int64_t n, int g, int p, int r,
                          const LatticeDev &lat, const CompT<double> *c64, const CompT<float> *c32,
                          const double *chi64, const float *chi32, EstepOut out, bool density_only,
                          int e2_mode, unsigned long long *rescue_list, unsigned *rescue_count, int *d_status,
-                         int pairs_per_warp, cudaStream_t st, SweepTiming tm = SweepTiming());
+                         int pairs_per_warp, cudaStream_t st, SweepTiming tm = SweepTiming(),
+                         int triage = 0, const double *d_pi = nullptr);
 
 // Elementwise single-precision normal functions (see cfust_normal_f32).
 cudaError_t launch_normal_f32(const float *x, float *out, int64_t n, int which, cudaStream_t st);

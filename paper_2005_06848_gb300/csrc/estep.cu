@@ -89,6 +89,8 @@ struct EArgs {
   unsigned long long *rescue_list;
   unsigned *rescue_count;
   int *status;
+  int triage;          // 1: skip queued pairs whose posterior weight is provably negligible
+  const double *pi;    // device [g], read by the triage
 };
 
 __host__ __device__ constexpr size_t align16(size_t x) { return (x + 15) & ~size_t(15); }
@@ -310,14 +312,24 @@ __device__ __forceinline__ bool pair_sweep(const EArgs &a, const CompT<T> &c, co
   }
 
   const T logf = static_cast<T>(pr.logt) + M::lg(SA) - M::lg(static_cast<T>(N));
-  if (check) {
-    const T thr = T(1e-20) * static_cast<T>(N);
-    bool need = !(SA >= thr) || !isfinite(logf);
-    if (!DENS) need = need || !(SB >= thr);
-    if (need) return true;
-  }
   const int64_t n = a.n;
   const int64_t ij = (int64_t)i * n + j;
+  if (check) {
+    const T thr = T(1e-20) * static_cast<T>(N);
+    const bool densok = (SA >= thr) && isfinite(logf);
+    bool need = !densok;
+    if (!DENS) need = need || !(SB >= thr);
+    if (need) {
+      // upper bound of log f for the triage: exact when the density sum was fine,
+      // else log t + log 1e-20 (the sum was below the threshold), +inf when unknown
+      if (a.triage && a.out.logf != nullptr && lane == 0) {
+        const double ub = densok ? (double)logf
+                                 : (isfinite((double)SA) ? pr.logt - 46.051701859880914 : INFINITY);
+        store<OT>(a.out.logf, ij, ub);
+      }
+      return true;
+    }
+  }
   if (a.out.logf != nullptr && lane == 0) store<OT>(a.out.logf, ij, logf);
   if (DENS) return false;
 
@@ -644,12 +656,39 @@ __global__ void __launch_bounds__(256) rescue_kernel(EArgs a, const CompT<double
   __shared__ double sm[8 * (2 + NV)];
   __shared__ Prologue<R> spr;
   const unsigned cnt = *a.rescue_count;
+  __shared__ int skip;
   for (unsigned w = blockIdx.x; w < cnt; w += gridDim.x) {
     const unsigned long long id = a.rescue_list[w];
     const int i = static_cast<int>(id / (unsigned long long)a.n);
     const int64_t j = static_cast<int64_t>(id % (unsigned long long)a.n);
-    if (threadIdx.x == 0) spr = prologue<double, R>(a, comp[i], j);
+    if (threadIdx.x == 0) {
+      skip = 0;
+      if (a.triage) {
+        // tau_ij < exp(-50) when log pi_i + ub_ij trails the best component by 50
+        const float *lf = reinterpret_cast<const float *>(a.out.logf);
+        double best = -INFINITY;
+        for (int h = 0; h < a.g; ++h) best = fmax(best, log(a.pi[h]) + (double)lf[(int64_t)h * a.n + j]);
+        const double mine = log(a.pi[i]) + (double)lf[(int64_t)i * a.n + j];
+        if (isfinite(best) && mine < best - 50.0) {
+          skip = 1;
+          const int64_t ij = (int64_t)i * a.n + j;
+          const int RP = R * (R + 1) / 2;
+          store<float>(a.out.logf, ij, -INFINITY);
+          if (!DENS) {
+            store<float>(a.out.e1, ij, 0.0);
+            store<float>(a.out.e2, ij, 0.0);
+            for (int t = 0; t < R; ++t) store<float>(a.out.e3, ((int64_t)i * R + t) * a.n + j, 0.0);
+            for (int t = 0; t < RP; ++t) store<float>(a.out.e4, ((int64_t)i * RP + t) * a.n + j, 0.0);
+          }
+        }
+      }
+      if (!skip) spr = prologue<double, R>(a, comp[i], j);
+    }
     __syncthreads();
+    if (skip) {
+      __syncthreads();
+      continue;
+    }
     const Prologue<R> pr = spr;
     const double *tA = chi + (int64_t)i * 2 * a.N;
     pair_sweep_log_cta<R, DENS>(a, comp[i], pr, tA, tA + a.N, i, j, sm);
@@ -733,7 +772,8 @@ cudaError_t launch_estep(int precision, const double *Y, int64_t n, int g, int p
                          const LatticeDev &lat, const CompT<double> *c64, const CompT<float> *c32,
                          const double *chi64, const float *chi32, EstepOut out, bool density_only,
                          int e2_mode, unsigned long long *rescue_list, unsigned *rescue_count, int *d_status,
-                         int pairs_per_warp, cudaStream_t st, SweepTiming tm) {
+                         int pairs_per_warp, cudaStream_t st, SweepTiming tm, int triage,
+                         const double *d_pi) {
   if (n <= 0) return cudaSuccess;
   EArgs a;
   a.Y = Y;
@@ -760,6 +800,8 @@ cudaError_t launch_estep(int precision, const double *Y, int64_t n, int g, int p
   a.rescue_list = rescue_list;
   a.rescue_count = rescue_count;
   a.status = d_status;
+  a.triage = (triage && out.logf != nullptr) ? 1 : 0;
+  a.pi = d_pi;
   if (precision == CFUST_FP64) {
     a.comp = c64;
     a.chi = chi64;
