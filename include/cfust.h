@@ -138,6 +138,10 @@ cfust_status cfust_fit(cfust_ctx *ctx, const double *Y, int64_t n,
                        cfust_params *params, double *loglik_trace, int *iters_done);
 
 /* Stepwise form of cfust_fit for callers that drive the iterations themselves.
+ * In the fit and log-likelihood paths a single-precision pair whose lattice
+ * sum underflows and whose posterior weight is provably below exp(-30) of the
+ * best component of its observation gets density 0 (tau = 0, e = 0) instead of
+ * the log-domain recomputation that cfust_estep always performs.
  * cfust_fit_begin uploads params and binds Y (device [n][p], kept until
  * cfust_fit_end) and resets the trace.  cfust_fit_step enqueues `iters` EM
  * iterations on the context's stream without synchronising (each a replay of
@@ -150,6 +154,11 @@ cfust_status cfust_fit_begin(cfust_ctx *ctx, const double *Y, int64_t n,
 cfust_status cfust_fit_step(cfust_ctx *ctx, int iters);
 cfust_status cfust_fit_end(cfust_ctx *ctx, cfust_params *params, double *loglik_trace,
                            int *iters_done);
+
+/* During a stepwise fit: synchronise and copy the log-likelihood trace so far,
+ * l(Psi^(0)) .. l(Psi^(k-1)) after k cfust_fit_step iterations, into trace
+ * (host, at least k entries); *count receives k. */
+cfust_status cfust_fit_trace(cfust_ctx *ctx, double *trace, int *count);
 
 /* Number of (i, j) pairs whose single-precision lattice sweep fell below the
  * underflow guard in the last E-step and were recomputed in double precision

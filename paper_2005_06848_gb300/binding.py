@@ -19,7 +19,7 @@ STATUS = {0: "CFUST_OK", -1: "CFUST_EINVAL", -2: "CFUST_ENOTPD", -3: "CFUST_ENUM
           -4: "CFUST_EDEGENERATE", -5: "CFUST_ETIMEOUT", -6: "CFUST_ECUDA", -7: "CFUST_ENOMEM"}
 
 EXPORTED = ["cfust_create", "cfust_destroy", "cfust_loglik", "cfust_estep", "cfust_mstep",
-            "cfust_fit", "cfust_fit_begin", "cfust_fit_step", "cfust_fit_end",
+            "cfust_fit", "cfust_fit_begin", "cfust_fit_step", "cfust_fit_end", "cfust_fit_trace",
             "cfust_last_rescued", "cfust_last_sweep_ms", "cfust_normal_f32", "cfust_last_error"]
 
 
@@ -72,6 +72,7 @@ def load(build_if_missing: bool = True) -> ctypes.CDLL:
         "cfust_fit_begin": ([vp, vp, i64, P], ctypes.c_int),
         "cfust_fit_step": ([vp, ctypes.c_int], ctypes.c_int),
         "cfust_fit_end": ([vp, P, dp, ctypes.POINTER(ctypes.c_int)], ctypes.c_int),
+        "cfust_fit_trace": ([vp, dp, ctypes.POINTER(ctypes.c_int)], ctypes.c_int),
         "cfust_last_rescued": ([vp, ctypes.POINTER(i64)], ctypes.c_int),
         "cfust_last_sweep_ms": ([vp, ctypes.POINTER(ctypes.c_float)], ctypes.c_int),
         "cfust_last_error": ([vp], ctypes.c_char_p),
@@ -210,6 +211,13 @@ class Context:
 
     def cfust_fit_step(self, iters=1):
         self._check(self.lib.cfust_fit_step(self.h, int(iters)))
+
+    def cfust_fit_trace(self):
+        buf = np.zeros(max(1, self.opts.max_iter))
+        cnt = ctypes.c_int()
+        self._check(self.lib.cfust_fit_trace(self.h, buf.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
+                                             ctypes.byref(cnt)))
+        return buf[:cnt.value]
 
     def cfust_fit_end(self):
         hp = self._fit_hp

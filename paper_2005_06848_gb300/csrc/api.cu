@@ -595,6 +595,18 @@ cfust_status cfust_fit_step(cfust_ctx *c, int iters) {
   return CFUST_OK;
 }
 
+cfust_status cfust_fit_trace(cfust_ctx *c, double *trace, int *count) {
+  if (!c || !trace || !count) return CFUST_EINVAL;
+  if (!c->fit_open) return fail(c, CFUST_EINVAL, "cfust_fit_begin has not been called");
+  DeviceGuard dg(c->device);
+  if (c->fit_done > 0)
+    CF_CUDA(c, cudaMemcpyAsync(trace, c->d_trace, sizeof(double) * c->fit_done, cudaMemcpyDeviceToHost,
+                               c->stream));
+  CF_CUDA(c, cudaStreamSynchronize(c->stream));
+  *count = c->fit_done;
+  return CFUST_OK;
+}
+
 cfust_status cfust_fit_end(cfust_ctx *c, cfust_params *P, double *trace, int *iters_done) {
   if (!c) return CFUST_EINVAL;
   if (!c->fit_open) return fail(c, CFUST_EINVAL, "cfust_fit_begin has not been called");

@@ -106,7 +106,7 @@ struct SweepTiming {
 // E-step lattice sweeps for all (i, j).  precision: CFUST_FP64 / CFUST_FP32.
 // In FP32 mode, pairs whose sweep underflows are appended to rescue_list and
 // recomputed by the log-domain rescue pass (both launched here).  With
-// `triage`, a queued pair whose posterior weight is below exp(-50) of the
+// `triage`, a queued pair whose posterior weight is below exp(-30) of the
 // best component of its observation (judged from an upper bound of its
 // density) gets log f = -inf and e = 0 instead (fit and log-likelihood paths).
 cudaError_t launch_estep(int precision, const double *Y, int64_t n, int g, int p, int r,

@@ -320,11 +320,12 @@ __device__ __forceinline__ bool pair_sweep(const EArgs &a, const CompT<T> &c, co
     bool need = !densok;
     if (!DENS) need = need || !(SB >= thr);
     if (need) {
-      // upper bound of log f for the triage: exact when the density sum was fine,
-      // else log t + log 1e-20 (the sum was below the threshold), +inf when unknown
+      // upper bound of log f for the triage: the float sum misses only point
+      // weights that fell below the float range, so T <= max(S_A / N, 1e-37) up
+      // to rounding; one nat of margin; +inf when the sum is not finite
       if (a.triage && a.out.logf != nullptr && lane == 0) {
-        const double ub = densok ? (double)logf
-                                 : (isfinite((double)SA) ? pr.logt - 46.051701859880914 : INFINITY);
+        const double sa = (double)SA / (double)N;
+        const double ub = isfinite(sa) ? pr.logt + log(fmax(sa, 1e-37)) + 1.0 : INFINITY;
         store<OT>(a.out.logf, ij, ub);
       }
       return true;
@@ -664,12 +665,12 @@ __global__ void __launch_bounds__(256) rescue_kernel(EArgs a, const CompT<double
     if (threadIdx.x == 0) {
       skip = 0;
       if (a.triage) {
-        // tau_ij < exp(-50) when log pi_i + ub_ij trails the best component by 50
+        // tau_ij < exp(-30) when log pi_i + ub_ij trails the best component by 30
         const float *lf = reinterpret_cast<const float *>(a.out.logf);
         double best = -INFINITY;
         for (int h = 0; h < a.g; ++h) best = fmax(best, log(a.pi[h]) + (double)lf[(int64_t)h * a.n + j]);
         const double mine = log(a.pi[i]) + (double)lf[(int64_t)i * a.n + j];
-        if (isfinite(best) && mine < best - 50.0) {
+        if (isfinite(best) && mine < best - 30.0) {
           skip = 1;
           const int64_t ij = (int64_t)i * a.n + j;
           const int RP = R * (R + 1) / 2;

@@ -279,3 +279,28 @@ def test_fp32_rescued_pairs_match_oracle():
     tiny = R["logf"] < -60.0
     assert tiny.sum() >= 2
     _cmp("logf tail", G["logf"][tiny], R["logf"][tiny], 0, 1e-4)
+
+
+def test_stepwise_fit_equals_fit_and_triage_keeps_loglik():
+    """cfust_fit_begin/step/trace/end reproduce cfust_fit bit for bit, and with
+    planted far outliers (whose float sums underflow and are triaged) the FP32
+    log-likelihood trace still matches the oracle to 1e-6 relative."""
+    torch = _torch()
+    Y, truth, init, lat = _problem("cfust_p4r4g3_n100000_N4096", 300, 512)
+    extra = [init.mu[i] - c * init.Delta[i].sum(axis=1) for i in range(init.g) for c in (4.0, 8.0, 16.0)]
+    Y = np.ascontiguousarray(np.vstack([Y, np.array(extra)]))
+    Yd = torch.from_numpy(Y).cuda()
+    with binding.Context(lat, precision=binding.CFUST_FP32, max_iter=3) as ctx:
+        p1, t1, d1 = ctx.cfust_fit(Yd, init)
+    with binding.Context(lat, precision=binding.CFUST_FP32, max_iter=3) as ctx:
+        ctx.cfust_fit_begin(Yd, init)
+        ctx.cfust_fit_step(2)
+        mid = ctx.cfust_fit_trace()
+        ctx.cfust_fit_step(1)
+        p2, t2, d2 = ctx.cfust_fit_end()
+    assert d1 == d2 == 3 and np.array_equal(t1, t2) and np.array_equal(mid, t1[:2])
+    for a, b in zip(p1.as_arrays(), p2.as_arrays()):
+        assert np.array_equal(a, b)
+    U = O.lattice_points(lat.n, lat.z, lat.shift)
+    ref = O.loglik(Y, init, U)
+    assert abs(t1[0] - ref) <= 1e-6 * abs(ref)
