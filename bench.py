@@ -144,6 +144,22 @@ def dist_env():
     return ws, rank, local
 
 
+def aggregate_ranks(local_ms: float, units_per_step: int, steps: int, device: str = "cpu"):
+    """Whole-job throughput over all ranks: the timed region is the slowest
+    rank's (max over ranks), the work is every rank's units.  Returns
+    (max_ms, units per second over the job, steps per second)."""
+    import torch
+    ws = 1
+    total_ms = float(local_ms)
+    if torch.distributed.is_available() and torch.distributed.is_initialized():
+        ws = torch.distributed.get_world_size()
+        t = torch.tensor([total_ms], dtype=torch.float64, device=device)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        total_ms = float(t.item())
+    secs = total_ms / 1e3
+    return total_ms, ws * units_per_step * steps / secs, steps / secs
+
+
 def cpu_baseline(rows: int = 1024):
     """The FP64 oracle (as it stands) on a bounded sample: E-step and M-step of
     `rows` observations x all components of the same workload, one core."""
@@ -255,14 +271,9 @@ def run_ours(args):
     params, trace, done = ctx.cfust_fit_end()
     ctx.close()
 
-    total_ms = float(sum(step_ms))
-    if ws > 1:
-        t = torch.tensor([total_ms], device="cuda", dtype=torch.float64)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        total_ms = float(t.item())
     pairs_per_step = n * g
-    value = ws * pairs_per_step * args.steps / (total_ms / 1e3)
-    iters_per_s = args.steps / (total_ms / 1e3)
+    total_ms, value, iters_per_s = aggregate_ranks(float(sum(step_ms)), pairs_per_step, args.steps,
+                                                   "cuda" if ws > 1 else "cpu")
 
     # roofline of the sweep kernel (the E-step's dominant kernel)
     mean_sweep_ms = float(np.mean(sweep_ms))

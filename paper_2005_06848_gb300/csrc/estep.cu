@@ -202,6 +202,7 @@ __device__ __forceinline__ bool pair_sweep(const EArgs &a, const CompT<T> &c, co
                                            int i, int64_t j, int lane, bool check) {
   using M = Num<T>;
   constexpr int RP = R * (R + 1) / 2;
+  constexpr bool PAIRED = (sizeof(T) == 4) && !DENS;
   const int N = a.N;
   const double nud64 = c.nu + pr.d;
   const double fA = sqrt(c.mA / nud64), fB = sqrt(c.mB / nud64);
@@ -218,6 +219,17 @@ __device__ __forceinline__ bool pair_sweep(const EArgs &a, const CompT<T> &c, co
     Li[t] = c.Linv[t];
 #pragma unroll
     for (int h = 0; h <= t; ++h) Lc[t * (t + 1) / 2 + h] = c.L[t * RMAX + h];
+  }
+  // paired operands: (pass A, pass B) limits and duplicated -L, 1/L_tt
+  float2 ab2[R], nL2[RP > 0 ? RP : 1], Li2[R];
+  if constexpr (PAIRED) {
+#pragma unroll
+    for (int t = 0; t < R; ++t) {
+      ab2[t] = make_float2((float)aA[t], (float)aB[t]);
+      Li2[t] = make_float2((float)Li[t], (float)Li[t]);
+#pragma unroll
+      for (int h = 0; h <= t; ++h) nL2[t * (t + 1) / 2 + h] = make_float2(-(float)Lc[t * (t + 1) / 2 + h], -(float)Lc[t * (t + 1) / 2 + h]);
+    }
   }
 
   // lattice state: fm_t = 2 m_t - N with m_t = (k z_t + sint_t) mod N for this
@@ -258,47 +270,75 @@ __device__ __forceinline__ bool pair_sweep(const EArgs &a, const CompT<T> &c, co
       fm[t] += fstep[t];
       if (fm[t] >= fN) fm[t] -= T(2) * fN;
     }
-    // pass A: density integral
-    const T sA = tA[k];
-    T wA = T(1);
-    T zA[R];
-#pragma unroll
-    for (int t = 0; t < R; ++t) {
-      T acc = aA[t] * sA;
-#pragma unroll
-      for (int h = 0; h < t; ++h) acc -= Lc[t * (t + 1) / 2 + h] * zA[h];
-      T pt, qt;
-      M::upper_pq(acc * Li[t], pt, qt);
-      wA *= pt;
-      if (t + 1 < R) zA[t] = M::neg_quantile(um[t], uu[t], pt, qt);
-    }
-    SA += wA;
-    if (e2lat) SL += wA * (logmA + T(2) * M::lg(sA));
-    if (!DENS) {
-      // pass B: the e1 numerator and the truncated moments
-      const T sB = tB[k];
-      const T isB = T(1) / sB;
-      T wB = T(1);
-      T zB[R];
+    if constexpr (PAIRED) {
+      // passes A and B side by side in FP32x2: .x is pass A, .y pass B
+      const float2 s2 = make_float2(tA[k], tB[k]);
+      float2 w2 = make_float2(1.0f, 1.0f);
+      float2 z2[R];
 #pragma unroll
       for (int t = 0; t < R; ++t) {
-        T acc = aB[t] * sB;
+        float2 acc2 = __fmul2_rn(ab2[t], s2);
 #pragma unroll
-        for (int h = 0; h < t; ++h) acc -= Lc[t * (t + 1) / 2 + h] * zB[h];
-        T pt, qt;
-        M::upper_pq(acc * Li[t], pt, qt);
-        wB *= pt;
-        zB[t] = M::neg_quantile(um[t], uu[t], pt, qt);
+        for (int h = 0; h < t; ++h) acc2 = __ffma2_rn(nL2[t * (t + 1) / 2 + h], z2[h], acc2);
+        float2 p2, q2;
+        phi_upper_pq_x2(__fmul2_rn(acc2, Li2[t]), p2, q2);
+        w2 = __fmul2_rn(w2, p2);
+        z2[t] = neg_quantile_x2(um[t], uu[t], p2, q2);
       }
-      SB += wB;
+      SA += w2.x;
+      if (e2lat) SL += w2.x * (logmA + T(2) * M::lg(s2.x));
+      SB += w2.y;
+      const float isB = __fdividef(1.0f, s2.y);
 #pragma unroll
       for (int t = 0; t < R; ++t) {
-        const T wv = wB * (zB[t] * isB);
+        const float wv = w2.y * (z2[t].y * isB);
 #pragma unroll
-        for (int h = 0; h <= t; ++h) M2[t * (t + 1) / 2 + h] += wv * (zB[h] * isB);
+        for (int h = 0; h <= t; ++h) M2[t * (t + 1) / 2 + h] += wv * (z2[h].y * isB);
         M1[t] += wv;
       }
-    }
+    } else {
+    // pass A: density integral
+      const T sA = tA[k];
+      T wA = T(1);
+      T zA[R];
+#pragma unroll
+      for (int t = 0; t < R; ++t) {
+        T acc = aA[t] * sA;
+#pragma unroll
+        for (int h = 0; h < t; ++h) acc -= Lc[t * (t + 1) / 2 + h] * zA[h];
+        T pt, qt;
+        M::upper_pq(acc * Li[t], pt, qt);
+        wA *= pt;
+        if (t + 1 < R) zA[t] = M::neg_quantile(um[t], uu[t], pt, qt);
+      }
+      SA += wA;
+      if (e2lat) SL += wA * (logmA + T(2) * M::lg(sA));
+      if (!DENS) {
+        // pass B: the e1 numerator and the truncated moments
+        const T sB = tB[k];
+        const T isB = T(1) / sB;
+        T wB = T(1);
+        T zB[R];
+#pragma unroll
+        for (int t = 0; t < R; ++t) {
+          T acc = aB[t] * sB;
+#pragma unroll
+          for (int h = 0; h < t; ++h) acc -= Lc[t * (t + 1) / 2 + h] * zB[h];
+          T pt, qt;
+          M::upper_pq(acc * Li[t], pt, qt);
+          wB *= pt;
+          zB[t] = M::neg_quantile(um[t], uu[t], pt, qt);
+        }
+        SB += wB;
+#pragma unroll
+        for (int t = 0; t < R; ++t) {
+          const T wv = wB * (zB[t] * isB);
+#pragma unroll
+          for (int h = 0; h <= t; ++h) M2[t * (t + 1) / 2 + h] += wv * (zB[h] * isB);
+          M1[t] += wv;
+        }
+      }
+      }
   }
 
   SA = warp_sum(SA);

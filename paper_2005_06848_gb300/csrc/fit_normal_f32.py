@@ -10,7 +10,9 @@ error by Lawson's method), fitted on y in [0, 40].
 Quantile: Phi^{-1}(x) = sqrt(2) erfinv(2x - 1) and erfinv(v) = v P(w) with
 w = -log(1 - v^2) = -log(4 x (1 - x)).  P is piecewise polynomial: degree 8
 in w - 2.5 for w < 5, degree 7 in sqrt(w) - c1 for 5 <= w < 16, degree 6 in
-sqrt(w) - c2 for 16 <= w <= 88 (x down to the smallest normal float).
+sqrt(w) - c2 for 16 <= w <= 88 (x down to the smallest normal float).  A
+branch-free variant for the paired sweep uses one tail piece instead:
+P = sqrt(w) T(1/sqrt(w) - c3), T of degree 9, for 5 <= w <= 88.
 The targets come from scipy.special (erfcx, ndtri) in double precision.
 """
 import os
@@ -63,6 +65,17 @@ def fit_quantile_piece(wlo, whi, use_sqrt, deg):
     return cen, lawson(np.vander(v, deg + 1, increasing=True), P)
 
 
+def fit_quantile_tail_inv(wlo, whi, deg):
+    a, b = 1.0 / np.sqrt(whi), 1.0 / np.sqrt(wlo)
+    v = cheb_nodes(a, b, 8000)
+    w = 1.0 / (v * v)
+    y = np.sqrt(-np.expm1(-w))
+    one_minus_y = np.exp(-w) / (1.0 + y)
+    P = -special.ndtri(one_minus_y / 2.0) / np.sqrt(2.0) / y
+    cen = 0.5 * (a + b)
+    return cen, lawson(np.vander(v - cen, deg + 1, increasing=True), P * v, iters=80)
+
+
 def fmt(arr):
     return ", ".join(f"{float(np.float32(a)):.9e}f" for a in arr)
 
@@ -74,6 +87,7 @@ def main():
     c0, p0 = fit_quantile_piece(1e-12, 5.0, False, 8)
     c1, p1 = fit_quantile_piece(5.0, 16.0, True, 7)
     c2, p2 = fit_quantile_piece(16.0, wmax, True, 6)
+    c3, p3 = fit_quantile_tail_inv(5.0, wmax, 9)
     text = f"""// Generated by fit_normal_f32.py (least-squares fits iterated towards minimax
 // relative error); see that script for the forms.  Do not edit by hand.
 #pragma once
@@ -92,6 +106,8 @@ constexpr float Q_S1 = {np.float32(c1):.9e}f;   // 5 <= w < 16: P = poly(sqrt(w)
 __device__ constexpr float Q_P1[8] = {{{fmt(p1)}}};
 constexpr float Q_S2 = {np.float32(c2):.9e}f;   // w >= 16: P = poly(sqrt(w) - Q_S2)
 __device__ constexpr float Q_P2[7] = {{{fmt(p2)}}};
+constexpr float Q_U3 = {np.float32(c3):.9e}f;   // w >= 5 (branch-free form): P = sqrt(w) poly(1/sqrt(w) - Q_U3)
+__device__ constexpr float Q_P3[10] = {{{fmt(p3)}}};
 
 }}  // namespace nf32
 }}  // namespace cfust

@@ -85,6 +85,65 @@ __device__ __forceinline__ float phi_inv_f32(float x) {
   return 1.41421356237f * v * p;
 }
 
+// ---- paired forms: two independent evaluations per FP32x2 instruction ------
+// Coefficients duplicated into (c, c) pairs in constant memory.
+namespace nf32 {
+struct Pairs {
+  float2 tail_q[9];
+  float2 p0[9];
+  float2 p3[10];
+};
+__constant__ Pairs kPairs = {
+    {{TAIL_Q[0], TAIL_Q[0]}, {TAIL_Q[1], TAIL_Q[1]}, {TAIL_Q[2], TAIL_Q[2]}, {TAIL_Q[3], TAIL_Q[3]},
+     {TAIL_Q[4], TAIL_Q[4]}, {TAIL_Q[5], TAIL_Q[5]}, {TAIL_Q[6], TAIL_Q[6]}, {TAIL_Q[7], TAIL_Q[7]},
+     {TAIL_Q[8], TAIL_Q[8]}},
+    {{Q_P0[0], Q_P0[0]}, {Q_P0[1], Q_P0[1]}, {Q_P0[2], Q_P0[2]}, {Q_P0[3], Q_P0[3]}, {Q_P0[4], Q_P0[4]},
+     {Q_P0[5], Q_P0[5]}, {Q_P0[6], Q_P0[6]}, {Q_P0[7], Q_P0[7]}, {Q_P0[8], Q_P0[8]}},
+    {{Q_P3[0], Q_P3[0]}, {Q_P3[1], Q_P3[1]}, {Q_P3[2], Q_P3[2]}, {Q_P3[3], Q_P3[3]}, {Q_P3[4], Q_P3[4]},
+     {Q_P3[5], Q_P3[5]}, {Q_P3[6], Q_P3[6]}, {Q_P3[7], Q_P3[7]}, {Q_P3[8], Q_P3[8]}, {Q_P3[9], Q_P3[9]}}};
+
+template <int K>
+__device__ __forceinline__ float2 horner2(const float2 (&c)[K], float2 t) {
+  float2 q = c[K - 1];
+#pragma unroll
+  for (int k = K - 2; k >= 0; --k) q = __ffma2_rn(q, t, c[k]);
+  return q;
+}
+}  // namespace nf32
+
+__device__ __forceinline__ float2 f2(float v) { return make_float2(v, v); }
+
+// Paired phi_upper_pq_fast_f32.
+__device__ __forceinline__ void phi_upper_pq_x2(float2 y, float2 &p, float2 &q) {
+  const float2 a = make_float2(fabsf(y.x), fabsf(y.y));
+  const float2 den = __ffma2_rn(f2(nf32::TAIL_C), a, f2(1.0f));
+  const float2 t = make_float2(__fdividef(1.0f, den.x), __fdividef(1.0f, den.y));
+  const float2 G = __fmul2_rn(nf32::horner2(nf32::kPairs.tail_q, t), t);
+  const float2 k = __fmul2_rn(__fmul2_rn(a, a), f2(-0.72134752044f));
+  const float2 tail = __fmul2_rn(G, make_float2(exp2f_approx(k.x), exp2f_approx(k.y)));
+  const float2 big = __ffma2_rn(tail, f2(-1.0f), f2(1.0f));
+  p = make_float2(y.x >= 0.0f ? tail.x : big.x, y.y >= 0.0f ? tail.y : big.y);
+  q = make_float2(y.x >= 0.0f ? big.x : tail.x, y.y >= 0.0f ? big.y : tail.y);
+}
+
+// Paired, branch-free neg_quantile_f32: central piece below w = 5, single
+// tail piece P = sqrt(w) T(1/sqrt(w)) above.
+__device__ __forceinline__ float2 neg_quantile_x2(float um, float u, float2 p, float2 q) {
+  const float2 x = __fmul2_rn(f2(um), p);
+  const float2 c = __ffma2_rn(f2(um), q, f2(u));  // 1 - x
+  const bool lx = x.x <= 0.5f, ly = x.y <= 0.5f;
+  const float2 xs = make_float2(lx ? fmaxf(x.x, 1.17549435e-38f) : c.x, ly ? fmaxf(x.y, 1.17549435e-38f) : c.y);
+  const float2 prod = __fmul2_rn(__fmul2_rn(xs, f2(4.0f)), __ffma2_rn(xs, f2(-1.0f), f2(1.0f)));
+  const float2 w = make_float2(-__logf(prod.x), -__logf(prod.y));
+  const float2 pc = nf32::horner2(nf32::kPairs.p0, __fadd2_rn(w, f2(-nf32::Q_W0)));
+  const float2 rs = make_float2(rsqrtf(w.x), rsqrtf(w.y));
+  const float2 pt = __fmul2_rn(nf32::horner2(nf32::kPairs.p3, __fadd2_rn(rs, f2(-nf32::Q_U3))), __fmul2_rn(w, rs));
+  const float2 P = make_float2(w.x < 5.0f ? pc.x : pt.x, w.y < 5.0f ? pc.y : pt.y);
+  const float2 v = __ffma2_rn(f2(2.0f), xs, f2(-1.0f));
+  const float2 zq = __fmul2_rn(__fmul2_rn(v, P), f2(1.41421356237f));
+  return make_float2(lx ? -zq.x : zq.x, ly ? -zq.y : zq.y);
+}
+
 // z = -Phi^{-1}(x) for x = um * p, given also u = 1 - um and q = 1 - p; when
 // x > 1/2 the quantile is taken of 1 - x = u + um q, which keeps full relative
 // precision where x itself is within rounding of 1.

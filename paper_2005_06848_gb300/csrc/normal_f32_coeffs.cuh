@@ -16,6 +16,8 @@ constexpr float Q_S1 = 3.118033886e+00f;   // 5 <= w < 16: P = poly(sqrt(w) - Q_
 __device__ constexpr float Q_P1[8] = {2.951328993e+00f, 1.003614783e+00f, 7.143120747e-03f, -5.344045814e-03f, 3.995609470e-03f, -2.799534472e-03f, 1.053906628e-03f, -1.923229320e-05f};
 constexpr float Q_S2 = 6.662355900e+00f;   // w >= 16: P = poly(sqrt(w) - Q_S2)
 __device__ constexpr float Q_P2[7] = {6.528412819e+00f, 1.008939028e+00f, -5.080039264e-04f, 6.837136652e-07f, 6.515165296e-06f, -3.699315812e-06f, 8.880823543e-07f};
+constexpr float Q_U3 = 2.772277594e-01f;   // w >= 5 (branch-free form): P = sqrt(w) poly(1/sqrt(w) - Q_U3)
+__device__ constexpr float Q_P3[10] = {9.546209574e-01f, -1.925693303e-01f, 1.252948493e-01f, 5.648402572e-01f, 8.162746429e-01f, 1.152263451e+01f, 9.296464920e+00f, -1.601646576e+02f, -2.552538452e+02f, 1.114506958e+03f};
 
 }  // namespace nf32
 }  // namespace cfust
