@@ -93,6 +93,7 @@ typedef struct {
   double tol;             /* Aitken stopping threshold (Algorithm 4); 0 disables it */
   int use_graph;          /* 1: cfust_fit replays one CUDA graph per EM iteration */
   int timing;             /* 1: bracket every lattice-sweep kernel launch with CUDA events */
+  int pairs_per_warp;     /* observations one warp sweeps in turn (1..32); 0 = chosen from n and g */
 } cfust_opts;
 
 typedef struct cfust_ctx cfust_ctx;

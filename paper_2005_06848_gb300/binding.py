@@ -45,18 +45,20 @@ class cfust_opts(ctypes.Structure):
     _fields_ = [("precision", ctypes.c_int), ("lattice", cfust_lattice), ("e2_mode", ctypes.c_int),
                 ("nu_min", ctypes.c_double), ("nu_max", ctypes.c_double),
                 ("max_iter", ctypes.c_int), ("tol", ctypes.c_double), ("use_graph", ctypes.c_int),
-                ("timing", ctypes.c_int)]
+                ("timing", ctypes.c_int), ("pairs_per_warp", ctypes.c_int)]
 
 
 _LIB = None
 
 
-def load(build_if_missing: bool = True) -> ctypes.CDLL:
-    """Load libcfust.so (building it in-tree with nvcc when absent or stale)."""
+def load(build_if_missing: bool = True, path: str | None = None) -> ctypes.CDLL:
+    """Load libcfust.so (building it in-tree with nvcc when absent or stale).
+    `path` loads another build of the same library instead."""
     global _LIB
-    if _LIB is not None:
+    if _LIB is not None and path is None:
         return _LIB
-    path = _build.build() if build_if_missing else _build.LIB
+    if path is None:
+        path = _build.build() if build_if_missing else _build.LIB
     if not os.path.exists(path):
         raise RuntimeError(f"libcfust.so not found at {path}")
     lib = ctypes.CDLL(path)
@@ -110,7 +112,7 @@ class Context:
     """A cfust_ctx bound to the current CUDA device and a torch stream."""
 
     def __init__(self, lattice, precision=CFUST_FP32, e2_mode=0, nu_min=0.0, nu_max=0.0,
-                 max_iter=0, tol=0.0, use_graph=True, timing=False, stream=None):
+                 max_iter=0, tol=0.0, use_graph=True, timing=False, pairs_per_warp=0, stream=None):
         import torch
         self.lib = load()
         self._z = np.ascontiguousarray(lattice.z, dtype=np.int64)
@@ -119,7 +121,8 @@ class Context:
                             self._z.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)),
                             self._shift.ctypes.data_as(ctypes.POINTER(ctypes.c_double)))
         self.opts = cfust_opts(int(precision), lat, int(e2_mode), float(nu_min), float(nu_max),
-                               int(max_iter), float(tol), 1 if use_graph else 0, 1 if timing else 0)
+                               int(max_iter), float(tol), 1 if use_graph else 0, 1 if timing else 0,
+                               int(pairs_per_warp))
         self.precision = int(precision)
         self.stream = stream if stream is not None else torch.cuda.current_stream()
         self.lattice_n = int(lattice.n)

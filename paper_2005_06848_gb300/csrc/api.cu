@@ -291,7 +291,7 @@ cfust_status enqueue_iteration(cfust_ctx *c, const double *Y, int64_t n, cudaStr
                                c->d_chi32, c->d_status, st));
   CF_CUDA(c, launch_estep(c->opts.precision, Y, n, c->g, c->p, c->r, c->lat, c->d_c64, c->d_c32,
                           c->d_chi64, c->d_chi32, ctx_out(c), false, c->opts.e2_mode,
-                          c->d_rescue, c->d_rescue_cnt, c->d_status, 0, st,
+                          c->d_rescue, c->d_rescue_cnt, c->d_status, c->opts.pairs_per_warp, st,
                           sweep_timing(c, st == c->cap_stream), 1,
                           param_view(c->d_params, c->g, c->p, c->r).pi));
   PosteriorArgs a = post_args(c, Y, n);
@@ -318,7 +318,7 @@ cfust_status enqueue_loglik(cfust_ctx *c, const double *Y, int64_t n, double *tr
   o.logf = c->d_logf;
   CF_CUDA(c, launch_estep(c->opts.precision, Y, n, c->g, c->p, c->r, c->lat, c->d_c64, c->d_c32,
                           c->d_chi64, c->d_chi32, o, true, c->opts.e2_mode,
-                          c->d_rescue, c->d_rescue_cnt, c->d_status, 0, c->stream,
+                          c->d_rescue, c->d_rescue_cnt, c->d_status, c->opts.pairs_per_warp, c->stream,
                           sweep_timing(c, false), 1, param_view(c->d_params, c->g, c->p, c->r).pi));
   PosteriorArgs a = post_args(c, Y, n);
   a.logf = c->d_logf;
@@ -354,6 +354,10 @@ cfust_status cfust_create(cfust_ctx **out, const cfust_opts *o, void *cuda_strea
   }
   if (o->e2_mode != 0 && o->e2_mode != 1) {
     g_create_error = "e2_mode must be 0 or 1";
+    return CFUST_EINVAL;
+  }
+  if (o->pairs_per_warp < 0 || o->pairs_per_warp > 32) {
+    g_create_error = "pairs_per_warp must be in [0, 32]";
     return CFUST_EINVAL;
   }
   if (o->max_iter < 0 || !(o->tol >= 0.0)) {
@@ -496,7 +500,7 @@ cfust_status cfust_estep(cfust_ctx *c, const double *Y, int64_t n, const cfust_p
   o.e4 = e4;
   CF_CUDA(c, launch_estep(c->opts.precision, Y, n, c->g, c->p, c->r, c->lat, c->d_c64, c->d_c32,
                           c->d_chi64, c->d_chi32, o, false, c->opts.e2_mode,
-                          c->d_rescue, c->d_rescue_cnt, c->d_status, 0, c->stream,
+                          c->d_rescue, c->d_rescue_cnt, c->d_status, c->opts.pairs_per_warp, c->stream,
                           sweep_timing(c, false)));
   PosteriorArgs a = post_args(c, Y, n);
   a.logf = o.logf;

@@ -80,6 +80,10 @@ struct EArgs {
   int step[RMAX + 1];
   int sint[RMAX + 1];
   double sfrac[RMAX + 1];
+  // single-precision copies read straight from the parameter bank by the sweep
+  float fstep2[RMAX + 1];  // 2 * step
+  float ftwo_sf[RMAX + 1];  // 2 * sfrac
+  float fsf[RMAX + 1];      // sfrac
   const void *comp;  // CompT<T>[g]
   const void *chi;   // T[g][2][N]
   EstepOut out;
@@ -148,6 +152,28 @@ __device__ __forceinline__ void store(void *base, int64_t idx, T v) {
   reinterpret_cast<OT *>(base)[idx] = static_cast<OT>(v);
 }
 
+// Per-component operands of the paired sweep, duplicated into (x, x) pairs,
+// kept in shared memory so they occupy no registers.
+struct PairedConsts {
+  float2 nL[RMAX * (RMAX + 1) / 2];  // -L_th, packed lower triangle
+  float2 Li[RMAX];                   // 1 / L_tt
+};
+
+// Lattice constants of coordinate t in the sweep's precision: the float copies
+// live in the kernel parameters, the double path derives them from sfrac.
+template <typename T>
+__device__ __forceinline__ T lat_sf(const EArgs &a, int t) {
+  if constexpr (sizeof(T) == 4) return a.fsf[t]; else return a.sfrac[t];
+}
+template <typename T>
+__device__ __forceinline__ T lat_two_sf(const EArgs &a, int t) {
+  if constexpr (sizeof(T) == 4) return a.ftwo_sf[t]; else return 2.0 * a.sfrac[t];
+}
+template <typename T>
+__device__ __forceinline__ T lat_step2(const EArgs &a, int t) {
+  if constexpr (sizeof(T) == 4) return a.fstep2[t]; else return (double)(2 * a.step[t]);
+}
+
 // Per-pair prologue in double precision: z = A (y - mu), d = z^T z, q = B z and
 // the log of the t_p factor with the constant c0 of Eq. 2.
 template <int R>
@@ -199,7 +225,8 @@ __device__ __forceinline__ Prologue<R> shfl_prologue(const Prologue<R> &mine, in
 template <typename T, typename OT, int R, bool DENS>
 __device__ __forceinline__ bool pair_sweep(const EArgs &a, const CompT<T> &c, const Prologue<R> &pr,
                                            const T *__restrict__ tA, const T *__restrict__ tB,
-                                           int i, int64_t j, int lane, bool check) {
+                                           int i, int64_t j, int lane, bool check,
+                                           const PairedConsts *pc) {
   using M = Num<T>;
   constexpr int RP = R * (R + 1) / 2;
   constexpr bool PAIRED = (sizeof(T) == 4) && !DENS;
@@ -220,28 +247,20 @@ __device__ __forceinline__ bool pair_sweep(const EArgs &a, const CompT<T> &c, co
 #pragma unroll
     for (int h = 0; h <= t; ++h) Lc[t * (t + 1) / 2 + h] = c.L[t * RMAX + h];
   }
-  // paired operands: (pass A, pass B) limits and duplicated -L, 1/L_tt
-  float2 ab2[R], nL2[RP > 0 ? RP : 1], Li2[R];
+  // paired operands: (pass A, pass B) limits; -L and 1/L_tt pairs come from shared memory
+  float2 ab2[R];
   if constexpr (PAIRED) {
 #pragma unroll
-    for (int t = 0; t < R; ++t) {
-      ab2[t] = make_float2((float)aA[t], (float)aB[t]);
-      Li2[t] = make_float2((float)Li[t], (float)Li[t]);
-#pragma unroll
-      for (int h = 0; h <= t; ++h) nL2[t * (t + 1) / 2 + h] = make_float2(-(float)Lc[t * (t + 1) / 2 + h], -(float)Lc[t * (t + 1) / 2 + h]);
-    }
+    for (int t = 0; t < R; ++t) ab2[t] = make_float2((float)aA[t], (float)aB[t]);
   }
 
   // lattice state: fm_t = 2 m_t - N with m_t = (k z_t + sint_t) mod N for this
   // lane's point; integers below 2^17 are exact in float, so the update is exact
-  T fm[R], fstep[R], two_sf[R], half_sf2[R];
+  T fm[R];
 #pragma unroll
   for (int t = 0; t < R; ++t) {
     const int m0 = static_cast<int>(((int64_t)lane * a.z[t + 1] + a.sint[t + 1]) % N);
     fm[t] = static_cast<T>(2 * m0 - N);
-    fstep[t] = static_cast<T>(2 * a.step[t + 1]);
-    two_sf[t] = static_cast<T>(2.0 * a.sfrac[t + 1]);
-    half_sf2[t] = static_cast<T>(a.sfrac[t + 1]);
   }
   const T fN = static_cast<T>(N);
   const T invN = T(1) / fN;
@@ -263,11 +282,12 @@ __device__ __forceinline__ bool pair_sweep(const EArgs &a, const CompT<T> &c, co
     T um[R], uu[R];
 #pragma unroll
     for (int t = 0; t < R; ++t) {
+      const T sf = lat_sf<T>(a, t + 1);
       const T mm = T(0.5) * (fm[t] + fN);
-      const T lo = mm + half_sf2[t], hi = (fN - mm) - half_sf2[t];
-      um[t] = M::mn(M::mx(M::ab(fm[t] + two_sf[t]) * invN, umin), umax);
+      const T lo = mm + sf, hi = (fN - mm) - sf;
+      um[t] = M::mn(M::mx(M::ab(fm[t] + lat_two_sf<T>(a, t + 1)) * invN, umin), umax);
       uu[t] = M::mx(T(2) * M::mn(lo, hi) * invN, umin);
-      fm[t] += fstep[t];
+      fm[t] += lat_step2<T>(a, t + 1);
       if (fm[t] >= fN) fm[t] -= T(2) * fN;
     }
     if constexpr (PAIRED) {
@@ -279,9 +299,9 @@ __device__ __forceinline__ bool pair_sweep(const EArgs &a, const CompT<T> &c, co
       for (int t = 0; t < R; ++t) {
         float2 acc2 = __fmul2_rn(ab2[t], s2);
 #pragma unroll
-        for (int h = 0; h < t; ++h) acc2 = __ffma2_rn(nL2[t * (t + 1) / 2 + h], z2[h], acc2);
+        for (int h = 0; h < t; ++h) acc2 = __ffma2_rn(pc->nL[t * (t + 1) / 2 + h], z2[h], acc2);
         float2 p2, q2;
-        phi_upper_pq_x2(__fmul2_rn(acc2, Li2[t]), p2, q2);
+        phi_upper_pq_x2(__fmul2_rn(acc2, pc->Li[t]), p2, q2);
         w2 = __fmul2_rn(w2, p2);
         z2[t] = neg_quantile_x2(um[t], uu[t], p2, q2);
       }
@@ -424,15 +444,23 @@ __device__ __forceinline__ bool pair_sweep(const EArgs &a, const CompT<T> &c, co
   return false;
 }
 
+// Minimum resident CTAs per SM the compiler must allow for the sweep kernel
+// (caps its registers at 65536 / (256 * CFUST_ESTEP_MINB)).
+#ifndef CFUST_ESTEP_MINB
+#define CFUST_ESTEP_MINB 2
+#endif
+
 template <typename T, int R, bool DENS>
-__global__ void __launch_bounds__(256) estep_kernel(EArgs a) {
+__global__ void __launch_bounds__(256, sizeof(T) == 4 ? CFUST_ESTEP_MINB : 1) estep_kernel(EArgs a) {
   extern __shared__ __align__(128) unsigned char smem[];
   const int i = blockIdx.y;
   const int N = a.N;
   const size_t tab_bytes = a.staged ? (size_t)(DENS ? 1 : 2) * N * sizeof(T) : 0;
   T *tab = reinterpret_cast<T *>(smem);
   CompT<T> *cs = reinterpret_cast<CompT<T> *>(smem + align16(tab_bytes));
-  uint64_t *bar = reinterpret_cast<uint64_t *>(smem + align16(tab_bytes) + align16(sizeof(CompT<T>)));
+  PairedConsts *pcs = reinterpret_cast<PairedConsts *>(smem + align16(tab_bytes) + align16(sizeof(CompT<T>)));
+  uint64_t *bar = reinterpret_cast<uint64_t *>(smem + align16(tab_bytes) + align16(sizeof(CompT<T>)) +
+                                               align16(sizeof(PairedConsts)));
   const T *gtab = reinterpret_cast<const T *>(a.chi) + (int64_t)i * 2 * N;
 
   if (a.staged && threadIdx.x == 0) {
@@ -443,6 +471,18 @@ __global__ void __launch_bounds__(256) estep_kernel(EArgs a) {
   const uint32_t *src = reinterpret_cast<const uint32_t *>(reinterpret_cast<const CompT<T> *>(a.comp) + i);
   uint32_t *dst = reinterpret_cast<uint32_t *>(cs);
   for (int w = threadIdx.x; w < (int)(sizeof(CompT<T>) / 4); w += blockDim.x) dst[w] = src[w];
+  __syncthreads();
+  if (threadIdx.x < RMAX * RMAX) {
+    const int t = threadIdx.x / RMAX, h = threadIdx.x % RMAX;
+    if (h <= t) {
+      const float v = -(float)cs->L[t * RMAX + h];
+      pcs->nL[t * (t + 1) / 2 + h] = make_float2(v, v);
+    }
+    if (h == 0) {
+      const float li = (float)cs->Linv[t];
+      pcs->Li[t] = make_float2(li, li);
+    }
+  }
   __syncthreads();
   if (a.staged) {
     if (!mbar_wait_bounded(bar, 0, 1 << 22)) {
@@ -465,7 +505,7 @@ __global__ void __launch_bounds__(256) estep_kernel(EArgs a) {
   for (int b = 0; b < cnt; ++b) {
     const Prologue<R> pr = shfl_prologue<R>(mine, b);
     const int64_t j = jw0 + b;
-    const bool need = pair_sweep<T, T, R, DENS>(a, *cs, pr, tA, tB, i, j, lane, check);
+    const bool need = pair_sweep<T, T, R, DENS>(a, *cs, pr, tA, tB, i, j, lane, check, pcs);
     if (need && lane == 0) {
       const unsigned slot = atomicAdd(a.rescue_count, 1u);
       a.rescue_list[slot] = (unsigned long long)i * (unsigned long long)a.n + (unsigned long long)j;
@@ -741,7 +781,8 @@ cudaError_t launch_r(EArgs a, int g, int64_t n, cudaStream_t st, bool fp32,
                      const CompT<double> *c64, const double *chi64, SweepTiming tm) {
   const size_t tab_bytes = (size_t)(DENS ? 1 : 2) * a.N * sizeof(T);
   a.staged = tab_bytes <= 160u * 1024u ? 1 : 0;
-  const size_t smem = (a.staged ? align16(tab_bytes) : 0) + align16(sizeof(CompT<T>)) + 16;
+  const size_t smem = (a.staged ? align16(tab_bytes) : 0) + align16(sizeof(CompT<T>)) +
+                      align16(sizeof(PairedConsts)) + 16;
   cudaError_t e = cudaFuncSetAttribute(estep_kernel<T, R, DENS>,
                                        cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
@@ -827,12 +868,17 @@ cudaError_t launch_estep(int precision, const double *Y, int64_t n, int g, int p
     a.step[t] = lat.step[t];
     a.sint[t] = lat.sint[t];
     a.sfrac[t] = lat.sfrac[t];
+    a.fstep2[t] = (float)(2 * lat.step[t]);
+    a.ftwo_sf[t] = (float)(2.0 * lat.sfrac[t]);
+    a.fsf[t] = (float)lat.sfrac[t];
   }
   a.out = out;
   a.e2_mode = e2_mode;
   if (pairs_per_warp <= 0) {
-    // enough CTAs for about four waves of two CTAs per SM, at most 32 pairs per warp
-    const int64_t target_ctas = 152 * 2 * 4;
+    // about sixteen waves of two resident CTAs per SM (8 warps each), so the
+    // last wave's imbalance stays small; 1..32 pairs per warp (measured best
+    // near 8 on the p=4, r=4, g=3, n=100000 workload)
+    const int64_t target_ctas = 152 * 2 * 16;
     int64_t ppw = ((int64_t)g * n) / (target_ctas * 8);
     pairs_per_warp = (int)(ppw < 1 ? 1 : (ppw > 32 ? 32 : ppw));
   }
