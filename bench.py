@@ -69,6 +69,24 @@ def peak_fp32_tflops(sm_mhz: float) -> float:
     return 152 * 128 * 2 * sm_mhz * 1e6 / 1e12
 
 
+def sweep_traffic_bytes():
+    """DRAM bytes per sweep launch from the committed ncu capture, or None when
+    the sweep sources changed since those counters were taken."""
+    import hashlib
+    try:
+        with open(os.path.join(ROOT, "profiles", "estep_kernel_p4r4g3_n100000_N4096.json")) as f:
+            rec = json.load(f)
+        h = hashlib.sha256()
+        for name in ("estep.cu", "normal_f32.cuh", "normal_f32_coeffs.cuh", "cfust_internal.cuh"):
+            with open(os.path.join(ROOT, "paper_2005_06848_gb300", "csrc", name), "rb") as f:
+                h.update(f.read())
+        if h.hexdigest() != rec["source_sha256"]:
+            return None
+        return int(rec["dram_bytes_read"]) + int(rec["dram_bytes_write"])
+    except Exception:
+        return None
+
+
 def load_peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
@@ -332,7 +350,7 @@ def run_ours(args):
         "loglik_first_last": [float(trace[0]), float(trace[-1])],
         "gpu_launches": 6 * args.steps,
         "roofline": {"bound": "alu", "kernel": "estep_kernel<float,4>", "achieved": achieved,
-                     "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak, "traffic": None,
+                     "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak, "traffic": sweep_traffic_bytes(),
                      "peak_source": f"FP32 FMA peak 152 SMs x 128 lanes x 2 x {sm_max:.0f} MHz (derived)",
                      "sweep_ms_mean": mean_sweep_ms,
                      "flops_per_launch": flops},
