@@ -180,6 +180,41 @@ cfust_status cfust_last_sweep_ms(cfust_ctx *ctx, float *ms);
  *         4: log Phi(-x) (this library)   5: -Phi^{-1}(exp(x)) (this library, x <= 0) */
 cfust_status cfust_normal_f32(const float *x, float *out, int64_t n, int which, void *stream);
 
+/* M-step without a context and without any device allocation.
+ *
+ * For callers that cannot allocate device memory on the call path, e.g. code
+ * running under an external memory manager that forbids cudaMalloc after
+ * start-up, or a host that must not grow its device footprint per call.  It
+ * computes what cfust_mstep computes (the eight sums of Section 3.2 and the
+ * conditional-maximisation update) from caller-owned inputs.  The paper has
+ * no counterpart: this is an interface variant only.
+ *
+ * Scratch (status words, the device copy of params, per-block partial sums)
+ * lives in one static device array of CFUST_NOALLOC_SCRATCH_BYTES (1 MiB) that
+ * every GPU loading this library holds until the process exits.  The number of
+ * reduction blocks is reduced to fit it, but at least CFUST_NOALLOC_MIN_BLOCKS
+ * blocks' partial sums (8 * g * (3 + p + r + p r + r(r+1)/2 + p(p+1)/2) bytes
+ * each) plus the parameters must fit; larger problems (e.g. g = 64, p = 16,
+ * r = 6) return CFUST_EINVAL with a message naming the limit.
+ * The first call on a device looks up the array's device address with
+ * cudaGetSymbolAddress (with that device current); make that first call
+ * before any stream capture.  All calls share the array: calls that overlap
+ * on the GPU (different streams, or different host threads) race and must be
+ * serialised by the caller.  No cudaMalloc, cudaFree or allocating library
+ * routine is called.
+ *
+ * precision: CFUST_FP64 or CFUST_FP32 (element type of tau, e1..e4).
+ * Y, tau, e1..e4: device, layouts as for cfust_estep.  params: host, updated
+ * in place.  nu_min, nu_max: 0, 0 selects [1, 200].  stream: cudaStream_t
+ * (NULL = legacy default stream).  Synchronises the stream.  Messages come
+ * from cfust_last_error(NULL). */
+#define CFUST_NOALLOC_SCRATCH_BYTES (1u << 20)
+#define CFUST_NOALLOC_MIN_BLOCKS 8
+cfust_status cfust_mstep_noalloc(int precision, const double *Y, int64_t n,
+                                 const void *tau, const void *e1, const void *e2,
+                                 const void *e3, const void *e4, double nu_min, double nu_max,
+                                 cfust_params *params, void *cuda_stream);
+
 /* Message for the last error on ctx (or on context creation when ctx is NULL). */
 const char *cfust_last_error(cfust_ctx *ctx);
 

@@ -20,7 +20,8 @@ STATUS = {0: "CFUST_OK", -1: "CFUST_EINVAL", -2: "CFUST_ENOTPD", -3: "CFUST_ENUM
 
 EXPORTED = ["cfust_create", "cfust_destroy", "cfust_loglik", "cfust_estep", "cfust_mstep",
             "cfust_fit", "cfust_fit_begin", "cfust_fit_step", "cfust_fit_end", "cfust_fit_trace",
-            "cfust_last_rescued", "cfust_last_sweep_ms", "cfust_normal_f32", "cfust_last_error"]
+            "cfust_last_rescued", "cfust_last_sweep_ms", "cfust_normal_f32", "cfust_mstep_noalloc",
+            "cfust_last_error"]
 
 
 class CfustError(RuntimeError):
@@ -79,6 +80,8 @@ def load(build_if_missing: bool = True, path: str | None = None) -> ctypes.CDLL:
         "cfust_last_sweep_ms": ([vp, ctypes.POINTER(ctypes.c_float)], ctypes.c_int),
         "cfust_last_error": ([vp], ctypes.c_char_p),
         "cfust_normal_f32": ([vp, vp, i64, ctypes.c_int, vp], ctypes.c_int),
+        "cfust_mstep_noalloc": ([ctypes.c_int, vp, i64, vp, vp, vp, vp, vp, ctypes.c_double,
+                                 ctypes.c_double, P, vp], ctypes.c_int),
     }
     for name, (args, res) in sig.items():
         fn = getattr(lib, name)
@@ -256,6 +259,21 @@ def cfust_normal_f32(x, which, stream=None):
         raise CfustError(rc, "cfust_normal_f32 failed")
     st.synchronize()
     return out
+
+
+def cfust_mstep_noalloc(precision, Y, E, params, nu_min=0.0, nu_max=0.0, stream=None):
+    """M-step through the allocation-free entry point (no context; scratch in a
+    static device array, see include/cfust.h).  Returns the updated params."""
+    import torch
+    lib = load()
+    hp = _HostParams(params)
+    st = stream if stream is not None else torch.cuda.current_stream()
+    rc = lib.cfust_mstep_noalloc(int(precision), _ptr(Y), Y.shape[0], _ptr(E["tau"]), _ptr(E["e1"]),
+                                 _ptr(E["e2"]), _ptr(E["e3"]), _ptr(E["e4"]), float(nu_min), float(nu_max),
+                                 ctypes.byref(hp.c), ctypes.c_void_p(st.cuda_stream))
+    if rc != 0:
+        raise CfustError(rc, lib.cfust_last_error(None).decode())
+    return hp.to_params()
 
 
 def unpack_e4(e4, r):

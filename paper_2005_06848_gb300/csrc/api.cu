@@ -5,6 +5,7 @@
 #include <stdio.h>
 #include <string.h>
 
+#include <mutex>
 #include <string>
 #include <vector>
 
@@ -668,3 +669,127 @@ cfust_status cfust_fit(cfust_ctx *c, const double *Y, int64_t n, cfust_params *P
 }
 
 }  // extern "C"
+
+// ---------------------------------------------------------------------------
+// M-step without allocation: scratch in a static device array.
+// ---------------------------------------------------------------------------
+
+namespace {
+
+// Every GPU that loads this library holds this array until the process exits.
+static __device__ __align__(256) unsigned char g_noalloc_scratch[CFUST_NOALLOC_SCRATCH_BYTES];
+
+constexpr int kMaxDevices = 64;
+std::mutex g_noalloc_mutex;
+void *g_noalloc_addr[kMaxDevices] = {};  // per device ordinal, looked up on first use
+
+size_t round256(size_t x) { return (x + 255) & ~size_t(255); }
+
+cfust_status noalloc_fail(cfust_status s, const char *msg) {
+  g_create_error = msg;
+  return s;
+}
+
+}  // namespace
+
+extern "C" cfust_status cfust_mstep_noalloc(int precision, const double *Y, int64_t n, const void *tau,
+                                           const void *e1, const void *e2, const void *e3,
+                                           const void *e4, double nu_min, double nu_max,
+                                           cfust_params *P, void *cuda_stream) {
+  g_create_error.clear();
+  if (precision != CFUST_FP64 && precision != CFUST_FP32)
+    return noalloc_fail(CFUST_EINVAL, "precision must be CFUST_FP64 or CFUST_FP32");
+  if (!Y || !tau || !e1 || !e2 || !e3 || !e4 || !P || n < 1)
+    return noalloc_fail(CFUST_EINVAL, "Y, tau, e1..e4 and params must be given and n >= 1");
+  const int g = P->g, p = P->p, r = P->r;
+  if (g < 1 || g > CFUST_GMAX || p < 1 || p > CFUST_PMAX || r < 1 || r > CFUST_RMAX)
+    return noalloc_fail(CFUST_EINVAL, "g, p or r out of range");
+  if (!P->pi || !P->mu || !P->Sigma || !P->Delta || !P->nu)
+    return noalloc_fail(CFUST_EINVAL, "a parameter array is NULL");
+  double spi = 0.0;
+  for (int i = 0; i < g; ++i) {
+    if (!(P->pi[i] > 0.0) || !(P->nu[i] > 0.0)) return noalloc_fail(CFUST_EINVAL, "pi_i and nu_i must be > 0");
+    spi += P->pi[i];
+  }
+  if (fabs(spi - 1.0) > 1e-10) return noalloc_fail(CFUST_EINVAL, "pi must sum to 1");
+  if ((nu_min != 0.0 || nu_max != 0.0) && !(nu_min > 0.0 && nu_max > nu_min))
+    return noalloc_fail(CFUST_EINVAL, "need 0 < nu_min < nu_max");
+  const double lo = nu_min > 0 ? nu_min : 1.0, hi = nu_max > 0 ? nu_max : 200.0;
+
+  // layout: [status: 2 ints][parameter block][per-block partial sums]
+  const size_t pbytes = sizeof(double) * (size_t)param_block_size(g, p, r);
+  const size_t off_params = 256, off_part = off_params + round256(pbytes);
+  const size_t per_block = sizeof(double) * (size_t)g * sums_width(p, r);
+  if (off_part + CFUST_NOALLOC_MIN_BLOCKS * per_block > CFUST_NOALLOC_SCRATCH_BYTES)
+    return noalloc_fail(CFUST_EINVAL,
+                        "parameters plus CFUST_NOALLOC_MIN_BLOCKS blocks of partial sums exceed "
+                        "CFUST_NOALLOC_SCRATCH_BYTES (1 MiB): g, p or r too large for cfust_mstep_noalloc");
+  int nb = posterior_nblocks(n);
+  const int cap = (int)((CFUST_NOALLOC_SCRATCH_BYTES - off_part) / per_block);
+  if (nb > cap) nb = cap;
+
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices)
+    return noalloc_fail(CFUST_ECUDA, "no usable current CUDA device");
+  unsigned char *base = nullptr;
+  {
+    std::lock_guard<std::mutex> lock(g_noalloc_mutex);
+    if (!g_noalloc_addr[dev]) {
+      void *addr = nullptr;
+      const cudaError_t e = cudaGetSymbolAddress(&addr, g_noalloc_scratch);
+      if (e != cudaSuccess || !addr) return noalloc_fail(CFUST_ECUDA, "cudaGetSymbolAddress failed");
+      g_noalloc_addr[dev] = addr;
+    }
+    base = static_cast<unsigned char *>(g_noalloc_addr[dev]);
+  }
+  cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
+  int *d_status = reinterpret_cast<int *>(base);
+  double *d_params = reinterpret_cast<double *>(base + off_params);
+  double *d_part = reinterpret_cast<double *>(base + off_part);
+  ParamView v = param_view(d_params, g, p, r);
+
+#define NA_CUDA(call)                                                   \
+  do {                                                                  \
+    if ((call) != cudaSuccess) return noalloc_fail(CFUST_ECUDA, #call); \
+  } while (0)
+  NA_CUDA(cudaMemsetAsync(d_status, 0, 2 * sizeof(int), st));
+  NA_CUDA(cudaMemcpyAsync(v.pi, P->pi, sizeof(double) * g, cudaMemcpyHostToDevice, st));
+  NA_CUDA(cudaMemcpyAsync(v.mu, P->mu, sizeof(double) * g * p, cudaMemcpyHostToDevice, st));
+  NA_CUDA(cudaMemcpyAsync(v.Sigma, P->Sigma, sizeof(double) * g * p * p, cudaMemcpyHostToDevice, st));
+  NA_CUDA(cudaMemcpyAsync(v.Delta, P->Delta, sizeof(double) * g * p * r, cudaMemcpyHostToDevice, st));
+  NA_CUDA(cudaMemcpyAsync(v.nu, P->nu, sizeof(double) * g, cudaMemcpyHostToDevice, st));
+  PosteriorArgs pa{};
+  pa.Y = Y;
+  pa.n = n;
+  pa.g = g;
+  pa.p = p;
+  pa.r = r;
+  pa.pi = v.pi;
+  pa.tau_in = tau;
+  pa.e1 = e1;
+  pa.e2 = e2;
+  pa.e3 = e3;
+  pa.e4 = e4;
+  pa.want_sums = true;
+  pa.partials = d_part;
+  pa.d_status = d_status;
+  pa.nblocks = nb;
+  NA_CUDA(launch_posterior(precision, pa, st));
+  NA_CUDA(launch_mstep_finalize(d_part, nb, g, p, r, n, lo, hi, d_params, d_status, st));
+  int bits = 0;
+  NA_CUDA(cudaMemcpyAsync(&bits, d_status, sizeof(int), cudaMemcpyDeviceToHost, st));
+  NA_CUDA(cudaStreamSynchronize(st));
+  if (bits != 0) {
+    if (bits & (ERR_NOTPD_S6 | ERR_NOTPD_SIGMA)) return noalloc_fail(CFUST_ENOTPD, "S6 or the updated Sigma not positive definite");
+    if (bits & ERR_DEGENERATE) return noalloc_fail(CFUST_EDEGENERATE, "a component lost its posterior weight");
+    return noalloc_fail(CFUST_ENUMERIC, "non-finite value in the M-step");
+  }
+  NA_CUDA(cudaMemcpyAsync(P->pi, v.pi, sizeof(double) * g, cudaMemcpyDeviceToHost, st));
+  NA_CUDA(cudaMemcpyAsync(P->mu, v.mu, sizeof(double) * g * p, cudaMemcpyDeviceToHost, st));
+  NA_CUDA(cudaMemcpyAsync(P->Sigma, v.Sigma, sizeof(double) * g * p * p, cudaMemcpyDeviceToHost, st));
+  NA_CUDA(cudaMemcpyAsync(P->Delta, v.Delta, sizeof(double) * g * p * r, cudaMemcpyDeviceToHost, st));
+  NA_CUDA(cudaMemcpyAsync(P->nu, v.nu, sizeof(double) * g, cudaMemcpyDeviceToHost, st));
+  NA_CUDA(cudaStreamSynchronize(st));
+#undef NA_CUDA
+  return CFUST_OK;
+}
