@@ -241,7 +241,8 @@ cfust_status check_common(cfust_ctx *c, const double *Y, int64_t n, const cfust_
   if (!c) return CFUST_EINVAL;
   if (!Y) return fail(c, CFUST_EINVAL, "Y is NULL");
   if (n < 1) return fail(c, CFUST_EINVAL, "n must be >= 1");
-  if ((uint64_t)n * (uint64_t)(P ? P->g : 1) >= (1ull << 40)) return fail(c, CFUST_EINVAL, "n too large");
+  if ((uint64_t)n >= (1ull << 32) || (uint64_t)n * (uint64_t)(P ? P->g : 1) >= (1ull << 40))
+    return fail(c, CFUST_EINVAL, "n too large (n < 2^32, n g < 2^40)");
   if (reinterpret_cast<uintptr_t>(Y) % 8 != 0) return fail(c, CFUST_EINVAL, "Y must be 8-byte aligned");
   return check_params(c, P);
 }

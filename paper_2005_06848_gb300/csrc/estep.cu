@@ -97,6 +97,32 @@ struct EArgs {
   const double *pi;    // device [g], read by the triage
 };
 
+// The per-fit part of a sweep: observations, their count, the component
+// count, the per-pair output arrays and the mixing proportions.  A single fit
+// takes it from EArgs; the batched sweep builds one per work item.
+struct FitView {
+  const double *Y;
+  int64_t n;
+  int g;
+  EstepOut out;
+  const double *pi;
+};
+
+__device__ __forceinline__ FitView fit_view(const EArgs &a) {
+  FitView f;
+  f.Y = a.Y;
+  f.n = a.n;
+  f.g = a.g;
+  f.out = a.out;
+  f.pi = a.pi;
+  return f;
+}
+
+// Queued pair: component index in the high 32 bits, observation in the low.
+__device__ __forceinline__ unsigned long long pair_id(int i, int64_t j) {
+  return ((unsigned long long)(unsigned)i << 32) | (unsigned long long)j;
+}
+
 __host__ __device__ constexpr size_t align16(size_t x) { return (x + 15) & ~size_t(15); }
 
 // ---- bulk async copy global -> shared, completion on an mbarrier ---------
@@ -183,10 +209,11 @@ struct Prologue {
 };
 
 template <typename T, int R>
-__device__ __forceinline__ Prologue<R> prologue(const EArgs &a, const CompT<T> &c, int64_t j) {
+__device__ __forceinline__ Prologue<R> prologue(const EArgs &a, const FitView &fv, const CompT<T> &c,
+                                                int64_t j) {
   Prologue<R> pr;
   const int p = a.p;
-  const double *yj = a.Y + j * (int64_t)p;
+  const double *yj = fv.Y + j * (int64_t)p;
   double yc[PMAX];
 #pragma unroll
   for (int k = 0; k < PMAX; ++k) yc[k] = (k < p) ? yj[k] - c.mu[k] : 0.0;
@@ -223,7 +250,8 @@ __device__ __forceinline__ Prologue<R> shfl_prologue(const Prologue<R> &mine, in
 // over the warp) when `check` is set and the single-precision sweep needs the
 // double rescue; in that case nothing is written.
 template <typename T, typename OT, int R, bool DENS>
-__device__ __forceinline__ bool pair_sweep(const EArgs &a, const CompT<T> &c, const Prologue<R> &pr,
+__device__ __forceinline__ bool pair_sweep(const EArgs &a, const FitView &fv, const CompT<T> &c,
+                                           const Prologue<R> &pr,
                                            const T *__restrict__ tA, const T *__restrict__ tB,
                                            int i, int64_t j, int lane, bool check,
                                            const PairedConsts *pc) {
@@ -372,7 +400,7 @@ __device__ __forceinline__ bool pair_sweep(const EArgs &a, const CompT<T> &c, co
   }
 
   const T logf = static_cast<T>(pr.logt) + M::lg(SA) - M::lg(static_cast<T>(N));
-  const int64_t n = a.n;
+  const int64_t n = fv.n;
   const int64_t ij = (int64_t)i * n + j;
   if (check) {
     const T thr = T(1e-20) * static_cast<T>(N);
@@ -383,15 +411,15 @@ __device__ __forceinline__ bool pair_sweep(const EArgs &a, const CompT<T> &c, co
       // upper bound of log f for the triage: the float sum misses only point
       // weights that fell below the float range, so T <= max(S_A / N, 1e-37) up
       // to rounding; one nat of margin; +inf when the sum is not finite
-      if (a.triage && a.out.logf != nullptr && lane == 0) {
+      if (a.triage && fv.out.logf != nullptr && lane == 0) {
         const double sa = (double)SA / (double)N;
         const double ub = isfinite(sa) ? pr.logt + log(fmax(sa, 1e-37)) + 1.0 : INFINITY;
-        store<OT>(a.out.logf, ij, ub);
+        store<OT>(fv.out.logf, ij, ub);
       }
       return true;
     }
   }
-  if (a.out.logf != nullptr && lane == 0) store<OT>(a.out.logf, ij, logf);
+  if (fv.out.logf != nullptr && lane == 0) store<OT>(fv.out.logf, ij, logf);
   if (DENS) return false;
 
   const bool ok = (SA > T(0)) && (SB > T(0));
@@ -414,11 +442,11 @@ __device__ __forceinline__ bool pair_sweep(const EArgs &a, const CompT<T> &c, co
     e2 = ok ? e1 - static_cast<T>(log(0.5 * nud64) + c.mA / nud64 - c.psiA) : T(0);
 
   // lane-parallel stores: lane 0 wrote logf; lane 1 e1, lane 2 e2, lanes 3.. e3 then e4
-  if (lane == 1) store<OT>(a.out.e1, ij, e1);
-  if (lane == 2) store<OT>(a.out.e2, ij, e2);
+  if (lane == 1) store<OT>(fv.out.e1, ij, e1);
+  if (lane == 2) store<OT>(fv.out.e2, ij, e2);
 #pragma unroll
   for (int t = 0; t < R; ++t) {
-    if (lane == 3 + t) store<OT>(a.out.e3, ((int64_t)i * R + t) * n + j, e1 * (q[t] + sig * LEV[t]));
+    if (lane == 3 + t) store<OT>(fv.out.e3, ((int64_t)i * R + t) * n + j, e1 * (q[t] + sig * LEV[t]));
   }
   // E[V V^T] in the L basis: (L EVV L^T)_th = sum_{a<=t} sum_{b<=h} L_ta EVV_ab L_hb
 #pragma unroll
@@ -437,11 +465,36 @@ __device__ __forceinline__ bool pair_sweep(const EArgs &a, const CompT<T> &c, co
           }
         }
         const T exx = q[t] * q[h] + sig * (q[t] * LEV[h] + LEV[t] * q[h]) + sig * sig * s;
-        store<OT>(a.out.e4, ((int64_t)i * RP + t * (t + 1) / 2 + h) * n + j, e1 * exx);
+        store<OT>(fv.out.e4, ((int64_t)i * RP + t * (t + 1) / 2 + h) * n + j, e1 * exx);
       }
     }
   }
   return false;
+}
+
+// One warp sweeps observations [jw0, jw0 + ppw) of component i of a fit: lane b
+// computes the double prologue of the b-th observation, then the warp sweeps
+// them one at a time.  `qi` is the component index recorded for queued pairs
+// (the fit's own index, or the global one in a batch).
+template <typename T, int R, bool DENS>
+__device__ __forceinline__ void sweep_warp_pairs(const EArgs &a, const FitView &fv, const CompT<T> &c,
+                                                 const PairedConsts *pcs, const T *tA, const T *tB,
+                                                 int i, int qi, int64_t jw0, int ppw) {
+  const int lane = threadIdx.x & 31;
+  int cnt = 0;
+  if (jw0 < fv.n) cnt = (int)((fv.n - jw0) < ppw ? (fv.n - jw0) : ppw);
+  Prologue<R> mine;
+  if (lane < cnt) mine = prologue<T, R>(a, fv, c, jw0 + lane);
+  const bool check = (sizeof(T) == 4);
+  for (int b = 0; b < cnt; ++b) {
+    const Prologue<R> pr = shfl_prologue<R>(mine, b);
+    const int64_t j = jw0 + b;
+    const bool need = pair_sweep<T, T, R, DENS>(a, fv, c, pr, tA, tB, i, j, lane, check, pcs);
+    if (need && lane == 0) {
+      const unsigned slot = atomicAdd(a.rescue_count, 1u);
+      a.rescue_list[slot] = pair_id(qi, j);
+    }
+  }
 }
 
 // Minimum resident CTAs per SM the compiler must allow for the sweep kernel
@@ -493,24 +546,9 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? CFUST_ESTEP_MINB : 1) es
   const T *tA = a.staged ? tab : gtab;
   const T *tB = tA + N;
 
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
-  // this warp's observations: ppw consecutive j; lane b computes the double
-  // prologue of the b-th of them, then the warp sweeps them one at a time
+  const int warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
   const int64_t jw0 = ((int64_t)blockIdx.x * nw + warp) * a.ppw;
-  int cnt = 0;
-  if (jw0 < a.n) cnt = (int)((a.n - jw0) < a.ppw ? (a.n - jw0) : a.ppw);
-  Prologue<R> mine;
-  if (lane < cnt) mine = prologue<T, R>(a, *cs, jw0 + lane);
-  const bool check = (sizeof(T) == 4);
-  for (int b = 0; b < cnt; ++b) {
-    const Prologue<R> pr = shfl_prologue<R>(mine, b);
-    const int64_t j = jw0 + b;
-    const bool need = pair_sweep<T, T, R, DENS>(a, *cs, pr, tA, tB, i, j, lane, check, pcs);
-    if (need && lane == 0) {
-      const unsigned slot = atomicAdd(a.rescue_count, 1u);
-      a.rescue_list[slot] = (unsigned long long)i * (unsigned long long)a.n + (unsigned long long)j;
-    }
-  }
+  sweep_warp_pairs<T, R, DENS>(a, fit_view(a), *cs, pcs, tA, tB, i, i, jw0, a.ppw);
 }
 
 // One coordinate of the log-domain sweep: log p for p = Phi(-lim) and the
@@ -564,7 +602,8 @@ __device__ __forceinline__ void lse_add(double &m, float &s, double lw, float &s
 // and accumulated against a running maximum, per lane, warp and CTA, so nothing
 // underflows.  `sm` is shared scratch of at least 8 * (4 + 3 + R + R(R+1)/2) words.
 template <int R, bool DENS>
-__device__ void pair_sweep_log_cta(const EArgs &a, const CompT<double> &c, const Prologue<R> &pr,
+__device__ void pair_sweep_log_cta(const EArgs &a, const FitView &fv, const CompT<double> &c,
+                                   const Prologue<R> &pr,
                                    const double *__restrict__ tA, const double *__restrict__ tB, int i,
                                    int64_t j, double *sm) {
   constexpr int RP = R * (R + 1) / 2;
@@ -688,12 +727,12 @@ __device__ void pair_sweep_log_cta(const EArgs &a, const CompT<double> &c, const
       tot[1] += rw[3] * fa;
       for (int t = 2; t < NV; ++t) tot[t] += rw[2 + t] * fb;
     }
-    const int64_t n = a.n;
+    const int64_t n = fv.n;
     const int64_t ij = (int64_t)i * n + j;
     const double logTA = gA + log(tot[0]) - log((double)N);
     const double logf_out = pr.logt + logTA;
     if (!isfinite(logf_out)) atomicOr(a.status, ERR_NUMERIC);
-    if (a.out.logf != nullptr) store<float>(a.out.logf, ij, logf_out);
+    if (fv.out.logf != nullptr) store<float>(fv.out.logf, ij, logf_out);
     if (!DENS) {
       const double logTB = gB + log(tot[2]) - log((double)N);
       const bool ok = isfinite(logTA) && isfinite(logTB);
@@ -711,9 +750,9 @@ __device__ void pair_sweep_log_cta(const EArgs &a, const CompT<double> &c, const
         e2 = ok ? tot[1] / tot[0] - log(nud64) : 0.0;
       else
         e2 = ok ? e1 - (log(0.5 * nud64) + c.mA / nud64 - c.psiA) : 0.0;
-      store<float>(a.out.e1, ij, e1);
-      store<float>(a.out.e2, ij, e2);
-      for (int t = 0; t < R; ++t) store<float>(a.out.e3, ((int64_t)i * R + t) * n + j, e1 * (pr.q[t] + sig * LEV[t]));
+      store<float>(fv.out.e1, ij, e1);
+      store<float>(fv.out.e2, ij, e2);
+      for (int t = 0; t < R; ++t) store<float>(fv.out.e3, ((int64_t)i * R + t) * n + j, e1 * (pr.q[t] + sig * LEV[t]));
       for (int t = 0; t < R; ++t)
         for (int h = 0; h <= t; ++h) {
           double sacc = 0.0;
@@ -723,11 +762,47 @@ __device__ void pair_sweep_log_cta(const EArgs &a, const CompT<double> &c, const
               sacc += Lc[t * (t + 1) / 2 + aa] * evv * Lc[h * (h + 1) / 2 + bb];
             }
           const double exx = pr.q[t] * pr.q[h] + sig * (pr.q[t] * LEV[h] + LEV[t] * pr.q[h]) + sig * sig * sacc;
-          store<float>(a.out.e4, ((int64_t)i * RP + t * (t + 1) / 2 + h) * n + j, e1 * exx);
+          store<float>(fv.out.e4, ((int64_t)i * RP + t * (t + 1) / 2 + h) * n + j, e1 * exx);
         }
     }
   }
   __syncthreads();
+}
+
+// Triage and log-domain recomputation of one queued pair by the whole CTA.
+template <int R, bool DENS>
+__device__ void rescue_one(const EArgs &a, const FitView &fv, const CompT<double> &comp, const double *tab,
+                           int i, int64_t j, double *sm, Prologue<R> &spr, int &skip) {
+  if (threadIdx.x == 0) {
+    skip = 0;
+    if (a.triage) {
+      // tau_ij < exp(-30) when log pi_i + ub_ij trails the best component by 30
+      const float *lf = reinterpret_cast<const float *>(fv.out.logf);
+      double best = -INFINITY;
+      for (int h = 0; h < fv.g; ++h) best = fmax(best, log(fv.pi[h]) + (double)lf[(int64_t)h * fv.n + j]);
+      const double mine = log(fv.pi[i]) + (double)lf[(int64_t)i * fv.n + j];
+      if (isfinite(best) && mine < best - 30.0) {
+        skip = 1;
+        const int64_t ij = (int64_t)i * fv.n + j;
+        const int RP = R * (R + 1) / 2;
+        store<float>(fv.out.logf, ij, -INFINITY);
+        if (!DENS) {
+          store<float>(fv.out.e1, ij, 0.0);
+          store<float>(fv.out.e2, ij, 0.0);
+          for (int t = 0; t < R; ++t) store<float>(fv.out.e3, ((int64_t)i * R + t) * fv.n + j, 0.0);
+          for (int t = 0; t < RP; ++t) store<float>(fv.out.e4, ((int64_t)i * RP + t) * fv.n + j, 0.0);
+        }
+      }
+    }
+    if (!skip) spr = prologue<double, R>(a, fv, comp, j);
+  }
+  __syncthreads();
+  if (skip) {
+    __syncthreads();
+    return;
+  }
+  const Prologue<R> pr = spr;
+  pair_sweep_log_cta<R, DENS>(a, fv, comp, pr, tab, tab + a.N, i, j, sm);
 }
 
 template <int R, bool DENS>
@@ -736,43 +811,14 @@ __global__ void __launch_bounds__(256) rescue_kernel(EArgs a, const CompT<double
   constexpr int NV = 3 + R + R * (R + 1) / 2;
   __shared__ double sm[8 * (2 + NV)];
   __shared__ Prologue<R> spr;
-  const unsigned cnt = *a.rescue_count;
   __shared__ int skip;
+  const unsigned cnt = *a.rescue_count;
+  const FitView fv = fit_view(a);
   for (unsigned w = blockIdx.x; w < cnt; w += gridDim.x) {
     const unsigned long long id = a.rescue_list[w];
-    const int i = static_cast<int>(id / (unsigned long long)a.n);
-    const int64_t j = static_cast<int64_t>(id % (unsigned long long)a.n);
-    if (threadIdx.x == 0) {
-      skip = 0;
-      if (a.triage) {
-        // tau_ij < exp(-30) when log pi_i + ub_ij trails the best component by 30
-        const float *lf = reinterpret_cast<const float *>(a.out.logf);
-        double best = -INFINITY;
-        for (int h = 0; h < a.g; ++h) best = fmax(best, log(a.pi[h]) + (double)lf[(int64_t)h * a.n + j]);
-        const double mine = log(a.pi[i]) + (double)lf[(int64_t)i * a.n + j];
-        if (isfinite(best) && mine < best - 30.0) {
-          skip = 1;
-          const int64_t ij = (int64_t)i * a.n + j;
-          const int RP = R * (R + 1) / 2;
-          store<float>(a.out.logf, ij, -INFINITY);
-          if (!DENS) {
-            store<float>(a.out.e1, ij, 0.0);
-            store<float>(a.out.e2, ij, 0.0);
-            for (int t = 0; t < R; ++t) store<float>(a.out.e3, ((int64_t)i * R + t) * a.n + j, 0.0);
-            for (int t = 0; t < RP; ++t) store<float>(a.out.e4, ((int64_t)i * RP + t) * a.n + j, 0.0);
-          }
-        }
-      }
-      if (!skip) spr = prologue<double, R>(a, comp[i], j);
-    }
-    __syncthreads();
-    if (skip) {
-      __syncthreads();
-      continue;
-    }
-    const Prologue<R> pr = spr;
-    const double *tA = chi + (int64_t)i * 2 * a.N;
-    pair_sweep_log_cta<R, DENS>(a, comp[i], pr, tA, tA + a.N, i, j, sm);
+    const int i = static_cast<int>(id >> 32);
+    const int64_t j = static_cast<int64_t>(id & 0xffffffffull);
+    rescue_one<R, DENS>(a, fv, comp[i], chi + (int64_t)i * 2 * a.N, i, j, sm, spr, skip);
   }
 }
 

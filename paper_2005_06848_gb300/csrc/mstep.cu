@@ -53,9 +53,11 @@ __device__ inline void entry_desc(int ent, int p, int r, int *w, int *y1, int *y
   *w = 2 + r + rp;                                  // S8
 }
 
+// One block's share of the posterior / sums work of one fit: tiles blk,
+// blk + nblk, ...; partial sums and the log-likelihood partial go to row blk.
 template <typename ET>
-__global__ void __launch_bounds__(THREADS) posterior_kernel(PosteriorArgs a, int c0, int c1) {
-  extern __shared__ __align__(16) unsigned char smem_raw[];
+__device__ __forceinline__ void posterior_block(const PosteriorArgs &a, int c0, int c1, int blk, int nblk,
+                                                unsigned char *smem_raw) {
   double *smem = reinterpret_cast<double *>(smem_raw);
   const int p = a.p, r = a.r, g = a.g;
   const int rp = r * (r + 1) / 2;
@@ -95,7 +97,7 @@ __global__ void __launch_bounds__(THREADS) posterior_kernel(PosteriorArgs a, int
   const int64_t ntiles = (n + TJ - 1) / TJ;
   const bool first_chunk = (c0 == 0);
 
-  for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+  for (int64_t tile = blk; tile < ntiles; tile += nblk) {
     const int64_t j0 = tile * TJ;
     const int nt = (int)((n - j0) < TJ ? (n - j0) : TJ);
     if (a.want_sums)
@@ -156,7 +158,7 @@ __global__ void __launch_bounds__(THREADS) posterior_kernel(PosteriorArgs a, int
   }
 
   if (a.want_sums) {
-    double *dst = a.partials + (int64_t)blockIdx.x * g * K;
+    double *dst = a.partials + (int64_t)blk * g * K;
 #pragma unroll
     for (int k = 0; k < MAXOWN; ++k) {
       const int e = threadIdx.x + k * THREADS;
@@ -170,9 +172,15 @@ __global__ void __launch_bounds__(THREADS) posterior_kernel(PosteriorArgs a, int
       if (threadIdx.x < s) red[threadIdx.x] += red[threadIdx.x + s];
       __syncthreads();
     }
-    if (threadIdx.x == 0) a.ll_partials[blockIdx.x] = red[0];
+    if (threadIdx.x == 0) a.ll_partials[blk] = red[0];
   }
   if (bad) atomicOr(a.d_status, ERR_ZERO_DENSITY);
+}
+
+template <typename ET>
+__global__ void __launch_bounds__(THREADS) posterior_kernel(PosteriorArgs a, int c0, int c1) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  posterior_block<ET>(a, c0, c1, blockIdx.x, gridDim.x, smem_raw);
 }
 
 __global__ void reduce_ll_kernel(const double *part, int nb, double *out, double *trace, int *iter) {
@@ -228,11 +236,12 @@ __device__ double solve_nu(double c, double lo, double hi) {
   return 0.5 * (lo + hi);
 }
 
-__global__ void mstep_finalize_kernel(const double *partials, int nb, int g, int p, int r, int64_t n,
-                                      double nu_min, double nu_max, double *params, int *status) {
+// Conditional-maximisation update of component i of one fit from the
+// per-block partial sums (block of 128 threads).
+__device__ void mstep_finalize_block(const double *partials, int nb, int g, int p, int r, int64_t n,
+                                     double nu_min, double nu_max, double *params, int *status, int i) {
   __shared__ double S[3 + PMAX + RMAX + PMAX * RMAX + RMAX * (RMAX + 1) / 2 + PMAX * (PMAX + 1) / 2];
   __shared__ double red[128];
-  const int i = blockIdx.x;
   const int K = sums_width(p, r);
   for (int e = threadIdx.x; e < K; e += blockDim.x) {
     double s = 0.0;
@@ -325,6 +334,11 @@ __global__ void mstep_finalize_kernel(const double *partials, int nb, int g, int
     for (int b = 0; b < p; ++b) Sig[a * p + b] = Sn[a * PMAX + b];
   }
   pv.nu[i] = solve_nu(S8 / S1, nu_min, nu_max);
+}
+
+__global__ void mstep_finalize_kernel(const double *partials, int nb, int g, int p, int r, int64_t n,
+                                      double nu_min, double nu_max, double *params, int *status) {
+  mstep_finalize_block(partials, nb, g, p, r, n, nu_min, nu_max, params, status, blockIdx.x);
 }
 
 }  // namespace

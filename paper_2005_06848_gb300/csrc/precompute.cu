@@ -43,29 +43,29 @@ __device__ inline double lattice_coord(int k, int z, int n, double shift) {
   return fmin(fmax(u, umin), 1.0 - umin);
 }
 
-__global__ void precompute_kernel(const double *params, int g, int p, int r, LatticeDev lat,
-                                  CompT<double> *c64, CompT<float> *c32, double *chi64,
-                                  float *chi32, int *status) {
-  const int i = blockIdx.y;
+// Component i of one fit (parameter block `params`): chi tables chi64/chi32
+// ([2][N] each, this component's rows) by the threads of blocks bx = 0..nbx-1,
+// and the factorisations into *o / *f by thread 0 of block 0.
+__device__ void precompute_component(const double *params, int g, int p, int r, int i, const LatticeDev &lat,
+                                     CompT<double> *o_out, CompT<float> *f_out, double *t64, float *t32,
+                                     int *status, int bx, int nbx) {
   ParamView pv = param_view(const_cast<double *>(params), g, p, r);
   const double nu = pv.nu[i];
   const int N = lat.n;
 
-  // chi-scale tables: [g][2][N]
-  for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < N; k += gridDim.x * blockDim.x) {
+  // chi-scale tables: [2][N]
+  for (int k = bx * blockDim.x + threadIdx.x; k < N; k += nbx * blockDim.x) {
     const double u0 = lattice_coord(k, lat.z[0], N, lat.shift[0]);
     const double mA = nu + p, mB = nu + p + 2.0;
     const double sA = sqrt(2.0 * inc_gamma_inv(0.5 * mA, u0) / mA);
     const double sB = sqrt(2.0 * inc_gamma_inv(0.5 * mB, u0) / mB);
-    double *t64 = chi64 + (int64_t)i * 2 * N;
-    float *t32 = chi32 + (int64_t)i * 2 * N;
     t64[k] = sA;
     t64[N + k] = sB;
     t32[k] = (float)sA;
     t32[N + k] = (float)sB;
   }
 
-  if (blockIdx.x != 0 || threadIdx.x != 0) return;
+  if (bx != 0 || threadIdx.x != 0) return;
 
   const double *mu = pv.mu + (int64_t)i * p;
   const double *Sig = pv.Sigma + (int64_t)i * p * p;
@@ -121,8 +121,8 @@ __global__ void precompute_kernel(const double *params, int g, int p, int r, Lat
   const double c0 = r * 0.69314718055994530942 + lgamma(0.5 * (nu + p)) - lgamma(0.5 * nu) -
                     0.5 * p * log(nu * pi_c) - 0.5 * logdet;
 
-  CompT<double> &o = c64[i];
-  CompT<float> &f = c32[i];
+  CompT<double> &o = *o_out;
+  CompT<float> &f = *f_out;
   for (int a = 0; a < PMAX; ++a) o.mu[a] = f.mu[a] = (a < p) ? mu[a] : 0.0;
   for (int a = 0; a < PMAX * PMAX; ++a) {
     const int row = a / PMAX, col = a % PMAX;
@@ -147,6 +147,14 @@ __global__ void precompute_kernel(const double *params, int g, int p, int r, Lat
   o.mB = f.mB = nu + p + 2.0;
   o.psiA = f.psiA = psiA;
   o.logmA = f.logmA = log(nu + p);
+}
+
+__global__ void precompute_kernel(const double *params, int g, int p, int r, LatticeDev lat,
+                                  CompT<double> *c64, CompT<float> *c32, double *chi64,
+                                  float *chi32, int *status) {
+  const int i = blockIdx.y;
+  precompute_component(params, g, p, r, i, lat, c64 + i, c32 + i, chi64 + (int64_t)i * 2 * lat.n,
+                       chi32 + (int64_t)i * 2 * lat.n, status, blockIdx.x, gridDim.x);
 }
 
 }  // namespace
