@@ -94,6 +94,8 @@ typedef struct {
   int use_graph;          /* 1: cfust_fit replays one CUDA graph per EM iteration */
   int timing;             /* 1: bracket every lattice-sweep kernel launch with CUDA events */
   int pairs_per_warp;     /* observations one warp sweeps in turn (1..32); 0 = chosen from n and g */
+  int autotune;           /* 1: cfust_fit_batched times candidate launch shapes (pairs per warp,
+                             resident CTAs per SM) on its first call for a batch and keeps the fastest */
 } cfust_opts;
 
 typedef struct cfust_ctx cfust_ctx;
@@ -160,6 +162,22 @@ cfust_status cfust_fit_end(cfust_ctx *ctx, cfust_params *params, double *loglik_
  * l(Psi^(0)) .. l(Psi^(k-1)) after k cfust_fit_step iterations, into trace
  * (host, at least k entries); *count receives k. */
 cfust_status cfust_fit_trace(cfust_ctx *ctx, double *trace, int *count);
+
+/* Many independent fits advanced together (Algorithm 1's multiple starts, or
+ * separate data sets): fit f has Y[f] (device [n[f]][p]) and params[f]
+ * (host, updated in place); every fit shares p, r and the context's lattice,
+ * g may differ.  Runs opts.max_iter EM iterations, each one CUDA graph whose
+ * E-step is a single persistent sweep launch over all fits' (component,
+ * observation tile) items.  loglik_trace (host [nfits][max_iter + 1], may be
+ * NULL) receives each fit's l(Psi^(0)) .. l(Psi^(max_iter)).  fit_status
+ * (host [nfits], may be NULL) receives each fit's cfust_status; the call
+ * returns the first non-zero one.  Y pointers must stay valid during the call. */
+cfust_status cfust_fit_batched(cfust_ctx *ctx, int nfits, const double *const *Y, const int64_t *n,
+                               cfust_params *params, double *loglik_trace, int *fit_status);
+
+/* Launch shape chosen for the last batched fit (by the autotuner or the
+ * default rule): pairs per warp and resident CTAs per SM of the sweep. */
+cfust_status cfust_batched_shape(cfust_ctx *ctx, int *pairs_per_warp, int *ctas_per_sm);
 
 /* Number of (i, j) pairs whose single-precision lattice sweep fell below the
  * underflow guard in the last E-step and were recomputed in double precision

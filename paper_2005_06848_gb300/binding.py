@@ -20,6 +20,7 @@ STATUS = {0: "CFUST_OK", -1: "CFUST_EINVAL", -2: "CFUST_ENOTPD", -3: "CFUST_ENUM
 
 EXPORTED = ["cfust_create", "cfust_destroy", "cfust_loglik", "cfust_estep", "cfust_mstep",
             "cfust_fit", "cfust_fit_begin", "cfust_fit_step", "cfust_fit_end", "cfust_fit_trace",
+            "cfust_fit_batched", "cfust_batched_shape",
             "cfust_last_rescued", "cfust_last_sweep_ms", "cfust_normal_f32", "cfust_mstep_noalloc",
             "cfust_last_error"]
 
@@ -46,7 +47,7 @@ class cfust_opts(ctypes.Structure):
     _fields_ = [("precision", ctypes.c_int), ("lattice", cfust_lattice), ("e2_mode", ctypes.c_int),
                 ("nu_min", ctypes.c_double), ("nu_max", ctypes.c_double),
                 ("max_iter", ctypes.c_int), ("tol", ctypes.c_double), ("use_graph", ctypes.c_int),
-                ("timing", ctypes.c_int), ("pairs_per_warp", ctypes.c_int)]
+                ("timing", ctypes.c_int), ("pairs_per_warp", ctypes.c_int), ("autotune", ctypes.c_int)]
 
 
 _LIB = None
@@ -76,6 +77,9 @@ def load(build_if_missing: bool = True, path: str | None = None) -> ctypes.CDLL:
         "cfust_fit_step": ([vp, ctypes.c_int], ctypes.c_int),
         "cfust_fit_end": ([vp, P, dp, ctypes.POINTER(ctypes.c_int)], ctypes.c_int),
         "cfust_fit_trace": ([vp, dp, ctypes.POINTER(ctypes.c_int)], ctypes.c_int),
+        "cfust_fit_batched": ([vp, ctypes.c_int, ctypes.POINTER(vp), ctypes.POINTER(i64), P, dp,
+                               ctypes.POINTER(ctypes.c_int)], ctypes.c_int),
+        "cfust_batched_shape": ([vp, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int)], ctypes.c_int),
         "cfust_last_rescued": ([vp, ctypes.POINTER(i64)], ctypes.c_int),
         "cfust_last_sweep_ms": ([vp, ctypes.POINTER(ctypes.c_float)], ctypes.c_int),
         "cfust_last_error": ([vp], ctypes.c_char_p),
@@ -115,7 +119,8 @@ class Context:
     """A cfust_ctx bound to the current CUDA device and a torch stream."""
 
     def __init__(self, lattice, precision=CFUST_FP32, e2_mode=0, nu_min=0.0, nu_max=0.0,
-                 max_iter=0, tol=0.0, use_graph=True, timing=False, pairs_per_warp=0, stream=None):
+                 max_iter=0, tol=0.0, use_graph=True, timing=False, pairs_per_warp=0, autotune=False,
+                 stream=None):
         import torch
         self.lib = load()
         self._z = np.ascontiguousarray(lattice.z, dtype=np.int64)
@@ -125,7 +130,7 @@ class Context:
                             self._shift.ctypes.data_as(ctypes.POINTER(ctypes.c_double)))
         self.opts = cfust_opts(int(precision), lat, int(e2_mode), float(nu_min), float(nu_max),
                                int(max_iter), float(tol), 1 if use_graph else 0, 1 if timing else 0,
-                               int(pairs_per_warp))
+                               int(pairs_per_warp), 1 if autotune else 0)
         self.precision = int(precision)
         self.stream = stream if stream is not None else torch.cuda.current_stream()
         self.lattice_n = int(lattice.n)
@@ -234,6 +239,27 @@ class Context:
                                            ctypes.byref(done)))
         self._fit_Y = None
         return hp.to_params(), trace[:done.value + 1], done.value
+
+    def cfust_fit_batched(self, Ys, params_list):
+        """Fit every (Y, params) pair together.  Returns (params list, traces
+        [nfits][max_iter+1], per-fit status list)."""
+        nf = len(Ys)
+        hps = [_HostParams(p) for p in params_list]
+        arr = (cfust_params * nf)(*[h.c for h in hps])
+        yp = (ctypes.c_void_p * nf)(*[y.data_ptr() for y in Ys])
+        ns = (ctypes.c_int64 * nf)(*[int(y.shape[0]) for y in Ys])
+        trace = np.zeros((nf, self.opts.max_iter + 1))
+        st = (ctypes.c_int * nf)()
+        rc = self.lib.cfust_fit_batched(self.h, nf, yp, ns, arr, trace.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
+                                        st)
+        self._check(rc)
+        # the library wrote the updated parameters through the struct pointers
+        return [h.to_params() for h in hps], trace, list(st)
+
+    def cfust_batched_shape(self):
+        a, b = ctypes.c_int(), ctypes.c_int()
+        self._check(self.lib.cfust_batched_shape(self.h, ctypes.byref(a), ctypes.byref(b)))
+        return a.value, b.value
 
     def cfust_last_sweep_ms(self) -> float:
         v = ctypes.c_float()

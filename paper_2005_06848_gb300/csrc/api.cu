@@ -46,6 +46,32 @@ struct cfust_ctx {
   const double *graph_Y = nullptr;
   int64_t graph_n = 0;
 
+  // batched fits (cfust_fit_batched)
+  struct Batch {
+    int nfits = 0, G = 0, p = 0, r = 0, g_max = 0, nitems = 0, nblocks = 0, K = 0;
+    int ppw = 0, cps = 2;
+    bool tuned = false;
+    std::vector<const double *> Y;
+    std::vector<int64_t> n;
+    std::vector<int> g;
+    int64_t pairs = 0, params_len = 0, part_len = 0;
+    FitDesc *d_fits = nullptr;
+    CompRef *d_comps = nullptr;
+    SweepItem *d_items = nullptr;
+    BlockRef *d_blocks = nullptr;
+    double *d_params = nullptr;
+    CompT<double> *c64 = nullptr;
+    CompT<float> *c32 = nullptr;
+    double *chi64 = nullptr;
+    float *chi32 = nullptr;
+    void *logf = nullptr, *e1 = nullptr, *e2 = nullptr, *e3 = nullptr, *e4 = nullptr;
+    unsigned long long *rescue = nullptr;
+    unsigned *rescue_cnt = nullptr, *counter = nullptr;
+    double *partials = nullptr, *llpart = nullptr, *trace = nullptr;
+    int *iter = nullptr, *fit_status = nullptr, *status = nullptr;
+    cudaGraphExec_t graph = nullptr;
+  } batch;
+
   // stepwise fit state
   const double *fit_Y = nullptr;
   int64_t fit_n = 0;
@@ -54,6 +80,8 @@ struct cfust_ctx {
 };
 
 namespace {
+
+void free_batch(cfust_ctx::Batch &b);
 
 thread_local std::string g_create_error;
 
@@ -420,6 +448,7 @@ cfust_status cfust_destroy(cfust_ctx *c) {
   DeviceGuard dg(c->device);
   drop_graph(c);
   if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
+  free_batch(c->batch);
   for (cudaEvent_t ev : c->ev_sweep)
     if (ev) cudaEventDestroy(ev);
   void *bufs[] = {c->d_params, c->d_c64, c->d_c32, c->d_chi64, c->d_chi32, c->d_status,
@@ -670,6 +699,323 @@ cfust_status cfust_fit(cfust_ctx *c, const double *Y, int64_t n, cfust_params *P
 }
 
 }  // extern "C"
+
+// ---------------------------------------------------------------------------
+// Batched fits
+// ---------------------------------------------------------------------------
+
+namespace {
+
+void free_batch(cfust_ctx::Batch &b) {
+  if (b.graph) cudaGraphExecDestroy(b.graph);
+  b.graph = nullptr;
+  void *bufs[] = {b.d_fits, b.d_comps, b.d_items, b.d_blocks, b.d_params, b.c64, b.c32, b.chi64, b.chi32,
+                  b.logf, b.e1, b.e2, b.e3, b.e4, b.rescue, b.rescue_cnt, b.counter, b.partials, b.llpart,
+                  b.trace, b.iter, b.fit_status, b.status};
+  for (void *p : bufs)
+    if (p) cudaFree(p);
+  cfust_ctx::Batch fresh;
+  fresh.tuned = b.tuned;
+  fresh.ppw = b.ppw;
+  fresh.cps = b.cps;
+  b = fresh;
+}
+
+BatchDev batch_dev(const cfust_ctx::Batch &b) {
+  BatchDev d;
+  d.fits = b.d_fits;
+  d.comps = b.d_comps;
+  d.nfits = b.nfits;
+  d.G = b.G;
+  d.params = b.d_params;
+  d.logf = b.logf;
+  d.e1 = b.e1;
+  d.e2 = b.e2;
+  d.e3 = b.e3;
+  d.e4 = b.e4;
+  d.fit_status = b.fit_status;
+  return d;
+}
+
+// Sweep items for a given pairs-per-warp: component by component, tiles of
+// 8 warps x ppw observations.
+std::vector<SweepItem> batch_items(const cfust_ctx::Batch &b, int ppw) {
+  std::vector<SweepItem> items;
+  const int64_t T = 8LL * ppw;
+  for (int f = 0; f < b.nfits; ++f)
+    for (int i = 0; i < b.g[f]; ++i) {
+      int gc = 0;
+      for (int h = 0; h < f; ++h) gc += b.g[h];
+      gc += i;
+      for (int64_t j0 = 0; j0 < b.n[f]; j0 += T) items.push_back(SweepItem{gc, (unsigned)j0});
+    }
+  return items;
+}
+
+int default_batch_ppw(int64_t pairs) {
+  int64_t ppw = pairs / (152LL * 2 * 16 * 8);
+  return (int)(ppw < 1 ? 1 : (ppw > 32 ? 32 : ppw));
+}
+
+cfust_status upload_items(cfust_ctx *c, int ppw) {
+  cfust_ctx::Batch &b = c->batch;
+  std::vector<SweepItem> items = batch_items(b, ppw);
+  if (b.d_items) cudaFree(b.d_items);
+  b.d_items = nullptr;
+  CF_CUDA(c, cudaMalloc(&b.d_items, sizeof(SweepItem) * items.size()));
+  CF_CUDA(c, cudaMemcpy(b.d_items, items.data(), sizeof(SweepItem) * items.size(), cudaMemcpyHostToDevice));
+  b.nitems = (int)items.size();
+  b.ppw = ppw;
+  return CFUST_OK;
+}
+
+cfust_status enqueue_batch_estep(cfust_ctx *c, cudaStream_t st, bool density_only) {
+  cfust_ctx::Batch &b = c->batch;
+  const BatchDev d = batch_dev(b);
+  CF_CUDA(c, launch_precompute_batched(d, b.p, b.r, c->lat, b.c64, b.c32, b.chi64, b.chi32, st));
+  CF_CUDA(c, launch_estep_batched(c->opts.precision, d, b.p, b.r, c->lat, b.c64, b.c32, b.chi64, b.chi32,
+                                  b.d_items, b.nitems, b.counter, density_only, c->opts.e2_mode, b.ppw, b.cps,
+                                  b.rescue, b.rescue_cnt, b.status, 1, st,
+                                  sweep_timing(c, st == c->cap_stream)));
+  return CFUST_OK;
+}
+
+cfust_status enqueue_batch_iteration(cfust_ctx *c, cudaStream_t st) {
+  cfust_ctx::Batch &b = c->batch;
+  cfust_status s = enqueue_batch_estep(c, st, false);
+  if (s != CFUST_OK) return s;
+  const BatchDev d = batch_dev(b);
+  CF_CUDA(c, launch_posterior_batched(c->opts.precision, d, b.p, b.r, b.d_blocks, b.nblocks, b.partials, b.llpart,
+                                      true, b.g_max, st));
+  CF_CUDA(c, launch_reduce_ll_batched(d, b.llpart, b.trace, c->opts.max_iter + 1, b.iter, st));
+  CF_CUDA(c, launch_finalize_batched(d, b.p, b.r, b.partials, nu_lo(c), nu_hi(c), st));
+  return CFUST_OK;
+}
+
+// Time one sweep per candidate shape on the real batch; keep the fastest.
+cfust_status autotune_batch(cfust_ctx *c) {
+  cfust_ctx::Batch &b = c->batch;
+  const int ppws[] = {2, 4, 8, 16};
+  const int cpss[] = {1, 2};
+  cudaEvent_t e0, e1;
+  CF_CUDA(c, cudaEventCreate(&e0));
+  CF_CUDA(c, cudaEventCreate(&e1));
+  const BatchDev d = batch_dev(b);
+  CF_CUDA(c, launch_precompute_batched(d, b.p, b.r, c->lat, b.c64, b.c32, b.chi64, b.chi32, c->stream));
+  float best = 1e30f;
+  int best_ppw = b.ppw, best_cps = b.cps;
+  for (int ppw : ppws) {
+    cfust_status s = upload_items(c, ppw);
+    if (s != CFUST_OK) return s;
+    for (int cps : cpss) {
+      float ms = 0.f;
+      for (int rep = 0; rep < 2; ++rep) {
+        CF_CUDA(c, cudaEventRecord(e0, c->stream));
+        CF_CUDA(c, launch_estep_batched(c->opts.precision, d, b.p, b.r, c->lat, b.c64, b.c32, b.chi64, b.chi32,
+                                        b.d_items, b.nitems, b.counter, false, c->opts.e2_mode, ppw, cps,
+                                        b.rescue, b.rescue_cnt, b.status, 1, c->stream));
+        CF_CUDA(c, cudaEventRecord(e1, c->stream));
+        CF_CUDA(c, cudaEventSynchronize(e1));
+        CF_CUDA(c, cudaEventElapsedTime(&ms, e0, e1));
+      }
+      if (ms < best) {
+        best = ms;
+        best_ppw = ppw;
+        best_cps = cps;
+      }
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  b.cps = best_cps;
+  b.tuned = true;
+  return upload_items(c, best_ppw);
+}
+
+}  // namespace
+
+extern "C" cfust_status cfust_batched_shape(cfust_ctx *c, int *ppw, int *cps) {
+  if (!c || !ppw || !cps) return CFUST_EINVAL;
+  *ppw = c->batch.ppw;
+  *cps = c->batch.cps;
+  return CFUST_OK;
+}
+
+extern "C" cfust_status cfust_fit_batched(cfust_ctx *c, int nfits, const double *const *Y, const int64_t *n,
+                                         cfust_params *P, double *trace_out, int *fit_status_out) {
+  if (!c) return CFUST_EINVAL;
+  if (nfits < 1 || !Y || !n || !P) return fail(c, CFUST_EINVAL, "nfits >= 1 with Y, n and params required");
+  DeviceGuard dg(c->device);
+  const int p = P[0].p, r = P[0].r;
+  for (int f = 0; f < nfits; ++f) {
+    cfust_status s = check_common(c, Y[f], n[f], &P[f]);
+    if (s != CFUST_OK) return fail(c, s, "fit " + std::to_string(f) + ": " + c->err);
+    if (P[f].p != p || P[f].r != r) return fail(c, CFUST_EINVAL, "all fits must share p and r");
+  }
+  const int K = c->opts.max_iter;
+  const int kK = sums_width(p, r);
+  cfust_ctx::Batch &b = c->batch;
+  bool same = b.nfits == nfits && b.p == p && b.r == r && b.graph != nullptr;
+  for (int f = 0; same && f < nfits; ++f) same = b.Y[f] == Y[f] && b.n[f] == n[f] && b.g[f] == P[f].g;
+  if (!same) {
+    free_batch(b);
+    b.nfits = nfits;
+    b.p = p;
+    b.r = r;
+    b.K = kK;
+    b.Y.assign(Y, Y + nfits);
+    b.n.assign(n, n + nfits);
+    b.g.resize(nfits);
+    std::vector<FitDesc> fits(nfits);
+    std::vector<CompRef> comps;
+    std::vector<BlockRef> blocks;
+    int64_t pair_off = 0, param_off = 0, part_off = 0;
+    int comp0 = 0, blk0 = 0;
+    for (int f = 0; f < nfits; ++f) {
+      const int g = P[f].g;
+      b.g[f] = g;
+      b.g_max = g > b.g_max ? g : b.g_max;
+      const int nb = posterior_nblocks(n[f]);
+      fits[f] = FitDesc{Y[f], n[f], g, comp0, pair_off, param_off, part_off, blk0, nb};
+      for (int i = 0; i < g; ++i) comps.push_back(CompRef{f, i});
+      for (int lb = 0; lb < nb; ++lb) blocks.push_back(BlockRef{f, lb});
+      comp0 += g;
+      pair_off += (int64_t)g * n[f];
+      param_off += param_block_size(g, p, r);
+      part_off += (int64_t)nb * g * kK;
+      blk0 += nb;
+    }
+    if (b.g_max * kK > 2048) return fail(c, CFUST_EINVAL, "g x sums per component too large for batched fits");
+    b.G = comp0;
+    b.pairs = pair_off;
+    b.params_len = param_off;
+    b.part_len = part_off;
+    b.nblocks = blk0;
+    const size_t es = elem_size(c);
+    const int rp = r * (r + 1) / 2;
+    const int N = c->lat.n;
+    CF_CUDA(c, cudaMalloc(&b.d_fits, sizeof(FitDesc) * nfits));
+    CF_CUDA(c, cudaMalloc(&b.d_comps, sizeof(CompRef) * comps.size()));
+    CF_CUDA(c, cudaMalloc(&b.d_blocks, sizeof(BlockRef) * blocks.size()));
+    CF_CUDA(c, cudaMalloc(&b.d_params, sizeof(double) * b.params_len));
+    CF_CUDA(c, cudaMalloc(&b.c64, sizeof(CompT<double>) * b.G));
+    CF_CUDA(c, cudaMalloc(&b.c32, sizeof(CompT<float>) * b.G));
+    CF_CUDA(c, cudaMalloc(&b.chi64, sizeof(double) * 2 * (size_t)N * b.G));
+    CF_CUDA(c, cudaMalloc(&b.chi32, sizeof(float) * 2 * (size_t)N * b.G));
+    CF_CUDA(c, cudaMalloc(&b.logf, es * b.pairs));
+    CF_CUDA(c, cudaMalloc(&b.e1, es * b.pairs));
+    CF_CUDA(c, cudaMalloc(&b.e2, es * b.pairs));
+    CF_CUDA(c, cudaMalloc(&b.e3, es * b.pairs * r));
+    CF_CUDA(c, cudaMalloc(&b.e4, es * b.pairs * rp));
+    CF_CUDA(c, cudaMalloc(&b.rescue, sizeof(unsigned long long) * b.pairs));
+    CF_CUDA(c, cudaMalloc(&b.rescue_cnt, sizeof(unsigned)));
+    CF_CUDA(c, cudaMalloc(&b.counter, sizeof(unsigned)));
+    CF_CUDA(c, cudaMalloc(&b.partials, sizeof(double) * b.part_len));
+    CF_CUDA(c, cudaMalloc(&b.llpart, sizeof(double) * b.nblocks));
+    CF_CUDA(c, cudaMalloc(&b.trace, sizeof(double) * (size_t)nfits * (K + 1)));
+    CF_CUDA(c, cudaMalloc(&b.iter, sizeof(int)));
+    CF_CUDA(c, cudaMalloc(&b.fit_status, sizeof(int) * nfits));
+    CF_CUDA(c, cudaMalloc(&b.status, sizeof(int)));
+    CF_CUDA(c, cudaMemcpy(b.d_fits, fits.data(), sizeof(FitDesc) * nfits, cudaMemcpyHostToDevice));
+    CF_CUDA(c, cudaMemcpy(b.d_comps, comps.data(), sizeof(CompRef) * comps.size(), cudaMemcpyHostToDevice));
+    CF_CUDA(c, cudaMemcpy(b.d_blocks, blocks.data(), sizeof(BlockRef) * blocks.size(), cudaMemcpyHostToDevice));
+  }
+  // parameters: one block per fit, back to back
+  {
+    std::vector<double> host(b.params_len);
+    int64_t off = 0;
+    for (int f = 0; f < nfits; ++f) {
+      const cfust_params &q = P[f];
+      const int g = q.g;
+      double *dst = host.data() + off;
+      ParamView v = param_view(dst, g, p, r);
+      memcpy(v.pi, q.pi, sizeof(double) * g);
+      memcpy(v.mu, q.mu, sizeof(double) * g * p);
+      memcpy(v.Sigma, q.Sigma, sizeof(double) * g * p * p);
+      memcpy(v.Delta, q.Delta, sizeof(double) * g * p * r);
+      memcpy(v.nu, q.nu, sizeof(double) * g);
+      off += param_block_size(g, p, r);
+    }
+    CF_CUDA(c, cudaMemcpyAsync(b.d_params, host.data(), sizeof(double) * b.params_len, cudaMemcpyHostToDevice,
+                               c->stream));
+    CF_CUDA(c, cudaStreamSynchronize(c->stream));
+  }
+  CF_CUDA(c, cudaMemsetAsync(b.iter, 0, sizeof(int), c->stream));
+  CF_CUDA(c, cudaMemsetAsync(b.fit_status, 0, sizeof(int) * nfits, c->stream));
+  CF_CUDA(c, cudaMemsetAsync(b.status, 0, sizeof(int), c->stream));
+  cfust_status s;
+  if (!same) {
+    if (c->opts.autotune && !b.tuned) {
+      if ((s = autotune_batch(c)) != CFUST_OK) return s;
+      CF_CUDA(c, cudaMemsetAsync(b.fit_status, 0, sizeof(int) * nfits, c->stream));
+      CF_CUDA(c, cudaMemsetAsync(b.status, 0, sizeof(int), c->stream));
+    } else if ((s = upload_items(c, b.tuned ? b.ppw : (c->opts.pairs_per_warp > 0 ? c->opts.pairs_per_warp
+                                                                                   : default_batch_ppw(b.pairs)))) !=
+               CFUST_OK) {
+      return s;
+    }
+    if (K > 0) {
+      cudaGraph_t gr = nullptr;
+      if (!c->cap_stream) CF_CUDA(c, cudaStreamCreateWithFlags(&c->cap_stream, cudaStreamNonBlocking));
+      CF_CUDA(c, cudaStreamBeginCapture(c->cap_stream, cudaStreamCaptureModeRelaxed));
+      cfust_status cs = enqueue_batch_iteration(c, c->cap_stream);
+      cudaError_t ce = cudaStreamEndCapture(c->cap_stream, &gr);
+      if (cs != CFUST_OK) {
+        if (gr) cudaGraphDestroy(gr);
+        return cs;
+      }
+      if (ce != cudaSuccess) return cuda_fail(c, ce, "cudaStreamEndCapture");
+      ce = cudaGraphInstantiate(&b.graph, gr, 0);
+      cudaGraphDestroy(gr);
+      if (ce != cudaSuccess) {
+        b.graph = nullptr;
+        return cuda_fail(c, ce, "cudaGraphInstantiate");
+      }
+    }
+  }
+  for (int k = 0; k < K; ++k) CF_CUDA(c, cudaGraphLaunch(b.graph, c->stream));
+  // final density sweep: l(Psi^(K)) of every fit
+  if ((s = enqueue_batch_estep(c, c->stream, true)) != CFUST_OK) return s;
+  {
+    const BatchDev d = batch_dev(b);
+    CF_CUDA(c, launch_posterior_batched(c->opts.precision, d, p, r, b.d_blocks, b.nblocks, b.partials, b.llpart,
+                                        false, b.g_max, c->stream));
+    CF_CUDA(c, launch_reduce_ll_batched(d, b.llpart, b.trace, K + 1, b.iter, c->stream));
+  }
+  std::vector<int> fst(nfits);
+  int bits = 0;
+  CF_CUDA(c, cudaMemcpyAsync(fst.data(), b.fit_status, sizeof(int) * nfits, cudaMemcpyDeviceToHost, c->stream));
+  CF_CUDA(c, cudaMemcpyAsync(&bits, b.status, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+  std::vector<double> host(b.params_len);
+  CF_CUDA(c, cudaMemcpyAsync(host.data(), b.d_params, sizeof(double) * b.params_len, cudaMemcpyDeviceToHost,
+                             c->stream));
+  if (trace_out)
+    CF_CUDA(c, cudaMemcpyAsync(trace_out, b.trace, sizeof(double) * (size_t)nfits * (K + 1),
+                               cudaMemcpyDeviceToHost, c->stream));
+  CF_CUDA(c, cudaStreamSynchronize(c->stream));
+  if (bits) return status_from_bits(c, bits);
+  cfust_status first = CFUST_OK;
+  int64_t off = 0;
+  for (int f = 0; f < nfits; ++f) {
+    const int g = P[f].g;
+    cfust_status fs = fst[f] ? status_from_bits(c, fst[f]) : CFUST_OK;
+    if (fit_status_out) fit_status_out[f] = fs;
+    if (fs != CFUST_OK && first == CFUST_OK) {
+      first = fs;
+      c->err = "fit " + std::to_string(f) + ": " + c->err;
+    }
+    if (fs == CFUST_OK) {
+      ParamView v = param_view(host.data() + off, g, p, r);
+      memcpy(P[f].pi, v.pi, sizeof(double) * g);
+      memcpy(P[f].mu, v.mu, sizeof(double) * g * p);
+      memcpy(P[f].Sigma, v.Sigma, sizeof(double) * g * p * p);
+      memcpy(P[f].Delta, v.Delta, sizeof(double) * g * p * r);
+      memcpy(P[f].nu, v.nu, sizeof(double) * g);
+    }
+    off += param_block_size(g, p, r);
+  }
+  return first;
+}
 
 // ---------------------------------------------------------------------------
 // M-step without allocation: scratch in a static device array.

@@ -150,4 +150,64 @@ cudaError_t launch_mstep_finalize(const double *partials, int nblocks, int g, in
                                   int64_t n, double nu_min, double nu_max, double *d_params,
                                   int *d_status, cudaStream_t st);
 
+// ---------------------------------------------------------------------------
+// Batched fits: many independent fits (same p, r and lattice; own n and g)
+// advanced together, one persistent sweep launch per EM iteration.
+// ---------------------------------------------------------------------------
+
+struct FitDesc {
+  const double *Y;    // device [n][p]
+  int64_t n;
+  int g;
+  int comp0;          // global index of this fit's first component
+  int64_t pair_off;   // this fit's rows in the per-pair buffers: sum of g n over earlier fits
+  int64_t param_off;  // offset (doubles) of this fit's parameter block
+  int64_t part_off;   // offset (doubles) of this fit's per-block partial sums
+  int blk0, nblk;     // this fit's posterior blocks (global block index, count)
+};
+
+struct CompRef {
+  int fit, i;         // global component -> (fit, component within the fit)
+};
+
+struct SweepItem {
+  int gc;             // global component
+  unsigned j0;        // first observation of the item
+};
+
+struct BlockRef {
+  int fit, lb;        // global posterior block -> (fit, block within the fit)
+};
+
+struct BatchDev {
+  const FitDesc *fits;
+  const CompRef *comps;
+  int nfits, G;
+  double *params;     // all parameter blocks back to back
+  void *logf, *e1, *e2, *e3, *e4;  // per-pair buffers (precision of the context)
+  int *fit_status;    // [nfits] error bits per fit
+};
+
+cudaError_t launch_precompute_batched(const BatchDev &b, int p, int r, const LatticeDev &lat,
+                                      CompT<double> *c64, CompT<float> *c32, double *chi64, float *chi32,
+                                      cudaStream_t st);
+
+cudaError_t launch_estep_batched(int precision, const BatchDev &b, int p, int r, const LatticeDev &lat,
+                                 const CompT<double> *c64, const CompT<float> *c32, const double *chi64,
+                                 const float *chi32, const SweepItem *items, int nitems,
+                                 unsigned *item_counter, bool density_only, int e2_mode, int ppw,
+                                 int ctas_per_sm, unsigned long long *rescue_list, unsigned *rescue_count,
+                                 int *d_status, int triage, cudaStream_t st, SweepTiming tm = SweepTiming());
+
+cudaError_t launch_posterior_batched(int precision, const BatchDev &b, int p, int r, const BlockRef *blocks,
+                                     int nblocks, double *partials, double *ll_partials, bool want_sums,
+                                     int g_max, cudaStream_t st);
+
+// trace[f * stride + *iter] = sum of fit f's log-likelihood partials; then ++*iter.
+cudaError_t launch_reduce_ll_batched(const BatchDev &b, const double *ll_partials, double *trace, int stride,
+                                     int *iter, cudaStream_t st);
+
+cudaError_t launch_finalize_batched(const BatchDev &b, int p, int r, const double *partials, double nu_min,
+                                    double nu_max, cudaStream_t st);
+
 }  // namespace cfust

@@ -871,6 +871,161 @@ cudaError_t dispatch_r(int r, EArgs a, int g, int64_t n, cudaStream_t st, bool f
   }
 }
 
+
+// ---------------------------------------------------------------------------
+// Batched fits
+// ---------------------------------------------------------------------------
+
+template <typename OT>
+__device__ __forceinline__ FitView batch_view(const BatchDev &b, const FitDesc &fd, int p, int r) {
+  FitView f;
+  f.Y = fd.Y;
+  f.n = fd.n;
+  f.g = fd.g;
+  const int rp = r * (r + 1) / 2;
+  f.out.logf = reinterpret_cast<OT *>(b.logf) + fd.pair_off;
+  f.out.e1 = reinterpret_cast<OT *>(b.e1) + fd.pair_off;
+  f.out.e2 = reinterpret_cast<OT *>(b.e2) + fd.pair_off;
+  f.out.e3 = reinterpret_cast<OT *>(b.e3) + fd.pair_off * r;
+  f.out.e4 = reinterpret_cast<OT *>(b.e4) + fd.pair_off * rp;
+  f.pi = param_view(b.params + fd.param_off, fd.g, p, r).pi;
+  return f;
+}
+
+// Persistent sweep over many fits: each CTA pulls (component, observation
+// tile) items from an atomic counter until none are left; the component's
+// chi tables are restaged by one bulk copy (bounded mbarrier wait) and its
+// constants copied only when the component changes from the CTA's previous
+// item.  Items are ordered component by component, so a CTA mostly stays on
+// one component.  A lost copy ends the whole CTA with ERR_TIMEOUT.
+template <typename T, int R, bool DENS>
+__global__ void __launch_bounds__(256, sizeof(T) == 4 ? CFUST_ESTEP_MINB : 1)
+    estep_batched_kernel(EArgs a, BatchDev b, const SweepItem *items, int nitems, unsigned *counter) {
+  extern __shared__ __align__(128) unsigned char smem[];
+  __shared__ int s_item;
+  __shared__ int s_fail;
+  const int N = a.N;
+  const size_t tab_bytes = a.staged ? (size_t)(DENS ? 1 : 2) * N * sizeof(T) : 0;
+  T *tab = reinterpret_cast<T *>(smem);
+  CompT<T> *cs = reinterpret_cast<CompT<T> *>(smem + align16(tab_bytes));
+  PairedConsts *pcs = reinterpret_cast<PairedConsts *>(smem + align16(tab_bytes) + align16(sizeof(CompT<T>)));
+  uint64_t *bar = reinterpret_cast<uint64_t *>(smem + align16(tab_bytes) + align16(sizeof(CompT<T>)) +
+                                               align16(sizeof(PairedConsts)));
+  const T *gtab_base = reinterpret_cast<const T *>(a.chi);
+  const CompT<T> *gcomp = reinterpret_cast<const CompT<T> *>(a.comp);
+  if (threadIdx.x == 0) {
+    if (a.staged) mbar_init(bar, 1);
+    s_fail = 0;
+  }
+  __syncthreads();
+  int cur = -1;
+  uint32_t phase = 0;
+  for (;;) {
+    if (threadIdx.x == 0) s_item = (int)atomicAdd(counter, 1u);
+    __syncthreads();
+    const int it = s_item;
+    if (it >= nitems) break;
+    const SweepItem item = items[it];
+    if (item.gc != cur) {
+      // every warp finished the previous item at the barrier above
+      if (a.staged && threadIdx.x == 0) {
+        mbar_expect_tx(bar, static_cast<uint32_t>(tab_bytes));
+        bulk_copy_g2s(tab, gtab_base + (int64_t)item.gc * 2 * N, static_cast<uint32_t>(tab_bytes), bar);
+      }
+      const uint32_t *src = reinterpret_cast<const uint32_t *>(gcomp + item.gc);
+      uint32_t *dst = reinterpret_cast<uint32_t *>(cs);
+      for (int w = threadIdx.x; w < (int)(sizeof(CompT<T>) / 4); w += blockDim.x) dst[w] = src[w];
+      __syncthreads();
+      if (threadIdx.x < RMAX * RMAX) {
+        const int t = threadIdx.x / RMAX, h = threadIdx.x % RMAX;
+        if (h <= t) {
+          const float v = -(float)cs->L[t * RMAX + h];
+          pcs->nL[t * (t + 1) / 2 + h] = make_float2(v, v);
+        }
+        if (h == 0) {
+          const float li = (float)cs->Linv[t];
+          pcs->Li[t] = make_float2(li, li);
+        }
+      }
+      if (a.staged && !mbar_wait_bounded(bar, phase, 1 << 22)) atomicOr(&s_fail, 1);
+      phase ^= 1u;
+      __syncthreads();
+      if (s_fail) {
+        if (threadIdx.x == 0) atomicOr(a.status, ERR_TIMEOUT);
+        return;
+      }
+      cur = item.gc;
+    }
+    const T *tA = a.staged ? tab : gtab_base + (int64_t)cur * 2 * N;
+    const T *tB = tA + N;
+    const CompRef cr = b.comps[item.gc];
+    const FitDesc fd = b.fits[cr.fit];
+    const FitView fv = batch_view<T>(b, fd, a.p, R);
+    const int warp = threadIdx.x >> 5;
+    const int64_t jw0 = (int64_t)item.j0 + (int64_t)warp * a.ppw;
+    sweep_warp_pairs<T, R, DENS>(a, fv, *cs, pcs, tA, tB, cr.i, item.gc, jw0, a.ppw);
+    __syncthreads();
+  }
+}
+
+template <int R, bool DENS>
+__global__ void __launch_bounds__(256) rescue_batched_kernel(EArgs a, BatchDev b, const CompT<double> *comp,
+                                                              const double *chi) {
+  constexpr int NV = 3 + R + R * (R + 1) / 2;
+  __shared__ double sm[8 * (2 + NV)];
+  __shared__ Prologue<R> spr;
+  __shared__ int skip;
+  const unsigned cnt = *a.rescue_count;
+  for (unsigned w = blockIdx.x; w < cnt; w += gridDim.x) {
+    const unsigned long long id = a.rescue_list[w];
+    const int gc = static_cast<int>(id >> 32);
+    const int64_t j = static_cast<int64_t>(id & 0xffffffffull);
+    const CompRef cr = b.comps[gc];
+    const FitDesc fd = b.fits[cr.fit];
+    const FitView fv = batch_view<float>(b, fd, a.p, R);
+    rescue_one<R, DENS>(a, fv, comp[gc], chi + (int64_t)gc * 2 * a.N, cr.i, j, sm, spr, skip);
+  }
+}
+
+template <typename T, int R, bool DENS>
+cudaError_t launch_batched_r(EArgs a, const BatchDev &b, const SweepItem *items, int nitems, unsigned *counter,
+                             int ctas_per_sm, cudaStream_t st, bool fp32, const CompT<double> *c64,
+                             const double *chi64, SweepTiming tm) {
+  const size_t tab_bytes = (size_t)(DENS ? 1 : 2) * a.N * sizeof(T);
+  a.staged = tab_bytes <= 160u * 1024u ? 1 : 0;
+  const size_t smem = (a.staged ? align16(tab_bytes) : 0) + align16(sizeof(CompT<T>)) +
+                      align16(sizeof(PairedConsts)) + 16;
+  cudaError_t e = cudaFuncSetAttribute(estep_batched_kernel<T, R, DENS>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  if ((e = cudaMemsetAsync(counter, 0, sizeof(unsigned), st)) != cudaSuccess) return e;
+  if (fp32 && (e = cudaMemsetAsync(a.rescue_count, 0, sizeof(unsigned), st)) != cudaSuccess) return e;
+  const unsigned evflag = tm.capturing ? cudaEventRecordExternal : cudaEventRecordDefault;
+  if (tm.start && (e = cudaEventRecordWithFlags(tm.start, st, evflag)) != cudaSuccess) return e;
+  estep_batched_kernel<T, R, DENS><<<152 * (ctas_per_sm > 0 ? ctas_per_sm : 2), 256, smem, st>>>(a, b, items,
+                                                                                                 nitems, counter);
+  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  if (tm.stop && (e = cudaEventRecordWithFlags(tm.stop, st, evflag)) != cudaSuccess) return e;
+  if (!fp32) return cudaSuccess;
+  rescue_batched_kernel<R, DENS><<<152 * 4, 256, 0, st>>>(a, b, c64, chi64);
+  return cudaGetLastError();
+}
+
+template <typename T, bool DENS>
+cudaError_t dispatch_batched(int r, EArgs a, const BatchDev &b, const SweepItem *items, int nitems,
+                             unsigned *counter, int cps, cudaStream_t st, bool fp32, const CompT<double> *c64,
+                             const double *chi64, SweepTiming tm) {
+  switch (r) {
+    case 1: return launch_batched_r<T, 1, DENS>(a, b, items, nitems, counter, cps, st, fp32, c64, chi64, tm);
+    case 2: return launch_batched_r<T, 2, DENS>(a, b, items, nitems, counter, cps, st, fp32, c64, chi64, tm);
+    case 3: return launch_batched_r<T, 3, DENS>(a, b, items, nitems, counter, cps, st, fp32, c64, chi64, tm);
+    case 4: return launch_batched_r<T, 4, DENS>(a, b, items, nitems, counter, cps, st, fp32, c64, chi64, tm);
+    case 5: return launch_batched_r<T, 5, DENS>(a, b, items, nitems, counter, cps, st, fp32, c64, chi64, tm);
+    case 6: return launch_batched_r<T, 6, DENS>(a, b, items, nitems, counter, cps, st, fp32, c64, chi64, tm);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
 __global__ void normal_f32_kernel(const float *x, float *out, int64_t n, int which) {
   for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < n; k += (int64_t)gridDim.x * blockDim.x) {
     const float v = x[k];
@@ -894,6 +1049,48 @@ cudaError_t launch_normal_f32(const float *x, float *out, int64_t n, int which, 
   const int64_t blocks = (n + 255) / 256;
   normal_f32_kernel<<<(unsigned)(blocks < 152 * 16 ? blocks : 152 * 16), 256, 0, st>>>(x, out, n, which);
   return cudaGetLastError();
+}
+
+cudaError_t launch_estep_batched(int precision, const BatchDev &b, int p, int r, const LatticeDev &lat,
+                                 const CompT<double> *c64, const CompT<float> *c32, const double *chi64,
+                                 const float *chi32, const SweepItem *items, int nitems,
+                                 unsigned *item_counter, bool density_only, int e2_mode, int ppw,
+                                 int ctas_per_sm, unsigned long long *rescue_list, unsigned *rescue_count,
+                                 int *d_status, int triage, cudaStream_t st, SweepTiming tm) {
+  if (nitems <= 0) return cudaSuccess;
+  EArgs a{};
+  a.Y = nullptr;
+  a.n = 0;
+  a.g = 0;
+  a.p = p;
+  a.N = lat.n;
+  for (int t = 0; t <= RMAX; ++t) {
+    a.z[t] = lat.z[t];
+    a.step[t] = lat.step[t];
+    a.sint[t] = lat.sint[t];
+    a.sfrac[t] = lat.sfrac[t];
+    a.fstep2[t] = (float)(2 * lat.step[t]);
+    a.ftwo_sf[t] = (float)(2.0 * lat.sfrac[t]);
+    a.fsf[t] = (float)lat.sfrac[t];
+  }
+  a.e2_mode = e2_mode;
+  a.ppw = ppw < 1 ? 1 : (ppw > 32 ? 32 : ppw);
+  a.rescue_list = rescue_list;
+  a.rescue_count = rescue_count;
+  a.status = d_status;
+  a.triage = triage ? 1 : 0;
+  if (precision == CFUST_FP64) {
+    a.comp = c64;
+    a.chi = chi64;
+    return density_only
+               ? dispatch_batched<double, true>(r, a, b, items, nitems, item_counter, ctas_per_sm, st, false, c64, chi64, tm)
+               : dispatch_batched<double, false>(r, a, b, items, nitems, item_counter, ctas_per_sm, st, false, c64, chi64, tm);
+  }
+  a.comp = c32;
+  a.chi = chi32;
+  return density_only
+             ? dispatch_batched<float, true>(r, a, b, items, nitems, item_counter, ctas_per_sm, st, true, c64, chi64, tm)
+             : dispatch_batched<float, false>(r, a, b, items, nitems, item_counter, ctas_per_sm, st, true, c64, chi64, tm);
 }
 
 cudaError_t launch_estep(int precision, const double *Y, int64_t n, int g, int p, int r,

@@ -341,7 +341,100 @@ __global__ void mstep_finalize_kernel(const double *partials, int nb, int g, int
   mstep_finalize_block(partials, nb, g, p, r, n, nu_min, nu_max, params, status, blockIdx.x);
 }
 
+template <typename ET>
+__global__ void __launch_bounds__(THREADS) posterior_batched_kernel(BatchDev b, int p, int r, const BlockRef *blocks,
+                                                                     double *partials, double *ll_partials,
+                                                                     bool want_sums) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const BlockRef br = blocks[blockIdx.x];
+  const FitDesc fd = b.fits[br.fit];
+  const int rp = r * (r + 1) / 2;
+  PosteriorArgs a{};
+  a.Y = fd.Y;
+  a.n = fd.n;
+  a.g = fd.g;
+  a.p = p;
+  a.r = r;
+  a.pi = param_view(b.params + fd.param_off, fd.g, p, r).pi;
+  a.logf = reinterpret_cast<const ET *>(b.logf) + fd.pair_off;
+  a.e1 = reinterpret_cast<const ET *>(b.e1) + fd.pair_off;
+  a.e2 = reinterpret_cast<const ET *>(b.e2) + fd.pair_off;
+  a.e3 = reinterpret_cast<const ET *>(b.e3) + fd.pair_off * r;
+  a.e4 = reinterpret_cast<const ET *>(b.e4) + fd.pair_off * rp;
+  a.want_sums = want_sums;
+  a.want_ll = true;
+  a.partials = partials + fd.part_off;
+  a.ll_partials = ll_partials + fd.blk0;
+  a.d_status = b.fit_status + br.fit;
+  a.nblocks = fd.nblk;
+  posterior_block<ET>(a, 0, fd.g, br.lb, fd.nblk, smem_raw);
+}
+
+__global__ void reduce_ll_batched_kernel(BatchDev b, const double *part, double *trace, int stride, int *iter) {
+  __shared__ double red[256];
+  const FitDesc fd = b.fits[blockIdx.x];
+  double s = 0.0;
+  for (int k = threadIdx.x; k < fd.nblk; k += 256) s += part[fd.blk0 + k];
+  red[threadIdx.x] = s;
+  __syncthreads();
+  for (int h = 128; h > 0; h >>= 1) {
+    if (threadIdx.x < h) red[threadIdx.x] += red[threadIdx.x + h];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) trace[(int64_t)blockIdx.x * stride + *iter] = red[0];
+}
+
+__global__ void advance_iter_kernel(int *iter) { *iter += 1; }
+
+__global__ void finalize_batched_kernel(BatchDev b, int p, int r, const double *partials, double nu_min,
+                                        double nu_max) {
+  const CompRef cr = b.comps[blockIdx.x];
+  const FitDesc fd = b.fits[cr.fit];
+  mstep_finalize_block(partials + fd.part_off, fd.nblk, fd.g, p, r, fd.n, nu_min, nu_max,
+                       b.params + fd.param_off, b.fit_status + cr.fit, cr.i);
+}
+
 }  // namespace
+
+cudaError_t launch_posterior_batched(int precision, const BatchDev &b, int p, int r, const BlockRef *blocks,
+                                     int nblocks, double *partials, double *ll_partials, bool want_sums,
+                                     int g_max, cudaStream_t st) {
+  const int WR = 3 + r + r * (r + 1) / 2;
+  const int K = sums_width(p, r);
+  if (want_sums && g_max * K > MAXOWN * THREADS) return cudaErrorInvalidValue;
+  const size_t smem = want_sums ? ((size_t)TJ * p + (size_t)g_max * TJ * WR) * 8 : 16;
+  if (smem > 200 * 1024) return cudaErrorInvalidValue;
+  cudaError_t e;
+  if (precision == CFUST_FP64) {
+    e = cudaFuncSetAttribute(posterior_batched_kernel<double>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)smem);
+    if (e != cudaSuccess) return e;
+    posterior_batched_kernel<double><<<nblocks, THREADS, smem, st>>>(b, p, r, blocks, partials, ll_partials,
+                                                                     want_sums);
+  } else {
+    e = cudaFuncSetAttribute(posterior_batched_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)smem);
+    if (e != cudaSuccess) return e;
+    posterior_batched_kernel<float><<<nblocks, THREADS, smem, st>>>(b, p, r, blocks, partials, ll_partials,
+                                                                    want_sums);
+  }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_reduce_ll_batched(const BatchDev &b, const double *ll_partials, double *trace, int stride,
+                                     int *iter, cudaStream_t st) {
+  reduce_ll_batched_kernel<<<b.nfits, 256, 0, st>>>(b, ll_partials, trace, stride, iter);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  advance_iter_kernel<<<1, 1, 0, st>>>(iter);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_finalize_batched(const BatchDev &b, int p, int r, const double *partials, double nu_min,
+                                    double nu_max, cudaStream_t st) {
+  finalize_batched_kernel<<<b.G, 128, 0, st>>>(b, p, r, partials, nu_min, nu_max);
+  return cudaGetLastError();
+}
 
 int posterior_nblocks(int64_t n) {
   const int64_t ntiles = (n + TJ - 1) / TJ;

@@ -157,7 +157,27 @@ __global__ void precompute_kernel(const double *params, int g, int p, int r, Lat
                        chi32 + (int64_t)i * 2 * lat.n, status, blockIdx.x, gridDim.x);
 }
 
+__global__ void precompute_batched_kernel(BatchDev b, int p, int r, LatticeDev lat, CompT<double> *c64,
+                                          CompT<float> *c32, double *chi64, float *chi32) {
+  const int gc = blockIdx.y;
+  const CompRef cr = b.comps[gc];
+  const FitDesc fd = b.fits[cr.fit];
+  precompute_component(b.params + fd.param_off, fd.g, p, r, cr.i, lat, c64 + gc, c32 + gc,
+                       chi64 + (int64_t)gc * 2 * lat.n, chi32 + (int64_t)gc * 2 * lat.n, b.fit_status + cr.fit,
+                       blockIdx.x, gridDim.x);
+}
+
 }  // namespace
+
+cudaError_t launch_precompute_batched(const BatchDev &b, int p, int r, const LatticeDev &lat,
+                                      CompT<double> *c64, CompT<float> *c32, double *chi64, float *chi32,
+                                      cudaStream_t st) {
+  const int threads = 128;
+  int bx = (lat.n + threads - 1) / threads;
+  if (bx < 1) bx = 1;
+  precompute_batched_kernel<<<dim3(bx, b.G), threads, 0, st>>>(b, p, r, lat, c64, c32, chi64, chi32);
+  return cudaGetLastError();
+}
 
 cudaError_t launch_precompute(const double *d_params, int g, int p, int r, const LatticeDev &lat,
                               CompT<double> *c64, CompT<float> *c32, double *chi64, float *chi32,

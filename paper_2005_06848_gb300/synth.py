@@ -22,7 +22,7 @@ import numpy as np
 __all__ = [
     "Params", "Lattice", "splitmix64_stream", "korobov_generator",
     "make_lattice", "sample_cfust", "perturb_params", "random_params",
-    "workload", "WORKLOADS",
+    "workload", "WORKLOADS", "batched_workload",
 ]
 
 
@@ -248,3 +248,23 @@ def workload(name: str, n: int | None = None, seed: int = 0):
     init = perturb_params(truth, rng)
     lattice = make_lattice(meta["lattice_n"], r + 1, seed)
     return Y, labels, truth, init, lattice, meta
+
+
+def batched_workload(nfits: int = 256, seed0: int = 0, n_lo: int = 5000, n_hi: int = 200000,
+                     p: int = 3, r: int = 3, g_lo: int = 2, g_hi: int = 5):
+    """Many independent fits: fit f draws with seed seed0 + f its component
+    count g ~ U{g_lo..g_hi}, its size n log-uniform in [n_lo, n_hi], its truth
+    (mu ~ N(0, 9I), Sigma = Wishart(p+2, I)/(p+2), Delta ~ U(-2, 2),
+    nu ~ U(3, 12), equal pi), its data, and a perturbed start (a random
+    restart).  Returns (list of Y, list of truth, list of init)."""
+    Ys, truths, inits = [], [], []
+    for f in range(nfits):
+        rng = np.random.default_rng(seed0 + f)
+        g = int(rng.integers(g_lo, g_hi + 1))
+        n = int(round(math.exp(rng.uniform(math.log(n_lo), math.log(n_hi)))))
+        truth = random_params(rng, g, p, r, 9.0, 2, 2.0, 3.0, 12.0)
+        Y, _ = sample_cfust(truth, n, rng)
+        Ys.append(Y)
+        truths.append(truth)
+        inits.append(perturb_params(truth, rng))
+    return Ys, truths, inits

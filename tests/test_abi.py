@@ -41,7 +41,7 @@ def test_create_rejects_bad_lattice_without_a_device():
     for n, dim, prec in [(100, 3, 1), (16, 3, 1), (1024, 9, 1), (1024, 3, 7)]:
         lat = binding.cfust_lattice(n, dim, z.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)),
                                     sh.ctypes.data_as(ctypes.POINTER(ctypes.c_double)))
-        opts = binding.cfust_opts(prec, lat, 0, 0.0, 0.0, 5, 0.0, 1, 0, 0)
+        opts = binding.cfust_opts(prec, lat, 0, 0.0, 0.0, 5, 0.0, 1, 0, 0, 0)
         h = ctypes.c_void_p()
         st = lib.cfust_create(ctypes.byref(h), ctypes.byref(opts), None)
         assert st == -1, (n, dim, prec, st)
@@ -49,7 +49,7 @@ def test_create_rejects_bad_lattice_without_a_device():
     bad_shift = np.array([0.1, 1.5, 0.3])
     lat = binding.cfust_lattice(1024, 3, z.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)),
                                 bad_shift.ctypes.data_as(ctypes.POINTER(ctypes.c_double)))
-    opts = binding.cfust_opts(1, lat, 0, 0.0, 0.0, 5, 0.0, 1, 0, 0)
+    opts = binding.cfust_opts(1, lat, 0, 0.0, 0.0, 5, 0.0, 1, 0, 0, 0)
     h = ctypes.c_void_p()
     st = lib.cfust_create(ctypes.byref(h), ctypes.byref(opts), None)
     assert st in (-1, -6)   # -6 when no device is visible (checked first on some hosts)

@@ -1,0 +1,87 @@
+"""Batched fits (one persistent sweep launch per EM iteration over every fit)
+against the same fits run one at a time, and against the FP64 oracle."""
+import numpy as np
+import pytest
+
+from oracle import cfust_oracle as O
+from paper_2005_06848_gb300 import binding, synth
+
+pytestmark = [pytest.mark.gpu, pytest.mark.filterwarnings("ignore::RuntimeWarning")]
+
+
+def _torch():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    return torch
+
+
+def _small_batch(nfits=5, seed0=40):
+    return synth.batched_workload(nfits, seed0=seed0, n_lo=60, n_hi=1500)
+
+
+@pytest.mark.parametrize("precision", [binding.CFUST_FP64, binding.CFUST_FP32])
+def test_batched_equals_single_fits(precision):
+    torch = _torch()
+    Ys, truths, inits = _small_batch()
+    lat = synth.make_lattice(256, 4, 0)
+    Yd = [torch.from_numpy(Y).cuda() for Y in Ys]
+    iters = 3
+    with binding.Context(lat, precision=precision, max_iter=iters) as ctx:
+        bp, btr, st = ctx.cfust_fit_batched(Yd, inits)
+    assert all(s == 0 for s in st)
+    for f, (Y, P0) in enumerate(zip(Yd, inits)):
+        with binding.Context(lat, precision=precision, max_iter=iters) as ctx:
+            sp, str_, _ = ctx.cfust_fit(Y, P0)
+        assert np.allclose(btr[f], str_, rtol=1e-12, atol=0), f
+        for a, b in zip(bp[f].as_arrays(), sp.as_arrays()):
+            assert np.allclose(a, b, rtol=1e-12, atol=1e-14), f
+
+
+def test_batched_fp64_matches_oracle_on_two_fits():
+    torch = _torch()
+    Ys, truths, inits = _small_batch(2, seed0=7)
+    lat = synth.make_lattice(256, 4, 3)
+    U = O.lattice_points(lat.n, lat.z, lat.shift)
+    with binding.Context(lat, precision=binding.CFUST_FP64, max_iter=2) as ctx:
+        bp, btr, st = ctx.cfust_fit_batched([torch.from_numpy(Y).cuda() for Y in Ys], inits)
+    for f in range(2):
+        ref, ref_tr = O.fit(Ys[f], inits[f], U, 2)
+        assert np.allclose(btr[f], ref_tr, rtol=1e-10, atol=0)
+        for a, b in zip(bp[f].as_arrays(), ref.as_arrays()):
+            assert np.allclose(a, b, rtol=1e-8, atol=1e-10)
+
+
+def test_autotuned_shape_gives_the_same_fits():
+    torch = _torch()
+    Ys, truths, inits = _small_batch(4, seed0=90)
+    lat = synth.make_lattice(512, 4, 0)
+    Yd = [torch.from_numpy(Y).cuda() for Y in Ys]
+    with binding.Context(lat, precision=binding.CFUST_FP32, max_iter=2, autotune=True) as ctx:
+        a, ta, _ = ctx.cfust_fit_batched(Yd, inits)
+        ppw, cps = ctx.cfust_batched_shape()
+        # a second call on the same batch reuses the tuned shape and the graph
+        a2, ta2, _ = ctx.cfust_fit_batched(Yd, inits)
+    assert ppw in (2, 4, 8, 16) and cps in (1, 2)
+    assert np.array_equal(ta, ta2)
+    with binding.Context(lat, precision=binding.CFUST_FP32, max_iter=2, pairs_per_warp=1) as ctx:
+        b, tb, _ = ctx.cfust_fit_batched(Yd, inits)
+    assert np.allclose(ta, tb, rtol=1e-12)
+    for pa, pb in zip(a, b):
+        for x, y in zip(pa.as_arrays(), pb.as_arrays()):
+            assert np.allclose(x, y, rtol=1e-12, atol=1e-14)
+
+
+def test_one_degenerate_fit_is_reported_alone():
+    torch = _torch()
+    Ys, truths, inits = _small_batch(3, seed0=11)
+    bad = inits[1].copy()
+    bad.mu[0] = 1e4            # no observation near this component
+    bad.Delta[0] = 0.0
+    inits = [inits[0], bad, inits[2]]
+    lat = synth.make_lattice(256, 4, 0)
+    with binding.Context(lat, precision=binding.CFUST_FP64, max_iter=2) as ctx:
+        with pytest.raises(binding.CfustError) as ei:
+            ctx.cfust_fit_batched([torch.from_numpy(Y).cuda() for Y in Ys], inits)
+    assert ei.value.status == -4
+    assert "fit 1" in str(ei.value)
