@@ -40,7 +40,8 @@ def test_batched_equals_single_fits(precision):
 
 def test_batched_fp64_matches_oracle_on_two_fits():
     torch = _torch()
-    Ys, truths, inits = _small_batch(2, seed0=7)
+    # two fits with every component well populated (S6 well conditioned)
+    Ys, truths, inits = synth.batched_workload(2, seed0=7, n_lo=800, n_hi=1500, g_hi=3)
     lat = synth.make_lattice(256, 4, 3)
     U = O.lattice_points(lat.n, lat.z, lat.shift)
     with binding.Context(lat, precision=binding.CFUST_FP64, max_iter=2) as ctx:
