@@ -86,3 +86,23 @@ def test_one_degenerate_fit_is_reported_alone():
             ctx.cfust_fit_batched([torch.from_numpy(Y).cuda() for Y in Ys], inits)
     assert ei.value.status == -4
     assert "fit 1" in str(ei.value)
+
+
+def test_full_batch_of_256_fits_matches_sampled_single_fits():
+    """The 256-fit workload (n log-uniform in [5000, 200000], g in 2..5, 2048-point
+    lattice) in the bench's launch configuration for one EM iteration; three
+    sampled fits are rerun alone and must agree."""
+    torch = _torch()
+    Ys, truths, inits = synth.batched_workload(256)
+    lat = synth.make_lattice(2048, 4, 0)
+    Yd = [torch.from_numpy(Y).cuda() for Y in Ys]
+    with binding.Context(lat, precision=binding.CFUST_FP32, max_iter=1, autotune=True) as ctx:
+        bp, btr, st = ctx.cfust_fit_batched(Yd, inits)
+    assert all(s == 0 for s in st)
+    assert np.all(np.isfinite(btr))
+    for f in (0, 97, 255):
+        with binding.Context(lat, precision=binding.CFUST_FP32, max_iter=1) as ctx:
+            sp, str_, _ = ctx.cfust_fit(Yd[f], inits[f])
+        assert np.allclose(btr[f], str_, rtol=1e-12, atol=0)
+        for a, b in zip(bp[f].as_arrays(), sp.as_arrays()):
+            assert np.allclose(a, b, rtol=1e-12, atol=1e-14)
