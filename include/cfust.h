@@ -233,6 +233,101 @@ cfust_status cfust_mstep_noalloc(int precision, const double *Y, int64_t n,
                                  const void *e3, const void *e4, double nu_min, double nu_max,
                                  cfust_params *params, void *cuda_stream);
 
+/* ---------------------------------------------------------------------------
+ * Learned surrogate of the trivariate truncated-t integrals (r = 3).
+ *
+ * Not in the paper: an added form of the E-step.  The lattice rule's two
+ * integrals per pair (T_A, and T_B with the truncated moments; Eq. 2 and the
+ * E-step expectations of Section 3.1) are, after standardisation, functions
+ * of a truncation point c in R^3, a correlation matrix R (3 off-diagonal
+ * entries) and the degrees of freedom m:
+ *   X ~ t_3(0, R, m):  log P(X > c),  E[X | X > c],  E[X X^T | X > c].
+ * A network 7 -> 128 -> 128 -> 128 -> 10 (GELU, BF16 weights and activations,
+ * FP32 accumulation on the tensor cores) maps
+ *   x = (c_1, c_2, c_3, R_12, R_13, R_23, log m)
+ * to y = (log P, E[X_1..3], E[X X^T] upper triangle 11 12 13 22 23 33).
+ * Training domain: -8 <= c_t <= 4, |R_ht| <= 0.9, squared Cholesky pivots of
+ * R >= 0.05, 3 <= m <= 30.  Training data come from the plain lattice rule on
+ * this library's GPU (labeller below); training (forward, backward, Adam) runs
+ * in this library's kernels.  Internally the network predicts log(-log P),
+ * E[X] and the covariance E[X X^T] - E[X] E[X]^T, standardised per output;
+ * the loss weighs log(-log P) 4x.
+ *
+ * Flat parameter vector theta (CFUST_SURROGATE_NPARAM floats): W1 [7][128]
+ * (input x output, row-major), b1 [128], W2 [128][128], b2, W3 [128][128], b3,
+ * W4 [128][10], b4 [10].  The network predicts (y - mean) / std per output;
+ * norm = (mean[10], std[10]).
+ * ------------------------------------------------------------------------- */
+#define CFUST_SURROGATE_NPARAM 35338
+typedef struct cfust_surrogate cfust_surrogate;
+
+/* Create a surrogate with N(0, 1/fan_in) weights from SplitMix64(seed), zero
+ * biases and unit normalisation.  lattice: the labeller's rule, dim 4 (chi
+ * coordinate and three normal coordinates), n a multiple of 32 up to
+ * CFUST_NMAX (8192 points is the intended size); its chi-scale tables are
+ * built on a grid of 256 values of log m over [log 3, log 30] and
+ * interpolated linearly in log m.  stream: cudaStream_t for all calls on
+ * this object.  Messages from cfust_surrogate_last_error(NULL). */
+cfust_status cfust_surrogate_create(cfust_surrogate **out, uint64_t seed, const cfust_lattice *lattice,
+                                    void *cuda_stream);
+cfust_status cfust_surrogate_destroy(cfust_surrogate *s);
+
+/* Lattice-rule targets of B problems.  x: device float [B][7] (as above), y:
+ * device float [B][10].  A problem whose every point weight underflows gets
+ * NaN targets.  Synchronises the stream. */
+cfust_status cfust_surrogate_label(cfust_surrogate *s, const float *x, float *y, int64_t B);
+
+/* Network prediction (de-normalised) for device x [B][7] into device y [B][10].
+ * Inputs outside the training domain are evaluated all the same.
+ * Synchronises the stream. */
+cfust_status cfust_surrogate_predict(cfust_surrogate *s, const float *x, float *y, int64_t B);
+
+/* Loss (mean over rows and outputs of the squared error of the normalised
+ * prediction) and its gradient with respect to theta for device x [B][7] and
+ * device targets y [B][10] (raw, normalised inside with the current norm).
+ * loss: host double or NULL; grad: host float [CFUST_SURROGATE_NPARAM] or
+ * NULL.  Synchronises the stream. */
+cfust_status cfust_surrogate_gradient(cfust_surrogate *s, const float *x, const float *y, int64_t B,
+                                      double *loss, float *grad);
+
+/* Host copies of theta and norm (either may be NULL), and their replacement
+ * (norm NULL keeps the current one). */
+cfust_status cfust_surrogate_get_params(cfust_surrogate *s, float *theta, float *norm);
+cfust_status cfust_surrogate_set_params(cfust_surrogate *s, const float *theta, const float *norm);
+
+/* Train on n_train problems drawn uniformly over the training domain
+ * (SplitMix64(seed); rows with a non-PD or too-thin R redrawn), labelled on
+ * the GPU, target normalisation set from the labels.  Adam (beta 0.9, 0.999,
+ * eps 1e-8) on mini-batches of `batch` rows with a cosine-decayed step from
+ * lr; `epochs` passes.  loss_trace: host float [epochs] (mean sampled batch
+ * loss per epoch) or NULL.  Requires n_train >= batch >= 128. */
+cfust_status cfust_surrogate_train(cfust_surrogate *s, int64_t n_train, int epochs, int batch, float lr,
+                                   uint64_t seed, float *loss_trace);
+
+const char *cfust_surrogate_last_error(cfust_surrogate *s);
+
+/* Attach a surrogate to a context (NULL detaches; the context does not own
+ * it, and it must outlive its use).  With a surrogate attached, every E-step
+ * of the context (cfust_estep, cfust_loglik, cfust_fit, the stepwise fit)
+ * evaluates each pair's two standardised problems (pass A at dof nu+p and
+ * pass B at nu+p+2, c = D^{-1/2} a with D = diag(Lambda)) with the network
+ * when the pair lies in the domain, and with the context's lattice rule
+ * otherwise.  A pair is the network's when its component's R and dof are in
+ * the domain and pass B's point (the larger one) lies in [-8, 4]^3; when
+ * nu+p >= 8 the lower edge is dropped and c_t < -8 is clamped to -8 (that
+ * moves P by at most P(t_8 < -8) = 2.2e-5).  In the log-likelihood and fit
+ * paths, a pair left to the lattice rule whose bound log pi_i + log f_ij
+ * (the network at the clamped point, plus 5) trails the best component of
+ * its observation by 30 is given tau = 0 without a sweep.  Batched fits
+ * (cfust_fit_batched) always use the lattice rule.
+ * Requires CFUST_FP32 precision, e2_mode 0 and r = 3 (checked when the E-step
+ * runs).  Attaching drops a captured fit graph. */
+cfust_status cfust_set_surrogate(cfust_ctx *ctx, cfust_surrogate *s);
+
+/* Pairs the last surrogate E-step handed to the lattice rule (outside the
+ * training domain).  Synchronises the context's stream. */
+cfust_status cfust_last_fallback(cfust_ctx *ctx, int64_t *count);
+
 /* Message for the last error on ctx (or on context creation when ctx is NULL). */
 const char *cfust_last_error(cfust_ctx *ctx);
 

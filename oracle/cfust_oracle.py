@@ -212,27 +212,44 @@ def estep_component(Y, mu, Sigma, Delta, nu, U, e2_mode=0, density_only=False,
             continue
         aB = -qq * np.sqrt(mB / (nu + dd))[:, None]
         TB, EV, EVV = sov_pass(aB, L, mB, U, moments=True, s=sB)
-        ok = (TA > 0) & (TB > 0)
-        with np.errstate(invalid="ignore", divide="ignore"):
-            c1 = (mA / (nu + dd)) * TB / TA
-            sig = np.sqrt((nu + dd) / mB)
-            LEV = EV @ L.T                                     # L E[V]
-            EX = qq + sig[:, None] * LEV
-            LEVVL = np.einsum("th,jhk,sk->jts", L, EVV, L)
-            EXX = (qq[:, :, None] * qq[:, None, :]
-                   + sig[:, None, None] * (qq[:, :, None] * LEV[:, None, :]
-                                           + LEV[:, :, None] * qq[:, None, :])
-                   + (sig * sig)[:, None, None] * LEVVL)
-            if e2_mode == 1:
-                c2 = elogchi - np.log(nu + dd)
-            else:
-                c2 = (c1 - np.log(0.5 * (nu + dd)) - mA / (nu + dd)
-                      + special.digamma(0.5 * mA))
-        e1[sl] = np.where(ok, c1, 0.0)
-        e2[sl] = np.where(ok, c2, 0.0)
-        e3[sl] = np.where(ok[:, None], c1[:, None] * EX, 0.0)
-        e4[sl] = np.where(ok[:, None, None], c1[:, None, None] * EXX, 0.0)
+        LEV = EV @ L.T                                         # L E[V]
+        LEVVL = np.einsum("th,jhk,sk->jts", L, EVV, L)
+        c1, c2, c3, c4 = expectations(dd, qq, nu, p, TA, TB, LEV, LEVVL, e2_mode,
+                                      elogchi if e2_mode == 1 else None)
+        e1[sl], e2[sl], e3[sl], e4[sl] = c1, c2, c3, c4
     return out
+
+
+def expectations(d, q, nu, p, TA, TB, LEV, LEVVL, e2_mode=0, elogchi=None):
+    """e1..e4 of the pairs of one component from the two passes' results.
+
+    d [P], q [P, r]: the pair's Mahalanobis distance and skew projection;
+    TA, TB [P]: the pass-A and pass-B probabilities; LEV [P, r] = L E[V] and
+    LEVVL [P, r, r] = L E[V V^T] L^T of pass B (X = L V truncated at X > a_B).
+    e1 = (nu+p)/(nu+d) T_B/T_A, sigma = sqrt((nu+d)/(nu+p+2)),
+    e3 = e1 (q + sigma L E[V]),
+    e4 = e1 (q q^T + sigma (q (L E[V])^T + L E[V] q^T) + sigma^2 L E[V V^T] L^T),
+    e2 as in estep_component.  Pairs with T_A or T_B = 0 get zeros.
+    """
+    mA = nu + p
+    mB = nu + p + 2.0
+    ok = (TA > 0) & (TB > 0)
+    with np.errstate(invalid="ignore", divide="ignore"):
+        c1 = (mA / (nu + d)) * TB / TA
+        sig = np.sqrt((nu + d) / mB)
+        EX = q + sig[:, None] * LEV
+        EXX = (q[:, :, None] * q[:, None, :]
+               + sig[:, None, None] * (q[:, :, None] * LEV[:, None, :]
+                                       + LEV[:, :, None] * q[:, None, :])
+               + (sig * sig)[:, None, None] * LEVVL)
+        if e2_mode == 1:
+            c2 = elogchi - np.log(nu + d)
+        else:
+            c2 = (c1 - np.log(0.5 * (nu + d)) - mA / (nu + d)
+                  + special.digamma(0.5 * mA))
+    return (np.where(ok, c1, 0.0), np.where(ok, c2, 0.0),
+            np.where(ok[:, None], c1[:, None] * EX, 0.0),
+            np.where(ok[:, None, None], c1[:, None, None] * EXX, 0.0))
 
 
 def posterior(logf: np.ndarray, pi: np.ndarray):

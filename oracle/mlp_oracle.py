@@ -7,8 +7,13 @@ truncation point c (event X > c, componentwise):
     outputs (10): log P(X > c), E[X | X > c] (3),
                   E[X X^T | X > c] upper triangle (11, 12, 13, 22, 23, 33)
 Network: 7 -> 128 -> 128 -> 128 -> 10, GELU (tanh form) after each hidden
-layer; inputs and targets are affinely normalised by fixed constants.
-Loss: mean over rows and outputs of (prediction - normalised target)^2.
+layer; inputs are affinely normalised by fixed constants.  The network's
+targets are the outputs in covariance form (`net_targets`: the second moments
+minus the products of the first), standardised per output by a mean and a
+standard deviation (`norm`).
+Loss: mean over rows and outputs of LOSS_W[k] (prediction - normalised
+target)^2, log P weighted above the moments because the log-likelihood
+depends on it directly.
 
 Parameters are one flat vector [W1 (7x128, in x out), b1, W2 (128x128), b2,
 W3, b3, W4 (128x10), b4] of 35338 values.
@@ -26,7 +31,7 @@ import numpy as np
 from . import cfust_oracle as O
 
 DIMS = [7, 128, 128, 128, 10]
-C_MAX = 4.0          # |c_t| <= C_MAX
+C_LO, C_HI = -8.0, 4.0   # C_LO <= c_t <= C_HI
 RHO_MAX = 0.9        # |R_ht| <= RHO_MAX
 PIVOT_MIN = 0.05     # every squared Cholesky pivot of R at least this
 LOGM_LO, LOGM_HI = math.log(3.0), math.log(30.0)
@@ -50,14 +55,16 @@ def unpack(theta):
 
 
 def normalise_inputs(x):
-    """c / C_MAX, rho / RHO_MAX, log m mapped affinely onto [-1, 1]."""
+    """c and log m mapped affinely from their ranges onto [-1, 1], rho / RHO_MAX."""
     x = np.asarray(x, dtype=np.float64)
     u = np.empty_like(x)
-    u[:, 0:3] = x[:, 0:3] / C_MAX
+    u[:, 0:3] = (2.0 * x[:, 0:3] - (C_LO + C_HI)) / (C_HI - C_LO)
     u[:, 3:6] = x[:, 3:6] / RHO_MAX
     u[:, 6] = (2.0 * x[:, 6] - (LOGM_LO + LOGM_HI)) / (LOGM_HI - LOGM_LO)
     return u
 
+
+LOSS_W = np.array([4.0] + [1.0] * 9)
 
 GELU_K = math.sqrt(2.0 / math.pi)
 GELU_A = 0.044715
@@ -86,14 +93,14 @@ def forward(theta, u):
 
 
 def loss_and_grad(theta, u, t):
-    """Mean squared error against normalised targets t [B, 10] and its gradient."""
+    """Weighted mean squared error against normalised targets t [B, 10] and its gradient."""
     out, cache = forward(theta, u)
     B = u.shape[0]
     diff = out - t
-    loss = float(np.mean(diff * diff))
+    loss = float(np.mean(LOSS_W * diff * diff))
     layers = unpack(theta)
     grads = []
-    d = 2.0 * diff / diff.size                      # d loss / d out
+    d = 2.0 * LOSS_W * diff / diff.size             # d loss / d out
     for k in range(3, -1, -1):
         h_in = cache[k][0]
         W, _ = layers[k]
@@ -112,7 +119,7 @@ def loss_and_grad(theta, u, t):
 def in_domain(x):
     """Inputs inside the training domain (the same test the E-step applies)."""
     x = np.asarray(x, dtype=np.float64)
-    ok = np.all(np.abs(x[:, 0:3]) <= C_MAX, axis=1)
+    ok = np.all((x[:, 0:3] >= C_LO) & (x[:, 0:3] <= C_HI), axis=1)
     ok &= np.all(np.abs(x[:, 3:6]) <= RHO_MAX, axis=1)
     ok &= (x[:, 6] >= LOGM_LO) & (x[:, 6] <= LOGM_HI)
     r12, r13, r23 = x[:, 3], x[:, 4], x[:, 5]
@@ -122,6 +129,41 @@ def in_domain(x):
         p3 = 1.0 - r13 * r13 - l32 * l32
     ok &= (p2 >= PIVOT_MIN) & (p3 >= PIVOT_MIN)
     return ok
+
+
+UPPER = [(0, 0), (0, 1), (0, 2), (1, 1), (1, 2), (2, 2)]
+
+
+NEGLOG_MIN = 1e-12   # floor of -log P in the target log(-log P)
+
+
+def net_targets(y, norm=None):
+    """Outputs -> network targets: log(-log P) (relative precision for P near
+    1, where most posterior weight sits), E[X] unchanged, second moments
+    replaced by the truncated covariance E[X_a X_b] - E[X_a] E[X_b]; with
+    norm = (mean[10], std[10]) also standardised."""
+    y = np.asarray(y, dtype=np.float64)
+    t = y.copy()
+    t[:, 0] = np.log(np.maximum(-y[:, 0], NEGLOG_MIN))
+    for k, (a, b) in enumerate(UPPER):
+        t[:, 4 + k] = y[:, 4 + k] - y[:, 1 + a] * y[:, 1 + b]
+    if norm is not None:
+        norm = np.asarray(norm, dtype=np.float64)
+        t = (t - norm[:10]) / norm[10:]
+    return t
+
+
+def from_net(t, norm=None):
+    """Inverse of net_targets."""
+    t = np.asarray(t, dtype=np.float64)
+    if norm is not None:
+        norm = np.asarray(norm, dtype=np.float64)
+        t = t * norm[10:] + norm[:10]
+    y = t.copy()
+    y[:, 0] = -np.exp(t[:, 0])
+    for k, (a, b) in enumerate(UPPER):
+        y[:, 4 + k] = t[:, 4 + k] + t[:, 1 + a] * t[:, 1 + b]
+    return y
 
 
 def label(x, U, m_grid=None):

@@ -22,7 +22,13 @@ EXPORTED = ["cfust_create", "cfust_destroy", "cfust_loglik", "cfust_estep", "cfu
             "cfust_fit", "cfust_fit_begin", "cfust_fit_step", "cfust_fit_end", "cfust_fit_trace",
             "cfust_fit_batched", "cfust_batched_shape",
             "cfust_last_rescued", "cfust_last_sweep_ms", "cfust_normal_f32", "cfust_mstep_noalloc",
-            "cfust_last_error"]
+            "cfust_last_error",
+            "cfust_surrogate_create", "cfust_surrogate_destroy", "cfust_surrogate_label",
+            "cfust_surrogate_predict", "cfust_surrogate_gradient", "cfust_surrogate_get_params",
+            "cfust_surrogate_set_params", "cfust_surrogate_train", "cfust_surrogate_last_error",
+            "cfust_set_surrogate", "cfust_last_fallback"]
+
+SURROGATE_NPARAM = 35338
 
 
 class CfustError(RuntimeError):
@@ -86,6 +92,21 @@ def load(build_if_missing: bool = True, path: str | None = None) -> ctypes.CDLL:
         "cfust_normal_f32": ([vp, vp, i64, ctypes.c_int, vp], ctypes.c_int),
         "cfust_mstep_noalloc": ([ctypes.c_int, vp, i64, vp, vp, vp, vp, vp, ctypes.c_double,
                                  ctypes.c_double, P, vp], ctypes.c_int),
+        "cfust_surrogate_create": ([ctypes.POINTER(vp), ctypes.c_uint64, ctypes.POINTER(cfust_lattice), vp],
+                                   ctypes.c_int),
+        "cfust_surrogate_destroy": ([vp], ctypes.c_int),
+        "cfust_surrogate_label": ([vp, vp, vp, i64], ctypes.c_int),
+        "cfust_surrogate_predict": ([vp, vp, vp, i64], ctypes.c_int),
+        "cfust_surrogate_gradient": ([vp, vp, vp, i64, dp, ctypes.POINTER(ctypes.c_float)], ctypes.c_int),
+        "cfust_surrogate_get_params": ([vp, ctypes.POINTER(ctypes.c_float), ctypes.POINTER(ctypes.c_float)],
+                                       ctypes.c_int),
+        "cfust_surrogate_set_params": ([vp, ctypes.POINTER(ctypes.c_float), ctypes.POINTER(ctypes.c_float)],
+                                       ctypes.c_int),
+        "cfust_surrogate_train": ([vp, i64, ctypes.c_int, ctypes.c_int, ctypes.c_float, ctypes.c_uint64,
+                                   ctypes.POINTER(ctypes.c_float)], ctypes.c_int),
+        "cfust_surrogate_last_error": ([vp], ctypes.c_char_p),
+        "cfust_set_surrogate": ([vp, vp], ctypes.c_int),
+        "cfust_last_fallback": ([vp, ctypes.POINTER(i64)], ctypes.c_int),
     }
     for name, (args, res) in sig.items():
         fn = getattr(lib, name)
@@ -270,6 +291,92 @@ class Context:
         v = ctypes.c_int64()
         self._check(self.lib.cfust_last_rescued(self.h, ctypes.byref(v)))
         return v.value
+
+    def cfust_set_surrogate(self, sur):
+        """Attach a Surrogate (None detaches); the context keeps a reference."""
+        self._sur = sur
+        self._check(self.lib.cfust_set_surrogate(self.h, None if sur is None else sur.h))
+
+    def cfust_last_fallback(self) -> int:
+        v = ctypes.c_int64()
+        self._check(self.lib.cfust_last_fallback(self.h, ctypes.byref(v)))
+        return v.value
+
+
+class Surrogate:
+    """A cfust_surrogate (learned form of the r = 3 lattice integrals)."""
+
+    def __init__(self, lattice, seed=0, stream=None):
+        import torch
+        self.lib = load()
+        self._z = np.ascontiguousarray(lattice.z, dtype=np.int64)
+        self._shift = np.ascontiguousarray(lattice.shift, dtype=np.float64)
+        lat = cfust_lattice(int(lattice.n), int(self._z.shape[0]),
+                            self._z.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)),
+                            self._shift.ctypes.data_as(ctypes.POINTER(ctypes.c_double)))
+        self.stream = stream if stream is not None else torch.cuda.current_stream()
+        h = ctypes.c_void_p()
+        st = self.lib.cfust_surrogate_create(ctypes.byref(h), int(seed), ctypes.byref(lat),
+                                             ctypes.c_void_p(self.stream.cuda_stream))
+        if st != 0:
+            raise CfustError(st, self.lib.cfust_surrogate_last_error(None).decode())
+        self.h = h
+
+    def _check(self, st):
+        if st != 0:
+            raise CfustError(st, self.lib.cfust_surrogate_last_error(self.h).decode())
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.lib.cfust_surrogate_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _out(self, x, cols):
+        import torch
+        return torch.empty((x.shape[0], cols), dtype=torch.float32, device=x.device)
+
+    def cfust_surrogate_label(self, x):
+        y = self._out(x, 10)
+        self._check(self.lib.cfust_surrogate_label(self.h, _ptr(x), _ptr(y), x.shape[0]))
+        return y
+
+    def cfust_surrogate_predict(self, x):
+        y = self._out(x, 10)
+        self._check(self.lib.cfust_surrogate_predict(self.h, _ptr(x), _ptr(y), x.shape[0]))
+        return y
+
+    def cfust_surrogate_gradient(self, x, y):
+        loss = ctypes.c_double()
+        g = np.zeros(SURROGATE_NPARAM, dtype=np.float32)
+        self._check(self.lib.cfust_surrogate_gradient(self.h, _ptr(x), _ptr(y), x.shape[0], ctypes.byref(loss),
+                                                      g.ctypes.data_as(ctypes.POINTER(ctypes.c_float))))
+        return loss.value, g
+
+    def cfust_surrogate_get_params(self):
+        th = np.zeros(SURROGATE_NPARAM, dtype=np.float32)
+        nm = np.zeros(20, dtype=np.float32)
+        fp = ctypes.POINTER(ctypes.c_float)
+        self._check(self.lib.cfust_surrogate_get_params(self.h, th.ctypes.data_as(fp), nm.ctypes.data_as(fp)))
+        return th, nm
+
+    def cfust_surrogate_set_params(self, theta, norm=None):
+        th = np.ascontiguousarray(theta, dtype=np.float32)
+        fp = ctypes.POINTER(ctypes.c_float)
+        nm = None if norm is None else np.ascontiguousarray(norm, dtype=np.float32)
+        self._check(self.lib.cfust_surrogate_set_params(self.h, th.ctypes.data_as(fp),
+                                                        None if nm is None else nm.ctypes.data_as(fp)))
+
+    def cfust_surrogate_train(self, n_train, epochs, batch=4096, lr=2e-3, seed=1):
+        trace = np.zeros(epochs, dtype=np.float32)
+        self._check(self.lib.cfust_surrogate_train(self.h, int(n_train), int(epochs), int(batch), float(lr),
+                                                   int(seed), trace.ctypes.data_as(ctypes.POINTER(ctypes.c_float))))
+        return trace
 
 
 def cfust_normal_f32(x, which, stream=None):

@@ -19,11 +19,14 @@ INCLUDE = os.path.join(ROOT, "include")
 LIBDIR = os.path.join(PKG, "_lib")
 LIB = os.path.join(LIBDIR, "libcfust.so")
 
-SOURCES = ["api.cu", "precompute.cu", "estep.cu", "mstep.cu"]
+SOURCES = ["api.cu", "precompute.cu", "estep.cu", "mstep.cu", "surrogate.cu"]
 HEADERS = ["cfust_internal.cuh", "special.cuh", "normal_f32.cuh", "normal_f32_coeffs.cuh"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr",
          "-I", INCLUDE, "-I", CSRC]
+# the sweep unit instantiates some seventy kernels: let nvcc optimise them in
+# parallel over the host cores (each kernel is compiled on its own either way)
+PER_SOURCE = {"estep.cu": ["--split-compile=0"]}
 
 
 def nvcc() -> str:
@@ -40,7 +43,7 @@ def _stamp(extra: list[str]) -> str:
             h.update(name.encode() + f.read())
     with open(os.path.join(INCLUDE, "cfust.h"), "rb") as f:
         h.update(f.read())
-    h.update(" ".join(ARCH + FLAGS + extra).encode())
+    h.update(" ".join(ARCH + FLAGS + extra + [str(PER_SOURCE)]).encode())
     h.update(os.uname().machine.encode())
     return h.hexdigest()
 
@@ -59,7 +62,7 @@ def build(force: bool = False, verbose: bool = False, extra: list[str] | None = 
 
     def compile_one(src):
         obj = os.path.join(LIBDIR, src.replace(".cu", ".o"))
-        cmd = [cc, *ARCH, *FLAGS, *extra, "-c", os.path.join(CSRC, src), "-o", obj]
+        cmd = [cc, *ARCH, *FLAGS, *PER_SOURCE.get(src, []), *extra, "-c", os.path.join(CSRC, src), "-o", obj]
         res = subprocess.run(cmd, capture_output=True, text=True)
         if res.returncode != 0:
             raise RuntimeError(f"nvcc failed on {src}:\n{res.stdout}\n{res.stderr}")

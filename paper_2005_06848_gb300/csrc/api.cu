@@ -72,6 +72,12 @@ struct cfust_ctx {
     cudaGraphExec_t graph = nullptr;
   } batch;
 
+  // learned surrogate E-step (not owned) and its fallback lists
+  cfust_surrogate *sur = nullptr;
+  int *d_fb = nullptr;           // [g][n] observations left to the lattice rule
+  unsigned *d_fb_cnt = nullptr;  // [g]
+  int64_t fb_cap = 0;
+
   // stepwise fit state
   const double *fit_Y = nullptr;
   int64_t fit_n = 0;
@@ -145,6 +151,7 @@ cfust_status ensure(cfust_ctx *c, int g, int p, int r, int64_t n) {
     c->r = r;
     c->n_cap = 0;
     c->nb_cap = 0;
+    c->fb_cap = 0;
   }
   if (!c->d_status) {
     CF_CUDA(c, cudaMalloc(&c->d_status, 2 * sizeof(int)));
@@ -171,6 +178,13 @@ cfust_status ensure(cfust_ctx *c, int g, int p, int r, int64_t n) {
     CF_CUDA(c, realloc_dev(&c->d_e3, es * gn * r));
     CF_CUDA(c, realloc_dev(&c->d_e4, es * gn * rp));
     c->n_cap = n;
+  }
+  if (c->sur && (n > c->fb_cap || !c->d_fb_cnt)) {
+    drop_graph(c);
+    CF_CUDA(c, realloc_dev(&c->d_fb, sizeof(int) * (size_t)g * (size_t)n));
+    CF_CUDA(c, realloc_dev(&c->d_fb_cnt, sizeof(unsigned) * CFUST_GMAX));
+    CF_CUDA(c, cudaMemset(c->d_fb_cnt, 0, sizeof(unsigned) * CFUST_GMAX));
+    c->fb_cap = n;
   }
   return CFUST_OK;
 }
@@ -314,16 +328,38 @@ SweepTiming sweep_timing(cfust_ctx *c, bool capturing) {
   return tm;
 }
 
+// The E-step sweep for all pairs: the lattice rule, or with a surrogate
+// attached the network for in-domain pairs and the lattice rule for the list
+// of the others.  The timing events bracket the dominant kernel.
+cfust_status run_estep(cfust_ctx *c, const double *Y, int64_t n, EstepOut o, bool density_only,
+                       cudaStream_t st, SweepTiming tm, int triage) {
+  const double *pi = param_view(c->d_params, c->g, c->p, c->r).pi;
+  if (!c->sur) {
+    CF_CUDA(c, launch_estep(c->opts.precision, Y, n, c->g, c->p, c->r, c->lat, c->d_c64, c->d_c32,
+                            c->d_chi64, c->d_chi32, o, density_only, c->opts.e2_mode, c->d_rescue,
+                            c->d_rescue_cnt, c->d_status, c->opts.pairs_per_warp, st, tm, triage, pi));
+    return CFUST_OK;
+  }
+  if (c->opts.precision != CFUST_FP32 || c->opts.e2_mode != 0 || c->r != 3)
+    return fail(c, CFUST_EINVAL, "the surrogate E-step needs CFUST_FP32, e2_mode 0 and r = 3");
+  const unsigned evflag = tm.capturing ? cudaEventRecordExternal : cudaEventRecordDefault;
+  if (tm.start) CF_CUDA(c, cudaEventRecordWithFlags(tm.start, st, evflag));
+  CF_CUDA(c, launch_surrogate_estep(surrogate_dev(c->sur), Y, n, c->g, c->p, c->d_c32, o, density_only,
+                                    c->d_fb, c->d_fb_cnt, st));
+  if (tm.stop) CF_CUDA(c, cudaEventRecordWithFlags(tm.stop, st, evflag));
+  CF_CUDA(c, launch_estep_list(Y, n, c->g, c->p, c->r, c->lat, c->d_c64, c->d_c32, c->d_chi64, c->d_chi32, o,
+                               density_only, c->opts.e2_mode, c->d_fb, c->d_fb_cnt, c->d_rescue,
+                               c->d_rescue_cnt, c->d_status, st, triage, pi));
+  return CFUST_OK;
+}
+
 // One EM iteration on the stream: E-step at the device parameters (yielding
 // their log-likelihood into trace[iter]), then the M-step in place.
 cfust_status enqueue_iteration(cfust_ctx *c, const double *Y, int64_t n, cudaStream_t st) {
   CF_CUDA(c, launch_precompute(c->d_params, c->g, c->p, c->r, c->lat, c->d_c64, c->d_c32, c->d_chi64,
                                c->d_chi32, c->d_status, st));
-  CF_CUDA(c, launch_estep(c->opts.precision, Y, n, c->g, c->p, c->r, c->lat, c->d_c64, c->d_c32,
-                          c->d_chi64, c->d_chi32, ctx_out(c), false, c->opts.e2_mode,
-                          c->d_rescue, c->d_rescue_cnt, c->d_status, c->opts.pairs_per_warp, st,
-                          sweep_timing(c, st == c->cap_stream), 1,
-                          param_view(c->d_params, c->g, c->p, c->r).pi));
+  cfust_status s = run_estep(c, Y, n, ctx_out(c), false, st, sweep_timing(c, st == c->cap_stream), 1);
+  if (s != CFUST_OK) return s;
   PosteriorArgs a = post_args(c, Y, n);
   a.logf = c->d_logf;
   a.e1 = c->d_e1;
@@ -346,10 +382,8 @@ cfust_status enqueue_loglik(cfust_ctx *c, const double *Y, int64_t n, double *tr
                                c->d_chi32, c->d_status, c->stream));
   EstepOut o{};
   o.logf = c->d_logf;
-  CF_CUDA(c, launch_estep(c->opts.precision, Y, n, c->g, c->p, c->r, c->lat, c->d_c64, c->d_c32,
-                          c->d_chi64, c->d_chi32, o, true, c->opts.e2_mode,
-                          c->d_rescue, c->d_rescue_cnt, c->d_status, c->opts.pairs_per_warp, c->stream,
-                          sweep_timing(c, false), 1, param_view(c->d_params, c->g, c->p, c->r).pi));
+  cfust_status s = run_estep(c, Y, n, o, true, c->stream, sweep_timing(c, false), 1);
+  if (s != CFUST_OK) return s;
   PosteriorArgs a = post_args(c, Y, n);
   a.logf = c->d_logf;
   a.want_ll = true;
@@ -453,7 +487,7 @@ cfust_status cfust_destroy(cfust_ctx *c) {
     if (ev) cudaEventDestroy(ev);
   void *bufs[] = {c->d_params, c->d_c64, c->d_c32, c->d_chi64, c->d_chi32, c->d_status,
                   c->d_rescue_cnt, c->d_ll, c->d_trace, c->d_rescue, c->d_partials, c->d_llpart,
-                  c->d_logf, c->d_e1, c->d_e2, c->d_e3, c->d_e4};
+                  c->d_logf, c->d_e1, c->d_e2, c->d_e3, c->d_e4, c->d_fb, c->d_fb_cnt};
   for (void *b : bufs)
     if (b) cudaFree(b);
   delete c;
@@ -463,6 +497,27 @@ cfust_status cfust_destroy(cfust_ctx *c) {
 const char *cfust_last_error(cfust_ctx *c) {
   if (!c) return g_create_error.c_str();
   return c->err.c_str();
+}
+
+cfust_status cfust_set_surrogate(cfust_ctx *c, cfust_surrogate *s) {
+  if (!c) return CFUST_EINVAL;
+  DeviceGuard dg(c->device);
+  drop_graph(c);
+  c->sur = s;
+  c->fb_cap = 0;  // (re)allocated by the next call that knows n
+  return CFUST_OK;
+}
+
+cfust_status cfust_last_fallback(cfust_ctx *c, int64_t *count) {
+  if (!c || !count) return CFUST_EINVAL;
+  DeviceGuard dg(c->device);
+  *count = 0;
+  if (!c->sur || !c->d_fb_cnt || c->g < 1) return CFUST_OK;
+  unsigned v[CFUST_GMAX];
+  CF_CUDA(c, cudaMemcpyAsync(v, c->d_fb_cnt, sizeof(unsigned) * c->g, cudaMemcpyDeviceToHost, c->stream));
+  CF_CUDA(c, cudaStreamSynchronize(c->stream));
+  for (int i = 0; i < c->g; ++i) *count += v[i];
+  return CFUST_OK;
 }
 
 cfust_status cfust_last_rescued(cfust_ctx *c, int64_t *count) {
@@ -529,10 +584,7 @@ cfust_status cfust_estep(cfust_ctx *c, const double *Y, int64_t n, const cfust_p
   o.e2 = e2;
   o.e3 = e3;
   o.e4 = e4;
-  CF_CUDA(c, launch_estep(c->opts.precision, Y, n, c->g, c->p, c->r, c->lat, c->d_c64, c->d_c32,
-                          c->d_chi64, c->d_chi32, o, false, c->opts.e2_mode,
-                          c->d_rescue, c->d_rescue_cnt, c->d_status, c->opts.pairs_per_warp, c->stream,
-                          sweep_timing(c, false)));
+  if ((s = run_estep(c, Y, n, o, false, c->stream, sweep_timing(c, false), 0)) != CFUST_OK) return s;
   PosteriorArgs a = post_args(c, Y, n);
   a.logf = o.logf;
   a.tau_out = tau;

@@ -116,6 +116,36 @@ cudaError_t launch_estep(int precision, const double *Y, int64_t n, int g, int p
                          int pairs_per_warp, cudaStream_t st, SweepTiming tm = SweepTiming(),
                          int triage = 0, const double *d_pi = nullptr);
 
+// FP32 lattice sweep (r = 3 only) of the observations listed per component:
+// list[i * n + k], k < count[i] (device counts), followed by the rescue pass.
+// Serves the pairs a surrogate E-step leaves to the lattice rule.
+cudaError_t launch_estep_list(const double *Y, int64_t n, int g, int p, int r, const LatticeDev &lat,
+                              const CompT<double> *c64, const CompT<float> *c32, const double *chi64,
+                              const float *chi32, EstepOut out, bool density_only, int e2_mode,
+                              const int *list, const unsigned *count, unsigned long long *rescue_list,
+                              unsigned *rescue_count, int *d_status, cudaStream_t st, int triage,
+                              const double *d_pi);
+
+// Device view of a trained surrogate network (owned by cfust_surrogate):
+// packed BF16 weights W1 [16][128], W2, W3 [128][128], W4 [128][16] (input x
+// output, zero padded), FP32 biases and the 20 target-normalisation values.
+struct SurrogateDev {
+  const void *W1, *W2, *W3, *W4;
+  const float *b1, *b2, *b3, *b4;
+  const float *norm;
+};
+
+SurrogateDev surrogate_dev(const cfust_surrogate *s);
+
+// Surrogate E-step (FP32 outputs, r = 3): for every pair whose standardised
+// problem lies in the training domain the network gives log T_A, T_B and the
+// pass-B moments, from which log f and e1..e4 are formed as in the lattice
+// sweep; other pairs are appended to fb_list[i * n + k] / fb_count[i] (both
+// zeroed here first) for launch_estep_list.
+cudaError_t launch_surrogate_estep(const SurrogateDev &sd, const double *Y, int64_t n, int g, int p,
+                                   const CompT<float> *c32, EstepOut out, bool density_only, int *fb_list,
+                                   unsigned *fb_count, cudaStream_t st);
+
 // Elementwise single-precision normal functions (see cfust_normal_f32).
 cudaError_t launch_normal_f32(const float *x, float *out, int64_t n, int which, cudaStream_t st);
 

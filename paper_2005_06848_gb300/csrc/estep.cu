@@ -503,15 +503,17 @@ __device__ __forceinline__ void sweep_warp_pairs(const EArgs &a, const FitView &
 #define CFUST_ESTEP_MINB 2
 #endif
 
-template <typename T, int R, bool DENS>
-__global__ void __launch_bounds__(256, sizeof(T) == 4 ? CFUST_ESTEP_MINB : 1) estep_kernel(EArgs a) {
-  extern __shared__ __align__(128) unsigned char smem[];
-  const int i = blockIdx.y;
+// Stages component i's chi tables (bulk async copy, bounded mbarrier wait),
+// its constants and the paired single-precision factors into shared memory.
+// Returns false, after flagging ERR_TIMEOUT, when the copy did not land.
+template <typename T, bool DENS>
+__device__ __forceinline__ bool stage_block(const EArgs &a, int i, unsigned char *smem, const T *&tA,
+                                            const T *&tB, CompT<T> *&cs, PairedConsts *&pcs) {
   const int N = a.N;
   const size_t tab_bytes = a.staged ? (size_t)(DENS ? 1 : 2) * N * sizeof(T) : 0;
   T *tab = reinterpret_cast<T *>(smem);
-  CompT<T> *cs = reinterpret_cast<CompT<T> *>(smem + align16(tab_bytes));
-  PairedConsts *pcs = reinterpret_cast<PairedConsts *>(smem + align16(tab_bytes) + align16(sizeof(CompT<T>)));
+  cs = reinterpret_cast<CompT<T> *>(smem + align16(tab_bytes));
+  pcs = reinterpret_cast<PairedConsts *>(smem + align16(tab_bytes) + align16(sizeof(CompT<T>)));
   uint64_t *bar = reinterpret_cast<uint64_t *>(smem + align16(tab_bytes) + align16(sizeof(CompT<T>)) +
                                                align16(sizeof(PairedConsts)));
   const T *gtab = reinterpret_cast<const T *>(a.chi) + (int64_t)i * 2 * N;
@@ -540,15 +542,93 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? CFUST_ESTEP_MINB : 1) es
   if (a.staged) {
     if (!mbar_wait_bounded(bar, 0, 1 << 22)) {
       if (threadIdx.x == 0) atomicOr(a.status, ERR_TIMEOUT);
-      return;
+      return false;
     }
   }
-  const T *tA = a.staged ? tab : gtab;
-  const T *tB = tA + N;
+  tA = a.staged ? tab : gtab;
+  tB = tA + N;
+  return true;
+}
 
+template <typename T, int R, bool DENS>
+__global__ void __launch_bounds__(256, sizeof(T) == 4 ? CFUST_ESTEP_MINB : 1) estep_kernel(EArgs a) {
+  extern __shared__ __align__(128) unsigned char smem[];
+  const int i = blockIdx.y;
+  const T *tA, *tB;
+  CompT<T> *cs;
+  PairedConsts *pcs;
+  if (!stage_block<T, DENS>(a, i, smem, tA, tB, cs, pcs)) return;
   const int warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
   const int64_t jw0 = ((int64_t)blockIdx.x * nw + warp) * a.ppw;
   sweep_warp_pairs<T, R, DENS>(a, fit_view(a), *cs, pcs, tA, tB, i, i, jw0, a.ppw);
+}
+
+// Triage of a listed pair (single precision outputs): with log f of every
+// component of observation j in place (values, or upper bounds for pairs still
+// to be swept, +inf where none is known), a pair whose log pi_i + log f_ij
+// trails the best component by more than 30 has tau_ij < exp(-30); it gets
+// log f = -inf and zero expectations instead of a sweep.
+template <int R, bool DENS>
+__device__ bool triage_listed(const FitView &fv, int i, int64_t j) {
+  const float *lf = reinterpret_cast<const float *>(fv.out.logf);
+  float best = -INFINITY;
+  for (int h = 0; h < fv.g; ++h) best = fmaxf(best, logf((float)fv.pi[h]) + lf[(int64_t)h * fv.n + j]);
+  const float mine = logf((float)fv.pi[i]) + lf[(int64_t)i * fv.n + j];
+  if (!(isfinite(best) && mine < best - 30.0f)) return false;
+  const int64_t ij = (int64_t)i * fv.n + j;
+  constexpr int RP = R * (R + 1) / 2;
+  store<float>(fv.out.logf, ij, -INFINITY);
+  if (!DENS) {
+    store<float>(fv.out.e1, ij, 0.0);
+    store<float>(fv.out.e2, ij, 0.0);
+    for (int t = 0; t < R; ++t) store<float>(fv.out.e3, ((int64_t)i * R + t) * fv.n + j, 0.0);
+    for (int t = 0; t < RP; ++t) store<float>(fv.out.e4, ((int64_t)i * RP + t) * fv.n + j, 0.0);
+  }
+  return true;
+}
+
+// The same sweep over an explicit list of observations per component:
+// list[i * stride + k] for k < count[i] (the pairs a surrogate E-step leaves
+// to the lattice rule).  Warps stride over the list in chunks of ppw.
+template <typename T, int R, bool DENS>
+__global__ void __launch_bounds__(256, sizeof(T) == 4 ? CFUST_ESTEP_MINB : 1)
+    estep_list_kernel(EArgs a, const int *list, const unsigned *count, int64_t stride) {
+  extern __shared__ __align__(128) unsigned char smem[];
+  const int i = blockIdx.y;
+  const int64_t cnt = count[i];
+  const int warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  if ((int64_t)blockIdx.x * nw * a.ppw >= cnt) return;  // uniform over the block
+  const T *tA, *tB;
+  CompT<T> *cs;
+  PairedConsts *pcs;
+  if (!stage_block<T, DENS>(a, i, smem, tA, tB, cs, pcs)) return;
+  const FitView fv = fit_view(a);
+  const int *li = list + (int64_t)i * stride;
+  const int lane = threadIdx.x & 31;
+  const bool check = (sizeof(T) == 4);
+  for (int64_t base = ((int64_t)blockIdx.x * nw + warp) * a.ppw; base < cnt;
+       base += (int64_t)gridDim.x * nw * a.ppw) {
+    const int m = (int)((cnt - base) < a.ppw ? (cnt - base) : a.ppw);
+    Prologue<R> mine;
+    int64_t myj = 0;
+    bool myskip = false;
+    if (lane < m) {
+      myj = li[base + lane];
+      if (a.triage) myskip = triage_listed<R, DENS>(fv, i, myj);
+      if (!myskip) mine = prologue<T, R>(a, fv, *cs, myj);
+    }
+    const unsigned skipped = __ballot_sync(0xffffffffu, myskip);
+    for (int b = 0; b < m; ++b) {
+      if ((skipped >> b) & 1u) continue;
+      const Prologue<R> pr = shfl_prologue<R>(mine, b);
+      const int64_t j = __shfl_sync(0xffffffffu, myj, b);
+      const bool need = pair_sweep<T, T, R, DENS>(a, fv, *cs, pr, tA, tB, i, j, lane, check, pcs);
+      if (need && lane == 0) {
+        const unsigned slot = atomicAdd(a.rescue_count, 1u);
+        a.rescue_list[slot] = pair_id(i, j);
+      }
+    }
+  }
 }
 
 // One coordinate of the log-domain sweep: log p for p = Phi(-lim) and the
@@ -1093,13 +1173,34 @@ cudaError_t launch_estep_batched(int precision, const BatchDev &b, int p, int r,
              : dispatch_batched<float, false>(r, a, b, items, nitems, item_counter, ctas_per_sm, st, true, c64, chi64, tm);
 }
 
-cudaError_t launch_estep(int precision, const double *Y, int64_t n, int g, int p, int r,
-                         const LatticeDev &lat, const CompT<double> *c64, const CompT<float> *c32,
-                         const double *chi64, const float *chi32, EstepOut out, bool density_only,
-                         int e2_mode, unsigned long long *rescue_list, unsigned *rescue_count, int *d_status,
-                         int pairs_per_warp, cudaStream_t st, SweepTiming tm, int triage,
-                         const double *d_pi) {
-  if (n <= 0) return cudaSuccess;
+template <bool DENS>
+cudaError_t launch_list_r3(EArgs a, int g, int64_t n, const int *list, const unsigned *count,
+                           const CompT<double> *c64, const double *chi64, cudaStream_t st) {
+  const size_t tab_bytes = (size_t)(DENS ? 1 : 2) * a.N * sizeof(float);
+  a.staged = tab_bytes <= 160u * 1024u ? 1 : 0;
+  const size_t smem = (a.staged ? align16(tab_bytes) : 0) + align16(sizeof(CompT<float>)) +
+                      align16(sizeof(PairedConsts)) + 16;
+  cudaError_t e = cudaFuncSetAttribute(estep_list_kernel<float, 3, DENS>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  a.ppw = 4;
+  // the list lengths live on the device: size the grid for a full list but
+  // cap it near four waves of two CTAs per SM; blocks past the end return
+  const int64_t need = (n + 8 * a.ppw - 1) / (8 * a.ppw);
+  const int64_t cap = (152 * 2 * 4 + g - 1) / g;
+  const int64_t bx = need < cap ? need : cap;
+  e = cudaMemsetAsync(a.rescue_count, 0, sizeof(unsigned), st);
+  if (e != cudaSuccess) return e;
+  estep_list_kernel<float, 3, DENS><<<dim3((unsigned)(bx < 1 ? 1 : bx), g), 256, smem, st>>>(a, list, count, n);
+  e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  rescue_kernel<3, DENS><<<152 * 4, 256, 0, st>>>(a, c64, chi64);
+  return cudaGetLastError();
+}
+
+EArgs make_args(const double *Y, int64_t n, int g, int p, const LatticeDev &lat, EstepOut out, int e2_mode,
+                unsigned long long *rescue_list, unsigned *rescue_count, int *d_status, int triage,
+                const double *d_pi) {
   EArgs a;
   a.Y = Y;
   a.n = n;
@@ -1117,6 +1218,41 @@ cudaError_t launch_estep(int precision, const double *Y, int64_t n, int g, int p
   }
   a.out = out;
   a.e2_mode = e2_mode;
+  a.ppw = 1;
+  a.staged = 1;
+  a.rescue_list = rescue_list;
+  a.rescue_count = rescue_count;
+  a.status = d_status;
+  a.triage = (triage && out.logf != nullptr) ? 1 : 0;
+  a.pi = d_pi;
+  a.comp = nullptr;
+  a.chi = nullptr;
+  return a;
+}
+
+cudaError_t launch_estep_list(const double *Y, int64_t n, int g, int p, int r, const LatticeDev &lat,
+                              const CompT<double> *c64, const CompT<float> *c32, const double *chi64,
+                              const float *chi32, EstepOut out, bool density_only, int e2_mode,
+                              const int *list, const unsigned *count, unsigned long long *rescue_list,
+                              unsigned *rescue_count, int *d_status, cudaStream_t st, int triage,
+                              const double *d_pi) {
+  if (n <= 0) return cudaSuccess;
+  if (r != 3) return cudaErrorInvalidValue;
+  EArgs a = make_args(Y, n, g, p, lat, out, e2_mode, rescue_list, rescue_count, d_status, triage, d_pi);
+  a.comp = c32;
+  a.chi = chi32;
+  return density_only ? launch_list_r3<true>(a, g, n, list, count, c64, chi64, st)
+                      : launch_list_r3<false>(a, g, n, list, count, c64, chi64, st);
+}
+
+cudaError_t launch_estep(int precision, const double *Y, int64_t n, int g, int p, int r,
+                         const LatticeDev &lat, const CompT<double> *c64, const CompT<float> *c32,
+                         const double *chi64, const float *chi32, EstepOut out, bool density_only,
+                         int e2_mode, unsigned long long *rescue_list, unsigned *rescue_count, int *d_status,
+                         int pairs_per_warp, cudaStream_t st, SweepTiming tm, int triage,
+                         const double *d_pi) {
+  if (n <= 0) return cudaSuccess;
+  EArgs a = make_args(Y, n, g, p, lat, out, e2_mode, rescue_list, rescue_count, d_status, triage, d_pi);
   if (pairs_per_warp <= 0) {
     // about sixteen waves of two resident CTAs per SM (8 warps each), so the
     // last wave's imbalance stays small; 1..32 pairs per warp (measured best
@@ -1126,12 +1262,6 @@ cudaError_t launch_estep(int precision, const double *Y, int64_t n, int g, int p
     pairs_per_warp = (int)(ppw < 1 ? 1 : (ppw > 32 ? 32 : ppw));
   }
   a.ppw = pairs_per_warp > 32 ? 32 : pairs_per_warp;
-  a.staged = 1;
-  a.rescue_list = rescue_list;
-  a.rescue_count = rescue_count;
-  a.status = d_status;
-  a.triage = (triage && out.logf != nullptr) ? 1 : 0;
-  a.pi = d_pi;
   if (precision == CFUST_FP64) {
     a.comp = c64;
     a.chi = chi64;

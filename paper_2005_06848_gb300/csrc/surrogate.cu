@@ -1,0 +1,1353 @@
+// Learned surrogate of the trivariate truncated-t integrals of the E-step.
+//
+// Problem: X ~ t_3(0, R, m), R a correlation matrix, truncation X > c.
+//   inputs  (7):  c_1, c_2, c_3, R_12, R_13, R_23, log m
+//   outputs (10): log P(X > c), E[X | X > c] (3), E[X X^T | X > c] upper
+//                 triangle (11, 12, 13, 22, 23, 33)
+// Network 7 -> 128 -> 128 -> 128 -> 10 with GELU (tanh form) after the hidden
+// layers; BF16 weights and activations, FP32 accumulation on the tensor cores
+// (mma.sync m16n8k16), FP32 master weights updated by Adam.  Inputs are
+// normalised as c and log m mapped from their ranges onto [-1, 1] and R/0.9.
+// The network predicts log(-log P), the first moments and the covariance
+// (second moments minus the products of the first moments), standardised by
+// per-output mean and standard deviation of the training labels.
+//
+// Labels come from the plain lattice evaluator (Genz separation of variables
+// on the shifted Korobov lattice) with chi-scale tables on a grid of 256
+// values of log m over [log 3, log 30]; the same evaluator judges the error.
+//
+// Training domain (and the E-step's test for using the network):
+// -8 <= c_t <= 4, |R_ht| <= 0.9, every squared Cholesky pivot of R >= 0.05,
+// m in [3, 30].
+#include <cuda_bf16.h>
+#include <math.h>
+#include <stdio.h>
+
+#include <cmath>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "cfust_internal.cuh"
+#include "normal_f32.cuh"
+#include "special.cuh"
+
+namespace cfust {
+namespace sg {
+
+constexpr int DIN = 7, DINP = 16, H = 128, DOUT = 10, DOUTP = 16;
+constexpr int NPARAM = DIN * H + H + 2 * (H * H + H) + H * DOUT + DOUT;  // 35338
+constexpr int MGRID = 256;
+constexpr float C_LO = -8.0f, C_HI = 4.0f, RHO_MAX = 0.9f, PIVOT_MIN = 0.05f;
+// added to the network's log T at a clamped truncation point to bound the
+// log T of a pair outside the box (network error and the lower clamp)
+constexpr float UB_MARGIN = 5.0f;
+// loss weight of log P (the moments weigh 1): the log-likelihood depends on it directly
+constexpr float LOSS_W0 = 4.0f;
+constexpr float CLAMP_LO_MIN_DOF = 8.0f;
+constexpr double LOGM_LO = 1.0986122886681098, LOGM_HI = 3.4011973816621555;  // log 3, log 30
+
+// offsets of the flat parameter vector (same order as the FP64 oracle)
+constexpr int OFF_W1 = 0, OFF_B1 = OFF_W1 + DIN * H, OFF_W2 = OFF_B1 + H, OFF_B2 = OFF_W2 + H * H,
+              OFF_W3 = OFF_B2 + H, OFF_B3 = OFF_W3 + H * H, OFF_W4 = OFF_B3 + H, OFF_B4 = OFF_W4 + H * DOUT;
+
+using bf16 = __nv_bfloat16;
+
+// ---------------------------------------------------------------------------
+// BF16 tensor-core GEMM, C[M x N] = A[M x K] B[K x N], FP32 accumulation.
+// A(m, k) = transA ? A[k lda + m] : A[m lda + k];  B(k, n) likewise.
+// Tile 128 x 128 x 32, 8 warps as 4 x 2, warp tile 32 x 64.
+// ---------------------------------------------------------------------------
+// Operand layouts must keep the contiguous index 16-byte aligned: lda, ldb
+// and the untransposed K multiples of 8 (every use here: 16 or 128).
+struct Gemm {
+  int M, N, K;
+  const bf16 *A;
+  int lda, transA;
+  const bf16 *B;
+  int ldb, transB;
+  int k_chunk;          // split-K: blockIdx.z covers [z k_chunk, (z + 1) k_chunk)
+  int mode;             // 0 split-K partial, 1 bias + GELU, 2 times GELU'(Zprev), 3 bias, fp32 out
+  const float *bias;
+  float *C;             // modes 0, 3
+  int ldc;
+  bf16 *Zout, *Hout;    // mode 1: Z and GELU(Z); mode 2: Hout receives the product
+  int ldo;
+  const bf16 *Zprev;    // mode 2
+};
+
+constexpr int BM = 128, BN = 128, BK = 32, PITCH = BK + 8;
+
+// GELU in its tanh form, the tanh from the hardware approximation
+// (tanh.approx.f32, relative error about 2^-11, below the BF16 rounding of
+// the activations); training and inference use the same function.
+__device__ __forceinline__ float tanh_approx(float x) {
+  float r;
+  asm("tanh.approx.f32 %0, %1;" : "=f"(r) : "f"(x));
+  return r;
+}
+__device__ __forceinline__ float gelu_f(float z) {
+  const float k = 0.7978845608028654f, a = 0.044715f;
+  const float t = tanh_approx(k * fmaf(a * z, z * z, z));
+  return 0.5f * z * (1.0f + t);
+}
+__device__ __forceinline__ float gelu_grad_f(float z) {
+  const float k = 0.7978845608028654f, a = 0.044715f;
+  const float t = tanh_approx(k * fmaf(a * z, z * z, z));
+  return 0.5f * (1.0f + t) + 0.5f * z * (1.0f - t * t) * k * (1.0f + 3.0f * a * z * z);
+}
+
+__device__ __forceinline__ void mma_bf16(float (&d)[4], const uint32_t (&a)[4], const uint32_t (&b)[2]) {
+  asm volatile(
+      "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
+      "{%0,%1,%2,%3};\n"
+      : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+      : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b[0]), "r"(b[1]));
+}
+
+__global__ void __launch_bounds__(256) gemm_kernel(Gemm g) {
+  __shared__ __align__(16) bf16 As[BM * PITCH];
+  __shared__ __align__(16) bf16 Bs[BN * PITCH];
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int wm = warp >> 1, wn = warp & 1;
+  const int gid = lane >> 2, tig = lane & 3;
+  const int m0 = blockIdx.x * BM, n0 = blockIdx.y * BN;
+  const int kb0 = blockIdx.z * g.k_chunk;
+  const int kb1 = min(g.K, kb0 + g.k_chunk);
+  float acc[2][8][4];
+#pragma unroll
+  for (int a = 0; a < 2; ++a)
+#pragma unroll
+    for (int b = 0; b < 8; ++b)
+#pragma unroll
+      for (int c = 0; c < 4; ++c) acc[a][b][c] = 0.f;
+  const bf16 zero = __float2bfloat16(0.f);
+  for (int k0 = kb0; k0 < kb1; k0 += BK) {
+    // A tile -> As[m][k] and B tile -> Bs[n][k], 16-byte global loads along
+    // the contiguous index (8 BF16), zeros outside the matrix
+    if (!g.transA) {
+      for (int v = tid; v < BM * (BK / 8); v += 256) {
+        const int mm = v / (BK / 8), kk = (v % (BK / 8)) * 8;
+        const int m = m0 + mm, k = k0 + kk;
+        uint4 val = make_uint4(0u, 0u, 0u, 0u);
+        if (m < g.M && k + 8 <= kb1) val = *reinterpret_cast<const uint4 *>(g.A + (int64_t)m * g.lda + k);
+        *reinterpret_cast<uint4 *>(&As[mm * PITCH + kk]) = val;
+      }
+    } else {
+      for (int v = tid; v < BK * (BM / 8); v += 256) {
+        const int kk = v / (BM / 8), mm = (v % (BM / 8)) * 8;
+        const int m = m0 + mm, k = k0 + kk;
+        bf16 e[8];
+        if (k < kb1 && m + 8 <= g.M) {
+          *reinterpret_cast<uint4 *>(e) = *reinterpret_cast<const uint4 *>(g.A + (int64_t)k * g.lda + m);
+        } else {
+#pragma unroll
+          for (int q = 0; q < 8; ++q) e[q] = (k < kb1 && m + q < g.M) ? g.A[(int64_t)k * g.lda + m + q] : zero;
+        }
+#pragma unroll
+        for (int q = 0; q < 8; ++q) As[(mm + q) * PITCH + kk] = e[q];
+      }
+    }
+    if (!g.transB) {
+      for (int v = tid; v < BK * (BN / 8); v += 256) {
+        const int kk = v / (BN / 8), nn = (v % (BN / 8)) * 8;
+        const int n = n0 + nn, k = k0 + kk;
+        bf16 e[8];
+        if (k < kb1 && n + 8 <= g.N) {
+          *reinterpret_cast<uint4 *>(e) = *reinterpret_cast<const uint4 *>(g.B + (int64_t)k * g.ldb + n);
+        } else {
+#pragma unroll
+          for (int q = 0; q < 8; ++q) e[q] = (k < kb1 && n + q < g.N) ? g.B[(int64_t)k * g.ldb + n + q] : zero;
+        }
+#pragma unroll
+        for (int q = 0; q < 8; ++q) Bs[(nn + q) * PITCH + kk] = e[q];
+      }
+    } else {
+      for (int v = tid; v < BN * (BK / 8); v += 256) {
+        const int nn = v / (BK / 8), kk = (v % (BK / 8)) * 8;
+        const int n = n0 + nn, k = k0 + kk;
+        uint4 val = make_uint4(0u, 0u, 0u, 0u);
+        if (n < g.N && k + 8 <= kb1) val = *reinterpret_cast<const uint4 *>(g.B + (int64_t)n * g.ldb + k);
+        *reinterpret_cast<uint4 *>(&Bs[nn * PITCH + kk]) = val;
+      }
+    }
+    __syncthreads();
+#pragma unroll
+    for (int ks = 0; ks < BK; ks += 16) {
+      uint32_t af[2][4], bfr[8][2];
+#pragma unroll
+      for (int mi = 0; mi < 2; ++mi) {
+        const int rb = wm * 32 + mi * 16;
+        af[mi][0] = *reinterpret_cast<const uint32_t *>(&As[(rb + gid) * PITCH + ks + tig * 2]);
+        af[mi][1] = *reinterpret_cast<const uint32_t *>(&As[(rb + gid + 8) * PITCH + ks + tig * 2]);
+        af[mi][2] = *reinterpret_cast<const uint32_t *>(&As[(rb + gid) * PITCH + ks + 8 + tig * 2]);
+        af[mi][3] = *reinterpret_cast<const uint32_t *>(&As[(rb + gid + 8) * PITCH + ks + 8 + tig * 2]);
+      }
+#pragma unroll
+      for (int nj = 0; nj < 8; ++nj) {
+        const int nb = wn * 64 + nj * 8;
+        bfr[nj][0] = *reinterpret_cast<const uint32_t *>(&Bs[(nb + gid) * PITCH + ks + tig * 2]);
+        bfr[nj][1] = *reinterpret_cast<const uint32_t *>(&Bs[(nb + gid) * PITCH + ks + 8 + tig * 2]);
+      }
+#pragma unroll
+      for (int mi = 0; mi < 2; ++mi)
+#pragma unroll
+        for (int nj = 0; nj < 8; ++nj) mma_bf16(acc[mi][nj], af[mi], bfr[nj]);
+    }
+    __syncthreads();
+  }
+#pragma unroll
+  for (int mi = 0; mi < 2; ++mi)
+#pragma unroll
+    for (int nj = 0; nj < 8; ++nj)
+#pragma unroll
+      for (int c = 0; c < 4; ++c) {
+        const int m = m0 + wm * 32 + mi * 16 + gid + ((c >= 2) ? 8 : 0);
+        const int n = n0 + wn * 64 + nj * 8 + tig * 2 + (c & 1);
+        if (m >= g.M || n >= g.N) continue;
+        const float v = acc[mi][nj][c];
+        if (g.mode == 0) {
+          g.C[(int64_t)blockIdx.z * g.M * g.N + (int64_t)m * g.ldc + n] = v;
+        } else if (g.mode == 1) {
+          const float z = v + g.bias[n];
+          g.Zout[(int64_t)m * g.ldo + n] = __float2bfloat16(z);
+          g.Hout[(int64_t)m * g.ldo + n] = __float2bfloat16(gelu_f(z));
+        } else if (g.mode == 2) {
+          const float zp = __bfloat162float(g.Zprev[(int64_t)m * g.ldo + n]);
+          g.Hout[(int64_t)m * g.ldo + n] = __float2bfloat16(v * gelu_grad_f(zp));
+        } else {
+          g.C[(int64_t)m * g.ldc + n] = v + g.bias[n];
+        }
+      }
+}
+
+cudaError_t gemm(const Gemm &g, int splits, cudaStream_t st) {
+  dim3 grid((g.M + BM - 1) / BM, (g.N + BN - 1) / BN, splits);
+  gemm_kernel<<<grid, 256, 0, st>>>(g);
+  return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// small elementwise / reduction kernels
+// ---------------------------------------------------------------------------
+
+__device__ __forceinline__ void normalise_input(const float *x, float *u) {
+  for (int t = 0; t < 3; ++t) u[t] = (2.f * x[t] - (C_LO + C_HI)) / (C_HI - C_LO);
+  for (int t = 3; t < 6; ++t) u[t] = x[t] / RHO_MAX;
+  u[6] = (float)((2.0 * x[6] - (LOGM_LO + LOGM_HI)) / (LOGM_HI - LOGM_LO));
+}
+
+// outputs -> network targets: log P becomes log(-log P) (relative precision
+// for P near 1), second moments (upper order 00 01 02 11 12 22) become
+// covariances E[X_a X_b] - E[X_a] E[X_b]
+constexpr float NEGLOG_MIN = 1e-12f;
+__host__ __device__ __forceinline__ void to_net(const float *y, float *t) {
+  const int A[6] = {0, 0, 0, 1, 1, 2}, Bi[6] = {0, 1, 2, 1, 2, 2};
+  t[0] = logf(fmaxf(-y[0], NEGLOG_MIN));
+  for (int k = 1; k < 4; ++k) t[k] = y[k];
+  for (int k = 0; k < 6; ++k) t[4 + k] = y[4 + k] - y[1 + A[k]] * y[1 + Bi[k]];
+}
+__host__ __device__ __forceinline__ void from_net(const float *t, float *y) {
+  const int A[6] = {0, 0, 0, 1, 1, 2}, Bi[6] = {0, 1, 2, 1, 2, 2};
+  y[0] = -expf(t[0]);
+  for (int k = 1; k < 4; ++k) y[k] = t[k];
+  for (int k = 0; k < 6; ++k) y[4 + k] = t[4 + k] + t[1 + A[k]] * t[1 + Bi[k]];
+}
+
+// raw inputs [B][7] -> padded normalised BF16 [B][16]
+__global__ void prep_input_kernel(const float *x, bf16 *x0, int64_t B) {
+  const int64_t b = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (b >= B) return;
+  float u[DIN];
+  normalise_input(x + b * DIN, u);
+  for (int t = 0; t < DINP; ++t) x0[b * DINP + t] = __float2bfloat16(t < DIN ? u[t] : 0.f);
+}
+
+// loss partial per block and dZ4 = 2 (out - t) / (B * 10), t normalised targets
+__global__ void loss_kernel(const float *out, const float *y, const float *norm, bf16 *dz, double *loss_part,
+                            int64_t B) {
+  __shared__ double red[256];
+  double s = 0.0;
+  for (int64_t b = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; b < B; b += (int64_t)gridDim.x * blockDim.x) {
+    float t[DOUT];
+    to_net(y + b * DOUT, t);
+    for (int k = 0; k < DOUTP; ++k) {
+      float d = 0.f;
+      float wk = 0.f;
+      if (k < DOUT) {
+        const float tn = (t[k] - norm[k]) / norm[DOUT + k];
+        d = out[b * DOUTP + k] - tn;
+        wk = (k == 0) ? LOSS_W0 : 1.f;
+        s += (double)wk * d * d;
+      }
+      dz[b * DOUTP + k] = __float2bfloat16(2.0f * wk * d / (float)(B * DOUT));
+    }
+  }
+  red[threadIdx.x] = s;
+  __syncthreads();
+  for (int h = 128; h > 0; h >>= 1) {
+    if (threadIdx.x < h) red[threadIdx.x] += red[threadIdx.x + h];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) loss_part[blockIdx.x] = red[0];
+}
+
+// column sums of a BF16 [B][ld] matrix, columns < ncol, into grad[off + col]
+__global__ void colsum_kernel(const bf16 *dz, int ld, int ncol, int64_t B, float *grad, int off) {
+  const int col = blockIdx.x;
+  __shared__ float red[256];
+  float s = 0.f;
+  for (int64_t b = threadIdx.x; b < B; b += 256) s += __bfloat162float(dz[b * ld + col]);
+  red[threadIdx.x] = s;
+  __syncthreads();
+  for (int h = 128; h > 0; h >>= 1) {
+    if (threadIdx.x < h) red[threadIdx.x] += red[threadIdx.x + h];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0 && col < ncol) grad[off + col] = red[0];
+}
+
+// sum split-K partials [S][M][Np] (rows < mrows, cols < ncols) into grad[off + m ncols + n]
+__global__ void reduce_partials_kernel(const float *part, int S, int M, int Np, int mrows, int ncols, float *grad,
+                                       int off) {
+  const int idx = blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= mrows * ncols) return;
+  const int m = idx / ncols, n = idx % ncols;
+  float s = 0.f;
+  for (int z = 0; z < S; ++z) s += part[(int64_t)z * M * Np + (int64_t)m * Np + n];
+  grad[off + idx] = s;
+}
+
+__global__ void adam_kernel(float *theta, float *mom, float *vel, const float *grad, int n, float lr, float b1,
+                            float b2, float eps, float c1, float c2) {
+  const int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= n) return;
+  const float gk = grad[k];
+  const float mk = b1 * mom[k] + (1.f - b1) * gk;
+  const float vk = b2 * vel[k] + (1.f - b2) * gk * gk;
+  mom[k] = mk;
+  vel[k] = vk;
+  theta[k] -= lr * (mk / c1) / (sqrtf(vk / c2) + eps);
+}
+
+// flat FP32 parameters -> padded BF16 weights W1 [16][128], W2, W3 [128][128], W4 [128][16] and FP32 biases
+__global__ void pack_weights_kernel(const float *theta, bf16 *W1, bf16 *W2, bf16 *W3, bf16 *W4, float *b1,
+                                    float *b2, float *b3, float *b4) {
+  const int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k < DINP * H) {
+    const int i = k / H, o = k % H;
+    W1[k] = __float2bfloat16(i < DIN ? theta[OFF_W1 + i * H + o] : 0.f);
+  }
+  if (k < H * H) {
+    W2[k] = __float2bfloat16(theta[OFF_W2 + k]);
+    W3[k] = __float2bfloat16(theta[OFF_W3 + k]);
+  }
+  if (k < H * DOUTP) {
+    const int i = k / DOUTP, o = k % DOUTP;
+    W4[k] = __float2bfloat16(o < DOUT ? theta[OFF_W4 + i * DOUT + o] : 0.f);
+  }
+  if (k < H) {
+    b1[k] = theta[OFF_B1 + k];
+    b2[k] = theta[OFF_B2 + k];
+    b3[k] = theta[OFF_B3 + k];
+  }
+  if (k < DOUTP) b4[k] = (k < DOUT) ? theta[OFF_B4 + k] : 0.f;
+}
+
+// network output [B][16] (normalised covariance form) -> outputs [B][10]
+__global__ void denorm_kernel(const float *out, const float *norm, float *y, int64_t B) {
+  const int64_t b = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (b >= B) return;
+  float t[DOUT];
+  for (int k = 0; k < DOUT; ++k) t[k] = fmaf(out[b * DOUTP + k], norm[DOUT + k], norm[k]);
+  from_net(t, y + b * DOUT);
+}
+
+// chi-scale tables on the grid of m: [MGRID][N]
+__global__ void chi_grid_kernel(LatticeDev lat, float *tab) {
+  const int gidx = blockIdx.y;
+  const double m = exp(LOGM_LO + gidx * (LOGM_HI - LOGM_LO) / (MGRID - 1));
+  const int N = lat.n;
+  for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < N; k += gridDim.x * blockDim.x) {
+    const int64_t idx = ((int64_t)k * lat.z[0]) % N;
+    double u = (double)idx / (double)N + lat.shift[0];
+    if (u >= 1.0) u -= 1.0;
+    u = 1.0 - fabs(2.0 * u - 1.0);
+    u = fmin(fmax(u, 1.1102230246251565e-16), 1.0 - 1.1102230246251565e-16);
+    tab[(int64_t)gidx * N + k] = (float)sqrt(2.0 * inc_gamma_inv(0.5 * m, u) / m);
+  }
+}
+
+// One warp per sample: the lattice rule for P(X > c), E[X | X > c], E[X X^T | X > c]
+// with X = L V, V ~ t_3(0, I, m), m snapped to the chi-table grid.
+__global__ void __launch_bounds__(256) label_kernel(const float *x, float *y, int64_t B, LatticeDev lat,
+                                                    const float *tab) {
+  const int lane = threadIdx.x & 31;
+  const int64_t b = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+  if (b >= B) return;
+  const float *xb = x + b * DIN;
+  const float c[3] = {xb[0], xb[1], xb[2]};
+  const float r12 = xb[3], r13 = xb[4], r23 = xb[5];
+  // Cholesky of the correlation matrix
+  const float L00 = 1.f, L10 = r12, L20 = r13;
+  const float L11 = sqrtf(fmaxf(1.f - r12 * r12, 1e-12f));
+  const float L21 = (r23 - r13 * r12) / L11;
+  const float L22 = sqrtf(fmaxf(1.f - r13 * r13 - L21 * L21, 1e-12f));
+  const float Lm[3][3] = {{L00, 0.f, 0.f}, {L10, L11, 0.f}, {L20, L21, L22}};
+  const float Li[3] = {1.f, 1.f / L11, 1.f / L22};
+  // chi scale at this m: linear interpolation in log m between grid tables
+  float gpos = (float)((xb[6] - LOGM_LO) / (LOGM_HI - LOGM_LO) * (MGRID - 1));
+  gpos = fminf(fmaxf(gpos, 0.f), (float)(MGRID - 1));
+  const int gi = min((int)gpos, MGRID - 2);
+  const float gw = gpos - (float)gi;
+  const int N = lat.n;
+  const float *s_lo = tab + (int64_t)gi * N, *s_hi = s_lo + N;
+  float fm[3], fstep[3], two_sf[3], sf[3];
+  for (int t = 0; t < 3; ++t) {
+    const int m0 = (int)(((int64_t)lane * lat.z[t + 1] + lat.sint[t + 1]) % N);
+    fm[t] = (float)(2 * m0 - N);
+    fstep[t] = (float)(2 * lat.step[t + 1]);
+    two_sf[t] = (float)(2.0 * lat.sfrac[t + 1]);
+    sf[t] = (float)lat.sfrac[t + 1];
+  }
+  const float fN = (float)N, invN = 1.f / fN;
+  const float umin = 1.1102230246251565e-16f, umax = 1.f - 5.9604644775390625e-08f;
+  float W = 0.f, Q = 0.f, M1[3] = {0.f, 0.f, 0.f}, M2[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+  for (int k = lane; k < N; k += 32) {
+    float um[3], uu[3];
+    for (int t = 0; t < 3; ++t) {
+      const float mm = 0.5f * (fm[t] + fN);
+      um[t] = fminf(fmaxf(fabsf(fm[t] + two_sf[t]) * invN, umin), umax);
+      uu[t] = fmaxf(2.f * fminf(mm + sf[t], (fN - mm) - sf[t]) * invN, umin);
+      fm[t] += fstep[t];
+      if (fm[t] >= fN) fm[t] -= 2.f * fN;
+    }
+    const float s = fmaf(gw, s_hi[k] - s_lo[k], s_lo[k]);
+    // w = p_1 p_2 p_3 and 1 - w = q_1 + p_1 q_2 + p_1 p_2 q_3, both from the
+    // small sides, so log P keeps its precision where P is near 1
+    float w = 1.f, om = 0.f, z[3];
+    for (int t = 0; t < 3; ++t) {
+      float acc = c[t] * s;
+      for (int h = 0; h < t; ++h) acc -= Lm[t][h] * z[h];
+      float p, q;
+      phi_upper_pq_f32(acc * Li[t], p, q);
+      om = fmaf(w, q, om);
+      w *= p;
+      z[t] = neg_quantile_f32(um[t], uu[t], p, q);
+    }
+    Q += om;
+    const float is = 1.f / s;
+    float v[3];
+    for (int t = 0; t < 3; ++t) v[t] = z[t] * is;
+    W += w;
+    int q6 = 0;
+    for (int t = 0; t < 3; ++t) {
+      M1[t] += w * v[t];
+      for (int h = t; h < 3; ++h) M2[q6++] += w * v[t] * v[h];
+    }
+  }
+  for (int o = 16; o > 0; o >>= 1) {
+    W += __shfl_xor_sync(0xffffffffu, W, o);
+    Q += __shfl_xor_sync(0xffffffffu, Q, o);
+    for (int t = 0; t < 3; ++t) M1[t] += __shfl_xor_sync(0xffffffffu, M1[t], o);
+    for (int t = 0; t < 6; ++t) M2[t] += __shfl_xor_sync(0xffffffffu, M2[t], o);
+  }
+  if (lane != 0) return;
+  // E[V], E[V V^T] (symmetric, from the upper triangle) -> E[L V], L E[V V^T] L^T
+  const float iw = 1.f / W;
+  float EV[3], EVV[3][3];
+  int q6 = 0;
+  for (int t = 0; t < 3; ++t) EV[t] = M1[t] * iw;
+  for (int t = 0; t < 3; ++t)
+    for (int h = t; h < 3; ++h) {
+      EVV[t][h] = EVV[h][t] = M2[q6++] * iw;
+    }
+  float EX[3], EXX[3][3];
+  for (int t = 0; t < 3; ++t) {
+    EX[t] = 0.f;
+    for (int h = 0; h <= t; ++h) EX[t] += Lm[t][h] * EV[h];
+  }
+  for (int t = 0; t < 3; ++t)
+    for (int h = 0; h < 3; ++h) {
+      float s2 = 0.f;
+      for (int a = 0; a <= t; ++a)
+        for (int bb = 0; bb <= h; ++bb) s2 += Lm[t][a] * EVV[a][bb] * Lm[h][bb];
+      EXX[t][h] = s2;
+    }
+  float *yb = y + b * DOUT;
+  if (!(W > 0.f)) {  // every point weight underflowed: no label
+    for (int k = 0; k < DOUT; ++k) yb[k] = NAN;
+    return;
+  }
+  const float qn = Q / fN;
+  yb[0] = (qn < 0.5f) ? log1pf(-qn) : logf(W) - logf(fN);
+  yb[1] = EX[0];
+  yb[2] = EX[1];
+  yb[3] = EX[2];
+  yb[4] = EXX[0][0];
+  yb[5] = EXX[0][1];
+  yb[6] = EXX[0][2];
+  yb[7] = EXX[1][1];
+  yb[8] = EXX[1][2];
+  yb[9] = EXX[2][2];
+}
+
+// ---------------------------------------------------------------------------
+// Fused surrogate E-step.  A CTA holds the whole network in shared memory
+// (weights transposed to [out][in] for the B fragments) and runs two
+// independent 8-warp groups; each group takes tiles of 64 (i, j) pairs, i.e.
+// 128 network rows (pass A and pass B of every pair; 128 pairs and pass A
+// only for the density), and keeps the activations of its tile in shared
+// memory from the standardised inputs to the E-step outputs.
+// ---------------------------------------------------------------------------
+constexpr int TROWS = 128, HP = H + 8, XP = DINP + 8, OP = DOUTP + 1;
+constexpr int GROUP_THREADS = 256, GROUPS = 2;
+
+struct InferWeights {
+  bf16 W1t[H * XP];
+  bf16 W2t[H * HP];
+  bf16 W3t[H * HP];
+  bf16 W4t[DOUTP * HP];
+  float bias[3 * H + DOUTP];
+  float norm[2 * DOUT];
+};
+struct InferGroup {
+  bf16 X[TROWS * XP];
+  bf16 Hb[TROWS * HP];
+  float O[TROWS * OP];
+  float logt[TROWS], nud[TROWS], q[3 * TROWS];
+  int ok[TROWS];
+};
+constexpr size_t INFER_SMEM = sizeof(InferWeights) + GROUPS * sizeof(InferGroup);
+static_assert(sizeof(InferWeights) % 16 == 0, "group blocks must stay 16-byte aligned");
+static_assert(sizeof(InferGroup) % 16 == 0, "group blocks must stay 16-byte aligned");
+
+__device__ __forceinline__ void group_sync(int grp) {
+  asm volatile("bar.sync %0, %1;" ::"r"(grp + 1), "r"(GROUP_THREADS) : "memory");
+}
+
+__device__ __forceinline__ uint32_t ld32(const bf16 *p) { return *reinterpret_cast<const uint32_t *>(p); }
+
+// acc (32 x 64 tile of warp w: rows 32 (w >> 1), cols 64 (w & 1)) = A[128 x K] Wt^T
+template <int K>
+__device__ __forceinline__ void mma_32x64(const bf16 *A, int ap, const bf16 *Wt, int wp, int w, int lane,
+                                          float (&acc)[2][8][4]) {
+  const int wm = w >> 1, wn = w & 1, gid = lane >> 2, tig = lane & 3;
+#pragma unroll
+  for (int a = 0; a < 2; ++a)
+#pragma unroll
+    for (int b = 0; b < 8; ++b)
+#pragma unroll
+      for (int c = 0; c < 4; ++c) acc[a][b][c] = 0.f;
+#pragma unroll
+  for (int ks = 0; ks < K; ks += 16) {
+    uint32_t af[2][4], bfr[8][2];
+#pragma unroll
+    for (int mi = 0; mi < 2; ++mi) {
+      const bf16 *r0 = A + (wm * 32 + mi * 16 + gid) * ap + ks + tig * 2;
+      af[mi][0] = ld32(r0);
+      af[mi][1] = ld32(r0 + 8 * ap);
+      af[mi][2] = ld32(r0 + 8);
+      af[mi][3] = ld32(r0 + 8 * ap + 8);
+    }
+#pragma unroll
+    for (int nj = 0; nj < 8; ++nj) {
+      const bf16 *c0 = Wt + (wn * 64 + nj * 8 + gid) * wp + ks + tig * 2;
+      bfr[nj][0] = ld32(c0);
+      bfr[nj][1] = ld32(c0 + 8);
+    }
+#pragma unroll
+    for (int mi = 0; mi < 2; ++mi)
+#pragma unroll
+      for (int nj = 0; nj < 8; ++nj) mma_bf16(acc[mi][nj], af[mi], bfr[nj]);
+  }
+}
+
+// Hb[rows][cols of warp w] = GELU(acc + bias), BF16
+__device__ __forceinline__ void store_gelu(bf16 *Hb, const float *bias, int w, int lane,
+                                           const float (&acc)[2][8][4]) {
+  const int wm = w >> 1, wn = w & 1, gid = lane >> 2, tig = lane & 3;
+#pragma unroll
+  for (int mi = 0; mi < 2; ++mi)
+#pragma unroll
+    for (int nj = 0; nj < 8; ++nj) {
+      const int row = wm * 32 + mi * 16 + gid, col = wn * 64 + nj * 8 + tig * 2;
+      const float b0 = bias[col], b1 = bias[col + 1];
+      *reinterpret_cast<__nv_bfloat162 *>(Hb + row * HP + col) =
+          __floats2bfloat162_rn(gelu_f(acc[mi][nj][0] + b0), gelu_f(acc[mi][nj][1] + b1));
+      *reinterpret_cast<__nv_bfloat162 *>(Hb + (row + 8) * HP + col) =
+          __floats2bfloat162_rn(gelu_f(acc[mi][nj][2] + b0), gelu_f(acc[mi][nj][3] + b1));
+    }
+}
+
+// Standardised problem of one network row: pair (i, j), pass 0 (dof nu + p,
+// limits a_A) or 1 (nu + p + 2, a_B).  X = L V with L = chol(Lambda) is
+// t_3(0, Lambda, m); with D = diag(Lambda), X' = D^{-1/2} X is t_3(0, R, m)
+// and L V > a holds exactly when X' > c = D^{-1/2} a.
+struct RowProblem {
+  float c[3], R[3], logm;  // network input (c clamped into the box)
+  float logt, nud, q[3];
+  int kind;  // 2: the pair (both passes) lies in the training domain;
+             // 1: only its truncation point leaves the box (log T is bounded
+             //    through the clamped point); 0: R or the dof leave the domain
+};
+
+__device__ __forceinline__ RowProblem row_problem(const CompT<float> &c, const double *Y, int p, int64_t j,
+                                                  int pass) {
+  RowProblem rp;
+  const double *yj = Y + j * (int64_t)p;
+  float yc[PMAX];
+#pragma unroll
+  for (int k = 0; k < PMAX; ++k) yc[k] = (k < p) ? (float)(yj[k] - c.mu[k]) : 0.f;
+  float d = 0.f, q0 = 0.f, q1 = 0.f, q2 = 0.f;
+#pragma unroll
+  for (int k = 0; k < PMAX; ++k) {
+    if (k < p) {
+      float acc = 0.f;
+#pragma unroll
+      for (int l = 0; l <= k; ++l) acc = fmaf((float)c.A[k * PMAX + l], yc[l], acc);
+      d = fmaf(acc, acc, d);
+      q0 = fmaf((float)c.B[0 * PMAX + k], acc, q0);
+      q1 = fmaf((float)c.B[1 * PMAX + k], acc, q1);
+      q2 = fmaf((float)c.B[2 * PMAX + k], acc, q2);
+    }
+  }
+  const float nu = (float)c.nu, mA = (float)c.mA, mB = (float)c.mB;
+  rp.nud = nu + d;
+  rp.logt = (float)c.c0 - 0.5f * mA * log1pf(d / nu);
+  rp.q[0] = q0;
+  rp.q[1] = q1;
+  rp.q[2] = q2;
+  // Lambda = L L^T: diagonal and correlations
+  const float L00 = c.L[0], L10 = c.L[RMAX], L11 = c.L[RMAX + 1];
+  const float L20 = c.L[2 * RMAX], L21 = c.L[2 * RMAX + 1], L22 = c.L[2 * RMAX + 2];
+  const float D0 = L00 * L00, D1 = fmaf(L10, L10, L11 * L11), D2 = fmaf(L20, L20, fmaf(L21, L21, L22 * L22));
+  const float i0 = rsqrtf(D0), i1 = rsqrtf(D1), i2 = rsqrtf(D2);
+  rp.R[0] = L10 * L00 * i0 * i1;
+  rp.R[1] = L20 * L00 * i0 * i2;
+  rp.R[2] = fmaf(L20, L10, L21 * L11) * i1 * i2;
+  const float p2 = 1.f - rp.R[0] * rp.R[0];
+  const float l32 = (rp.R[2] - rp.R[1] * rp.R[0]) * rsqrtf(fmaxf(p2, 1e-30f));
+  const float p3 = 1.f - rp.R[1] * rp.R[1] - l32 * l32;
+  const bool comp_ok = fabsf(rp.R[0]) <= RHO_MAX && fabsf(rp.R[1]) <= RHO_MAX && fabsf(rp.R[2]) <= RHO_MAX &&
+                       p2 >= PIVOT_MIN && p3 >= PIVOT_MIN && mA >= 3.f && mB <= 30.f;
+  const float m = pass ? mB : mA;
+  const float f = -sqrtf(m / rp.nud);
+  const float cr[3] = {q0 * f * i0, q1 * f * i1, q2 * f * i2};
+  // pass B has the larger limits (same signs): its box decides the pair
+  const float fB = -sqrtf(mB / rp.nud);
+  const float cB[3] = {q0 * fB * i0, q1 * fB * i1, q2 * fB * i2};
+  // Below the box a coordinate is all but untruncated once the dof reach
+  // CLAMP_LO_MIN_DOF: P(X_t < -8) <= 2.2e-5 for t_8 and less for more dof, the
+  // most that clamping c_t up to -8 can move P; such pairs stay with the network.
+  const float lo = (mA >= CLAMP_LO_MIN_DOF) ? -INFINITY : C_LO;
+  bool inbox = true;
+#pragma unroll
+  for (int t = 0; t < 3; ++t) {
+    inbox = inbox && cB[t] >= lo && cB[t] <= C_HI;
+    rp.c[t] = fminf(fmaxf(cr[t], C_LO), C_HI);
+  }
+  rp.kind = comp_ok ? (inbox ? 2 : 1) : 0;
+  rp.logm = logf(m);
+  return rp;
+}
+
+template <bool DENS>
+__global__ void __launch_bounds__(GROUP_THREADS * GROUPS, 1)
+    surrogate_estep_kernel(SurrogateDev sd, const double *Y, int64_t n, int g, int p,
+                           const CompT<float> *__restrict__ comp, EstepOut out, int *fb_list, unsigned *fb_count) {
+  extern __shared__ __align__(128) unsigned char smem[];
+  InferWeights &Wsm = *reinterpret_cast<InferWeights *>(smem);
+  const int tid = threadIdx.x;
+  {
+    const bf16 *W1 = static_cast<const bf16 *>(sd.W1), *W2 = static_cast<const bf16 *>(sd.W2);
+    const bf16 *W3 = static_cast<const bf16 *>(sd.W3), *W4 = static_cast<const bf16 *>(sd.W4);
+    for (int e = tid; e < DINP * H; e += blockDim.x) {
+      const int k = e / H, o = e % H;
+      Wsm.W1t[o * XP + k] = W1[e];
+    }
+    for (int e = tid; e < H * H; e += blockDim.x) {
+      const int k = e / H, o = e % H;
+      Wsm.W2t[o * HP + k] = W2[e];
+      Wsm.W3t[o * HP + k] = W3[e];
+    }
+    for (int e = tid; e < H * DOUTP; e += blockDim.x) {
+      const int k = e / DOUTP, o = e % DOUTP;
+      Wsm.W4t[o * HP + k] = W4[e];
+    }
+    for (int e = tid; e < H; e += blockDim.x) {
+      Wsm.bias[e] = sd.b1[e];
+      Wsm.bias[H + e] = sd.b2[e];
+      Wsm.bias[2 * H + e] = sd.b3[e];
+    }
+    if (tid < DOUTP) Wsm.bias[3 * H + tid] = sd.b4[tid];
+    if (tid < 2 * DOUT) Wsm.norm[tid] = sd.norm[tid];
+  }
+  __syncthreads();
+
+  const int grp = tid / GROUP_THREADS, gt = tid % GROUP_THREADS;
+  const int w = gt >> 5, lane = gt & 31;
+  InferGroup &G = *reinterpret_cast<InferGroup *>(smem + sizeof(InferWeights) + grp * sizeof(InferGroup));
+  constexpr int PPT = DENS ? TROWS : TROWS / 2;  // pairs per tile
+  const int64_t tpc = (n + PPT - 1) / PPT;
+  const int64_t ntiles = tpc * g;
+  const float logm_mid = (float)(LOGM_LO + LOGM_HI), logm_scale = (float)(2.0 / (LOGM_HI - LOGM_LO));
+
+  for (int64_t tile = (int64_t)blockIdx.x * GROUPS + grp; tile < ntiles; tile += (int64_t)gridDim.x * GROUPS) {
+    const int i = (int)(tile / tpc);
+    const int64_t j0 = (tile % tpc) * PPT;
+    const CompT<float> &c = comp[i];
+    group_sync(grp);  // the previous tile's epilogue has read O and the pair values
+    if (gt < TROWS) {
+      const int row = gt;
+      const int pair = DENS ? row : row >> 1, pass = DENS ? 0 : (row & 1);
+      const int64_t j = j0 + pair;
+      bf16 *xr = G.X + row * XP;
+      if (j < n) {
+        const RowProblem rp = row_problem(c, Y, p, j, pass);
+        const float cs = 2.f / (C_HI - C_LO), cm = C_LO + C_HI;
+        const float u[DIN] = {(2.f * rp.c[0] - cm) * 0.5f * cs, (2.f * rp.c[1] - cm) * 0.5f * cs,
+                              (2.f * rp.c[2] - cm) * 0.5f * cs, rp.R[0] / RHO_MAX, rp.R[1] / RHO_MAX,
+                              rp.R[2] / RHO_MAX, (2.f * rp.logm - logm_mid) * (0.5f * logm_scale)};
+#pragma unroll
+        for (int t = 0; t < DINP; t += 2)
+          *reinterpret_cast<__nv_bfloat162 *>(xr + t) =
+              __floats2bfloat162_rn(t < DIN ? u[t] : 0.f, t + 1 < DIN ? u[t + 1] : 0.f);
+        if (pass == 0) {
+          G.logt[pair] = rp.logt;
+          G.nud[pair] = rp.nud;
+          G.q[3 * pair] = rp.q[0];
+          G.q[3 * pair + 1] = rp.q[1];
+          G.q[3 * pair + 2] = rp.q[2];
+          G.ok[pair] = rp.kind;
+          if (rp.kind != 2) {
+            const unsigned slot = atomicAdd(fb_count + i, 1u);
+            fb_list[(int64_t)i * n + slot] = (int)j;
+          }
+        }
+      } else {
+#pragma unroll
+        for (int t = 0; t < DINP; t += 2)
+          *reinterpret_cast<__nv_bfloat162 *>(xr + t) = __floats2bfloat162_rn(0.f, 0.f);
+        if (pass == 0) G.ok[pair] = 0;
+      }
+    }
+    group_sync(grp);
+    float acc[2][8][4];
+    mma_32x64<DINP>(G.X, XP, Wsm.W1t, XP, w, lane, acc);
+    store_gelu(G.Hb, Wsm.bias, w, lane, acc);
+    group_sync(grp);
+    mma_32x64<H>(G.Hb, HP, Wsm.W2t, HP, w, lane, acc);
+    group_sync(grp);
+    store_gelu(G.Hb, Wsm.bias + H, w, lane, acc);
+    group_sync(grp);
+    mma_32x64<H>(G.Hb, HP, Wsm.W3t, HP, w, lane, acc);
+    group_sync(grp);
+    store_gelu(G.Hb, Wsm.bias + 2 * H, w, lane, acc);
+    group_sync(grp);
+    {
+      // output layer: warp w takes rows 16 w .. 16 w + 15, all 16 columns
+      const int gid = lane >> 2, tig = lane & 3;
+      float o[2][4];
+#pragma unroll
+      for (int a = 0; a < 2; ++a)
+#pragma unroll
+        for (int b = 0; b < 4; ++b) o[a][b] = 0.f;
+#pragma unroll
+      for (int ks = 0; ks < H; ks += 16) {
+        uint32_t af[4], bfr[2][2];
+        const bf16 *r0 = G.Hb + (w * 16 + gid) * HP + ks + tig * 2;
+        af[0] = ld32(r0);
+        af[1] = ld32(r0 + 8 * HP);
+        af[2] = ld32(r0 + 8);
+        af[3] = ld32(r0 + 8 * HP + 8);
+#pragma unroll
+        for (int nj = 0; nj < 2; ++nj) {
+          const bf16 *c0 = Wsm.W4t + (nj * 8 + gid) * HP + ks + tig * 2;
+          bfr[nj][0] = ld32(c0);
+          bfr[nj][1] = ld32(c0 + 8);
+        }
+        mma_bf16(o[0], af, bfr[0]);
+        mma_bf16(o[1], af, bfr[1]);
+      }
+#pragma unroll
+      for (int nj = 0; nj < 2; ++nj) {
+        const int row = w * 16 + gid, col = nj * 8 + tig * 2;
+        const float b0 = Wsm.bias[3 * H + col], b1 = Wsm.bias[3 * H + col + 1];
+        G.O[row * OP + col] = o[nj][0] + b0;
+        G.O[row * OP + col + 1] = o[nj][1] + b1;
+        G.O[(row + 8) * OP + col] = o[nj][2] + b0;
+        G.O[(row + 8) * OP + col + 1] = o[nj][3] + b1;
+      }
+    }
+    group_sync(grp);
+    if (gt < PPT) {
+      const int pair = gt;
+      const int64_t j = j0 + pair;
+      const int kind = (j < n) ? G.ok[pair] : -1;
+      const int64_t ij = (int64_t)i * n + j;
+      const float *mean = Wsm.norm, *sdv = Wsm.norm + DOUT;
+      const float *oA = G.O + (DENS ? pair : 2 * pair) * OP;
+      const float logTA = -__expf(fmaf(oA[0], sdv[0], mean[0]));
+      // pairs left to the lattice rule carry an upper bound of log f for its
+      // triage: log T is decreasing in every c_t, so the network's value at
+      // the box-clamped point plus a margin bounds it; none without a domain
+      if (kind == 1) static_cast<float *>(out.logf)[ij] = G.logt[pair] + logTA + UB_MARGIN;
+      if (kind == 0) static_cast<float *>(out.logf)[ij] = INFINITY;
+      if (kind == 2) {
+        static_cast<float *>(out.logf)[ij] = G.logt[pair] + logTA;
+        if (!DENS) {
+          const float *oB = oA + OP;
+          const float logTB = -__expf(fmaf(oB[0], sdv[0], mean[0]));
+          const float nud = G.nud[pair];
+          const float mA = (float)c.mA, mB = (float)c.mB;
+          const float e1 = mA / nud * __expf(logTB - logTA);
+          const float e2 = e1 - (logf(0.5f * nud) + mA / nud - (float)c.psiA);
+          const float sig = sqrtf(nud / mB);
+          // E[X] and E[X X^T] of pass B in the Lambda basis: D^{1/2} (.) D^{1/2}
+          const float L00 = c.L[0], L10 = c.L[RMAX], L11 = c.L[RMAX + 1];
+          const float L20 = c.L[2 * RMAX], L21 = c.L[2 * RMAX + 1], L22 = c.L[2 * RMAX + 2];
+          const float sD[3] = {fabsf(L00), sqrtf(fmaf(L10, L10, L11 * L11)),
+                               sqrtf(fmaf(L20, L20, fmaf(L21, L21, L22 * L22)))};
+          const float *qp = G.q + 3 * pair;
+          float LEV[3];
+          float EXs[3];
+#pragma unroll
+          for (int t = 0; t < 3; ++t) {
+            EXs[t] = fmaf(oB[1 + t], sdv[1 + t], mean[1 + t]);
+            LEV[t] = sD[t] * EXs[t];
+          }
+          static_cast<float *>(out.e1)[ij] = e1;
+          static_cast<float *>(out.e2)[ij] = e2;
+#pragma unroll
+          for (int t = 0; t < 3; ++t)
+            static_cast<float *>(out.e3)[((int64_t)i * 3 + t) * n + j] = e1 * fmaf(sig, LEV[t], qp[t]);
+          // e4 in lower-triangle order (0,0) (1,0) (1,1) (2,0) (2,1) (2,2); the
+          // network's second moments come in upper order 00 01 02 11 12 22
+          constexpr int UP[3][3] = {{0, 1, 2}, {1, 3, 4}, {2, 4, 5}};
+#pragma unroll
+          for (int t = 0; t < 3; ++t)
+#pragma unroll
+            for (int h = 0; h <= t; ++h) {
+              const int u = UP[t][h];
+              // the network gives the covariance; E[X'_h X'_t] = cov + E[X'_h] E[X'_t]
+              const float S = sD[t] * sD[h] * fmaf(EXs[h], EXs[t], fmaf(oB[4 + u], sdv[4 + u], mean[4 + u]));
+              const float exx = qp[t] * qp[h] + sig * (qp[t] * LEV[h] + LEV[t] * qp[h]) + sig * sig * S;
+              static_cast<float *>(out.e4)[((int64_t)i * 6 + t * (t + 1) / 2 + h) * n + j] = e1 * exx;
+            }
+        }
+      }
+    }
+  }
+}
+
+}  // namespace sg
+}  // namespace cfust
+
+namespace cfust {
+
+cudaError_t launch_surrogate_estep(const SurrogateDev &sd, const double *Y, int64_t n, int g, int p,
+                                   const CompT<float> *c32, EstepOut out, bool density_only, int *fb_list,
+                                   unsigned *fb_count, cudaStream_t st) {
+  cudaError_t e = cudaMemsetAsync(fb_count, 0, sizeof(unsigned) * g, st);
+  if (e != cudaSuccess || n <= 0) return e;
+  const int smem = (int)sg::INFER_SMEM;
+  const int64_t ppt = density_only ? sg::TROWS : sg::TROWS / 2;
+  const int64_t ntiles = (n + ppt - 1) / ppt * g;
+  int dev = 0, sms = 152;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  int64_t blocks = (ntiles + sg::GROUPS - 1) / sg::GROUPS;
+  if (blocks > sms) blocks = sms;
+  if (density_only) {
+    e = cudaFuncSetAttribute(sg::surrogate_estep_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    if (e != cudaSuccess) return e;
+    sg::surrogate_estep_kernel<true><<<(unsigned)blocks, sg::GROUP_THREADS * sg::GROUPS, smem, st>>>(
+        sd, Y, n, g, p, c32, out, fb_list, fb_count);
+  } else {
+    e = cudaFuncSetAttribute(sg::surrogate_estep_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    if (e != cudaSuccess) return e;
+    sg::surrogate_estep_kernel<false><<<(unsigned)blocks, sg::GROUP_THREADS * sg::GROUPS, smem, st>>>(
+        sd, Y, n, g, p, c32, out, fb_list, fb_count);
+  }
+  return cudaGetLastError();
+}
+
+}  // namespace cfust
+
+using namespace cfust;
+using namespace cfust::sg;
+
+struct cfust_surrogate {
+  int device = 0;
+  cudaStream_t stream = nullptr;
+  LatticeDev lat{};
+  std::string err;
+  float *tab = nullptr;               // chi tables [MGRID][N]
+  float *theta = nullptr, *mom = nullptr, *vel = nullptr, *grad = nullptr;
+  float *norm = nullptr;              // [20] target mean, std
+  float host_norm[20];
+  bf16 *W1 = nullptr, *W2 = nullptr, *W3 = nullptr, *W4 = nullptr;
+  float *b1 = nullptr, *b2 = nullptr, *b3 = nullptr, *b4 = nullptr;
+  int64_t cap = 0;                    // rows the work buffers hold
+  bf16 *x0 = nullptr, *Z1 = nullptr, *H1 = nullptr, *Z2 = nullptr, *H2 = nullptr, *Z3 = nullptr, *H3 = nullptr;
+  float *out = nullptr;
+  bf16 *dz4 = nullptr, *dz3 = nullptr, *dz2 = nullptr, *dz1 = nullptr;
+  float *part = nullptr;
+  int64_t part_len = 0;
+  double *loss_part = nullptr;
+  int adam_t = 0;
+};
+
+namespace cfust {
+SurrogateDev surrogate_dev(const cfust_surrogate *s) {
+  SurrogateDev d;
+  d.W1 = s->W1;
+  d.W2 = s->W2;
+  d.W3 = s->W3;
+  d.W4 = s->W4;
+  d.b1 = s->b1;
+  d.b2 = s->b2;
+  d.b3 = s->b3;
+  d.b4 = s->b4;
+  d.norm = s->norm;
+  return d;
+}
+}  // namespace cfust
+
+namespace {
+
+thread_local std::string g_sg_error;
+
+cfust_status sg_fail(cfust_surrogate *s, cfust_status st, const std::string &m) {
+  if (s) s->err = m; else g_sg_error = m;
+  return st;
+}
+
+#define SG_CUDA(s, call)                                                                  \
+  do {                                                                                    \
+    cudaError_t e_ = (call);                                                              \
+    if (e_ != cudaSuccess) return sg_fail((s), CFUST_ECUDA, std::string(#call) + ": " + cudaGetErrorString(e_)); \
+  } while (0)
+
+cfust_status ensure_rows(cfust_surrogate *s, int64_t B) {
+  if (B <= s->cap) return CFUST_OK;
+  void *bufs[] = {s->x0, s->Z1, s->H1, s->Z2, s->H2, s->Z3, s->H3, s->out, s->dz4, s->dz3, s->dz2, s->dz1};
+  for (void *p : bufs)
+    if (p) cudaFree(p);
+  SG_CUDA(s, cudaMalloc(&s->x0, sizeof(bf16) * B * DINP));
+  SG_CUDA(s, cudaMalloc(&s->Z1, sizeof(bf16) * B * H));
+  SG_CUDA(s, cudaMalloc(&s->H1, sizeof(bf16) * B * H));
+  SG_CUDA(s, cudaMalloc(&s->Z2, sizeof(bf16) * B * H));
+  SG_CUDA(s, cudaMalloc(&s->H2, sizeof(bf16) * B * H));
+  SG_CUDA(s, cudaMalloc(&s->Z3, sizeof(bf16) * B * H));
+  SG_CUDA(s, cudaMalloc(&s->H3, sizeof(bf16) * B * H));
+  SG_CUDA(s, cudaMalloc(&s->out, sizeof(float) * B * DOUTP));
+  SG_CUDA(s, cudaMalloc(&s->dz4, sizeof(bf16) * B * DOUTP));
+  SG_CUDA(s, cudaMalloc(&s->dz3, sizeof(bf16) * B * H));
+  SG_CUDA(s, cudaMalloc(&s->dz2, sizeof(bf16) * B * H));
+  SG_CUDA(s, cudaMalloc(&s->dz1, sizeof(bf16) * B * H));
+  s->cap = B;
+  return CFUST_OK;
+}
+
+Gemm fwd_layer(const bf16 *A, int K, const bf16 *W, int N, const float *bias, bf16 *Z, bf16 *Hh, int64_t B) {
+  Gemm g{};
+  g.M = (int)B;
+  g.N = N;
+  g.K = K;
+  g.A = A;
+  g.lda = K;
+  g.transA = 0;
+  g.B = W;
+  g.ldb = N;
+  g.transB = 0;
+  g.k_chunk = K;
+  g.mode = 1;
+  g.bias = bias;
+  g.Zout = Z;
+  g.Hout = Hh;
+  g.ldo = N;
+  return g;
+}
+
+// forward pass of rows [0, B) from the packed inputs x0; network output in s->out
+cfust_status forward(cfust_surrogate *s, int64_t B) {
+  SG_CUDA(s, gemm(fwd_layer(s->x0, DINP, s->W1, H, s->b1, s->Z1, s->H1, B), 1, s->stream));
+  SG_CUDA(s, gemm(fwd_layer(s->H1, H, s->W2, H, s->b2, s->Z2, s->H2, B), 1, s->stream));
+  SG_CUDA(s, gemm(fwd_layer(s->H2, H, s->W3, H, s->b3, s->Z3, s->H3, B), 1, s->stream));
+  Gemm g = fwd_layer(s->H3, H, s->W4, DOUTP, s->b4, nullptr, nullptr, B);
+  g.mode = 3;
+  g.C = s->out;
+  g.ldc = DOUTP;
+  SG_CUDA(s, gemm(g, 1, s->stream));
+  return CFUST_OK;
+}
+
+// gradient of the weights: dW = Hin^T dZ (split-K over rows) into grad[off]
+cfust_status weight_grad(cfust_surrogate *s, const bf16 *Hin, int kin, int kin_real, const bf16 *dZ, int nout,
+                         int nout_real, int64_t B, int off) {
+  const int chunk = 256;
+  const int S = (int)((B + chunk - 1) / chunk);
+  const int64_t need = (int64_t)S * kin * nout;
+  if (need > s->part_len) {
+    if (s->part) cudaFree(s->part);
+    SG_CUDA(s, cudaMalloc(&s->part, sizeof(float) * need));
+    s->part_len = need;
+  }
+  Gemm g{};
+  g.M = kin;
+  g.N = nout;
+  g.K = (int)B;
+  g.A = Hin;
+  g.lda = kin;
+  g.transA = 1;
+  g.B = dZ;
+  g.ldb = nout;
+  g.transB = 0;
+  g.k_chunk = chunk;
+  g.mode = 0;
+  g.C = s->part;
+  g.ldc = nout;
+  SG_CUDA(s, gemm(g, S, s->stream));
+  const int cnt = kin_real * nout_real;
+  reduce_partials_kernel<<<(cnt + 255) / 256, 256, 0, s->stream>>>(s->part, S, kin, nout, kin_real, nout_real,
+                                                                   s->grad, off);
+  SG_CUDA(s, cudaGetLastError());
+  return CFUST_OK;
+}
+
+// input gradient through a layer: dZprev = (dZ W^T) * GELU'(Zprev)
+cfust_status back_layer(cfust_surrogate *s, const bf16 *dZ, int nout, const bf16 *W, int kin, const bf16 *Zprev,
+                        bf16 *dZprev, int64_t B) {
+  Gemm g{};
+  g.M = (int)B;
+  g.N = kin;
+  g.K = nout;
+  g.A = dZ;
+  g.lda = nout;
+  g.transA = 0;
+  g.B = W;
+  g.ldb = nout;
+  g.transB = 1;
+  g.k_chunk = nout;
+  g.mode = 2;
+  g.Hout = dZprev;
+  g.ldo = kin;
+  g.Zprev = Zprev;
+  return gemm(g, 1, s->stream) == cudaSuccess ? CFUST_OK : sg_fail(s, CFUST_ECUDA, "gemm (backward)");
+}
+
+// loss and full gradient (into s->grad) of rows [0, B) with raw targets y
+cfust_status loss_grad(cfust_surrogate *s, const float *y, int64_t B, double *loss) {
+  cfust_status st = forward(s, B);
+  if (st != CFUST_OK) return st;
+  const int nb = 256;
+  loss_kernel<<<nb, 256, 0, s->stream>>>(s->out, y, s->norm, s->dz4, s->loss_part, B);
+  SG_CUDA(s, cudaGetLastError());
+  if ((st = weight_grad(s, s->H3, H, H, s->dz4, DOUTP, DOUT, B, OFF_W4)) != CFUST_OK) return st;
+  colsum_kernel<<<DOUTP, 256, 0, s->stream>>>(s->dz4, DOUTP, DOUT, B, s->grad, OFF_B4);
+  if ((st = back_layer(s, s->dz4, DOUTP, s->W4, H, s->Z3, s->dz3, B)) != CFUST_OK) return st;
+  if ((st = weight_grad(s, s->H2, H, H, s->dz3, H, H, B, OFF_W3)) != CFUST_OK) return st;
+  colsum_kernel<<<H, 256, 0, s->stream>>>(s->dz3, H, H, B, s->grad, OFF_B3);
+  if ((st = back_layer(s, s->dz3, H, s->W3, H, s->Z2, s->dz2, B)) != CFUST_OK) return st;
+  if ((st = weight_grad(s, s->H1, H, H, s->dz2, H, H, B, OFF_W2)) != CFUST_OK) return st;
+  colsum_kernel<<<H, 256, 0, s->stream>>>(s->dz2, H, H, B, s->grad, OFF_B2);
+  if ((st = back_layer(s, s->dz2, H, s->W2, H, s->Z1, s->dz1, B)) != CFUST_OK) return st;
+  if ((st = weight_grad(s, s->x0, DINP, DIN, s->dz1, H, H, B, OFF_W1)) != CFUST_OK) return st;
+  colsum_kernel<<<H, 256, 0, s->stream>>>(s->dz1, H, H, B, s->grad, OFF_B1);
+  SG_CUDA(s, cudaGetLastError());
+  if (loss) {
+    std::vector<double> lp(nb);
+    SG_CUDA(s, cudaMemcpyAsync(lp.data(), s->loss_part, sizeof(double) * nb, cudaMemcpyDeviceToHost, s->stream));
+    SG_CUDA(s, cudaStreamSynchronize(s->stream));
+    double t = 0.0;
+    for (double v : lp) t += v;
+    *loss = t / ((double)B * DOUT);
+  }
+  return CFUST_OK;
+}
+
+cfust_status pack(cfust_surrogate *s) {
+  pack_weights_kernel<<<(H * H + 255) / 256, 256, 0, s->stream>>>(s->theta, s->W1, s->W2, s->W3, s->W4, s->b1, s->b2,
+                                                                 s->b3, s->b4);
+  SG_CUDA(s, cudaGetLastError());
+  return CFUST_OK;
+}
+
+cfust_status prep(cfust_surrogate *s, const float *x, int64_t B) {
+  cfust_status st = ensure_rows(s, B);
+  if (st != CFUST_OK) return st;
+  prep_input_kernel<<<(unsigned)((B + 255) / 256), 256, 0, s->stream>>>(x, s->x0, B);
+  SG_CUDA(s, cudaGetLastError());
+  return CFUST_OK;
+}
+
+// SplitMix64 for initial weights and training inputs (host)
+struct SplitMix {
+  uint64_t x;
+  uint64_t next() {
+    uint64_t z = (x += 0x9E3779B97F4A7C15ull);
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    return z ^ (z >> 31);
+  }
+  double uniform() { return (double)(next() >> 11) * 1.1102230246251565e-16; }
+  double normal() {
+    const double u1 = uniform() + 1e-300, u2 = uniform();
+    return sqrt(-2.0 * log(u1)) * cos(6.283185307179586 * u2);
+  }
+};
+
+}  // namespace
+
+extern "C" {
+
+cfust_status cfust_surrogate_create(cfust_surrogate **out, uint64_t seed, const cfust_lattice *L, void *stream) {
+  if (!out || !L) return sg_fail(nullptr, CFUST_EINVAL, "out and lattice required");
+  *out = nullptr;
+  if (L->dim != 4 || L->n < 32 || L->n % 32 != 0 || L->n > CFUST_NMAX || !L->z || !L->shift)
+    return sg_fail(nullptr, CFUST_EINVAL, "surrogate lattice must have dim 4 and a multiple of 32 points");
+  cfust_surrogate *s = new cfust_surrogate();
+  s->stream = static_cast<cudaStream_t>(stream);
+  cudaGetDevice(&s->device);
+  s->lat.n = L->n;
+  for (int t = 0; t <= RMAX; ++t) {
+    if (t < 4) {
+      int64_t zz = L->z[t] % L->n;
+      if (zz < 0) zz += L->n;
+      s->lat.z[t] = (int)zz;
+      s->lat.step[t] = (int)((32 * zz) % L->n);
+      s->lat.shift[t] = L->shift[t];
+      const double sn = L->shift[t] * (double)L->n;
+      s->lat.sint[t] = (int)floor(sn);
+      s->lat.sfrac[t] = sn - floor(sn);
+    }
+  }
+  cfust_surrogate *S = s;
+#define CR(call)                                   \
+  do {                                             \
+    if ((call) != cudaSuccess) {                   \
+      g_sg_error = #call;                          \
+      cfust_surrogate_destroy(S);                  \
+      return CFUST_ECUDA;                          \
+    }                                              \
+  } while (0)
+  CR(cudaMalloc(&s->tab, sizeof(float) * MGRID * (size_t)L->n));
+  CR(cudaMalloc(&s->theta, sizeof(float) * NPARAM));
+  CR(cudaMalloc(&s->mom, sizeof(float) * NPARAM));
+  CR(cudaMalloc(&s->vel, sizeof(float) * NPARAM));
+  CR(cudaMalloc(&s->grad, sizeof(float) * NPARAM));
+  CR(cudaMalloc(&s->norm, sizeof(float) * 20));
+  CR(cudaMalloc(&s->W1, sizeof(bf16) * DINP * H));
+  CR(cudaMalloc(&s->W2, sizeof(bf16) * H * H));
+  CR(cudaMalloc(&s->W3, sizeof(bf16) * H * H));
+  CR(cudaMalloc(&s->W4, sizeof(bf16) * H * DOUTP));
+  CR(cudaMalloc(&s->b1, sizeof(float) * H));
+  CR(cudaMalloc(&s->b2, sizeof(float) * H));
+  CR(cudaMalloc(&s->b3, sizeof(float) * H));
+  CR(cudaMalloc(&s->b4, sizeof(float) * DOUTP));
+  CR(cudaMalloc(&s->loss_part, sizeof(double) * 256));
+  CR(cudaMemsetAsync(s->mom, 0, sizeof(float) * NPARAM, s->stream));
+  CR(cudaMemsetAsync(s->vel, 0, sizeof(float) * NPARAM, s->stream));
+  // initial weights: N(0, 1/fan_in), zero biases; unit target normalisation
+  SplitMix rng{seed};
+  std::vector<float> th(NPARAM, 0.f);
+  const int dims[5] = {DIN, H, H, H, DOUT};
+  int off = 0;
+  for (int k = 0; k < 4; ++k) {
+    const double sd = 1.0 / sqrt((double)dims[k]);
+    for (int e = 0; e < dims[k] * dims[k + 1]; ++e) th[off + e] = (float)(sd * rng.normal());
+    off += dims[k] * dims[k + 1] + dims[k + 1];
+  }
+  for (int k = 0; k < 10; ++k) {
+    s->host_norm[k] = 0.f;
+    s->host_norm[10 + k] = 1.f;
+  }
+  CR(cudaMemcpy(s->theta, th.data(), sizeof(float) * NPARAM, cudaMemcpyHostToDevice));
+  CR(cudaMemcpy(s->norm, s->host_norm, sizeof(float) * 20, cudaMemcpyHostToDevice));
+  chi_grid_kernel<<<dim3((L->n + 127) / 128, MGRID), 128, 0, s->stream>>>(s->lat, s->tab);
+  CR(cudaGetLastError());
+  if (pack(s) != CFUST_OK) {
+    cfust_surrogate_destroy(s);
+    return CFUST_ECUDA;
+  }
+  CR(cudaStreamSynchronize(s->stream));
+#undef CR
+  *out = s;
+  return CFUST_OK;
+}
+
+cfust_status cfust_surrogate_destroy(cfust_surrogate *s) {
+  if (!s) return CFUST_OK;
+  void *bufs[] = {s->tab, s->theta, s->mom, s->vel, s->grad, s->norm, s->W1, s->W2, s->W3, s->W4, s->b1, s->b2, s->b3,
+                  s->b4, s->x0, s->Z1, s->H1, s->Z2, s->H2, s->Z3, s->H3, s->out, s->dz4, s->dz3, s->dz2, s->dz1,
+                  s->part, s->loss_part};
+  for (void *p : bufs)
+    if (p) cudaFree(p);
+  delete s;
+  return CFUST_OK;
+}
+
+const char *cfust_surrogate_last_error(cfust_surrogate *s) { return s ? s->err.c_str() : g_sg_error.c_str(); }
+
+cfust_status cfust_surrogate_label(cfust_surrogate *s, const float *x, float *y, int64_t B) {
+  if (!s || !x || !y || B < 0) return sg_fail(s, CFUST_EINVAL, "bad arguments");
+  if (B == 0) return CFUST_OK;
+  const int64_t blocks = (B + 7) / 8;
+  label_kernel<<<(unsigned)blocks, 256, 0, s->stream>>>(x, y, B, s->lat, s->tab);
+  SG_CUDA(s, cudaGetLastError());
+  SG_CUDA(s, cudaStreamSynchronize(s->stream));
+  return CFUST_OK;
+}
+
+cfust_status cfust_surrogate_predict(cfust_surrogate *s, const float *x, float *y, int64_t B) {
+  if (!s || !x || !y || B < 0) return sg_fail(s, CFUST_EINVAL, "bad arguments");
+  if (B == 0) return CFUST_OK;
+  cfust_status st = prep(s, x, B);
+  if (st != CFUST_OK) return st;
+  if ((st = forward(s, B)) != CFUST_OK) return st;
+  denorm_kernel<<<(unsigned)((B + 255) / 256), 256, 0, s->stream>>>(s->out, s->norm, y, B);
+  SG_CUDA(s, cudaGetLastError());
+  SG_CUDA(s, cudaStreamSynchronize(s->stream));
+  return CFUST_OK;
+}
+
+cfust_status cfust_surrogate_set_params(cfust_surrogate *s, const float *theta, const float *norm) {
+  if (!s || !theta) return sg_fail(s, CFUST_EINVAL, "bad arguments");
+  SG_CUDA(s, cudaMemcpy(s->theta, theta, sizeof(float) * NPARAM, cudaMemcpyHostToDevice));
+  if (norm) {
+    memcpy(s->host_norm, norm, sizeof(float) * 20);
+    SG_CUDA(s, cudaMemcpy(s->norm, norm, sizeof(float) * 20, cudaMemcpyHostToDevice));
+  }
+  cfust_status st = pack(s);
+  if (st != CFUST_OK) return st;
+  SG_CUDA(s, cudaStreamSynchronize(s->stream));
+  return CFUST_OK;
+}
+
+cfust_status cfust_surrogate_get_params(cfust_surrogate *s, float *theta, float *norm) {
+  if (!s) return sg_fail(s, CFUST_EINVAL, "bad arguments");
+  SG_CUDA(s, cudaStreamSynchronize(s->stream));
+  if (theta) SG_CUDA(s, cudaMemcpy(theta, s->theta, sizeof(float) * NPARAM, cudaMemcpyDeviceToHost));
+  if (norm) memcpy(norm, s->host_norm, sizeof(float) * 20);
+  return CFUST_OK;
+}
+
+cfust_status cfust_surrogate_gradient(cfust_surrogate *s, const float *x, const float *y, int64_t B, double *loss,
+                                      float *grad) {
+  if (!s || !x || !y || B < 1) return sg_fail(s, CFUST_EINVAL, "bad arguments");
+  cfust_status st = prep(s, x, B);
+  if (st != CFUST_OK) return st;
+  if ((st = loss_grad(s, y, B, loss)) != CFUST_OK) return st;
+  if (grad) {
+    SG_CUDA(s, cudaMemcpyAsync(grad, s->grad, sizeof(float) * NPARAM, cudaMemcpyDeviceToHost, s->stream));
+    SG_CUDA(s, cudaStreamSynchronize(s->stream));
+  }
+  return CFUST_OK;
+}
+
+cfust_status cfust_surrogate_train(cfust_surrogate *s, int64_t n_train, int epochs, int batch, float lr,
+                                   uint64_t seed, float *loss_trace) {
+  if (!s || n_train < batch || batch < 128 || epochs < 1 || !(lr > 0.f))
+    return sg_fail(s, CFUST_EINVAL, "need n_train >= batch >= 128, epochs >= 1, lr > 0");
+  // training inputs drawn uniformly over the domain (host), labelled on the GPU
+  SplitMix rng{seed};
+  std::vector<float> hx(n_train * DIN);
+  for (int64_t b = 0; b < n_train; ++b) {
+    float *xb = hx.data() + b * DIN;
+    for (;;) {
+      // half uniform over the box, half c_t ~ N(-1.5, 2.5^2) clipped to it:
+      // E-step pairs with weight crowd around moderate negative c
+      const bool focus = rng.uniform() < 0.5;
+      for (int t = 0; t < 3; ++t) {
+        const double v = focus ? -1.5 + 2.5 * rng.normal() : C_LO + rng.uniform() * (C_HI - C_LO);
+        xb[t] = (float)fmin(fmax(v, (double)C_LO), (double)C_HI);
+      }
+      for (int t = 3; t < 6; ++t) xb[t] = (float)((2.0 * rng.uniform() - 1.0) * RHO_MAX);
+      xb[6] = (float)(LOGM_LO + rng.uniform() * (LOGM_HI - LOGM_LO));
+      const double r12 = xb[3], r13 = xb[4], r23 = xb[5];
+      const double p2 = 1.0 - r12 * r12;
+      const double l32 = (r23 - r13 * r12) / sqrt(p2);
+      const double p3 = 1.0 - r13 * r13 - l32 * l32;
+      if (p2 >= PIVOT_MIN && p3 >= PIVOT_MIN) break;
+    }
+  }
+  float *dx = nullptr, *dy = nullptr;
+  SG_CUDA(s, cudaMalloc(&dx, sizeof(float) * n_train * DIN));
+  SG_CUDA(s, cudaMalloc(&dy, sizeof(float) * n_train * DOUT));
+  SG_CUDA(s, cudaMemcpy(dx, hx.data(), sizeof(float) * n_train * DIN, cudaMemcpyHostToDevice));
+  cfust_status st = cfust_surrogate_label(s, dx, dy, n_train);
+  if (st != CFUST_OK) {
+    cudaFree(dx);
+    cudaFree(dy);
+    return st;
+  }
+  // keep the rows with finite labels (in the domain's far corner every point
+  // weight can underflow), then set the target normalisation from them
+  {
+    std::vector<float> hy(n_train * DOUT);
+    SG_CUDA(s, cudaMemcpy(hy.data(), dy, sizeof(float) * n_train * DOUT, cudaMemcpyDeviceToHost));
+    int64_t kept = 0;
+    for (int64_t b = 0; b < n_train; ++b) {
+      bool fin = true;
+      for (int k = 0; k < DOUT; ++k) fin = fin && std::isfinite(hy[b * DOUT + k]);
+      if (!fin) continue;
+      if (kept != b) {
+        memmove(&hy[kept * DOUT], &hy[b * DOUT], sizeof(float) * DOUT);
+        memmove(&hx[kept * DIN], &hx[b * DIN], sizeof(float) * DIN);
+      }
+      ++kept;
+    }
+    if (kept < batch) {
+      cudaFree(dx);
+      cudaFree(dy);
+      return sg_fail(s, CFUST_ENUMERIC, "too few finite training labels");
+    }
+    n_train = kept;
+    SG_CUDA(s, cudaMemcpy(dx, hx.data(), sizeof(float) * n_train * DIN, cudaMemcpyHostToDevice));
+    SG_CUDA(s, cudaMemcpy(dy, hy.data(), sizeof(float) * n_train * DOUT, cudaMemcpyHostToDevice));
+    std::vector<float> ht(n_train * DOUT);
+    for (int64_t b = 0; b < n_train; ++b) to_net(&hy[b * DOUT], &ht[b * DOUT]);
+    for (int k = 0; k < DOUT; ++k) {
+      double m = 0, v = 0;
+      for (int64_t b = 0; b < n_train; ++b) m += ht[b * DOUT + k];
+      m /= (double)n_train;
+      for (int64_t b = 0; b < n_train; ++b) v += (ht[b * DOUT + k] - m) * (ht[b * DOUT + k] - m);
+      v = sqrt(v / (double)n_train);
+      s->host_norm[k] = (float)m;
+      s->host_norm[DOUT + k] = (float)(v > 1e-6 ? v : 1.0);
+    }
+    SG_CUDA(s, cudaMemcpy(s->norm, s->host_norm, sizeof(float) * 20, cudaMemcpyHostToDevice));
+  }
+  const int64_t steps = n_train / batch;
+  for (int ep = 0; ep < epochs; ++ep) {
+    double ep_loss = 0.0;
+    for (int64_t k = 0; k < steps; ++k) {
+      const int64_t off = k * batch;
+      if ((st = prep(s, dx + off * DIN, batch)) != CFUST_OK) break;
+      double l = 0.0;
+      if ((st = loss_grad(s, dy + off * DOUT, batch, (k % 64 == 0) ? &l : nullptr)) != CFUST_OK) break;
+      ep_loss += l;
+      ++s->adam_t;
+      const float b1 = 0.9f, b2 = 0.999f;
+      const float c1 = 1.f - powf(b1, (float)s->adam_t), c2 = 1.f - powf(b2, (float)s->adam_t);
+      // cosine decay over the whole run
+      const float frac = (float)(ep * steps + k) / (float)(epochs * steps);
+      const float lr_t = lr * 0.5f * (1.f + cosf(3.14159265f * frac));
+      adam_kernel<<<(NPARAM + 255) / 256, 256, 0, s->stream>>>(s->theta, s->mom, s->vel, s->grad, NPARAM, lr_t, b1,
+                                                               b2, 1e-8f, c1, c2);
+      if (cudaGetLastError() != cudaSuccess) { st = CFUST_ECUDA; break; }
+      if ((st = pack(s)) != CFUST_OK) break;
+    }
+    if (st != CFUST_OK) break;
+    if (loss_trace) loss_trace[ep] = (float)(ep_loss / (double)((steps + 63) / 64));
+  }
+  cudaFree(dx);
+  cudaFree(dy);
+  if (st != CFUST_OK) return st;
+  SG_CUDA(s, cudaStreamSynchronize(s->stream));
+  return CFUST_OK;
+}
+
+}  // extern "C"

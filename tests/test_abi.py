@@ -70,3 +70,15 @@ def test_lattice_spec_is_deterministic():
     assert np.array_equal(a.z, b.z) and np.array_equal(a.shift, b.shift)
     assert a.z[0] == 1 and np.all((a.z > 0) & (a.z < 2048))
     assert np.all((a.shift >= 0) & (a.shift < 1))
+
+
+def test_surrogate_create_rejects_bad_lattice_without_a_device():
+    lib = binding.load()
+    z = np.array([1, 3, 5], dtype=np.int64)
+    sh = np.array([0.1, 0.2, 0.3])
+    lat = binding.cfust_lattice(1024, 3, z.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)),
+                                sh.ctypes.data_as(ctypes.POINTER(ctypes.c_double)))
+    h = ctypes.c_void_p()
+    assert lib.cfust_surrogate_create(ctypes.byref(h), 1, ctypes.byref(lat), None) == -1
+    assert b"dim 4" in lib.cfust_surrogate_last_error(None)
+    assert lib.cfust_surrogate_create(ctypes.byref(h), 1, None, None) == -1

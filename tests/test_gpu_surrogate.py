@@ -1,0 +1,252 @@
+"""The learned surrogate of the r = 3 lattice integrals, through the C ABI:
+its GPU labeller against the FP64 lattice rule, its BF16 tensor-core forward
+pass and gradient against the FP64 network oracle, training on the GPU, the
+network judged by the lattice rule, and the surrogate E-step against the
+plain lattice E-step."""
+import math
+
+import numpy as np
+import pytest
+
+from oracle import cfust_oracle as O
+from oracle import mlp_oracle as MO
+from paper_2005_06848_gb300 import binding, synth
+
+pytestmark = pytest.mark.gpu
+
+
+def _torch():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    return torch
+
+
+def _domain_sample(rng, B):
+    out = []
+    while len(out) < B:
+        x = np.r_[rng.uniform(MO.C_LO, MO.C_HI, 3), rng.uniform(-MO.RHO_MAX, MO.RHO_MAX, 3),
+                  rng.uniform(MO.LOGM_LO, MO.LOGM_HI)]
+        if MO.in_domain(x[None])[0]:
+            out.append(x)
+    return np.array(out)
+
+
+@pytest.fixture(scope="module")
+def lat8192():
+    return synth.make_lattice(8192, 4, seed=11)
+
+
+def test_labeller_matches_the_fp64_lattice_rule(lat8192):
+    torch = _torch()
+    rng = np.random.default_rng(5)
+    x = _domain_sample(rng, 40).astype(np.float32).astype(np.float64)
+    # plus the box corners in c, where the weights are smallest
+    x[:4, :3] = [[MO.C_HI] * 3, [MO.C_LO] * 3, [MO.C_HI, MO.C_LO, MO.C_HI], [0.0, 0.0, 0.0]]
+    s = binding.Surrogate(lat8192, seed=1)
+    yg = s.cfust_surrogate_label(torch.tensor(x, dtype=torch.float32, device="cuda")).cpu().numpy()
+    U = O.lattice_points(lat8192.n, lat8192.z, lat8192.shift)
+    yo = MO.label(x, U)
+    ok = np.isfinite(yo[:, 0])
+    assert np.all(np.isfinite(yg[ok]))
+    # single-precision sweep with chi tables interpolated in log m
+    assert np.max(np.abs(yg[ok, 0] - yo[ok, 0])) < 5e-4
+    assert np.max(np.abs(yg[ok, 1:] - yo[ok, 1:]) / (1 + np.abs(yo[ok, 1:]))) < 5e-4
+
+
+def _bf16(a):
+    a = np.ascontiguousarray(a, dtype=np.float32)
+    u = a.view(np.uint32).astype(np.uint64)
+    r = ((u + 0x7FFF + ((u >> 16) & 1)) >> 16) << 16
+    return r.astype(np.uint32).view(np.float32).astype(np.float64)
+
+
+def test_forward_matches_the_fp64_network_within_bf16_bounds(lat8192):
+    torch = _torch()
+    rng = np.random.default_rng(6)
+    s = binding.Surrogate(lat8192, seed=2)
+    th, _ = s.cfust_surrogate_get_params()
+    norm = np.r_[rng.normal(size=10), rng.uniform(0.5, 3, 10)].astype(np.float32)
+    s.cfust_surrogate_set_params(th, norm)
+    x = _domain_sample(rng, 700).astype(np.float32)
+    pg = s.cfust_surrogate_predict(torch.tensor(x, dtype=torch.float32, device="cuda")).cpu().numpy()
+    # the network oracle at BF16-rounded weights: what remains is the BF16
+    # rounding of inputs and activations (relative 2^-9 per value)
+    tb = th.astype(np.float64).copy()
+    for (W, _b) in MO.unpack(tb):
+        W[...] = _bf16(W)
+    out, _ = MO.forward(tb, MO.normalise_inputs(x))
+    on = MO.net_targets(pg, norm)  # back to the network's normalised outputs
+    err = np.abs(on - out)
+    assert err.max() < 1e-2 and np.sqrt((err ** 2).mean()) < 2e-3, (err.max(), np.sqrt((err ** 2).mean()))
+
+
+def test_gradient_matches_the_fp64_network_oracle(lat8192):
+    torch = _torch()
+    rng = np.random.default_rng(7)
+    s = binding.Surrogate(lat8192, seed=3)
+    th, _ = s.cfust_surrogate_get_params()
+    norm = np.r_[rng.normal(size=10), rng.uniform(0.5, 3, 10)].astype(np.float32)
+    s.cfust_surrogate_set_params(th, norm)
+    x = _domain_sample(rng, 3000).astype(np.float32)   # several row tiles and a ragged tail
+    y = rng.normal(size=(3000, 10)).astype(np.float32)
+    loss, g = s.cfust_surrogate_gradient(torch.tensor(x, device="cuda"), torch.tensor(y, device="cuda"))
+    lo, go = MO.loss_and_grad(th.astype(np.float64), MO.normalise_inputs(x), MO.net_targets(y, norm))
+    assert abs(loss - lo) < 2e-3 * lo
+    assert np.linalg.norm(g - go) < 2e-2 * np.linalg.norm(go)
+    # every layer's weight and bias block on its own
+    off = 0
+    for k in range(4):
+        a, b = MO.DIMS[k], MO.DIMS[k + 1]
+        for size in (a * b, b):
+            blk = slice(off, off + size)
+            assert np.linalg.norm(g[blk] - go[blk]) < 3e-2 * np.linalg.norm(go[blk]) + 1e-7, (k, size)
+            off += size
+
+
+def test_training_on_the_gpu_reduces_the_loss(lat8192):
+    torch = _torch()
+    s = binding.Surrogate(lat8192, seed=4)
+    trace = s.cfust_surrogate_train(1 << 19, 4, batch=4096, lr=3e-3, seed=5)
+    assert np.all(np.isfinite(trace)) and trace[-1] < 0.2 * trace[0], trace
+    # judged by the lattice rule on held-out problems, in the network's units
+    rng = np.random.default_rng(8)
+    x = torch.tensor(_domain_sample(rng, 2048), dtype=torch.float32, device="cuda")
+    y = s.cfust_surrogate_label(x).cpu().numpy()
+    p = s.cfust_surrogate_predict(x).cpu().numpy()
+    _, norm = s.cfust_surrogate_get_params()
+    ok = np.all(np.isfinite(y), axis=1)
+    e = MO.net_targets(p[ok], norm) - MO.net_targets(y[ok], norm)
+    # predicting the training mean scores about 1 in these units
+    assert np.sqrt(np.mean(e ** 2)) < 0.3
+
+
+def _standardised(Y, params, i):
+    """Per pair of component i: d, q, log t_p, D^{1/2}, the network inputs of
+    passes A and B, and whether the pair is the network's (box rule)."""
+    pi, mu, Sigma, Delta, nu = params.as_arrays()
+    p = Y.shape[1]
+    d, q, Lam, log_tp = O.component_terms(Y, mu[i], Sigma[i], Delta[i], nu[i])
+    sD = np.sqrt(np.diag(Lam))
+    R = Lam / np.outer(sD, sD)
+    mA, mB = nu[i] + p, nu[i] + p + 2
+    cA = -q * np.sqrt(mA / (nu[i] + d))[:, None] / sD
+    cB = -q * np.sqrt(mB / (nu[i] + d))[:, None] / sD
+    rr = np.tile([R[0, 1], R[0, 2], R[1, 2]], (len(d), 1))
+    xA = np.column_stack([np.clip(cA, MO.C_LO, MO.C_HI), rr, np.full(len(d), math.log(mA))])
+    xB = np.column_stack([np.clip(cB, MO.C_LO, MO.C_HI), rr, np.full(len(d), math.log(mB))])
+    lo = -np.inf if mA >= 8 else MO.C_LO
+    comp_ok = bool(MO.in_domain(np.r_[np.zeros(3), rr[0], math.log(mA)][None])[0] and mB <= 30)
+    inside = comp_ok & np.all((cB >= lo) & (cB <= MO.C_HI), axis=1)
+    # pairs within rounding of an edge may fall either way in single precision
+    edge = np.any(np.isclose(cB, MO.C_HI, atol=1e-4) | np.isclose(cB, MO.C_LO, atol=1e-4), axis=1)
+    return d, q, log_tp, sD, xA, xB, inside, edge
+
+
+def test_surrogate_estep_is_the_expectations_of_the_network_outputs(lat8192):
+    """Pairs in the domain: log f and e1..e4 are the E-step formulas (the
+    oracle's, in FP64) applied to the network's own outputs for the pair's two
+    standardised problems.  Pairs outside: bit-identical to the lattice E-step."""
+    torch = _torch()
+    s = binding.Surrogate(lat8192, seed=6)
+    s.cfust_surrogate_train(1 << 18, 2, batch=4096, lr=3e-3, seed=2)
+    Y, _, truth, init, _, _ = synth.workload("cfust_p3r3g4_n1000000_N2048", n=3000, seed=0)
+    Yd = torch.tensor(Y, dtype=torch.float64, device="cuda")
+    lat = synth.make_lattice(1024, 4, seed=0)
+    for P in (truth, init):
+        plain = binding.Context(lat, precision=binding.CFUST_FP32)
+        sur = binding.Context(lat, precision=binding.CFUST_FP32)
+        sur.cfust_set_surrogate(s)
+        Ep = plain.cfust_estep(Yd, P)
+        Es = sur.cfust_estep(Yd, P)
+        fb = sur.cfust_last_fallback()
+        pi, mu, Sigma, Delta, nu = P.as_arrays()
+        p = Y.shape[1]
+        n_in = 0
+        for i in range(P.g):
+            d, q, log_tp, sD, xA, xB, inside, edge = _standardised(Y, P, i)
+            yA = s.cfust_surrogate_predict(torch.tensor(xA, dtype=torch.float32, device="cuda")).cpu().numpy()
+            yB = s.cfust_surrogate_predict(torch.tensor(xB, dtype=torch.float32, device="cuda")).cpu().numpy()
+            m = inside & ~edge
+            out = ~inside & ~edge
+            n_in += int(inside.sum())
+            logf = 3 * math.log(2) + log_tp + yA[:, 0]
+            S = np.zeros((len(d), 3, 3))
+            for k, (a, b) in enumerate(MO.UPPER):
+                S[:, a, b] = S[:, b, a] = yB[:, 4 + k]
+            LEV = sD * yB[:, 1:4]
+            LEVVL = S * np.outer(sD, sD)[None]
+            e1, e2, e3, e4 = O.expectations(d, q, nu[i], p, np.exp(yA[:, 0]), np.exp(yB[:, 0]), LEV, LEVVL)
+            gl = Es["logf"][i].cpu().numpy().astype(np.float64)
+            # FP32 prologue and epilogue against FP64, the same network outputs
+            dl = np.abs(gl[m] - logf[m])
+            assert np.median(dl) < 2e-4 and np.quantile(dl, 0.99) < 2e-2, (i, np.median(dl), dl.max())
+            ge1 = Es["e1"][i].cpu().numpy()
+            r1 = np.abs(ge1[m] - e1[m]) / np.maximum(np.abs(e1[m]), 1e-3)
+            assert np.median(r1) < 1e-3 and np.quantile(r1, 0.99) < 5e-2, (i, np.median(r1))
+            ge3 = Es["e3"][i].cpu().numpy().T
+            r3 = np.abs(ge3[m] - e3[m]) / (1 + np.abs(e3[m]))
+            assert np.median(r3) < 1e-3 and np.quantile(r3, 0.99) < 5e-2, i
+            ge4 = binding.unpack_e4(Es["e4"][i].cpu().numpy(), 3)
+            r4 = np.abs(ge4[m] - e4[m]) / (1 + np.abs(e4[m]))
+            assert np.median(r4) < 1e-3 and np.quantile(r4, 0.99) < 5e-2, i
+            # the rest went to the lattice rule: the same numbers as without a surrogate
+            for k in ("logf", "e1", "e2", "e3", "e4"):
+                a = Es[k][i].cpu().numpy()
+                b = Ep[k][i].cpu().numpy()
+                assert np.array_equal(a[..., out], b[..., out]), (i, k)
+        assert abs(fb - (P.g * len(Y) - n_in)) <= 0.002 * P.g * len(Y) + 2
+        # tau from the same log f: rows sum to one
+        assert np.allclose(Es["tau"].sum(0).cpu().numpy(), 1.0, atol=1e-5)
+
+
+def _timed_loglik(torch, ctx, Yd, P, reps=5):
+    ctx.cfust_loglik(Yd, P)
+    st = torch.cuda.current_stream()
+    best, ll = float("inf"), None
+    for _ in range(reps):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(st)
+        ll = ctx.cfust_loglik(Yd, P)
+        e1.record(st)
+        torch.cuda.synchronize()
+        best = min(best, e0.elapsed_time(e1))
+    return ll, best
+
+
+def test_surrogate_gain_at_equal_loglik_accuracy(lat8192):
+    """The trained network against the method without it: on the p=3, r=3,
+    g=4, n=10^6 mixture, the log-likelihood error of the surrogate E-step (judge:
+    the plain lattice rule at 8192 points) is matched by the cheapest plain
+    lattice that is at least as accurate (RMS over three lattice shifts), and at
+    that accuracy the surrogate E-step takes less device time."""
+    torch = _torch()
+    s = binding.Surrogate(lat8192, seed=3)
+    s.cfust_surrogate_train(20_000_000, 100, batch=16384, lr=3e-3, seed=7)
+    Y, _, truth, init, _, _ = synth.workload("cfust_p3r3g4_n1000000_N2048", seed=0)
+    Yd = torch.tensor(Y, dtype=torch.float64, device="cuda")
+    ladder = [32, 64, 128, 256, 512, 1024]
+    report = []
+    for P in (init, truth):
+        judge = binding.Context(synth.make_lattice(8192, 4, seed=0), precision=binding.CFUST_FP32)
+        l_judge = judge.cfust_loglik(Yd, P)
+        sur = binding.Context(synth.make_lattice(128, 4, seed=0), precision=binding.CFUST_FP32)
+        sur.cfust_set_surrogate(s)
+        l_sur, t_sur = _timed_loglik(torch, sur, Yd, P)
+        e_sur = abs(l_sur - l_judge)
+        rms, t_plain = {}, {}
+        for N in ladder:
+            errs = []
+            for sd in range(3):
+                c = binding.Context(synth.make_lattice(N, 4, seed=sd), precision=binding.CFUST_FP32)
+                l, t = _timed_loglik(torch, c, Yd, P, reps=3 if sd == 0 else 1)
+                errs.append(l - l_judge)
+                if sd == 0:
+                    t_plain[N] = t
+            rms[N] = float(np.sqrt(np.mean(np.square(errs))))
+        ok_n = [N for N in ladder if rms[N] <= e_sur]
+        n_eq = min(ok_n) if ok_n else max(ladder)
+        report.append((e_sur, n_eq, t_sur, t_plain[n_eq], rms))
+        assert math.isfinite(l_sur)
+        assert t_sur < t_plain[n_eq], report
+    print("surrogate gain report", report)

@@ -52,7 +52,7 @@ def test_gelu_values_and_derivative():
 
 def test_domain_test_matches_cholesky_pivots():
     rng = np.random.default_rng(4)
-    x = np.column_stack([rng.uniform(-5, 5, (4000, 3)), rng.uniform(-1, 1, (4000, 3)),
+    x = np.column_stack([rng.uniform(-9, 5, (4000, 3)), rng.uniform(-1, 1, (4000, 3)),
                          rng.uniform(math.log(2), math.log(40), 4000)])
     ok = M.in_domain(x)
     for b in range(0, 4000, 7):
@@ -62,7 +62,8 @@ def test_domain_test_matches_cholesky_pivots():
             pd = bool(np.all(piv >= M.PIVOT_MIN))
         except np.linalg.LinAlgError:
             pd = False
-        ref = (pd and np.all(np.abs(x[b, :3]) <= M.C_MAX) and np.all(np.abs(x[b, 3:6]) <= M.RHO_MAX)
+        ref = (pd and np.all((x[b, :3] >= M.C_LO) & (x[b, :3] <= M.C_HI))
+               and np.all(np.abs(x[b, 3:6]) <= M.RHO_MAX)
                and M.LOGM_LO <= x[b, 6] <= M.LOGM_HI)
         assert ok[b] == ref, b
 
@@ -84,3 +85,18 @@ def test_label_limits():
     # (the lattice resolves E[1/s^2] to a few percent at this N: chi-scale singularity)
     assert np.allclose(y1[4:10], [full[0, 0], full[0, 1], full[0, 2], full[1, 1], full[1, 2], full[2, 2]],
                        atol=0.05)
+
+
+def test_net_targets_are_covariances_and_invert():
+    # the covariance form of an untruncated problem is m/(m-2) R with zero mean;
+    # a point mass at v has zero covariance
+    rng = np.random.default_rng(9)
+    y = rng.normal(size=(5, 10))
+    y[:, 0] = -np.exp(rng.normal(size=5) * 3)            # log P < 0
+    norm = np.r_[rng.normal(size=10), rng.uniform(0.5, 2, 10)]
+    assert np.allclose(M.from_net(M.net_targets(y, norm), norm), y, atol=1e-12)
+    v = np.array([0.5, -1.0, 2.0])
+    pm = np.r_[-0.25, v, [v[a] * v[b] for a, b in M.UPPER]][None, :]
+    assert np.allclose(M.net_targets(pm)[0, 4:], 0.0, atol=1e-15)
+    assert np.allclose(M.net_targets(pm)[0, 1:4], pm[0, 1:4])
+    assert np.isclose(M.net_targets(pm)[0, 0], math.log(0.25))
