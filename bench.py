@@ -479,25 +479,28 @@ def run_surrogate(args):
     torch.cuda.synchronize()
     train_s = time.perf_counter() - t0
 
-    judge = binding.Context(synth.make_lattice(8192, 4, seed=0), precision=binding.CFUST_FP32)
-    l_judge = judge.cfust_loglik(Yd, init)
-    judge.close()
     ctx_s = binding.Context(synth.make_lattice(args.sg_fallback_n, 4, seed=0), precision=binding.CFUST_FP32,
                             max_iter=args.warmup + args.steps + 1, use_graph=True, timing=True)
     ctx_s.cfust_set_surrogate(sur)
     l_sur, _ = _loglik_ms(torch, ctx_s, Yd, init)
     fallback = ctx_s.cfust_last_fallback()
-    e_sur = abs(l_sur - l_judge)
-    ladder = [32, 64, 128, 256, 512, 1024]
-    rms = {}
-    for N in ladder:
-        errs = []
-        for sd in range(3):
-            with binding.Context(synth.make_lattice(N, 4, seed=sd), precision=binding.CFUST_FP32) as c:
-                errs.append(c.cfust_loglik(Yd, init) - l_judge)
-        rms[N] = float(np.sqrt(np.mean(np.square(errs))))
-    ok_n = [N for N in ladder if rms[N] <= e_sur]
-    n_eq = min(ok_n) if ok_n else max(ladder)
+    rms, l_judge = {}, None
+    if args.sg_plain_n:
+        n_eq = args.sg_plain_n   # profiling runs: the plain lattice given, no accuracy ladder
+    else:
+        judge = binding.Context(synth.make_lattice(8192, 4, seed=0), precision=binding.CFUST_FP32)
+        l_judge = judge.cfust_loglik(Yd, init)
+        judge.close()
+        e_sur = abs(l_sur - l_judge)
+        ladder = [32, 64, 128, 256, 512, 1024]
+        for N in ladder:
+            errs = []
+            for sd in range(3):
+                with binding.Context(synth.make_lattice(N, 4, seed=sd), precision=binding.CFUST_FP32) as c:
+                    errs.append(c.cfust_loglik(Yd, init) - l_judge)
+            rms[N] = float(np.sqrt(np.mean(np.square(errs))))
+        ok_n = [N for N in ladder if rms[N] <= e_sur]
+        n_eq = min(ok_n) if ok_n else max(ladder)
 
     sampler = ClockSampler(torch.cuda.current_device())
     sampler.start()
@@ -554,7 +557,8 @@ def run_surrogate(args):
                    "step": "one EM iteration (CUDA graph replay) from the same start",
                    "l2": "flushed between timed steps"},
         "em_iters_per_s": 1.0 / step_s,
-        "loglik_error_vs_8192_point_rule": {"surrogate": l_sur - l_judge, "plain_rms_by_points": rms},
+        "loglik_error_vs_8192_point_rule": ({"surrogate": l_sur - l_judge, "plain_rms_by_points": rms}
+                                            if l_judge is not None else None),
         "plain_at_equal_accuracy": {"lattice_points": n_eq, "value": pairs / step_p, "ms_per_step": step_p * 1e3,
                                     "em_iters_per_s": 1.0 / step_p, "sweep_ms": float(np.mean(kern_p))},
         "speedup_vs_plain_at_equal_accuracy": step_p / step_s,
@@ -586,6 +590,8 @@ def main(argv=None):
     ap.add_argument("--sg-train", type=int, default=20_000_000)
     ap.add_argument("--sg-epochs", type=int, default=100)
     ap.add_argument("--sg-fallback-n", type=int, default=128)
+    ap.add_argument("--sg-plain-n", type=int, default=0,
+                    help="plain lattice points to compare with (skips the accuracy ladder; for profiling)")
     ap.add_argument("--nfits", type=int, default=256)
     args = ap.parse_args(argv)
     if args.warmup < 3:

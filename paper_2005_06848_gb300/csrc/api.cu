@@ -74,6 +74,7 @@ struct cfust_ctx {
 
   // learned surrogate E-step (not owned) and its fallback lists
   cfust_surrogate *sur = nullptr;
+  float *d_utab = nullptr;       // lattice uniforms (LatticeDev::utab)
   int *d_fb = nullptr;           // [g][n] observations left to the lattice rule
   unsigned *d_fb_cnt = nullptr;  // [g]
   int64_t fb_cap = 0;
@@ -473,6 +474,23 @@ cfust_status cfust_create(cfust_ctx **out, const cfust_opts *o, void *cuda_strea
       c->lat.sfrac[t] = 0.0;
     }
   }
+  {
+    const int r = L.dim - 1;
+    float *tab = nullptr;
+    if (cudaMalloc(&tab, sizeof(float) * (size_t)L.n * uniform_stride(r)) != cudaSuccess) {
+      g_create_error = "cudaMalloc of the lattice table failed";
+      cfust_destroy(c);
+      return CFUST_ENOMEM;
+    }
+    c->d_utab = tab;
+    c->lat.utab = tab;
+    if (launch_uniform_table(c->lat, r, tab, c->stream) != cudaSuccess ||
+        cudaStreamSynchronize(c->stream) != cudaSuccess) {
+      g_create_error = "building the lattice table failed";
+      cfust_destroy(c);
+      return CFUST_ECUDA;
+    }
+  }
   *out = c;
   return CFUST_OK;
 }
@@ -487,7 +505,7 @@ cfust_status cfust_destroy(cfust_ctx *c) {
     if (ev) cudaEventDestroy(ev);
   void *bufs[] = {c->d_params, c->d_c64, c->d_c32, c->d_chi64, c->d_chi32, c->d_status,
                   c->d_rescue_cnt, c->d_ll, c->d_trace, c->d_rescue, c->d_partials, c->d_llpart,
-                  c->d_logf, c->d_e1, c->d_e2, c->d_e3, c->d_e4, c->d_fb, c->d_fb_cnt};
+                  c->d_logf, c->d_e1, c->d_e2, c->d_e3, c->d_e4, c->d_fb, c->d_fb_cnt, c->d_utab};
   for (void *b : bufs)
     if (b) cudaFree(b);
   delete c;

@@ -85,7 +85,18 @@ struct LatticeDev {
   int sint[RMAX + 1];
   double sfrac[RMAX + 1];
   double shift[RMAX + 1];
+  // single-precision uniforms of every point for the r normal coordinates:
+  // row k = [1 - u_1 .. 1 - u_r, u_1 .. u_r, padding] with a row stride of
+  // uniform_stride(r) floats (device memory; built by launch_uniform_table)
+  const float *utab = nullptr;
 };
+
+__host__ __device__ constexpr int uniform_stride(int r) { return ((2 * r + 3) / 4) * 4; }
+
+// Fill the uniform table of `lat` for r normal coordinates into tab
+// [lat.n][uniform_stride(r)], with the same single-precision arithmetic as the
+// sweep used to form them per point.
+cudaError_t launch_uniform_table(const LatticeDev &lat, int r, float *tab, cudaStream_t st);
 
 // Precompute: factorisations, constants and chi-scale tables for every component.
 cudaError_t launch_precompute(const double *d_params, int g, int p, int r, const LatticeDev &lat,

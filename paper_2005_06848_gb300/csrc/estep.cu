@@ -51,6 +51,7 @@ struct Num<float> {
   // side of a lattice coordinate keeps its value down to where the oracle clamps
   __device__ static constexpr float umin() { return 1.1102230246251565e-16f; }
   __device__ static float lg(float x) { return logf(x); }
+  __device__ static float sq(float x) { return sqrtf(x); }
   __device__ static float ab(float x) { return fabsf(x); }
   __device__ static float mn(float x, float y) { return fminf(x, y); }
   __device__ static float mx(float x, float y) { return fmaxf(x, y); }
@@ -67,6 +68,7 @@ struct Num<double> {
   }
   __device__ static constexpr double umin() { return 1.1102230246251565e-16; }  // 2^-53
   __device__ static double lg(double x) { return log(x); }
+  __device__ static double sq(double x) { return sqrt(x); }
   __device__ static double ab(double x) { return fabs(x); }
   __device__ static double mn(double x, double y) { return fmin(x, y); }
   __device__ static double mx(double x, double y) { return fmax(x, y); }
@@ -84,6 +86,7 @@ struct EArgs {
   float fstep2[RMAX + 1];  // 2 * step
   float ftwo_sf[RMAX + 1];  // 2 * sfrac
   float fsf[RMAX + 1];      // sfrac
+  const float *utab; // lattice uniforms, [N][uniform_stride(r)] (single precision sweeps)
   const void *comp;  // CompT<T>[g]
   const void *chi;   // T[g][2][N]
   EstepOut out;
@@ -259,14 +262,18 @@ __device__ __forceinline__ bool pair_sweep(const EArgs &a, const FitView &fv, co
   constexpr int RP = R * (R + 1) / 2;
   constexpr bool PAIRED = (sizeof(T) == 4) && !DENS;
   const int N = a.N;
-  const double nud64 = c.nu + pr.d;
-  const double fA = sqrt(c.mA / nud64), fB = sqrt(c.mB / nud64);
+  // per-pair scalars, run by every lane: in the precision of the sweep (FP64
+  // divides, roots and logarithms cost 64x on this GPU, and in single
+  // precision every one of these rounds to float anyway)
+  const T nud = static_cast<T>(c.nu + pr.d);
+  const T mAT = static_cast<T>(c.mA), mBT = static_cast<T>(c.mB);
+  const T fA = M::sq(mAT / nud), fB = M::sq(mBT / nud);
   T q[R], aA[R], aB[R];
 #pragma unroll
   for (int t = 0; t < R; ++t) {
     q[t] = static_cast<T>(pr.q[t]);
-    aA[t] = static_cast<T>(-pr.q[t] * fA);
-    aB[t] = static_cast<T>(-pr.q[t] * fB);
+    aA[t] = -q[t] * fA;
+    aB[t] = -q[t] * fB;
   }
   T Lc[RP], Li[R];
 #pragma unroll
@@ -306,17 +313,37 @@ __device__ __forceinline__ bool pair_sweep(const EArgs &a, const FitView &fv, co
 
   for (int k = lane; k < N; k += WARP) {
     // 1 - u_t = |2 m - N + 2 sfrac| / N and u_t = 2 min(m + sfrac, N - m - sfrac) / N,
-    // each formed from an exact integer and the fraction so the small side stays exact
+    // each formed from an exact integer and the fraction so the small side stays exact;
+    // in single precision they come from the lattice's table (the same numbers)
     T um[R], uu[R];
+    if constexpr (sizeof(T) == 4) {
+      constexpr int US = uniform_stride(R);
+      const float4 *row = reinterpret_cast<const float4 *>(a.utab) + (size_t)k * (US / 4);
+      float v[US];
 #pragma unroll
-    for (int t = 0; t < R; ++t) {
-      const T sf = lat_sf<T>(a, t + 1);
-      const T mm = T(0.5) * (fm[t] + fN);
-      const T lo = mm + sf, hi = (fN - mm) - sf;
-      um[t] = M::mn(M::mx(M::ab(fm[t] + lat_two_sf<T>(a, t + 1)) * invN, umin), umax);
-      uu[t] = M::mx(T(2) * M::mn(lo, hi) * invN, umin);
-      fm[t] += lat_step2<T>(a, t + 1);
-      if (fm[t] >= fN) fm[t] -= T(2) * fN;
+      for (int q4 = 0; q4 < US / 4; ++q4) {
+        const float4 f4 = __ldg(row + q4);
+        v[4 * q4] = f4.x;
+        v[4 * q4 + 1] = f4.y;
+        v[4 * q4 + 2] = f4.z;
+        v[4 * q4 + 3] = f4.w;
+      }
+#pragma unroll
+      for (int t = 0; t < R; ++t) {
+        um[t] = v[t];
+        uu[t] = v[R + t];
+      }
+    } else {
+#pragma unroll
+      for (int t = 0; t < R; ++t) {
+        const T sf = lat_sf<T>(a, t + 1);
+        const T mm = T(0.5) * (fm[t] + fN);
+        const T lo = mm + sf, hi = (fN - mm) - sf;
+        um[t] = M::mn(M::mx(M::ab(fm[t] + lat_two_sf<T>(a, t + 1)) * invN, umin), umax);
+        uu[t] = M::mx(T(2) * M::mn(lo, hi) * invN, umin);
+        fm[t] += lat_step2<T>(a, t + 1);
+        if (fm[t] >= fN) fm[t] -= T(2) * fN;
+      }
     }
     if constexpr (PAIRED) {
       // passes A and B side by side in FP32x2: .x is pass A, .y pass B
@@ -423,9 +450,9 @@ __device__ __forceinline__ bool pair_sweep(const EArgs &a, const FitView &fv, co
   if (DENS) return false;
 
   const bool ok = (SA > T(0)) && (SB > T(0));
-  const T ratio = static_cast<T>(c.mA / nud64);
+  const T ratio = mAT / nud;
   const T e1 = ok ? ratio * (SB / SA) : T(0);
-  const T sig = static_cast<T>(sqrt(nud64 / c.mB));
+  const T sig = M::sq(nud / mBT);
   const T iSB = ok ? T(1) / SB : T(0);
   T LEV[R];
 #pragma unroll
@@ -437,9 +464,9 @@ __device__ __forceinline__ bool pair_sweep(const EArgs &a, const FitView &fv, co
   }
   T e2;
   if (e2lat)
-    e2 = ok ? SL / SA - static_cast<T>(log(nud64)) : T(0);
+    e2 = ok ? SL / SA - M::lg(nud) : T(0);
   else
-    e2 = ok ? e1 - static_cast<T>(log(0.5 * nud64) + c.mA / nud64 - c.psiA) : T(0);
+    e2 = ok ? e1 - (M::lg(T(0.5) * nud) + ratio - static_cast<T>(c.psiA)) : T(0);
 
   // lane-parallel stores: lane 0 wrote logf; lane 1 e1, lane 2 e2, lanes 3.. e3 then e4
   if (lane == 1) store<OT>(fv.out.e1, ij, e1);
@@ -567,12 +594,16 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? CFUST_ESTEP_MINB : 1) es
 // component of observation j in place (values, or upper bounds for pairs still
 // to be swept, +inf where none is known), a pair whose log pi_i + log f_ij
 // trails the best component by more than 30 has tau_ij < exp(-30); it gets
-// log f = -inf and zero expectations instead of a sweep.
+// log f = -inf and zero expectations instead of a sweep.  Unknown entries do
+// not count towards the best (that only makes the test more cautious).
 template <int R, bool DENS>
 __device__ bool triage_listed(const FitView &fv, int i, int64_t j) {
   const float *lf = reinterpret_cast<const float *>(fv.out.logf);
   float best = -INFINITY;
-  for (int h = 0; h < fv.g; ++h) best = fmaxf(best, logf((float)fv.pi[h]) + lf[(int64_t)h * fv.n + j]);
+  for (int h = 0; h < fv.g; ++h) {
+    const float v = lf[(int64_t)h * fv.n + j];
+    if (v < INFINITY) best = fmaxf(best, logf((float)fv.pi[h]) + v);
+  }
   const float mine = logf((float)fv.pi[i]) + lf[(int64_t)i * fv.n + j];
   if (!(isfinite(best) && mine < best - 30.0f)) return false;
   const int64_t ij = (int64_t)i * fv.n + j;
@@ -1153,6 +1184,7 @@ cudaError_t launch_estep_batched(int precision, const BatchDev &b, int p, int r,
     a.ftwo_sf[t] = (float)(2.0 * lat.sfrac[t]);
     a.fsf[t] = (float)lat.sfrac[t];
   }
+  a.utab = lat.utab;
   a.e2_mode = e2_mode;
   a.ppw = ppw < 1 ? 1 : (ppw > 32 ? 32 : ppw);
   a.rescue_list = rescue_list;
@@ -1171,6 +1203,25 @@ cudaError_t launch_estep_batched(int precision, const BatchDev &b, int p, int r,
   return density_only
              ? dispatch_batched<float, true>(r, a, b, items, nitems, item_counter, ctas_per_sm, st, true, c64, chi64, tm)
              : dispatch_batched<float, false>(r, a, b, items, nitems, item_counter, ctas_per_sm, st, true, c64, chi64, tm);
+}
+
+__global__ void uniform_table_kernel(LatticeDev lat, int r, int us, float *tab) {
+  const int k = blockIdx.x * blockDim.x + threadIdx.x;
+  const int N = lat.n;
+  if (k >= N) return;
+  const float fN = (float)N, invN = 1.0f / fN;
+  const float umin = 1.1102230246251565e-16f, umax = 1.0f - 5.9604644775390625e-08f;
+  float *row = tab + (int64_t)k * us;
+  for (int t = 0; t < r; ++t) {
+    const int m = (int)(((int64_t)k * lat.z[t + 1] + lat.sint[t + 1]) % N);
+    const float fm = (float)(2 * m - N);
+    const float sf = (float)lat.sfrac[t + 1], two_sf = (float)(2.0 * lat.sfrac[t + 1]);
+    const float mm = 0.5f * (fm + fN);
+    const float lo = mm + sf, hi = (fN - mm) - sf;
+    row[t] = fminf(fmaxf(fabsf(fm + two_sf) * invN, umin), umax);
+    row[r + t] = fmaxf(2.0f * fminf(lo, hi) * invN, umin);
+  }
+  for (int t = 2 * r; t < us; ++t) row[t] = 0.0f;
 }
 
 template <bool DENS>
@@ -1217,6 +1268,7 @@ EArgs make_args(const double *Y, int64_t n, int g, int p, const LatticeDev &lat,
     a.fsf[t] = (float)lat.sfrac[t];
   }
   a.out = out;
+  a.utab = lat.utab;
   a.e2_mode = e2_mode;
   a.ppw = 1;
   a.staged = 1;
@@ -1243,6 +1295,12 @@ cudaError_t launch_estep_list(const double *Y, int64_t n, int g, int p, int r, c
   a.chi = chi32;
   return density_only ? launch_list_r3<true>(a, g, n, list, count, c64, chi64, st)
                       : launch_list_r3<false>(a, g, n, list, count, c64, chi64, st);
+}
+
+cudaError_t launch_uniform_table(const LatticeDev &lat, int r, float *tab, cudaStream_t st) {
+  if (lat.n <= 0 || r < 1 || r > RMAX) return cudaErrorInvalidValue;
+  uniform_table_kernel<<<(lat.n + 255) / 256, 256, 0, st>>>(lat, r, uniform_stride(r), tab);
+  return cudaGetLastError();
 }
 
 cudaError_t launch_estep(int precision, const double *Y, int64_t n, int g, int p, int r,

@@ -53,16 +53,14 @@ __device__ void precompute_component(const double *params, int g, int p, int r, 
   const double nu = pv.nu[i];
   const int N = lat.n;
 
-  // chi-scale tables: [2][N]
-  for (int k = bx * blockDim.x + threadIdx.x; k < N; k += nbx * blockDim.x) {
+  // chi-scale tables: [2][N], one quantile per thread (pass A rows, then pass B)
+  for (int kk = bx * blockDim.x + threadIdx.x; kk < 2 * N; kk += nbx * blockDim.x) {
+    const int k = kk < N ? kk : kk - N;
     const double u0 = lattice_coord(k, lat.z[0], N, lat.shift[0]);
-    const double mA = nu + p, mB = nu + p + 2.0;
-    const double sA = sqrt(2.0 * inc_gamma_inv(0.5 * mA, u0) / mA);
-    const double sB = sqrt(2.0 * inc_gamma_inv(0.5 * mB, u0) / mB);
-    t64[k] = sA;
-    t64[N + k] = sB;
-    t32[k] = (float)sA;
-    t32[N + k] = (float)sB;
+    const double m = nu + p + (kk < N ? 0.0 : 2.0);
+    const double sc = sqrt(2.0 * inc_gamma_inv(0.5 * m, u0) / m);
+    t64[kk] = sc;
+    t32[kk] = (float)sc;
   }
 
   if (bx != 0 || threadIdx.x != 0) return;
@@ -172,8 +170,8 @@ __global__ void precompute_batched_kernel(BatchDev b, int p, int r, LatticeDev l
 cudaError_t launch_precompute_batched(const BatchDev &b, int p, int r, const LatticeDev &lat,
                                       CompT<double> *c64, CompT<float> *c32, double *chi64, float *chi32,
                                       cudaStream_t st) {
-  const int threads = 128;
-  int bx = (lat.n + threads - 1) / threads;
+  const int threads = 64;
+  int bx = (2 * lat.n + threads - 1) / threads;
   if (bx < 1) bx = 1;
   precompute_batched_kernel<<<dim3(bx, b.G), threads, 0, st>>>(b, p, r, lat, c64, c32, chi64, chi32);
   return cudaGetLastError();
@@ -182,8 +180,8 @@ cudaError_t launch_precompute_batched(const BatchDev &b, int p, int r, const Lat
 cudaError_t launch_precompute(const double *d_params, int g, int p, int r, const LatticeDev &lat,
                               CompT<double> *c64, CompT<float> *c32, double *chi64, float *chi32,
                               int *d_status, cudaStream_t st) {
-  const int threads = 128;
-  int bx = (lat.n + threads - 1) / threads;
+  const int threads = 64;
+  int bx = (2 * lat.n + threads - 1) / threads;
   if (bx < 1) bx = 1;
   dim3 grid(bx, g);
   precompute_kernel<<<grid, threads, 0, st>>>(d_params, g, p, r, lat, c64, c32, chi64, chi32,

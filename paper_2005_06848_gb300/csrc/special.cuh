@@ -6,66 +6,123 @@
 //    continued fraction of Q otherwise (DLMF 8.9.2), evaluated with the modified
 //    Lentz method (Thompson & Barnett 1986).
 //  - inc_gamma_inv: x with P(a, x) = u, from a Wilson-Hilferty (1931) start and
-//    bracketed Halley steps; the upper-tail equation Q(a, x) = 1 - u is solved
-//    for u >= 1/2 so that both tails keep full relative accuracy.
+//    bracketed Halley steps, first in single precision, then in double; the
+//    upper-tail equation Q(a, x) = 1 - u is solved for u >= 1/2 so that both
+//    tails keep full relative accuracy.
 //  - digamma: the recurrence psi(x) = psi(x + 1) - 1/x (DLMF 5.5.2) up to
 //    x >= 10, then the asymptotic series in Bernoulli numbers (DLMF 5.11.2).
 //
-// lgamma, log, exp and normcdfinv are CUDA's own functions, called as-is.
+// lgamma(f), log(f), exp(f) and normcdfinv are CUDA's own functions, called as-is.
 #pragma once
 
 #include <cuda_runtime.h>
 
 namespace cfust {
 
-__device__ inline void inc_gamma_pq(double a, double x, double *P, double *Q) {
-  if (!(x > 0.0)) {
-    *P = 0.0;
-    *Q = 1.0;
+// Precision traits of the incomplete-gamma routines.
+template <typename T>
+struct GammaT;
+template <>
+struct GammaT<double> {
+  __device__ static double lgam(double x) { return lgamma(x); }
+  __device__ static double ex(double x) { return exp(x); }
+  __device__ static double lg(double x) { return log(x); }
+  static constexpr double series_eps = 1e-17, cf_eps = 1e-16, tiny = 1e-300, big = 1e308;
+};
+template <>
+struct GammaT<float> {
+  __device__ static float lgam(float x) { return lgammaf(x); }
+  __device__ static float ex(float x) { return expf(x); }
+  __device__ static float lg(float x) { return logf(x); }
+  static constexpr float series_eps = 1e-8f, cf_eps = 1e-7f, tiny = 1e-30f, big = 3e38f;
+};
+
+template <typename T>
+__device__ inline void inc_gamma_pq_t(T a, T x, T *P, T *Q) {
+  using G = GammaT<T>;
+  if (!(x > T(0))) {
+    *P = T(0);
+    *Q = T(1);
     return;
   }
-  const double lpre = a * log(x) - x - lgamma(a);
-  if (x < a + 1.0) {
-    double term = 1.0 / a, sum = term, den = a;
+  const T lpre = a * G::lg(x) - x - G::lgam(a);
+  if (x < a + T(1)) {
+    T term = T(1) / a, sum = term, den = a;
     for (int k = 0; k < 1000; ++k) {
-      den += 1.0;
+      den += T(1);
       term *= x / den;
       sum += term;
-      if (fabs(term) <= fabs(sum) * 1e-17) break;
+      if (fabs(term) <= fabs(sum) * G::series_eps) break;
     }
-    const double p = sum * exp(lpre);
+    const T p = sum * G::ex(lpre);
     *P = p;
-    *Q = 1.0 - p;
+    *Q = T(1) - p;
   } else {
-    const double tiny = 1e-300;
-    double b = x + 1.0 - a;
-    double c = 1.0 / tiny;
-    double d = 1.0 / b;
-    double h = d;
+    const T tiny = G::tiny;
+    T b = x + T(1) - a;
+    T c = T(1) / tiny;
+    T d = T(1) / b;
+    T h = d;
     for (int k = 1; k < 1000; ++k) {
-      const double an = -(double)k * ((double)k - a);
-      b += 2.0;
+      const T an = -(T)k * ((T)k - a);
+      b += T(2);
       d = an * d + b;
       if (fabs(d) < tiny) d = tiny;
       c = b + an / c;
       if (fabs(c) < tiny) c = tiny;
-      d = 1.0 / d;
-      const double delta = d * c;
+      d = T(1) / d;
+      const T delta = d * c;
       h *= delta;
-      if (fabs(delta - 1.0) <= 1e-16) break;
+      if (fabs(delta - T(1)) <= G::cf_eps) break;
     }
-    const double q = exp(lpre) * h;
+    const T q = G::ex(lpre) * h;
     *Q = q;
-    *P = 1.0 - q;
+    *P = T(1) - q;
   }
 }
 
+__device__ inline void inc_gamma_pq(double a, double x, double *P, double *Q) {
+  inc_gamma_pq_t<double>(a, x, P, Q);
+}
+
+// Bracketed Halley iteration for P(a, x) = u (or Q(a, x) = uc, uc = 1 - u,
+// when `upper`) from the start x; stops when a step moves x by at most rtol
+// relative.
+template <typename T>
+__device__ inline T inc_gamma_halley(T a, T u, T uc, bool upper, T x, int max_it, T rtol) {
+  using G = GammaT<T>;
+  const T lga = G::lgam(a);
+  T lo = T(0), hi = G::big;
+  for (int it = 0; it < max_it; ++it) {
+    T P, Q;
+    inc_gamma_pq_t<T>(a, x, &P, &Q);
+    const T f = upper ? (uc - Q) : (P - u);  // increasing in x
+    if (f == T(0)) return x;
+    if (f < T(0)) lo = x; else hi = x;
+    const T dens = G::ex((a - T(1)) * G::lg(x) - x - lga);  // dP/dx
+    T xn;
+    if (dens > T(0) && isfinite(dens)) {
+      const T ratio = f / dens;
+      T corr = T(1) - T(0.5) * ratio * ((a - T(1)) / x - T(1));
+      if (!(corr > T(0.5))) corr = T(1);  // keep the step Newton-like when Halley is unsafe
+      xn = x - ratio / corr;
+    } else {
+      xn = (hi < G::big) ? T(0.5) * (lo + hi) : T(2) * x;
+    }
+    if (!(xn > lo && xn < hi)) xn = (hi < G::big) ? T(0.5) * (lo + hi) : T(2) * x;
+    if (fabs(xn - x) <= rtol * xn) return xn;
+    x = xn;
+  }
+  return x;
+}
+
 // Inverse of the regularised lower incomplete gamma function in x, a > 0,
-// 0 < u < 1.  Returns x >= 0.
+// 0 < u < 1.  Returns x >= 0.  The root is first found in single precision
+// (to about 1e-6) and then polished in double, so most of the work runs at
+// the single-precision rate.
 __device__ inline double inc_gamma_inv(double a, double u) {
   const bool upper = u >= 0.5;
   const double uc = 1.0 - u;  // exact for u >= 1/2
-  const double lga = lgamma(a);
   // Wilson-Hilferty: chi^2_{2a} / (2a) ~ (1 - 1/(9a) + z / (3 sqrt(a)))^3.
   const double zq = upper ? -normcdfinv(uc) : normcdfinv(u);
   const double t = 1.0 / (9.0 * a);
@@ -77,28 +134,9 @@ __device__ inline double inc_gamma_inv(double a, double u) {
     if (!(x > 0.0) || xs < x) x = xs;
   }
   if (!(x > 0.0)) x = a;
-  double lo = 0.0, hi = 1e308;
-  for (int it = 0; it < 100; ++it) {
-    double P, Q;
-    inc_gamma_pq(a, x, &P, &Q);
-    const double f = upper ? (uc - Q) : (P - u);  // increasing in x
-    if (f == 0.0) return x;
-    if (f < 0.0) lo = x; else hi = x;
-    const double dens = exp((a - 1.0) * log(x) - x - lga);  // dP/dx
-    double xn;
-    if (dens > 0.0 && isfinite(dens)) {
-      const double ratio = f / dens;
-      double corr = 1.0 - 0.5 * ratio * ((a - 1.0) / x - 1.0);
-      if (!(corr > 0.5)) corr = 1.0;  // keep the step Newton-like when Halley is unsafe
-      xn = x - ratio / corr;
-    } else {
-      xn = (hi < 1e308) ? 0.5 * (lo + hi) : 2.0 * x;
-    }
-    if (!(xn > lo && xn < hi)) xn = (hi < 1e308) ? 0.5 * (lo + hi) : 2.0 * x;
-    if (fabs(xn - x) <= 4e-16 * xn) return xn;
-    x = xn;
-  }
-  return x;
+  const float xf = inc_gamma_halley<float>((float)a, (float)u, (float)uc, upper, (float)x, 30, 1e-6f);
+  if (xf > 0.0f && isfinite(xf)) x = (double)xf;
+  return inc_gamma_halley<double>(a, u, uc, upper, x, 100, 4e-16);
 }
 
 __device__ inline double digamma(double x) {

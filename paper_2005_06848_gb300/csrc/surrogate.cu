@@ -515,7 +515,7 @@ struct InferGroup {
   bf16 X[TROWS * XP];
   bf16 Hb[TROWS * HP];
   float O[TROWS * OP];
-  float logt[TROWS], nud[TROWS], q[3 * TROWS];
+  float logt[TROWS], nud[TROWS], q[3 * TROWS], cmax[TROWS];
   int ok[TROWS];
 };
 constexpr size_t INFER_SMEM = sizeof(InferWeights) + GROUPS * sizeof(InferGroup);
@@ -584,9 +584,30 @@ __device__ __forceinline__ void store_gelu(bf16 *Hb, const float *bias, int w, i
 // limits a_A) or 1 (nu + p + 2, a_B).  X = L V with L = chol(Lambda) is
 // t_3(0, Lambda, m); with D = diag(Lambda), X' = D^{-1/2} X is t_3(0, R, m)
 // and L V > a holds exactly when X' > c = D^{-1/2} a.
+// Nearest-structure PSD repair of a predicted 3x3 covariance (upper order
+// 00 01 02 11 12 22): LDL^T with every pivot floored at PSD_FLOOR, rebuilt.
+// A positive definite input comes back unchanged up to rounding; a
+// prediction that is not keeps e4 positive semi-definite, as the exact
+// conditional moments are.
+constexpr float PSD_FLOOR = 1e-6f;
+__device__ __forceinline__ void psd_repair3(float *v) {
+  const float d0 = fmaxf(v[0], PSD_FLOOR);
+  const float l10 = v[1] / d0, l20 = v[2] / d0;
+  const float d1 = fmaxf(v[3] - l10 * l10 * d0, PSD_FLOOR);
+  const float l21 = (v[4] - l20 * l10 * d0) / d1;
+  const float d2 = fmaxf(v[5] - l20 * l20 * d0 - l21 * l21 * d1, PSD_FLOOR);
+  v[0] = d0;
+  v[1] = l10 * d0;
+  v[2] = l20 * d0;
+  v[3] = fmaf(l10 * l10, d0, d1);
+  v[4] = fmaf(l20 * l10, d0, l21 * d1);
+  v[5] = fmaf(l20 * l20, d0, fmaf(l21 * l21, d1, d2));
+}
+
 struct RowProblem {
   float c[3], R[3], logm;  // network input (c clamped into the box)
   float logt, nud, q[3];
+  float cmaxA;  // largest coordinate of pass A's point (unclamped)
   int kind;  // 2: the pair (both passes) lies in the training domain;
              // 1: only its truncation point leaves the box (log T is bounded
              //    through the clamped point); 0: R or the dof leave the domain
@@ -634,6 +655,8 @@ __device__ __forceinline__ RowProblem row_problem(const CompT<float> &c, const d
   const float m = pass ? mB : mA;
   const float f = -sqrtf(m / rp.nud);
   const float cr[3] = {q0 * f * i0, q1 * f * i1, q2 * f * i2};
+  const float fA = -sqrtf(mA / rp.nud);
+  rp.cmaxA = fmaxf(q0 * fA * i0, fmaxf(q1 * fA * i1, q2 * fA * i2));
   // pass B has the larger limits (same signs): its box decides the pair
   const float fB = -sqrtf(mB / rp.nud);
   const float cB[3] = {q0 * fB * i0, q1 * fB * i1, q2 * fB * i2};
@@ -720,6 +743,7 @@ __global__ void __launch_bounds__(GROUP_THREADS * GROUPS, 1)
           G.q[3 * pair + 1] = rp.q[1];
           G.q[3 * pair + 2] = rp.q[2];
           G.ok[pair] = rp.kind;
+          G.cmax[pair] = rp.cmaxA;
           if (rp.kind != 2) {
             const unsigned slot = atomicAdd(fb_count + i, 1u);
             fb_list[(int64_t)i * n + slot] = (int)j;
@@ -792,7 +816,20 @@ __global__ void __launch_bounds__(GROUP_THREADS * GROUPS, 1)
       // pairs left to the lattice rule carry an upper bound of log f for its
       // triage: log T is decreasing in every c_t, so the network's value at
       // the box-clamped point plus a margin bounds it; none without a domain
-      if (kind == 1) static_cast<float *>(out.logf)[ij] = G.logt[pair] + logTA + UB_MARGIN;
+      if (kind == 1) {
+        // and P(X > c) <= P(X_t > c_t) <= (m + c_t^2) f_m(c_t) / ((m - 1) c_t)
+        // for c_t > 0, f_m the t_m density (from d/dx[(m + x^2) f_m(x)] =
+        // -(m - 1) x f_m(x)); the bound decreases in c_t, so the largest
+        // coordinate of pass A's point gives the tightest one
+        float ub = logTA + UB_MARGIN;
+        const float cm = G.cmax[pair], m = (float)c.mA;
+        if (cm > 0.f && m > 1.f) {
+          const float lnorm = lgammaf(0.5f * (m + 1.f)) - lgammaf(0.5f * m) - 0.5f * logf(m * 3.14159265f);
+          const float lb = logf((m + cm * cm) / ((m - 1.f) * cm)) + lnorm - 0.5f * (m + 1.f) * log1pf(cm * cm / m);
+          ub = fminf(ub, lb + 1e-3f);
+        }
+        static_cast<float *>(out.logf)[ij] = G.logt[pair] + ub;
+      }
       if (kind == 0) static_cast<float *>(out.logf)[ij] = INFINITY;
       if (kind == 2) {
         static_cast<float *>(out.logf)[ij] = G.logt[pair] + logTA;
@@ -823,15 +860,19 @@ __global__ void __launch_bounds__(GROUP_THREADS * GROUPS, 1)
           for (int t = 0; t < 3; ++t)
             static_cast<float *>(out.e3)[((int64_t)i * 3 + t) * n + j] = e1 * fmaf(sig, LEV[t], qp[t]);
           // e4 in lower-triangle order (0,0) (1,0) (1,1) (2,0) (2,1) (2,2); the
-          // network's second moments come in upper order 00 01 02 11 12 22
+          // network's covariance comes in upper order 00 01 02 11 12 22
           constexpr int UP[3][3] = {{0, 1, 2}, {1, 3, 4}, {2, 4, 5}};
+          float cv[6];
+#pragma unroll
+          for (int u = 0; u < 6; ++u) cv[u] = fmaf(oB[4 + u], sdv[4 + u], mean[4 + u]);
+          psd_repair3(cv);
 #pragma unroll
           for (int t = 0; t < 3; ++t)
 #pragma unroll
             for (int h = 0; h <= t; ++h) {
               const int u = UP[t][h];
               // the network gives the covariance; E[X'_h X'_t] = cov + E[X'_h] E[X'_t]
-              const float S = sD[t] * sD[h] * fmaf(EXs[h], EXs[t], fmaf(oB[4 + u], sdv[4 + u], mean[4 + u]));
+              const float S = sD[t] * sD[h] * fmaf(EXs[h], EXs[t], cv[u]);
               const float exx = qp[t] * qp[h] + sig * (qp[t] * LEV[h] + LEV[t] * qp[h]) + sig * sig * S;
               static_cast<float *>(out.e4)[((int64_t)i * 6 + t * (t + 1) / 2 + h) * n + j] = e1 * exx;
             }

@@ -143,6 +143,17 @@ def _standardised(Y, params, i):
     return d, q, log_tp, sD, xA, xB, inside, edge
 
 
+def _psd_repair(v, floor=1e-6):
+    v = np.asarray(v, dtype=np.float64)
+    d0 = np.maximum(v[:, 0], floor)
+    l10, l20 = v[:, 1] / d0, v[:, 2] / d0
+    d1 = np.maximum(v[:, 3] - l10 * l10 * d0, floor)
+    l21 = (v[:, 4] - l20 * l10 * d0) / d1
+    d2 = np.maximum(v[:, 5] - l20 * l20 * d0 - l21 * l21 * d1, floor)
+    return np.column_stack([d0, l10 * d0, l20 * d0, l10 * l10 * d0 + d1, l20 * l10 * d0 + l21 * d1,
+                            l20 * l20 * d0 + l21 * l21 * d1 + d2])
+
+
 def test_surrogate_estep_is_the_expectations_of_the_network_outputs(lat8192):
     """Pairs in the domain: log f and e1..e4 are the E-step formulas (the
     oracle's, in FP64) applied to the network's own outputs for the pair's two
@@ -171,9 +182,13 @@ def test_surrogate_estep_is_the_expectations_of_the_network_outputs(lat8192):
             out = ~inside & ~edge
             n_in += int(inside.sum())
             logf = 3 * math.log(2) + log_tp + yA[:, 0]
+            # covariance of pass B, made positive semi-definite the way the
+            # E-step does (LDL^T with pivots floored at 1e-6), then E[X X^T]
+            cov = MO.net_targets(yB)[:, 4:]
+            cov = _psd_repair(cov)
             S = np.zeros((len(d), 3, 3))
             for k, (a, b) in enumerate(MO.UPPER):
-                S[:, a, b] = S[:, b, a] = yB[:, 4 + k]
+                S[:, a, b] = S[:, b, a] = cov[:, k] + yB[:, 1 + a] * yB[:, 1 + b]
             LEV = sD * yB[:, 1:4]
             LEVVL = S * np.outer(sD, sD)[None]
             e1, e2, e3, e4 = O.expectations(d, q, nu[i], p, np.exp(yA[:, 0]), np.exp(yB[:, 0]), LEV, LEVVL)
