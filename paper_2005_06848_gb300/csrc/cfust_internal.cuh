@@ -41,6 +41,10 @@ struct CompT {
   double logmA;           // log(nu + p)
   T L[RMAX * RMAX];       // r x r, stride RMAX, lower triangle used
   T Linv[RMAX];           // 1 / L_tt
+  // single-precision copies for code that runs in float throughout (the
+  // surrogate E-step), so it converts nothing per pair
+  float fmu[PMAX], fA[PMAX * PMAX], fB[RMAX * PMAX];
+  float fc0, fnu, fmA, fmB, fpsiA;
 };
 
 // Layout of the device parameter block (doubles): pi[g] mu[g][p] Sigma[g][p][p]

@@ -96,6 +96,11 @@ __device__ __forceinline__ void posterior_block(const PosteriorArgs &a, int c0, 
   int bad = 0;
   const int64_t ntiles = (n + TJ - 1) / TJ;
   const bool first_chunk = (c0 == 0);
+  // log pi_i once per block (a double logarithm costs ~40 operations of the
+  // 1/64-rate pipe; per observation it was taken three times per component)
+  __shared__ double lpi[CFUST_GMAX];
+  for (int i = threadIdx.x; i < g; i += THREADS) lpi[i] = log(a.pi[i]);
+  __syncthreads();
 
   for (int64_t tile = blk; tile < ntiles; tile += nblk) {
     const int64_t j0 = tile * TJ;
@@ -107,17 +112,24 @@ __device__ __forceinline__ void posterior_block(const PosteriorArgs &a, int c0, 
       const int64_t j = j0 + jj;
       if (logf != nullptr) {
         double mx = -INFINITY;
-        for (int i = 0; i < g; ++i) mx = fmax(mx, log(a.pi[i]) + (double)logf[(int64_t)i * n + j]);
+        for (int i = 0; i < g; ++i) mx = fmax(mx, lpi[i] + (double)logf[(int64_t)i * n + j]);
+        // tau_ij = exp(a_i - mx) / sum_h exp(a_h - mx): the exponentials of the
+        // sum are kept (in the tile's rows) and scaled once the sum is known
         double s = 0.0;
-        for (int i = 0; i < g; ++i) s += exp(log(a.pi[i]) + (double)logf[(int64_t)i * n + j] - mx);
+        for (int i = 0; i < g; ++i) {
+          const double e = exp(lpi[i] + (double)logf[(int64_t)i * n + j] - mx);
+          s += e;
+          if (a.want_sums && i >= c0 && i < c1) ws[((i - c0) * TJ + jj) * WR] = e;
+        }
         const double lse = mx + log(s);
         if (!isfinite(lse)) bad = 1;
         llacc += lse;
-        for (int i = 0; i < g; ++i) {
-          const double t = exp(log(a.pi[i]) + (double)logf[(int64_t)i * n + j] - lse);
-          if (tau_out != nullptr && first_chunk) tau_out[(int64_t)i * n + j] = (ET)t;
-          if (a.want_sums && i >= c0 && i < c1) ws[((i - c0) * TJ + jj) * WR] = t;
-        }
+        const double inv = 1.0 / s;
+        if (a.want_sums)
+          for (int i = c0; i < c1; ++i) ws[((i - c0) * TJ + jj) * WR] *= inv;
+        if (tau_out != nullptr && first_chunk)
+          for (int i = 0; i < g; ++i)
+            tau_out[(int64_t)i * n + j] = (ET)(exp(lpi[i] + (double)logf[(int64_t)i * n + j] - mx) * inv);
       } else if (a.want_sums) {
         for (int i = c0; i < c1; ++i) ws[((i - c0) * TJ + jj) * WR] = (double)tau_in[(int64_t)i * n + j];
       }
@@ -222,47 +234,34 @@ __device__ double nu_equation(double nu, double c) {
   return log(0.5 * nu) - digamma(0.5 * nu) + 1.0 + c;
 }
 
-// Root of log(nu/2) - psi(nu/2) + 1 + c = 0 in [lo, hi] by bisection; the
-// left side decreases in nu, so the bound is returned when there is no sign change.
-__device__ double solve_nu(double c, double lo, double hi) {
+// Root of log(nu/2) - psi(nu/2) + 1 + c = 0 in [lo, hi]; the left side
+// decreases in nu, so the bound is returned when there is no sign change.
+// Every thread of the block evaluates one interior point of the bracket per
+// round and the count of positive values picks the subinterval holding the
+// sign change: the bracket shrinks (blockDim.x + 1)-fold per round.  All
+// threads of the block must call it with the same arguments.
+__device__ double solve_nu_block(double c, double lo, double hi) {
   if (nu_equation(hi, c) >= 0.0) return hi;
   if (nu_equation(lo, c) <= 0.0) return lo;
-  for (int it = 0; it < 200; ++it) {
-    const double mid = 0.5 * (lo + hi);
-    if (mid <= lo || mid >= hi) break;
-    if (nu_equation(mid, c) > 0.0) lo = mid; else hi = mid;
-    if (hi - lo <= 2e-16 * hi) break;
+  const int T = blockDim.x;
+  for (int round = 0; round < 60; ++round) {
+    const double w = (hi - lo) / (double)(T + 1);
+    const double x = lo + (double)(threadIdx.x + 1) * w;
+    const int npos = __syncthreads_count(nu_equation(x, c) > 0.0);
+    const double nlo = (npos == 0) ? lo : lo + (double)npos * w;
+    const double nhi = (npos == T) ? hi : lo + (double)(npos + 1) * w;
+    lo = nlo;
+    hi = nhi;
+    if (!(hi - lo > 2e-16 * hi)) break;
   }
   return 0.5 * (lo + hi);
 }
 
-// Conditional-maximisation update of component i of one fit from the
-// per-block partial sums (block of 128 threads).
-__device__ void mstep_finalize_block(const double *partials, int nb, int g, int p, int r, int64_t n,
-                                     double nu_min, double nu_max, double *params, int *status, int i) {
-  __shared__ double S[3 + PMAX + RMAX + PMAX * RMAX + RMAX * (RMAX + 1) / 2 + PMAX * (PMAX + 1) / 2];
-  __shared__ double red[128];
-  const int K = sums_width(p, r);
-  for (int e = threadIdx.x; e < K; e += blockDim.x) {
-    double s = 0.0;
-    for (int b = 0; b < nb; ++b) s += partials[(int64_t)b * g * K + (int64_t)i * K + e];
-    S[e] = s;
-  }
-  // total posterior weight over all components (= n when every tau row sums to 1)
-  double tw = 0.0;
-  for (int q = threadIdx.x; q < g * nb; q += blockDim.x) {
-    const int ic = q / nb, b = q % nb;
-    tw += partials[(int64_t)b * g * K + (int64_t)ic * K];
-  }
-  red[threadIdx.x] = tw;
-  __syncthreads();
-  for (int h = 64; h > 0; h >>= 1) {
-    if (threadIdx.x < h) red[threadIdx.x] += red[threadIdx.x + h];
-    __syncthreads();
-  }
-  if (threadIdx.x != 0) return;
-  const double total_weight = red[0];
-
+// Thread 0 of the finalize block: pi, mu, Delta, Sigma of component i from its
+// sums S (Algorithm 3); false (status flagged) when the update is not defined.
+// *nu_c receives the constant S8 / S1 of the nu equation.
+__device__ bool mstep_update_thread0(const double *S, double total_weight, int g, int p, int r, int64_t n,
+                                     double *params, int *status, int i, double *nu_c) {
   const int rp = r * (r + 1) / 2;
   const double S1 = S[0], S2 = S[1];
   const double *S3 = S + 2;
@@ -273,7 +272,7 @@ __device__ void mstep_finalize_block(const double *partials, int nb, int g, int 
   const double S8 = S7p[p * (p + 1) / 2];
   if (!(S1 > 1e-10 * (double)n) || !(S2 > 0.0)) {
     atomicOr(status, ERR_DEGENERATE);
-    return;
+    return false;
   }
   ParamView pv = param_view(params, g, p, r);
   double *mu = pv.mu + (int64_t)i * p;
@@ -294,7 +293,7 @@ __device__ void mstep_finalize_block(const double *partials, int nb, int g, int 
     for (int h = 0; h < r; ++h) Lc[t * RMAX + h] = S6[t * RMAX + h];
   if (!chol_inplace(Lc, r, RMAX)) {
     atomicOr(status, ERR_NOTPD_S6);
-    return;
+    return false;
   }
   // Delta row a solves S6 x = C[a, :]^T
   for (int a = 0; a < p; ++a) {
@@ -324,7 +323,7 @@ __device__ void mstep_finalize_block(const double *partials, int nb, int g, int 
   for (int a = 0; a < p * PMAX; ++a) Lt[a] = Sn[a];
   if (!chol_inplace(Lt, p, PMAX)) {
     atomicOr(status, ERR_NOTPD_SIGMA);
-    return;
+    return false;
   }
   // pi_i maximises sum_i S1_i log pi_i subject to sum_i pi_i = 1
   pv.pi[i] = S1 / total_weight;
@@ -333,7 +332,41 @@ __device__ void mstep_finalize_block(const double *partials, int nb, int g, int 
     for (int t = 0; t < r; ++t) Del[a * r + t] = D[a * RMAX + t];
     for (int b = 0; b < p; ++b) Sig[a * p + b] = Sn[a * PMAX + b];
   }
-  pv.nu[i] = solve_nu(S8 / S1, nu_min, nu_max);
+  *nu_c = S8 / S1;
+  return true;
+}
+
+// Conditional-maximisation update of component i of one fit from the
+// per-block partial sums (block of 128 threads).
+__device__ void mstep_finalize_block(const double *partials, int nb, int g, int p, int r, int64_t n,
+                                     double nu_min, double nu_max, double *params, int *status, int i) {
+  __shared__ double S[3 + PMAX + RMAX + PMAX * RMAX + RMAX * (RMAX + 1) / 2 + PMAX * (PMAX + 1) / 2];
+  __shared__ double red[128];
+  const int K = sums_width(p, r);
+  for (int e = threadIdx.x; e < K; e += blockDim.x) {
+    double s = 0.0;
+    for (int b = 0; b < nb; ++b) s += partials[(int64_t)b * g * K + (int64_t)i * K + e];
+    S[e] = s;
+  }
+  // total posterior weight over all components (= n when every tau row sums to 1)
+  double tw = 0.0;
+  for (int q = threadIdx.x; q < g * nb; q += blockDim.x) {
+    const int ic = q / nb, b = q % nb;
+    tw += partials[(int64_t)b * g * K + (int64_t)ic * K];
+  }
+  red[threadIdx.x] = tw;
+  __syncthreads();
+  for (int h = 64; h > 0; h >>= 1) {
+    if (threadIdx.x < h) red[threadIdx.x] += red[threadIdx.x + h];
+    __syncthreads();
+  }
+  __shared__ double nu_c;
+  __shared__ int nu_go;
+  if (threadIdx.x == 0) nu_go = mstep_update_thread0(S, red[0], g, p, r, n, params, status, i, &nu_c) ? 1 : 0;
+  __syncthreads();
+  if (!nu_go) return;
+  const double nu = solve_nu_block(nu_c, nu_min, nu_max);
+  if (threadIdx.x == 0) param_view(params, g, p, r).nu[i] = nu;
 }
 
 __global__ void mstep_finalize_kernel(const double *partials, int nb, int g, int p, int r, int64_t n,

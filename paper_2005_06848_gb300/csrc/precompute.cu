@@ -145,6 +145,14 @@ __device__ void precompute_component(const double *params, int g, int p, int r, 
   o.mB = f.mB = nu + p + 2.0;
   o.psiA = f.psiA = psiA;
   o.logmA = f.logmA = log(nu + p);
+  for (int a = 0; a < PMAX; ++a) o.fmu[a] = f.fmu[a] = (float)o.mu[a];
+  for (int a = 0; a < PMAX * PMAX; ++a) o.fA[a] = f.fA[a] = (float)o.A[a];
+  for (int a = 0; a < RMAX * PMAX; ++a) o.fB[a] = f.fB[a] = (float)o.B[a];
+  o.fc0 = f.fc0 = (float)c0;
+  o.fnu = f.fnu = (float)nu;
+  o.fmA = f.fmA = (float)(nu + p);
+  o.fmB = f.fmB = (float)(nu + p + 2.0);
+  o.fpsiA = f.fpsiA = (float)psiA;
 }
 
 __global__ void precompute_kernel(const double *params, int g, int p, int r, LatticeDev lat,

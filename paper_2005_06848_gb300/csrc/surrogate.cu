@@ -619,23 +619,23 @@ __device__ __forceinline__ RowProblem row_problem(const CompT<float> &c, const d
   const double *yj = Y + j * (int64_t)p;
   float yc[PMAX];
 #pragma unroll
-  for (int k = 0; k < PMAX; ++k) yc[k] = (k < p) ? (float)(yj[k] - c.mu[k]) : 0.f;
+  for (int k = 0; k < PMAX; ++k) yc[k] = (k < p) ? (float)yj[k] - c.fmu[k] : 0.f;
   float d = 0.f, q0 = 0.f, q1 = 0.f, q2 = 0.f;
 #pragma unroll
   for (int k = 0; k < PMAX; ++k) {
     if (k < p) {
       float acc = 0.f;
 #pragma unroll
-      for (int l = 0; l <= k; ++l) acc = fmaf((float)c.A[k * PMAX + l], yc[l], acc);
+      for (int l = 0; l <= k; ++l) acc = fmaf(c.fA[k * PMAX + l], yc[l], acc);
       d = fmaf(acc, acc, d);
-      q0 = fmaf((float)c.B[0 * PMAX + k], acc, q0);
-      q1 = fmaf((float)c.B[1 * PMAX + k], acc, q1);
-      q2 = fmaf((float)c.B[2 * PMAX + k], acc, q2);
+      q0 = fmaf(c.fB[0 * PMAX + k], acc, q0);
+      q1 = fmaf(c.fB[1 * PMAX + k], acc, q1);
+      q2 = fmaf(c.fB[2 * PMAX + k], acc, q2);
     }
   }
-  const float nu = (float)c.nu, mA = (float)c.mA, mB = (float)c.mB;
+  const float nu = c.fnu, mA = c.fmA, mB = c.fmB;
   rp.nud = nu + d;
-  rp.logt = (float)c.c0 - 0.5f * mA * log1pf(d / nu);
+  rp.logt = c.fc0 - 0.5f * mA * log1pf(d / nu);
   rp.q[0] = q0;
   rp.q[1] = q1;
   rp.q[2] = q2;
@@ -822,7 +822,7 @@ __global__ void __launch_bounds__(GROUP_THREADS * GROUPS, 1)
         // -(m - 1) x f_m(x)); the bound decreases in c_t, so the largest
         // coordinate of pass A's point gives the tightest one
         float ub = logTA + UB_MARGIN;
-        const float cm = G.cmax[pair], m = (float)c.mA;
+        const float cm = G.cmax[pair], m = c.fmA;
         if (cm > 0.f && m > 1.f) {
           const float lnorm = lgammaf(0.5f * (m + 1.f)) - lgammaf(0.5f * m) - 0.5f * logf(m * 3.14159265f);
           const float lb = logf((m + cm * cm) / ((m - 1.f) * cm)) + lnorm - 0.5f * (m + 1.f) * log1pf(cm * cm / m);
@@ -837,9 +837,9 @@ __global__ void __launch_bounds__(GROUP_THREADS * GROUPS, 1)
           const float *oB = oA + OP;
           const float logTB = -__expf(fmaf(oB[0], sdv[0], mean[0]));
           const float nud = G.nud[pair];
-          const float mA = (float)c.mA, mB = (float)c.mB;
+          const float mA = c.fmA, mB = c.fmB;
           const float e1 = mA / nud * __expf(logTB - logTA);
-          const float e2 = e1 - (logf(0.5f * nud) + mA / nud - (float)c.psiA);
+          const float e2 = e1 - (logf(0.5f * nud) + mA / nud - c.fpsiA);
           const float sig = sqrtf(nud / mB);
           // E[X] and E[X X^T] of pass B in the Lambda basis: D^{1/2} (.) D^{1/2}
           const float L00 = c.L[0], L10 = c.L[RMAX], L11 = c.L[RMAX + 1];

@@ -265,3 +265,41 @@ def test_surrogate_gain_at_equal_loglik_accuracy(lat8192):
         assert math.isfinite(l_sur)
         assert t_sur < t_plain[n_eq], report
     print("surrogate gain report", report)
+
+
+def test_surrogate_edge_cases(lat8192):
+    """Attachment rules: FP64 contexts and r != 3 are refused when the E-step
+    runs; a mixture whose dof leave the network's domain (nu + p + 2 > 30)
+    sends every pair to the lattice rule and reproduces the plain E-step
+    bit for bit; detaching restores the plain path."""
+    torch = _torch()
+    s = binding.Surrogate(lat8192, seed=9)
+    Y, _, truth, _, _, _ = synth.workload("cfust_p3r3g4_n1000000_N2048", n=700, seed=1)
+    Yd = torch.tensor(Y, dtype=torch.float64, device="cuda")
+    lat = synth.make_lattice(256, 4, seed=0)
+    c64 = binding.Context(lat, precision=binding.CFUST_FP64)
+    c64.cfust_set_surrogate(s)
+    with pytest.raises(binding.CfustError) as ei:
+        c64.cfust_loglik(Yd, truth)
+    assert ei.value.status == -1
+    # r = 2 mixture on a 3-dimensional lattice context
+    Y2, _, t2, _, lat2, _ = synth.workload("cfust_p2r2g2_n2000_N1024", n=300, seed=0)
+    c2 = binding.Context(lat2, precision=binding.CFUST_FP32)
+    c2.cfust_set_surrogate(s)
+    with pytest.raises(binding.CfustError):
+        c2.cfust_loglik(torch.tensor(Y2, dtype=torch.float64, device="cuda"), t2)
+    # dof outside the domain: all pairs to the lattice rule
+    pi, mu, Sigma, Delta, nu = truth.as_arrays()
+    high = synth.Params(pi, mu, Sigma, Delta, np.full_like(nu, 40.0))
+    plain = binding.Context(lat, precision=binding.CFUST_FP32)
+    sur = binding.Context(lat, precision=binding.CFUST_FP32)
+    sur.cfust_set_surrogate(s)
+    Ep, Es = plain.cfust_estep(Yd, high), sur.cfust_estep(Yd, high)
+    assert sur.cfust_last_fallback() == high.g * len(Y)
+    for k in ("logf", "tau", "e1", "e2", "e3", "e4"):
+        assert torch.equal(Ep[k], Es[k]), k
+    assert Ep["loglik"] == Es["loglik"]
+    # detach: the plain path again
+    sur.cfust_set_surrogate(None)
+    assert sur.cfust_loglik(Yd, truth) == plain.cfust_loglik(Yd, truth)
+    assert sur.cfust_last_fallback() == 0
