@@ -13,6 +13,13 @@ in w - 2.5 for w < 5, degree 7 in sqrt(w) - c1 for 5 <= w < 16, degree 6 in
 sqrt(w) - c2 for 16 <= w <= 88 (x down to the smallest normal float).  A
 branch-free variant for the paired sweep uses one tail piece instead:
 P = sqrt(w) T(1/sqrt(w) - c3), T of degree 9, for 5 <= w <= 88.
+The paired sweep (two evaluations per FP32x2 instruction) has its own,
+shorter set, since its exponential is the hardware exp2 approximation
+(relative error ~3e-6) anyway and the single-precision tolerances leave room:
+G of degree 6 fitted on y in [0, 14] (beyond, the weight underflows) and the
+central quantile piece of degree 6.  The tail quantile keeps degree 9: an
+error in a deep conditional draw is amplified by the next limit (d log Phi(-y)
+/ dy ~ -y), and degree 7 pushed log f past 1e-4 on deep-tail pairs.
 The targets come from scipy.special (erfcx, ndtri) in double precision.
 """
 import os
@@ -88,6 +95,9 @@ def main():
     c1, p1 = fit_quantile_piece(5.0, 16.0, True, 7)
     c2, p2 = fit_quantile_piece(16.0, wmax, True, 6)
     c3, p3 = fit_quantile_tail_inv(5.0, wmax, 9)
+    cf = 0.36
+    qf = fit_tail(cf, 6, 14.0)
+    c0f, p0f = fit_quantile_piece(1e-12, 5.0, False, 6)
     text = f"""// Generated by fit_normal_f32.py (least-squares fits iterated towards minimax
 // relative error); see that script for the forms.  Do not edit by hand.
 #pragma once
@@ -108,6 +118,12 @@ constexpr float Q_S2 = {np.float32(c2):.9e}f;   // w >= 16: P = poly(sqrt(w) - Q
 __device__ constexpr float Q_P2[7] = {{{fmt(p2)}}};
 constexpr float Q_U3 = {np.float32(c3):.9e}f;   // w >= 5 (branch-free form): P = sqrt(w) poly(1/sqrt(w) - Q_U3)
 __device__ constexpr float Q_P3[10] = {{{fmt(p3)}}};
+
+// Shorter set of the paired sweep (same forms)
+constexpr float TAIL_CF = {np.float32(cf):.9e}f;
+__device__ constexpr float TAIL_QF[7] = {{{fmt(qf)}}};
+constexpr float Q_W0F = {np.float32(c0f):.9e}f;
+__device__ constexpr float Q_P0F[7] = {{{fmt(p0f)}}};
 
 }}  // namespace nf32
 }}  // namespace cfust

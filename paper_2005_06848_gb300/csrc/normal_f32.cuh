@@ -86,19 +86,19 @@ __device__ __forceinline__ float phi_inv_f32(float x) {
 }
 
 // ---- paired forms: two independent evaluations per FP32x2 instruction ------
-// Coefficients duplicated into (c, c) pairs in constant memory.
+// Coefficients (the sweep's shorter set, see fit_normal_f32.py) duplicated
+// into (c, c) pairs in constant memory.
 namespace nf32 {
 struct Pairs {
-  float2 tail_q[9];
-  float2 p0[9];
+  float2 tail_q[7];
+  float2 p0[7];
   float2 p3[10];
 };
 __constant__ Pairs kPairs = {
-    {{TAIL_Q[0], TAIL_Q[0]}, {TAIL_Q[1], TAIL_Q[1]}, {TAIL_Q[2], TAIL_Q[2]}, {TAIL_Q[3], TAIL_Q[3]},
-     {TAIL_Q[4], TAIL_Q[4]}, {TAIL_Q[5], TAIL_Q[5]}, {TAIL_Q[6], TAIL_Q[6]}, {TAIL_Q[7], TAIL_Q[7]},
-     {TAIL_Q[8], TAIL_Q[8]}},
-    {{Q_P0[0], Q_P0[0]}, {Q_P0[1], Q_P0[1]}, {Q_P0[2], Q_P0[2]}, {Q_P0[3], Q_P0[3]}, {Q_P0[4], Q_P0[4]},
-     {Q_P0[5], Q_P0[5]}, {Q_P0[6], Q_P0[6]}, {Q_P0[7], Q_P0[7]}, {Q_P0[8], Q_P0[8]}},
+    {{TAIL_QF[0], TAIL_QF[0]}, {TAIL_QF[1], TAIL_QF[1]}, {TAIL_QF[2], TAIL_QF[2]}, {TAIL_QF[3], TAIL_QF[3]},
+     {TAIL_QF[4], TAIL_QF[4]}, {TAIL_QF[5], TAIL_QF[5]}, {TAIL_QF[6], TAIL_QF[6]}},
+    {{Q_P0F[0], Q_P0F[0]}, {Q_P0F[1], Q_P0F[1]}, {Q_P0F[2], Q_P0F[2]}, {Q_P0F[3], Q_P0F[3]}, {Q_P0F[4], Q_P0F[4]},
+     {Q_P0F[5], Q_P0F[5]}, {Q_P0F[6], Q_P0F[6]}},
     {{Q_P3[0], Q_P3[0]}, {Q_P3[1], Q_P3[1]}, {Q_P3[2], Q_P3[2]}, {Q_P3[3], Q_P3[3]}, {Q_P3[4], Q_P3[4]},
      {Q_P3[5], Q_P3[5]}, {Q_P3[6], Q_P3[6]}, {Q_P3[7], Q_P3[7]}, {Q_P3[8], Q_P3[8]}, {Q_P3[9], Q_P3[9]}}};
 
@@ -113,10 +113,11 @@ __device__ __forceinline__ float2 horner2(const float2 (&c)[K], float2 t) {
 
 __device__ __forceinline__ float2 f2(float v) { return make_float2(v, v); }
 
-// Paired phi_upper_pq_fast_f32.
+// Paired counterpart of phi_upper_pq_fast_f32 with the sweep's degree-6 tail
+// factor (fitted for y <= 14; beyond, exp2 of -y^2/2 flushes the weight to 0).
 __device__ __forceinline__ void phi_upper_pq_x2(float2 y, float2 &p, float2 &q) {
   const float2 a = make_float2(fabsf(y.x), fabsf(y.y));
-  const float2 den = __ffma2_rn(f2(nf32::TAIL_C), a, f2(1.0f));
+  const float2 den = __ffma2_rn(f2(nf32::TAIL_CF), a, f2(1.0f));
   const float2 t = make_float2(__fdividef(1.0f, den.x), __fdividef(1.0f, den.y));
   const float2 G = __fmul2_rn(nf32::horner2(nf32::kPairs.tail_q, t), t);
   const float2 k = __fmul2_rn(__fmul2_rn(a, a), f2(-0.72134752044f));
@@ -135,7 +136,7 @@ __device__ __forceinline__ float2 neg_quantile_x2(float um, float u, float2 p, f
   const float2 xs = make_float2(lx ? fmaxf(x.x, 1.17549435e-38f) : c.x, ly ? fmaxf(x.y, 1.17549435e-38f) : c.y);
   const float2 prod = __fmul2_rn(__fmul2_rn(xs, f2(4.0f)), __ffma2_rn(xs, f2(-1.0f), f2(1.0f)));
   const float2 w = make_float2(-__logf(prod.x), -__logf(prod.y));
-  const float2 pc = nf32::horner2(nf32::kPairs.p0, __fadd2_rn(w, f2(-nf32::Q_W0)));
+  const float2 pc = nf32::horner2(nf32::kPairs.p0, __fadd2_rn(w, f2(-nf32::Q_W0F)));
   const float2 rs = make_float2(rsqrtf(w.x), rsqrtf(w.y));
   const float2 pt = __fmul2_rn(nf32::horner2(nf32::kPairs.p3, __fadd2_rn(rs, f2(-nf32::Q_U3))), __fmul2_rn(w, rs));
   const float2 P = make_float2(w.x < 5.0f ? pc.x : pt.x, w.y < 5.0f ? pc.y : pt.y);

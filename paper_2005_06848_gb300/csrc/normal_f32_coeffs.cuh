@@ -19,5 +19,11 @@ __device__ constexpr float Q_P2[7] = {6.528412819e+00f, 1.008939028e+00f, -5.080
 constexpr float Q_U3 = 2.772277594e-01f;   // w >= 5 (branch-free form): P = sqrt(w) poly(1/sqrt(w) - Q_U3)
 __device__ constexpr float Q_P3[10] = {9.546209574e-01f, -1.925693303e-01f, 1.252948493e-01f, 5.648402572e-01f, 8.162746429e-01f, 1.152263451e+01f, 9.296464920e+00f, -1.601646576e+02f, -2.552538452e+02f, 1.114506958e+03f};
 
+// Shorter set of the paired sweep (same forms)
+constexpr float TAIL_CF = 3.600000143e-01f;
+__device__ constexpr float TAIL_QF[7] = {1.437126100e-01f, 1.417795271e-01f, 1.396742910e-01f, 2.669101395e-02f, 1.807190627e-01f, -1.795689166e-01f, 4.699178413e-02f};
+constexpr float Q_W0F = 2.500000000e+00f;
+__device__ constexpr float Q_P0F[7] = {1.501409888e+00f, 2.466495484e-01f, -4.178334959e-03f, -1.265231404e-03f, 2.182244789e-04f, -6.660533813e-07f, -3.280813644e-06f};
+
 }  // namespace nf32
 }  // namespace cfust
