@@ -272,7 +272,8 @@ cfust_status cfust_surrogate_create(cfust_surrogate **out, uint64_t seed, const 
                                     void *cuda_stream);
 cfust_status cfust_surrogate_destroy(cfust_surrogate *s);
 
-/* Lattice-rule targets of B problems.  x: device float [B][7] (as above), y:
+/* Lattice-rule targets of B problems (B <= 2^30 here and in the calls below;
+ * larger counts return CFUST_EINVAL).  x: device float [B][7] (as above), y:
  * device float [B][10].  A problem whose every point weight underflows gets
  * NaN targets.  Synchronises the stream. */
 cfust_status cfust_surrogate_label(cfust_surrogate *s, const float *x, float *y, int64_t B);
@@ -295,9 +296,11 @@ cfust_status cfust_surrogate_gradient(cfust_surrogate *s, const float *x, const 
 cfust_status cfust_surrogate_get_params(cfust_surrogate *s, float *theta, float *norm);
 cfust_status cfust_surrogate_set_params(cfust_surrogate *s, const float *theta, const float *norm);
 
-/* Train on n_train problems drawn uniformly over the training domain
- * (SplitMix64(seed); rows with a non-PD or too-thin R redrawn), labelled on
- * the GPU, target normalisation set from the labels.  Adam (beta 0.9, 0.999,
+/* Train on n_train problems drawn over the training domain (SplitMix64(seed);
+ * R and log m uniform, rows with a non-PD or too-thin R redrawn), labelled on
+ * the GPU, target normalisation set from the labels (rows whose labels are not
+ * finite are dropped).  Problems: half uniform over the box, half with c_t
+ * drawn from N(-1.5, 2.5^2) clipped to it.  Adam (beta 0.9, 0.999,
  * eps 1e-8) on mini-batches of `batch` rows with a cosine-decayed step from
  * lr; `epochs` passes.  loss_trace: host float [epochs] (mean sampled batch
  * loss per epoch) or NULL.  Requires n_train >= batch >= 128. */

@@ -134,14 +134,14 @@ __device__ __forceinline__ float2 neg_quantile_x2(float um, float u, float2 p, f
   const float2 c = __ffma2_rn(f2(um), q, f2(u));  // 1 - x
   const bool lx = x.x <= 0.5f, ly = x.y <= 0.5f;
   const float2 xs = make_float2(lx ? fmaxf(x.x, 1.17549435e-38f) : c.x, ly ? fmaxf(x.y, 1.17549435e-38f) : c.y);
-  const float2 prod = __fmul2_rn(__fmul2_rn(xs, f2(4.0f)), __ffma2_rn(xs, f2(-1.0f), f2(1.0f)));
+  const float2 prod = __fmul2_rn(xs, __ffma2_rn(xs, f2(-4.0f), f2(4.0f)));  // 4 x (1 - x), exactly
   const float2 w = make_float2(-__logf(prod.x), -__logf(prod.y));
   const float2 pc = nf32::horner2(nf32::kPairs.p0, __fadd2_rn(w, f2(-nf32::Q_W0F)));
   const float2 rs = make_float2(rsqrtf(w.x), rsqrtf(w.y));
   const float2 pt = __fmul2_rn(nf32::horner2(nf32::kPairs.p3, __fadd2_rn(rs, f2(-nf32::Q_U3))), __fmul2_rn(w, rs));
   const float2 P = make_float2(w.x < 5.0f ? pc.x : pt.x, w.y < 5.0f ? pc.y : pt.y);
-  const float2 v = __ffma2_rn(f2(2.0f), xs, f2(-1.0f));
-  const float2 zq = __fmul2_rn(__fmul2_rn(v, P), f2(1.41421356237f));
+  const float2 v = __ffma2_rn(f2(2.82842712475f), xs, f2(-1.41421356237f));  // sqrt(2) (2x - 1)
+  const float2 zq = __fmul2_rn(v, P);
   return make_float2(lx ? -zq.x : zq.x, ly ? -zq.y : zq.y);
 }
 

@@ -973,9 +973,14 @@ cfust_status sg_fail(cfust_surrogate *s, cfust_status st, const std::string &m) 
 
 cfust_status ensure_rows(cfust_surrogate *s, int64_t B) {
   if (B <= s->cap) return CFUST_OK;
-  void *bufs[] = {s->x0, s->Z1, s->H1, s->Z2, s->H2, s->Z3, s->H3, s->out, s->dz4, s->dz3, s->dz2, s->dz1};
-  for (void *p : bufs)
-    if (p) cudaFree(p);
+  void **bufs[] = {(void **)&s->x0, (void **)&s->Z1, (void **)&s->H1, (void **)&s->Z2,
+                   (void **)&s->H2, (void **)&s->Z3, (void **)&s->H3, (void **)&s->out,
+                   (void **)&s->dz4, (void **)&s->dz3, (void **)&s->dz2, (void **)&s->dz1};
+  for (void **p : bufs) {
+    if (*p) cudaFree(*p);
+    *p = nullptr;
+  }
+  s->cap = 0;
   SG_CUDA(s, cudaMalloc(&s->x0, sizeof(bf16) * B * DINP));
   SG_CUDA(s, cudaMalloc(&s->Z1, sizeof(bf16) * B * H));
   SG_CUDA(s, cudaMalloc(&s->H1, sizeof(bf16) * B * H));
@@ -1033,6 +1038,8 @@ cfust_status weight_grad(cfust_surrogate *s, const bf16 *Hin, int kin, int kin_r
   const int64_t need = (int64_t)S * kin * nout;
   if (need > s->part_len) {
     if (s->part) cudaFree(s->part);
+    s->part = nullptr;
+    s->part_len = 0;
     SG_CUDA(s, cudaMalloc(&s->part, sizeof(float) * need));
     s->part_len = need;
   }
@@ -1123,6 +1130,17 @@ cfust_status prep(cfust_surrogate *s, const float *x, int64_t B) {
   SG_CUDA(s, cudaGetLastError());
   return CFUST_OK;
 }
+
+// Device buffer released when it goes out of scope (error paths included).
+struct DevBuf {
+  float *p = nullptr;
+  ~DevBuf() {
+    if (p) cudaFree(p);
+  }
+};
+
+// Largest row count of one call: the GEMMs index rows with 32-bit integers.
+constexpr int64_t MAX_ROWS = (int64_t)1 << 30;
 
 // SplitMix64 for initial weights and training inputs (host)
 struct SplitMix {
@@ -1233,7 +1251,7 @@ cfust_status cfust_surrogate_destroy(cfust_surrogate *s) {
 const char *cfust_surrogate_last_error(cfust_surrogate *s) { return s ? s->err.c_str() : g_sg_error.c_str(); }
 
 cfust_status cfust_surrogate_label(cfust_surrogate *s, const float *x, float *y, int64_t B) {
-  if (!s || !x || !y || B < 0) return sg_fail(s, CFUST_EINVAL, "bad arguments");
+  if (!s || !x || !y || B < 0 || B > MAX_ROWS) return sg_fail(s, CFUST_EINVAL, "bad arguments (0 <= B <= 2^30)");
   if (B == 0) return CFUST_OK;
   const int64_t blocks = (B + 7) / 8;
   label_kernel<<<(unsigned)blocks, 256, 0, s->stream>>>(x, y, B, s->lat, s->tab);
@@ -1243,7 +1261,7 @@ cfust_status cfust_surrogate_label(cfust_surrogate *s, const float *x, float *y,
 }
 
 cfust_status cfust_surrogate_predict(cfust_surrogate *s, const float *x, float *y, int64_t B) {
-  if (!s || !x || !y || B < 0) return sg_fail(s, CFUST_EINVAL, "bad arguments");
+  if (!s || !x || !y || B < 0 || B > MAX_ROWS) return sg_fail(s, CFUST_EINVAL, "bad arguments (0 <= B <= 2^30)");
   if (B == 0) return CFUST_OK;
   cfust_status st = prep(s, x, B);
   if (st != CFUST_OK) return st;
@@ -1277,7 +1295,7 @@ cfust_status cfust_surrogate_get_params(cfust_surrogate *s, float *theta, float 
 
 cfust_status cfust_surrogate_gradient(cfust_surrogate *s, const float *x, const float *y, int64_t B, double *loss,
                                       float *grad) {
-  if (!s || !x || !y || B < 1) return sg_fail(s, CFUST_EINVAL, "bad arguments");
+  if (!s || !x || !y || B < 1 || B > MAX_ROWS) return sg_fail(s, CFUST_EINVAL, "bad arguments (1 <= B <= 2^30)");
   cfust_status st = prep(s, x, B);
   if (st != CFUST_OK) return st;
   if ((st = loss_grad(s, y, B, loss)) != CFUST_OK) return st;
@@ -1292,7 +1310,9 @@ cfust_status cfust_surrogate_train(cfust_surrogate *s, int64_t n_train, int epoc
                                    uint64_t seed, float *loss_trace) {
   if (!s || n_train < batch || batch < 128 || epochs < 1 || !(lr > 0.f))
     return sg_fail(s, CFUST_EINVAL, "need n_train >= batch >= 128, epochs >= 1, lr > 0");
-  // training inputs drawn uniformly over the domain (host), labelled on the GPU
+  if (n_train > MAX_ROWS) return sg_fail(s, CFUST_EINVAL, "n_train above 2^30");
+  // training inputs drawn on the host over the domain (a box mixture, below),
+  // labelled on the GPU
   SplitMix rng{seed};
   std::vector<float> hx(n_train * DIN);
   for (int64_t b = 0; b < n_train; ++b) {
@@ -1314,16 +1334,13 @@ cfust_status cfust_surrogate_train(cfust_surrogate *s, int64_t n_train, int epoc
       if (p2 >= PIVOT_MIN && p3 >= PIVOT_MIN) break;
     }
   }
-  float *dx = nullptr, *dy = nullptr;
-  SG_CUDA(s, cudaMalloc(&dx, sizeof(float) * n_train * DIN));
-  SG_CUDA(s, cudaMalloc(&dy, sizeof(float) * n_train * DOUT));
+  DevBuf bx, by;
+  SG_CUDA(s, cudaMalloc(&bx.p, sizeof(float) * n_train * DIN));
+  SG_CUDA(s, cudaMalloc(&by.p, sizeof(float) * n_train * DOUT));
+  float *dx = bx.p, *dy = by.p;
   SG_CUDA(s, cudaMemcpy(dx, hx.data(), sizeof(float) * n_train * DIN, cudaMemcpyHostToDevice));
   cfust_status st = cfust_surrogate_label(s, dx, dy, n_train);
-  if (st != CFUST_OK) {
-    cudaFree(dx);
-    cudaFree(dy);
-    return st;
-  }
+  if (st != CFUST_OK) return st;
   // keep the rows with finite labels (in the domain's far corner every point
   // weight can underflow), then set the target normalisation from them
   {
@@ -1340,11 +1357,7 @@ cfust_status cfust_surrogate_train(cfust_surrogate *s, int64_t n_train, int epoc
       }
       ++kept;
     }
-    if (kept < batch) {
-      cudaFree(dx);
-      cudaFree(dy);
-      return sg_fail(s, CFUST_ENUMERIC, "too few finite training labels");
-    }
+    if (kept < batch) return sg_fail(s, CFUST_ENUMERIC, "too few finite training labels");
     n_train = kept;
     SG_CUDA(s, cudaMemcpy(dx, hx.data(), sizeof(float) * n_train * DIN, cudaMemcpyHostToDevice));
     SG_CUDA(s, cudaMemcpy(dy, hy.data(), sizeof(float) * n_train * DOUT, cudaMemcpyHostToDevice));
@@ -1384,8 +1397,6 @@ cfust_status cfust_surrogate_train(cfust_surrogate *s, int64_t n_train, int epoc
     if (st != CFUST_OK) break;
     if (loss_trace) loss_trace[ep] = (float)(ep_loss / (double)((steps + 63) / 64));
   }
-  cudaFree(dx);
-  cudaFree(dy);
   if (st != CFUST_OK) return st;
   SG_CUDA(s, cudaStreamSynchronize(s->stream));
   return CFUST_OK;
