@@ -184,8 +184,7 @@ __device__ __forceinline__ void store(void *base, int64_t idx, T v) {
 // Per-component operands of the paired sweep, duplicated into (x, x) pairs,
 // kept in shared memory so they occupy no registers.
 struct PairedConsts {
-  float2 nL[RMAX * (RMAX + 1) / 2];  // -L_th, packed lower triangle
-  float2 Li[RMAX];                   // 1 / L_tt
+  float2 nL[RMAX * (RMAX + 1) / 2];  // -L_th / L_tt (h < t), packed lower triangle
 };
 
 // Lattice constants of coordinate t in the sweep's precision: the float copies
@@ -283,10 +282,15 @@ __device__ __forceinline__ bool pair_sweep(const EArgs &a, const FitView &fv, co
     for (int h = 0; h <= t; ++h) Lc[t * (t + 1) / 2 + h] = c.L[t * RMAX + h];
   }
   // paired operands: (pass A, pass B) limits; -L and 1/L_tt pairs come from shared memory
+  // (pass A, pass B) limits over L_tt: with the staged -L_th / L_tt the
+  // standardised limit of coordinate t is one multiply-add chain per point
   float2 ab2[R];
   if constexpr (PAIRED) {
 #pragma unroll
-    for (int t = 0; t < R; ++t) ab2[t] = make_float2((float)aA[t], (float)aB[t]);
+    for (int t = 0; t < R; ++t) {
+      const float li = (float)c.Linv[t];
+      ab2[t] = make_float2((float)aA[t] * li, (float)aB[t] * li);
+    }
   }
 
   // lattice state: fm_t = 2 m_t - N with m_t = (k z_t + sint_t) mod N for this
@@ -356,7 +360,7 @@ __device__ __forceinline__ bool pair_sweep(const EArgs &a, const FitView &fv, co
 #pragma unroll
         for (int h = 0; h < t; ++h) acc2 = __ffma2_rn(pc->nL[t * (t + 1) / 2 + h], z2[h], acc2);
         float2 p2, q2;
-        phi_upper_pq_x2(__fmul2_rn(acc2, pc->Li[t]), p2, q2);
+        phi_upper_pq_x2(acc2, p2, q2);
         w2 = __fmul2_rn(w2, p2);
         z2[t] = neg_quantile_x2(um[t], uu[t], p2, q2);
       }
@@ -557,12 +561,8 @@ __device__ __forceinline__ bool stage_block(const EArgs &a, int i, unsigned char
   if (threadIdx.x < RMAX * RMAX) {
     const int t = threadIdx.x / RMAX, h = threadIdx.x % RMAX;
     if (h <= t) {
-      const float v = -(float)cs->L[t * RMAX + h];
+      const float v = -(float)cs->L[t * RMAX + h] * (float)cs->Linv[t];
       pcs->nL[t * (t + 1) / 2 + h] = make_float2(v, v);
-    }
-    if (h == 0) {
-      const float li = (float)cs->Linv[t];
-      pcs->Li[t] = make_float2(li, li);
     }
   }
   __syncthreads();
@@ -1050,12 +1050,8 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? CFUST_ESTEP_MINB : 1)
       if (threadIdx.x < RMAX * RMAX) {
         const int t = threadIdx.x / RMAX, h = threadIdx.x % RMAX;
         if (h <= t) {
-          const float v = -(float)cs->L[t * RMAX + h];
+          const float v = -(float)cs->L[t * RMAX + h] * (float)cs->Linv[t];
           pcs->nL[t * (t + 1) / 2 + h] = make_float2(v, v);
-        }
-        if (h == 0) {
-          const float li = (float)cs->Linv[t];
-          pcs->Li[t] = make_float2(li, li);
         }
       }
       if (a.staged && !mbar_wait_bounded(bar, phase, 1 << 22)) atomicOr(&s_fail, 1);
@@ -1234,7 +1230,9 @@ cudaError_t launch_list_r3(EArgs a, int g, int64_t n, const int *list, const uns
   cudaError_t e = cudaFuncSetAttribute(estep_list_kernel<float, 3, DENS>,
                                        cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
-  a.ppw = 4;
+  // 16 listed pairs per warp chunk: their FP64 prologues and triage tests run
+  // lane-parallel, which matters at the small lattices this path serves
+  a.ppw = 16;
   // the list lengths live on the device: size the grid for a full list but
   // cap it near four waves of two CTAs per SM; blocks past the end return
   const int64_t need = (n + 8 * a.ppw - 1) / (8 * a.ppw);
