@@ -189,12 +189,48 @@ def cpu_baseline(rows: int = 1024):
     t0 = time.perf_counter()
     E = O.estep(Ys, init, U)
     S = O.mstep_sums(Ys, E["tau"], E["e1"], E["e2"], E["e3"], E["e4"])
-    O.mstep_update(S, init, rows)
+    P1 = O.mstep_update(S, init, rows)
     dt = time.perf_counter() - t0
     pairs = rows * meta["g"]
-    return {"value": pairs / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": f"{rows} of {meta['n']} observations x {meta['g']} components, "
-                      f"{lat.n}-point lattice, one E-step + M-step, FP64 numpy/scipy, {dt:.1f} s"}
+    return ({"value": pairs / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
+             "sample": f"{rows} of {meta['n']} observations x {meta['g']} components, "
+                       f"{lat.n}-point lattice, one E-step + M-step, FP64 numpy/scipy, {dt:.1f} s"},
+            (Ys, init, E, P1))
+
+
+def fp32_error_vs_oracle(ref, lat, stream):
+    """The FP32 path's error against the FP64 oracle on the baseline's sample,
+    stated per result: log f, tau, e1..e4, the log-likelihood and the M-step
+    parameters (the tolerances the parity tests hold it to beside each)."""
+    import torch
+    from paper_2005_06848_gb300 import binding
+    Ys, init, E, P1 = ref
+    Yd = torch.from_numpy(Ys).cuda()
+    with binding.Context(lat, precision=binding.CFUST_FP32, stream=stream) as ctx:
+        G = ctx.cfust_estep(Yd, init)
+        P1g = ctx.cfust_mstep(Yd, G, init)
+    r = init.r
+
+    def f64(t):
+        return t.cpu().numpy().astype(np.float64)
+
+    lf, lo = f64(G["logf"]), E["logf"]
+    fin = np.isfinite(lo)
+    e3g = np.transpose(f64(G["e3"]), (0, 2, 1))
+    e4g = binding.unpack_e4(f64(G["e4"]), r)
+
+    def rel(a, b):
+        return float(np.max(np.abs(a - b) / np.maximum(1.0, np.abs(b))))
+    return {
+        "sample": f"{Ys.shape[0]} observations x {init.g} components of the bench workload",
+        "logf_max_abs": float(np.max(np.abs(lf[fin] - lo[fin]))), "logf_tol": 1e-4,
+        "tau_max_abs": float(np.max(np.abs(f64(G["tau"]) - E["tau"]))), "tau_tol": 1e-5,
+        "e1_e4_max_rel": max(rel(f64(G["e1"]), E["e1"]), rel(f64(G["e2"]), E["e2"]),
+                             rel(e3g, E["e3"]), rel(e4g, E["e4"])), "e_tol": 2e-4,
+        "loglik_rel": abs(G["loglik"] - E["loglik"]) / abs(E["loglik"]), "loglik_tol": 1e-6,
+        "mstep_params_max_rel": max(rel(a, b) for a, b in zip(P1g.as_arrays(), P1.as_arrays())),
+        "params_tol": 1e-3,
+    }
 
 
 def run_reference(args):
@@ -358,7 +394,8 @@ def run_ours(args):
         "e2e": e2e,
     }
     if not args.no_cpu_baseline:
-        line["cpu_baseline"] = cpu_baseline(args.cpu_rows)
+        line["cpu_baseline"], ref = cpu_baseline(args.cpu_rows)
+        line["fp32_error_vs_oracle"] = fp32_error_vs_oracle(ref, lat, stream)
     print(json.dumps(line), flush=True)
     if ws > 1:
         torch.distributed.destroy_process_group()
