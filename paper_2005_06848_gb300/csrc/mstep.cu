@@ -154,15 +154,36 @@ __device__ __forceinline__ void posterior_block(const PosteriorArgs &a, int c0, 
         if (own_c[k] >= 0) {
           const double *col = ws + own_c[k] * TJ * WR + own_w[k];
           const int y1 = own_y1[k], y2 = own_y2[k];
-          double s = 0.0;
+          // four interleaved partial sums (fixed order): independent chains
+          // of the long-latency double multiply-add
+          double s0 = 0.0, s1 = 0.0, s2 = 0.0, s3 = 0.0;
+          int jj = 0;
           if (y1 < 0) {
-            for (int jj = 0; jj < nt; ++jj) s += col[jj * WR];
+            for (; jj + 4 <= nt; jj += 4) {
+              s0 += col[jj * WR];
+              s1 += col[(jj + 1) * WR];
+              s2 += col[(jj + 2) * WR];
+              s3 += col[(jj + 3) * WR];
+            }
+            for (; jj < nt; ++jj) s0 += col[jj * WR];
           } else if (y2 < 0) {
-            for (int jj = 0; jj < nt; ++jj) s += col[jj * WR] * ys[jj * p + y1];
+            for (; jj + 4 <= nt; jj += 4) {
+              s0 = fma(col[jj * WR], ys[jj * p + y1], s0);
+              s1 = fma(col[(jj + 1) * WR], ys[(jj + 1) * p + y1], s1);
+              s2 = fma(col[(jj + 2) * WR], ys[(jj + 2) * p + y1], s2);
+              s3 = fma(col[(jj + 3) * WR], ys[(jj + 3) * p + y1], s3);
+            }
+            for (; jj < nt; ++jj) s0 = fma(col[jj * WR], ys[jj * p + y1], s0);
           } else {
-            for (int jj = 0; jj < nt; ++jj) s += col[jj * WR] * ys[jj * p + y1] * ys[jj * p + y2];
+            for (; jj + 4 <= nt; jj += 4) {
+              s0 = fma(col[jj * WR] * ys[jj * p + y1], ys[jj * p + y2], s0);
+              s1 = fma(col[(jj + 1) * WR] * ys[(jj + 1) * p + y1], ys[(jj + 1) * p + y2], s1);
+              s2 = fma(col[(jj + 2) * WR] * ys[(jj + 2) * p + y1], ys[(jj + 2) * p + y2], s2);
+              s3 = fma(col[(jj + 3) * WR] * ys[(jj + 3) * p + y1], ys[(jj + 3) * p + y2], s3);
+            }
+            for (; jj < nt; ++jj) s0 = fma(col[jj * WR] * ys[jj * p + y1], ys[jj * p + y2], s0);
           }
-          acc[k] += s;
+          acc[k] += (s0 + s1) + (s2 + s3);
         }
       }
     }
