@@ -307,6 +307,15 @@ cfust_status cfust_surrogate_set_params(cfust_surrogate *s, const float *theta, 
 cfust_status cfust_surrogate_train(cfust_surrogate *s, int64_t n_train, int epochs, int batch, float lr,
                                    uint64_t seed, float *loss_trace);
 
+/* Continue training on given problems: x device float [rows][7] (e.g. from
+ * cfust_surrogate_problems), labelled by the lattice rule inside; rows without
+ * finite labels are dropped and the rest shuffled (SplitMix64(seed)); the
+ * target normalisation stays as trained; Adam continues from its state with a
+ * step cosine-decayed from lr over `epochs` passes.  loss_trace: host float
+ * [epochs] or NULL.  Requires 128 <= batch <= rows <= 2^30. */
+cfust_status cfust_surrogate_finetune(cfust_surrogate *s, const float *x, int64_t rows, int epochs, int batch,
+                                      float lr, uint64_t seed, float *loss_trace);
+
 const char *cfust_surrogate_last_error(cfust_surrogate *s);
 
 /* Attach a surrogate to a context (NULL detaches; the context does not own
@@ -326,6 +335,16 @@ const char *cfust_surrogate_last_error(cfust_surrogate *s);
  * Requires CFUST_FP32 precision, e2_mode 0 and r = 3 (checked when the E-step
  * runs).  Attaching drops a captured fit graph. */
 cfust_status cfust_set_surrogate(cfust_ctx *ctx, cfust_surrogate *s);
+
+/* The standardised problems the surrogate E-step would hand the network for
+ * every stride-th (i, j) pair (pair index i n + j) in its domain at params P:
+ * two rows (pass A, pass B) of (c_1, c_2, c_3, R_12, R_13, R_23, log m) per
+ * pair, written to x_out (device float [max_rows][7]) in no particular order.
+ * *rows (host) receives the rows written (at most max_rows).  Requires r = 3;
+ * Y as for cfust_estep.  Synchronises the context's stream.  For tuning a
+ * network to the problems a family of fits poses (cfust_surrogate_finetune). */
+cfust_status cfust_surrogate_problems(cfust_ctx *ctx, const double *Y, int64_t n, const cfust_params *P,
+                                      int64_t stride, float *x_out, int64_t max_rows, int64_t *rows);
 
 /* Pairs the last surrogate E-step handed to the lattice rule (outside the
  * training domain).  Synchronises the context's stream. */

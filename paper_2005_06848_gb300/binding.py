@@ -26,7 +26,8 @@ EXPORTED = ["cfust_create", "cfust_destroy", "cfust_loglik", "cfust_estep", "cfu
             "cfust_surrogate_create", "cfust_surrogate_destroy", "cfust_surrogate_label",
             "cfust_surrogate_predict", "cfust_surrogate_gradient", "cfust_surrogate_get_params",
             "cfust_surrogate_set_params", "cfust_surrogate_train", "cfust_surrogate_last_error",
-            "cfust_set_surrogate", "cfust_last_fallback"]
+            "cfust_set_surrogate", "cfust_last_fallback", "cfust_surrogate_problems",
+            "cfust_surrogate_finetune"]
 
 SURROGATE_NPARAM = 35338
 
@@ -107,6 +108,9 @@ def load(build_if_missing: bool = True, path: str | None = None) -> ctypes.CDLL:
         "cfust_surrogate_last_error": ([vp], ctypes.c_char_p),
         "cfust_set_surrogate": ([vp, vp], ctypes.c_int),
         "cfust_last_fallback": ([vp, ctypes.POINTER(i64)], ctypes.c_int),
+        "cfust_surrogate_problems": ([vp, vp, i64, P, i64, vp, i64, ctypes.POINTER(i64)], ctypes.c_int),
+        "cfust_surrogate_finetune": ([vp, vp, i64, ctypes.c_int, ctypes.c_int, ctypes.c_float, ctypes.c_uint64,
+                                      ctypes.POINTER(ctypes.c_float)], ctypes.c_int),
     }
     for name, (args, res) in sig.items():
         fn = getattr(lib, name)
@@ -302,6 +306,19 @@ class Context:
         self._check(self.lib.cfust_last_fallback(self.h, ctypes.byref(v)))
         return v.value
 
+    def cfust_surrogate_problems(self, Y, params, stride=1, max_rows=None):
+        """Standardised problems (float32 CUDA tensor [rows, 7]) of every
+        stride-th pair in the surrogate's domain at `params` (r = 3)."""
+        import torch
+        if max_rows is None:
+            max_rows = 2 * ((params.g * Y.shape[0] + stride - 1) // stride)
+        x = torch.empty((max_rows, 7), dtype=torch.float32, device=Y.device)
+        hp = _HostParams(params)
+        rows = ctypes.c_int64()
+        self._check(self.lib.cfust_surrogate_problems(self.h, _ptr(Y), Y.shape[0], ctypes.byref(hp.c), int(stride),
+                                                      _ptr(x), int(max_rows), ctypes.byref(rows)))
+        return x[:rows.value]
+
 
 class Surrogate:
     """A cfust_surrogate (learned form of the r = 3 lattice integrals)."""
@@ -371,6 +388,13 @@ class Surrogate:
         nm = None if norm is None else np.ascontiguousarray(norm, dtype=np.float32)
         self._check(self.lib.cfust_surrogate_set_params(self.h, th.ctypes.data_as(fp),
                                                         None if nm is None else nm.ctypes.data_as(fp)))
+
+    def cfust_surrogate_finetune(self, x, epochs, batch=16384, lr=5e-4, seed=1):
+        trace = np.zeros(epochs, dtype=np.float32)
+        self._check(self.lib.cfust_surrogate_finetune(self.h, _ptr(x), x.shape[0], int(epochs), int(batch),
+                                                      float(lr), int(seed),
+                                                      trace.ctypes.data_as(ctypes.POINTER(ctypes.c_float))))
+        return trace
 
     def cfust_surrogate_train(self, n_train, epochs, batch=4096, lr=2e-3, seed=1):
         trace = np.zeros(epochs, dtype=np.float32)

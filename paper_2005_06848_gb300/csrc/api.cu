@@ -75,6 +75,7 @@ struct cfust_ctx {
   // learned surrogate E-step (not owned) and its fallback lists
   cfust_surrogate *sur = nullptr;
   float *d_utab = nullptr;       // lattice uniforms (LatticeDev::utab)
+  unsigned long long *d_prob_cnt = nullptr;  // cfust_surrogate_problems row count
   int *d_fb = nullptr;           // [g][n] observations left to the lattice rule
   unsigned *d_fb_cnt = nullptr;  // [g]
   int64_t fb_cap = 0;
@@ -505,7 +506,8 @@ cfust_status cfust_destroy(cfust_ctx *c) {
     if (ev) cudaEventDestroy(ev);
   void *bufs[] = {c->d_params, c->d_c64, c->d_c32, c->d_chi64, c->d_chi32, c->d_status,
                   c->d_rescue_cnt, c->d_ll, c->d_trace, c->d_rescue, c->d_partials, c->d_llpart,
-                  c->d_logf, c->d_e1, c->d_e2, c->d_e3, c->d_e4, c->d_fb, c->d_fb_cnt, c->d_utab};
+                  c->d_logf, c->d_e1, c->d_e2, c->d_e3, c->d_e4, c->d_fb, c->d_fb_cnt, c->d_utab,
+                  c->d_prob_cnt};
   for (void *b : bufs)
     if (b) cudaFree(b);
   delete c;
@@ -523,6 +525,29 @@ cfust_status cfust_set_surrogate(cfust_ctx *c, cfust_surrogate *s) {
   drop_graph(c);
   c->sur = s;
   c->fb_cap = 0;  // (re)allocated by the next call that knows n
+  return CFUST_OK;
+}
+
+cfust_status cfust_surrogate_problems(cfust_ctx *c, const double *Y, int64_t n, const cfust_params *P,
+                                      int64_t stride, float *x_out, int64_t max_rows, int64_t *rows) {
+  cfust_status s = check_common(c, Y, n, P);
+  if (s != CFUST_OK) return s;
+  if (P->r != 3) return fail(c, CFUST_EINVAL, "the surrogate's problems need r = 3");
+  if (stride < 1 || max_rows < 0 || !rows || (max_rows > 0 && !x_out))
+    return fail(c, CFUST_EINVAL, "stride >= 1, max_rows >= 0, rows and x_out required");
+  DeviceGuard dg(c->device);
+  if ((s = ensure(c, P->g, P->p, P->r, n)) != CFUST_OK) return s;
+  if ((s = upload_params(c, P)) != CFUST_OK) return s;
+  if (!c->d_prob_cnt) CF_CUDA(c, cudaMalloc(&c->d_prob_cnt, sizeof(unsigned long long)));
+  CF_CUDA(c, cudaMemsetAsync(c->d_status, 0, 2 * sizeof(int), c->stream));
+  CF_CUDA(c, launch_precompute(c->d_params, c->g, c->p, c->r, c->lat, c->d_c64, c->d_c32, c->d_chi64,
+                               c->d_chi32, c->d_status, c->stream));
+  CF_CUDA(c, launch_surrogate_problems(Y, n, c->g, c->p, c->d_c32, stride, x_out, max_rows, c->d_prob_cnt,
+                                       c->stream));
+  unsigned long long cnt = 0;
+  CF_CUDA(c, cudaMemcpyAsync(&cnt, c->d_prob_cnt, sizeof(cnt), cudaMemcpyDeviceToHost, c->stream));
+  if ((s = finish(c)) != CFUST_OK) return s;
+  *rows = (int64_t)cnt < max_rows ? (int64_t)cnt : max_rows;
   return CFUST_OK;
 }
 

@@ -152,6 +152,13 @@ struct SurrogateDev {
 
 SurrogateDev surrogate_dev(const cfust_surrogate *s);
 
+// Standardised problems (network inputs, two rows per pair) of every
+// stride-th pair in the network's domain into x_out [max_rows][7]; the number
+// of rows wanted goes to *count (device).
+cudaError_t launch_surrogate_problems(const double *Y, int64_t n, int g, int p, const CompT<float> *c32,
+                                      int64_t stride, float *x_out, int64_t max_rows, unsigned long long *count,
+                                      cudaStream_t st);
+
 // Surrogate E-step (FP32 outputs, r = 3): for every pair whose standardised
 // problem lies in the training domain the network gives log T_A, T_B and the
 // pass-B moments, from which log f and e1..e4 are formed as in the lattice

@@ -26,6 +26,7 @@
 #include <cmath>
 #include <cstring>
 #include <string>
+#include <utility>
 #include <vector>
 
 #include "cfust_internal.cuh"
@@ -882,10 +883,45 @@ __global__ void __launch_bounds__(GROUP_THREADS * GROUPS, 1)
   }
 }
 
+// The standardised problems (network inputs of pass A and pass B) of every
+// stride-th (i, j) pair in the network's domain, appended to x_out [max_rows][7]
+// two rows per pair; *count receives the number of rows wanted.
+__global__ void problems_kernel(const double *Y, int64_t n, int g, int p, const CompT<float> *comp, int64_t stride,
+                                float *x_out, int64_t max_rows, unsigned long long *count) {
+  const int64_t k = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) * stride;
+  if (k >= (int64_t)g * n) return;
+  const int i = (int)(k / n);
+  const int64_t j = k % n;
+  const RowProblem ra = row_problem(comp[i], Y, p, j, 0);
+  if (ra.kind != 2) return;
+  const RowProblem rb = row_problem(comp[i], Y, p, j, 1);
+  const unsigned long long slot = atomicAdd(count, 2ull);
+  if ((int64_t)slot + 2 > max_rows) return;
+  float *xa = x_out + (int64_t)slot * DIN;
+  const RowProblem *rr[2] = {&ra, &rb};
+  for (int q = 0; q < 2; ++q) {
+    float *xr = xa + q * DIN;
+    for (int t = 0; t < 3; ++t) xr[t] = rr[q]->c[t];
+    for (int t = 0; t < 3; ++t) xr[3 + t] = rr[q]->R[t];
+    xr[6] = rr[q]->logm;
+  }
+}
+
 }  // namespace sg
 }  // namespace cfust
 
 namespace cfust {
+
+cudaError_t launch_surrogate_problems(const double *Y, int64_t n, int g, int p, const CompT<float> *c32,
+                                      int64_t stride, float *x_out, int64_t max_rows, unsigned long long *count,
+                                      cudaStream_t st) {
+  cudaError_t e = cudaMemsetAsync(count, 0, sizeof(unsigned long long), st);
+  if (e != cudaSuccess) return e;
+  const int64_t m = ((int64_t)g * n + stride - 1) / stride;
+  if (m <= 0) return cudaSuccess;
+  sg::problems_kernel<<<(unsigned)((m + 255) / 256), 256, 0, st>>>(Y, n, g, p, c32, stride, x_out, max_rows, count);
+  return cudaGetLastError();
+}
 
 cudaError_t launch_surrogate_estep(const SurrogateDev &sd, const double *Y, int64_t n, int g, int p,
                                    const CompT<float> *c32, EstepOut out, bool density_only, int *fb_list,
@@ -1158,6 +1194,42 @@ struct SplitMix {
   }
 };
 
+// Adam (beta 0.9, 0.999, eps 1e-8) on mini-batches of `batch` consecutive
+// rows of (dx, dy), `epochs` passes, step size cosine-decayed from lr over the
+// run; loss_trace[ep] = mean of the sampled batch losses of epoch ep.
+cfust_status train_loop(cfust_surrogate *s, const float *dx, const float *dy, int64_t rows, int epochs, int batch,
+                        float lr, float *loss_trace) {
+  cfust_status st = CFUST_OK;
+  const int64_t steps = rows / batch;
+  for (int ep = 0; ep < epochs; ++ep) {
+    double ep_loss = 0.0;
+    for (int64_t k = 0; k < steps; ++k) {
+      const int64_t off = k * batch;
+      if ((st = prep(s, dx + off * DIN, batch)) != CFUST_OK) break;
+      double l = 0.0;
+      if ((st = loss_grad(s, dy + off * DOUT, batch, (k % 64 == 0) ? &l : nullptr)) != CFUST_OK) break;
+      ep_loss += l;
+      ++s->adam_t;
+      const float b1 = 0.9f, b2 = 0.999f;
+      const float c1 = 1.f - powf(b1, (float)s->adam_t), c2 = 1.f - powf(b2, (float)s->adam_t);
+      const float frac = (float)(ep * steps + k) / (float)(epochs * steps);
+      const float lr_t = lr * 0.5f * (1.f + cosf(3.14159265f * frac));
+      adam_kernel<<<(NPARAM + 255) / 256, 256, 0, s->stream>>>(s->theta, s->mom, s->vel, s->grad, NPARAM, lr_t, b1,
+                                                               b2, 1e-8f, c1, c2);
+      if (cudaGetLastError() != cudaSuccess) {
+        st = sg_fail(s, CFUST_ECUDA, "adam_kernel launch");
+        break;
+      }
+      if ((st = pack(s)) != CFUST_OK) break;
+    }
+    if (st != CFUST_OK) break;
+    if (loss_trace) loss_trace[ep] = (float)(ep_loss / (double)((steps + 63) / 64));
+  }
+  if (st != CFUST_OK) return st;
+  SG_CUDA(s, cudaStreamSynchronize(s->stream));
+  return CFUST_OK;
+}
+
 }  // namespace
 
 extern "C" {
@@ -1374,32 +1446,48 @@ cfust_status cfust_surrogate_train(cfust_surrogate *s, int64_t n_train, int epoc
     }
     SG_CUDA(s, cudaMemcpy(s->norm, s->host_norm, sizeof(float) * 20, cudaMemcpyHostToDevice));
   }
-  const int64_t steps = n_train / batch;
-  for (int ep = 0; ep < epochs; ++ep) {
-    double ep_loss = 0.0;
-    for (int64_t k = 0; k < steps; ++k) {
-      const int64_t off = k * batch;
-      if ((st = prep(s, dx + off * DIN, batch)) != CFUST_OK) break;
-      double l = 0.0;
-      if ((st = loss_grad(s, dy + off * DOUT, batch, (k % 64 == 0) ? &l : nullptr)) != CFUST_OK) break;
-      ep_loss += l;
-      ++s->adam_t;
-      const float b1 = 0.9f, b2 = 0.999f;
-      const float c1 = 1.f - powf(b1, (float)s->adam_t), c2 = 1.f - powf(b2, (float)s->adam_t);
-      // cosine decay over the whole run
-      const float frac = (float)(ep * steps + k) / (float)(epochs * steps);
-      const float lr_t = lr * 0.5f * (1.f + cosf(3.14159265f * frac));
-      adam_kernel<<<(NPARAM + 255) / 256, 256, 0, s->stream>>>(s->theta, s->mom, s->vel, s->grad, NPARAM, lr_t, b1,
-                                                               b2, 1e-8f, c1, c2);
-      if (cudaGetLastError() != cudaSuccess) { st = CFUST_ECUDA; break; }
-      if ((st = pack(s)) != CFUST_OK) break;
-    }
-    if (st != CFUST_OK) break;
-    if (loss_trace) loss_trace[ep] = (float)(ep_loss / (double)((steps + 63) / 64));
-  }
+  return train_loop(s, dx, dy, n_train, epochs, batch, lr, loss_trace);
+}
+
+cfust_status cfust_surrogate_finetune(cfust_surrogate *s, const float *x, int64_t rows, int epochs, int batch,
+                                      float lr, uint64_t seed, float *loss_trace) {
+  if (!s || !x || rows < batch || batch < 128 || epochs < 1 || !(lr > 0.f) || rows > MAX_ROWS)
+    return sg_fail(s, CFUST_EINVAL, "need 128 <= batch <= rows <= 2^30, epochs >= 1, lr > 0");
+  // label the given problems, drop rows without finite labels and shuffle
+  // (callers pass problems grouped by component and observation)
+  DevBuf by;
+  SG_CUDA(s, cudaMalloc(&by.p, sizeof(float) * rows * DOUT));
+  cfust_status st = cfust_surrogate_label(s, x, by.p, rows);
   if (st != CFUST_OK) return st;
-  SG_CUDA(s, cudaStreamSynchronize(s->stream));
-  return CFUST_OK;
+  std::vector<float> hx(rows * DIN), hy(rows * DOUT);
+  SG_CUDA(s, cudaMemcpy(hx.data(), x, sizeof(float) * rows * DIN, cudaMemcpyDeviceToHost));
+  SG_CUDA(s, cudaMemcpy(hy.data(), by.p, sizeof(float) * rows * DOUT, cudaMemcpyDeviceToHost));
+  std::vector<int64_t> keep;
+  keep.reserve(rows);
+  for (int64_t b = 0; b < rows; ++b) {
+    bool fin = true;
+    for (int k = 0; k < DOUT; ++k) fin = fin && std::isfinite(hy[b * DOUT + k]);
+    if (fin) keep.push_back(b);
+  }
+  const int64_t kept = (int64_t)keep.size();
+  if (kept < batch) return sg_fail(s, CFUST_ENUMERIC, "too few finite labels");
+  SplitMix rng{seed};
+  for (int64_t a = kept - 1; a > 0; --a) {
+    const int64_t b = (int64_t)(rng.next() % (uint64_t)(a + 1));
+    std::swap(keep[a], keep[b]);
+  }
+  std::vector<float> sx(kept * DIN), sy(kept * DOUT);
+  for (int64_t a = 0; a < kept; ++a) {
+    memcpy(&sx[a * DIN], &hx[keep[a] * DIN], sizeof(float) * DIN);
+    memcpy(&sy[a * DOUT], &hy[keep[a] * DOUT], sizeof(float) * DOUT);
+  }
+  DevBuf bx, by2;
+  SG_CUDA(s, cudaMalloc(&bx.p, sizeof(float) * kept * DIN));
+  SG_CUDA(s, cudaMalloc(&by2.p, sizeof(float) * kept * DOUT));
+  SG_CUDA(s, cudaMemcpy(bx.p, sx.data(), sizeof(float) * kept * DIN, cudaMemcpyHostToDevice));
+  SG_CUDA(s, cudaMemcpy(by2.p, sy.data(), sizeof(float) * kept * DOUT, cudaMemcpyHostToDevice));
+  // the target normalisation stays as trained
+  return train_loop(s, bx.p, by2.p, kept, epochs, batch, lr, loss_trace);
 }
 
 }  // extern "C"

@@ -303,3 +303,38 @@ def test_surrogate_edge_cases(lat8192):
     sur.cfust_set_surrogate(None)
     assert sur.cfust_loglik(Yd, truth) == plain.cfust_loglik(Yd, truth)
     assert sur.cfust_last_fallback() == 0
+
+
+def test_problems_and_finetune(lat8192):
+    """cfust_surrogate_problems returns the network inputs of exactly the pairs
+    the surrogate E-step keeps (two rows each, inside the domain box), and
+    fine-tuning on them lowers the network's error on those problems."""
+    torch = _torch()
+    s = binding.Surrogate(lat8192, seed=12)
+    s.cfust_surrogate_train(1 << 19, 3, batch=4096, lr=3e-3, seed=4)
+    Y, _, truth, _, _, _ = synth.workload("cfust_p3r3g4_n1000000_N2048", n=6000, seed=2)
+    Yd = torch.tensor(Y, dtype=torch.float64, device="cuda")
+    ctx = binding.Context(synth.make_lattice(256, 4, seed=0), precision=binding.CFUST_FP32)
+    x = ctx.cfust_surrogate_problems(Yd, truth)
+    ctx.cfust_set_surrogate(s)
+    ctx.cfust_estep(Yd, truth)
+    kept = truth.g * len(Y) - ctx.cfust_last_fallback()
+    assert x.shape[0] == 2 * kept
+    xn = x.cpu().numpy().astype(np.float64)
+    assert np.all(xn[:, :3] >= MO.C_LO - 1e-6) and np.all(xn[:, :3] <= MO.C_HI + 1e-6)
+    assert np.all(np.abs(xn[:, 3:6]) <= MO.RHO_MAX + 1e-6)
+    assert np.all((xn[:, 6] >= MO.LOGM_LO - 1e-5) & (xn[:, 6] <= MO.LOGM_HI + 1e-5))
+    # every other row: a stride of 3 keeps a third of the pairs
+    x3 = ctx.cfust_surrogate_problems(Yd, truth, stride=3)
+    assert abs(x3.shape[0] - x.shape[0] / 3) <= 0.05 * x.shape[0] / 3 + 4
+
+    def err():
+        y = s.cfust_surrogate_label(x).cpu().numpy()
+        p = s.cfust_surrogate_predict(x).cpu().numpy()
+        _, norm = s.cfust_surrogate_get_params()
+        ok = np.all(np.isfinite(y), axis=1)
+        return float(np.sqrt(np.mean((MO.net_targets(p[ok], norm) - MO.net_targets(y[ok], norm)) ** 2)))
+    before = err()
+    trace = s.cfust_surrogate_finetune(x, 4, batch=1024, lr=1e-3, seed=5)
+    assert np.all(np.isfinite(trace))
+    assert err() < 0.8 * before
