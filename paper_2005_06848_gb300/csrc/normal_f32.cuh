@@ -92,15 +92,19 @@ namespace nf32 {
 struct Pairs {
   float2 tail_q[7];
   float2 p0[7];
-  float2 p3[10];
+  float2 p3[10];  // the tail quantile piece times -sqrt(ln 2) (see neg_quantile_x2)
 };
+constexpr float NSQRT_LN2 = -0.832554611158f;
 __constant__ Pairs kPairs = {
     {{TAIL_QF[0], TAIL_QF[0]}, {TAIL_QF[1], TAIL_QF[1]}, {TAIL_QF[2], TAIL_QF[2]}, {TAIL_QF[3], TAIL_QF[3]},
      {TAIL_QF[4], TAIL_QF[4]}, {TAIL_QF[5], TAIL_QF[5]}, {TAIL_QF[6], TAIL_QF[6]}},
     {{Q_P0F[0], Q_P0F[0]}, {Q_P0F[1], Q_P0F[1]}, {Q_P0F[2], Q_P0F[2]}, {Q_P0F[3], Q_P0F[3]}, {Q_P0F[4], Q_P0F[4]},
      {Q_P0F[5], Q_P0F[5]}, {Q_P0F[6], Q_P0F[6]}},
-    {{Q_P3[0], Q_P3[0]}, {Q_P3[1], Q_P3[1]}, {Q_P3[2], Q_P3[2]}, {Q_P3[3], Q_P3[3]}, {Q_P3[4], Q_P3[4]},
-     {Q_P3[5], Q_P3[5]}, {Q_P3[6], Q_P3[6]}, {Q_P3[7], Q_P3[7]}, {Q_P3[8], Q_P3[8]}, {Q_P3[9], Q_P3[9]}}};
+    {{Q_P3[0] * NSQRT_LN2, Q_P3[0] * NSQRT_LN2}, {Q_P3[1] * NSQRT_LN2, Q_P3[1] * NSQRT_LN2},
+     {Q_P3[2] * NSQRT_LN2, Q_P3[2] * NSQRT_LN2}, {Q_P3[3] * NSQRT_LN2, Q_P3[3] * NSQRT_LN2},
+     {Q_P3[4] * NSQRT_LN2, Q_P3[4] * NSQRT_LN2}, {Q_P3[5] * NSQRT_LN2, Q_P3[5] * NSQRT_LN2},
+     {Q_P3[6] * NSQRT_LN2, Q_P3[6] * NSQRT_LN2}, {Q_P3[7] * NSQRT_LN2, Q_P3[7] * NSQRT_LN2},
+     {Q_P3[8] * NSQRT_LN2, Q_P3[8] * NSQRT_LN2}, {Q_P3[9] * NSQRT_LN2, Q_P3[9] * NSQRT_LN2}}};
 
 template <int K>
 __device__ __forceinline__ float2 horner2(const float2 (&c)[K], float2 t) {
@@ -135,11 +139,16 @@ __device__ __forceinline__ float2 neg_quantile_x2(float um, float u, float2 p, f
   const bool lx = x.x <= 0.5f, ly = x.y <= 0.5f;
   const float2 xs = make_float2(lx ? fmaxf(x.x, 1.17549435e-38f) : c.x, ly ? fmaxf(x.y, 1.17549435e-38f) : c.y);
   const float2 prod = __fmul2_rn(xs, __ffma2_rn(xs, f2(-4.0f), f2(4.0f)));  // 4 x (1 - x), exactly
-  const float2 w = make_float2(-__logf(prod.x), -__logf(prod.y));
-  const float2 pc = nf32::horner2(nf32::kPairs.p0, __fadd2_rn(w, f2(-nf32::Q_W0F)));
-  const float2 rs = make_float2(rsqrtf(w.x), rsqrtf(w.y));
-  const float2 pt = __fmul2_rn(nf32::horner2(nf32::kPairs.p3, __fadd2_rn(rs, f2(-nf32::Q_U3))), __fmul2_rn(w, rs));
-  const float2 P = make_float2(w.x < 5.0f ? pc.x : pt.x, w.y < 5.0f ? pc.y : pt.y);
+  // with l = log2(4 x (1 - x)) <= 0, w = -ln2 l: the central argument is one
+  // fused step from l, and 1/sqrt(w) = rsqrt(-l)/sqrt(ln2), sqrt(w) =
+  // -sqrt(ln2) l rsqrt(-l), the constant factor living in the tail coefficients
+  const float2 l = make_float2(__log2f(prod.x), __log2f(prod.y));
+  const float2 pc = nf32::horner2(nf32::kPairs.p0, __ffma2_rn(l, f2(-0.69314718056f), f2(-nf32::Q_W0F)));
+  const float2 rn = make_float2(rsqrtf(-l.x), rsqrtf(-l.y));
+  const float2 pt = __fmul2_rn(nf32::horner2(nf32::kPairs.p3, __ffma2_rn(rn, f2(1.20112240879f), f2(-nf32::Q_U3))),
+                               __fmul2_rn(l, rn));
+  // w < 5  <=>  l > -5 / ln2
+  const float2 P = make_float2(l.x > -7.21347520444f ? pc.x : pt.x, l.y > -7.21347520444f ? pc.y : pt.y);
   const float2 v = __ffma2_rn(f2(2.82842712475f), xs, f2(-1.41421356237f));  // sqrt(2) (2x - 1)
   const float2 zq = __fmul2_rn(v, P);
   return make_float2(lx ? -zq.x : zq.x, ly ? -zq.y : zq.y);
