@@ -14,11 +14,15 @@
 //
 // Labels come from the plain lattice evaluator (Genz separation of variables
 // on the shifted Korobov lattice) with chi-scale tables on a grid of 256
-// values of log m over [log 3, log 30]; the same evaluator judges the error.
+// values of log m over [log 3, log 30], interpolated linearly in log m; the
+// same evaluator judges the error.
 //
-// Training domain (and the E-step's test for using the network):
-// -8 <= c_t <= 4, |R_ht| <= 0.9, every squared Cholesky pivot of R >= 0.05,
-// m in [3, 30].
+// Training domain: -8 <= c_t <= 4, |R_ht| <= 0.9, every squared Cholesky
+// pivot of R >= 0.05, m in [3, 30].  The E-step uses the network for a pair
+// whose pass-B point lies in the box (below it too once nu + p >= 8, where a
+// coordinate under -8 is clamped: it moves P by at most P(t_8 < -8)); the
+// other pairs go to the lattice rule with an upper bound of their log T for
+// its triage.
 #include <cuda_bf16.h>
 #include <math.h>
 #include <stdio.h>
