@@ -499,14 +499,17 @@ __global__ void __launch_bounds__(256) label_kernel(const float *x, float *y, in
 
 // ---------------------------------------------------------------------------
 // Fused surrogate E-step.  A CTA holds the whole network in shared memory
-// (weights transposed to [out][in] for the B fragments) and runs two
-// independent 8-warp groups; each group takes tiles of 64 (i, j) pairs, i.e.
-// 128 network rows (pass A and pass B of every pair; 128 pairs and pass A
-// only for the density), and keeps the activations of its tile in shared
-// memory from the standardised inputs to the E-step outputs.
+// (weights transposed to [out][in] for the B fragments); each of its 16 warps
+// independently takes tiles of 8 (i, j) pairs = 16 network rows (pass A and
+// pass B of every pair; 16 pairs and pass A only for the density) and carries
+// them through the four layers in registers: the accumulator fragments of a
+// layer are, pair by pair of n-tiles, exactly the A fragments of the next
+// layer's m16n8k16 MMAs, so activations never leave the warp and the loop has
+// no block barrier.  Per-warp shared scratch holds only the inputs and the
+// outputs of the tile.
 // ---------------------------------------------------------------------------
-constexpr int TROWS = 128, HP = H + 8, XP = DINP + 8, OP = DOUTP + 1;
-constexpr int GROUP_THREADS = 256, GROUPS = 2;
+constexpr int HP = H + 8, XP = DINP + 8, OP = DOUTP + 1;
+constexpr int WARPS = 16, WROWS = 16;
 
 struct InferWeights {
   bf16 W1t[H * XP];
@@ -516,79 +519,60 @@ struct InferWeights {
   float bias[3 * H + DOUTP];
   float norm[2 * DOUT];
 };
-struct InferGroup {
-  bf16 X[TROWS * XP];
-  bf16 Hb[TROWS * HP];
-  float O[TROWS * OP];
-  float logt[TROWS], nud[TROWS], q[3 * TROWS], cmax[TROWS];
-  int ok[TROWS];
+struct WarpScratch {
+  bf16 X[WROWS * XP];
+  float O[WROWS * OP];
+  float logt[WROWS], nud[WROWS], q[3 * WROWS], cmax[WROWS];
+  int kind[WROWS];
 };
-constexpr size_t INFER_SMEM = sizeof(InferWeights) + GROUPS * sizeof(InferGroup);
-static_assert(sizeof(InferWeights) % 16 == 0, "group blocks must stay 16-byte aligned");
-static_assert(sizeof(InferGroup) % 16 == 0, "group blocks must stay 16-byte aligned");
-
-__device__ __forceinline__ void group_sync(int grp) {
-  asm volatile("bar.sync %0, %1;" ::"r"(grp + 1), "r"(GROUP_THREADS) : "memory");
-}
+constexpr size_t INFER_SMEM = sizeof(InferWeights) + WARPS * sizeof(WarpScratch);
+static_assert(sizeof(InferWeights) % 16 == 0, "scratch blocks must stay 16-byte aligned");
+static_assert(sizeof(WarpScratch) % 16 == 0, "scratch blocks must stay 16-byte aligned");
 
 __device__ __forceinline__ uint32_t ld32(const bf16 *p) { return *reinterpret_cast<const uint32_t *>(p); }
 
-// acc (32 x 64 tile of warp w: rows 32 (w >> 1), cols 64 (w & 1)) = A[128 x K] Wt^T
-template <int K>
-__device__ __forceinline__ void mma_32x64(const bf16 *A, int ap, const bf16 *Wt, int wp, int w, int lane,
-                                          float (&acc)[2][8][4]) {
-  const int wm = w >> 1, wn = w & 1, gid = lane >> 2, tig = lane & 3;
+__device__ __forceinline__ uint32_t pack_bf16x2(float lo, float hi) {
+  const __nv_bfloat162 v = __floats2bfloat162_rn(lo, hi);
+  return *reinterpret_cast<const uint32_t *>(&v);
+}
+
+// One hidden layer for the warp's 16 rows: out = GELU(in Wt^T + bias), with
+// `in` as KT k-tiles of A fragments and `out` as the 8 k-tiles (128 columns)
+// of the next layer's A fragments.  Computed in two halves of 64 columns to
+// bound the live accumulators.
+template <int KT>
+__device__ __forceinline__ void dense_gelu(const uint32_t (&in)[KT][4], const bf16 *Wt, int wp, const float *bias,
+                                           uint32_t (&out)[8][4], int gid, int tig) {
 #pragma unroll
-  for (int a = 0; a < 2; ++a)
+  for (int half = 0; half < 2; ++half) {
+    float acc[8][4];
 #pragma unroll
-    for (int b = 0; b < 8; ++b)
+    for (int nt = 0; nt < 8; ++nt)
 #pragma unroll
-      for (int c = 0; c < 4; ++c) acc[a][b][c] = 0.f;
+      for (int c = 0; c < 4; ++c) acc[nt][c] = 0.f;
 #pragma unroll
-  for (int ks = 0; ks < K; ks += 16) {
-    uint32_t af[2][4], bfr[8][2];
+    for (int kt = 0; kt < KT; ++kt)
 #pragma unroll
-    for (int mi = 0; mi < 2; ++mi) {
-      const bf16 *r0 = A + (wm * 32 + mi * 16 + gid) * ap + ks + tig * 2;
-      af[mi][0] = ld32(r0);
-      af[mi][1] = ld32(r0 + 8 * ap);
-      af[mi][2] = ld32(r0 + 8);
-      af[mi][3] = ld32(r0 + 8 * ap + 8);
+      for (int nt = 0; nt < 8; ++nt) {
+        const bf16 *c0 = Wt + ((half * 8 + nt) * 8 + gid) * wp + kt * 16 + tig * 2;
+        const uint32_t b[2] = {ld32(c0), ld32(c0 + 8)};
+        mma_bf16(acc[nt], in[kt], b);
+      }
+    // columns 16 q .. 16 q + 15 (n-tiles 2q and 2q + 1) form k-tile q of the
+    // next layer: (row gid | gid + 8) x (k 2 tig, 2 tig + 1 | + 8)
+#pragma unroll
+    for (int nt = 0; nt < 8; nt += 2) {
+      const int q = half * 4 + nt / 2;
+      const int col0 = (half * 8 + nt) * 8 + tig * 2, col1 = col0 + 8;
+      const float b00 = bias[col0], b01 = bias[col0 + 1], b10 = bias[col1], b11 = bias[col1 + 1];
+      out[q][0] = pack_bf16x2(gelu_f(acc[nt][0] + b00), gelu_f(acc[nt][1] + b01));
+      out[q][1] = pack_bf16x2(gelu_f(acc[nt][2] + b00), gelu_f(acc[nt][3] + b01));
+      out[q][2] = pack_bf16x2(gelu_f(acc[nt + 1][0] + b10), gelu_f(acc[nt + 1][1] + b11));
+      out[q][3] = pack_bf16x2(gelu_f(acc[nt + 1][2] + b10), gelu_f(acc[nt + 1][3] + b11));
     }
-#pragma unroll
-    for (int nj = 0; nj < 8; ++nj) {
-      const bf16 *c0 = Wt + (wn * 64 + nj * 8 + gid) * wp + ks + tig * 2;
-      bfr[nj][0] = ld32(c0);
-      bfr[nj][1] = ld32(c0 + 8);
-    }
-#pragma unroll
-    for (int mi = 0; mi < 2; ++mi)
-#pragma unroll
-      for (int nj = 0; nj < 8; ++nj) mma_bf16(acc[mi][nj], af[mi], bfr[nj]);
   }
 }
 
-// Hb[rows][cols of warp w] = GELU(acc + bias), BF16
-__device__ __forceinline__ void store_gelu(bf16 *Hb, const float *bias, int w, int lane,
-                                           const float (&acc)[2][8][4]) {
-  const int wm = w >> 1, wn = w & 1, gid = lane >> 2, tig = lane & 3;
-#pragma unroll
-  for (int mi = 0; mi < 2; ++mi)
-#pragma unroll
-    for (int nj = 0; nj < 8; ++nj) {
-      const int row = wm * 32 + mi * 16 + gid, col = wn * 64 + nj * 8 + tig * 2;
-      const float b0 = bias[col], b1 = bias[col + 1];
-      *reinterpret_cast<__nv_bfloat162 *>(Hb + row * HP + col) =
-          __floats2bfloat162_rn(gelu_f(acc[mi][nj][0] + b0), gelu_f(acc[mi][nj][1] + b1));
-      *reinterpret_cast<__nv_bfloat162 *>(Hb + (row + 8) * HP + col) =
-          __floats2bfloat162_rn(gelu_f(acc[mi][nj][2] + b0), gelu_f(acc[mi][nj][3] + b1));
-    }
-}
-
-// Standardised problem of one network row: pair (i, j), pass 0 (dof nu + p,
-// limits a_A) or 1 (nu + p + 2, a_B).  X = L V with L = chol(Lambda) is
-// t_3(0, Lambda, m); with D = diag(Lambda), X' = D^{-1/2} X is t_3(0, R, m)
-// and L V > a holds exactly when X' > c = D^{-1/2} a.
 // Nearest-structure PSD repair of a predicted 3x3 covariance (upper order
 // 00 01 02 11 12 22): LDL^T with every pivot floored at PSD_FLOOR, rebuilt.
 // A positive definite input comes back unchanged up to rounding; a
@@ -609,6 +593,10 @@ __device__ __forceinline__ void psd_repair3(float *v) {
   v[5] = fmaf(l20 * l20, d0, fmaf(l21 * l21, d1, d2));
 }
 
+// Standardised problem of one network row: pair (i, j), pass 0 (dof nu + p,
+// limits a_A) or 1 (nu + p + 2, a_B).  X = L V with L = chol(Lambda) is
+// t_3(0, Lambda, m); with D = diag(Lambda), X' = D^{-1/2} X is t_3(0, R, m)
+// and L V > a holds exactly when X' > c = D^{-1/2} a.
 struct RowProblem {
   float c[3], R[3], logm;  // network input (c clamped into the box)
   float logt, nud, q[3];
@@ -681,7 +669,7 @@ __device__ __forceinline__ RowProblem row_problem(const CompT<float> &c, const d
 }
 
 template <bool DENS>
-__global__ void __launch_bounds__(GROUP_THREADS * GROUPS, 1)
+__global__ void __launch_bounds__(WARPS * 32, 1)
     surrogate_estep_kernel(SurrogateDev sd, const double *Y, int64_t n, int g, int p,
                            const CompT<float> *__restrict__ comp, EstepOut out, int *fb_list, unsigned *fb_count) {
   extern __shared__ __align__(128) unsigned char smem[];
@@ -711,29 +699,30 @@ __global__ void __launch_bounds__(GROUP_THREADS * GROUPS, 1)
     if (tid < DOUTP) Wsm.bias[3 * H + tid] = sd.b4[tid];
     if (tid < 2 * DOUT) Wsm.norm[tid] = sd.norm[tid];
   }
-  __syncthreads();
+  __syncthreads();  // the only block barrier: the warps are independent from here
 
-  const int grp = tid / GROUP_THREADS, gt = tid % GROUP_THREADS;
-  const int w = gt >> 5, lane = gt & 31;
-  InferGroup &G = *reinterpret_cast<InferGroup *>(smem + sizeof(InferWeights) + grp * sizeof(InferGroup));
-  constexpr int PPT = DENS ? TROWS : TROWS / 2;  // pairs per tile
+  const int warp = tid >> 5, lane = tid & 31, gid = lane >> 2, tig = lane & 3;
+  WarpScratch &S = *reinterpret_cast<WarpScratch *>(smem + sizeof(InferWeights) + warp * sizeof(WarpScratch));
+  constexpr int PPT = DENS ? WROWS : WROWS / 2;  // pairs per warp tile
   const int64_t tpc = (n + PPT - 1) / PPT;
   const int64_t ntiles = tpc * g;
   const float logm_mid = (float)(LOGM_LO + LOGM_HI), logm_scale = (float)(2.0 / (LOGM_HI - LOGM_LO));
+  const float cs = 2.f / (C_HI - C_LO), cm = C_LO + C_HI;
 
-  for (int64_t tile = (int64_t)blockIdx.x * GROUPS + grp; tile < ntiles; tile += (int64_t)gridDim.x * GROUPS) {
+  for (int64_t tile = (int64_t)blockIdx.x * WARPS + warp; tile < ntiles; tile += (int64_t)gridDim.x * WARPS) {
     const int i = (int)(tile / tpc);
     const int64_t j0 = (tile % tpc) * PPT;
     const CompT<float> &c = comp[i];
-    group_sync(grp);  // the previous tile's epilogue has read O and the pair values
-    if (gt < TROWS) {
-      const int row = gt;
+    // prep: lanes 0..15 are the tile's rows
+    bool push = false;
+    int64_t push_j = 0;
+    if (lane < WROWS) {
+      const int row = lane;
       const int pair = DENS ? row : row >> 1, pass = DENS ? 0 : (row & 1);
       const int64_t j = j0 + pair;
-      bf16 *xr = G.X + row * XP;
+      bf16 *xr = S.X + row * XP;
       if (j < n) {
         const RowProblem rp = row_problem(c, Y, p, j, pass);
-        const float cs = 2.f / (C_HI - C_LO), cm = C_LO + C_HI;
         const float u[DIN] = {(2.f * rp.c[0] - cm) * 0.5f * cs, (2.f * rp.c[1] - cm) * 0.5f * cs,
                               (2.f * rp.c[2] - cm) * 0.5f * cs, rp.R[0] / RHO_MAX, rp.R[1] / RHO_MAX,
                               rp.R[2] / RHO_MAX, (2.f * rp.logm - logm_mid) * (0.5f * logm_scale)};
@@ -742,148 +731,157 @@ __global__ void __launch_bounds__(GROUP_THREADS * GROUPS, 1)
           *reinterpret_cast<__nv_bfloat162 *>(xr + t) =
               __floats2bfloat162_rn(t < DIN ? u[t] : 0.f, t + 1 < DIN ? u[t + 1] : 0.f);
         if (pass == 0) {
-          G.logt[pair] = rp.logt;
-          G.nud[pair] = rp.nud;
-          G.q[3 * pair] = rp.q[0];
-          G.q[3 * pair + 1] = rp.q[1];
-          G.q[3 * pair + 2] = rp.q[2];
-          G.ok[pair] = rp.kind;
-          G.cmax[pair] = rp.cmaxA;
-          if (rp.kind != 2) {
-            const unsigned slot = atomicAdd(fb_count + i, 1u);
-            fb_list[(int64_t)i * n + slot] = (int)j;
-          }
+          S.logt[pair] = rp.logt;
+          S.nud[pair] = rp.nud;
+          S.q[3 * pair] = rp.q[0];
+          S.q[3 * pair + 1] = rp.q[1];
+          S.q[3 * pair + 2] = rp.q[2];
+          S.kind[pair] = rp.kind;
+          S.cmax[pair] = rp.cmaxA;
+          push = (rp.kind != 2);
+          push_j = j;
         }
       } else {
 #pragma unroll
         for (int t = 0; t < DINP; t += 2)
           *reinterpret_cast<__nv_bfloat162 *>(xr + t) = __floats2bfloat162_rn(0.f, 0.f);
-        if (pass == 0) G.ok[pair] = 0;
+        if (pass == 0) S.kind[pair] = -1;
       }
     }
-    group_sync(grp);
-    float acc[2][8][4];
-    mma_32x64<DINP>(G.X, XP, Wsm.W1t, XP, w, lane, acc);
-    store_gelu(G.Hb, Wsm.bias, w, lane, acc);
-    group_sync(grp);
-    mma_32x64<H>(G.Hb, HP, Wsm.W2t, HP, w, lane, acc);
-    group_sync(grp);
-    store_gelu(G.Hb, Wsm.bias + H, w, lane, acc);
-    group_sync(grp);
-    mma_32x64<H>(G.Hb, HP, Wsm.W3t, HP, w, lane, acc);
-    group_sync(grp);
-    store_gelu(G.Hb, Wsm.bias + 2 * H, w, lane, acc);
-    group_sync(grp);
+    // pairs outside the domain go to the lattice rule's list: one atomic per warp
+    const unsigned pm = __ballot_sync(0xffffffffu, push);
+    if (pm) {
+      unsigned base = 0;
+      if (lane == 0) base = atomicAdd(fb_count + i, (unsigned)__popc(pm));
+      base = __shfl_sync(0xffffffffu, base, 0);
+      if (push) fb_list[(int64_t)i * n + base + __popc(pm & ((1u << lane) - 1u))] = (int)push_j;
+    }
+    __syncwarp();
+
+    // layer 1: A fragment of the 16 x 16 (zero-padded) input tile
+    uint32_t a0[1][4];
     {
-      // output layer: warp w takes rows 16 w .. 16 w + 15, all 16 columns
-      const int gid = lane >> 2, tig = lane & 3;
+      const bf16 *r0 = S.X + gid * XP + tig * 2;
+      a0[0][0] = ld32(r0);
+      a0[0][1] = ld32(r0 + 8 * XP);
+      a0[0][2] = ld32(r0 + 8);
+      a0[0][3] = ld32(r0 + 8 * XP + 8);
+    }
+    uint32_t h1[8][4], h2[8][4];
+    dense_gelu<1>(a0, Wsm.W1t, XP, Wsm.bias, h1, gid, tig);
+    dense_gelu<8>(h1, Wsm.W2t, HP, Wsm.bias + H, h2, gid, tig);
+    dense_gelu<8>(h2, Wsm.W3t, HP, Wsm.bias + 2 * H, h1, gid, tig);
+    {
+      // output layer: 16 rows x 16 columns (10 used)
       float o[2][4];
 #pragma unroll
       for (int a = 0; a < 2; ++a)
 #pragma unroll
         for (int b = 0; b < 4; ++b) o[a][b] = 0.f;
 #pragma unroll
-      for (int ks = 0; ks < H; ks += 16) {
-        uint32_t af[4], bfr[2][2];
-        const bf16 *r0 = G.Hb + (w * 16 + gid) * HP + ks + tig * 2;
-        af[0] = ld32(r0);
-        af[1] = ld32(r0 + 8 * HP);
-        af[2] = ld32(r0 + 8);
-        af[3] = ld32(r0 + 8 * HP + 8);
+      for (int kt = 0; kt < 8; ++kt)
 #pragma unroll
-        for (int nj = 0; nj < 2; ++nj) {
-          const bf16 *c0 = Wsm.W4t + (nj * 8 + gid) * HP + ks + tig * 2;
-          bfr[nj][0] = ld32(c0);
-          bfr[nj][1] = ld32(c0 + 8);
+        for (int nt = 0; nt < 2; ++nt) {
+          const bf16 *c0 = Wsm.W4t + (nt * 8 + gid) * HP + kt * 16 + tig * 2;
+          const uint32_t b[2] = {ld32(c0), ld32(c0 + 8)};
+          mma_bf16(o[nt], h1[kt], b);
         }
-        mma_bf16(o[0], af, bfr[0]);
-        mma_bf16(o[1], af, bfr[1]);
-      }
 #pragma unroll
-      for (int nj = 0; nj < 2; ++nj) {
-        const int row = w * 16 + gid, col = nj * 8 + tig * 2;
+      for (int nt = 0; nt < 2; ++nt) {
+        const int col = nt * 8 + tig * 2;
         const float b0 = Wsm.bias[3 * H + col], b1 = Wsm.bias[3 * H + col + 1];
-        G.O[row * OP + col] = o[nj][0] + b0;
-        G.O[row * OP + col + 1] = o[nj][1] + b1;
-        G.O[(row + 8) * OP + col] = o[nj][2] + b0;
-        G.O[(row + 8) * OP + col + 1] = o[nj][3] + b1;
+        S.O[gid * OP + col] = o[nt][0] + b0;
+        S.O[gid * OP + col + 1] = o[nt][1] + b1;
+        S.O[(gid + 8) * OP + col] = o[nt][2] + b0;
+        S.O[(gid + 8) * OP + col + 1] = o[nt][3] + b1;
       }
     }
-    group_sync(grp);
-    if (gt < PPT) {
-      const int pair = gt;
+    __syncwarp();
+
+    // epilogue: one lane per pair for the density; four lanes per pair for
+    // the full E-step (part 0: log f, e1, e2; part 1: e3; parts 2, 3: e4)
+    constexpr int PARTS = DENS ? 1 : 4;
+    if (lane < PPT * PARTS) {
+      const int pair = lane / PARTS, part = lane % PARTS;
       const int64_t j = j0 + pair;
-      const int kind = (j < n) ? G.ok[pair] : -1;
+      const int kind = (j < n) ? S.kind[pair] : -1;
       const int64_t ij = (int64_t)i * n + j;
       const float *mean = Wsm.norm, *sdv = Wsm.norm + DOUT;
-      const float *oA = G.O + (DENS ? pair : 2 * pair) * OP;
+      const float *oA = S.O + (DENS ? pair : 2 * pair) * OP;
       const float logTA = -__expf(fmaf(oA[0], sdv[0], mean[0]));
       // pairs left to the lattice rule carry an upper bound of log f for its
       // triage: log T is decreasing in every c_t, so the network's value at
       // the box-clamped point plus a margin bounds it; none without a domain
-      if (kind == 1) {
+      if (kind == 1 && part == 0) {
         // and P(X > c) <= P(X_t > c_t) <= (m + c_t^2) f_m(c_t) / ((m - 1) c_t)
         // for c_t > 0, f_m the t_m density (from d/dx[(m + x^2) f_m(x)] =
         // -(m - 1) x f_m(x)); the bound decreases in c_t, so the largest
         // coordinate of pass A's point gives the tightest one
         float ub = logTA + UB_MARGIN;
-        const float cm = G.cmax[pair], m = c.fmA;
-        if (cm > 0.f && m > 1.f) {
+        const float cmx = S.cmax[pair], m = c.fmA;
+        if (cmx > 0.f && m > 1.f) {
           const float lnorm = lgammaf(0.5f * (m + 1.f)) - lgammaf(0.5f * m) - 0.5f * logf(m * 3.14159265f);
-          const float lb = logf((m + cm * cm) / ((m - 1.f) * cm)) + lnorm - 0.5f * (m + 1.f) * log1pf(cm * cm / m);
+          const float lb = logf((m + cmx * cmx) / ((m - 1.f) * cmx)) + lnorm - 0.5f * (m + 1.f) * log1pf(cmx * cmx / m);
           ub = fminf(ub, lb + 1e-3f);
         }
-        static_cast<float *>(out.logf)[ij] = G.logt[pair] + ub;
+        static_cast<float *>(out.logf)[ij] = S.logt[pair] + ub;
       }
-      if (kind == 0) static_cast<float *>(out.logf)[ij] = INFINITY;
+      if (kind == 0 && part == 0) static_cast<float *>(out.logf)[ij] = INFINITY;
       if (kind == 2) {
-        static_cast<float *>(out.logf)[ij] = G.logt[pair] + logTA;
+        if (part == 0) static_cast<float *>(out.logf)[ij] = S.logt[pair] + logTA;
         if (!DENS) {
           const float *oB = oA + OP;
           const float logTB = -__expf(fmaf(oB[0], sdv[0], mean[0]));
-          const float nud = G.nud[pair];
+          const float nud = S.nud[pair];
           const float mA = c.fmA, mB = c.fmB;
           const float e1 = mA / nud * __expf(logTB - logTA);
-          const float e2 = e1 - (logf(0.5f * nud) + mA / nud - c.fpsiA);
-          const float sig = sqrtf(nud / mB);
-          // E[X] and E[X X^T] of pass B in the Lambda basis: D^{1/2} (.) D^{1/2}
-          const float L00 = c.L[0], L10 = c.L[RMAX], L11 = c.L[RMAX + 1];
-          const float L20 = c.L[2 * RMAX], L21 = c.L[2 * RMAX + 1], L22 = c.L[2 * RMAX + 2];
-          const float sD[3] = {fabsf(L00), sqrtf(fmaf(L10, L10, L11 * L11)),
-                               sqrtf(fmaf(L20, L20, fmaf(L21, L21, L22 * L22)))};
-          const float *qp = G.q + 3 * pair;
-          float LEV[3];
-          float EXs[3];
+          if (part == 0) {
+            static_cast<float *>(out.e1)[ij] = e1;
+            static_cast<float *>(out.e2)[ij] = e1 - (logf(0.5f * nud) + mA / nud - c.fpsiA);
+          } else {
+            const float sig = sqrtf(nud / mB);
+            // E[X] and E[X X^T] of pass B in the Lambda basis: D^{1/2} (.) D^{1/2}
+            const float L00 = c.L[0], L10 = c.L[RMAX], L11 = c.L[RMAX + 1];
+            const float L20 = c.L[2 * RMAX], L21 = c.L[2 * RMAX + 1], L22 = c.L[2 * RMAX + 2];
+            const float sD[3] = {fabsf(L00), sqrtf(fmaf(L10, L10, L11 * L11)),
+                                 sqrtf(fmaf(L20, L20, fmaf(L21, L21, L22 * L22)))};
+            const float *qp = S.q + 3 * pair;
+            float LEV[3], EXs[3];
 #pragma unroll
-          for (int t = 0; t < 3; ++t) {
-            EXs[t] = fmaf(oB[1 + t], sdv[1 + t], mean[1 + t]);
-            LEV[t] = sD[t] * EXs[t];
-          }
-          static_cast<float *>(out.e1)[ij] = e1;
-          static_cast<float *>(out.e2)[ij] = e2;
-#pragma unroll
-          for (int t = 0; t < 3; ++t)
-            static_cast<float *>(out.e3)[((int64_t)i * 3 + t) * n + j] = e1 * fmaf(sig, LEV[t], qp[t]);
-          // e4 in lower-triangle order (0,0) (1,0) (1,1) (2,0) (2,1) (2,2); the
-          // network's covariance comes in upper order 00 01 02 11 12 22
-          constexpr int UP[3][3] = {{0, 1, 2}, {1, 3, 4}, {2, 4, 5}};
-          float cv[6];
-#pragma unroll
-          for (int u = 0; u < 6; ++u) cv[u] = fmaf(oB[4 + u], sdv[4 + u], mean[4 + u]);
-          psd_repair3(cv);
-#pragma unroll
-          for (int t = 0; t < 3; ++t)
-#pragma unroll
-            for (int h = 0; h <= t; ++h) {
-              const int u = UP[t][h];
-              // the network gives the covariance; E[X'_h X'_t] = cov + E[X'_h] E[X'_t]
-              const float S = sD[t] * sD[h] * fmaf(EXs[h], EXs[t], cv[u]);
-              const float exx = qp[t] * qp[h] + sig * (qp[t] * LEV[h] + LEV[t] * qp[h]) + sig * sig * S;
-              static_cast<float *>(out.e4)[((int64_t)i * 6 + t * (t + 1) / 2 + h) * n + j] = e1 * exx;
+            for (int t = 0; t < 3; ++t) {
+              EXs[t] = fmaf(oB[1 + t], sdv[1 + t], mean[1 + t]);
+              LEV[t] = sD[t] * EXs[t];
             }
+            if (part == 1) {
+#pragma unroll
+              for (int t = 0; t < 3; ++t)
+                static_cast<float *>(out.e3)[((int64_t)i * 3 + t) * n + j] = e1 * fmaf(sig, LEV[t], qp[t]);
+            } else {
+              // e4 in lower-triangle order (0,0) (1,0) (1,1) | (2,0) (2,1) (2,2)
+              // (part 2 | part 3); the network's covariance comes in upper
+              // order 00 01 02 11 12 22
+              constexpr int UP[3][3] = {{0, 1, 2}, {1, 3, 4}, {2, 4, 5}};
+              float cv[6];
+#pragma unroll
+              for (int u = 0; u < 6; ++u) cv[u] = fmaf(oB[4 + u], sdv[4 + u], mean[4 + u]);
+              psd_repair3(cv);
+#pragma unroll
+              for (int t = 0; t < 3; ++t)
+#pragma unroll
+                for (int h = 0; h <= t; ++h) {
+                  if ((t == 2) != (part == 3)) continue;
+                  const int u = UP[t][h];
+                  // the network gives the covariance; E[X'_h X'_t] = cov + E[X'_h] E[X'_t]
+                  const float Sth = sD[t] * sD[h] * fmaf(EXs[h], EXs[t], cv[u]);
+                  const float exx = qp[t] * qp[h] + sig * (qp[t] * LEV[h] + LEV[t] * qp[h]) + sig * sig * Sth;
+                  static_cast<float *>(out.e4)[((int64_t)i * 6 + t * (t + 1) / 2 + h) * n + j] = e1 * exx;
+                }
+            }
+          }
         }
       }
     }
+    __syncwarp();  // the scratch is reused by the next tile
   }
 }
 
@@ -933,23 +931,23 @@ cudaError_t launch_surrogate_estep(const SurrogateDev &sd, const double *Y, int6
   cudaError_t e = cudaMemsetAsync(fb_count, 0, sizeof(unsigned) * g, st);
   if (e != cudaSuccess || n <= 0) return e;
   const int smem = (int)sg::INFER_SMEM;
-  const int64_t ppt = density_only ? sg::TROWS : sg::TROWS / 2;
+  const int64_t ppt = density_only ? sg::WROWS : sg::WROWS / 2;
   const int64_t ntiles = (n + ppt - 1) / ppt * g;
   int dev = 0, sms = 152;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  int64_t blocks = (ntiles + sg::GROUPS - 1) / sg::GROUPS;
+  int64_t blocks = (ntiles + sg::WARPS - 1) / sg::WARPS;
   if (blocks > sms) blocks = sms;
   if (density_only) {
     e = cudaFuncSetAttribute(sg::surrogate_estep_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     if (e != cudaSuccess) return e;
-    sg::surrogate_estep_kernel<true><<<(unsigned)blocks, sg::GROUP_THREADS * sg::GROUPS, smem, st>>>(
-        sd, Y, n, g, p, c32, out, fb_list, fb_count);
+    sg::surrogate_estep_kernel<true><<<(unsigned)blocks, sg::WARPS * 32, smem, st>>>(sd, Y, n, g, p, c32, out,
+                                                                                     fb_list, fb_count);
   } else {
     e = cudaFuncSetAttribute(sg::surrogate_estep_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     if (e != cudaSuccess) return e;
-    sg::surrogate_estep_kernel<false><<<(unsigned)blocks, sg::GROUP_THREADS * sg::GROUPS, smem, st>>>(
-        sd, Y, n, g, p, c32, out, fb_list, fb_count);
+    sg::surrogate_estep_kernel<false><<<(unsigned)blocks, sg::WARPS * 32, smem, st>>>(sd, Y, n, g, p, c32, out,
+                                                                                      fb_list, fb_count);
   }
   return cudaGetLastError();
 }
