@@ -91,15 +91,24 @@ __device__ __forceinline__ float tanh_approx(float x) {
   asm("tanh.approx.f32 %0, %1;" : "=f"(r) : "f"(x));
   return r;
 }
+// GELU(z) = z/2 (1 + t), t = tanh(z (k + a k z^2)), k = sqrt(2/pi), a = 0.044715,
+// evaluated in the same operation order in the scalar and the paired forms
+// (so the GEMM path and the fused E-step produce the same activations).
+constexpr float GELU_K = 0.7978845608028654f, GELU_AK = 0.044715f * 0.7978845608028654f;
 __device__ __forceinline__ float gelu_f(float z) {
-  const float k = 0.7978845608028654f, a = 0.044715f;
-  const float t = tanh_approx(k * fmaf(a * z, z * z, z));
-  return 0.5f * z * (1.0f + t);
+  const float arg = z * fmaf(z * z, GELU_AK, GELU_K);
+  const float hz = 0.5f * z;
+  return fmaf(hz, tanh_approx(arg), hz);
+}
+__device__ __forceinline__ float2 gelu_x2(float2 z) {
+  const float2 arg = __fmul2_rn(z, __ffma2_rn(__fmul2_rn(z, z), make_float2(GELU_AK, GELU_AK),
+                                              make_float2(GELU_K, GELU_K)));
+  const float2 hz = __fmul2_rn(z, make_float2(0.5f, 0.5f));
+  return __ffma2_rn(hz, make_float2(tanh_approx(arg.x), tanh_approx(arg.y)), hz);
 }
 __device__ __forceinline__ float gelu_grad_f(float z) {
-  const float k = 0.7978845608028654f, a = 0.044715f;
-  const float t = tanh_approx(k * fmaf(a * z, z * z, z));
-  return 0.5f * (1.0f + t) + 0.5f * z * (1.0f - t * t) * k * (1.0f + 3.0f * a * z * z);
+  const float t = tanh_approx(z * fmaf(z * z, GELU_AK, GELU_K));
+  return 0.5f * (1.0f + t) + 0.5f * z * (1.0f - t * t) * fmaf(3.0f * GELU_AK, z * z, GELU_K);
 }
 
 __device__ __forceinline__ void mma_bf16(float (&d)[4], const uint32_t (&a)[4], const uint32_t (&b)[2]) {
@@ -559,16 +568,21 @@ __device__ __forceinline__ void dense_gelu(const uint32_t (&in)[KT][4], const bf
         mma_bf16(acc[nt], in[kt], b);
       }
     // columns 16 q .. 16 q + 15 (n-tiles 2q and 2q + 1) form k-tile q of the
-    // next layer: (row gid | gid + 8) x (k 2 tig, 2 tig + 1 | + 8)
+    // next layer: (row gid | gid + 8) x (k 2 tig, 2 tig + 1 | + 8); each
+    // register pair holds two adjacent columns, evaluated as one FP32x2 pair
 #pragma unroll
     for (int nt = 0; nt < 8; nt += 2) {
       const int q = half * 4 + nt / 2;
       const int col0 = (half * 8 + nt) * 8 + tig * 2, col1 = col0 + 8;
-      const float b00 = bias[col0], b01 = bias[col0 + 1], b10 = bias[col1], b11 = bias[col1 + 1];
-      out[q][0] = pack_bf16x2(gelu_f(acc[nt][0] + b00), gelu_f(acc[nt][1] + b01));
-      out[q][1] = pack_bf16x2(gelu_f(acc[nt][2] + b00), gelu_f(acc[nt][3] + b01));
-      out[q][2] = pack_bf16x2(gelu_f(acc[nt + 1][0] + b10), gelu_f(acc[nt + 1][1] + b11));
-      out[q][3] = pack_bf16x2(gelu_f(acc[nt + 1][2] + b10), gelu_f(acc[nt + 1][3] + b11));
+      const float2 b0 = make_float2(bias[col0], bias[col0 + 1]), b1 = make_float2(bias[col1], bias[col1 + 1]);
+      const float2 g0 = gelu_x2(__fadd2_rn(make_float2(acc[nt][0], acc[nt][1]), b0));
+      const float2 g1 = gelu_x2(__fadd2_rn(make_float2(acc[nt][2], acc[nt][3]), b0));
+      const float2 g2 = gelu_x2(__fadd2_rn(make_float2(acc[nt + 1][0], acc[nt + 1][1]), b1));
+      const float2 g3 = gelu_x2(__fadd2_rn(make_float2(acc[nt + 1][2], acc[nt + 1][3]), b1));
+      out[q][0] = pack_bf16x2(g0.x, g0.y);
+      out[q][1] = pack_bf16x2(g1.x, g1.y);
+      out[q][2] = pack_bf16x2(g2.x, g2.y);
+      out[q][3] = pack_bf16x2(g3.x, g3.y);
     }
   }
 }
