@@ -82,10 +82,6 @@ struct EArgs {
   int step[RMAX + 1];
   int sint[RMAX + 1];
   double sfrac[RMAX + 1];
-  // single-precision copies read straight from the parameter bank by the sweep
-  float fstep2[RMAX + 1];  // 2 * step
-  float ftwo_sf[RMAX + 1];  // 2 * sfrac
-  float fsf[RMAX + 1];      // sfrac
   const float *utab; // lattice uniforms, [N][uniform_stride(r)] (single precision sweeps)
   const void *comp;  // CompT<T>[g]
   const void *chi;   // T[g][2][N]
@@ -187,20 +183,11 @@ struct PairedConsts {
   float2 nL[RMAX * (RMAX + 1) / 2];  // -L_th / L_tt (h < t), packed lower triangle
 };
 
-// Lattice constants of coordinate t in the sweep's precision: the float copies
-// live in the kernel parameters, the double path derives them from sfrac.
-template <typename T>
-__device__ __forceinline__ T lat_sf(const EArgs &a, int t) {
-  if constexpr (sizeof(T) == 4) return a.fsf[t]; else return a.sfrac[t];
-}
-template <typename T>
-__device__ __forceinline__ T lat_two_sf(const EArgs &a, int t) {
-  if constexpr (sizeof(T) == 4) return a.ftwo_sf[t]; else return 2.0 * a.sfrac[t];
-}
-template <typename T>
-__device__ __forceinline__ T lat_step2(const EArgs &a, int t) {
-  if constexpr (sizeof(T) == 4) return a.fstep2[t]; else return (double)(2 * a.step[t]);
-}
+// Lattice constants of coordinate t for the double-precision sweep (the
+// single-precision sweep reads its uniforms from the lattice table).
+__device__ __forceinline__ double lat_sf(const EArgs &a, int t) { return a.sfrac[t]; }
+__device__ __forceinline__ double lat_two_sf(const EArgs &a, int t) { return 2.0 * a.sfrac[t]; }
+__device__ __forceinline__ double lat_step2(const EArgs &a, int t) { return (double)(2 * a.step[t]); }
 
 // Per-pair prologue in double precision: z = A (y - mu), d = z^T z, q = B z and
 // the log of the t_p factor with the constant c0 of Eq. 2.
@@ -340,12 +327,12 @@ __device__ __forceinline__ bool pair_sweep(const EArgs &a, const FitView &fv, co
     } else {
 #pragma unroll
       for (int t = 0; t < R; ++t) {
-        const T sf = lat_sf<T>(a, t + 1);
+        const T sf = static_cast<T>(lat_sf(a, t + 1));
         const T mm = T(0.5) * (fm[t] + fN);
         const T lo = mm + sf, hi = (fN - mm) - sf;
-        um[t] = M::mn(M::mx(M::ab(fm[t] + lat_two_sf<T>(a, t + 1)) * invN, umin), umax);
+        um[t] = M::mn(M::mx(M::ab(fm[t] + static_cast<T>(lat_two_sf(a, t + 1))) * invN, umin), umax);
         uu[t] = M::mx(T(2) * M::mn(lo, hi) * invN, umin);
-        fm[t] += lat_step2<T>(a, t + 1);
+        fm[t] += static_cast<T>(lat_step2(a, t + 1));
         if (fm[t] >= fN) fm[t] -= T(2) * fN;
       }
     }
@@ -1176,9 +1163,6 @@ cudaError_t launch_estep_batched(int precision, const BatchDev &b, int p, int r,
     a.step[t] = lat.step[t];
     a.sint[t] = lat.sint[t];
     a.sfrac[t] = lat.sfrac[t];
-    a.fstep2[t] = (float)(2 * lat.step[t]);
-    a.ftwo_sf[t] = (float)(2.0 * lat.sfrac[t]);
-    a.fsf[t] = (float)lat.sfrac[t];
   }
   a.utab = lat.utab;
   a.e2_mode = e2_mode;
@@ -1261,9 +1245,6 @@ EArgs make_args(const double *Y, int64_t n, int g, int p, const LatticeDev &lat,
     a.step[t] = lat.step[t];
     a.sint[t] = lat.sint[t];
     a.sfrac[t] = lat.sfrac[t];
-    a.fstep2[t] = (float)(2 * lat.step[t]);
-    a.ftwo_sf[t] = (float)(2.0 * lat.sfrac[t]);
-    a.fsf[t] = (float)lat.sfrac[t];
   }
   a.out = out;
   a.utab = lat.utab;
