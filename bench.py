@@ -448,6 +448,9 @@ def run_batched(args):
                    "step": "one EM iteration of every fit; the timed call adds one final density sweep",
                    "l2": "inputs larger than L2"},
         "fit_iters_per_s": args.nfits * args.steps / (ms / 1e3),
+        # per iteration: precompute, persistent sweep, rescue, posterior/sums,
+        # log-likelihood reduce, finalize; then one density pass (five kernels)
+        "gpu_launches": 6 * args.steps + 5,
         "clocks": clocks,
         "fits_failed": int(sum(1 for s in st if s != 0)),
     }
@@ -600,7 +603,9 @@ def run_surrogate(args):
                                     "em_iters_per_s": 1.0 / step_p, "sweep_ms": float(np.mean(kern_p))},
         "speedup_vs_plain_at_equal_accuracy": step_p / step_s,
         "fallback_pairs": int(fallback), "fallback_fraction": fallback / pairs,
-        "gpu_launches": 9 * args.steps,
+        # per EM iteration: precompute, network kernel, list sweep, rescue,
+        # posterior/sums, log-likelihood reduce, finalize
+        "gpu_launches": 7 * args.steps,
         "roofline": {"bound": "tensor", "kernel": "surrogate_estep_kernel<false>", "achieved": achieved,
                      "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak, "traffic": None,
                      "peak_source": "measured cuBLAS bf16 (MEASURED_PEAKS.json)" if peaks else "fallback 1.7 PFLOP/s",
