@@ -147,6 +147,28 @@ def test_estep_full_size_sampled_fp32():
     assert np.all(np.isfinite(G["logf"]))
 
 
+def test_estep_full_size_sampled_fp32_largest_workload():
+    """The largest workload (p=8, r=4, g=6, n=10^6, 8192-point lattice) in
+    single precision through the same launch path as the bench; the oracle
+    recomputes 16 sampled observations (all six components each) and every
+    E-step output is held to the single-precision bars."""
+    Y, truth, init, lat = _problem("cfust_p8r4g6_n1000000_N8192", None, 8192)
+    G = _gpu_estep(Y, init, lat, binding.CFUST_FP32)
+    assert np.allclose(G["tau"].sum(axis=0), 1.0, atol=1e-5)
+    assert np.all(np.isfinite(G["logf"]) | (G["logf"] == -np.inf))
+    idx = np.sort(np.random.default_rng(11).choice(Y.shape[0], 16, replace=False))
+    R = _oracle_estep(Y[idx], init, lat)
+    sub = {k: (v[:, idx] if k in ("logf", "tau", "e1", "e2") else v[..., idx]) for k, v in G.items()
+           if k not in ("loglik", "rescued")}
+    r = init.r
+    _cmp("logf", sub["logf"], R["logf"], 0, 1e-4)
+    _cmp("tau", sub["tau"], R["tau"], 0, 1e-5)
+    for k in ("e1", "e2"):
+        _cmp(k, sub[k], R[k], 2e-4)
+    _cmp("e3", sub["e3"], np.transpose(R["e3"], (0, 2, 1)), 2e-4)
+    _cmp("e4", sub["e4"], np.stack([R["e4"][:, :, t, h] for t in range(r) for h in range(t + 1)], axis=1), 2e-4)
+
+
 def test_loglik_matches_oracle_fp64():
     torch = _torch()
     Y, truth, init, lat = _problem("cfust_p4r4g3_n100000_N4096", 257, 1024)
