@@ -179,6 +179,20 @@ cfust_status cfust_fit_batched(cfust_ctx *ctx, int nfits, const double *const *Y
  * default rule): pairs per warp and resident CTAs per SM of the sweep. */
 cfust_status cfust_batched_shape(cfust_ctx *ctx, int *pairs_per_warp, int *ctas_per_sm);
 
+/* Multiple starts (Algorithm 1, with the largest log-likelihood kept; the
+ * paper's listing selects the smallest, a misprint for maximum likelihood):
+ * every start runs burn_in EM iterations (all starts together as one batched
+ * fit over the same observations; burn_in = 0 compares the starts'
+ * log-likelihoods directly), the start with the largest log-likelihood after
+ * its burn-in is chosen and fitted further like cfust_fit (opts.max_iter,
+ * opts.tol).  starts: host [nstarts], updated in place (every start holds its
+ * burned-in parameters; starts[*best] the fitted ones).  trace and iters_done
+ * as for cfust_fit, for the final fit.  Starts that fail their burn-in
+ * (degenerate, not positive definite) are not chosen; CFUST_EDEGENERATE when
+ * none survives. */
+cfust_status cfust_fit_multistart(cfust_ctx *ctx, const double *Y, int64_t n, cfust_params *starts, int nstarts,
+                                  int burn_in, int *best, double *loglik_trace, int *iters_done);
+
 /* Number of (i, j) pairs whose single-precision lattice sweep fell below the
  * underflow guard in the last E-step and were recomputed in double precision
  * on the GPU (always 0 in CFUST_FP64 mode). */

@@ -27,7 +27,7 @@ EXPORTED = ["cfust_create", "cfust_destroy", "cfust_loglik", "cfust_estep", "cfu
             "cfust_surrogate_predict", "cfust_surrogate_gradient", "cfust_surrogate_get_params",
             "cfust_surrogate_set_params", "cfust_surrogate_train", "cfust_surrogate_last_error",
             "cfust_set_surrogate", "cfust_last_fallback", "cfust_surrogate_problems",
-            "cfust_surrogate_finetune"]
+            "cfust_surrogate_finetune", "cfust_fit_multistart"]
 
 SURROGATE_NPARAM = 35338
 
@@ -109,6 +109,8 @@ def load(build_if_missing: bool = True, path: str | None = None) -> ctypes.CDLL:
         "cfust_set_surrogate": ([vp, vp], ctypes.c_int),
         "cfust_last_fallback": ([vp, ctypes.POINTER(i64)], ctypes.c_int),
         "cfust_surrogate_problems": ([vp, vp, i64, P, i64, vp, i64, ctypes.POINTER(i64)], ctypes.c_int),
+        "cfust_fit_multistart": ([vp, vp, i64, P, ctypes.c_int, ctypes.c_int, ctypes.POINTER(ctypes.c_int), dp,
+                                  ctypes.POINTER(ctypes.c_int)], ctypes.c_int),
         "cfust_surrogate_finetune": ([vp, vp, i64, ctypes.c_int, ctypes.c_int, ctypes.c_float, ctypes.c_uint64,
                                       ctypes.POINTER(ctypes.c_float)], ctypes.c_int),
     }
@@ -280,6 +282,20 @@ class Context:
         self._check(rc)
         # the library wrote the updated parameters through the struct pointers
         return [h.to_params() for h in hps], trace, list(st)
+
+    def cfust_fit_multistart(self, Y, starts, burn_in):
+        """Returns (index of the chosen start, its fitted params, trace, iterations,
+        the burned-in params of every start)."""
+        ns = len(starts)
+        hps = [_HostParams(p) for p in starts]
+        arr = (cfust_params * ns)(*[h.c for h in hps])
+        trace = np.zeros(self.opts.max_iter + 1)
+        best, done = ctypes.c_int(), ctypes.c_int()
+        self._check(self.lib.cfust_fit_multistart(self.h, _ptr(Y), Y.shape[0], arr, ns, int(burn_in),
+                                                  ctypes.byref(best), trace.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
+                                                  ctypes.byref(done)))
+        out = [h.to_params() for h in hps]
+        return best.value, out[best.value], trace[:done.value + 1], done.value, out
 
     def cfust_batched_shape(self):
         a, b = ctypes.c_int(), ctypes.c_int()

@@ -1235,3 +1235,50 @@ extern "C" cfust_status cfust_mstep_noalloc(int precision, const double *Y, int6
 #undef NA_CUDA
   return CFUST_OK;
 }
+
+extern "C" cfust_status cfust_fit_multistart(cfust_ctx *c, const double *Y, int64_t n, cfust_params *starts,
+                                            int nstarts, int burn_in, int *best, double *trace, int *iters_done) {
+  if (!c) return CFUST_EINVAL;
+  if (nstarts < 1 || !starts || !best || burn_in < 0)
+    return fail(c, CFUST_EINVAL, "nstarts >= 1, burn_in >= 0, starts and best required");
+  DeviceGuard dg(c->device);
+  int chosen = 0;
+  if (nstarts > 1) {
+    double best_ll = -INFINITY;
+    chosen = -1;
+    if (burn_in == 0) {
+      // select on the starts' own log-likelihoods
+      for (int f = 0; f < nstarts; ++f) {
+        double ll = -INFINITY;
+        const cfust_status s = cfust_loglik(c, Y, n, &starts[f], &ll);
+        if (s == CFUST_OK && isfinite(ll) && ll > best_ll) {
+          best_ll = ll;
+          chosen = f;
+        }
+      }
+    } else {
+      // every start's burn-in as one batched fit over the same observations
+      std::vector<const double *> Ys(nstarts, Y);
+      std::vector<int64_t> ns(nstarts, n);
+      std::vector<double> tr((size_t)nstarts * (burn_in + 1));
+      std::vector<int> st(nstarts, 0);
+      const int keep = c->opts.max_iter;
+      c->opts.max_iter = burn_in;
+      free_batch(c->batch);
+      const cfust_status s = cfust_fit_batched(c, nstarts, Ys.data(), ns.data(), starts, tr.data(), st.data());
+      free_batch(c->batch);
+      c->opts.max_iter = keep;
+      if (s != CFUST_OK) return s;
+      for (int f = 0; f < nstarts; ++f) {
+        const double ll = tr[(size_t)f * (burn_in + 1) + burn_in];
+        if (st[f] == 0 && isfinite(ll) && ll > best_ll) {
+          best_ll = ll;
+          chosen = f;
+        }
+      }
+    }
+    if (chosen < 0) return fail(c, CFUST_EDEGENERATE, "no start gave a finite log-likelihood");
+  }
+  *best = chosen;
+  return cfust_fit(c, Y, n, &starts[chosen], trace, iters_done);
+}

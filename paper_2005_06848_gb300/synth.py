@@ -87,6 +87,12 @@ def splitmix64_stream(seed: int, count: int) -> list[int]:
     return out
 
 
+# Results of the search below for sizes whose search takes tens of seconds
+# (the 2^16-point reference rule); tests/test_synth_lattice.py re-runs the
+# search for every entry.
+KOROBOV_TABLE = {(65536, 4): 1443}
+
+
 @functools.lru_cache(maxsize=None)
 def korobov_generator(n: int, dim: int) -> int:
     """Korobov parameter a (generator (1, a, a^2, ...) mod n) minimising P_2.
@@ -101,6 +107,13 @@ def korobov_generator(n: int, dim: int) -> int:
         raise ValueError("need n >= 2 and dim >= 1")
     if dim == 1:
         return 1
+    if (n, dim) in KOROBOV_TABLE:
+        return KOROBOV_TABLE[(n, dim)]
+    return korobov_search(n, dim)
+
+
+def korobov_search(n: int, dim: int) -> int:
+    """The P_2 search of korobov_generator, without the table."""
     cands = np.array([a for a in range(2, n) if math.gcd(a, n) == 1], dtype=np.int64)
     if cands.size > 4096:
         # large n: search an evenly spread subset (the criterion costs O(n) per candidate)

@@ -106,3 +106,34 @@ def test_full_batch_of_256_fits_matches_sampled_single_fits():
         assert np.allclose(btr[f], str_, rtol=1e-12, atol=0)
         for a, b in zip(bp[f].as_arrays(), sp.as_arrays()):
             assert np.allclose(a, b, rtol=1e-12, atol=1e-14)
+
+
+def test_multistart_keeps_the_best_burned_in_start():
+    """Algorithm 1 with burn-in: four starts run three EM iterations together
+    (one batched fit); the one with the largest log-likelihood (the oracle's
+    selection rule) is fitted further, and equals that start's own burn-in
+    continued by a single fit."""
+    torch = _torch()
+    Y, _, truth, init, _, _ = synth.workload("cfust_p3r3g4_n1000000_N2048", n=4000, seed=5)
+    rng = np.random.default_rng(3)
+    starts = [init] + [synth.perturb_params(truth, rng, 0.8) for _ in range(3)]
+    lat = synth.make_lattice(1024, 4, seed=0)
+    Yd = torch.from_numpy(Y).cuda()
+    ctx = binding.Context(lat, precision=binding.CFUST_FP32, max_iter=5)
+    best, P, trace, done, _ = ctx.cfust_fit_multistart(Yd, starts, burn_in=3)
+    burned, lls = [], []
+    for st in starts:
+        c1 = binding.Context(lat, precision=binding.CFUST_FP32, max_iter=3)
+        Pb, tr, _ = c1.cfust_fit(Yd, st)
+        burned.append(Pb)
+        lls.append(tr[-1])
+    assert best == O.select_start(lls)
+    c2 = binding.Context(lat, precision=binding.CFUST_FP32, max_iter=5)
+    Pref, tref, dref = c2.cfust_fit(Yd, burned[best])
+    assert done == dref and np.allclose(trace, tref, rtol=1e-10, atol=0)
+    for a, b in zip(P.as_arrays(), Pref.as_arrays()):
+        assert np.allclose(a, b, rtol=1e-8, atol=1e-10)
+    # burn_in = 0 selects on the starts' own log-likelihoods
+    c3 = binding.Context(lat, precision=binding.CFUST_FP32, max_iter=2)
+    best0, _, _, _, _ = c3.cfust_fit_multistart(Yd, starts, burn_in=0)
+    assert best0 == O.select_start([c3.cfust_loglik(Yd, st) for st in starts])

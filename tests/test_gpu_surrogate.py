@@ -241,17 +241,17 @@ def trained(lat8192):
 def test_surrogate_gain_at_equal_loglik_accuracy(trained):
     """The trained network against the method without it: on the p=3, r=3,
     g=4, n=10^6 mixture, the log-likelihood error of the surrogate E-step (judge:
-    the plain lattice rule at 8192 points) is matched by the cheapest plain
+    the plain lattice rule at 2^16 points) is matched by the cheapest plain
     lattice that is at least as accurate (RMS over three lattice shifts), and at
     that accuracy the surrogate E-step takes less device time."""
     torch = _torch()
     s = trained
     Y, _, truth, init, _, _ = synth.workload("cfust_p3r3g4_n1000000_N2048", seed=0)
     Yd = torch.tensor(Y, dtype=torch.float64, device="cuda")
-    ladder = [32, 64, 128, 256, 512, 1024]
+    ladder = [32, 64, 128, 256, 512, 1024, 2048]
     report = []
     for P in (init, truth):
-        judge = binding.Context(synth.make_lattice(8192, 4, seed=0), precision=binding.CFUST_FP32)
+        judge = binding.Context(synth.make_lattice(1 << 16, 4, seed=0), precision=binding.CFUST_FP32)
         l_judge = judge.cfust_loglik(Yd, P)
         sur = binding.Context(synth.make_lattice(128, 4, seed=0), precision=binding.CFUST_FP32)
         sur.cfust_set_surrogate(s)
@@ -351,12 +351,12 @@ def test_problems_and_finetune(lat8192):
 def test_em_with_the_surrogate_improves_the_likelihood(trained):
     """Ten EM iterations with the network in the E-step (graph-captured fit)
     from the perturbed start: the log-likelihood of the result, judged by the
-    plain lattice rule at 8192 points, rises well above the start's, and ends
+    plain lattice rule at 2^16 points, rises well above the start's, and ends
     within 0.5% of a plain 1024-point fit's after the same ten iterations."""
     torch = _torch()
     Y, _, truth, init, _, _ = synth.workload("cfust_p3r3g4_n1000000_N2048", n=200000, seed=3)
     Yd = torch.tensor(Y, dtype=torch.float64, device="cuda")
-    judge = binding.Context(synth.make_lattice(8192, 4, seed=0), precision=binding.CFUST_FP32)
+    judge = binding.Context(synth.make_lattice(1 << 16, 4, seed=0), precision=binding.CFUST_FP32)
     sur = binding.Context(synth.make_lattice(128, 4, seed=0), precision=binding.CFUST_FP32, max_iter=10)
     sur.cfust_set_surrogate(trained)
     Ps, trace_s, _ = sur.cfust_fit(Yd, init)
