@@ -53,11 +53,193 @@ __device__ inline void entry_desc(int ent, int p, int r, int *w, int *y1, int *y
   *w = 2 + r + rp;                                  // S8
 }
 
+// hi + lo += x with Knuth's two-sum: the rounding error of hi + x is exact in
+// single precision and goes to lo (the _rn intrinsics keep the compiler from
+// fusing or reordering the steps).
+__device__ __forceinline__ void two_sum_acc(float &hi, float &lo, float x) {
+  const float s = __fadd_rn(hi, x);
+  const float bp = __fsub_rn(s, hi);
+  const float err = __fadd_rn(__fsub_rn(hi, __fsub_rn(s, bp)), __fsub_rn(x, bp));
+  hi = s;
+  lo = __fadd_rn(lo, err);
+}
+
+// Single-precision E-step outputs (CFUST_FP32).  Double-precision work costs
+// 64 times single-precision work on this GPU, so only what needs it stays
+// double: log pi_i + log f_ij, its maximum and the differences (the
+// exponents of the log-sum-exp), l_j = max + log s_j and its sum, and the
+// per-tile totals of the sums.  The exponentials, tau (to 1e-7 relative,
+// the level of the single-precision log f_ij it comes from), the products
+// tau e y of the sums (each rounded once per factor, as are its inputs) and
+// their sums within a tile (two-sum compensated: exact up to O(64 u^2)) are
+// single precision.
+__device__ __forceinline__ void posterior_block_f32(const PosteriorArgs &a, int c0, int c1, int blk, int nblk,
+                                                    unsigned char *smem_raw) {
+  const int p = a.p, r = a.r, g = a.g;
+  const int rp = r * (r + 1) / 2;
+  const int K = sums_width(p, r);
+  const int WR = 3 + r + rp;
+  const int gc = c1 - c0;
+  const int64_t n = a.n;
+  float *ys = reinterpret_cast<float *>(smem_raw);  // [TJ][p]
+  float *ws = ys + TJ * p;                          // [gc][TJ][WR]
+  __shared__ double red[THREADS];
+
+  const float *lfp = reinterpret_cast<const float *>(a.logf);
+  const float *tau_in = reinterpret_cast<const float *>(a.tau_in);
+  const float *e1 = reinterpret_cast<const float *>(a.e1);
+  const float *e2 = reinterpret_cast<const float *>(a.e2);
+  const float *e3 = reinterpret_cast<const float *>(a.e3);
+  const float *e4 = reinterpret_cast<const float *>(a.e4);
+  float *tau_out = reinterpret_cast<float *>(a.tau_out);
+
+  int own_w[MAXOWN], own_y1[MAXOWN], own_y2[MAXOWN], own_c[MAXOWN];
+  double acc[MAXOWN];
+  const int E = a.want_sums ? gc * K : 0;
+#pragma unroll
+  for (int k = 0; k < MAXOWN; ++k) {
+    const int e = threadIdx.x + k * THREADS;
+    acc[k] = 0.0;
+    own_c[k] = -1;
+    own_w[k] = 0;
+    own_y1[k] = own_y2[k] = -1;
+    if (e < E) {
+      own_c[k] = e / K;
+      entry_desc(e % K, p, r, &own_w[k], &own_y1[k], &own_y2[k]);
+    }
+  }
+  double llacc = 0.0;
+  int bad = 0;
+  const int64_t ntiles = (n + TJ - 1) / TJ;
+  const bool first_chunk = (c0 == 0);
+  __shared__ double lpi[CFUST_GMAX];
+  for (int i = threadIdx.x; i < g; i += THREADS) lpi[i] = log(a.pi[i]);
+  __syncthreads();
+
+  for (int64_t tile = blk; tile < ntiles; tile += nblk) {
+    const int64_t j0 = tile * TJ;
+    const int nt = (int)((n - j0) < TJ ? (n - j0) : TJ);
+    if (a.want_sums)
+      for (int idx = threadIdx.x; idx < nt * p; idx += THREADS) ys[idx] = (float)a.Y[j0 * p + idx];
+    if (threadIdx.x < nt) {
+      const int jj = threadIdx.x;
+      const int64_t j = j0 + jj;
+      if (lfp != nullptr) {
+        double mx = -INFINITY;
+        for (int i = 0; i < g; ++i) mx = fmax(mx, lpi[i] + (double)lfp[(int64_t)i * n + j]);
+        if (!isfinite(mx)) {
+          // no component gives the observation a positive density: flagged,
+          // and its weights are zero so that the sums stay defined
+          bad = 1;
+          if (a.want_sums)
+            for (int i = c0; i < c1; ++i) ws[((i - c0) * TJ + jj) * WR] = 0.0f;
+          if (tau_out != nullptr && first_chunk)
+            for (int i = 0; i < g; ++i) tau_out[(int64_t)i * n + j] = 0.0f;
+        } else {
+          float s = 0.0f;
+          for (int i = 0; i < g; ++i) {
+            const float ex = expf((float)(lpi[i] + (double)lfp[(int64_t)i * n + j] - mx));
+            s = __fadd_rn(s, ex);
+            if (a.want_sums && i >= c0 && i < c1) ws[((i - c0) * TJ + jj) * WR] = ex;
+            if (tau_out != nullptr && first_chunk) tau_out[(int64_t)i * n + j] = ex;
+          }
+          // s is in [1, g]: its single-precision logarithm is good to 1e-7
+          // absolute, below the error of the log f_ij it sums
+          const double lse = mx + (double)logf(s);
+          if (!isfinite(lse)) bad = 1;
+          llacc += lse;
+          const float inv = 1.0f / s;
+          if (a.want_sums)
+            for (int i = c0; i < c1; ++i) ws[((i - c0) * TJ + jj) * WR] *= inv;
+          if (tau_out != nullptr && first_chunk)
+            for (int i = 0; i < g; ++i) tau_out[(int64_t)i * n + j] *= inv;
+        }
+      } else if (a.want_sums) {
+        for (int i = c0; i < c1; ++i) ws[((i - c0) * TJ + jj) * WR] = tau_in[(int64_t)i * n + j];
+      }
+    }
+    __syncthreads();
+    if (a.want_sums) {
+      for (int idx = threadIdx.x; idx < gc * nt; idx += THREADS) {
+        const int ic = idx / nt, jj = idx % nt;
+        const int i = c0 + ic;
+        const int64_t j = j0 + jj;
+        float *row = ws + (ic * TJ + jj) * WR;
+        const float t = row[0];
+        const float v1 = e1[(int64_t)i * n + j];
+        row[1] = __fmul_rn(t, v1);
+        for (int q = 0; q < r; ++q) row[2 + q] = __fmul_rn(t, e3[((int64_t)i * r + q) * n + j]);
+        for (int q = 0; q < rp; ++q) row[2 + r + q] = __fmul_rn(t, e4[((int64_t)i * rp + q) * n + j]);
+        row[2 + r + rp] = __fmul_rn(t, __fsub_rn(e2[(int64_t)i * n + j], v1));
+      }
+      __syncthreads();
+#pragma unroll
+      for (int k = 0; k < MAXOWN; ++k) {
+        if (own_c[k] >= 0) {
+          const float *col = ws + own_c[k] * TJ * WR + own_w[k];
+          const int y1 = own_y1[k], y2 = own_y2[k];
+          // two compensated chains (even and odd rows) for instruction-level
+          // parallelism, merged by a further two-sum
+          float h0 = 0.0f, l0 = 0.0f, h1 = 0.0f, l1 = 0.0f;
+          int jj = 0;
+          if (y1 < 0) {
+            for (; jj + 2 <= nt; jj += 2) {
+              two_sum_acc(h0, l0, col[jj * WR]);
+              two_sum_acc(h1, l1, col[(jj + 1) * WR]);
+            }
+            if (jj < nt) two_sum_acc(h0, l0, col[jj * WR]);
+          } else if (y2 < 0) {
+            for (; jj + 2 <= nt; jj += 2) {
+              two_sum_acc(h0, l0, __fmul_rn(col[jj * WR], ys[jj * p + y1]));
+              two_sum_acc(h1, l1, __fmul_rn(col[(jj + 1) * WR], ys[(jj + 1) * p + y1]));
+            }
+            if (jj < nt) two_sum_acc(h0, l0, __fmul_rn(col[jj * WR], ys[jj * p + y1]));
+          } else {
+            for (; jj + 2 <= nt; jj += 2) {
+              two_sum_acc(h0, l0, __fmul_rn(__fmul_rn(col[jj * WR], ys[jj * p + y1]), ys[jj * p + y2]));
+              two_sum_acc(h1, l1,
+                          __fmul_rn(__fmul_rn(col[(jj + 1) * WR], ys[(jj + 1) * p + y1]), ys[(jj + 1) * p + y2]));
+            }
+            if (jj < nt)
+              two_sum_acc(h0, l0, __fmul_rn(__fmul_rn(col[jj * WR], ys[jj * p + y1]), ys[jj * p + y2]));
+          }
+          two_sum_acc(h0, l0, h1);
+          acc[k] += (double)h0 + (double)__fadd_rn(l0, l1);
+        }
+      }
+    }
+    __syncthreads();
+  }
+
+  if (a.want_sums) {
+    double *dst = a.partials + (int64_t)blk * g * K;
+#pragma unroll
+    for (int k = 0; k < MAXOWN; ++k) {
+      const int e = threadIdx.x + k * THREADS;
+      if (e < E) dst[(int64_t)c0 * K + e] = acc[k];
+    }
+  }
+  if (a.want_ll && first_chunk) {
+    red[threadIdx.x] = llacc;
+    __syncthreads();
+    for (int s = THREADS / 2; s > 0; s >>= 1) {
+      if (threadIdx.x < s) red[threadIdx.x] += red[threadIdx.x + s];
+      __syncthreads();
+    }
+    if (threadIdx.x == 0) a.ll_partials[blk] = red[0];
+  }
+  if (bad) atomicOr(a.d_status, ERR_ZERO_DENSITY);
+}
+
 // One block's share of the posterior / sums work of one fit: tiles blk,
 // blk + nblk, ...; partial sums and the log-likelihood partial go to row blk.
 template <typename ET>
 __device__ __forceinline__ void posterior_block(const PosteriorArgs &a, int c0, int c1, int blk, int nblk,
                                                 unsigned char *smem_raw) {
+  if constexpr (sizeof(ET) == 4) {
+    posterior_block_f32(a, c0, c1, blk, nblk, smem_raw);
+    return;
+  }
   double *smem = reinterpret_cast<double *>(smem_raw);
   const int p = a.p, r = a.r, g = a.g;
   const int rp = r * (r + 1) / 2;
@@ -251,31 +433,57 @@ __device__ bool chol_inplace(double *S, int n, int ld) {
   return true;
 }
 
-__device__ double nu_equation(double nu, double c) {
-  return log(0.5 * nu) - digamma(0.5 * nu) + 1.0 + c;
-}
-
-// Root of log(nu/2) - psi(nu/2) + 1 + c = 0 in [lo, hi]; the left side
-// decreases in nu, so the bound is returned when there is no sign change.
-// Every thread of the block evaluates one interior point of the bracket per
-// round and the count of positive values picks the subinterval holding the
-// sign change: the bracket shrinks (blockDim.x + 1)-fold per round.  All
-// threads of the block must call it with the same arguments.
+// Root of h(nu) = log(nu/2) - psi(nu/2) + 1 + c in [lo, hi]; h decreases in
+// nu, so the bound is returned when there is no sign change.  Double-precision
+// work costs 64 times single-precision work on this GPU and a warp
+// instruction of it costs the same whatever the number of active lanes, so
+// warp 0 brackets the root with single-precision evaluations (32 interior
+// points per round, the bracket shrinks 33-fold per round, to ~1e-7
+// relative) and finishes with Newton steps on the double-precision h; h is
+// convex, so the steps approach the root monotonically once on its left, and
+// each is clamped to the bracket that the double-precision end values
+// certify.  The derivative enters only the step length, so its single-precision
+// value costs no accuracy.  All threads of the block must call it with the
+// same arguments.
 __device__ double solve_nu_block(double c, double lo, double hi) {
-  if (nu_equation(hi, c) >= 0.0) return hi;
-  if (nu_equation(lo, c) <= 0.0) return lo;
-  const int T = blockDim.x;
-  for (int round = 0; round < 60; ++round) {
-    const double w = (hi - lo) / (double)(T + 1);
-    const double x = lo + (double)(threadIdx.x + 1) * w;
-    const int npos = __syncthreads_count(nu_equation(x, c) > 0.0);
-    const double nlo = (npos == 0) ? lo : lo + (double)npos * w;
-    const double nhi = (npos == T) ? hi : lo + (double)(npos + 1) * w;
-    lo = nlo;
-    hi = nhi;
-    if (!(hi - lo > 2e-16 * hi)) break;
+  __shared__ double nu_out;
+  if (threadIdx.x < 32) {
+    const unsigned full = 0xffffffffu;
+    const int lane = threadIdx.x;
+    const double he = log_minus_digamma(0.5 * ((lane & 1) ? hi : lo)) + 1.0 + c;
+    const double h_lo = __shfl_sync(full, he, 0), h_hi = __shfl_sync(full, he, 1);
+    double nu;
+    if (h_hi >= 0.0) {
+      nu = hi;
+    } else if (h_lo <= 0.0) {
+      nu = lo;
+    } else {
+      float flo = (float)lo, fhi = (float)hi;
+      const float cp = (float)(1.0 + c);
+      for (int round = 0; round < 6; ++round) {
+        const float w = (fhi - flo) * (1.0f / 33.0f);
+        const float x = flo + (float)(lane + 1) * w;
+        const int npos = __popc(__ballot_sync(full, log_minus_digamma_f(0.5f * x) + cp > 0.0f));
+        const float nlo = (npos == 0) ? flo : flo + (float)npos * w;
+        const float nhi = (npos == 32) ? fhi : flo + (float)(npos + 1) * w;
+        flo = nlo;
+        fhi = nhi;
+      }
+      nu = 0.5 * ((double)flo + (double)fhi);
+      for (int it = 0; it < 6; ++it) {
+        const double h = log_minus_digamma(0.5 * nu) + 1.0 + c;
+        const double dh = 0.5 * (double)dlog_minus_digamma_f((float)(0.5 * nu));
+        const double nn = fmin(fmax(nu - h / dh, lo), hi);
+        // a step of 1e-8 relative leaves an error of order 1e-16 after it
+        const bool done = fabs(nn - nu) <= 1e-8 * nu;
+        nu = nn;
+        if (done) break;
+      }
+    }
+    if (lane == 0) nu_out = nu;
   }
-  return 0.5 * (lo + hi);
+  __syncthreads();
+  return nu_out;
 }
 
 // Thread 0 of the finalize block: pi, mu, Delta, Sigma of component i from its
@@ -364,10 +572,35 @@ __device__ void mstep_finalize_block(const double *partials, int nb, int g, int 
   __shared__ double S[3 + PMAX + RMAX + PMAX * RMAX + RMAX * (RMAX + 1) / 2 + PMAX * (PMAX + 1) / 2];
   __shared__ double red[128];
   const int K = sums_width(p, r);
-  for (int e = threadIdx.x; e < K; e += blockDim.x) {
-    double s = 0.0;
-    for (int b = 0; b < nb; ++b) s += partials[(int64_t)b * g * K + (int64_t)i * K + e];
-    S[e] = s;
+  // every warp takes a share of the blocks' partial sums (double-precision
+  // adds issue at 1/64 rate: one warp alone would run nb of them in a row),
+  // combined in a fixed order
+  const int splits = (int)blockDim.x / K < 8 ? (int)blockDim.x / K : 8;
+  if (splits > 1) {
+    const int e = threadIdx.x % K, sp = threadIdx.x / K;
+    if (sp < splits) {
+      double s0 = 0.0, s1 = 0.0;
+      int b = sp;
+      for (; b + splits < nb; b += 2 * splits) {
+        s0 += partials[(int64_t)b * g * K + (int64_t)i * K + e];
+        s1 += partials[(int64_t)(b + splits) * g * K + (int64_t)i * K + e];
+      }
+      if (b < nb) s0 += partials[(int64_t)b * g * K + (int64_t)i * K + e];
+      red[threadIdx.x] = s0 + s1;
+    }
+    __syncthreads();
+    if (threadIdx.x < K) {
+      double s = 0.0;
+      for (int q = 0; q < splits; ++q) s += red[q * K + threadIdx.x];
+      S[threadIdx.x] = s;
+    }
+    __syncthreads();
+  } else {
+    for (int e = threadIdx.x; e < K; e += blockDim.x) {
+      double s = 0.0;
+      for (int b = 0; b < nb; ++b) s += partials[(int64_t)b * g * K + (int64_t)i * K + e];
+      S[e] = s;
+    }
   }
   // total posterior weight over all components (= n when every tau row sums to 1)
   double tw = 0.0;

@@ -11,6 +11,10 @@
 //    tails keep full relative accuracy.
 //  - digamma: the recurrence psi(x) = psi(x + 1) - 1/x (DLMF 5.5.2) up to
 //    x >= 10, then the asymptotic series in Bernoulli numbers (DLMF 5.11.2).
+//  - log_minus_digamma: D(x) = log x - psi(x) without the cancellation of the
+//    two (same recurrence and series, the series taken for the difference),
+//    in double and single precision, and its derivative 1/x - psi'(x) in
+//    single precision (recurrence DLMF 5.15.5, series DLMF 5.15.8).
 //
 // lgamma(f), log(f), exp(f) and normcdfinv are CUDA's own functions, called as-is.
 #pragma once
@@ -158,6 +162,63 @@ __device__ inline double digamma(double x) {
                 f * (-1.0 / 252.0 +
                      f * (1.0 / 240.0 + f * (-1.0 / 132.0 + f * (691.0 / 32760.0 + f * (-1.0 / 12.0)))))));
   return acc + log(x) - 0.5 / x + series;
+}
+
+// D(x) = log x - psi(x), x > 0.  psi(x) = psi(x + m) - sum_{k<m} 1/(x + k)
+// with x + m >= 10 gives D(x) = -log1p(m/x) + sum_{k<m} 1/(x + k) + D(x + m);
+// the sum is accumulated as one fraction (a single division), and
+// D(y) = 1/(2y) + sum_k B_2k / (2k y^2k) to y^-14 (error below 5e-16 y^-16).
+__device__ inline double log_minus_digamma(double x) {
+  double num = 0.0, den = 1.0, y = x;
+  int m = 0;
+  while (y < 10.0) {
+    num = num * y + den;
+    den *= y;
+    y += 1.0;
+    ++m;
+  }
+  const double f = 1.0 / (y * y);
+  const double series =
+      f * (1.0 / 12.0 +
+           f * (-1.0 / 120.0 +
+                f * (1.0 / 252.0 +
+                     f * (-1.0 / 240.0 + f * (1.0 / 132.0 + f * (-691.0 / 32760.0 + f * (1.0 / 12.0)))))));
+  double d = 0.5 / y + series;
+  if (m > 0) d += num / den - log1p((double)m / x);
+  return d;
+}
+
+// Single-precision D(x) (series to y^-6: the next term is below 2e-9 y^-8).
+__device__ inline float log_minus_digamma_f(float x) {
+  float num = 0.0f, den = 1.0f, y = x;
+  int m = 0;
+  while (y < 10.0f) {
+    num = num * y + den;
+    den *= y;
+    y += 1.0f;
+    ++m;
+  }
+  const float f = 1.0f / (y * y);
+  float d = 0.5f / y + f * (1.0f / 12.0f + f * (-1.0f / 120.0f + f * (1.0f / 252.0f)));
+  if (m > 0) d += num / den - log1pf((float)m / x);
+  return d;
+}
+
+// Single-precision D'(x) = 1/x - psi'(x) (< 0).  psi'(x) = psi'(x + m) +
+// sum_{k<m} 1/(x + k)^2, so D'(x) = m / (x (x + m)) - sum_{k<m} 1/(x + k)^2 +
+// D'(x + m), and D'(y) = -1/(2y^2) - 1/(6y^3) + 1/(30y^5) - 1/(42y^7).
+__device__ inline float dlog_minus_digamma_f(float x) {
+  float s2 = 0.0f, y = x;
+  int m = 0;
+  while (y < 10.0f) {
+    s2 += 1.0f / (y * y);
+    y += 1.0f;
+    ++m;
+  }
+  const float iy = 1.0f / y, f = iy * iy;
+  float d = -f * (0.5f + iy * (1.0f / 6.0f + f * (-1.0f / 30.0f + f * (1.0f / 42.0f))));
+  if (m > 0) d += (float)m / (x * y) - s2;
+  return d;
 }
 
 }  // namespace cfust

@@ -195,6 +195,36 @@ def test_mstep_matches_oracle_fp64():
         _cmp(name, a, b, 1e-10)
 
 
+def test_mstep_matches_oracle_fp32():
+    """Single-precision M-step sums (CFUST_FP32) against the oracle's FP64
+    M-step on the same single-precision tau and e1..e4.
+
+    The kernel rounds each product tau e y to single precision (at most five
+    roundings of 2^-24 per term, relative to the sum of |terms|) and sums a
+    tile's products with two-sum compensation, tile totals in FP64.  Sigma
+    cancels the mean part of S7 (|mu|^2 / sigma^2 of order 10 here), and the
+    nu equation uses 1 + S8/S1, of order 1/nu, so nu's error is ~nu times the
+    sums': 1e-5 for pi, mu, Sigma, Delta and 1e-4 for nu cover both with a
+    margin of ~3.  2000 rows: 32 tiles, spread over many blocks, a ragged
+    last tile (2000 = 31 x 64 + 16).
+    """
+    torch = _torch()
+    Y, truth, init, lat = _problem("cfust_p4r4g3_n100000_N4096", 2000, 1024)
+    R = _oracle_estep(Y, init, lat)
+    r = init.r
+    f32 = lambda a: np.ascontiguousarray(a, dtype=np.float32)
+    tau, e1, e2, e3, e4 = (f32(R[k]) for k in ("tau", "e1", "e2", "e3", "e4"))
+    ref = O.mstep_update(O.mstep_sums(Y, tau.astype(np.float64), e1.astype(np.float64), e2.astype(np.float64),
+                                      e3.astype(np.float64), e4.astype(np.float64)), init, Y.shape[0])
+    dev = lambda a: torch.from_numpy(np.ascontiguousarray(a)).cuda()
+    E = dict(tau=dev(tau), e1=dev(e1), e2=dev(e2), e3=dev(np.transpose(e3, (0, 2, 1))),
+             e4=dev(np.stack([e4[:, :, t, h] for t in range(r) for h in range(t + 1)], axis=1)))
+    with binding.Context(lat, precision=binding.CFUST_FP32) as ctx:
+        got = ctx.cfust_mstep(dev(Y), E, init)
+    for a, b, name in zip(got.as_arrays(), ref.as_arrays(), ("pi", "mu", "Sigma", "Delta", "nu")):
+        _cmp(name, a, b, 1e-4 if name == "nu" else 1e-5)
+
+
 def _fit_gpu(Y, params, lat, precision, iters, use_graph=True):
     torch = _torch()
     with binding.Context(lat, precision=precision, max_iter=iters, use_graph=use_graph) as ctx:
