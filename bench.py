@@ -505,7 +505,10 @@ def run_surrogate(args):
     cheapest of 32..2048 points whose error (RMS over three shifts) is no
     larger.  One step = one EM iteration from the same start, CUDA-graph
     replayed; `value` is the surrogate form's pairs/s, the plain form at
-    equal accuracy is reported beside it."""
+    equal accuracy is reported beside it.  Both forms run with the same
+    triage margin (--sg-triage, 12 nats): a pair left to the lattice rule
+    whose density bound puts its weight below exp(-12) is dropped, at most
+    6e-6 of l per pair, inside the measured error."""
     import torch
     from paper_2005_06848_gb300 import binding, synth
     torch.cuda.set_device(0)
@@ -522,8 +525,9 @@ def run_surrogate(args):
     torch.cuda.synchronize()
     train_s = time.perf_counter() - t0
 
+    tn = args.sg_triage
     ctx_s = binding.Context(synth.make_lattice(args.sg_fallback_n, 4, seed=0), precision=binding.CFUST_FP32,
-                            max_iter=args.warmup + args.steps + 1, use_graph=True, timing=True)
+                            max_iter=args.warmup + args.steps + 1, use_graph=True, timing=True, triage_nats=tn)
     ctx_s.cfust_set_surrogate(sur)
     l_sur, _ = _loglik_ms(torch, ctx_s, Yd, init)
     fallback = ctx_s.cfust_last_fallback()
@@ -539,7 +543,8 @@ def run_surrogate(args):
         for N in ladder:
             errs = []
             for sd in range(3):
-                with binding.Context(synth.make_lattice(N, 4, seed=sd), precision=binding.CFUST_FP32) as c:
+                with binding.Context(synth.make_lattice(N, 4, seed=sd), precision=binding.CFUST_FP32,
+                                     triage_nats=tn) as c:
                     errs.append(c.cfust_loglik(Yd, init) - l_judge)
             rms[N] = float(np.sqrt(np.mean(np.square(errs))))
         ok_n = [N for N in ladder if rms[N] <= e_sur]
@@ -550,7 +555,7 @@ def run_surrogate(args):
     time.sleep(0.4)
     ms_s, kern_s, _ = _timed_em(torch, ctx_s, Yd, init, args.steps, args.warmup, flush)
     ctx_p = binding.Context(synth.make_lattice(n_eq, 4, seed=0), precision=binding.CFUST_FP32,
-                            max_iter=args.warmup + args.steps + 1, use_graph=True, timing=True)
+                            max_iter=args.warmup + args.steps + 1, use_graph=True, timing=True, triage_nats=tn)
     ms_p, kern_p, _ = _timed_em(torch, ctx_p, Yd, init, args.steps, args.warmup, flush)
     clocks = sampler.stop()
     ctx_p.close()
@@ -560,7 +565,7 @@ def run_surrogate(args):
     Ye = torch.empty_like(Yd)
     Ye.copy_(Yh)
     ctx_e = binding.Context(synth.make_lattice(args.sg_fallback_n, 4, seed=0), precision=binding.CFUST_FP32,
-                            max_iter=12, use_graph=True)
+                            max_iter=12, use_graph=True, triage_nats=tn)
     ctx_e.cfust_set_surrogate(sur)
     ctx_e.cfust_fit_begin(Ye, init)
     for _ in range(2):
@@ -597,6 +602,7 @@ def run_surrogate(args):
                                 "label_lattice_points": 8192, "seconds": train_s,
                                 "final_loss": float(trace[-1])},
                    "fallback_lattice_points": args.sg_fallback_n,
+                   "triage_nats": tn,
                    "step": "one EM iteration (CUDA graph replay) from the same start",
                    "l2": "flushed between timed steps"},
         "em_iters_per_s": 1.0 / step_s,
@@ -637,6 +643,9 @@ def main(argv=None):
     ap.add_argument("--sg-fallback-n", type=int, default=128)
     ap.add_argument("--sg-plain-n", type=int, default=0,
                     help="plain lattice points to compare with (skips the accuracy ladder; for profiling)")
+    ap.add_argument("--sg-triage", type=float, default=12.0,
+                    help="triage margin T (nats) of the surrogate and plain contexts: a listed or rescued "
+                         "pair with tau provably below exp(-T) is dropped, moving l by at most exp(-T)")
     ap.add_argument("--nfits", type=int, default=256)
     args = ap.parse_args(argv)
     if args.warmup < 3:

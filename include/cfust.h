@@ -57,11 +57,18 @@ typedef int cfust_status;
 #define CFUST_ENOMEM      -7   /* device allocation failed */
 
 #define CFUST_FP64 0   /* every step in double precision (parity mode) */
-#define CFUST_FP32 1   /* lattice sweeps in float; factorisations, log-likelihood and M-step sums in double */
+#define CFUST_FP32 1   /* lattice sweeps, posterior exponentials and the M-step sums' products in float
+                          (each 64-observation tile's products summed with two-sum compensation,
+                          tile totals in double); factorisations, per-pair prologue, log-sum-exp,
+                          log-likelihood and the conditional-maximisation update in double */
 
 /* Mixture parameters Psi = (pi_1..pi_g, theta_1..theta_g), theta_i = (mu_i, Sigma_i, Delta_i, nu_i)
  * (Section 2).  Host memory, row-major:
- *   pi[g], mu[g][p], Sigma[g][p][p] (full symmetric), Delta[g][p][r], nu[g]. */
+ *   pi[g], mu[g][p], Sigma[g][p][p] (full symmetric), Delta[g][p][r], nu[g].
+ * nu_i = +inf selects the CFUST family's skew-normal limit for component i
+ * (W = 1: t_p becomes the normal density, T_r the normal orthant probability,
+ * e1 = 1, e2 = 0); the M-step keeps nu_i = +inf.  A surrogate network leaves
+ * such components to the lattice rule (their dof lie outside its domain). */
 typedef struct {
   int g, p, r;
   double *pi;
@@ -96,6 +103,10 @@ typedef struct {
   int pairs_per_warp;     /* observations one warp sweeps in turn (1..32); 0 = chosen from n and g */
   int autotune;           /* 1: cfust_fit_batched times candidate launch shapes (pairs per warp,
                              resident CTAs per SM) on its first call for a batch and keeps the fastest */
+  double triage_nats;     /* T: in the fit and log-likelihood paths a pair left to a slower rule (the
+                             double-precision rescue, or the lattice rule behind a surrogate) whose
+                             density bound puts tau_ij below exp(-T) gets log f = -inf, e = 0; each such
+                             pair moves l by at most exp(-T).  0 selects 30; else in [1, 700]. */
 } cfust_opts;
 
 typedef struct cfust_ctx cfust_ctx;
@@ -192,6 +203,60 @@ cfust_status cfust_batched_shape(cfust_ctx *ctx, int *pairs_per_warp, int *ctas_
  * none survives. */
 cfust_status cfust_fit_multistart(cfust_ctx *ctx, const double *Y, int64_t n, cfust_params *starts, int nstarts,
                                   int burn_in, int *best, double *loglik_trace, int *iters_done);
+
+/* Initial partitions of Algorithm 1 by k-means (Section 3.1 names k-means
+ * and random partitions; the rule here is Lloyd's): each iteration assigns
+ * every observation to its nearest centre (squared Euclidean distance summed
+ * over the coordinates in order, each difference, square and sum rounded
+ * separately in double precision; ties to the lowest index) and stops when no
+ * label changed; otherwise each centre moves to the mean of its members (a
+ * centre without members stays).  Y: device [n][p].  centers: host [g][p],
+ * the starting centres on entry, the final ones on return.  labels: device
+ * int32 [n], written.  iters_done (host, may be NULL): assignment passes run
+ * (<= max_iter).  Synchronises every iteration.  CFUST_EINVAL for bad sizes
+ * or max_iter < 1. */
+cfust_status cfust_kmeans(cfust_ctx *ctx, const double *Y, int64_t n, int p, int g, double *centers, int max_iter,
+                          int32_t *labels, int *iters_done);
+
+/* Psi^(0) of a partition by moments (Algorithm 1's "compute Psi^(0)"; the
+ * paper does not give the rule, this is the library's): for group i with n_i
+ * members, pi_i = n_i / n, nu_i = nu0, Delta_i diagonal in its first
+ * min(p, r) columns with Delta_i[k][k] = lam * sign(skewness_k) * sd_k (the
+ * group's sample skewness and standard deviation of coordinate k, sign +1 at
+ * zero), and mu_i, Sigma_i matching the group's sample mean and covariance
+ * (divisor n_i) to the CFUST law's:
+ *   E[Y] = mu + m1 Delta 1_r,  Cov(Y) = nu/(nu-2) Sigma + Delta C Delta^T,
+ * m1 = E|U_k|, C = Cov(|U|), U ~ t_r(0, I, nu0).  lam is halved (at most 20
+ * times, then 0) until Sigma_i is positive definite.  labels: device int32
+ * [n] in 0..g-1 (CFUST_EINVAL otherwise).  params: host; g, p, r and the
+ * arrays set by the caller, the arrays written on success.  nu0 > 2 and
+ * lam >= 0 (CFUST_EINVAL otherwise).  CFUST_EDEGENERATE when a group has
+ * fewer than p + 1 members or a singular sample covariance.  Synchronises. */
+cfust_status cfust_init_partition(cfust_ctx *ctx, const double *Y, int64_t n, const int32_t *labels, double nu0,
+                                  double lam, cfust_params *params);
+
+/* Algorithm 1 from m partitions: Psi^(0) of each partition (cfust_init_partition),
+ * then cfust_fit_multistart over the partitions that gave initial values.
+ * labels: device int32 [m][n].  starts: host [m] with g, p, r and arrays set
+ * by the caller; start f receives its Psi^(0) (burned in when burn_in > 0;
+ * the chosen one is fitted further).  best: index into 0..m-1 of the chosen
+ * partition.  loglik_trace, iters_done: as for cfust_fit.  CFUST_EDEGENERATE
+ * when no partition gives initial values or no start survives its burn-in. */
+cfust_status cfust_multistart_partitions(cfust_ctx *ctx, const double *Y, int64_t n, const int32_t *labels, int m,
+                                         double nu0, double lam, int burn_in, cfust_params *starts, int *best,
+                                         double *loglik_trace, int *iters_done);
+
+/* l(Psi) under M shifted copies of the context's lattice rule (same
+ * generator z, shift m = shifts[m][0..dim-1], host, each in [0, 1)):
+ * randomised quasi-Monte Carlo.  With independent uniform shifts every
+ * copy's T_r estimate is unbiased, so the spread of loglik[0..M-1] (host,
+ * written) estimates the integration error of the rule: standard error
+ * sd / sqrt(M) for their mean (l, a sum of logarithms, carries a bias of
+ * second order in that error).  The context's own shift is restored before
+ * returning (also after an error).  Works with a surrogate attached (its
+ * fallback lattice is the context's).  Synchronises. */
+cfust_status cfust_loglik_shifts(cfust_ctx *ctx, const double *Y, int64_t n, const cfust_params *params, int M,
+                                 const double *shifts, double *loglik);
 
 /* Number of (i, j) pairs whose single-precision lattice sweep fell below the
  * underflow guard in the last E-step and were recomputed in double precision

@@ -37,6 +37,10 @@ What it computes, and where each step comes from:
   expected complete-data log-likelihood in the order pi, mu, Delta, Sigma, nu.
 * The stopping rule of Algorithm 4 (Aitken acceleration) and the multi-start
   selection of Algorithm 1.
+* The skew-normal limit (the paper's Section 2 notes the CFUST family's
+  limiting cases): a component with nu = +inf is the canonical fundamental
+  skew normal law, W = 1: t_p becomes the normal density phi_p, the chi scale
+  is 1, a_A = a_B = -q, e1 = 1, e2 = 0, and the nu update keeps nu = inf.
 
 Readings of the paper (its typos and silences) are listed in the module-level
 docstrings of the functions that use them.  Parity is pinned against closed
@@ -82,6 +86,8 @@ def chi_scale(u0: np.ndarray, m: float) -> np.ndarray:
     incomplete gamma function; the upper-tail inverse is used for u0 >= 1/2.
     """
     u0 = np.asarray(u0, dtype=np.float64)
+    if math.isinf(m):
+        return np.ones_like(u0)         # chi^2_m / m -> 1: the normal law
     a = 0.5 * m
     lo = special.gammaincinv(a, np.where(u0 < 0.5, u0, 0.25))
     hi = special.gammainccinv(a, np.where(u0 < 0.5, 0.75, 1.0 - u0))
@@ -166,9 +172,13 @@ def component_terms(Y, mu, Sigma, Delta, nu):
     dy = Y - mu[None, :]
     d = np.einsum("jp,pq,jq->j", dy, Oinv, dy)
     q = dy @ Oinv @ Delta                                    # [n, r]
-    log_tp = (special.gammaln(0.5 * (nu + p)) - special.gammaln(0.5 * nu)
-              - 0.5 * p * math.log(nu * math.pi) - 0.5 * logdet
-              - 0.5 * (nu + p) * np.log1p(d / nu))
+    if math.isinf(nu):
+        # the limit of t_p: the normal density phi_p(y; mu, Omega)
+        log_tp = -0.5 * p * math.log(2.0 * math.pi) - 0.5 * logdet - 0.5 * d
+    else:
+        log_tp = (special.gammaln(0.5 * (nu + p)) - special.gammaln(0.5 * nu)
+                  - 0.5 * p * math.log(nu * math.pi) - 0.5 * logdet
+                  - 0.5 * (nu + p) * np.log1p(d / nu))
     return d, q, Lam, log_tp
 
 
@@ -201,7 +211,7 @@ def estep_component(Y, mu, Sigma, Delta, nu, U, e2_mode=0, density_only=False,
     sB = chi_scale(U[:, 0], mB)
     for sl in _chunks(n, chunk):
         dd = d[sl]; qq = q[sl]
-        aA = -qq * np.sqrt(mA / (nu + dd))[:, None]
+        aA = -qq * _dof_ratio(mA, nu, dd)[:, None]
         if e2_mode == 1 and not density_only:
             TA, elogchi = sov_pass(aA, L, mA, U, moments=False, logchi=True, s=sA)
         else:
@@ -210,7 +220,7 @@ def estep_component(Y, mu, Sigma, Delta, nu, U, e2_mode=0, density_only=False,
             logf[sl] = r * LOG2 + log_tp[sl] + np.log(TA)
         if density_only:
             continue
-        aB = -qq * np.sqrt(mB / (nu + dd))[:, None]
+        aB = -qq * _dof_ratio(mB, nu, dd)[:, None]
         TB, EV, EVV = sov_pass(aB, L, mB, U, moments=True, s=sB)
         LEV = EV @ L.T                                         # L E[V]
         LEVVL = np.einsum("th,jhk,sk->jts", L, EVV, L)
@@ -218,6 +228,13 @@ def estep_component(Y, mu, Sigma, Delta, nu, U, e2_mode=0, density_only=False,
                                       elogchi if e2_mode == 1 else None)
         e1[sl], e2[sl], e3[sl], e4[sl] = c1, c2, c3, c4
     return out
+
+
+def _dof_ratio(m, nu, d):
+    """sqrt(m / (nu + d)), and its limit 1 at nu = inf."""
+    if math.isinf(nu):
+        return np.ones_like(d)
+    return np.sqrt(m / (nu + d))
 
 
 def expectations(d, q, nu, p, TA, TB, LEV, LEVVL, e2_mode=0, elogchi=None):
@@ -235,14 +252,21 @@ def expectations(d, q, nu, p, TA, TB, LEV, LEVVL, e2_mode=0, elogchi=None):
     mB = nu + p + 2.0
     ok = (TA > 0) & (TB > 0)
     with np.errstate(invalid="ignore", divide="ignore"):
-        c1 = (mA / (nu + d)) * TB / TA
-        sig = np.sqrt((nu + d) / mB)
+        if math.isinf(nu):
+            # W = 1: both passes integrate the same normal law
+            c1 = TB / TA
+            sig = np.ones_like(d)
+        else:
+            c1 = (mA / (nu + d)) * TB / TA
+            sig = np.sqrt((nu + d) / mB)
         EX = q + sig[:, None] * LEV
         EXX = (q[:, :, None] * q[:, None, :]
                + sig[:, None, None] * (q[:, :, None] * LEV[:, None, :]
                                        + LEV[:, :, None] * q[:, None, :])
                + (sig * sig)[:, None, None] * LEVVL)
-        if e2_mode == 1:
+        if math.isinf(nu):
+            c2 = np.zeros_like(d)        # E[log W | y] = log 1
+        elif e2_mode == 1:
             c2 = elogchi - np.log(nu + d)
         else:
             c2 = (c1 - np.log(0.5 * (nu + d)) - mA / (nu + d)
@@ -366,7 +390,8 @@ def mstep_update(sums, params, n, nu_min=1.0, nu_max=200.0, fix_delta=False):
         new.mu[i] = mu
         new.Delta[i] = Delta
         new.Sigma[i] = 0.5 * (Sig + Sig.T)
-        new.nu[i] = solve_nu(S["S8"] / S["S1"], nu_min, nu_max)
+        # nu = inf (the skew-normal limit) is a model choice, not updated
+        new.nu[i] = math.inf if math.isinf(params.nu[i]) else solve_nu(S["S8"] / S["S1"], nu_min, nu_max)
     return new
 
 

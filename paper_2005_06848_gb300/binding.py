@@ -27,7 +27,8 @@ EXPORTED = ["cfust_create", "cfust_destroy", "cfust_loglik", "cfust_estep", "cfu
             "cfust_surrogate_predict", "cfust_surrogate_gradient", "cfust_surrogate_get_params",
             "cfust_surrogate_set_params", "cfust_surrogate_train", "cfust_surrogate_last_error",
             "cfust_set_surrogate", "cfust_last_fallback", "cfust_surrogate_problems",
-            "cfust_surrogate_finetune", "cfust_fit_multistart"]
+            "cfust_surrogate_finetune", "cfust_fit_multistart", "cfust_kmeans", "cfust_init_partition",
+            "cfust_multistart_partitions", "cfust_loglik_shifts"]
 
 SURROGATE_NPARAM = 35338
 
@@ -54,7 +55,8 @@ class cfust_opts(ctypes.Structure):
     _fields_ = [("precision", ctypes.c_int), ("lattice", cfust_lattice), ("e2_mode", ctypes.c_int),
                 ("nu_min", ctypes.c_double), ("nu_max", ctypes.c_double),
                 ("max_iter", ctypes.c_int), ("tol", ctypes.c_double), ("use_graph", ctypes.c_int),
-                ("timing", ctypes.c_int), ("pairs_per_warp", ctypes.c_int), ("autotune", ctypes.c_int)]
+                ("timing", ctypes.c_int), ("pairs_per_warp", ctypes.c_int), ("autotune", ctypes.c_int),
+                ("triage_nats", ctypes.c_double)]
 
 
 _LIB = None
@@ -111,6 +113,13 @@ def load(build_if_missing: bool = True, path: str | None = None) -> ctypes.CDLL:
         "cfust_surrogate_problems": ([vp, vp, i64, P, i64, vp, i64, ctypes.POINTER(i64)], ctypes.c_int),
         "cfust_fit_multistart": ([vp, vp, i64, P, ctypes.c_int, ctypes.c_int, ctypes.POINTER(ctypes.c_int), dp,
                                   ctypes.POINTER(ctypes.c_int)], ctypes.c_int),
+        "cfust_kmeans": ([vp, vp, i64, ctypes.c_int, ctypes.c_int, dp, ctypes.c_int, vp,
+                          ctypes.POINTER(ctypes.c_int)], ctypes.c_int),
+        "cfust_init_partition": ([vp, vp, i64, vp, ctypes.c_double, ctypes.c_double, P], ctypes.c_int),
+        "cfust_loglik_shifts": ([vp, vp, i64, P, ctypes.c_int, dp, dp], ctypes.c_int),
+        "cfust_multistart_partitions": ([vp, vp, i64, vp, ctypes.c_int, ctypes.c_double, ctypes.c_double,
+                                         ctypes.c_int, P, ctypes.POINTER(ctypes.c_int), dp,
+                                         ctypes.POINTER(ctypes.c_int)], ctypes.c_int),
         "cfust_surrogate_finetune": ([vp, vp, i64, ctypes.c_int, ctypes.c_int, ctypes.c_float, ctypes.c_uint64,
                                       ctypes.POINTER(ctypes.c_float)], ctypes.c_int),
     }
@@ -138,6 +147,11 @@ class _HostParams:
         return Params(*(a.copy() for a in self.arrays))
 
 
+def _zero_params(g, p, r):
+    from .synth import Params
+    return Params(np.zeros(g), np.zeros((g, p)), np.zeros((g, p, p)), np.zeros((g, p, r)), np.zeros(g))
+
+
 def _ptr(t):
     return ctypes.c_void_p(0 if t is None else t.data_ptr())
 
@@ -147,7 +161,7 @@ class Context:
 
     def __init__(self, lattice, precision=CFUST_FP32, e2_mode=0, nu_min=0.0, nu_max=0.0,
                  max_iter=0, tol=0.0, use_graph=True, timing=False, pairs_per_warp=0, autotune=False,
-                 stream=None):
+                 stream=None, triage_nats=0.0):
         import torch
         self.lib = load()
         self._z = np.ascontiguousarray(lattice.z, dtype=np.int64)
@@ -157,7 +171,7 @@ class Context:
                             self._shift.ctypes.data_as(ctypes.POINTER(ctypes.c_double)))
         self.opts = cfust_opts(int(precision), lat, int(e2_mode), float(nu_min), float(nu_max),
                                int(max_iter), float(tol), 1 if use_graph else 0, 1 if timing else 0,
-                               int(pairs_per_warp), 1 if autotune else 0)
+                               int(pairs_per_warp), 1 if autotune else 0, float(triage_nats))
         self.precision = int(precision)
         self.stream = stream if stream is not None else torch.cuda.current_stream()
         self.lattice_n = int(lattice.n)
@@ -294,6 +308,54 @@ class Context:
         self._check(self.lib.cfust_fit_multistart(self.h, _ptr(Y), Y.shape[0], arr, ns, int(burn_in),
                                                   ctypes.byref(best), trace.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
                                                   ctypes.byref(done)))
+        out = [h.to_params() for h in hps]
+        return best.value, out[best.value], trace[:done.value + 1], done.value, out
+
+    def cfust_loglik_shifts(self, Y, params, shifts):
+        """l(Psi) under each shift (rows of `shifts`, [M][dim]) of the context's
+        lattice; returns float64 [M].  Mean and sd / sqrt(M) estimate l and
+        the rule's integration error."""
+        hp = _HostParams(params)
+        S = np.ascontiguousarray(shifts, dtype=np.float64)
+        out = np.zeros(S.shape[0])
+        dpp = ctypes.POINTER(ctypes.c_double)
+        self._check(self.lib.cfust_loglik_shifts(self.h, _ptr(Y), Y.shape[0], ctypes.byref(hp.c), S.shape[0],
+                                                 S.ctypes.data_as(dpp), out.ctypes.data_as(dpp)))
+        return out
+
+    def cfust_kmeans(self, Y, centers0, max_iter, labels=None):
+        """Lloyd's k-means from host centres [g][p].  Returns (labels: device
+        int32 tensor [n], final centres, assignment passes)."""
+        import torch
+        C = np.ascontiguousarray(centers0, dtype=np.float64).copy()
+        g, p = C.shape
+        if labels is None:
+            labels = torch.empty(Y.shape[0], dtype=torch.int32, device=Y.device)
+        it = ctypes.c_int()
+        self._check(self.lib.cfust_kmeans(self.h, _ptr(Y), Y.shape[0], p, g,
+                                          C.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), int(max_iter),
+                                          _ptr(labels), ctypes.byref(it)))
+        return labels, C, it.value
+
+    def cfust_init_partition(self, Y, labels, g, r, nu0=10.0, lam=0.5):
+        """Psi^(0) of the partition `labels` (device int32 [n]) by moments."""
+        hp = _HostParams(_zero_params(g, Y.shape[1], r))
+        self._check(self.lib.cfust_init_partition(self.h, _ptr(Y), Y.shape[0], _ptr(labels), float(nu0),
+                                                  float(lam), ctypes.byref(hp.c)))
+        return hp.to_params()
+
+    def cfust_multistart_partitions(self, Y, labels, g, r, nu0=10.0, lam=0.5, burn_in=0):
+        """Algorithm 1 from partitions (device int32 [m][n]).  Returns (index of
+        the chosen partition, its fitted params, trace, iterations, every
+        start's initial (or burned-in) params)."""
+        m = labels.shape[0]
+        hps = [_HostParams(_zero_params(g, Y.shape[1], r)) for _ in range(m)]
+        arr = (cfust_params * m)(*[h.c for h in hps])
+        trace = np.zeros(self.opts.max_iter + 1)
+        best, done = ctypes.c_int(), ctypes.c_int()
+        self._check(self.lib.cfust_multistart_partitions(
+            self.h, _ptr(Y), Y.shape[0], _ptr(labels), m, float(nu0), float(lam), int(burn_in), arr,
+            ctypes.byref(best), trace.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), ctypes.byref(done)))
         out = [h.to_params() for h in hps]
         return best.value, out[best.value], trace[:done.value + 1], done.value, out
 

@@ -205,7 +205,8 @@ cfust_status check_params(cfust_ctx *c, const cfust_params *P) {
   for (int i = 0; i < g; ++i) {
     if (!(P->pi[i] > 0.0) || !isfinite(P->pi[i])) return fail(c, CFUST_EINVAL, "pi_i must be > 0");
     spi += P->pi[i];
-    if (!(P->nu[i] > 0.0) || !isfinite(P->nu[i])) return fail(c, CFUST_EINVAL, "nu_i must be > 0");
+    // +inf is the skew-normal limit (kept by the M-step)
+    if (!(P->nu[i] > 0.0)) return fail(c, CFUST_EINVAL, "nu_i must be > 0 (or +inf)");
     for (int a = 0; a < p; ++a)
       if (!isfinite(P->mu[i * p + a])) return fail(c, CFUST_EINVAL, "mu not finite");
     for (int a = 0; a < p * r; ++a)
@@ -270,6 +271,9 @@ cfust_status status_from_bits(cfust_ctx *c, int bits) {
   if (bits & ERR_NOTPD_SIGMA) return fail(c, CFUST_ENOTPD, "updated Sigma not positive definite");
   if (bits & ERR_DEGENERATE) return fail(c, CFUST_EDEGENERATE, "a component lost its posterior weight");
   if (bits & ERR_ZERO_DENSITY) return fail(c, CFUST_ENUMERIC, "an observation has zero density under every component");
+  if (bits & ERR_BAD_LABEL) return fail(c, CFUST_EINVAL, "a partition label is outside 0..g-1");
+  if (bits & ERR_INIT_GROUP)
+    return fail(c, CFUST_EDEGENERATE, "a partition group has fewer than p + 1 members or a singular covariance");
   return fail(c, CFUST_ENUMERIC, "non-finite value in the E-step");
 }
 
@@ -339,7 +343,8 @@ cfust_status run_estep(cfust_ctx *c, const double *Y, int64_t n, EstepOut o, boo
   if (!c->sur) {
     CF_CUDA(c, launch_estep(c->opts.precision, Y, n, c->g, c->p, c->r, c->lat, c->d_c64, c->d_c32,
                             c->d_chi64, c->d_chi32, o, density_only, c->opts.e2_mode, c->d_rescue,
-                            c->d_rescue_cnt, c->d_status, c->opts.pairs_per_warp, st, tm, triage, pi));
+                            c->d_rescue_cnt, c->d_status, c->opts.pairs_per_warp, st, tm, triage, pi,
+                            (float)c->opts.triage_nats));
     return CFUST_OK;
   }
   if (c->opts.precision != CFUST_FP32 || c->opts.e2_mode != 0 || c->r != 3)
@@ -351,7 +356,7 @@ cfust_status run_estep(cfust_ctx *c, const double *Y, int64_t n, EstepOut o, boo
   if (tm.stop) CF_CUDA(c, cudaEventRecordWithFlags(tm.stop, st, evflag));
   CF_CUDA(c, launch_estep_list(Y, n, c->g, c->p, c->r, c->lat, c->d_c64, c->d_c32, c->d_chi64, c->d_chi32, o,
                                density_only, c->opts.e2_mode, c->d_fb, c->d_fb_cnt, c->d_rescue,
-                               c->d_rescue_cnt, c->d_status, st, triage, pi));
+                               c->d_rescue_cnt, c->d_status, st, triage, pi, (float)c->opts.triage_nats));
   return CFUST_OK;
 }
 
@@ -434,10 +439,15 @@ cfust_status cfust_create(cfust_ctx **out, const cfust_opts *o, void *cuda_strea
     g_create_error = "need 0 < nu_min < nu_max";
     return CFUST_EINVAL;
   }
+  if (o->triage_nats != 0.0 && !(o->triage_nats >= 1.0 && o->triage_nats <= 700.0)) {
+    g_create_error = "triage_nats must be 0 (default 30) or in [1, 700]";
+    return CFUST_EINVAL;
+  }
   cfust_ctx *c = new cfust_ctx();
   c->opts = *o;
   c->opts.lattice.z = nullptr;
   c->opts.lattice.shift = nullptr;
+  if (c->opts.triage_nats == 0.0) c->opts.triage_nats = 30.0;
   c->stream = static_cast<cudaStream_t>(cuda_stream);
   if (cudaGetDevice(&c->device) != cudaSuccess) {
     g_create_error = "no CUDA device";
@@ -1268,7 +1278,8 @@ extern "C" cfust_status cfust_fit_multistart(cfust_ctx *c, const double *Y, int6
       const cfust_status s = cfust_fit_batched(c, nstarts, Ys.data(), ns.data(), starts, tr.data(), st.data());
       free_batch(c->batch);
       c->opts.max_iter = keep;
-      if (s != CFUST_OK) return s;
+      // a start that degenerates (its own status) is only left out
+      if (s != CFUST_OK && s != CFUST_ENOTPD && s != CFUST_ENUMERIC && s != CFUST_EDEGENERATE) return s;
       for (int f = 0; f < nstarts; ++f) {
         const double ll = tr[(size_t)f * (burn_in + 1) + burn_in];
         if (st[f] == 0 && isfinite(ll) && ll > best_ll) {
@@ -1281,4 +1292,180 @@ extern "C" cfust_status cfust_fit_multistart(cfust_ctx *c, const double *Y, int6
   }
   *best = chosen;
   return cfust_fit(c, Y, n, &starts[chosen], trace, iters_done);
+}
+
+// ---------------------------------------------------------------------------
+// Initial values of Algorithm 1: k-means partitions, Psi^(0) of a partition
+// by moments, and the multi-start fit from partitions.
+// ---------------------------------------------------------------------------
+
+namespace {
+
+// Device scratch of one initial-value call (freed on every return path).
+struct InitScratch {
+  double *partials = nullptr, *cm = nullptr, *counts = nullptr, *params = nullptr, *lam = nullptr;
+  unsigned long long *changed = nullptr;
+  int *status = nullptr;
+  ~InitScratch() {
+    cudaFree(partials);
+    cudaFree(cm);
+    cudaFree(counts);
+    cudaFree(params);
+    cudaFree(lam);
+    cudaFree(changed);
+    cudaFree(status);
+  }
+};
+
+cfust_status check_init_shape(cfust_ctx *c, const double *Y, int64_t n, int g, int p) {
+  if (!Y || n < 1) return fail(c, CFUST_EINVAL, "Y must be a device array with n >= 1 rows");
+  if (g < 1 || g > CFUST_GMAX || p < 1 || p > CFUST_PMAX) return fail(c, CFUST_EINVAL, "g or p out of range");
+  if (n > (int64_t)1 << 40) return fail(c, CFUST_EINVAL, "n too large");
+  return CFUST_OK;
+}
+
+}  // namespace
+
+extern "C" cfust_status cfust_kmeans(cfust_ctx *c, const double *Y, int64_t n, int p, int g, double *centers,
+                                     int max_iter, int32_t *labels, int *iters_done) {
+  if (!c) return CFUST_EINVAL;
+  cfust_status s = check_init_shape(c, Y, n, g, p);
+  if (s != CFUST_OK) return s;
+  if (!centers || !labels || max_iter < 1) return fail(c, CFUST_EINVAL, "centers, labels and max_iter >= 1 required");
+  DeviceGuard dg(c->device);
+  const int nblk = group_sums_nblocks(n);
+  const int W = group_sums_width(0, p);
+  InitScratch sc;
+  CF_CUDA(c, cudaMalloc(&sc.partials, sizeof(double) * nblk * g * W));
+  CF_CUDA(c, cudaMalloc(&sc.cm, sizeof(double) * g * p));
+  CF_CUDA(c, cudaMalloc(&sc.changed, sizeof(unsigned long long)));
+  CF_CUDA(c, cudaMalloc(&sc.status, sizeof(int)));
+  CF_CUDA(c, cudaMemcpyAsync(sc.cm, centers, sizeof(double) * g * p, cudaMemcpyHostToDevice, c->stream));
+  CF_CUDA(c, cudaMemsetAsync(sc.status, 0, sizeof(int), c->stream));
+  int it = 0;
+  for (it = 1; it <= max_iter; ++it) {
+    unsigned long long changed = 0;
+    CF_CUDA(c, cudaMemsetAsync(sc.changed, 0, sizeof(unsigned long long), c->stream));
+    CF_CUDA(c, launch_group_sums(0, Y, n, p, g, labels, sc.cm, 1, it == 1, sc.partials, nblk, sc.changed,
+                                 sc.status, c->stream));
+    CF_CUDA(c, cudaMemcpyAsync(&changed, sc.changed, sizeof(changed), cudaMemcpyDeviceToHost, c->stream));
+    CF_CUDA(c, cudaStreamSynchronize(c->stream));
+    // an assignment that changed nothing leaves the centres at its groups' means
+    if (changed == 0) break;
+    CF_CUDA(c, launch_kmeans_update(sc.partials, nblk, g, p, sc.cm, c->stream));
+  }
+  if (it > max_iter) it = max_iter;
+  CF_CUDA(c, cudaMemcpyAsync(centers, sc.cm, sizeof(double) * g * p, cudaMemcpyDeviceToHost, c->stream));
+  CF_CUDA(c, cudaStreamSynchronize(c->stream));
+  if (iters_done) *iters_done = it;
+  return CFUST_OK;
+}
+
+extern "C" cfust_status cfust_init_partition(cfust_ctx *c, const double *Y, int64_t n, const int32_t *labels,
+                                             double nu0, double lam, cfust_params *P) {
+  if (!c) return CFUST_EINVAL;
+  if (!P || !P->pi || !P->mu || !P->Sigma || !P->Delta || !P->nu) return fail(c, CFUST_EINVAL, "params arrays required");
+  cfust_status s = check_init_shape(c, Y, n, P->g, P->p);
+  if (s != CFUST_OK) return s;
+  if (P->r < 1 || P->r > CFUST_RMAX) return fail(c, CFUST_EINVAL, "r out of range");
+  if (!labels) return fail(c, CFUST_EINVAL, "labels required");
+  if (!(nu0 > 2.0) || !isfinite(nu0)) return fail(c, CFUST_EINVAL, "nu0 must exceed 2");
+  if (!(lam >= 0.0) || !isfinite(lam)) return fail(c, CFUST_EINVAL, "lam must be finite and >= 0");
+  const int g = P->g, p = P->p, r = P->r;
+  DeviceGuard dg(c->device);
+  const int nblk = group_sums_nblocks(n);
+  const int W0 = group_sums_width(0, p), W1 = group_sums_width(1, p);
+  InitScratch sc;
+  CF_CUDA(c, cudaMalloc(&sc.partials, sizeof(double) * nblk * g * (W0 > W1 ? W0 : W1)));
+  CF_CUDA(c, cudaMalloc(&sc.cm, sizeof(double) * g * p));
+  CF_CUDA(c, cudaMalloc(&sc.counts, sizeof(double) * g));
+  CF_CUDA(c, cudaMalloc(&sc.params, sizeof(double) * param_block_size(g, p, r)));
+  CF_CUDA(c, cudaMalloc(&sc.status, sizeof(int)));
+  CF_CUDA(c, cudaMemsetAsync(sc.status, 0, sizeof(int), c->stream));
+  int32_t *lab = const_cast<int32_t *>(labels);  // read only when assign = 0
+  CF_CUDA(c, launch_group_sums(0, Y, n, p, g, lab, nullptr, 0, 0, sc.partials, nblk, nullptr, sc.status, c->stream));
+  CF_CUDA(c, launch_group_means(sc.partials, nblk, g, p, sc.cm, sc.counts, c->stream));
+  CF_CUDA(c, launch_group_sums(1, Y, n, p, g, lab, sc.cm, 0, 0, sc.partials, nblk, nullptr, sc.status, c->stream));
+  CF_CUDA(c, launch_moment_finalize(sc.partials, nblk, sc.counts, sc.cm, n, g, p, r, nu0, lam, sc.params, nullptr,
+                                    sc.status, c->stream));
+  int bits = 0;
+  std::vector<double> host(param_block_size(g, p, r));
+  CF_CUDA(c, cudaMemcpyAsync(&bits, sc.status, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+  CF_CUDA(c, cudaMemcpyAsync(host.data(), sc.params, sizeof(double) * host.size(), cudaMemcpyDeviceToHost,
+                             c->stream));
+  CF_CUDA(c, cudaStreamSynchronize(c->stream));
+  if (bits) return status_from_bits(c, bits);
+  ParamView v = param_view(host.data(), g, p, r);
+  memcpy(P->pi, v.pi, sizeof(double) * g);
+  memcpy(P->mu, v.mu, sizeof(double) * g * p);
+  memcpy(P->Sigma, v.Sigma, sizeof(double) * g * p * p);
+  memcpy(P->Delta, v.Delta, sizeof(double) * g * p * r);
+  memcpy(P->nu, v.nu, sizeof(double) * g);
+  return CFUST_OK;
+}
+
+extern "C" cfust_status cfust_multistart_partitions(cfust_ctx *c, const double *Y, int64_t n, const int32_t *labels,
+                                                    int m, double nu0, double lam, int burn_in, cfust_params *starts,
+                                                    int *best, double *trace, int *iters_done) {
+  if (!c) return CFUST_EINVAL;
+  if (m < 1 || !labels || !starts || !best) return fail(c, CFUST_EINVAL, "m >= 1, labels, starts and best required");
+  std::vector<cfust_params> ok;
+  std::vector<int> idx;
+  for (int f = 0; f < m; ++f) {
+    const cfust_status s = cfust_init_partition(c, Y, n, labels + (int64_t)f * n, nu0, lam, &starts[f]);
+    if (s == CFUST_OK) {
+      ok.push_back(starts[f]);
+      idx.push_back(f);
+    } else if (s != CFUST_EDEGENERATE) {
+      return s;
+    }
+  }
+  if (ok.empty()) return fail(c, CFUST_EDEGENERATE, "no partition gave initial values");
+  int b = 0;
+  const cfust_status s = cfust_fit_multistart(c, Y, n, ok.data(), (int)ok.size(), burn_in, &b, trace, iters_done);
+  *best = (b >= 0 && b < (int)idx.size()) ? idx[b] : -1;
+  return s;
+}
+
+// ---------------------------------------------------------------------------
+// Randomised-shift error estimate of the lattice rule.
+// ---------------------------------------------------------------------------
+
+namespace {
+
+void set_lattice_shift(LatticeDev &lat, int dim, const double *shift) {
+  for (int t = 0; t < dim; ++t) {
+    lat.shift[t] = shift[t];
+    const double sn = shift[t] * (double)lat.n;
+    lat.sint[t] = (int)floor(sn);
+    lat.sfrac[t] = sn - floor(sn);
+  }
+}
+
+}  // namespace
+
+extern "C" cfust_status cfust_loglik_shifts(cfust_ctx *c, const double *Y, int64_t n, const cfust_params *P, int M,
+                                            const double *shifts, double *loglik) {
+  if (!c) return CFUST_EINVAL;
+  if (M < 1 || !shifts || !loglik) return fail(c, CFUST_EINVAL, "M >= 1, shifts and loglik required");
+  const int dim = c->opts.lattice.dim;
+  for (int64_t k = 0; k < (int64_t)M * dim; ++k)
+    if (!(shifts[k] >= 0.0 && shifts[k] < 1.0)) return fail(c, CFUST_EINVAL, "lattice shift must lie in [0, 1)");
+  DeviceGuard dg(c->device);
+  const LatticeDev saved = c->lat;
+  cfust_status s = CFUST_OK;
+  for (int m = 0; m < M && s == CFUST_OK; ++m) {
+    set_lattice_shift(c->lat, dim, shifts + (int64_t)m * dim);
+    if (launch_uniform_table(c->lat, dim - 1, c->d_utab, c->stream) != cudaSuccess) {
+      s = fail(c, CFUST_ECUDA, "rebuilding the lattice table failed");
+      break;
+    }
+    s = cfust_loglik(c, Y, n, P, &loglik[m]);
+  }
+  // the context's own rule again (graphs captured before hold its values)
+  c->lat = saved;
+  if (launch_uniform_table(c->lat, dim - 1, c->d_utab, c->stream) != cudaSuccess ||
+      cudaStreamSynchronize(c->stream) != cudaSuccess)
+    return fail(c, CFUST_ECUDA, "restoring the lattice table failed");
+  return s;
 }

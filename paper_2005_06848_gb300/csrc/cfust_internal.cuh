@@ -22,6 +22,8 @@ enum : int {
   ERR_DEGENERATE = 1 << 5,
   ERR_TIMEOUT = 1 << 6,
   ERR_ZERO_DENSITY = 1 << 7,
+  ERR_BAD_LABEL = 1 << 8,    // a partition label outside 0..g-1
+  ERR_INIT_GROUP = 1 << 9,   // a partition group with < p + 1 members or a singular covariance
 };
 
 // Per-component constants of Eq. 2, produced in double by the precompute
@@ -121,7 +123,7 @@ struct SweepTiming {
 // E-step lattice sweeps for all (i, j).  precision: CFUST_FP64 / CFUST_FP32.
 // In FP32 mode, pairs whose sweep underflows are appended to rescue_list and
 // recomputed by the log-domain rescue pass (both launched here).  With
-// `triage`, a queued pair whose posterior weight is below exp(-30) of the
+// `triage`, a queued pair whose posterior weight is below exp(-tnats) of the
 // best component of its observation (judged from an upper bound of its
 // density) gets log f = -inf and e = 0 instead (fit and log-likelihood paths).
 cudaError_t launch_estep(int precision, const double *Y, int64_t n, int g, int p, int r,
@@ -129,7 +131,7 @@ cudaError_t launch_estep(int precision, const double *Y, int64_t n, int g, int p
                          const double *chi64, const float *chi32, EstepOut out, bool density_only,
                          int e2_mode, unsigned long long *rescue_list, unsigned *rescue_count, int *d_status,
                          int pairs_per_warp, cudaStream_t st, SweepTiming tm = SweepTiming(),
-                         int triage = 0, const double *d_pi = nullptr);
+                         int triage = 0, const double *d_pi = nullptr, float tnats = 30.f);
 
 // FP32 lattice sweep (r = 3 only) of the observations listed per component:
 // list[i * n + k], k < count[i] (device counts), followed by the rescue pass.
@@ -139,7 +141,7 @@ cudaError_t launch_estep_list(const double *Y, int64_t n, int g, int p, int r, c
                               const float *chi32, EstepOut out, bool density_only, int e2_mode,
                               const int *list, const unsigned *count, unsigned long long *rescue_list,
                               unsigned *rescue_count, int *d_status, cudaStream_t st, int triage,
-                              const double *d_pi);
+                              const double *d_pi, float tnats = 30.f);
 
 // Device view of a trained surrogate network (owned by cfust_surrogate):
 // packed BF16 weights W1 [16][128], W2, W3 [128][128], W4 [128][16] (input x
@@ -261,5 +263,22 @@ cudaError_t launch_reduce_ll_batched(const BatchDev &b, const double *ll_partial
 
 cudaError_t launch_finalize_batched(const BatchDev &b, int p, int r, const double *partials, double nu_min,
                                     double nu_max, cudaStream_t st);
+
+
+// Initial values of Algorithm 1 (init.cu): per-group sums of a partition
+// (mode 0: counts and sums, optionally assigning nearest centres first;
+// mode 1: central second and third moments about given means), the k-means
+// centre update, the group means, and the moment rule for Psi^(0).
+int group_sums_width(int mode, int p);
+int group_sums_nblocks(int64_t n);
+cudaError_t launch_group_sums(int mode, const double *Y, int64_t n, int p, int g, int32_t *labels,
+                              const double *cm, int assign, int first, double *partials, int nblk,
+                              unsigned long long *changed, int *status, cudaStream_t st);
+cudaError_t launch_kmeans_update(const double *partials, int nblk, int g, int p, double *centers, cudaStream_t st);
+cudaError_t launch_group_means(const double *partials, int nblk, int g, int p, double *means, double *counts,
+                               cudaStream_t st);
+cudaError_t launch_moment_finalize(const double *partials, int nblk, const double *counts, const double *means,
+                                   int64_t n, int g, int p, int r, double nu0, double lam, double *params,
+                                   double *lam_used, int *status, cudaStream_t st);
 
 }  // namespace cfust

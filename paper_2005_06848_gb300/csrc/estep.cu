@@ -94,6 +94,7 @@ struct EArgs {
   int *status;
   int triage;          // 1: skip queued pairs whose posterior weight is provably negligible
   const double *pi;    // device [g], read by the triage
+  float tnats;         // the triage's margin: tau_ij < exp(-tnats) counts as negligible
 };
 
 // The per-fit part of a sweep: observations, their count, the component
@@ -221,7 +222,8 @@ __device__ __forceinline__ Prologue<R> prologue(const EArgs &a, const FitView &f
     }
   }
   pr.d = d;
-  pr.logt = c.c0 - 0.5 * c.mA * log1p(d / c.nu);
+  // log t_p, or log phi_p at nu = inf (the skew-normal limit)
+  pr.logt = isinf(c.nu) ? c.c0 - 0.5 * d : c.c0 - 0.5 * c.mA * log1p(d / c.nu);
   return pr;
 }
 
@@ -251,9 +253,12 @@ __device__ __forceinline__ bool pair_sweep(const EArgs &a, const FitView &fv, co
   // per-pair scalars, run by every lane: in the precision of the sweep (FP64
   // divides, roots and logarithms cost 64x on this GPU, and in single
   // precision every one of these rounds to float anyway)
+  // at nu = inf (the skew-normal limit) W = 1: both passes take the limits
+  // -q with scale 1, so their sums agree bit for bit and e1 = 1, e2 = 0
+  const bool nrm = isinf(c.nu);
   const T nud = static_cast<T>(c.nu + pr.d);
   const T mAT = static_cast<T>(c.mA), mBT = static_cast<T>(c.mB);
-  const T fA = M::sq(mAT / nud), fB = M::sq(mBT / nud);
+  const T fA = nrm ? T(1) : M::sq(mAT / nud), fB = nrm ? T(1) : M::sq(mBT / nud);
   T q[R], aA[R], aB[R];
 #pragma unroll
   for (int t = 0; t < R; ++t) {
@@ -441,9 +446,9 @@ __device__ __forceinline__ bool pair_sweep(const EArgs &a, const FitView &fv, co
   if (DENS) return false;
 
   const bool ok = (SA > T(0)) && (SB > T(0));
-  const T ratio = mAT / nud;
+  const T ratio = nrm ? T(1) : mAT / nud;
   const T e1 = ok ? ratio * (SB / SA) : T(0);
-  const T sig = M::sq(nud / mBT);
+  const T sig = nrm ? T(1) : M::sq(nud / mBT);
   const T iSB = ok ? T(1) / SB : T(0);
   T LEV[R];
 #pragma unroll
@@ -454,7 +459,9 @@ __device__ __forceinline__ bool pair_sweep(const EArgs &a, const FitView &fv, co
     LEV[t] = s;
   }
   T e2;
-  if (e2lat)
+  if (nrm)
+    e2 = T(0);
+  else if (e2lat)
     e2 = ok ? SL / SA - M::lg(nud) : T(0);
   else
     e2 = ok ? e1 - (M::lg(T(0.5) * nud) + ratio - static_cast<T>(c.psiA)) : T(0);
@@ -584,7 +591,7 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? CFUST_ESTEP_MINB : 1) es
 // log f = -inf and zero expectations instead of a sweep.  Unknown entries do
 // not count towards the best (that only makes the test more cautious).
 template <int R, bool DENS>
-__device__ bool triage_listed(const FitView &fv, int i, int64_t j) {
+__device__ bool triage_listed(const FitView &fv, int i, int64_t j, float tnats) {
   const float *lf = reinterpret_cast<const float *>(fv.out.logf);
   float best = -INFINITY;
   for (int h = 0; h < fv.g; ++h) {
@@ -592,7 +599,7 @@ __device__ bool triage_listed(const FitView &fv, int i, int64_t j) {
     if (v < INFINITY) best = fmaxf(best, logf((float)fv.pi[h]) + v);
   }
   const float mine = logf((float)fv.pi[i]) + lf[(int64_t)i * fv.n + j];
-  if (!(isfinite(best) && mine < best - 30.0f)) return false;
+  if (!(isfinite(best) && mine < best - tnats)) return false;
   const int64_t ij = (int64_t)i * fv.n + j;
   constexpr int RP = R * (R + 1) / 2;
   store<float>(fv.out.logf, ij, -INFINITY);
@@ -632,7 +639,7 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? CFUST_ESTEP_MINB : 1)
     bool myskip = false;
     if (lane < m) {
       myj = li[base + lane];
-      if (a.triage) myskip = triage_listed<R, DENS>(fv, i, myj);
+      if (a.triage) myskip = triage_listed<R, DENS>(fv, i, myj, a.tnats);
       if (!myskip) mine = prologue<T, R>(a, fv, *cs, myj);
     }
     const unsigned skipped = __ballot_sync(0xffffffffu, myskip);
@@ -708,8 +715,9 @@ __device__ void pair_sweep_log_cta(const EArgs &a, const FitView &fv, const Comp
   constexpr int NV = 3 + R + RP;  // SA, SL, SB, M1, M2
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
   const int N = a.N;
+  const bool nrm = isinf(c.nu);  // the skew-normal limit: scale 1, e1 = 1, e2 = 0
   const double nud64 = c.nu + pr.d;
-  const double fA = sqrt(c.mA / nud64), fB = sqrt(c.mB / nud64);
+  const double fA = nrm ? 1.0 : sqrt(c.mA / nud64), fB = nrm ? 1.0 : sqrt(c.mB / nud64);
   double aA[R], aB[R], Lc[RP], Li[R];
 #pragma unroll
   for (int t = 0; t < R; ++t) {
@@ -834,8 +842,8 @@ __device__ void pair_sweep_log_cta(const EArgs &a, const FitView &fv, const Comp
     if (!DENS) {
       const double logTB = gB + log(tot[2]) - log((double)N);
       const bool ok = isfinite(logTA) && isfinite(logTB);
-      const double e1 = ok ? c.mA / nud64 * exp(logTB - logTA) : 0.0;
-      const double sig = sqrt(nud64 / c.mB);
+      const double e1 = ok ? (nrm ? 1.0 : c.mA / nud64) * exp(logTB - logTA) : 0.0;
+      const double sig = nrm ? 1.0 : sqrt(nud64 / c.mB);
       const double iSB = ok ? 1.0 / tot[2] : 0.0;
       double LEV[R];
       for (int t = 0; t < R; ++t) {
@@ -844,7 +852,9 @@ __device__ void pair_sweep_log_cta(const EArgs &a, const FitView &fv, const Comp
         LEV[t] = sacc;
       }
       double e2;
-      if (e2lat)
+      if (nrm)
+        e2 = 0.0;
+      else if (e2lat)
         e2 = ok ? tot[1] / tot[0] - log(nud64) : 0.0;
       else
         e2 = ok ? e1 - (log(0.5 * nud64) + c.mA / nud64 - c.psiA) : 0.0;
@@ -874,12 +884,12 @@ __device__ void rescue_one(const EArgs &a, const FitView &fv, const CompT<double
   if (threadIdx.x == 0) {
     skip = 0;
     if (a.triage) {
-      // tau_ij < exp(-30) when log pi_i + ub_ij trails the best component by 30
+      // tau_ij < exp(-tnats) when log pi_i + ub_ij trails the best component by tnats
       const float *lf = reinterpret_cast<const float *>(fv.out.logf);
       double best = -INFINITY;
       for (int h = 0; h < fv.g; ++h) best = fmax(best, log(fv.pi[h]) + (double)lf[(int64_t)h * fv.n + j]);
       const double mine = log(fv.pi[i]) + (double)lf[(int64_t)i * fv.n + j];
-      if (isfinite(best) && mine < best - 30.0) {
+      if (isfinite(best) && mine < best - (double)a.tnats) {
         skip = 1;
         const int64_t ij = (int64_t)i * fv.n + j;
         const int RP = R * (R + 1) / 2;
@@ -1171,6 +1181,7 @@ cudaError_t launch_estep_batched(int precision, const BatchDev &b, int p, int r,
   a.rescue_count = rescue_count;
   a.status = d_status;
   a.triage = triage ? 1 : 0;
+  a.tnats = 30.f;
   if (precision == CFUST_FP64) {
     a.comp = c64;
     a.chi = chi64;
@@ -1217,10 +1228,13 @@ cudaError_t launch_list_r3(EArgs a, int g, int64_t n, const int *list, const uns
   // 16 listed pairs per warp chunk: their FP64 prologues and triage tests run
   // lane-parallel, which matters at the small lattices this path serves
   a.ppw = 16;
-  // the list lengths live on the device: size the grid for a full list but
-  // cap it near four waves of two CTAs per SM; blocks past the end return
+  // the list lengths live on the device: size every component's column of
+  // the grid for a full list, capped near four waves of two CTAs per SM;
+  // blocks past the end of their list return at once.  The lists are often
+  // lopsided (one component's far tail can hold most listed pairs), so each
+  // column gets the whole cap rather than a 1/g share of it
   const int64_t need = (n + 8 * a.ppw - 1) / (8 * a.ppw);
-  const int64_t cap = (152 * 2 * 4 + g - 1) / g;
+  const int64_t cap = 152 * 2 * 4;
   const int64_t bx = need < cap ? need : cap;
   e = cudaMemsetAsync(a.rescue_count, 0, sizeof(unsigned), st);
   if (e != cudaSuccess) return e;
@@ -1233,7 +1247,7 @@ cudaError_t launch_list_r3(EArgs a, int g, int64_t n, const int *list, const uns
 
 EArgs make_args(const double *Y, int64_t n, int g, int p, const LatticeDev &lat, EstepOut out, int e2_mode,
                 unsigned long long *rescue_list, unsigned *rescue_count, int *d_status, int triage,
-                const double *d_pi) {
+                const double *d_pi, float tnats) {
   EArgs a;
   a.Y = Y;
   a.n = n;
@@ -1255,6 +1269,7 @@ EArgs make_args(const double *Y, int64_t n, int g, int p, const LatticeDev &lat,
   a.rescue_count = rescue_count;
   a.status = d_status;
   a.triage = (triage && out.logf != nullptr) ? 1 : 0;
+  a.tnats = tnats;
   a.pi = d_pi;
   a.comp = nullptr;
   a.chi = nullptr;
@@ -1266,10 +1281,10 @@ cudaError_t launch_estep_list(const double *Y, int64_t n, int g, int p, int r, c
                               const float *chi32, EstepOut out, bool density_only, int e2_mode,
                               const int *list, const unsigned *count, unsigned long long *rescue_list,
                               unsigned *rescue_count, int *d_status, cudaStream_t st, int triage,
-                              const double *d_pi) {
+                              const double *d_pi, float tnats) {
   if (n <= 0) return cudaSuccess;
   if (r != 3) return cudaErrorInvalidValue;
-  EArgs a = make_args(Y, n, g, p, lat, out, e2_mode, rescue_list, rescue_count, d_status, triage, d_pi);
+  EArgs a = make_args(Y, n, g, p, lat, out, e2_mode, rescue_list, rescue_count, d_status, triage, d_pi, tnats);
   a.comp = c32;
   a.chi = chi32;
   return density_only ? launch_list_r3<true>(a, g, n, list, count, c64, chi64, st)
@@ -1287,9 +1302,9 @@ cudaError_t launch_estep(int precision, const double *Y, int64_t n, int g, int p
                          const double *chi64, const float *chi32, EstepOut out, bool density_only,
                          int e2_mode, unsigned long long *rescue_list, unsigned *rescue_count, int *d_status,
                          int pairs_per_warp, cudaStream_t st, SweepTiming tm, int triage,
-                         const double *d_pi) {
+                         const double *d_pi, float tnats) {
   if (n <= 0) return cudaSuccess;
-  EArgs a = make_args(Y, n, g, p, lat, out, e2_mode, rescue_list, rescue_count, d_status, triage, d_pi);
+  EArgs a = make_args(Y, n, g, p, lat, out, e2_mode, rescue_list, rescue_count, d_status, triage, d_pi, tnats);
   if (pairs_per_warp <= 0) {
     // about sixteen waves of two resident CTAs per SM (8 warps each), so the
     // last wave's imbalance stays small; 1..32 pairs per warp (measured best

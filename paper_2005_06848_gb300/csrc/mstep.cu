@@ -619,6 +619,8 @@ __device__ void mstep_finalize_block(const double *partials, int nb, int g, int 
   if (threadIdx.x == 0) nu_go = mstep_update_thread0(S, red[0], g, p, r, n, params, status, i, &nu_c) ? 1 : 0;
   __syncthreads();
   if (!nu_go) return;
+  // nu = inf selects the skew-normal limit, a model choice the update keeps
+  if (isinf(param_view(params, g, p, r).nu[i])) return;
   const double nu = solve_nu_block(nu_c, nu_min, nu_max);
   if (threadIdx.x == 0) param_view(params, g, p, r).nu[i] = nu;
 }

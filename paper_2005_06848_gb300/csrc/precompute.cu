@@ -58,7 +58,8 @@ __device__ void precompute_component(const double *params, int g, int p, int r, 
     const int k = kk < N ? kk : kk - N;
     const double u0 = lattice_coord(k, lat.z[0], N, lat.shift[0]);
     const double m = nu + p + (kk < N ? 0.0 : 2.0);
-    const double sc = sqrt(2.0 * inc_gamma_inv(0.5 * m, u0) / m);
+    // nu = inf (the skew-normal limit): chi^2_m / m -> 1
+    const double sc = isinf(nu) ? 1.0 : sqrt(2.0 * inc_gamma_inv(0.5 * m, u0) / m);
     t64[kk] = sc;
     t32[kk] = (float)sc;
   }
@@ -116,8 +117,11 @@ __device__ void precompute_component(const double *params, int g, int p, int r, 
     return;
   }
   const double pi_c = 3.14159265358979323846;
-  const double c0 = r * 0.69314718055994530942 + lgamma(0.5 * (nu + p)) - lgamma(0.5 * nu) -
-                    0.5 * p * log(nu * pi_c) - 0.5 * logdet;
+  // log of 2^r times the normalising constant of t_p(.; mu, Omega, nu); at
+  // nu = inf that of the normal density phi_p, (2 pi)^{-p/2} |Omega|^{-1/2}
+  const double c0 = isinf(nu) ? r * 0.69314718055994530942 - 0.5 * p * log(2.0 * pi_c) - 0.5 * logdet
+                              : r * 0.69314718055994530942 + lgamma(0.5 * (nu + p)) - lgamma(0.5 * nu) -
+                                    0.5 * p * log(nu * pi_c) - 0.5 * logdet;
 
   CompT<double> &o = *o_out;
   CompT<float> &f = *f_out;
@@ -138,13 +142,14 @@ __device__ void precompute_component(const double *params, int g, int p, int r, 
     o.Linv[t] = li;
     f.Linv[t] = (float)li;
   }
-  const double psiA = digamma(0.5 * (nu + p));
+  // psi((nu+p)/2) and log(nu+p) enter e2 only, which is 0 at nu = inf
+  const double psiA = isinf(nu) ? 0.0 : digamma(0.5 * (nu + p));
   o.c0 = f.c0 = c0;
   o.nu = f.nu = nu;
   o.mA = f.mA = nu + p;
   o.mB = f.mB = nu + p + 2.0;
   o.psiA = f.psiA = psiA;
-  o.logmA = f.logmA = log(nu + p);
+  o.logmA = f.logmA = isinf(nu) ? 0.0 : log(nu + p);
   for (int a = 0; a < PMAX; ++a) o.fmu[a] = f.fmu[a] = (float)o.mu[a];
   for (int a = 0; a < PMAX * PMAX; ++a) o.fA[a] = f.fA[a] = (float)o.A[a];
   for (int a = 0; a < RMAX * PMAX; ++a) o.fB[a] = f.fB[a] = (float)o.B[a];

@@ -22,7 +22,7 @@ import numpy as np
 __all__ = [
     "Params", "Lattice", "splitmix64_stream", "korobov_generator",
     "make_lattice", "sample_cfust", "perturb_params", "random_params",
-    "workload", "WORKLOADS", "batched_workload",
+    "workload", "WORKLOADS", "batched_workload", "random_partitions", "initial_centres",
 ]
 
 
@@ -281,3 +281,17 @@ def batched_workload(nfits: int = 256, seed0: int = 0, n_lo: int = 5000, n_hi: i
         truths.append(truth)
         inits.append(perturb_params(truth, rng))
     return Ys, truths, inits
+
+
+def random_partitions(n: int, g: int, m: int, seed: int = 0) -> np.ndarray:
+    """m seeded random partitions of n observations into g groups (Algorithm 1's
+    random initial partitions): int32 [m, n], labels uniform on 0..g-1."""
+    rng = np.random.default_rng(seed)
+    return np.ascontiguousarray(rng.integers(0, g, size=(m, n)).astype(np.int32))
+
+
+def initial_centres(Y: np.ndarray, g: int, m: int, seed: int = 0) -> np.ndarray:
+    """m seeded sets of k-means starting centres: g distinct observations each,
+    float64 [m, g, p]."""
+    rng = np.random.default_rng(seed)
+    return np.stack([Y[rng.choice(Y.shape[0], size=g, replace=False)] for _ in range(m)]).astype(np.float64)

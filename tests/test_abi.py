@@ -53,6 +53,12 @@ def test_create_rejects_bad_lattice_without_a_device():
     h = ctypes.c_void_p()
     st = lib.cfust_create(ctypes.byref(h), ctypes.byref(opts), None)
     assert st in (-1, -6)   # -6 when no device is visible (checked first on some hosts)
+    good = binding.cfust_lattice(1024, 3, z.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)),
+                                 sh.ctypes.data_as(ctypes.POINTER(ctypes.c_double)))
+    for nats in (0.5, -1.0, 701.0, float("nan")):
+        opts = binding.cfust_opts(1, good, 0, 0.0, 0.0, 5, 0.0, 1, 0, 0, 0, nats)
+        st = lib.cfust_create(ctypes.byref(h), ctypes.byref(opts), None)
+        assert st == -1 and b"triage_nats" in lib.cfust_last_error(None), nats
 
 
 def test_unpack_e4_round_trip():

@@ -179,6 +179,58 @@ def test_loglik_matches_oracle_fp64():
     assert abs(got - ref) <= 1e-10 * abs(ref)
 
 
+@pytest.mark.parametrize("precision", [binding.CFUST_FP64, binding.CFUST_FP32])
+def test_skew_normal_limit_matches_oracle(precision):
+    """A mixture with one component in the skew-normal limit (nu = inf) beside
+    skew t components: every E-step output against the oracle (the limit's
+    e1 = 1 and e2 = 0 exactly), and the M-step keeps nu = inf."""
+    import math
+    torch = _torch()
+    Y, truth, init, lat = _problem("cfust_p3r3g4_n1000000_N2048", 150, 1024)
+    P = init.copy()
+    P.nu[1] = math.inf
+    R = _oracle_estep(Y, P, lat)
+    G = _gpu_estep(Y, P, lat, precision)
+    _compare_estep(G, R, P.r, precision == binding.CFUST_FP64)
+    live = R["tau"][1] > 0
+    assert np.all(G["e1"][1][live] == 1.0) and np.all(G["e2"][1][live] == 0.0)
+    if precision == binding.CFUST_FP64:
+        ref = O.mstep_update(O.mstep_sums(Y, R["tau"], R["e1"], R["e2"], R["e3"], R["e4"]), P, Y.shape[0])
+        r = P.r
+        dev = lambda a: torch.from_numpy(np.ascontiguousarray(a)).cuda()
+        E = dict(tau=dev(R["tau"]), e1=dev(R["e1"]), e2=dev(R["e2"]),
+                 e3=dev(np.transpose(R["e3"], (0, 2, 1))),
+                 e4=dev(np.stack([R["e4"][:, :, t, h] for t in range(r) for h in range(t + 1)], axis=1)))
+        with binding.Context(lat, precision=binding.CFUST_FP64) as ctx:
+            got = ctx.cfust_mstep(dev(Y), E, P)
+        assert math.isinf(got.nu[1]) and math.isinf(ref.nu[1])
+        for a, b, name in zip(got.as_arrays(), ref.as_arrays(), ("pi", "mu", "Sigma", "Delta", "nu")):
+            _cmp(name, a, b, 1e-10)
+
+
+def test_loglik_shifts_match_oracle_and_restore_the_rule():
+    """l(Psi) under three shifted copies of the lattice (randomised QMC error
+    estimate) against the oracle at each shifted rule; the context's own
+    rule is back afterwards (bitwise), also after a rejected shift."""
+    torch = _torch()
+    Y, truth, init, lat = _problem("cfust_p3r3g4_n1000000_N2048", 130, 256)
+    shifts = np.stack([synth.make_lattice(lat.n, 4, s).shift for s in (3, 4, 5)])
+    Yd = torch.from_numpy(Y).cuda()
+    with binding.Context(lat, precision=binding.CFUST_FP64) as ctx:
+        before = ctx.cfust_loglik(Yd, init)
+        got = ctx.cfust_loglik_shifts(Yd, init, shifts)
+        assert ctx.cfust_loglik(Yd, init) == before
+        bad = shifts.copy()
+        bad[1, 2] = 1.0
+        with pytest.raises(binding.CfustError):
+            ctx.cfust_loglik_shifts(Yd, init, bad)
+        assert ctx.cfust_loglik(Yd, init) == before
+    for m in range(shifts.shape[0]):
+        ref = O.loglik(Y, init, O.lattice_points(lat.n, lat.z, shifts[m]))
+        assert abs(got[m] - ref) <= 1e-10 * abs(ref), (m, got[m], ref)
+    assert np.std(got) > 0
+
+
 def test_mstep_matches_oracle_fp64():
     torch = _torch()
     Y, truth, init, lat = _problem("cfust_p4r4g3_n100000_N4096", 300, 1024)

@@ -275,6 +275,24 @@ def test_surrogate_gain_at_equal_loglik_accuracy(trained):
     print("surrogate gain report", report)
 
 
+def test_triage_margin_bounds_the_loglik_change(trained):
+    """A triage margin of 12 nats instead of 30: every listed pair the lattice
+    sweep then skips has tau_ij < exp(-12) by a proven upper bound of its
+    density, so l moves by at most (listed pairs) x exp(-12)."""
+    torch = _torch()
+    Y, _, truth, init, _, _ = synth.workload("cfust_p3r3g4_n1000000_N2048", n=200_000, seed=0)
+    Yd = torch.tensor(Y, dtype=torch.float64, device="cuda")
+    lat = synth.make_lattice(128, 4, seed=0)
+    ls, listed = {}, {}
+    for T in (30.0, 12.0):
+        with binding.Context(lat, precision=binding.CFUST_FP32, triage_nats=T) as c:
+            c.cfust_set_surrogate(trained)
+            ls[T] = c.cfust_loglik(Yd, init)
+            listed[T] = c.cfust_last_fallback()
+    assert listed[30.0] == listed[12.0] > 0
+    assert abs(ls[12.0] - ls[30.0]) <= listed[12.0] * math.exp(-12.0), (ls, listed)
+
+
 def test_surrogate_edge_cases(lat8192):
     """Attachment rules: FP64 contexts and r != 3 are refused when the E-step
     runs; a mixture whose dof leave the network's domain (nu + p + 2 > 30)

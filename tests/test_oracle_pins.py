@@ -112,6 +112,25 @@ def test_orthant_probabilities_r2_r3():
             assert abs(T[0] - ex) < 2e-5
 
 
+def test_random_shifts_give_an_unbiased_rule_and_an_honest_error_estimate():
+    """Randomised QMC: with independent uniform shifts the lattice estimate of
+    an orthant probability (closed form: 1/4 + asin(rho)/(2 pi)) is unbiased
+    and the spread over shifts bounds its error: over 120 shifts of a small
+    64-point rule the mean lies within 4 standard errors of the exact value,
+    while single shifts do miss it by more than their own standard error."""
+    rng = np.random.default_rng(7)
+    Lam = np.array([[1.0, 0.6], [0.6, 1.0]])
+    ex = 0.25 + math.asin(0.6) / (2 * math.pi)
+    z = synth.make_lattice(64, 3, 0).z
+    L = np.linalg.cholesky(Lam)
+    Ts = np.array([O.sov_pass(np.zeros((1, 2)), L, 6.0, O.lattice_points(64, z, rng.uniform(size=3)), False)[0]
+                   for _ in range(120)])
+    se = Ts.std(ddof=1) / math.sqrt(Ts.size)
+    assert se > 0
+    assert abs(Ts.mean() - ex) <= 4 * se, (Ts.mean(), ex, se)
+    assert np.max(np.abs(Ts - ex)) > se
+
+
 @pytest.mark.parametrize("r", [2, 3, 4])
 def test_identity_lambda_zero_limit_half_t_moments(r):
     """Lambda = I, a = 0: every point has weight 2^-r, so T is exact; the moments
@@ -381,3 +400,93 @@ def test_aitken_exact_on_geometric_sequence():
 
 def test_select_start_largest_first_on_ties():
     assert O.select_start([-10.0, -3.0, -5.0, -3.0]) == 1
+
+
+# --------------------------------------------------------------------------- skew-normal limit (nu = inf)
+
+def _sn_case(rng, p, r):
+    A = rng.standard_normal((p, p))
+    Sigma = A @ A.T / p + 0.5 * np.eye(p)
+    Delta = rng.uniform(-1.2, 1.2, (p, r))
+    mu = rng.standard_normal(p)
+    return mu, Sigma, Delta
+
+
+def test_skew_normal_limit_r1_matches_the_closed_form():
+    """nu = inf, r = 1: f(y) = 2 phi_p(y; mu, Omega) Phi(q / sqrt(Lambda)), the
+    multivariate skew-normal density (Azzalini & Dalla Valle), exact on the
+    lattice (with s = 1 every point has the same weight); U | y is N(q, Lambda)
+    truncated to U > 0, whose moments scipy's truncnorm gives; W = 1."""
+    rng = np.random.default_rng(11)
+    p = 3
+    mu, Sigma, Delta = _sn_case(rng, p, 1)
+    Y = mu + rng.standard_normal((40, p)) * 1.5
+    out = O.estep_component(Y, mu, Sigma, Delta, math.inf, _U(1 << 14, 2, 1))
+    coarse = O.estep_component(Y, mu, Sigma, Delta, math.inf, _U(1024, 2, 1))
+    Omega = Sigma + Delta @ Delta.T
+    Oinv = np.linalg.inv(Omega)
+    q = (Y - mu) @ Oinv @ Delta[:, 0]
+    lam = 1.0 - Delta[:, 0] @ Oinv @ Delta[:, 0]
+    ref = (math.log(2.0) + stats.multivariate_normal(mu, Omega).logpdf(Y)
+           + stats.norm.logcdf(q / math.sqrt(lam)))
+    assert np.allclose(out["logf"], ref, rtol=0, atol=1e-11)
+    assert np.all(out["e1"] == 1.0) and np.all(out["e2"] == 0.0)
+    sd = math.sqrt(lam)
+    tn = stats.truncnorm(-q / sd, np.inf, loc=q, scale=sd)
+    # the lattice moments converge (the draw -Phi^-1((1-u)p) is unbounded as
+    # u -> 1, so slowly; the second moment more so): at 16384 points ten times
+    # closer than at 1024, within 1e-5 (mean) and 5e-5 (second moment)
+    for k, ex, tol in (("e3", tn.mean(), 1e-5), ("e4", tn.moment(2), 5e-5)):
+        fine = np.abs(out[k].reshape(len(Y)) - ex).max()
+        rough = np.abs(coarse[k].reshape(len(Y)) - ex).max()
+        assert 10 * fine < rough and fine < tol * max(1.0, np.abs(ex).max()), (k, fine, rough)
+
+
+def test_skew_normal_is_the_large_nu_limit():
+    """nu = inf against nu = 1e8 (the law differs by O(1/sqrt(nu)) in the chi
+    scale and O(1/nu) elsewhere): p = 3, r = 2, every output."""
+    rng = np.random.default_rng(12)
+    mu, Sigma, Delta = _sn_case(rng, 3, 2)
+    Y = mu + rng.standard_normal((30, 3)) * 1.5
+    U = _U(2048, 3, 4)
+    a = O.estep_component(Y, mu, Sigma, Delta, math.inf, U)
+    b = O.estep_component(Y, mu, Sigma, Delta, 1e8, U)
+    assert np.allclose(a["logf"], b["logf"], rtol=0, atol=2e-3)
+    for k in ("e1", "e3", "e4"):
+        assert np.allclose(a[k], b[k], rtol=2e-3, atol=2e-3), k
+    assert np.allclose(b["e2"], 0.0, atol=2e-3)
+
+
+def test_skew_normal_density_integrates_to_one_p1():
+    mu, Sigma, Delta = np.array([0.2]), np.array([[0.8]]), np.array([[1.3, -0.8]])
+    x, wq = np.polynomial.legendre.leggauss(400)
+    th = 0.5 * math.pi * x * (1 - 1e-12)
+    c = 2.0
+    Y = (mu + c * np.tan(th))[:, None]
+    jac = c / np.cos(th) ** 2 * 0.5 * math.pi
+    out = O.estep_component(Y, mu, Sigma, Delta, math.inf, _U(1 << 14, 3, 2), density_only=True)
+    assert abs(np.sum(wq * jac * np.exp(out["logf"])) - 1.0) < 2e-5
+
+
+def test_skew_normal_delta_zero_is_the_gaussian_mixture_update():
+    """nu = inf and Delta = 0: the E-step is the Gaussian mixture's (e1 = 1) and
+    the M-step the textbook weighted mean and covariance; nu stays inf."""
+    Y, _, _, init, lat, _ = synth.workload("cfust_p2r2g2_n2000_N1024", n=200)
+    U = O.lattice_points(lat.n, lat.z, lat.shift)
+    P = init.copy()
+    P.Delta[:] = 0.0
+    P.nu[:] = math.inf
+    E = O.estep(Y, P, U)
+    for i in range(P.g):
+        ref = stats.multivariate_normal(P.mu[i], P.Sigma[i]).logpdf(Y)
+        assert np.allclose(E["logf"][i], ref + P.r * math.log(2.0) + P.r * math.log(0.5), atol=1e-12)
+    new = O.mstep_update(O.mstep_sums(Y, E["tau"], E["e1"], E["e2"], E["e3"], E["e4"]),
+                         P, Y.shape[0], fix_delta=True)
+    for i in range(P.g):
+        t = E["tau"][i]
+        mu = (t[:, None] * Y).sum(0) / t.sum()
+        dy = Y - mu
+        Sig = (t[:, None, None] * dy[:, :, None] * dy[:, None, :]).sum(0) / t.sum()
+        assert np.allclose(new.mu[i], mu, rtol=1e-12)
+        assert np.allclose(new.Sigma[i], Sig, rtol=1e-11)
+        assert math.isinf(new.nu[i])
