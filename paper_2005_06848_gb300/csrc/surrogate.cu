@@ -540,6 +540,18 @@ static_assert(sizeof(WarpScratch) % 16 == 0, "scratch blocks must stay 16-byte a
 
 __device__ __forceinline__ uint32_t ld32(const bf16 *p) { return *reinterpret_cast<const uint32_t *>(p); }
 
+// Four 8x8 bf16 matrices from shared memory in one instruction; lane l gives
+// the address of row (l & 7) of matrix (l >> 3) (16-byte aligned) and receives
+// row l / 4, columns 2 (l % 4) and 2 (l % 4) + 1 of each matrix.  With the
+// weights stored [out][in], matrices (n-tile, k 0..7), (n-tile, k 8..15) are
+// exactly the two B registers of an m16n8k16 MMA for that n-tile.
+__device__ __forceinline__ void ldsm_x4(uint32_t (&r)[4], const bf16 *p) {
+  const unsigned a = (unsigned)__cvta_generic_to_shared(p);
+  asm volatile("ldmatrix.sync.aligned.m8n8.x4.shared.b16 {%0, %1, %2, %3}, [%4];\n"
+               : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3])
+               : "r"(a));
+}
+
 __device__ __forceinline__ uint32_t pack_bf16x2(float lo, float hi) {
   const __nv_bfloat162 v = __floats2bfloat162_rn(lo, hi);
   return *reinterpret_cast<const uint32_t *>(&v);
@@ -559,13 +571,18 @@ __device__ __forceinline__ void dense_gelu(const uint32_t (&in)[KT][4], const bf
     for (int nt = 0; nt < 8; ++nt)
 #pragma unroll
       for (int c = 0; c < 4; ++c) acc[nt][c] = 0.f;
+    // this lane's ldmatrix row: n-tile nt + (l >> 4), row l & 7, k half (l >> 3) & 1
+    const int lane = (gid << 2) | tig;
+    const bf16 *wl = Wt + (((lane >> 4) * 8 + (lane & 7)) * wp + ((lane >> 3) & 1) * 8);
 #pragma unroll
     for (int kt = 0; kt < KT; ++kt)
 #pragma unroll
-      for (int nt = 0; nt < 8; ++nt) {
-        const bf16 *c0 = Wt + ((half * 8 + nt) * 8 + gid) * wp + kt * 16 + tig * 2;
-        const uint32_t b[2] = {ld32(c0), ld32(c0 + 8)};
-        mma_bf16(acc[nt], in[kt], b);
+      for (int nt = 0; nt < 8; nt += 2) {
+        uint32_t b4[4];
+        ldsm_x4(b4, wl + (half * 8 + nt) * 8 * wp + kt * 16);
+        const uint32_t b0[2] = {b4[0], b4[1]}, b1[2] = {b4[2], b4[3]};
+        mma_bf16(acc[nt], in[kt], b0);
+        mma_bf16(acc[nt + 1], in[kt], b1);
       }
     // columns 16 q .. 16 q + 15 (n-tiles 2q and 2q + 1) form k-tile q of the
     // next layer: (row gid | gid + 8) x (k 2 tig, 2 tig + 1 | + 8); each
@@ -792,14 +809,16 @@ __global__ void __launch_bounds__(WARPS * 32, 1)
       for (int a = 0; a < 2; ++a)
 #pragma unroll
         for (int b = 0; b < 4; ++b) o[a][b] = 0.f;
+      const int lane = (gid << 2) | tig;
+      const bf16 *wl = Wsm.W4t + (((lane >> 4) * 8 + (lane & 7)) * HP + ((lane >> 3) & 1) * 8);
 #pragma unroll
-      for (int kt = 0; kt < 8; ++kt)
-#pragma unroll
-        for (int nt = 0; nt < 2; ++nt) {
-          const bf16 *c0 = Wsm.W4t + (nt * 8 + gid) * HP + kt * 16 + tig * 2;
-          const uint32_t b[2] = {ld32(c0), ld32(c0 + 8)};
-          mma_bf16(o[nt], h1[kt], b);
-        }
+      for (int kt = 0; kt < 8; ++kt) {
+        uint32_t b4[4];
+        ldsm_x4(b4, wl + kt * 16);
+        const uint32_t b0[2] = {b4[0], b4[1]}, b1[2] = {b4[2], b4[3]};
+        mma_bf16(o[0], h1[kt], b0);
+        mma_bf16(o[1], h1[kt], b1);
+      }
 #pragma unroll
       for (int nt = 0; nt < 2; ++nt) {
         const int col = nt * 8 + tig * 2;
