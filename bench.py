@@ -4,8 +4,10 @@
 One step = one EM iteration (Section 2 outline, Algorithms 2 and 3) on the
 synthetic workload p=4, r=4, g=3, n=100000 with a 4096-point lattice: the
 per-component precompute, the E-step lattice sweeps over all n*g pairs
-(single precision, double-precision prologue), the posterior / log-likelihood
-/ M-step sums in double, and the conditional-maximisation update, replayed
+(single precision, double-precision prologue), the posterior, the
+log-likelihood and the M-step sums (double-precision accuracy; in the
+single-precision mode as double-float arithmetic on the FP32 pipe), and the
+conditional-maximisation update, replayed
 from one CUDA graph.  Inputs are resident in HBM before timing; L2 is
 flushed (a 256 MiB write) between timed steps.  Throughput is E-step pairs
 (observation x component) per second over the whole job; EM iterations per

@@ -57,10 +57,10 @@ typedef int cfust_status;
 #define CFUST_ENOMEM      -7   /* device allocation failed */
 
 #define CFUST_FP64 0   /* every step in double precision (parity mode) */
-#define CFUST_FP32 1   /* lattice sweeps, posterior exponentials and the M-step sums' products in float
-                          (each 64-observation tile's products summed with two-sum compensation,
-                          tile totals in double); factorisations, per-pair prologue, log-sum-exp,
-                          log-likelihood and the conditional-maximisation update in double */
+#define CFUST_FP32 1   /* lattice sweeps and posterior exponentials in float; the M-step sums to
+                          double accuracy as double-float arithmetic (exact products, two-sum
+                          compensated tile sums, tile totals in double); factorisations, per-pair
+                          prologue, log-sum-exp, log-likelihood and the update in double */
 
 /* Mixture parameters Psi = (pi_1..pi_g, theta_1..theta_g), theta_i = (mu_i, Sigma_i, Delta_i, nu_i)
  * (Section 2).  Host memory, row-major:

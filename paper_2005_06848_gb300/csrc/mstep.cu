@@ -53,26 +53,43 @@ __device__ inline void entry_desc(int ent, int p, int r, int *w, int *y1, int *y
   *w = 2 + r + rp;                                  // S8
 }
 
-// hi + lo += x with Knuth's two-sum: the rounding error of hi + x is exact in
-// single precision and goes to lo (the _rn intrinsics keep the compiler from
-// fusing or reordering the steps).
-__device__ __forceinline__ void two_sum_acc(float &hi, float &lo, float x) {
-  const float s = __fadd_rn(hi, x);
+// Double-float numbers (hi + lo, two floats): products formed exactly by
+// Dekker's two-product (hi = fl(a b), lo = fma(a, b, -hi) is the exact rest),
+// cross terms of a double-float product in single precision (their own error
+// is of order 2^-48 of the product).
+__device__ __forceinline__ float2 two_prod(float a, float b) {
+  const float p = __fmul_rn(a, b);
+  return make_float2(p, __fmaf_rn(a, b, -p));
+}
+__device__ __forceinline__ float2 df_mul(float2 x, float2 y) {
+  const float p = __fmul_rn(x.x, y.x);
+  float e = __fmaf_rn(x.x, y.x, -p);
+  e = __fmaf_rn(x.x, y.y, e);
+  e = __fmaf_rn(x.y, y.x, e);
+  return make_float2(p, e);
+}
+// hi + lo += v.x + v.y (two-sum on the leading parts, the rests added to lo)
+__device__ __forceinline__ void df_acc(float &hi, float &lo, float2 v) {
+  const float s = __fadd_rn(hi, v.x);
   const float bp = __fsub_rn(s, hi);
-  const float err = __fadd_rn(__fsub_rn(hi, __fsub_rn(s, bp)), __fsub_rn(x, bp));
+  const float err = __fadd_rn(__fsub_rn(hi, __fsub_rn(s, bp)), __fsub_rn(v.x, bp));
   hi = s;
-  lo = __fadd_rn(lo, err);
+  lo = __fadd_rn(lo, __fadd_rn(err, v.y));
 }
 
 // Single-precision E-step outputs (CFUST_FP32).  Double-precision work costs
-// 64 times single-precision work on this GPU, so only what needs it stays
-// double: log pi_i + log f_ij, its maximum and the differences (the
-// exponents of the log-sum-exp), l_j = max + log s_j and its sum, and the
-// per-tile totals of the sums.  The exponentials, tau (to 1e-7 relative,
-// the level of the single-precision log f_ij it comes from), the products
-// tau e y of the sums (each rounded once per factor, as are its inputs) and
-// their sums within a tile (two-sum compensated: exact up to O(64 u^2)) are
-// single precision.
+// 64 times single-precision work on this GPU, so the double-precision parts
+// run as double-float arithmetic on the single-precision pipe where they are
+// bulk work: the M-step sums take the exact products of the single-precision
+// tau, e1..e4 and the double-precision observations (y split into two
+// floats), summed within a 64-observation tile with two-sum compensation
+// (about 2^-42 of the sum of |terms| per tile) and across tiles in double:
+// double-precision sums of the same inputs up to ~1e-13.  Native double
+// precision keeps log pi_i + log f_ij, its maximum and the differences (the
+// log-sum-exp's exponents), and l_j = max + log s_j with its sum over the
+// observations; the exponentials and tau are single precision (tau to 1e-7
+// relative, the level of the single-precision log f_ij it comes from), and
+// so is log s_j (s_j in [1, g]: 1e-7 absolute).
 __device__ __forceinline__ void posterior_block_f32(const PosteriorArgs &a, int c0, int c1, int blk, int nblk,
                                                     unsigned char *smem_raw) {
   const int p = a.p, r = a.r, g = a.g;
@@ -81,8 +98,8 @@ __device__ __forceinline__ void posterior_block_f32(const PosteriorArgs &a, int 
   const int WR = 3 + r + rp;
   const int gc = c1 - c0;
   const int64_t n = a.n;
-  float *ys = reinterpret_cast<float *>(smem_raw);  // [TJ][p]
-  float *ws = ys + TJ * p;                          // [gc][TJ][WR]
+  float2 *ys = reinterpret_cast<float2 *>(smem_raw);  // [TJ][p] (hi, lo) of y
+  float2 *ws = ys + TJ * p;                           // [gc][TJ][WR] exact products
   __shared__ double red[THREADS];
 
   const float *lfp = reinterpret_cast<const float *>(a.logf);
@@ -120,7 +137,11 @@ __device__ __forceinline__ void posterior_block_f32(const PosteriorArgs &a, int 
     const int64_t j0 = tile * TJ;
     const int nt = (int)((n - j0) < TJ ? (n - j0) : TJ);
     if (a.want_sums)
-      for (int idx = threadIdx.x; idx < nt * p; idx += THREADS) ys[idx] = (float)a.Y[j0 * p + idx];
+      for (int idx = threadIdx.x; idx < nt * p; idx += THREADS) {
+        const double y = a.Y[j0 * p + idx];
+        const float yh = (float)y;
+        ys[idx] = make_float2(yh, (float)(y - (double)yh));
+      }
     if (threadIdx.x < nt) {
       const int jj = threadIdx.x;
       const int64_t j = j0 + jj;
@@ -132,7 +153,7 @@ __device__ __forceinline__ void posterior_block_f32(const PosteriorArgs &a, int 
           // and its weights are zero so that the sums stay defined
           bad = 1;
           if (a.want_sums)
-            for (int i = c0; i < c1; ++i) ws[((i - c0) * TJ + jj) * WR] = 0.0f;
+            for (int i = c0; i < c1; ++i) ws[((i - c0) * TJ + jj) * WR] = make_float2(0.0f, 0.0f);
           if (tau_out != nullptr && first_chunk)
             for (int i = 0; i < g; ++i) tau_out[(int64_t)i * n + j] = 0.0f;
         } else {
@@ -140,7 +161,7 @@ __device__ __forceinline__ void posterior_block_f32(const PosteriorArgs &a, int 
           for (int i = 0; i < g; ++i) {
             const float ex = expf((float)(lpi[i] + (double)lfp[(int64_t)i * n + j] - mx));
             s = __fadd_rn(s, ex);
-            if (a.want_sums && i >= c0 && i < c1) ws[((i - c0) * TJ + jj) * WR] = ex;
+            if (a.want_sums && i >= c0 && i < c1) ws[((i - c0) * TJ + jj) * WR] = make_float2(ex, 0.0f);
             if (tau_out != nullptr && first_chunk) tau_out[(int64_t)i * n + j] = ex;
           }
           // s is in [1, g]: its single-precision logarithm is good to 1e-7
@@ -150,12 +171,12 @@ __device__ __forceinline__ void posterior_block_f32(const PosteriorArgs &a, int 
           llacc += lse;
           const float inv = 1.0f / s;
           if (a.want_sums)
-            for (int i = c0; i < c1; ++i) ws[((i - c0) * TJ + jj) * WR] *= inv;
+            for (int i = c0; i < c1; ++i) ws[((i - c0) * TJ + jj) * WR].x *= inv;
           if (tau_out != nullptr && first_chunk)
             for (int i = 0; i < g; ++i) tau_out[(int64_t)i * n + j] *= inv;
         }
       } else if (a.want_sums) {
-        for (int i = c0; i < c1; ++i) ws[((i - c0) * TJ + jj) * WR] = tau_in[(int64_t)i * n + j];
+        for (int i = c0; i < c1; ++i) ws[((i - c0) * TJ + jj) * WR] = make_float2(tau_in[(int64_t)i * n + j], 0.0f);
       }
     }
     __syncthreads();
@@ -164,19 +185,26 @@ __device__ __forceinline__ void posterior_block_f32(const PosteriorArgs &a, int 
         const int ic = idx / nt, jj = idx % nt;
         const int i = c0 + ic;
         const int64_t j = j0 + jj;
-        float *row = ws + (ic * TJ + jj) * WR;
-        const float t = row[0];
+        float2 *row = ws + (ic * TJ + jj) * WR;
+        const float t = row[0].x;
         const float v1 = e1[(int64_t)i * n + j];
-        row[1] = __fmul_rn(t, v1);
-        for (int q = 0; q < r; ++q) row[2 + q] = __fmul_rn(t, e3[((int64_t)i * r + q) * n + j]);
-        for (int q = 0; q < rp; ++q) row[2 + r + q] = __fmul_rn(t, e4[((int64_t)i * rp + q) * n + j]);
-        row[2 + r + rp] = __fmul_rn(t, __fsub_rn(e2[(int64_t)i * n + j], v1));
+        row[1] = two_prod(t, v1);
+        for (int q = 0; q < r; ++q) row[2 + q] = two_prod(t, e3[((int64_t)i * r + q) * n + j]);
+        for (int q = 0; q < rp; ++q) row[2 + r + q] = two_prod(t, e4[((int64_t)i * rp + q) * n + j]);
+        // e2 - e1 as an exact float pair (two-sum), then times tau
+        const float v2 = e2[(int64_t)i * n + j];
+        const float d = __fsub_rn(v2, v1);
+        const float bp = __fsub_rn(d, v2);
+        const float dlo = __fadd_rn(__fsub_rn(v2, __fsub_rn(d, bp)), __fsub_rn(-v1, bp));
+        float2 pd = two_prod(t, d);
+        pd.y = __fmaf_rn(t, dlo, pd.y);
+        row[2 + r + rp] = pd;
       }
       __syncthreads();
 #pragma unroll
       for (int k = 0; k < MAXOWN; ++k) {
         if (own_c[k] >= 0) {
-          const float *col = ws + own_c[k] * TJ * WR + own_w[k];
+          const float2 *col = ws + own_c[k] * TJ * WR + own_w[k];
           const int y1 = own_y1[k], y2 = own_y2[k];
           // two compensated chains (even and odd rows) for instruction-level
           // parallelism, merged by a further two-sum
@@ -184,27 +212,25 @@ __device__ __forceinline__ void posterior_block_f32(const PosteriorArgs &a, int 
           int jj = 0;
           if (y1 < 0) {
             for (; jj + 2 <= nt; jj += 2) {
-              two_sum_acc(h0, l0, col[jj * WR]);
-              two_sum_acc(h1, l1, col[(jj + 1) * WR]);
+              df_acc(h0, l0, col[jj * WR]);
+              df_acc(h1, l1, col[(jj + 1) * WR]);
             }
-            if (jj < nt) two_sum_acc(h0, l0, col[jj * WR]);
+            if (jj < nt) df_acc(h0, l0, col[jj * WR]);
           } else if (y2 < 0) {
             for (; jj + 2 <= nt; jj += 2) {
-              two_sum_acc(h0, l0, __fmul_rn(col[jj * WR], ys[jj * p + y1]));
-              two_sum_acc(h1, l1, __fmul_rn(col[(jj + 1) * WR], ys[(jj + 1) * p + y1]));
+              df_acc(h0, l0, df_mul(col[jj * WR], ys[jj * p + y1]));
+              df_acc(h1, l1, df_mul(col[(jj + 1) * WR], ys[(jj + 1) * p + y1]));
             }
-            if (jj < nt) two_sum_acc(h0, l0, __fmul_rn(col[jj * WR], ys[jj * p + y1]));
+            if (jj < nt) df_acc(h0, l0, df_mul(col[jj * WR], ys[jj * p + y1]));
           } else {
             for (; jj + 2 <= nt; jj += 2) {
-              two_sum_acc(h0, l0, __fmul_rn(__fmul_rn(col[jj * WR], ys[jj * p + y1]), ys[jj * p + y2]));
-              two_sum_acc(h1, l1,
-                          __fmul_rn(__fmul_rn(col[(jj + 1) * WR], ys[(jj + 1) * p + y1]), ys[(jj + 1) * p + y2]));
+              df_acc(h0, l0, df_mul(df_mul(col[jj * WR], ys[jj * p + y1]), ys[jj * p + y2]));
+              df_acc(h1, l1, df_mul(df_mul(col[(jj + 1) * WR], ys[(jj + 1) * p + y1]), ys[(jj + 1) * p + y2]));
             }
-            if (jj < nt)
-              two_sum_acc(h0, l0, __fmul_rn(__fmul_rn(col[jj * WR], ys[jj * p + y1]), ys[jj * p + y2]));
+            if (jj < nt) df_acc(h0, l0, df_mul(df_mul(col[jj * WR], ys[jj * p + y1]), ys[jj * p + y2]));
           }
-          two_sum_acc(h0, l0, h1);
-          acc[k] += (double)h0 + (double)__fadd_rn(l0, l1);
+          df_acc(h0, l0, make_float2(h1, l1));
+          acc[k] += (double)h0 + (double)l0;
         }
       }
     }

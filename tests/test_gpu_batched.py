@@ -53,6 +53,26 @@ def test_batched_fp64_matches_oracle_on_two_fits():
             assert np.allclose(a, b, rtol=1e-8, atol=1e-10)
 
 
+def test_batched_skew_normal_limit_matches_oracle():
+    """Two fits, one with a component in the skew-normal limit (nu = inf):
+    FP64 batched EM against the oracle's fit; nu = inf is kept."""
+    import math
+    torch = _torch()
+    Ys, truths, inits = synth.batched_workload(2, seed0=7, n_lo=800, n_hi=1500, g_hi=3)
+    inits[0].nu[0] = math.inf
+    lat = synth.make_lattice(256, 4, 3)
+    U = O.lattice_points(lat.n, lat.z, lat.shift)
+    with binding.Context(lat, precision=binding.CFUST_FP64, max_iter=2) as ctx:
+        bp, btr, st = ctx.cfust_fit_batched([torch.from_numpy(Y).cuda() for Y in Ys], inits)
+    assert all(s_ == 0 for s_ in st)
+    assert math.isinf(bp[0].nu[0])
+    for f in range(2):
+        ref, ref_tr = O.fit(Ys[f], inits[f], U, 2)
+        assert np.allclose(btr[f], ref_tr, rtol=1e-10, atol=0)
+        for a, b in zip(bp[f].as_arrays(), ref.as_arrays()):
+            assert np.allclose(a, b, rtol=1e-8, atol=1e-10)
+
+
 def test_autotuned_shape_gives_the_same_fits():
     torch = _torch()
     Ys, truths, inits = _small_batch(4, seed0=90)

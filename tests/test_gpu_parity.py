@@ -248,17 +248,17 @@ def test_mstep_matches_oracle_fp64():
 
 
 def test_mstep_matches_oracle_fp32():
-    """Single-precision M-step sums (CFUST_FP32) against the oracle's FP64
+    """Single-precision-mode M-step (CFUST_FP32) against the oracle's FP64
     M-step on the same single-precision tau and e1..e4.
 
-    The kernel rounds each product tau e y to single precision (at most five
-    roundings of 2^-24 per term, relative to the sum of |terms|) and sums a
-    tile's products with two-sum compensation, tile totals in FP64.  Sigma
-    cancels the mean part of S7 (|mu|^2 / sigma^2 of order 10 here), and the
-    nu equation uses 1 + S8/S1, of order 1/nu, so nu's error is ~nu times the
-    sums': 1e-5 for pi, mu, Sigma, Delta and 1e-4 for nu cover both with a
-    margin of ~3.  2000 rows: 32 tiles, spread over many blocks, a ragged
-    last tile (2000 = 31 x 64 + 16).
+    The kernel forms every product tau e y exactly (two-product, y split
+    into two floats) and sums them in double-float within a 64-observation
+    tile, in double across tiles: the double-precision sums of the same
+    inputs up to ~1e-13 of the sum of |terms|.  Sigma's update cancels the
+    mean part of S7 (|mu|^2 / sigma^2 of order 10) and nu's equation uses
+    1 + S8/S1 (of order 1/nu), so 1e-9 relative keeps a margin of ~100 on
+    both.  2000 rows: 32 tiles over many blocks, a ragged last tile
+    (2000 = 31 x 64 + 16).
     """
     torch = _torch()
     Y, truth, init, lat = _problem("cfust_p4r4g3_n100000_N4096", 2000, 1024)
@@ -274,7 +274,7 @@ def test_mstep_matches_oracle_fp32():
     with binding.Context(lat, precision=binding.CFUST_FP32) as ctx:
         got = ctx.cfust_mstep(dev(Y), E, init)
     for a, b, name in zip(got.as_arrays(), ref.as_arrays(), ("pi", "mu", "Sigma", "Delta", "nu")):
-        _cmp(name, a, b, 1e-4 if name == "nu" else 1e-5)
+        _cmp(name, a, b, 1e-9)
 
 
 def _fit_gpu(Y, params, lat, precision, iters, use_graph=True):
