@@ -269,6 +269,13 @@ cfust_status cfust_last_rescued(cfust_ctx *ctx, int64_t *count);
  * CFUST_EINVAL when timing is off or nothing has run yet. */
 cfust_status cfust_last_sweep_ms(cfust_ctx *ctx, float *ms);
 
+/* Device time (ms) of the last posterior / M-step-sums kernel launch of an
+ * EM iteration (the eight sums of Section 3.2, unfused from the E-step),
+ * from CUDA events recorded around it on the launching stream when
+ * opts.timing is 1 (inside the captured graph too).  Synchronises on the
+ * stop event.  CFUST_EINVAL when timing is off or no iteration has run. */
+cfust_status cfust_last_mstep_ms(cfust_ctx *ctx, float *ms);
+
 /* Single-precision normal functions of the lattice sweep, exposed for
  * verification.  x, out: device float arrays of n elements; stream: a
  * cudaStream_t (NULL = legacy default stream); stream-ordered.

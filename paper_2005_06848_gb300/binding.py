@@ -28,7 +28,7 @@ EXPORTED = ["cfust_create", "cfust_destroy", "cfust_loglik", "cfust_estep", "cfu
             "cfust_surrogate_set_params", "cfust_surrogate_train", "cfust_surrogate_last_error",
             "cfust_set_surrogate", "cfust_last_fallback", "cfust_surrogate_problems",
             "cfust_surrogate_finetune", "cfust_fit_multistart", "cfust_kmeans", "cfust_init_partition",
-            "cfust_multistart_partitions", "cfust_loglik_shifts"]
+            "cfust_multistart_partitions", "cfust_loglik_shifts", "cfust_last_mstep_ms"]
 
 SURROGATE_NPARAM = 35338
 
@@ -91,6 +91,7 @@ def load(build_if_missing: bool = True, path: str | None = None) -> ctypes.CDLL:
         "cfust_batched_shape": ([vp, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int)], ctypes.c_int),
         "cfust_last_rescued": ([vp, ctypes.POINTER(i64)], ctypes.c_int),
         "cfust_last_sweep_ms": ([vp, ctypes.POINTER(ctypes.c_float)], ctypes.c_int),
+        "cfust_last_mstep_ms": ([vp, ctypes.POINTER(ctypes.c_float)], ctypes.c_int),
         "cfust_last_error": ([vp], ctypes.c_char_p),
         "cfust_normal_f32": ([vp, vp, i64, ctypes.c_int, vp], ctypes.c_int),
         "cfust_mstep_noalloc": ([ctypes.c_int, vp, i64, vp, vp, vp, vp, vp, ctypes.c_double,
@@ -367,6 +368,11 @@ class Context:
     def cfust_last_sweep_ms(self) -> float:
         v = ctypes.c_float()
         self._check(self.lib.cfust_last_sweep_ms(self.h, ctypes.byref(v)))
+        return v.value
+
+    def cfust_last_mstep_ms(self) -> float:
+        v = ctypes.c_float()
+        self._check(self.lib.cfust_last_mstep_ms(self.h, ctypes.byref(v)))
         return v.value
 
     def cfust_last_rescued(self) -> int:

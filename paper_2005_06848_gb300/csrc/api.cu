@@ -42,6 +42,8 @@ struct cfust_ctx {
   cudaStream_t cap_stream = nullptr;  // private stream for graph capture
   cudaEvent_t ev_sweep[2] = {nullptr, nullptr};
   bool sweep_recorded = false;
+  cudaEvent_t ev_post[2] = {nullptr, nullptr};  // around the posterior / M-step sums launch
+  bool post_recorded = false;
   cudaGraphExec_t gexec = nullptr;
   const double *graph_Y = nullptr;
   int64_t graph_n = 0;
@@ -375,7 +377,14 @@ cfust_status enqueue_iteration(cfust_ctx *c, const double *Y, int64_t n, cudaStr
   a.e4 = c->d_e4;
   a.want_sums = true;
   a.want_ll = true;
+  const bool tpost = c->opts.timing && c->ev_post[0];
+  const unsigned evflag = (st == c->cap_stream) ? cudaEventRecordExternal : cudaEventRecordDefault;
+  if (tpost) CF_CUDA(c, cudaEventRecordWithFlags(c->ev_post[0], st, evflag));
   CF_CUDA(c, launch_posterior(c->opts.precision, a, st));
+  if (tpost) {
+    CF_CUDA(c, cudaEventRecordWithFlags(c->ev_post[1], st, evflag));
+    c->post_recorded = true;
+  }
   CF_CUDA(c, launch_reduce_ll(c->d_llpart, a.nblocks, c->d_ll, c->d_trace, c->d_status + 1, st));
   CF_CUDA(c, launch_mstep_finalize(c->d_partials, a.nblocks, c->g, c->p, c->r, n, nu_lo(c), nu_hi(c),
                                    c->d_params, c->d_status, st));
@@ -455,7 +464,8 @@ cfust_status cfust_create(cfust_ctx **out, const cfust_opts *o, void *cuda_strea
     return CFUST_ECUDA;
   }
   if (o->timing) {
-    if (cudaEventCreate(&c->ev_sweep[0]) != cudaSuccess || cudaEventCreate(&c->ev_sweep[1]) != cudaSuccess) {
+    if (cudaEventCreate(&c->ev_sweep[0]) != cudaSuccess || cudaEventCreate(&c->ev_sweep[1]) != cudaSuccess ||
+        cudaEventCreate(&c->ev_post[0]) != cudaSuccess || cudaEventCreate(&c->ev_post[1]) != cudaSuccess) {
       g_create_error = "cudaEventCreate failed";
       delete c;
       return CFUST_ECUDA;
@@ -512,6 +522,8 @@ cfust_status cfust_destroy(cfust_ctx *c) {
   drop_graph(c);
   if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
   free_batch(c->batch);
+  for (cudaEvent_t ev : c->ev_post)
+    if (ev) cudaEventDestroy(ev);
   for (cudaEvent_t ev : c->ev_sweep)
     if (ev) cudaEventDestroy(ev);
   void *bufs[] = {c->d_params, c->d_c64, c->d_c32, c->d_chi64, c->d_chi32, c->d_status,
@@ -591,6 +603,15 @@ cfust_status cfust_normal_f32(const float *x, float *out, int64_t n, int which, 
   if (n < 0 || (n > 0 && (!x || !out)) || which < 0 || which > 5) return CFUST_EINVAL;
   if (launch_normal_f32(x, out, n, which, static_cast<cudaStream_t>(stream)) != cudaSuccess)
     return CFUST_ECUDA;
+  return CFUST_OK;
+}
+
+cfust_status cfust_last_mstep_ms(cfust_ctx *c, float *ms) {
+  if (!c || !ms) return CFUST_EINVAL;
+  if (!c->opts.timing || !c->post_recorded) return fail(c, CFUST_EINVAL, "no timed M-step recorded");
+  DeviceGuard dg(c->device);
+  CF_CUDA(c, cudaEventSynchronize(c->ev_post[1]));
+  CF_CUDA(c, cudaEventElapsedTime(ms, c->ev_post[0], c->ev_post[1]));
   return CFUST_OK;
 }
 
