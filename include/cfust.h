@@ -107,6 +107,12 @@ typedef struct {
                              double-precision rescue, or the lattice rule behind a surrogate) whose
                              density bound puts tau_ij below exp(-T) gets log f = -inf, e = 0; each such
                              pair moves l by at most exp(-T).  0 selects 30; else in [1, 700]. */
+  int prioritise;         /* 1: Genz variable prioritisation: each pair's r variables are integrated in
+                             decreasing order of the standardised limit -q_t / sqrt(Lambda_tt) (ties
+                             keep the lower index) with the Cholesky factor of the permuted Lambda;
+                             the moments come back in the original order.  Same integral, much
+                             smaller lattice error for pairs in the tails.  Single fits only:
+                             CFUST_EINVAL with a surrogate attached or in cfust_fit_batched. */
 } cfust_opts;
 
 typedef struct cfust_ctx cfust_ctx;
@@ -200,7 +206,8 @@ cfust_status cfust_batched_shape(cfust_ctx *ctx, int *pairs_per_warp, int *ctas_
  * burned-in parameters; starts[*best] the fitted ones).  trace and iters_done
  * as for cfust_fit, for the final fit.  Starts that fail their burn-in
  * (degenerate, not positive definite) are not chosen; CFUST_EDEGENERATE when
- * none survives. */
+ * none survives.  The burn-in runs as a batched fit, so a context with
+ * opts.prioritise refuses burn_in > 0 (CFUST_EINVAL). */
 cfust_status cfust_fit_multistart(cfust_ctx *ctx, const double *Y, int64_t n, cfust_params *starts, int nstarts,
                                   int burn_in, int *best, double *loglik_trace, int *iters_done);
 

@@ -182,8 +182,45 @@ def component_terms(Y, mu, Sigma, Delta, nu):
     return d, q, Lam, log_tp
 
 
+def prioritised_order(a, Lam):
+    """Genz's variable prioritisation, in this library's reading: the r
+    variables of a pair are integrated in decreasing order of their
+    standardised limit a_t / sqrt(Lambda_tt), i.e. the smallest marginal
+    probability P(X_t > a_t) first (the most restrictive limit outermost);
+    ties keep the lower index.  a: [P, r].  Returns [P, r] permutations."""
+    c = a / np.sqrt(np.diag(Lam))[None, :]
+    return np.argsort(-c, axis=1, kind="stable")
+
+
+def _passes(aA, aB, L, Lam, mA, mB, U, sA, sB, logchi, density_only, prioritise):
+    """Pass A (T_A, optionally E[log chi^2]) and pass B (T_B, L E[V], L E[V V^T] L^T)
+    of the pairs of one chunk, in natural or prioritised variable order; the
+    moments come back in the natural order of X = L V."""
+    P, r = aA.shape
+    perms = prioritised_order(aA, Lam) if (prioritise and r > 1) else np.tile(np.arange(r), (P, 1))
+    TA = np.empty(P); EL = np.empty(P) if logchi else None
+    TB = np.empty(P); LEV = np.empty((P, r)); LEVVL = np.empty((P, r, r))
+    for perm in np.unique(perms, axis=0):
+        idx = np.nonzero((perms == perm).all(axis=1))[0]
+        Lp = L if np.array_equal(perm, np.arange(r)) else np.linalg.cholesky(Lam[np.ix_(perm, perm)])
+        if logchi:
+            TA[idx], EL[idx] = sov_pass(aA[idx][:, perm], Lp, mA, U, moments=False, logchi=True, s=sA)
+        else:
+            TA[idx] = sov_pass(aA[idx][:, perm], Lp, mA, U, moments=False, s=sA)
+        if density_only:
+            continue
+        tb, EV, EVV = sov_pass(aB[idx][:, perm], Lp, mB, U, moments=True, s=sB)
+        TB[idx] = tb
+        # X_perm = Lp V: scatter its moments back to the natural coordinates
+        lev = EV @ Lp.T
+        levvl = np.einsum("th,jhk,sk->jts", Lp, EVV, Lp)
+        LEV[np.ix_(idx, perm)] = lev
+        LEVVL[np.ix_(idx, perm, perm)] = levvl
+    return TA, EL, TB, LEV, LEVVL
+
+
 def estep_component(Y, mu, Sigma, Delta, nu, U, e2_mode=0, density_only=False,
-                    chunk=None):
+                    chunk=None, prioritise=False):
     """log f_i(y_j) and e1..e4 for every observation j of one component i.
 
     Returns dict with logf [n], and unless ``density_only``: e1 [n], e2 [n],
@@ -191,7 +228,9 @@ def estep_component(Y, mu, Sigma, Delta, nu, U, e2_mode=0, density_only=False,
     e2 = e1 - log((nu+d)/2) - (nu+p)/(nu+d) + psi((nu+p)/2) (exact at Delta = 0);
     e2_mode 1 uses the lattice estimate E[log chi^2_{nu+p}] - log(nu+d) from
     the density pass.  Reading: where T_A or T_B is 0 (underflow), log f is
-    -inf and e1..e4 are set to 0, their weight tau being 0.
+    -inf and e1..e4 are set to 0, their weight tau being 0.  ``prioritise``
+    integrates each pair's variables in the order of ``prioritised_order``
+    (pass B's limits are a positive multiple of pass A's: the same order).
     """
     n, p = Y.shape
     r = Delta.shape[1]
@@ -212,18 +251,14 @@ def estep_component(Y, mu, Sigma, Delta, nu, U, e2_mode=0, density_only=False,
     for sl in _chunks(n, chunk):
         dd = d[sl]; qq = q[sl]
         aA = -qq * _dof_ratio(mA, nu, dd)[:, None]
-        if e2_mode == 1 and not density_only:
-            TA, elogchi = sov_pass(aA, L, mA, U, moments=False, logchi=True, s=sA)
-        else:
-            TA = sov_pass(aA, L, mA, U, moments=False, s=sA)
+        aB = -qq * _dof_ratio(mB, nu, dd)[:, None]
+        logchi = (e2_mode == 1 and not density_only)
+        TA, elogchi, TB, LEV, LEVVL = _passes(aA, aB, L, Lam, mA, mB, U, sA, sB, logchi, density_only,
+                                              prioritise)
         with np.errstate(divide="ignore"):
             logf[sl] = r * LOG2 + log_tp[sl] + np.log(TA)
         if density_only:
             continue
-        aB = -qq * _dof_ratio(mB, nu, dd)[:, None]
-        TB, EV, EVV = sov_pass(aB, L, mB, U, moments=True, s=sB)
-        LEV = EV @ L.T                                         # L E[V]
-        LEVVL = np.einsum("th,jhk,sk->jts", L, EVV, L)
         c1, c2, c3, c4 = expectations(dd, qq, nu, p, TA, TB, LEV, LEVVL, e2_mode,
                                       elogchi if e2_mode == 1 else None)
         e1[sl], e2[sl], e3[sl], e4[sl] = c1, c2, c3, c4
@@ -290,7 +325,7 @@ def posterior(logf: np.ndarray, pi: np.ndarray):
     return tau, float(lse.sum()), lse
 
 
-def estep(Y, params, lattice_U, e2_mode=0):
+def estep(Y, params, lattice_U, e2_mode=0, prioritise=False):
     """E-step of Section 2 for all (i, j): log f_ij, tau_ij, e1..e4 and l(Psi).
 
     ``params`` has arrays pi[g], mu[g,p], Sigma[g,p,p], Delta[g,p,r], nu[g].
@@ -299,7 +334,8 @@ def estep(Y, params, lattice_U, e2_mode=0):
     """
     g = params.pi.shape[0]
     comps = [estep_component(Y, params.mu[i], params.Sigma[i], params.Delta[i],
-                             params.nu[i], lattice_U, e2_mode=e2_mode) for i in range(g)]
+                             params.nu[i], lattice_U, e2_mode=e2_mode, prioritise=prioritise)
+             for i in range(g)]
     out = {k: np.stack([c[k] for c in comps]) for k in comps[0]}
     tau, ll, _ = posterior(out["logf"], params.pi)
     out["tau"] = tau
@@ -307,11 +343,12 @@ def estep(Y, params, lattice_U, e2_mode=0):
     return out
 
 
-def loglik(Y, params, lattice_U):
+def loglik(Y, params, lattice_U, prioritise=False):
     """l(Psi) = sum_j log sum_i pi_i f_i(y_j) (Eq. 1, Eq. 3): density pass only."""
     g = params.pi.shape[0]
     logf = np.stack([estep_component(Y, params.mu[i], params.Sigma[i], params.Delta[i],
-                                     params.nu[i], lattice_U, density_only=True)["logf"]
+                                     params.nu[i], lattice_U, density_only=True,
+                                     prioritise=prioritise)["logf"]
                      for i in range(g)])
     return posterior(logf, params.pi)[1]
 

@@ -346,7 +346,7 @@ cfust_status run_estep(cfust_ctx *c, const double *Y, int64_t n, EstepOut o, boo
     CF_CUDA(c, launch_estep(c->opts.precision, Y, n, c->g, c->p, c->r, c->lat, c->d_c64, c->d_c32,
                             c->d_chi64, c->d_chi32, o, density_only, c->opts.e2_mode, c->d_rescue,
                             c->d_rescue_cnt, c->d_status, c->opts.pairs_per_warp, st, tm, triage, pi,
-                            (float)c->opts.triage_nats));
+                            (float)c->opts.triage_nats, c->opts.prioritise));
     return CFUST_OK;
   }
   if (c->opts.precision != CFUST_FP32 || c->opts.e2_mode != 0 || c->r != 3)
@@ -448,6 +448,10 @@ cfust_status cfust_create(cfust_ctx **out, const cfust_opts *o, void *cuda_strea
     g_create_error = "need 0 < nu_min < nu_max";
     return CFUST_EINVAL;
   }
+  if (o->prioritise != 0 && o->prioritise != 1) {
+    g_create_error = "prioritise must be 0 or 1";
+    return CFUST_EINVAL;
+  }
   if (o->triage_nats != 0.0 && !(o->triage_nats >= 1.0 && o->triage_nats <= 700.0)) {
     g_create_error = "triage_nats must be 0 (default 30) or in [1, 700]";
     return CFUST_EINVAL;
@@ -543,6 +547,8 @@ const char *cfust_last_error(cfust_ctx *c) {
 
 cfust_status cfust_set_surrogate(cfust_ctx *c, cfust_surrogate *s) {
   if (!c) return CFUST_EINVAL;
+  if (s && c->opts.prioritise)
+    return fail(c, CFUST_EINVAL, "variable prioritisation serves the lattice sweep of single fits, not a surrogate");
   DeviceGuard dg(c->device);
   drop_graph(c);
   c->sur = s;
@@ -971,6 +977,7 @@ extern "C" cfust_status cfust_fit_batched(cfust_ctx *c, int nfits, const double 
                                          cfust_params *P, double *trace_out, int *fit_status_out) {
   if (!c) return CFUST_EINVAL;
   if (nfits < 1 || !Y || !n || !P) return fail(c, CFUST_EINVAL, "nfits >= 1 with Y, n and params required");
+  if (c->opts.prioritise) return fail(c, CFUST_EINVAL, "variable prioritisation is for single fits");
   DeviceGuard dg(c->device);
   const int p = P[0].p, r = P[0].r;
   for (int f = 0; f < nfits; ++f) {

@@ -43,6 +43,8 @@ struct CompT {
   double logmA;           // log(nu + p)
   T L[RMAX * RMAX];       // r x r, stride RMAX, lower triangle used
   T Linv[RMAX];           // 1 / L_tt
+  double lamd[RMAX];      // 1 / sqrt(Lambda_tt): standardises the limits for the variable order
+  double lam[RMAX * (RMAX + 1) / 2];  // Lambda, packed lower (t, h <= t at t(t+1)/2 + h)
   // single-precision copies for code that runs in float throughout (the
   // surrogate E-step), so it converts nothing per pair
   float fmu[PMAX], fA[PMAX * PMAX], fB[RMAX * PMAX];
@@ -131,7 +133,7 @@ cudaError_t launch_estep(int precision, const double *Y, int64_t n, int g, int p
                          const double *chi64, const float *chi32, EstepOut out, bool density_only,
                          int e2_mode, unsigned long long *rescue_list, unsigned *rescue_count, int *d_status,
                          int pairs_per_warp, cudaStream_t st, SweepTiming tm = SweepTiming(),
-                         int triage = 0, const double *d_pi = nullptr, float tnats = 30.f);
+                         int triage = 0, const double *d_pi = nullptr, float tnats = 30.f, int prio = 0);
 
 // FP32 lattice sweep (r = 3 only) of the observations listed per component:
 // list[i * n + k], k < count[i] (device counts), followed by the rescue pass.

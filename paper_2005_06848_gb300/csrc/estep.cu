@@ -95,6 +95,7 @@ struct EArgs {
   int triage;          // 1: skip queued pairs whose posterior weight is provably negligible
   const double *pi;    // device [g], read by the triage
   float tnats;         // the triage's margin: tau_ij < exp(-tnats) counts as negligible
+  int prio;            // 1: variable prioritisation (single-fit sweeps and their rescue)
 };
 
 // The per-fit part of a sweep: observations, their count, the component
@@ -184,6 +185,72 @@ struct PairedConsts {
   float2 nL[RMAX * (RMAX + 1) / 2];  // -L_th / L_tt (h < t), packed lower triangle
 };
 
+// One pair's variable order and the factor of its permuted Lambda (variable
+// prioritisation), written by one thread, read by the warp (or CTA) sweeping it.
+struct PrioSlot {
+  double q[RMAX];                      // q in the prioritised order
+  double L[RMAX * (RMAX + 1) / 2];     // Cholesky factor of the permuted Lambda, packed lower
+  double Li[RMAX];                     // 1 / L_tt
+  int ord[RMAX];                       // original coordinate of position t
+  PairedConsts pc;                     // -L_th / L_tt pairs for the paired sweep
+};
+
+// Variable prioritisation (Genz's reordering, this library's reading): the
+// coordinates are integrated in decreasing order of the standardised limit
+// -q_t / sqrt(Lambda_tt) (pass B's limits are a positive multiple of pass
+// A's, so one order serves both), ties keeping the lower index, with the
+// Cholesky factor of the permuted Lambda.  The order is decided in double
+// from the double prologue, as the oracle decides it.  Not inlined: its
+// dynamically indexed arrays stay out of the sweep's registers.
+template <int R>
+__device__ __noinline__ void prio_setup(const double *q, const double *lam, const double *lamd, PrioSlot *s) {
+  int ord[R];
+  double key[R];
+  for (int t = 0; t < R; ++t) {
+    ord[t] = t;
+    key[t] = -q[t] * lamd[t];
+  }
+  for (int t = 1; t < R; ++t) {  // stable insertion sort, descending
+    const int o = ord[t];
+    const double k = key[t];
+    int u = t - 1;
+    while (u >= 0 && key[u] < k) {
+      key[u + 1] = key[u];
+      ord[u + 1] = ord[u];
+      --u;
+    }
+    key[u + 1] = k;
+    ord[u + 1] = o;
+  }
+  double Lm[R * R];
+  for (int t = 0; t < R; ++t)
+    for (int h = 0; h <= t; ++h) {
+      const int x = ord[t] > ord[h] ? ord[t] : ord[h], y = ord[t] > ord[h] ? ord[h] : ord[t];
+      Lm[t * R + h] = lam[x * (x + 1) / 2 + y];
+    }
+  for (int j = 0; j < R; ++j) {
+    double d = Lm[j * R + j];
+    for (int k = 0; k < j; ++k) d -= Lm[j * R + k] * Lm[j * R + k];
+    d = sqrt(fmax(d, 1e-300));  // a permutation of a positive definite Lambda stays so
+    Lm[j * R + j] = d;
+    for (int i = j + 1; i < R; ++i) {
+      double v = Lm[i * R + j];
+      for (int k = 0; k < j; ++k) v -= Lm[i * R + k] * Lm[j * R + k];
+      Lm[i * R + j] = v / d;
+    }
+  }
+  for (int t = 0; t < R; ++t) {
+    s->ord[t] = ord[t];
+    s->q[t] = q[ord[t]];
+    s->Li[t] = 1.0 / Lm[t * R + t];
+    for (int h = 0; h <= t; ++h) {
+      s->L[t * (t + 1) / 2 + h] = Lm[t * R + h];
+      const float v = -(float)Lm[t * R + h] * (float)s->Li[t];
+      s->pc.nL[t * (t + 1) / 2 + h] = make_float2(v, v);
+    }
+  }
+}
+
 // Lattice constants of coordinate t for the double-precision sweep (the
 // single-precision sweep reads its uniforms from the lattice table).
 __device__ __forceinline__ double lat_sf(const EArgs &a, int t) { return a.sfrac[t]; }
@@ -245,7 +312,7 @@ __device__ __forceinline__ bool pair_sweep(const EArgs &a, const FitView &fv, co
                                            const Prologue<R> &pr,
                                            const T *__restrict__ tA, const T *__restrict__ tB,
                                            int i, int64_t j, int lane, bool check,
-                                           const PairedConsts *pc) {
+                                           const PairedConsts *pc, PrioSlot *slot) {
   using M = Num<T>;
   constexpr int RP = R * (R + 1) / 2;
   constexpr bool PAIRED = (sizeof(T) == 4) && !DENS;
@@ -273,6 +340,29 @@ __device__ __forceinline__ bool pair_sweep(const EArgs &a, const FitView &fv, co
 #pragma unroll
     for (int h = 0; h <= t; ++h) Lc[t * (t + 1) / 2 + h] = c.L[t * RMAX + h];
   }
+  // variable prioritisation: lane 0 orders the coordinates and factors the
+  // permuted Lambda into this warp's slot; the sweep then runs in that order
+  // and the moments are stored back at their original coordinates
+  int ord[R];
+#pragma unroll
+  for (int t = 0; t < R; ++t) ord[t] = t;
+  const PairedConsts *pcu = pc;
+  if (a.prio) {
+    __syncwarp();  // every lane is done with the slot's previous pair
+    if (lane == 0) prio_setup<R>(pr.q, c.lam, c.lamd, slot);
+    __syncwarp();
+#pragma unroll
+    for (int t = 0; t < R; ++t) {
+      ord[t] = slot->ord[t];
+      q[t] = static_cast<T>(slot->q[t]);
+      aA[t] = -q[t] * fA;
+      aB[t] = -q[t] * fB;
+      Li[t] = static_cast<T>(slot->Li[t]);
+#pragma unroll
+      for (int h = 0; h <= t; ++h) Lc[t * (t + 1) / 2 + h] = static_cast<T>(slot->L[t * (t + 1) / 2 + h]);
+    }
+    pcu = &slot->pc;
+  }
   // paired operands: (pass A, pass B) limits; -L and 1/L_tt pairs come from shared memory
   // (pass A, pass B) limits over L_tt: with the staged -L_th / L_tt the
   // standardised limit of coordinate t is one multiply-add chain per point
@@ -280,7 +370,7 @@ __device__ __forceinline__ bool pair_sweep(const EArgs &a, const FitView &fv, co
   if constexpr (PAIRED) {
 #pragma unroll
     for (int t = 0; t < R; ++t) {
-      const float li = (float)c.Linv[t];
+      const float li = (float)Li[t];
       ab2[t] = make_float2((float)aA[t] * li, (float)aB[t] * li);
     }
   }
@@ -350,7 +440,7 @@ __device__ __forceinline__ bool pair_sweep(const EArgs &a, const FitView &fv, co
       for (int t = 0; t < R; ++t) {
         float2 acc2 = __fmul2_rn(ab2[t], s2);
 #pragma unroll
-        for (int h = 0; h < t; ++h) acc2 = __ffma2_rn(pc->nL[t * (t + 1) / 2 + h], z2[h], acc2);
+        for (int h = 0; h < t; ++h) acc2 = __ffma2_rn(pcu->nL[t * (t + 1) / 2 + h], z2[h], acc2);
         float2 p2, q2;
         phi_upper_pq_x2(acc2, p2, q2);
         w2 = __fmul2_rn(w2, p2);
@@ -471,7 +561,7 @@ __device__ __forceinline__ bool pair_sweep(const EArgs &a, const FitView &fv, co
   if (lane == 2) store<OT>(fv.out.e2, ij, e2);
 #pragma unroll
   for (int t = 0; t < R; ++t) {
-    if (lane == 3 + t) store<OT>(fv.out.e3, ((int64_t)i * R + t) * n + j, e1 * (q[t] + sig * LEV[t]));
+    if (lane == 3 + t) store<OT>(fv.out.e3, ((int64_t)i * R + ord[t]) * n + j, e1 * (q[t] + sig * LEV[t]));
   }
   // E[V V^T] in the L basis: (L EVV L^T)_th = sum_{a<=t} sum_{b<=h} L_ta EVV_ab L_hb
 #pragma unroll
@@ -490,7 +580,9 @@ __device__ __forceinline__ bool pair_sweep(const EArgs &a, const FitView &fv, co
           }
         }
         const T exx = q[t] * q[h] + sig * (q[t] * LEV[h] + LEV[t] * q[h]) + sig * sig * s;
-        store<OT>(fv.out.e4, ((int64_t)i * RP + t * (t + 1) / 2 + h) * n + j, e1 * exx);
+        // entry (t, h) of the prioritised order is (ord_t, ord_h) of the original
+        const int x = ord[t] > ord[h] ? ord[t] : ord[h], y = ord[t] > ord[h] ? ord[h] : ord[t];
+        store<OT>(fv.out.e4, ((int64_t)i * RP + x * (x + 1) / 2 + y) * n + j, e1 * exx);
       }
     }
   }
@@ -504,7 +596,7 @@ __device__ __forceinline__ bool pair_sweep(const EArgs &a, const FitView &fv, co
 template <typename T, int R, bool DENS>
 __device__ __forceinline__ void sweep_warp_pairs(const EArgs &a, const FitView &fv, const CompT<T> &c,
                                                  const PairedConsts *pcs, const T *tA, const T *tB,
-                                                 int i, int qi, int64_t jw0, int ppw) {
+                                                 int i, int qi, int64_t jw0, int ppw, PrioSlot *slot) {
   const int lane = threadIdx.x & 31;
   int cnt = 0;
   if (jw0 < fv.n) cnt = (int)((fv.n - jw0) < ppw ? (fv.n - jw0) : ppw);
@@ -514,7 +606,7 @@ __device__ __forceinline__ void sweep_warp_pairs(const EArgs &a, const FitView &
   for (int b = 0; b < cnt; ++b) {
     const Prologue<R> pr = shfl_prologue<R>(mine, b);
     const int64_t j = jw0 + b;
-    const bool need = pair_sweep<T, T, R, DENS>(a, fv, c, pr, tA, tB, i, j, lane, check, pcs);
+    const bool need = pair_sweep<T, T, R, DENS>(a, fv, c, pr, tA, tB, i, j, lane, check, pcs, slot);
     if (need && lane == 0) {
       const unsigned slot = atomicAdd(a.rescue_count, 1u);
       a.rescue_list[slot] = pair_id(qi, j);
@@ -581,13 +673,20 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? CFUST_ESTEP_MINB : 1) es
   if (!stage_block<T, DENS>(a, i, smem, tA, tB, cs, pcs)) return;
   const int warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
   const int64_t jw0 = ((int64_t)blockIdx.x * nw + warp) * a.ppw;
-  sweep_warp_pairs<T, R, DENS>(a, fit_view(a), *cs, pcs, tA, tB, i, i, jw0, a.ppw);
+  // with prioritisation, one order-and-factor slot per warp after the staged constants
+  PrioSlot *slot = nullptr;
+  if (a.prio) {
+    const size_t tab_bytes = a.staged ? (size_t)(DENS ? 1 : 2) * a.N * sizeof(T) : 0;
+    slot = reinterpret_cast<PrioSlot *>(smem + align16(tab_bytes) + align16(sizeof(CompT<T>)) +
+                                        align16(sizeof(PairedConsts)) + 16) + warp;
+  }
+  sweep_warp_pairs<T, R, DENS>(a, fit_view(a), *cs, pcs, tA, tB, i, i, jw0, a.ppw, slot);
 }
 
 // Triage of a listed pair (single precision outputs): with log f of every
 // component of observation j in place (values, or upper bounds for pairs still
 // to be swept, +inf where none is known), a pair whose log pi_i + log f_ij
-// trails the best component by more than 30 has tau_ij < exp(-30); it gets
+// trails the best component by more than tnats has tau_ij < exp(-tnats); it gets
 // log f = -inf and zero expectations instead of a sweep.  Unknown entries do
 // not count towards the best (that only makes the test more cautious).
 template <int R, bool DENS>
@@ -647,7 +746,7 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? CFUST_ESTEP_MINB : 1)
       if ((skipped >> b) & 1u) continue;
       const Prologue<R> pr = shfl_prologue<R>(mine, b);
       const int64_t j = __shfl_sync(0xffffffffu, myj, b);
-      const bool need = pair_sweep<T, T, R, DENS>(a, fv, *cs, pr, tA, tB, i, j, lane, check, pcs);
+      const bool need = pair_sweep<T, T, R, DENS>(a, fv, *cs, pr, tA, tB, i, j, lane, check, pcs, nullptr);
       if (need && lane == 0) {
         const unsigned slot = atomicAdd(a.rescue_count, 1u);
         a.rescue_list[slot] = pair_id(i, j);
@@ -718,14 +817,36 @@ __device__ void pair_sweep_log_cta(const EArgs &a, const FitView &fv, const Comp
   const bool nrm = isinf(c.nu);  // the skew-normal limit: scale 1, e1 = 1, e2 = 0
   const double nud64 = c.nu + pr.d;
   const double fA = nrm ? 1.0 : sqrt(c.mA / nud64), fB = nrm ? 1.0 : sqrt(c.mB / nud64);
-  double aA[R], aB[R], Lc[RP], Li[R];
+  double aA[R], aB[R], Lc[RP], Li[R], qv[R];
+  int ord[R];
 #pragma unroll
   for (int t = 0; t < R; ++t) {
-    aA[t] = -pr.q[t] * fA;
-    aB[t] = -pr.q[t] * fB;
+    qv[t] = pr.q[t];
+    ord[t] = t;
     Li[t] = c.Linv[t];
 #pragma unroll
     for (int h = 0; h <= t; ++h) Lc[t * (t + 1) / 2 + h] = c.L[t * RMAX + h];
+  }
+  if (a.prio) {
+    // the variable order and permuted factor of the single-precision sweep,
+    // so the rescued pair is integrated by the same rule
+    __shared__ PrioSlot rslot;
+    __syncthreads();
+    if (threadIdx.x == 0) prio_setup<R>(pr.q, c.lam, c.lamd, &rslot);
+    __syncthreads();
+#pragma unroll
+    for (int t = 0; t < R; ++t) {
+      ord[t] = rslot.ord[t];
+      qv[t] = rslot.q[t];
+      Li[t] = rslot.Li[t];
+#pragma unroll
+      for (int h = 0; h <= t; ++h) Lc[t * (t + 1) / 2 + h] = rslot.L[t * (t + 1) / 2 + h];
+    }
+  }
+#pragma unroll
+  for (int t = 0; t < R; ++t) {
+    aA[t] = -qv[t] * fA;
+    aB[t] = -qv[t] * fB;
   }
   const int k0 = warp * WARP + lane, kstride = nw * WARP;
   float fm[R], fstep[R], two_sf[R], sf[R];
@@ -860,7 +981,7 @@ __device__ void pair_sweep_log_cta(const EArgs &a, const FitView &fv, const Comp
         e2 = ok ? e1 - (log(0.5 * nud64) + c.mA / nud64 - c.psiA) : 0.0;
       store<float>(fv.out.e1, ij, e1);
       store<float>(fv.out.e2, ij, e2);
-      for (int t = 0; t < R; ++t) store<float>(fv.out.e3, ((int64_t)i * R + t) * n + j, e1 * (pr.q[t] + sig * LEV[t]));
+      for (int t = 0; t < R; ++t) store<float>(fv.out.e3, ((int64_t)i * R + ord[t]) * n + j, e1 * (qv[t] + sig * LEV[t]));
       for (int t = 0; t < R; ++t)
         for (int h = 0; h <= t; ++h) {
           double sacc = 0.0;
@@ -869,8 +990,9 @@ __device__ void pair_sweep_log_cta(const EArgs &a, const FitView &fv, const Comp
               const double evv = (aa >= bb ? tot[3 + R + aa * (aa + 1) / 2 + bb] : tot[3 + R + bb * (bb + 1) / 2 + aa]) * iSB;
               sacc += Lc[t * (t + 1) / 2 + aa] * evv * Lc[h * (h + 1) / 2 + bb];
             }
-          const double exx = pr.q[t] * pr.q[h] + sig * (pr.q[t] * LEV[h] + LEV[t] * pr.q[h]) + sig * sig * sacc;
-          store<float>(fv.out.e4, ((int64_t)i * RP + t * (t + 1) / 2 + h) * n + j, e1 * exx);
+          const double exx = qv[t] * qv[h] + sig * (qv[t] * LEV[h] + LEV[t] * qv[h]) + sig * sig * sacc;
+          const int x = ord[t] > ord[h] ? ord[t] : ord[h], y = ord[t] > ord[h] ? ord[h] : ord[t];
+          store<float>(fv.out.e4, ((int64_t)i * RP + x * (x + 1) / 2 + y) * n + j, e1 * exx);
         }
     }
   }
@@ -936,7 +1058,7 @@ cudaError_t launch_r(EArgs a, int g, int64_t n, cudaStream_t st, bool fp32,
   const size_t tab_bytes = (size_t)(DENS ? 1 : 2) * a.N * sizeof(T);
   a.staged = tab_bytes <= 160u * 1024u ? 1 : 0;
   const size_t smem = (a.staged ? align16(tab_bytes) : 0) + align16(sizeof(CompT<T>)) +
-                      align16(sizeof(PairedConsts)) + 16;
+                      align16(sizeof(PairedConsts)) + 16 + (a.prio ? 8 * sizeof(PrioSlot) : 0);
   cudaError_t e = cudaFuncSetAttribute(estep_kernel<T, R, DENS>,
                                        cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
@@ -1067,7 +1189,7 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? CFUST_ESTEP_MINB : 1)
     const FitView fv = batch_view<T>(b, fd, a.p, R);
     const int warp = threadIdx.x >> 5;
     const int64_t jw0 = (int64_t)item.j0 + (int64_t)warp * a.ppw;
-    sweep_warp_pairs<T, R, DENS>(a, fv, *cs, pcs, tA, tB, cr.i, item.gc, jw0, a.ppw);
+    sweep_warp_pairs<T, R, DENS>(a, fv, *cs, pcs, tA, tB, cr.i, item.gc, jw0, a.ppw, nullptr);
     __syncthreads();
   }
 }
@@ -1182,6 +1304,7 @@ cudaError_t launch_estep_batched(int precision, const BatchDev &b, int p, int r,
   a.status = d_status;
   a.triage = triage ? 1 : 0;
   a.tnats = 30.f;
+  a.prio = 0;
   if (precision == CFUST_FP64) {
     a.comp = c64;
     a.chi = chi64;
@@ -1247,7 +1370,7 @@ cudaError_t launch_list_r3(EArgs a, int g, int64_t n, const int *list, const uns
 
 EArgs make_args(const double *Y, int64_t n, int g, int p, const LatticeDev &lat, EstepOut out, int e2_mode,
                 unsigned long long *rescue_list, unsigned *rescue_count, int *d_status, int triage,
-                const double *d_pi, float tnats) {
+                const double *d_pi, float tnats, int prio = 0) {
   EArgs a;
   a.Y = Y;
   a.n = n;
@@ -1270,6 +1393,7 @@ EArgs make_args(const double *Y, int64_t n, int g, int p, const LatticeDev &lat,
   a.status = d_status;
   a.triage = (triage && out.logf != nullptr) ? 1 : 0;
   a.tnats = tnats;
+  a.prio = prio ? 1 : 0;
   a.pi = d_pi;
   a.comp = nullptr;
   a.chi = nullptr;
@@ -1302,9 +1426,10 @@ cudaError_t launch_estep(int precision, const double *Y, int64_t n, int g, int p
                          const double *chi64, const float *chi32, EstepOut out, bool density_only,
                          int e2_mode, unsigned long long *rescue_list, unsigned *rescue_count, int *d_status,
                          int pairs_per_warp, cudaStream_t st, SweepTiming tm, int triage,
-                         const double *d_pi, float tnats) {
+                         const double *d_pi, float tnats, int prio) {
   if (n <= 0) return cudaSuccess;
-  EArgs a = make_args(Y, n, g, p, lat, out, e2_mode, rescue_list, rescue_count, d_status, triage, d_pi, tnats);
+  EArgs a = make_args(Y, n, g, p, lat, out, e2_mode, rescue_list, rescue_count, d_status, triage, d_pi, tnats,
+                      prio);
   if (pairs_per_warp <= 0) {
     // about sixteen waves of two resident CTAs per SM (8 warps each), so the
     // last wave's imbalance stays small; 1..32 pairs per warp (measured best

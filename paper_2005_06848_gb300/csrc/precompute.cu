@@ -112,6 +112,10 @@ __device__ void precompute_component(const double *params, int g, int p, int r, 
       const double s = 0.5 * (Lam[t * RMAX + h] + Lam[h * RMAX + t]);
       Lam[t * RMAX + h] = Lam[h * RMAX + t] = s;
     }
+  double lamd[RMAX], lamp[RMAX * (RMAX + 1) / 2];
+  for (int t = 0; t < RMAX; ++t) lamd[t] = (t < r && Lam[t * RMAX + t] > 0.0) ? 1.0 / sqrt(Lam[t * RMAX + t]) : 0.0;
+  for (int t = 0; t < RMAX; ++t)
+    for (int h = 0; h <= t; ++h) lamp[t * (t + 1) / 2 + h] = (t < r) ? Lam[t * RMAX + h] : 0.0;
   if (!cholesky_lower(Lam, r, RMAX, L, RMAX)) {
     atomicOr(status, ERR_NOTPD_LAMBDA);
     return;
@@ -141,6 +145,8 @@ __device__ void precompute_component(const double *params, int g, int p, int r, 
     const double li = (t < r) ? 1.0 / L[t * RMAX + t] : 0.0;
     o.Linv[t] = li;
     f.Linv[t] = (float)li;
+    o.lamd[t] = f.lamd[t] = lamd[t];
+    for (int h = 0; h <= t; ++h) o.lam[t * (t + 1) / 2 + h] = f.lam[t * (t + 1) / 2 + h] = lamp[t * (t + 1) / 2 + h];
   }
   // psi((nu+p)/2) and log(nu+p) enter e2 only, which is 0 at nu = inf
   const double psiA = isinf(nu) ? 0.0 : digamma(0.5 * (nu + p));
