@@ -92,6 +92,46 @@ def sweep_traffic_bytes():
         return None
 
 
+def accuracy_vs_judge(torch, binding, synth, Yd, P, lat, stream, r, pairs):
+    """Log-likelihood and per-pair log f error of the bench's 4096-point FP32
+    rule, natural and prioritised order, against the 65536-point FP32 rule in
+    prioritised order (tau-weighted RMS of log f: the pairs that carry the
+    posterior weight); and the EM-iteration time of the prioritised order."""
+    judge_lat = synth.make_lattice(1 << 16, r + 1, 0)
+    with binding.Context(judge_lat, precision=binding.CFUST_FP32, prioritise=True, stream=stream) as cj:
+        J = cj.cfust_estep(Yd, P)
+    jl = J["logf"].double()
+    tau = J["tau"].double()
+    out = {"judge": "65536-point lattice, prioritised order, FP32", "lattice_points": lat.n}
+    for prio in (False, True):
+        with binding.Context(lat, precision=binding.CFUST_FP32, prioritise=prio, stream=stream) as c:
+            E = c.cfust_estep(Yd, P)
+            d = (E["logf"].double() - jl)
+            d = torch.where(torch.isfinite(d), d, torch.zeros_like(d))
+            w = float((tau * d * d).sum() / tau.sum()) ** 0.5
+            out["prioritised" if prio else "natural"] = {
+                "loglik_error": float(E["loglik"] - J["loglik"]),
+                "logf_rms_error_tau_weighted": w,
+                "tau_max_abs_error": float((E["tau"].double() - tau).abs().max())}
+    with binding.Context(lat, precision=binding.CFUST_FP32, max_iter=8, use_graph=True, timing=True,
+                         prioritise=True, stream=stream) as c:
+        c.cfust_fit_begin(Yd, P)
+        for _ in range(3):
+            c.cfust_fit_step(1)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(5):
+            c.cfust_fit_step(1)
+        e1.record(stream)
+        e1.synchronize()
+        ms = e0.elapsed_time(e1) / 5
+        c.cfust_fit_end()
+    out["prioritised"]["ms_per_step"] = ms
+    out["prioritised"]["value"] = pairs / (ms / 1e3)
+    return out
+
+
 def mstep_roofline(n, g, p, r, ms, peaks):
     """Achieved HBM bandwidth of the posterior / M-step sums kernel."""
     K = 3 + p + r + p * r + r * (r + 1) // 2 + p * (p + 1) // 2
@@ -410,6 +450,10 @@ def run_ours(args):
                      "peak_source": f"FP32 FMA peak 152 SMs x 128 lanes x 2 x {sm_max:.0f} MHz (derived)",
                      "sweep_ms_mean": mean_sweep_ms,
                      "flops_per_launch": flops},
+        # accuracy of the timed rule against a 65536-point prioritised rule
+        # on the same data, in natural and prioritised variable order
+        "accuracy": accuracy_vs_judge(torch, binding, synth, Yd, init, lat, stream, r, pairs_per_step)
+        if (rank == 0 or ws == 1) and not args.no_accuracy else None,
         # the unfused M-step sums against HBM: algorithmic bytes = the E-step
         # outputs read once (log f, e1, e2, e3, e4 in float) + Y once (double)
         # + the per-block partial sums written once; the kernel is bound by
@@ -660,6 +704,8 @@ def main(argv=None):
     ap.add_argument("--cpu-rows", type=int, default=1024)
     ap.add_argument("--ref-rows", type=int, default=128)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-accuracy", action="store_true",
+                    help="skip the accuracy comparison against the 65536-point rule")
     ap.add_argument("--workload", choices=["single", "batched", "surrogate"], default="single")
     ap.add_argument("--sg-train", type=int, default=20_000_000)
     ap.add_argument("--sg-epochs", type=int, default=100)

@@ -90,7 +90,7 @@ def splitmix64_stream(seed: int, count: int) -> list[int]:
 # Results of the search below for sizes whose search takes tens of seconds
 # (the 2^16-point reference rule); tests/test_synth_lattice.py re-runs the
 # search for every entry.
-KOROBOV_TABLE = {(65536, 4): 1443}
+KOROBOV_TABLE = {(65536, 4): 1443, (65536, 5): 15845}
 
 
 @functools.lru_cache(maxsize=None)
