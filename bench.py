@@ -599,6 +599,7 @@ def run_surrogate(args):
     l_sur, _ = _loglik_ms(torch, ctx_s, Yd, init)
     fallback = ctx_s.cfust_last_fallback()
     rms, l_judge = {}, None
+    rms_p, l_judge_p, n_eq_p = {}, None, None
     if args.sg_plain_n:
         n_eq = args.sg_plain_n   # profiling runs: the plain lattice given, no accuracy ladder
     else:
@@ -616,6 +617,21 @@ def run_surrogate(args):
             rms[N] = float(np.sqrt(np.mean(np.square(errs))))
         ok_n = [N for N in ladder if rms[N] <= e_sur]
         n_eq = min(ok_n) if ok_n else max(ladder)
+        # the plain rule with variable prioritisation, judged by the
+        # prioritised 65536-point rule (the surrogate judged by it too)
+        with binding.Context(synth.make_lattice(JUDGE_POINTS, 4, seed=0), precision=binding.CFUST_FP32,
+                             prioritise=True) as judge_p:
+            l_judge_p = judge_p.cfust_loglik(Yd, init)
+        e_sur_p = abs(l_sur - l_judge_p)
+        for N in ladder:
+            errs = []
+            for sd in range(3):
+                with binding.Context(synth.make_lattice(N, 4, seed=sd), precision=binding.CFUST_FP32,
+                                     triage_nats=tn, prioritise=True) as c:
+                    errs.append(c.cfust_loglik(Yd, init) - l_judge_p)
+            rms_p[N] = float(np.sqrt(np.mean(np.square(errs))))
+        ok_p = [N for N in ladder if rms_p[N] <= e_sur_p]
+        n_eq_p = min(ok_p) if ok_p else max(ladder)
 
     sampler = ClockSampler(torch.cuda.current_device())
     sampler.start()
@@ -624,8 +640,15 @@ def run_surrogate(args):
     ctx_p = binding.Context(synth.make_lattice(n_eq, 4, seed=0), precision=binding.CFUST_FP32,
                             max_iter=args.warmup + args.steps + 1, use_graph=True, timing=True, triage_nats=tn)
     ms_p, kern_p, _ = _timed_em(torch, ctx_p, Yd, init, args.steps, args.warmup, flush)
-    clocks = sampler.stop()
     ctx_p.close()
+    ms_q = None
+    if n_eq_p is not None:
+        ctx_q = binding.Context(synth.make_lattice(n_eq_p, 4, seed=0), precision=binding.CFUST_FP32,
+                                max_iter=args.warmup + args.steps + 1, use_graph=True, timing=True,
+                                triage_nats=tn, prioritise=True)
+        ms_q, _, _ = _timed_em(torch, ctx_q, Yd, init, args.steps, args.warmup, flush)
+        ctx_q.close()
+    clocks = sampler.stop()
 
     # end to end through the public API with the surrogate attached
     Yh = torch.from_numpy(Y).pin_memory()
@@ -678,6 +701,12 @@ def run_surrogate(args):
         "plain_at_equal_accuracy": {"lattice_points": n_eq, "value": pairs / step_p, "ms_per_step": step_p * 1e3,
                                     "em_iters_per_s": 1.0 / step_p, "sweep_ms": float(np.mean(kern_p))},
         "speedup_vs_plain_at_equal_accuracy": step_p / step_s,
+        "prioritised_plain": ({
+            "judge": "65536-point rule, prioritised order",
+            "surrogate_loglik_error": l_sur - l_judge_p, "plain_rms_by_points": rms_p,
+            "lattice_points_at_equal_accuracy": n_eq_p,
+            "ms_per_step": float(np.mean(ms_q)), "value": pairs / (float(np.mean(ms_q)) / 1e3),
+            "speedup_of_surrogate": float(np.mean(ms_q)) / 1e3 / step_s} if ms_q is not None else None),
         "fallback_pairs": int(fallback), "fallback_fraction": fallback / pairs,
         # per EM iteration: precompute, network kernel, list sweep, rescue,
         # posterior/sums, log-likelihood reduce, finalize

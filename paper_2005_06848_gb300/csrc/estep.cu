@@ -200,9 +200,11 @@ struct PrioSlot {
 // -q_t / sqrt(Lambda_tt) (pass B's limits are a positive multiple of pass
 // A's, so one order serves both), ties keeping the lower index, with the
 // Cholesky factor of the permuted Lambda.  The order is decided in double
-// from the double prologue, as the oracle decides it.  Not inlined: its
-// dynamically indexed arrays stay out of the sweep's registers.
-template <int R>
+// from the double prologue, as the oracle decides it; the factor is formed
+// in the sweep's precision T (double work costs 64 times single on this GPU,
+// and the single-precision sweep rounds the factor to float anyway).  Not
+// inlined: its dynamically indexed arrays stay out of the sweep's registers.
+template <int R, typename T>
 __device__ __noinline__ void prio_setup(const double *q, const double *lam, const double *lamd, PrioSlot *s) {
   int ord[R];
   double key[R];
@@ -222,19 +224,20 @@ __device__ __noinline__ void prio_setup(const double *q, const double *lam, cons
     key[u + 1] = k;
     ord[u + 1] = o;
   }
-  double Lm[R * R];
+  T Lm[R * R];
   for (int t = 0; t < R; ++t)
     for (int h = 0; h <= t; ++h) {
       const int x = ord[t] > ord[h] ? ord[t] : ord[h], y = ord[t] > ord[h] ? ord[h] : ord[t];
-      Lm[t * R + h] = lam[x * (x + 1) / 2 + y];
+      Lm[t * R + h] = static_cast<T>(lam[x * (x + 1) / 2 + y]);
     }
   for (int j = 0; j < R; ++j) {
-    double d = Lm[j * R + j];
+    T d = Lm[j * R + j];
     for (int k = 0; k < j; ++k) d -= Lm[j * R + k] * Lm[j * R + k];
-    d = sqrt(fmax(d, 1e-300));  // a permutation of a positive definite Lambda stays so
+    // a permutation of a positive definite Lambda stays so
+    d = Num<T>::sq(d > T(0) ? d : static_cast<T>(sizeof(T) == 4 ? 1e-30 : 1e-300));
     Lm[j * R + j] = d;
     for (int i = j + 1; i < R; ++i) {
-      double v = Lm[i * R + j];
+      T v = Lm[i * R + j];
       for (int k = 0; k < j; ++k) v -= Lm[i * R + k] * Lm[j * R + k];
       Lm[i * R + j] = v / d;
     }
@@ -242,13 +245,54 @@ __device__ __noinline__ void prio_setup(const double *q, const double *lam, cons
   for (int t = 0; t < R; ++t) {
     s->ord[t] = ord[t];
     s->q[t] = q[ord[t]];
-    s->Li[t] = 1.0 / Lm[t * R + t];
+    const T li = T(1) / Lm[t * R + t];
+    s->Li[t] = (double)li;
     for (int h = 0; h <= t; ++h) {
-      s->L[t * (t + 1) / 2 + h] = Lm[t * R + h];
-      const float v = -(float)Lm[t * R + h] * (float)s->Li[t];
+      s->L[t * (t + 1) / 2 + h] = (double)Lm[t * R + h];
+      const float v = -(float)Lm[t * R + h] * (float)li;
       s->pc.nL[t * (t + 1) / 2 + h] = make_float2(v, v);
     }
   }
+}
+
+// The same order and factor held per lane: in a warp's chunk of pairs every
+// lane prepares its own pair (as it computes its prologue), and the warp
+// takes pair b's values by shuffles when it sweeps it.  ord packs the
+// original coordinate of position t in bits 3t .. 3t + 2.
+template <int R, typename T>
+struct PrioLane {
+  T q[R];
+  T L[R * (R + 1) / 2];
+  T Li[R];
+  int ord;
+};
+
+template <int R, typename T>
+__device__ __noinline__ void prio_lane(const double *q, const double *lam, const double *lamd, PrioLane<R, T> *o) {
+  PrioSlot s;
+  prio_setup<R, T>(q, lam, lamd, &s);
+  int packed = 0;
+  for (int t = 0; t < R; ++t) {
+    packed |= s.ord[t] << (3 * t);
+    o->q[t] = static_cast<T>(s.q[t]);
+    o->Li[t] = static_cast<T>(s.Li[t]);
+    for (int h = 0; h <= t; ++h) o->L[t * (t + 1) / 2 + h] = static_cast<T>(s.L[t * (t + 1) / 2 + h]);
+  }
+  o->ord = packed;
+}
+
+template <int R, typename T>
+__device__ __forceinline__ PrioLane<R, T> shfl_prio(const PrioLane<R, T> &m, int src) {
+  PrioLane<R, T> o;
+#pragma unroll
+  for (int t = 0; t < R; ++t) {
+    o.q[t] = __shfl_sync(0xffffffffu, m.q[t], src);
+    o.Li[t] = __shfl_sync(0xffffffffu, m.Li[t], src);
+  }
+#pragma unroll
+  for (int k = 0; k < R * (R + 1) / 2; ++k) o.L[k] = __shfl_sync(0xffffffffu, m.L[k], src);
+  o.ord = __shfl_sync(0xffffffffu, m.ord, src);
+  return o;
 }
 
 // Lattice constants of coordinate t for the double-precision sweep (the
@@ -307,12 +351,13 @@ __device__ __forceinline__ Prologue<R> shfl_prologue(const Prologue<R> &mine, in
 // One (i, j) pair on one warp, its prologue given.  Returns true (uniformly
 // over the warp) when `check` is set and the single-precision sweep needs the
 // double rescue; in that case nothing is written.
-template <typename T, typename OT, int R, bool DENS>
+template <typename T, typename OT, int R, bool DENS, bool PRIO = false>
 __device__ __forceinline__ bool pair_sweep(const EArgs &a, const FitView &fv, const CompT<T> &c,
                                            const Prologue<R> &pr,
                                            const T *__restrict__ tA, const T *__restrict__ tB,
                                            int i, int64_t j, int lane, bool check,
-                                           const PairedConsts *pc, PrioSlot *slot) {
+                                           const PairedConsts *pc, PairedConsts *wpc,
+                                           const PrioLane<R, T> *pp) {
   using M = Num<T>;
   constexpr int RP = R * (R + 1) / 2;
   constexpr bool PAIRED = (sizeof(T) == 4) && !DENS;
@@ -340,28 +385,40 @@ __device__ __forceinline__ bool pair_sweep(const EArgs &a, const FitView &fv, co
 #pragma unroll
     for (int h = 0; h <= t; ++h) Lc[t * (t + 1) / 2 + h] = c.L[t * RMAX + h];
   }
-  // variable prioritisation: lane 0 orders the coordinates and factors the
-  // permuted Lambda into this warp's slot; the sweep then runs in that order
-  // and the moments are stored back at their original coordinates
+  // variable prioritisation: the pair's order and permuted factor (prepared
+  // lane-parallel with the prologues); the sweep runs in that order and the
+  // moments are stored back at their original coordinates
   int ord[R];
 #pragma unroll
   for (int t = 0; t < R; ++t) ord[t] = t;
   const PairedConsts *pcu = pc;
-  if (a.prio) {
-    __syncwarp();  // every lane is done with the slot's previous pair
-    if (lane == 0) prio_setup<R>(pr.q, c.lam, c.lamd, slot);
-    __syncwarp();
+  if constexpr (PRIO) {
 #pragma unroll
     for (int t = 0; t < R; ++t) {
-      ord[t] = slot->ord[t];
-      q[t] = static_cast<T>(slot->q[t]);
+      ord[t] = (pp->ord >> (3 * t)) & 7;
+      q[t] = pp->q[t];
       aA[t] = -q[t] * fA;
       aB[t] = -q[t] * fB;
-      Li[t] = static_cast<T>(slot->Li[t]);
+      Li[t] = pp->Li[t];
 #pragma unroll
-      for (int h = 0; h <= t; ++h) Lc[t * (t + 1) / 2 + h] = static_cast<T>(slot->L[t * (t + 1) / 2 + h]);
+      for (int h = 0; h <= t; ++h) Lc[t * (t + 1) / 2 + h] = pp->L[t * (t + 1) / 2 + h];
     }
-    pcu = &slot->pc;
+    if constexpr (PAIRED) {
+      // the paired loop reads -L_th / L_tt from shared memory: this warp's slot
+      __syncwarp();  // every lane is done with the slot's previous pair
+#pragma unroll
+      for (int t = 1; t < R; ++t)
+#pragma unroll
+        for (int h = 0; h < t; ++h) {
+          const int k = t * (t + 1) / 2 + h;
+          if (lane == k) {
+            const float v = -(float)Lc[k] * (float)Li[t];
+            wpc->nL[k] = make_float2(v, v);
+          }
+        }
+      __syncwarp();
+      pcu = wpc;
+    }
   }
   // paired operands: (pass A, pass B) limits; -L and 1/L_tt pairs come from shared memory
   // (pass A, pass B) limits over L_tt: with the staged -L_th / L_tt the
@@ -593,20 +650,26 @@ __device__ __forceinline__ bool pair_sweep(const EArgs &a, const FitView &fv, co
 // computes the double prologue of the b-th observation, then the warp sweeps
 // them one at a time.  `qi` is the component index recorded for queued pairs
 // (the fit's own index, or the global one in a batch).
-template <typename T, int R, bool DENS>
+template <typename T, int R, bool DENS, bool PRIO = false>
 __device__ __forceinline__ void sweep_warp_pairs(const EArgs &a, const FitView &fv, const CompT<T> &c,
                                                  const PairedConsts *pcs, const T *tA, const T *tB,
-                                                 int i, int qi, int64_t jw0, int ppw, PrioSlot *slot) {
+                                                 int i, int qi, int64_t jw0, int ppw, PairedConsts *wpc) {
   const int lane = threadIdx.x & 31;
   int cnt = 0;
   if (jw0 < fv.n) cnt = (int)((fv.n - jw0) < ppw ? (fv.n - jw0) : ppw);
   Prologue<R> mine;
   if (lane < cnt) mine = prologue<T, R>(a, fv, c, jw0 + lane);
+  PrioLane<R, T> pmine;
+  if constexpr (PRIO) {
+    if (lane < cnt) prio_lane<R, T>(mine.q, c.lam, c.lamd, &pmine);
+  }
   const bool check = (sizeof(T) == 4);
   for (int b = 0; b < cnt; ++b) {
     const Prologue<R> pr = shfl_prologue<R>(mine, b);
+    PrioLane<R, T> pp;
+    if constexpr (PRIO) pp = shfl_prio<R, T>(pmine, b);
     const int64_t j = jw0 + b;
-    const bool need = pair_sweep<T, T, R, DENS>(a, fv, c, pr, tA, tB, i, j, lane, check, pcs, slot);
+    const bool need = pair_sweep<T, T, R, DENS, PRIO>(a, fv, c, pr, tA, tB, i, j, lane, check, pcs, wpc, &pp);
     if (need && lane == 0) {
       const unsigned slot = atomicAdd(a.rescue_count, 1u);
       a.rescue_list[slot] = pair_id(qi, j);
@@ -663,7 +726,7 @@ __device__ __forceinline__ bool stage_block(const EArgs &a, int i, unsigned char
   return true;
 }
 
-template <typename T, int R, bool DENS>
+template <typename T, int R, bool DENS, bool PRIO>
 __global__ void __launch_bounds__(256, sizeof(T) == 4 ? CFUST_ESTEP_MINB : 1) estep_kernel(EArgs a) {
   extern __shared__ __align__(128) unsigned char smem[];
   const int i = blockIdx.y;
@@ -674,13 +737,13 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? CFUST_ESTEP_MINB : 1) es
   const int warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
   const int64_t jw0 = ((int64_t)blockIdx.x * nw + warp) * a.ppw;
   // with prioritisation, one order-and-factor slot per warp after the staged constants
-  PrioSlot *slot = nullptr;
-  if (a.prio) {
+  PairedConsts *wpc = nullptr;
+  if constexpr (PRIO) {
     const size_t tab_bytes = a.staged ? (size_t)(DENS ? 1 : 2) * a.N * sizeof(T) : 0;
-    slot = reinterpret_cast<PrioSlot *>(smem + align16(tab_bytes) + align16(sizeof(CompT<T>)) +
-                                        align16(sizeof(PairedConsts)) + 16) + warp;
+    wpc = reinterpret_cast<PairedConsts *>(smem + align16(tab_bytes) + align16(sizeof(CompT<T>)) +
+                                           align16(sizeof(PairedConsts)) + 16) + warp;
   }
-  sweep_warp_pairs<T, R, DENS>(a, fit_view(a), *cs, pcs, tA, tB, i, i, jw0, a.ppw, slot);
+  sweep_warp_pairs<T, R, DENS, PRIO>(a, fit_view(a), *cs, pcs, tA, tB, i, i, jw0, a.ppw, wpc);
 }
 
 // Triage of a listed pair (single precision outputs): with log f of every
@@ -746,7 +809,8 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? CFUST_ESTEP_MINB : 1)
       if ((skipped >> b) & 1u) continue;
       const Prologue<R> pr = shfl_prologue<R>(mine, b);
       const int64_t j = __shfl_sync(0xffffffffu, myj, b);
-      const bool need = pair_sweep<T, T, R, DENS>(a, fv, *cs, pr, tA, tB, i, j, lane, check, pcs, nullptr);
+      const bool need = pair_sweep<T, T, R, DENS>(a, fv, *cs, pr, tA, tB, i, j, lane, check, pcs, nullptr,
+                                                  nullptr);
       if (need && lane == 0) {
         const unsigned slot = atomicAdd(a.rescue_count, 1u);
         a.rescue_list[slot] = pair_id(i, j);
@@ -832,7 +896,7 @@ __device__ void pair_sweep_log_cta(const EArgs &a, const FitView &fv, const Comp
     // so the rescued pair is integrated by the same rule
     __shared__ PrioSlot rslot;
     __syncthreads();
-    if (threadIdx.x == 0) prio_setup<R>(pr.q, c.lam, c.lamd, &rslot);
+    if (threadIdx.x == 0) prio_setup<R, double>(pr.q, c.lam, c.lamd, &rslot);
     __syncthreads();
 #pragma unroll
     for (int t = 0; t < R; ++t) {
@@ -1058,9 +1122,14 @@ cudaError_t launch_r(EArgs a, int g, int64_t n, cudaStream_t st, bool fp32,
   const size_t tab_bytes = (size_t)(DENS ? 1 : 2) * a.N * sizeof(T);
   a.staged = tab_bytes <= 160u * 1024u ? 1 : 0;
   const size_t smem = (a.staged ? align16(tab_bytes) : 0) + align16(sizeof(CompT<T>)) +
-                      align16(sizeof(PairedConsts)) + 16 + (a.prio ? 8 * sizeof(PrioSlot) : 0);
-  cudaError_t e = cudaFuncSetAttribute(estep_kernel<T, R, DENS>,
-                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+                      align16(sizeof(PairedConsts)) + 16 + (a.prio ? 8 * sizeof(PairedConsts) : 0);
+  // the prioritised sweep is its own instantiation (r >= 2), so the default
+  // one carries none of its registers
+  const bool prio = a.prio && R >= 2;
+  cudaError_t e = prio ? cudaFuncSetAttribute(estep_kernel<T, R, DENS, (R >= 2)>,
+                                              cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)
+                       : cudaFuncSetAttribute(estep_kernel<T, R, DENS, false>,
+                                              cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   const int64_t per_cta = (int64_t)a.ppw * 8;
   const int64_t bx = (n + per_cta - 1) / per_cta;
@@ -1075,7 +1144,10 @@ cudaError_t launch_r(EArgs a, int g, int64_t n, cudaStream_t st, bool fp32,
     e = cudaEventRecordWithFlags(tm.start, st, evflag);
     if (e != cudaSuccess) return e;
   }
-  estep_kernel<T, R, DENS><<<grid, 256, smem, st>>>(a);
+  if (prio)
+    estep_kernel<T, R, DENS, (R >= 2)><<<grid, 256, smem, st>>>(a);
+  else
+    estep_kernel<T, R, DENS, false><<<grid, 256, smem, st>>>(a);
   e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   if (tm.stop) {
