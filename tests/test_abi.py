@@ -88,3 +88,37 @@ def test_surrogate_create_rejects_bad_lattice_without_a_device():
     assert lib.cfust_surrogate_create(ctypes.byref(h), 1, ctypes.byref(lat), None) == -1
     assert b"dim 4" in lib.cfust_surrogate_last_error(None)
     assert lib.cfust_surrogate_create(ctypes.byref(h), 1, None, None) == -1
+
+
+def test_ctypes_structs_match_the_c_header_layout(tmp_path):
+    """The binding's ctypes mirrors of cfust_params, cfust_lattice and
+    cfust_opts have the C header's size and field offsets (a field added on
+    one side only would shift every later option silently)."""
+    import shutil
+    import subprocess
+    if shutil.which("gcc") is None:
+        import pytest
+        pytest.skip("no C compiler")
+    structs = {"cfust_params": binding.cfust_params, "cfust_lattice": binding.cfust_lattice,
+               "cfust_opts": binding.cfust_opts}
+    lines = ['#include <stddef.h>', '#include <stdio.h>', '#include "cfust.h"', "int main(void) {"]
+    for name, cls in structs.items():
+        lines.append(f'  printf("{name} size %zu\\n", sizeof({name}));')
+        for field, _ in cls._fields_:
+            lines.append(f'  printf("{name} {field} %zu\\n", offsetof({name}, {field}));')
+    lines += ["  return 0;", "}"]
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines) + "\n")
+    exe = tmp_path / "layout"
+    include = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "include")
+    subprocess.run(["gcc", "-std=c99", "-I", include, str(src), "-o", str(exe)], check=True)
+    out = subprocess.run([str(exe)], check=True, capture_output=True, text=True).stdout.split("\n")
+    got = {}
+    for line in out:
+        if line.strip():
+            parts = line.split()
+            got[tuple(parts[:-1])] = int(parts[-1])
+    for name, cls in structs.items():
+        assert got[(name, "size")] == ctypes.sizeof(cls), name
+        for field, _ in cls._fields_:
+            assert got[(name, field)] == getattr(cls, field).offset, (name, field)
