@@ -257,6 +257,51 @@ def cpu_baseline(rows: int = 1024):
             (Ys, init, E, P1))
 
 
+def _oracle_estep_rows(args):
+    """One worker's share of the all-core baseline: the oracle's E-step of
+    observations [j0, j1) of the bench workload (module-level so a spawned
+    worker can import it)."""
+    j0, j1 = args
+    from oracle import cfust_oracle as O
+    from paper_2005_06848_gb300 import synth
+    Y, _, _, init, lat, _ = synth.workload(WORKLOAD)
+    U = O.lattice_points(lat.n, lat.z, lat.shift)
+    t0 = time.perf_counter()
+    O.estep(Y[j0:j1], init, U)
+    return time.perf_counter() - t0
+
+
+def cpu_baseline_all_cores(rows_per_core: int = 256):
+    """The same oracle E-step spread over every host core (a spawn-context
+    process pool, one contiguous block of rows per worker): pairs per second
+    of wall time across the pool.  Returns None with the reason when the pool
+    cannot run here."""
+    import multiprocessing as mp
+    cores = os.cpu_count() or 1
+    try:
+        from paper_2005_06848_gb300 import synth
+        g = synth.WORKLOADS[WORKLOAD]["g"]
+        n = synth.WORKLOADS[WORKLOAD]["n"]
+        blocks = [(k * rows_per_core, (k + 1) * rows_per_core) for k in range(cores)]
+        blocks = [b for b in blocks if b[1] <= n]
+        # spawned workers inherit the one-thread BLAS/OpenMP settings made at
+        # the top of this module, so each process is one core
+        ctx = mp.get_context("spawn")
+        # bounded waits: a worker that dies would leave a plain map waiting;
+        # leaving the block terminates the pool
+        with ctx.Pool(len(blocks)) as pool:
+            pool.map_async(_oracle_estep_rows, [(0, 8)] * len(blocks)).get(timeout=120)  # start-up, untimed
+            t0 = time.perf_counter()
+            pool.map_async(_oracle_estep_rows, blocks).get(timeout=120)
+            dt = time.perf_counter() - t0
+        pairs = len(blocks) * rows_per_core * g
+        return {"value": pairs / dt, "unit": UNIT, "cores": len(blocks), "kind": "oracle",
+                "sample": f"{len(blocks)} x {rows_per_core} observations x {g} components, E-step only, "
+                          f"one spawned process per core, {dt:.1f} s wall"}
+    except Exception as exc:  # the single-core baseline stands on its own
+        return {"unavailable": f"{type(exc).__name__}: {exc}"[:200]}
+
+
 def fp32_error_vs_oracle(ref, lat, stream):
     """The FP32 path's error against the FP64 oracle on the baseline's sample,
     stated per result: log f, tau, e1..e4, the log-likelihood and the M-step
@@ -465,6 +510,8 @@ def run_ours(args):
     if not args.no_cpu_baseline:
         line["cpu_baseline"], ref = cpu_baseline(args.cpu_rows)
         line["fp32_error_vs_oracle"] = fp32_error_vs_oracle(ref, lat, stream)
+        if ws == 1:
+            line["cpu_baseline_all_cores"] = cpu_baseline_all_cores()
     print(json.dumps(line), flush=True)
     if ws > 1:
         torch.distributed.destroy_process_group()
