@@ -49,34 +49,37 @@ L2_FLUSH_BYTES = 256 << 20
 # difference, ~1e-9 relative, is far below the errors it judges)
 JUDGE_POINTS = 1 << 16
 
-# Algorithmic cost model of one lattice point of one pair (flop-equivalents,
-# one per FP32 add / multiply / compare, two per fused multiply-add), used for
-# the achieved throughput of the sweep kernel.  PHI and PHIINV are the costs
-# of one single-precision normal CDF and inverse-CDF evaluation.
+# Algorithmic work of one lattice point of one pair, counted as the hot-path
+# table states it: 2r normal-tail evaluations (Phi), 2r - 1 normal quantiles
+# (Phi^-1), r(r - 1) conditional-limit FMAs and r + r(r+1)/2 moment FMAs over
+# the two passes, in FP32 flop-equivalents (an FMA is 2).  PHI_FLOPS and
+# PHIINV_FLOPS convert one Phi and one Phi^-1 evaluation into flop-equivalents;
+# they are derived from the sweep kernel's measured FP32 instruction mix
+# (profiles/estep_kernel_p4r4g3_n100000_N4096.md).
 PHI_FLOPS = 24
 PHIINV_FLOPS = 30
 
 
 def sweep_flops_per_point(r: int, density_only: bool = False) -> int:
-    """Flop-equivalents of both separation-of-variables passes at one point."""
-    lattice = 4 * r                                   # 1 - u: add, abs, mul, clamp per coordinate
-    cond = r * (r - 1)                                # sum_{h<t} L_th z_h as FMAs
-    pass_a = r * (PHI_FLOPS + 3) + cond + (r - 1) * (PHIINV_FLOPS + 1) + 1
+    """Flop-equivalents of one lattice point of one pair (both passes, or pass A alone)."""
     if density_only:
-        return lattice + pass_a
-    rp = r * (r + 1) // 2
-    pass_b = r * (PHI_FLOPS + 3) + cond + r * (PHIINV_FLOPS + 1) + 1 + 1 + 2 * r + r + 2 * rp
-    return lattice + pass_a + pass_b
+        return r * PHI_FLOPS + (r - 1) * PHIINV_FLOPS + r * (r - 1)
+    return 2 * r * PHI_FLOPS + (2 * r - 1) * PHIINV_FLOPS + 2 * r * (r - 1) + 2 * (r + r * (r + 1) // 2)
 
 
-def peak_fp32_tflops(sm_mhz: float) -> float:
-    """152 SMs x 128 FP32 lanes x 2 flops per FMA x clock."""
-    return 152 * 128 * 2 * sm_mhz * 1e6 / 1e12
+def sm_count() -> int:
+    import torch
+    return int(torch.cuda.get_device_properties(torch.cuda.current_device()).multi_processor_count)
 
 
-def sweep_traffic_bytes():
-    """DRAM bytes per sweep launch from the committed ncu capture, or None when
-    the sweep sources changed since those counters were taken."""
+def peak_fp32_tflops(sm_mhz: float, sms: int) -> float:
+    """FP32 FMA peak: SMs x 128 FP32 lanes x 2 flops per FMA x clock."""
+    return sms * 128 * 2 * sm_mhz * 1e6 / 1e12
+
+
+def sweep_profile():
+    """The committed ncu record of one sweep launch, or None when the sweep
+    sources changed since it was taken."""
     import hashlib
     try:
         with open(os.path.join(ROOT, "profiles", "estep_kernel_p4r4g3_n100000_N4096.json")) as f:
@@ -87,9 +90,17 @@ def sweep_traffic_bytes():
                 h.update(f.read())
         if h.hexdigest() != rec["source_sha256"]:
             return None
-        return int(rec["dram_bytes_read"]) + int(rec["dram_bytes_write"])
+        return rec
     except Exception:
         return None
+
+
+def sweep_traffic_bytes():
+    """DRAM bytes per sweep launch from the committed ncu capture (None when stale)."""
+    rec = sweep_profile()
+    if rec is None:
+        return None
+    return int(rec["dram_bytes_read"]) + int(rec["dram_bytes_write"])
 
 
 def accuracy_vs_judge(torch, binding, synth, Yd, P, lat, stream, r, pairs):
@@ -132,10 +143,10 @@ def accuracy_vs_judge(torch, binding, synth, Yd, P, lat, stream, r, pairs):
     return out
 
 
-def mstep_roofline(n, g, p, r, ms, peaks):
+def mstep_roofline(n, g, p, r, ms, peaks, sms):
     """Achieved HBM bandwidth of the posterior / M-step sums kernel."""
     K = 3 + p + r + p * r + r * (r + 1) // 2 + p * (p + 1) // 2
-    nblk = min((n + 63) // 64, 152 * 4)
+    nblk = min((n + 63) // 64, sms * 4)
     nbytes = n * g * 4 * (3 + r + r * (r + 1) // 2) + n * p * 8 + nblk * g * K * 8
     hbm = (peaks or {}).get("hbm_gbs")
     gbs = nbytes / (ms / 1e3) / 1e9
@@ -309,6 +320,10 @@ def fp32_error_vs_oracle(ref, lat, stream):
     import torch
     from paper_2005_06848_gb300 import binding
     Ys, init, E, P1 = ref
+    if P1 is None:
+        from oracle import cfust_oracle as O
+        S = O.mstep_sums(Ys, E["tau"], E["e1"], E["e2"], E["e3"], E["e4"])
+        P1 = O.mstep_update(S, init, Ys.shape[0])
     Yd = torch.from_numpy(Ys).cuda()
     with binding.Context(lat, precision=binding.CFUST_FP32, stream=stream) as ctx:
         G = ctx.cfust_estep(Yd, init)
@@ -335,6 +350,97 @@ def fp32_error_vs_oracle(ref, lat, stream):
         "mstep_params_max_rel": max(rel(a, b) for a, b in zip(P1g.as_arrays(), P1.as_arrays())),
         "params_tol": 1e-3,
     }
+
+
+def _oracle_estep_block(args):
+    """One spawned worker: the oracle's E-step of rows [j0, j1) of a named
+    workload (module-level so a spawned process can import it)."""
+    name, j0, j1 = args
+    from oracle import cfust_oracle as O
+    from paper_2005_06848_gb300 import synth
+    Y, _, _, init, lat, _ = synth.workload(name)
+    U = O.lattice_points(lat.n, lat.z, lat.shift)
+    t0 = time.perf_counter()
+    E = O.estep(Y[j0:j1], init, U)
+    return E, time.perf_counter() - t0
+
+
+def oracle_estep_pool(name, rows):
+    """The oracle's E-step of the first `rows` observations of a workload on
+    every host core (a spawn-context pool, one contiguous block per worker).
+    Returns (E for those rows, wall seconds, workers)."""
+    import multiprocessing as mp
+    cores = max(1, min(os.cpu_count() or 1, rows))
+    edges = [rows * k // cores for k in range(cores + 1)]
+    blocks = [(name, edges[k], edges[k + 1]) for k in range(cores) if edges[k + 1] > edges[k]]
+    ctx = mp.get_context("spawn")
+    with ctx.Pool(len(blocks)) as pool:
+        pool.map_async(_oracle_estep_block, [(name, 0, 4)] * len(blocks)).get(timeout=300)  # start-up, untimed
+        t0 = time.perf_counter()
+        parts = pool.map_async(_oracle_estep_block, blocks).get(timeout=900)
+        wall = time.perf_counter() - t0
+    E = {}
+    for k in ("logf", "tau", "e1", "e2", "e3", "e4"):
+        E[k] = np.concatenate([P[0][k] for P in parts], axis=1)
+    E["loglik"] = float(sum(P[0]["loglik"] for P in parts))
+    return E, wall, len(blocks)
+
+
+C5_WORKLOAD = "cfust_p8r4g6_n1000000_N8192"
+
+
+def large_line(args, steps, warmup):
+    """The large fit (p=8, r=4, g=6, n=10^6, 8192-point lattice, FP32 sweeps):
+    EM iterations timed like the default line, and the oracle on a subsample
+    of the same rows on every host core, which gives both the oracle's rate and
+    the FP32 path's error per result.  The learned form covers r = 3 only."""
+    import torch
+    from paper_2005_06848_gb300 import binding, synth
+    Y, _, truth, init, lat, meta = synth.workload(C5_WORKLOAD)
+    n, g, p, r = meta["n"], meta["g"], meta["p"], meta["r"]
+    Yd = torch.from_numpy(Y).cuda()
+    stream = torch.cuda.current_stream()
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
+    ctx = binding.Context(lat, precision=binding.CFUST_FP32, max_iter=warmup + steps + 1, use_graph=True,
+                          timing=True, stream=stream)
+    sampler = ClockSampler(torch.cuda.current_device())
+    sampler.start()
+    time.sleep(0.4)
+    ms, kern, params = _timed_em(torch, ctx, Yd, init, steps, warmup, flush)
+    clocks = sampler.stop()
+    ctx.close()
+    pairs = n * g
+    step_s = float(np.mean(ms)) / 1e3
+    sweep_ms = float(np.mean(kern))
+    peaks = load_peaks() or {}
+    sm_max = peaks.get("sm_max_mhz", 2070.0)
+    flops = pairs * lat.n * sweep_flops_per_point(r)
+    achieved = flops / (sweep_ms / 1e3) / 1e12
+    peak = peak_fp32_tflops(sm_max, sm_count())
+    rows = args.c5_oracle_rows
+    E, wall, cores = oracle_estep_pool(C5_WORKLOAD, rows)
+    err = fp32_error_vs_oracle((Y[:rows], init, E, None), lat, stream)
+    return {
+        "workload": C5_WORKLOAD, "n": n, "g": g, "p": p, "r": r, "lattice_points": lat.n,
+        "value": pairs / step_s, "unit": UNIT, "ms_per_step": step_s * 1e3, "em_iters_per_s": 1.0 / step_s,
+        "steps": steps, "warmup": warmup, "dtype": "f32",
+        "step": "one EM iteration (CUDA graph replay), L2 flushed between timed steps",
+        "roofline": {"bound": "alu", "kernel": "estep_kernel<float,4>", "achieved": achieved, "peak": peak,
+                     "unit": "TFLOP/s", "frac": achieved / peak, "sweep_ms_mean": sweep_ms,
+                     "flops_per_point": sweep_flops_per_point(r)},
+        "oracle": {"value": rows * g / wall, "unit": UNIT, "cores": cores, "kind": "oracle",
+                   "sample": f"first {rows} of {n} observations x {g} components, E-step, one spawned "
+                             f"process per core, {wall:.1f} s wall"},
+        "fp32_error_vs_oracle": err,
+        "surrogate": "not applicable: the learned form covers r = 3 and this workload has r = 4",
+        "clocks": clocks,
+        "gpu_launches": 6 * steps,
+    }
+
+
+def run_large(args):
+    print(json.dumps(large_line(args, args.steps, args.warmup)), flush=True)
+    return 0
 
 
 def run_reference(args):
@@ -388,7 +494,7 @@ def run_ours(args):
         torch.cuda.set_device(0)
     dev = torch.cuda.current_device()
 
-    Y, _, truth, init, lat, meta = synth.workload(WORKLOAD, seed=rank)
+    Y, _, truth, init, lat, meta = synth.workload(WORKLOAD, seed=rank, n=args.rows or None)
     n, g, p, r = meta["n"], meta["g"], meta["p"], meta["r"]
     Yd = torch.from_numpy(Y).cuda()
     stream = torch.cuda.current_stream()
@@ -440,7 +546,9 @@ def run_ours(args):
     achieved = flops / (mean_sweep_ms / 1e3) / 1e12
     peaks = load_peaks()
     sm_max = (peaks or {}).get("sm_max_mhz", 2070.0)
-    peak = peak_fp32_tflops(sm_max)
+    sms = sm_count()
+    peak = peak_fp32_tflops(sm_max, sms)
+    prof = sweep_profile() or {}
 
     # end-to-end through the public API: every step copies Y from pinned host
     # memory into the bound device buffer, runs one EM iteration, and reads the
@@ -492,9 +600,17 @@ def run_ours(args):
         "gpu_launches": 6 * args.steps,
         "roofline": {"bound": "alu", "kernel": "estep_kernel<float,4>", "achieved": achieved,
                      "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak, "traffic": sweep_traffic_bytes(),
-                     "peak_source": f"FP32 FMA peak 152 SMs x 128 lanes x 2 x {sm_max:.0f} MHz (derived)",
+                     "peak_source": f"FP32 FMA peak {sms} SMs x 128 lanes x 2 x {sm_max:.0f} MHz "
+                                    "(derived from unit counts and the maximum SM clock)",
                      "sweep_ms_mean": mean_sweep_ms,
-                     "flops_per_launch": flops},
+                     "flops_per_launch": flops,
+                     "flops_per_point": sweep_flops_per_point(r),
+                     "count": f"per point: 2r Phi x {PHI_FLOPS} + (2r-1) Phi^-1 x {PHIINV_FLOPS} "
+                              "+ r(r-1) conditional FMAs + (r + r(r+1)/2) moment FMAs, FMA = 2 flops",
+                     "ncu": {k: prof[k] for k in ("fma_pipe_pct", "xu_pipe_pct", "issue_active_pct",
+                                                  "fp32_flop_eq_per_point", "xu_inst_per_point")
+                             if k in prof} or None},
+        "sm_count": sms,
         # accuracy of the timed rule against a 65536-point prioritised rule
         # on the same data, in natural and prioritised variable order
         "accuracy": accuracy_vs_judge(torch, binding, synth, Yd, init, lat, stream, r, pairs_per_step)
@@ -503,7 +619,7 @@ def run_ours(args):
         # outputs read once (log f, e1, e2, e3, e4 in float) + Y once (double)
         # + the per-block partial sums written once; the kernel is bound by
         # its double-precision-accurate arithmetic, not by these bytes
-        "mstep": mstep_roofline(n, g, p, r, float(np.mean(mstep_ms)), peaks),
+        "mstep": mstep_roofline(n, g, p, r, float(np.mean(mstep_ms)), peaks, sms),
         "clocks": clocks,
         "e2e": e2e,
     }
@@ -512,6 +628,18 @@ def run_ours(args):
         line["fp32_error_vs_oracle"] = fp32_error_vs_oracle(ref, lat, stream)
         if ws == 1:
             line["cpu_baseline_all_cores"] = cpu_baseline_all_cores()
+    if ws == 1 and not args.no_extras:
+        # the metric's comparisons on the other synthetic workloads, each
+        # measured in this same run: batched fits, the learned form against
+        # the plain rule at equal log-likelihood accuracy, the large fit
+        extras = {}
+        for key, fn in (("batched_256_fits", batched_line), ("learned_form", surrogate_line),
+                        ("large_fit", large_line)):
+            try:
+                extras[key] = fn(args, 5, 3)
+            except Exception as exc:  # one workload's failure is reported, not hidden
+                extras[key] = {"error": f"{type(exc).__name__}: {exc}"[:300]}
+        line["workloads"] = extras
     print(json.dumps(line), flush=True)
     if ws > 1:
         torch.distributed.destroy_process_group()
@@ -519,7 +647,13 @@ def run_ours(args):
 
 
 def run_batched(args):
-    """Batched-fits workload (one JSON line, not the default bench): 256
+    print(json.dumps(batched_line(args, args.steps, args.warmup)), flush=True)
+    return 0
+
+
+def batched_line(args, steps, warmup):
+    """Batched-fits workload (its own JSON line with --workload batched, and a
+    key of the default line): 256
     independent fits, p=3, r=3, n log-uniform in [5000, 200000], g in 2..5,
     2048-point lattice, FP32 sweeps; one step = one EM iteration of every fit
     (one persistent sweep launch inside one CUDA graph).  The timed call runs
@@ -534,11 +668,11 @@ def run_batched(args):
     stream = torch.cuda.current_stream()
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
     # warm-up call: autotune, buffers, graph capture
-    with binding.Context(lat, precision=binding.CFUST_FP32, max_iter=args.warmup, autotune=True,
+    with binding.Context(lat, precision=binding.CFUST_FP32, max_iter=warmup, autotune=True,
                          stream=stream) as ctx:
         ctx.cfust_fit_batched(Yd, inits)
         ppw, cps = ctx.cfust_batched_shape()
-    ctx = binding.Context(lat, precision=binding.CFUST_FP32, max_iter=args.steps, pairs_per_warp=ppw,
+    ctx = binding.Context(lat, precision=binding.CFUST_FP32, max_iter=steps, pairs_per_warp=ppw,
                           stream=stream)
     ctx.cfust_fit_batched(Yd, inits)            # buffers + graph for this iteration count
     flush.zero_()
@@ -556,22 +690,21 @@ def run_batched(args):
     ms = ev0.elapsed_time(ev1)
     ctx.close()
     line = {
-        "metric": METRIC, "value": pairs * args.steps / (ms / 1e3), "unit": UNIT, "n_gpus": 1,
-        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
+        "metric": METRIC, "value": pairs * steps / (ms / 1e3), "unit": UNIT, "n_gpus": 1,
+        "steps": steps, "warmup": warmup, "ms_per_step": ms / steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "config": {"workload": f"batched_{args.nfits}fits_p3r3_n5000-200000_g2-5_N2048",
                    "pairs_per_iteration": int(pairs), "pairs_per_warp": ppw, "ctas_per_sm": cps,
                    "step": "one EM iteration of every fit; the timed call adds one final density sweep",
                    "l2": "inputs larger than L2"},
-        "fit_iters_per_s": args.nfits * args.steps / (ms / 1e3),
+        "fit_iters_per_s": args.nfits * steps / (ms / 1e3),
         # per iteration: precompute, persistent sweep, rescue, posterior/sums,
         # log-likelihood reduce, finalize; then one density pass (five kernels)
-        "gpu_launches": 6 * args.steps + 5,
+        "gpu_launches": 6 * steps + 5,
         "clocks": clocks,
         "fits_failed": int(sum(1 for s in st if s != 0)),
     }
-    print(json.dumps(line), flush=True)
-    return 0
+    return line
 
 
 def _loglik_ms(torch, ctx, Yd, P, reps=3):
@@ -610,7 +743,40 @@ def _timed_em(torch, ctx, Yd, P, steps, warmup, flush):
 
 
 def run_surrogate(args):
-    """Learned-surrogate workload (one JSON line, not the default bench):
+    print(json.dumps(surrogate_line(args, args.steps, args.warmup)), flush=True)
+    return 0
+
+
+LADDER = [32, 64, 128, 256, 512, 1024, 2048]
+LADDER_SHIFTS = 8
+
+
+def _accuracy_ladder(binding, synth, Yd, P, l_judge, tn, prioritise, target):
+    """Log-likelihood error of the plain lattice rule at each size of LADDER,
+    over LADDER_SHIFTS independent shifts of the same lattice (randomised QMC,
+    cfust_loglik_shifts): RMS, mean and the mean's standard error per size.
+    The size of equal accuracy is the smallest whose RMS error, and that of
+    every larger size, is at most `target` (the largest size when none is)."""
+    out = {}
+    for N in LADDER:
+        shifts = np.stack([synth.make_lattice(N, 4, seed=sd).shift for sd in range(LADDER_SHIFTS)])
+        with binding.Context(synth.make_lattice(N, 4, seed=0), precision=binding.CFUST_FP32, triage_nats=tn,
+                             prioritise=prioritise) as c:
+            errs = np.asarray(c.cfust_loglik_shifts(Yd, P, shifts)) - l_judge
+        out[N] = {"rms": float(np.sqrt(np.mean(np.square(errs)))), "mean": float(np.mean(errs)),
+                  "se": float(np.std(errs, ddof=1) / math.sqrt(len(errs)))}
+    n_eq = max(LADDER)
+    for N in reversed(LADDER):
+        if out[N]["rms"] <= target:
+            n_eq = N
+        else:
+            break
+    return out, n_eq
+
+
+def surrogate_line(args, steps, warmup):
+    """Learned-surrogate workload (its own JSON line with --workload
+    surrogate, and a key of the default line):
     p=3, r=3, g=4, n=10^6.  The network (7 -> 128 x 3 -> 10, BF16, GELU) is
     trained on the GPU on 20M problems labelled by the lattice rule at 8192
     points (timed apart).  Its E-step log-likelihood error against the plain
@@ -627,7 +793,7 @@ def run_surrogate(args):
     from paper_2005_06848_gb300 import binding, synth
     torch.cuda.set_device(0)
     name = "cfust_p3r3g4_n1000000_N2048"
-    Y, _, truth, init, _, meta = synth.workload(name, seed=0)
+    Y, _, truth, init, _, meta = synth.workload(name, seed=0, n=args.rows or None)
     n, g = meta["n"], meta["g"]
     Yd = torch.from_numpy(Y).cuda()
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
@@ -641,7 +807,7 @@ def run_surrogate(args):
 
     tn = args.sg_triage
     ctx_s = binding.Context(synth.make_lattice(args.sg_fallback_n, 4, seed=0), precision=binding.CFUST_FP32,
-                            max_iter=args.warmup + args.steps + 1, use_graph=True, timing=True, triage_nats=tn)
+                            max_iter=warmup + steps + 1, use_graph=True, timing=True, triage_nats=tn)
     ctx_s.cfust_set_surrogate(sur)
     l_sur, _ = _loglik_ms(torch, ctx_s, Yd, init)
     fallback = ctx_s.cfust_last_fallback()
@@ -654,46 +820,29 @@ def run_surrogate(args):
         l_judge = judge.cfust_loglik(Yd, init)
         judge.close()
         e_sur = abs(l_sur - l_judge)
-        ladder = [32, 64, 128, 256, 512, 1024, 2048]
-        for N in ladder:
-            errs = []
-            for sd in range(3):
-                with binding.Context(synth.make_lattice(N, 4, seed=sd), precision=binding.CFUST_FP32,
-                                     triage_nats=tn) as c:
-                    errs.append(c.cfust_loglik(Yd, init) - l_judge)
-            rms[N] = float(np.sqrt(np.mean(np.square(errs))))
-        ok_n = [N for N in ladder if rms[N] <= e_sur]
-        n_eq = min(ok_n) if ok_n else max(ladder)
+        rms, n_eq = _accuracy_ladder(binding, synth, Yd, init, l_judge, tn, False, e_sur)
         # the plain rule with variable prioritisation, judged by the
         # prioritised 65536-point rule (the surrogate judged by it too)
         with binding.Context(synth.make_lattice(JUDGE_POINTS, 4, seed=0), precision=binding.CFUST_FP32,
                              prioritise=True) as judge_p:
             l_judge_p = judge_p.cfust_loglik(Yd, init)
         e_sur_p = abs(l_sur - l_judge_p)
-        for N in ladder:
-            errs = []
-            for sd in range(3):
-                with binding.Context(synth.make_lattice(N, 4, seed=sd), precision=binding.CFUST_FP32,
-                                     triage_nats=tn, prioritise=True) as c:
-                    errs.append(c.cfust_loglik(Yd, init) - l_judge_p)
-            rms_p[N] = float(np.sqrt(np.mean(np.square(errs))))
-        ok_p = [N for N in ladder if rms_p[N] <= e_sur_p]
-        n_eq_p = min(ok_p) if ok_p else max(ladder)
+        rms_p, n_eq_p = _accuracy_ladder(binding, synth, Yd, init, l_judge_p, tn, True, e_sur_p)
 
     sampler = ClockSampler(torch.cuda.current_device())
     sampler.start()
     time.sleep(0.4)
-    ms_s, kern_s, _ = _timed_em(torch, ctx_s, Yd, init, args.steps, args.warmup, flush)
+    ms_s, kern_s, _ = _timed_em(torch, ctx_s, Yd, init, steps, warmup, flush)
     ctx_p = binding.Context(synth.make_lattice(n_eq, 4, seed=0), precision=binding.CFUST_FP32,
-                            max_iter=args.warmup + args.steps + 1, use_graph=True, timing=True, triage_nats=tn)
-    ms_p, kern_p, _ = _timed_em(torch, ctx_p, Yd, init, args.steps, args.warmup, flush)
+                            max_iter=warmup + steps + 1, use_graph=True, timing=True, triage_nats=tn)
+    ms_p, kern_p, _ = _timed_em(torch, ctx_p, Yd, init, steps, warmup, flush)
     ctx_p.close()
     ms_q = None
     if n_eq_p is not None:
         ctx_q = binding.Context(synth.make_lattice(n_eq_p, 4, seed=0), precision=binding.CFUST_FP32,
-                                max_iter=args.warmup + args.steps + 1, use_graph=True, timing=True,
+                                max_iter=warmup + steps + 1, use_graph=True, timing=True,
                                 triage_nats=tn, prioritise=True)
-        ms_q, _, _ = _timed_em(torch, ctx_q, Yd, init, args.steps, args.warmup, flush)
+        ms_q, _, _ = _timed_em(torch, ctx_q, Yd, init, steps, warmup, flush)
         ctx_q.close()
     clocks = sampler.stop()
 
@@ -730,8 +879,8 @@ def run_surrogate(args):
     peak = peaks.get("bf16_tflops_sustained") or peaks.get("bf16_tflops") or 1700.0
     achieved = flops / (kern_ms / 1e3) / 1e12
     line = {
-        "metric": METRIC, "value": pairs / step_s, "unit": UNIT, "n_gpus": 1, "steps": args.steps,
-        "warmup": args.warmup, "ms_per_step": step_s * 1e3, "higher_is_better": True, "scaling": "weak",
+        "metric": METRIC, "value": pairs / step_s, "unit": UNIT, "n_gpus": 1, "steps": steps,
+        "warmup": warmup, "ms_per_step": step_s * 1e3, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "bf16 network, f32 lattice fallback", "data": "synthetic",
         "config": {"workload": name + "_surrogate", "n": n, "g": g, "p": 3, "r": 3,
                    "network": "7-128-128-128-10 GELU, BF16 weights/activations, FP32 accumulation",
@@ -743,21 +892,22 @@ def run_surrogate(args):
                    "step": "one EM iteration (CUDA graph replay) from the same start",
                    "l2": "flushed between timed steps"},
         "em_iters_per_s": 1.0 / step_s,
-        "loglik_error_vs_65536_point_rule": ({"surrogate": l_sur - l_judge, "plain_rms_by_points": rms}
+        "loglik_error_vs_65536_point_rule": ({"surrogate": l_sur - l_judge, "plain_by_points": rms,
+                                             "shifts": LADDER_SHIFTS}
                                             if l_judge is not None else None),
         "plain_at_equal_accuracy": {"lattice_points": n_eq, "value": pairs / step_p, "ms_per_step": step_p * 1e3,
                                     "em_iters_per_s": 1.0 / step_p, "sweep_ms": float(np.mean(kern_p))},
         "speedup_vs_plain_at_equal_accuracy": step_p / step_s,
         "prioritised_plain": ({
             "judge": "65536-point rule, prioritised order",
-            "surrogate_loglik_error": l_sur - l_judge_p, "plain_rms_by_points": rms_p,
+            "surrogate_loglik_error": l_sur - l_judge_p, "plain_by_points": rms_p,
             "lattice_points_at_equal_accuracy": n_eq_p,
             "ms_per_step": float(np.mean(ms_q)), "value": pairs / (float(np.mean(ms_q)) / 1e3),
             "speedup_of_surrogate": float(np.mean(ms_q)) / 1e3 / step_s} if ms_q is not None else None),
         "fallback_pairs": int(fallback), "fallback_fraction": fallback / pairs,
         # per EM iteration: precompute, network kernel, list sweep, rescue,
         # posterior/sums, log-likelihood reduce, finalize
-        "gpu_launches": 7 * args.steps,
+        "gpu_launches": 7 * steps,
         "roofline": {"bound": "tensor", "kernel": "surrogate_estep_kernel<false>", "achieved": achieved,
                      "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak, "traffic": None,
                      "peak_source": "measured cuBLAS bf16 (MEASURED_PEAKS.json)" if peaks else "fallback 1.7 PFLOP/s",
@@ -767,8 +917,7 @@ def run_surrogate(args):
                 "d2h_bytes_per_step": int(8 * len(tr)),
                 "path": "cfust_fit_step with the surrogate attached; Y copied from pinned host memory each step"},
     }
-    print(json.dumps(line), flush=True)
-    return 0
+    return line
 
 
 def main(argv=None):
@@ -782,7 +931,11 @@ def main(argv=None):
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-accuracy", action="store_true",
                     help="skip the accuracy comparison against the 65536-point rule")
-    ap.add_argument("--workload", choices=["single", "batched", "surrogate"], default="single")
+    ap.add_argument("--workload", choices=["single", "batched", "surrogate", "large"], default="single")
+    ap.add_argument("--no-extras", action="store_true",
+                    help="default workload only: skip the batched, learned-form and large-fit measurements")
+    ap.add_argument("--c5-oracle-rows", type=int, default=10000,
+                    help="observations of the large fit the oracle recomputes on the host cores")
     ap.add_argument("--sg-train", type=int, default=20_000_000)
     ap.add_argument("--sg-epochs", type=int, default=100)
     ap.add_argument("--sg-fallback-n", type=int, default=128)
@@ -792,6 +945,9 @@ def main(argv=None):
                     help="triage margin T (nats) of the surrogate and plain contexts: a listed or rescued "
                          "pair with tau provably below exp(-T) is dropped, moving l by at most exp(-T)")
     ap.add_argument("--nfits", type=int, default=256)
+    ap.add_argument("--rows", type=int, default=0,
+                    help="observations of the single-fit workload (0: the workload's 100000); for small "
+                         "profiling captures only, the bench line is quoted at the default")
     args = ap.parse_args(argv)
     if args.warmup < 3:
         args.warmup = 3
@@ -801,6 +957,8 @@ def main(argv=None):
         return run_batched(args)
     if args.workload == "surrogate":
         return run_surrogate(args)
+    if args.workload == "large":
+        return run_large(args)
     return run_ours(args)
 
 

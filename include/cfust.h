@@ -111,8 +111,15 @@ typedef struct {
                              decreasing order of the standardised limit -q_t / sqrt(Lambda_tt) (ties
                              keep the lower index) with the Cholesky factor of the permuted Lambda;
                              the moments come back in the original order.  Same integral, much
-                             smaller lattice error for pairs in the tails.  Single fits only:
-                             CFUST_EINVAL with a surrogate attached or in cfust_fit_batched. */
+                             smaller lattice error for pairs in the tails.  Every lattice sweep takes
+                             it: single and batched fits, and the pairs a surrogate leaves to the
+                             lattice rule (the network's own pairs are not integrated). */
+  int test_wait_polls;    /* for tests of the timeout path only; 0 in normal use.  The lattice sweeps
+                             stage a component's chi tables with an asynchronous bulk copy and wait on
+                             its completion for a bounded number of polls (2^22 by default) before they
+                             give up with CFUST_ETIMEOUT; k > 0 sets that bound, -1 makes the wait give
+                             up at once.  On giving up a block first lets its copy land (bounded by the
+                             default), then returns: no fault, no hang, the context stays usable. */
 } cfust_opts;
 
 typedef struct cfust_ctx cfust_ctx;
@@ -148,6 +155,37 @@ cfust_status cfust_estep(cfust_ctx *ctx, const double *Y, int64_t n,
 cfust_status cfust_mstep(cfust_ctx *ctx, const double *Y, int64_t n,
                          const void *tau, const void *e1, const void *e2,
                          const void *e3, const void *e4, cfust_params *params);
+
+/* The M-step split at its one exchange point, for fits whose observations
+ * are spread over several processes or devices (Algorithm 2's per-worker
+ * partial sums, Section 3.2, and Algorithm 3's combine by the master,
+ * Section 3.3): every worker runs cfust_estep on its own rows and
+ * cfust_mstep_sums on them; the workers add their sums vectors (e.g. one
+ * all-reduce of g K doubles) and every worker runs cfust_mstep_apply on the
+ * totals, which gives each the same parameters.
+ *
+ * cfust_mstep_sums: the eight per-component sums of Section 3.2 over this
+ * call's n observations into sums (host, [g][K] doubles, K = 3 + p + r + p r
+ * + r(r+1)/2 + p(p+1)/2), component i's vector at i K:
+ *   S1 = sum tau, S2 = sum tau e1, S3[a] = sum tau e1 y_a (p entries),
+ *   S4[t] = sum tau e3_t (r), S5[a][t] = sum tau y_a e3_t (p r, a-major),
+ *   S6 = sum tau e4 (packed lower triangle, r(r+1)/2), S7 = sum tau e1 y y^T
+ *   (packed lower triangle, p(p+1)/2), S8 = sum tau (e2 - e1).
+ * Inputs as for cfust_mstep; params: host, read only (its g, p, r give the
+ * shapes).  Synchronises.
+ *
+ * cfust_mstep_apply: Algorithm 3's conditional-maximisation update (the
+ * same update as cfust_mstep) from sums (host [g][K], the totals over every
+ * worker's rows) and the total number of observations n_total; params (host)
+ * in: the current parameters (Delta enters the mu update), out: the update.
+ * CFUST_ENUMERIC when a sum is not finite.  Synchronises.  Summing the
+ * workers' vectors in another order changes the result only by rounding. */
+cfust_status cfust_mstep_sums(cfust_ctx *ctx, const double *Y, int64_t n,
+                              const void *tau, const void *e1, const void *e2,
+                              const void *e3, const void *e4, const cfust_params *params,
+                              double *sums);
+cfust_status cfust_mstep_apply(cfust_ctx *ctx, const double *sums, int64_t n_total,
+                               cfust_params *params);
 
 /* Full EM (Section 2 outline) from params (updated in place): at most
  * opts.max_iter iterations, stopping early by Algorithm 4 when opts.tol > 0.
@@ -206,8 +244,7 @@ cfust_status cfust_batched_shape(cfust_ctx *ctx, int *pairs_per_warp, int *ctas_
  * burned-in parameters; starts[*best] the fitted ones).  trace and iters_done
  * as for cfust_fit, for the final fit.  Starts that fail their burn-in
  * (degenerate, not positive definite) are not chosen; CFUST_EDEGENERATE when
- * none survives.  The burn-in runs as a batched fit, so a context with
- * opts.prioritise refuses burn_in > 0 (CFUST_EINVAL). */
+ * none survives.  The burn-in runs as a batched fit. */
 cfust_status cfust_fit_multistart(cfust_ctx *ctx, const double *Y, int64_t n, cfust_params *starts, int nstarts,
                                   int burn_in, int *best, double *loglik_trace, int *iters_done);
 
@@ -315,10 +352,11 @@ cfust_status cfust_normal_f32(const float *x, float *out, int64_t n, int which, 
  * routine is called.
  *
  * precision: CFUST_FP64 or CFUST_FP32 (element type of tau, e1..e4).
- * Y, tau, e1..e4: device, layouts as for cfust_estep.  params: host, updated
- * in place.  nu_min, nu_max: 0, 0 selects [1, 200].  stream: cudaStream_t
- * (NULL = legacy default stream).  Synchronises the stream.  Messages come
- * from cfust_last_error(NULL). */
+ * Y, tau, e1..e4: device memory of the CURRENT device (checked: CFUST_EINVAL
+ * otherwise), layouts as for cfust_estep; stream: a cudaStream_t of that
+ * device (NULL = legacy default stream).  params: host, updated in place.
+ * nu_min, nu_max: 0, 0 selects [1, 200].  Synchronises the stream.  Messages
+ * come from cfust_last_error(NULL), which keeps one message per host thread. */
 #define CFUST_NOALLOC_SCRATCH_BYTES (1u << 20)
 #define CFUST_NOALLOC_MIN_BLOCKS 8
 cfust_status cfust_mstep_noalloc(int precision, const double *Y, int64_t n,
@@ -336,7 +374,8 @@ cfust_status cfust_mstep_noalloc(int precision, const double *Y, int64_t n,
  * entries) and the degrees of freedom m:
  *   X ~ t_3(0, R, m):  log P(X > c),  E[X | X > c],  E[X X^T | X > c].
  * A network 7 -> 128 -> 128 -> 128 -> 10 (GELU, BF16 weights and activations,
- * FP32 accumulation on the tensor cores) maps
+ * FP32 accumulation on the tensor cores: tcgen05 MMAs with accumulators in
+ * tensor memory for prediction and the E-step) maps
  *   x = (c_1, c_2, c_3, R_12, R_13, R_23, log m)
  * to y = (log P, E[X_1..3], E[X X^T] upper triangle 11 12 13 22 23 33).
  * Training domain: -8 <= c_t <= 4, |R_ht| <= 0.9, squared Cholesky pivots of
@@ -439,11 +478,25 @@ cfust_status cfust_set_surrogate(cfust_ctx *ctx, cfust_surrogate *s);
 cfust_status cfust_surrogate_problems(cfust_ctx *ctx, const double *Y, int64_t n, const cfust_params *P,
                                       int64_t stride, float *x_out, int64_t max_rows, int64_t *rows);
 
+/* Both network inputs of every (i, j) pair exactly as the surrogate E-step
+ * hands them to the tensor cores at params P, for verification: the
+ * standardised problem of pass A (dof nu+p) and pass B (nu+p+2), normalised
+ * (c and log m mapped from their ranges onto [-1, 1], R / 0.9) and rounded to
+ * BF16, written as floats to x_out (device float [g][n][2][7], pair (i, j) at
+ * (i n + j)); kind (device int32 [g][n]) receives the pair's class: 2 the
+ * network's, 1 its point leaves the box (lattice rule, log T bounded through
+ * the clamped point), 0 R or the dof outside the domain (lattice rule).
+ * Requires r = 3; Y as for cfust_estep.  Synchronises the context's stream. */
+cfust_status cfust_surrogate_inputs(cfust_ctx *ctx, const double *Y, int64_t n, const cfust_params *P,
+                                    float *x_out, int32_t *kind);
+
 /* Pairs the last surrogate E-step handed to the lattice rule (outside the
  * training domain).  Synchronises the context's stream. */
 cfust_status cfust_last_fallback(cfust_ctx *ctx, int64_t *count);
 
-/* Message for the last error on ctx (or on context creation when ctx is NULL). */
+/* Message for the last error on ctx; with ctx NULL, the message of the last
+ * failed cfust_create or cfust_mstep_noalloc call of the calling host thread
+ * (kept per thread). */
 const char *cfust_last_error(cfust_ctx *ctx);
 
 #ifdef __cplusplus

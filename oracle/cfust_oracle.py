@@ -227,8 +227,10 @@ def estep_component(Y, mu, Sigma, Delta, nu, U, e2_mode=0, density_only=False,
     e3 [n, r], e4 [n, r, r].  e2_mode 0 uses the usual CFUST-EM approximation
     e2 = e1 - log((nu+d)/2) - (nu+p)/(nu+d) + psi((nu+p)/2) (exact at Delta = 0);
     e2_mode 1 uses the lattice estimate E[log chi^2_{nu+p}] - log(nu+d) from
-    the density pass.  Reading: where T_A or T_B is 0 (underflow), log f is
-    -inf and e1..e4 are set to 0, their weight tau being 0.  ``prioritise``
+    the density pass.  Reading: where T_A or T_B underflows (is 0 or below the
+    smallest normal double, where its subnormal value keeps too few bits for
+    the pair's outputs to be determined), log f is -inf (T_A) and e1..e4 are
+    set to 0, their weight tau being 0.  ``prioritise``
     integrates each pair's variables in the order of ``prioritised_order``
     (pass B's limits are a positive multiple of pass A's: the same order).
     """
@@ -256,7 +258,10 @@ def estep_component(Y, mu, Sigma, Delta, nu, U, e2_mode=0, density_only=False,
         TA, elogchi, TB, LEV, LEVVL = _passes(aA, aB, L, Lam, mA, mB, U, sA, sB, logchi, density_only,
                                               prioritise)
         with np.errstate(divide="ignore"):
-            logf[sl] = r * LOG2 + log_tp[sl] + np.log(TA)
+            # a probability below the smallest normal double counts as
+            # underflowed (reading: subnormal values carry too few bits to
+            # take part in the rule), so log f = -inf there
+            logf[sl] = r * LOG2 + log_tp[sl] + np.log(np.where(TA >= TINY64, TA, 0.0))
         if density_only:
             continue
         c1, c2, c3, c4 = expectations(dd, qq, nu, p, TA, TB, LEV, LEVVL, e2_mode,
@@ -281,11 +286,13 @@ def expectations(d, q, nu, p, TA, TB, LEV, LEVVL, e2_mode=0, elogchi=None):
     e1 = (nu+p)/(nu+d) T_B/T_A, sigma = sqrt((nu+d)/(nu+p+2)),
     e3 = e1 (q + sigma L E[V]),
     e4 = e1 (q q^T + sigma (q (L E[V])^T + L E[V] q^T) + sigma^2 L E[V V^T] L^T),
-    e2 as in estep_component.  Pairs with T_A or T_B = 0 get zeros.
+    e2 as in estep_component.  Pairs with T_A or T_B underflowed (below the
+    smallest normal double) get zeros.
     """
     mA = nu + p
     mB = nu + p + 2.0
-    ok = (TA > 0) & (TB > 0)
+    # underflow: T_A or T_B below the smallest normal double (see estep_component)
+    ok = (TA >= TINY64) & (TB >= TINY64)
     with np.errstate(invalid="ignore", divide="ignore"):
         if math.isinf(nu):
             # W = 1: both passes integrate the same normal law

@@ -28,7 +28,7 @@ EXPORTED = ["cfust_create", "cfust_destroy", "cfust_loglik", "cfust_estep", "cfu
             "cfust_surrogate_set_params", "cfust_surrogate_train", "cfust_surrogate_last_error",
             "cfust_set_surrogate", "cfust_last_fallback", "cfust_surrogate_problems",
             "cfust_surrogate_finetune", "cfust_fit_multistart", "cfust_kmeans", "cfust_init_partition",
-            "cfust_multistart_partitions", "cfust_loglik_shifts", "cfust_last_mstep_ms"]
+            "cfust_multistart_partitions", "cfust_loglik_shifts", "cfust_last_mstep_ms", "cfust_mstep_sums", "cfust_mstep_apply", "cfust_surrogate_inputs"]
 
 SURROGATE_NPARAM = 35338
 
@@ -56,7 +56,8 @@ class cfust_opts(ctypes.Structure):
                 ("nu_min", ctypes.c_double), ("nu_max", ctypes.c_double),
                 ("max_iter", ctypes.c_int), ("tol", ctypes.c_double), ("use_graph", ctypes.c_int),
                 ("timing", ctypes.c_int), ("pairs_per_warp", ctypes.c_int), ("autotune", ctypes.c_int),
-                ("triage_nats", ctypes.c_double), ("prioritise", ctypes.c_int)]
+                ("triage_nats", ctypes.c_double), ("prioritise", ctypes.c_int),
+                ("test_wait_polls", ctypes.c_int)]
 
 
 _LIB = None
@@ -121,6 +122,9 @@ def load(build_if_missing: bool = True, path: str | None = None) -> ctypes.CDLL:
         "cfust_multistart_partitions": ([vp, vp, i64, vp, ctypes.c_int, ctypes.c_double, ctypes.c_double,
                                          ctypes.c_int, P, ctypes.POINTER(ctypes.c_int), dp,
                                          ctypes.POINTER(ctypes.c_int)], ctypes.c_int),
+        "cfust_surrogate_inputs": ([vp, vp, i64, P, vp, vp], ctypes.c_int),
+        "cfust_mstep_sums": ([vp, vp, i64, vp, vp, vp, vp, vp, P, dp], ctypes.c_int),
+        "cfust_mstep_apply": ([vp, dp, i64, P], ctypes.c_int),
         "cfust_surrogate_finetune": ([vp, vp, i64, ctypes.c_int, ctypes.c_int, ctypes.c_float, ctypes.c_uint64,
                                       ctypes.POINTER(ctypes.c_float)], ctypes.c_int),
     }
@@ -157,12 +161,35 @@ def _ptr(t):
     return ctypes.c_void_p(0 if t is None else t.data_ptr())
 
 
+def _check_mstep_inputs(Y, E, params, dtype):
+    """Shapes, dtypes, contiguity and device of the M-step's device inputs
+    (Y [n][p] float64; tau, e1, e2 [g][n], e3 [g][r][n], e4 [g][r(r+1)/2][n]
+    in the E-step's element type), so that a mismatch raises here instead of
+    letting a kernel read past a buffer."""
+    import torch
+    g, r = params.g, params.r
+    p = params.mu.shape[1]
+    if Y.dim() != 2 or Y.shape[1] != p or Y.dtype != torch.float64:
+        raise ValueError(f"Y must be float64 [n][{p}], got {Y.dtype} {tuple(Y.shape)}")
+    n = Y.shape[0]
+    want = {"tau": (g, n), "e1": (g, n), "e2": (g, n), "e3": (g, r, n), "e4": (g, r * (r + 1) // 2, n)}
+    dev = torch.device("cuda", torch.cuda.current_device())
+    for k, shp in want.items():
+        t = E[k]
+        if tuple(t.shape) != shp or t.dtype != dtype:
+            raise ValueError(f"{k} must be {dtype} {shp}, got {t.dtype} {tuple(t.shape)}")
+    for k, t in [("Y", Y)] + [(k, E[k]) for k in want]:
+        if not t.is_contiguous() or t.device != dev:
+            raise ValueError(f"{k} must be contiguous and on the current CUDA device {dev}")
+    return n
+
+
 class Context:
     """A cfust_ctx bound to the current CUDA device and a torch stream."""
 
     def __init__(self, lattice, precision=CFUST_FP32, e2_mode=0, nu_min=0.0, nu_max=0.0,
                  max_iter=0, tol=0.0, use_graph=True, timing=False, pairs_per_warp=0, autotune=False,
-                 stream=None, triage_nats=0.0, prioritise=False):
+                 stream=None, triage_nats=0.0, prioritise=False, test_wait_polls=0):
         import torch
         self.lib = load()
         self._z = np.ascontiguousarray(lattice.z, dtype=np.int64)
@@ -173,7 +200,7 @@ class Context:
         self.opts = cfust_opts(int(precision), lat, int(e2_mode), float(nu_min), float(nu_max),
                                int(max_iter), float(tol), 1 if use_graph else 0, 1 if timing else 0,
                                int(pairs_per_warp), 1 if autotune else 0, float(triage_nats),
-                               1 if prioritise else 0)
+                               1 if prioritise else 0, int(test_wait_polls))
         self.precision = int(precision)
         self.stream = stream if stream is not None else torch.cuda.current_stream()
         self.lattice_n = int(lattice.n)
@@ -242,9 +269,30 @@ class Context:
         return out
 
     def cfust_mstep(self, Y, E, params):
+        _check_mstep_inputs(Y, E, params, self.dtype)
         hp = _HostParams(params)
         self._check(self.lib.cfust_mstep(self.h, _ptr(Y), Y.shape[0], _ptr(E["tau"]), _ptr(E["e1"]),
                                          _ptr(E["e2"]), _ptr(E["e3"]), _ptr(E["e4"]), ctypes.byref(hp.c)))
+        return hp.to_params()
+
+    def cfust_mstep_sums(self, Y, E, params):
+        """The eight per-component sums over Y's rows: float64 [g][K] (numpy)."""
+        _check_mstep_inputs(Y, E, params, self.dtype)
+        hp = _HostParams(params)
+        sums = np.zeros((params.g, sums_width(params.mu.shape[1], params.r)))
+        self._check(self.lib.cfust_mstep_sums(self.h, _ptr(Y), Y.shape[0], _ptr(E["tau"]), _ptr(E["e1"]),
+                                              _ptr(E["e2"]), _ptr(E["e3"]), _ptr(E["e4"]), ctypes.byref(hp.c),
+                                              sums.ctypes.data_as(ctypes.POINTER(ctypes.c_double))))
+        return sums
+
+    def cfust_mstep_apply(self, sums, n_total, params):
+        """Algorithm 3's update from sums totalled over every worker's rows."""
+        hp = _HostParams(params)
+        sums = np.ascontiguousarray(sums, dtype=np.float64)
+        if sums.shape != (params.g, sums_width(params.mu.shape[1], params.r)):
+            raise ValueError(f"sums must be [g][K], got {sums.shape}")
+        self._check(self.lib.cfust_mstep_apply(self.h, sums.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
+                                               int(n_total), ctypes.byref(hp.c)))
         return hp.to_params()
 
     def cfust_fit(self, Y, params, max_iter=None):
@@ -391,6 +439,17 @@ class Context:
         self._check(self.lib.cfust_last_fallback(self.h, ctypes.byref(v)))
         return v.value
 
+    def cfust_surrogate_inputs(self, Y, params):
+        """Both network inputs of every pair as the surrogate E-step forms them:
+        (x [g][n][2][7] float32 (BF16-rounded), kind [g][n] int32) on the device."""
+        import torch
+        n, g = Y.shape[0], params.g
+        x = torch.empty((g, n, 2, 7), dtype=torch.float32, device=Y.device)
+        kind = torch.empty((g, n), dtype=torch.int32, device=Y.device)
+        hp = _HostParams(params)
+        self._check(self.lib.cfust_surrogate_inputs(self.h, _ptr(Y), n, ctypes.byref(hp.c), _ptr(x), _ptr(kind)))
+        return x, kind
+
     def cfust_surrogate_problems(self, Y, params, stride=1, max_rows=None):
         """Standardised problems (float32 CUDA tensor [rows, 7]) of every
         stride-th pair in the surrogate's domain at `params` (r = 3)."""
@@ -507,6 +566,9 @@ def cfust_mstep_noalloc(precision, Y, E, params, nu_min=0.0, nu_max=0.0, stream=
     """M-step through the allocation-free entry point (no context; scratch in a
     static device array, see include/cfust.h).  Returns the updated params."""
     import torch
+    if precision not in (CFUST_FP64, CFUST_FP32):
+        raise ValueError("precision must be CFUST_FP64 or CFUST_FP32")
+    _check_mstep_inputs(Y, E, params, torch.float64 if precision == CFUST_FP64 else torch.float32)
     lib = load()
     hp = _HostParams(params)
     st = stream if stream is not None else torch.cuda.current_stream()
@@ -516,6 +578,11 @@ def cfust_mstep_noalloc(precision, Y, E, params, nu_min=0.0, nu_max=0.0, stream=
     if rc != 0:
         raise CfustError(rc, lib.cfust_last_error(None).decode())
     return hp.to_params()
+
+
+def sums_width(p, r):
+    """Doubles in one component's sums vector (S1..S8 of Section 3.2)."""
+    return 3 + p + r + p * r + r * (r + 1) // 2 + p * (p + 1) // 2
 
 
 def unpack_e4(e4, r):

@@ -20,7 +20,7 @@ LIBDIR = os.path.join(PKG, "_lib")
 LIB = os.path.join(LIBDIR, "libcfust.so")
 
 SOURCES = ["api.cu", "precompute.cu", "estep.cu", "mstep.cu", "surrogate.cu", "init.cu"]
-HEADERS = ["cfust_internal.cuh", "special.cuh", "normal_f32.cuh", "normal_f32_coeffs.cuh"]
+HEADERS = ["cfust_internal.cuh", "special.cuh", "normal_f32.cuh", "normal_f32_coeffs.cuh", "tcgen05.cuh"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr",
          "-I", INCLUDE, "-I", CSRC]

@@ -13,6 +13,25 @@
 
 using namespace cfust;
 
+namespace cfust {
+
+int sm_count() {
+  constexpr int kDevices = 64;
+  static int cached[kDevices] = {};
+  static std::mutex m;
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kDevices) dev = -1;
+  std::lock_guard<std::mutex> lock(m);
+  if (dev >= 0 && cached[dev] > 0) return cached[dev];
+  int sms = 0;
+  if (dev < 0 || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || sms < 1)
+    return 1;  // no device answers: one SM's worth of blocks, the launch itself will report the error
+  cached[dev] = sms;
+  return sms;
+}
+
+}  // namespace cfust
+
 struct cfust_ctx {
   int device = 0;
   cudaStream_t stream = nullptr;
@@ -36,6 +55,7 @@ struct cfust_ctx {
   int trace_cap = 0;
   unsigned long long *d_rescue = nullptr;
   double *d_partials = nullptr;
+  double *d_sums = nullptr;     // [g][K] totals of cfust_mstep_sums
   double *d_llpart = nullptr;
   void *d_logf = nullptr, *d_e1 = nullptr, *d_e2 = nullptr, *d_e3 = nullptr, *d_e4 = nullptr;
 
@@ -150,6 +170,7 @@ cfust_status ensure(cfust_ctx *c, int g, int p, int r, int64_t n) {
     CF_CUDA(c, realloc_dev(&c->d_c32, sizeof(CompT<float>) * g));
     CF_CUDA(c, realloc_dev(&c->d_chi64, sizeof(double) * 2 * (size_t)N * g));
     CF_CUDA(c, realloc_dev(&c->d_chi32, sizeof(float) * 2 * (size_t)N * g));
+    CF_CUDA(c, realloc_dev(&c->d_sums, sizeof(double) * (size_t)g * sums_width(p, r)));
     c->g = g;
     c->p = p;
     c->r = r;
@@ -354,11 +375,12 @@ cfust_status run_estep(cfust_ctx *c, const double *Y, int64_t n, EstepOut o, boo
   const unsigned evflag = tm.capturing ? cudaEventRecordExternal : cudaEventRecordDefault;
   if (tm.start) CF_CUDA(c, cudaEventRecordWithFlags(tm.start, st, evflag));
   CF_CUDA(c, launch_surrogate_estep(surrogate_dev(c->sur), Y, n, c->g, c->p, c->d_c32, o, density_only,
-                                    c->d_fb, c->d_fb_cnt, st));
+                                    c->d_fb, c->d_fb_cnt, c->d_status, st));
   if (tm.stop) CF_CUDA(c, cudaEventRecordWithFlags(tm.stop, st, evflag));
   CF_CUDA(c, launch_estep_list(Y, n, c->g, c->p, c->r, c->lat, c->d_c64, c->d_c32, c->d_chi64, c->d_chi32, o,
                                density_only, c->opts.e2_mode, c->d_fb, c->d_fb_cnt, c->d_rescue,
-                               c->d_rescue_cnt, c->d_status, st, triage, pi, (float)c->opts.triage_nats));
+                               c->d_rescue_cnt, c->d_status, st, triage, pi, (float)c->opts.triage_nats,
+                               c->opts.prioritise));
   return CFUST_OK;
 }
 
@@ -456,8 +478,13 @@ cfust_status cfust_create(cfust_ctx **out, const cfust_opts *o, void *cuda_strea
     g_create_error = "triage_nats must be 0 (default 30) or in [1, 700]";
     return CFUST_EINVAL;
   }
+  if (o->test_wait_polls < -1) {
+    g_create_error = "test_wait_polls must be -1, 0 or positive";
+    return CFUST_EINVAL;
+  }
   cfust_ctx *c = new cfust_ctx();
   c->opts = *o;
+  c->lat.wait_polls = o->test_wait_polls == 0 ? (1 << 22) : (o->test_wait_polls < 0 ? 0 : o->test_wait_polls);
   c->opts.lattice.z = nullptr;
   c->opts.lattice.shift = nullptr;
   if (c->opts.triage_nats == 0.0) c->opts.triage_nats = 30.0;
@@ -533,7 +560,7 @@ cfust_status cfust_destroy(cfust_ctx *c) {
   void *bufs[] = {c->d_params, c->d_c64, c->d_c32, c->d_chi64, c->d_chi32, c->d_status,
                   c->d_rescue_cnt, c->d_ll, c->d_trace, c->d_rescue, c->d_partials, c->d_llpart,
                   c->d_logf, c->d_e1, c->d_e2, c->d_e3, c->d_e4, c->d_fb, c->d_fb_cnt, c->d_utab,
-                  c->d_prob_cnt};
+                  c->d_prob_cnt, c->d_sums};
   for (void *b : bufs)
     if (b) cudaFree(b);
   delete c;
@@ -547,8 +574,6 @@ const char *cfust_last_error(cfust_ctx *c) {
 
 cfust_status cfust_set_surrogate(cfust_ctx *c, cfust_surrogate *s) {
   if (!c) return CFUST_EINVAL;
-  if (s && c->opts.prioritise)
-    return fail(c, CFUST_EINVAL, "variable prioritisation serves the lattice sweep of single fits, not a surrogate");
   DeviceGuard dg(c->device);
   drop_graph(c);
   c->sur = s;
@@ -577,6 +602,22 @@ cfust_status cfust_surrogate_problems(cfust_ctx *c, const double *Y, int64_t n, 
   if ((s = finish(c)) != CFUST_OK) return s;
   *rows = (int64_t)cnt < max_rows ? (int64_t)cnt : max_rows;
   return CFUST_OK;
+}
+
+cfust_status cfust_surrogate_inputs(cfust_ctx *c, const double *Y, int64_t n, const cfust_params *P, float *x_out,
+                                    int32_t *kind) {
+  cfust_status s = check_common(c, Y, n, P);
+  if (s != CFUST_OK) return s;
+  if (P->r != 3) return fail(c, CFUST_EINVAL, "the surrogate's inputs need r = 3");
+  if (!x_out || !kind) return fail(c, CFUST_EINVAL, "x_out and kind required");
+  DeviceGuard dg(c->device);
+  if ((s = ensure(c, P->g, P->p, P->r, n)) != CFUST_OK) return s;
+  if ((s = upload_params(c, P)) != CFUST_OK) return s;
+  CF_CUDA(c, cudaMemsetAsync(c->d_status, 0, 2 * sizeof(int), c->stream));
+  CF_CUDA(c, launch_precompute(c->d_params, c->g, c->p, c->r, c->lat, c->d_c64, c->d_c32, c->d_chi64,
+                               c->d_chi32, c->d_status, c->stream));
+  CF_CUDA(c, launch_surrogate_inputs(Y, n, c->g, c->p, c->d_c32, x_out, kind, c->stream));
+  return finish(c);
 }
 
 cfust_status cfust_last_fallback(cfust_ctx *c, int64_t *count) {
@@ -697,6 +738,52 @@ cfust_status cfust_mstep(cfust_ctx *c, const double *Y, int64_t n, const void *t
   CF_CUDA(c, launch_posterior(c->opts.precision, a, c->stream));
   CF_CUDA(c, launch_mstep_finalize(c->d_partials, a.nblocks, c->g, c->p, c->r, n, nu_lo(c), nu_hi(c),
                                    c->d_params, c->d_status, c->stream));
+  if ((s = finish(c)) != CFUST_OK) return s;
+  if ((s = download_params(c, P)) != CFUST_OK) return s;
+  CF_CUDA(c, cudaStreamSynchronize(c->stream));
+  return CFUST_OK;
+}
+
+cfust_status cfust_mstep_sums(cfust_ctx *c, const double *Y, int64_t n, const void *tau, const void *e1,
+                              const void *e2, const void *e3, const void *e4, const cfust_params *P,
+                              double *sums) {
+  cfust_status s = check_common(c, Y, n, P);
+  if (s != CFUST_OK) return s;
+  if (!tau || !e1 || !e2 || !e3 || !e4 || !sums) return fail(c, CFUST_EINVAL, "an input or sums is NULL");
+  DeviceGuard dg(c->device);
+  if ((s = ensure(c, P->g, P->p, P->r, n)) != CFUST_OK) return s;
+  if ((s = upload_params(c, P)) != CFUST_OK) return s;
+  CF_CUDA(c, cudaMemsetAsync(c->d_status, 0, 2 * sizeof(int), c->stream));
+  PosteriorArgs a = post_args(c, Y, n);
+  a.tau_in = tau;
+  a.e1 = e1;
+  a.e2 = e2;
+  a.e3 = e3;
+  a.e4 = e4;
+  a.want_sums = true;
+  CF_CUDA(c, launch_posterior(c->opts.precision, a, c->stream));
+  const int gK = c->g * sums_width(c->p, c->r);
+  CF_CUDA(c, launch_sum_partials(c->d_partials, a.nblocks, gK, c->d_sums, c->stream));
+  CF_CUDA(c, cudaMemcpyAsync(sums, c->d_sums, sizeof(double) * gK, cudaMemcpyDeviceToHost, c->stream));
+  return finish(c);
+}
+
+cfust_status cfust_mstep_apply(cfust_ctx *c, const double *sums, int64_t n_total, cfust_params *P) {
+  if (!c) return CFUST_EINVAL;
+  cfust_status s = check_params(c, P);
+  if (s != CFUST_OK) return s;
+  if (!sums || n_total < 1) return fail(c, CFUST_EINVAL, "sums must be given and n_total >= 1");
+  const int gK = P->g * sums_width(P->p, P->r);
+  for (int e = 0; e < gK; ++e)
+    if (!isfinite(sums[e])) return fail(c, CFUST_ENUMERIC, "a sum is not finite");
+  DeviceGuard dg(c->device);
+  if ((s = ensure(c, P->g, P->p, P->r, 1)) != CFUST_OK) return s;
+  if ((s = upload_params(c, P)) != CFUST_OK) return s;
+  CF_CUDA(c, cudaMemsetAsync(c->d_status, 0, 2 * sizeof(int), c->stream));
+  // the totals enter the finalize as the partials of a single block
+  CF_CUDA(c, cudaMemcpyAsync(c->d_partials, sums, sizeof(double) * gK, cudaMemcpyHostToDevice, c->stream));
+  CF_CUDA(c, launch_mstep_finalize(c->d_partials, 1, c->g, c->p, c->r, n_total, nu_lo(c), nu_hi(c), c->d_params,
+                                   c->d_status, c->stream));
   if ((s = finish(c)) != CFUST_OK) return s;
   if ((s = download_params(c, P)) != CFUST_OK) return s;
   CF_CUDA(c, cudaStreamSynchronize(c->stream));
@@ -885,7 +972,7 @@ std::vector<SweepItem> batch_items(const cfust_ctx::Batch &b, int ppw) {
 }
 
 int default_batch_ppw(int64_t pairs) {
-  int64_t ppw = pairs / (152LL * 2 * 16 * 8);
+  int64_t ppw = pairs / ((int64_t)sm_count() * 2 * 16 * 8);
   return (int)(ppw < 1 ? 1 : (ppw > 32 ? 32 : ppw));
 }
 
@@ -908,7 +995,7 @@ cfust_status enqueue_batch_estep(cfust_ctx *c, cudaStream_t st, bool density_onl
   CF_CUDA(c, launch_estep_batched(c->opts.precision, d, b.p, b.r, c->lat, b.c64, b.c32, b.chi64, b.chi32,
                                   b.d_items, b.nitems, b.counter, density_only, c->opts.e2_mode, b.ppw, b.cps,
                                   b.rescue, b.rescue_cnt, b.status, 1, st,
-                                  sweep_timing(c, st == c->cap_stream)));
+                                  sweep_timing(c, st == c->cap_stream), c->opts.prioritise));
   return CFUST_OK;
 }
 
@@ -945,7 +1032,8 @@ cfust_status autotune_batch(cfust_ctx *c) {
         CF_CUDA(c, cudaEventRecord(e0, c->stream));
         CF_CUDA(c, launch_estep_batched(c->opts.precision, d, b.p, b.r, c->lat, b.c64, b.c32, b.chi64, b.chi32,
                                         b.d_items, b.nitems, b.counter, false, c->opts.e2_mode, ppw, cps,
-                                        b.rescue, b.rescue_cnt, b.status, 1, c->stream));
+                                        b.rescue, b.rescue_cnt, b.status, 1, c->stream, SweepTiming(),
+                                        c->opts.prioritise));
         CF_CUDA(c, cudaEventRecord(e1, c->stream));
         CF_CUDA(c, cudaEventSynchronize(e1));
         CF_CUDA(c, cudaEventElapsedTime(&ms, e0, e1));
@@ -977,7 +1065,6 @@ extern "C" cfust_status cfust_fit_batched(cfust_ctx *c, int nfits, const double 
                                          cfust_params *P, double *trace_out, int *fit_status_out) {
   if (!c) return CFUST_EINVAL;
   if (nfits < 1 || !Y || !n || !P) return fail(c, CFUST_EINVAL, "nfits >= 1 with Y, n and params required");
-  if (c->opts.prioritise) return fail(c, CFUST_EINVAL, "variable prioritisation is for single fits");
   DeviceGuard dg(c->device);
   const int p = P[0].p, r = P[0].r;
   for (int f = 0; f < nfits; ++f) {
@@ -1211,6 +1298,20 @@ extern "C" cfust_status cfust_mstep_noalloc(int precision, const double *Y, int6
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices)
     return noalloc_fail(CFUST_ECUDA, "no usable current CUDA device");
+  // the inputs must live on the current device, where the scratch array is
+  // looked up and the kernels run (a pointer query allocates nothing)
+  {
+    const void *ptrs[6] = {Y, tau, e1, e2, e3, e4};
+    for (const void *q : ptrs) {
+      cudaPointerAttributes at{};
+      if (cudaPointerGetAttributes(&at, q) != cudaSuccess) {
+        cudaGetLastError();
+        return noalloc_fail(CFUST_EINVAL, "Y, tau and e1..e4 must be device memory of the current device");
+      }
+      if ((at.type != cudaMemoryTypeDevice && at.type != cudaMemoryTypeManaged) || at.device != dev)
+        return noalloc_fail(CFUST_EINVAL, "Y, tau and e1..e4 must be device memory of the current device");
+    }
+  }
   unsigned char *base = nullptr;
   {
     std::lock_guard<std::mutex> lock(g_noalloc_mutex);

@@ -9,6 +9,11 @@
 namespace cfust {
 
 constexpr int PMAX = CFUST_PMAX;
+
+// Streaming multiprocessors of the current CUDA device (cudaDevAttrMultiProcessorCount,
+// queried once per device ordinal and cached).  Persistent grids and block caps
+// are sized from it.
+int sm_count();
 constexpr int RMAX = CFUST_RMAX;
 constexpr int WARP = 32;
 
@@ -93,6 +98,9 @@ struct LatticeDev {
   int sint[RMAX + 1];
   double sfrac[RMAX + 1];
   double shift[RMAX + 1];
+  // polls of a bounded mbarrier wait (the sweeps' staging of this lattice's
+  // tables) before it gives up with ERR_TIMEOUT; 2^22 unless a test lowers it
+  int wait_polls = 1 << 22;
   // single-precision uniforms of every point for the r normal coordinates:
   // row k = [1 - u_1 .. 1 - u_r, u_1 .. u_r, padding] with a row stride of
   // uniform_stride(r) floats (device memory; built by launch_uniform_table)
@@ -143,7 +151,7 @@ cudaError_t launch_estep_list(const double *Y, int64_t n, int g, int p, int r, c
                               const float *chi32, EstepOut out, bool density_only, int e2_mode,
                               const int *list, const unsigned *count, unsigned long long *rescue_list,
                               unsigned *rescue_count, int *d_status, cudaStream_t st, int triage,
-                              const double *d_pi, float tnats = 30.f);
+                              const double *d_pi, float tnats = 30.f, int prio = 0);
 
 // Device view of a trained surrogate network (owned by cfust_surrogate):
 // packed BF16 weights W1 [16][128], W2, W3 [128][128], W4 [128][16] (input x
@@ -163,6 +171,12 @@ cudaError_t launch_surrogate_problems(const double *Y, int64_t n, int g, int p, 
                                       int64_t stride, float *x_out, int64_t max_rows, unsigned long long *count,
                                       cudaStream_t st);
 
+// Both network inputs of every pair as the surrogate E-step forms them
+// (BF16-rounded values as floats) into x_out [g n][2][7], and each pair's
+// domain class into kind [g n].
+cudaError_t launch_surrogate_inputs(const double *Y, int64_t n, int g, int p, const CompT<float> *c32, float *x_out,
+                                    int *kind, cudaStream_t st);
+
 // Surrogate E-step (FP32 outputs, r = 3): for every pair whose standardised
 // problem lies in the training domain the network gives log T_A, T_B and the
 // pass-B moments, from which log f and e1..e4 are formed as in the lattice
@@ -170,7 +184,7 @@ cudaError_t launch_surrogate_problems(const double *Y, int64_t n, int g, int p, 
 // zeroed here first) for launch_estep_list.
 cudaError_t launch_surrogate_estep(const SurrogateDev &sd, const double *Y, int64_t n, int g, int p,
                                    const CompT<float> *c32, EstepOut out, bool density_only, int *fb_list,
-                                   unsigned *fb_count, cudaStream_t st);
+                                   unsigned *fb_count, int *status, cudaStream_t st);
 
 // Elementwise single-precision normal functions (see cfust_normal_f32).
 cudaError_t launch_normal_f32(const float *x, float *out, int64_t n, int which, cudaStream_t st);
@@ -200,6 +214,10 @@ int posterior_nblocks(int64_t n);
 // and when trace != NULL also trace[*iter] = sum and ++*iter.
 cudaError_t launch_reduce_ll(const double *ll_partials, int nblocks, double *ll_out,
                              double *trace, int *iter, cudaStream_t st);
+
+// Totals of the per-block partial sums, out[e] = sum_b partials[b][e] for
+// e < gK, added block by block in order (one thread per entry).
+cudaError_t launch_sum_partials(const double *partials, int nblocks, int gK, double *out, cudaStream_t st);
 
 // Algorithm 3: per-component conditional-maximisation update from the sums.
 cudaError_t launch_mstep_finalize(const double *partials, int nblocks, int g, int p, int r,
@@ -253,7 +271,8 @@ cudaError_t launch_estep_batched(int precision, const BatchDev &b, int p, int r,
                                  const float *chi32, const SweepItem *items, int nitems,
                                  unsigned *item_counter, bool density_only, int e2_mode, int ppw,
                                  int ctas_per_sm, unsigned long long *rescue_list, unsigned *rescue_count,
-                                 int *d_status, int triage, cudaStream_t st, SweepTiming tm = SweepTiming());
+                                 int *d_status, int triage, cudaStream_t st, SweepTiming tm = SweepTiming(),
+                                 int prio = 0);
 
 cudaError_t launch_posterior_batched(int precision, const BatchDev &b, int p, int r, const BlockRef *blocks,
                                      int nblocks, double *partials, double *ll_partials, bool want_sums,

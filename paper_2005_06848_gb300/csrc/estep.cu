@@ -95,7 +95,8 @@ struct EArgs {
   int triage;          // 1: skip queued pairs whose posterior weight is provably negligible
   const double *pi;    // device [g], read by the triage
   float tnats;         // the triage's margin: tau_ij < exp(-tnats) counts as negligible
-  int prio;            // 1: variable prioritisation (single-fit sweeps and their rescue)
+  int prio;            // 1: variable prioritisation (every sweep and its rescue)
+  int wait_polls;      // polls of the staging wait before it gives up (LatticeDev::wait_polls)
 };
 
 // The per-fit part of a sweep: observations, their count, the component
@@ -569,7 +570,13 @@ __device__ __forceinline__ bool pair_sweep(const EArgs &a, const FitView &fv, co
     for (int t = 0; t < RP; ++t) M2[t] = warp_sum(M2[t]);
   }
 
-  const T logf = static_cast<T>(pr.logt) + M::lg(SA) - M::lg(static_cast<T>(N));
+  // double precision: a probability below the smallest normal double counts
+  // as underflowed (log f = -inf, expectations 0); a single-precision sum that
+  // small is queued for the log-domain rescue below
+  constexpr bool dbl = sizeof(T) == 8;
+  const T tiny_sum = dbl ? static_cast<T>(2.2250738585072014e-308 * (double)N) : T(0);
+  const T logf = (dbl && !(SA >= tiny_sum)) ? static_cast<T>(-INFINITY)
+                                             : static_cast<T>(pr.logt) + M::lg(SA) - M::lg(static_cast<T>(N));
   const int64_t n = fv.n;
   const int64_t ij = (int64_t)i * n + j;
   if (check) {
@@ -592,17 +599,20 @@ __device__ __forceinline__ bool pair_sweep(const EArgs &a, const FitView &fv, co
   if (fv.out.logf != nullptr && lane == 0) store<OT>(fv.out.logf, ij, logf);
   if (DENS) return false;
 
-  const bool ok = (SA > T(0)) && (SB > T(0));
+  const bool ok = dbl ? (SA >= tiny_sum && SB >= tiny_sum) : (SA > T(0) && SB > T(0));
   const T ratio = nrm ? T(1) : mAT / nud;
   const T e1 = ok ? ratio * (SB / SA) : T(0);
   const T sig = nrm ? T(1) : M::sq(nud / mBT);
+  // the weighted means M / S_B (S_B at least the smallest normal times N here,
+  // so 1 / S_B stays finite)
   const T iSB = ok ? T(1) / SB : T(0);
+  const auto mean_of = [&](T m) -> T { return ok ? m * iSB : T(0); };
   T LEV[R];
 #pragma unroll
   for (int t = 0; t < R; ++t) {
     T s = T(0);
 #pragma unroll
-    for (int h = 0; h <= t; ++h) s += Lc[t * (t + 1) / 2 + h] * (M1[h] * iSB);
+    for (int h = 0; h <= t; ++h) s += Lc[t * (t + 1) / 2 + h] * mean_of(M1[h]);
     LEV[t] = s;
   }
   T e2;
@@ -632,7 +642,7 @@ __device__ __forceinline__ bool pair_sweep(const EArgs &a, const FitView &fv, co
         for (int aa = 0; aa <= t; ++aa) {
 #pragma unroll
           for (int bb = 0; bb <= h; ++bb) {
-            const T evv = (aa >= bb ? M2[aa * (aa + 1) / 2 + bb] : M2[bb * (bb + 1) / 2 + aa]) * iSB;
+            const T evv = mean_of(aa >= bb ? M2[aa * (aa + 1) / 2 + bb] : M2[bb * (bb + 1) / 2 + aa]);
             s += Lc[t * (t + 1) / 2 + aa] * evv * Lc[h * (h + 1) / 2 + bb];
           }
         }
@@ -698,6 +708,8 @@ __device__ __forceinline__ bool stage_block(const EArgs &a, int i, unsigned char
                                                align16(sizeof(PairedConsts)));
   const T *gtab = reinterpret_cast<const T *>(a.chi) + (int64_t)i * 2 * N;
 
+  __shared__ int s_fail;
+  if (threadIdx.x == 0) s_fail = 0;
   if (a.staged && threadIdx.x == 0) {
     mbar_init(bar, 1);
     mbar_expect_tx(bar, static_cast<uint32_t>(tab_bytes));
@@ -716,8 +728,18 @@ __device__ __forceinline__ bool stage_block(const EArgs &a, int i, unsigned char
   }
   __syncthreads();
   if (a.staged) {
-    if (!mbar_wait_bounded(bar, 0, 1 << 22)) {
-      if (threadIdx.x == 0) atomicOr(a.status, ERR_TIMEOUT);
+    // the decision to give up is the block's, never a single thread's: a lane
+    // that left alone would break the warp's full-mask shuffles in the sweep
+    if (!mbar_wait_bounded(bar, 0, a.wait_polls)) atomicOr(&s_fail, 1);
+    __syncthreads();
+    if (s_fail) {
+      // the copy may still be in flight: let it land (bounded) before the
+      // block's shared memory is released, then report the timeout
+      if (threadIdx.x == 0) {
+        mbar_wait_bounded(bar, 0, 1 << 22);
+        atomicOr(a.status, ERR_TIMEOUT);
+      }
+      __syncthreads();
       return false;
     }
   }
@@ -777,7 +799,7 @@ __device__ bool triage_listed(const FitView &fv, int i, int64_t j, float tnats) 
 // The same sweep over an explicit list of observations per component:
 // list[i * stride + k] for k < count[i] (the pairs a surrogate E-step leaves
 // to the lattice rule).  Warps stride over the list in chunks of ppw.
-template <typename T, int R, bool DENS>
+template <typename T, int R, bool DENS, bool PRIO = false>
 __global__ void __launch_bounds__(256, sizeof(T) == 4 ? CFUST_ESTEP_MINB : 1)
     estep_list_kernel(EArgs a, const int *list, const unsigned *count, int64_t stride) {
   extern __shared__ __align__(128) unsigned char smem[];
@@ -793,24 +815,36 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? CFUST_ESTEP_MINB : 1)
   const int *li = list + (int64_t)i * stride;
   const int lane = threadIdx.x & 31;
   const bool check = (sizeof(T) == 4);
+  // with prioritisation, one order-and-factor slot per warp after the staged constants
+  PairedConsts *wpc = nullptr;
+  if constexpr (PRIO) {
+    const size_t tab_bytes = a.staged ? (size_t)(DENS ? 1 : 2) * a.N * sizeof(T) : 0;
+    wpc = reinterpret_cast<PairedConsts *>(smem + align16(tab_bytes) + align16(sizeof(CompT<T>)) +
+                                           align16(sizeof(PairedConsts)) + 16) + warp;
+  }
   for (int64_t base = ((int64_t)blockIdx.x * nw + warp) * a.ppw; base < cnt;
        base += (int64_t)gridDim.x * nw * a.ppw) {
     const int m = (int)((cnt - base) < a.ppw ? (cnt - base) : a.ppw);
     Prologue<R> mine;
     int64_t myj = 0;
     bool myskip = false;
+    PrioLane<R, T> pmine;
     if (lane < m) {
       myj = li[base + lane];
       if (a.triage) myskip = triage_listed<R, DENS>(fv, i, myj, a.tnats);
-      if (!myskip) mine = prologue<T, R>(a, fv, *cs, myj);
+      if (!myskip) {
+        mine = prologue<T, R>(a, fv, *cs, myj);
+        if constexpr (PRIO) prio_lane<R, T>(mine.q, cs->lam, cs->lamd, &pmine);
+      }
     }
     const unsigned skipped = __ballot_sync(0xffffffffu, myskip);
     for (int b = 0; b < m; ++b) {
       if ((skipped >> b) & 1u) continue;
       const Prologue<R> pr = shfl_prologue<R>(mine, b);
+      PrioLane<R, T> pp;
+      if constexpr (PRIO) pp = shfl_prio<R, T>(pmine, b);
       const int64_t j = __shfl_sync(0xffffffffu, myj, b);
-      const bool need = pair_sweep<T, T, R, DENS>(a, fv, *cs, pr, tA, tB, i, j, lane, check, pcs, nullptr,
-                                                  nullptr);
+      const bool need = pair_sweep<T, T, R, DENS, PRIO>(a, fv, *cs, pr, tA, tB, i, j, lane, check, pcs, wpc, &pp);
       if (need && lane == 0) {
         const unsigned slot = atomicAdd(a.rescue_count, 1u);
         a.rescue_list[slot] = pair_id(i, j);
@@ -1155,7 +1189,7 @@ cudaError_t launch_r(EArgs a, int g, int64_t n, cudaStream_t st, bool fp32,
     if (e != cudaSuccess) return e;
   }
   if (!fp32) return e;
-  rescue_kernel<R, DENS><<<152 * 4, 256, 0, st>>>(a, c64, chi64);
+  rescue_kernel<R, DENS><<<sm_count() * 4, 256, 0, st>>>(a, c64, chi64);
   return cudaGetLastError();
 }
 
@@ -1200,7 +1234,7 @@ __device__ __forceinline__ FitView batch_view(const BatchDev &b, const FitDesc &
 // constants copied only when the component changes from the CTA's previous
 // item.  Items are ordered component by component, so a CTA mostly stays on
 // one component.  A lost copy ends the whole CTA with ERR_TIMEOUT.
-template <typename T, int R, bool DENS>
+template <typename T, int R, bool DENS, bool PRIO = false>
 __global__ void __launch_bounds__(256, sizeof(T) == 4 ? CFUST_ESTEP_MINB : 1)
     estep_batched_kernel(EArgs a, BatchDev b, const SweepItem *items, int nitems, unsigned *counter) {
   extern __shared__ __align__(128) unsigned char smem[];
@@ -1245,13 +1279,18 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? CFUST_ESTEP_MINB : 1)
           pcs->nL[t * (t + 1) / 2 + h] = make_float2(v, v);
         }
       }
-      if (a.staged && !mbar_wait_bounded(bar, phase, 1 << 22)) atomicOr(&s_fail, 1);
-      phase ^= 1u;
+      if (a.staged && !mbar_wait_bounded(bar, phase, a.wait_polls)) atomicOr(&s_fail, 1);
       __syncthreads();
       if (s_fail) {
-        if (threadIdx.x == 0) atomicOr(a.status, ERR_TIMEOUT);
+        // let the copy in flight land (bounded) before the block exits
+        if (threadIdx.x == 0) {
+          mbar_wait_bounded(bar, phase, 1 << 22);
+          atomicOr(a.status, ERR_TIMEOUT);
+        }
+        __syncthreads();
         return;
       }
+      phase ^= 1u;
       cur = item.gc;
     }
     const T *tA = a.staged ? tab : gtab_base + (int64_t)cur * 2 * N;
@@ -1261,7 +1300,11 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? CFUST_ESTEP_MINB : 1)
     const FitView fv = batch_view<T>(b, fd, a.p, R);
     const int warp = threadIdx.x >> 5;
     const int64_t jw0 = (int64_t)item.j0 + (int64_t)warp * a.ppw;
-    sweep_warp_pairs<T, R, DENS>(a, fv, *cs, pcs, tA, tB, cr.i, item.gc, jw0, a.ppw, nullptr);
+    // with prioritisation, one order-and-factor slot per warp after the mbarrier
+    PairedConsts *wpc = nullptr;
+    if constexpr (PRIO)
+      wpc = reinterpret_cast<PairedConsts *>(reinterpret_cast<unsigned char *>(bar) + 16) + warp;
+    sweep_warp_pairs<T, R, DENS, PRIO>(a, fv, *cs, pcs, tA, tB, cr.i, item.gc, jw0, a.ppw, wpc);
     __syncthreads();
   }
 }
@@ -1291,21 +1334,27 @@ cudaError_t launch_batched_r(EArgs a, const BatchDev &b, const SweepItem *items,
                              const double *chi64, SweepTiming tm) {
   const size_t tab_bytes = (size_t)(DENS ? 1 : 2) * a.N * sizeof(T);
   a.staged = tab_bytes <= 160u * 1024u ? 1 : 0;
+  const bool prio = a.prio && R >= 2;
   const size_t smem = (a.staged ? align16(tab_bytes) : 0) + align16(sizeof(CompT<T>)) +
-                      align16(sizeof(PairedConsts)) + 16;
-  cudaError_t e = cudaFuncSetAttribute(estep_batched_kernel<T, R, DENS>,
-                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+                      align16(sizeof(PairedConsts)) + 16 + (prio ? 8 * sizeof(PairedConsts) : 0);
+  cudaError_t e = prio ? cudaFuncSetAttribute(estep_batched_kernel<T, R, DENS, (R >= 2)>,
+                                              cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)
+                       : cudaFuncSetAttribute(estep_batched_kernel<T, R, DENS, false>,
+                                              cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   if ((e = cudaMemsetAsync(counter, 0, sizeof(unsigned), st)) != cudaSuccess) return e;
   if (fp32 && (e = cudaMemsetAsync(a.rescue_count, 0, sizeof(unsigned), st)) != cudaSuccess) return e;
   const unsigned evflag = tm.capturing ? cudaEventRecordExternal : cudaEventRecordDefault;
   if (tm.start && (e = cudaEventRecordWithFlags(tm.start, st, evflag)) != cudaSuccess) return e;
-  estep_batched_kernel<T, R, DENS><<<152 * (ctas_per_sm > 0 ? ctas_per_sm : 2), 256, smem, st>>>(a, b, items,
-                                                                                                 nitems, counter);
+  const unsigned grid = (unsigned)(sm_count() * (ctas_per_sm > 0 ? ctas_per_sm : 2));
+  if (prio)
+    estep_batched_kernel<T, R, DENS, (R >= 2)><<<grid, 256, smem, st>>>(a, b, items, nitems, counter);
+  else
+    estep_batched_kernel<T, R, DENS, false><<<grid, 256, smem, st>>>(a, b, items, nitems, counter);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
   if (tm.stop && (e = cudaEventRecordWithFlags(tm.stop, st, evflag)) != cudaSuccess) return e;
   if (!fp32) return cudaSuccess;
-  rescue_batched_kernel<R, DENS><<<152 * 4, 256, 0, st>>>(a, b, c64, chi64);
+  rescue_batched_kernel<R, DENS><<<sm_count() * 4, 256, 0, st>>>(a, b, c64, chi64);
   return cudaGetLastError();
 }
 
@@ -1345,7 +1394,8 @@ __global__ void normal_f32_kernel(const float *x, float *out, int64_t n, int whi
 cudaError_t launch_normal_f32(const float *x, float *out, int64_t n, int which, cudaStream_t st) {
   if (n <= 0) return cudaSuccess;
   const int64_t blocks = (n + 255) / 256;
-  normal_f32_kernel<<<(unsigned)(blocks < 152 * 16 ? blocks : 152 * 16), 256, 0, st>>>(x, out, n, which);
+  const int64_t bcap = (int64_t)sm_count() * 16;
+  normal_f32_kernel<<<(unsigned)(blocks < bcap ? blocks : bcap), 256, 0, st>>>(x, out, n, which);
   return cudaGetLastError();
 }
 
@@ -1354,7 +1404,7 @@ cudaError_t launch_estep_batched(int precision, const BatchDev &b, int p, int r,
                                  const float *chi32, const SweepItem *items, int nitems,
                                  unsigned *item_counter, bool density_only, int e2_mode, int ppw,
                                  int ctas_per_sm, unsigned long long *rescue_list, unsigned *rescue_count,
-                                 int *d_status, int triage, cudaStream_t st, SweepTiming tm) {
+                                 int *d_status, int triage, cudaStream_t st, SweepTiming tm, int prio) {
   if (nitems <= 0) return cudaSuccess;
   EArgs a{};
   a.Y = nullptr;
@@ -1376,7 +1426,8 @@ cudaError_t launch_estep_batched(int precision, const BatchDev &b, int p, int r,
   a.status = d_status;
   a.triage = triage ? 1 : 0;
   a.tnats = 30.f;
-  a.prio = 0;
+  a.prio = prio ? 1 : 0;
+  a.wait_polls = lat.wait_polls;
   if (precision == CFUST_FP64) {
     a.comp = c64;
     a.chi = chi64;
@@ -1416,9 +1467,11 @@ cudaError_t launch_list_r3(EArgs a, int g, int64_t n, const int *list, const uns
   const size_t tab_bytes = (size_t)(DENS ? 1 : 2) * a.N * sizeof(float);
   a.staged = tab_bytes <= 160u * 1024u ? 1 : 0;
   const size_t smem = (a.staged ? align16(tab_bytes) : 0) + align16(sizeof(CompT<float>)) +
-                      align16(sizeof(PairedConsts)) + 16;
-  cudaError_t e = cudaFuncSetAttribute(estep_list_kernel<float, 3, DENS>,
-                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+                      align16(sizeof(PairedConsts)) + 16 + (a.prio ? 8 * sizeof(PairedConsts) : 0);
+  cudaError_t e = a.prio ? cudaFuncSetAttribute(estep_list_kernel<float, 3, DENS, true>,
+                                                cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)
+                         : cudaFuncSetAttribute(estep_list_kernel<float, 3, DENS, false>,
+                                                cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   // 16 listed pairs per warp chunk: their FP64 prologues and triage tests run
   // lane-parallel, which matters at the small lattices this path serves
@@ -1429,14 +1482,18 @@ cudaError_t launch_list_r3(EArgs a, int g, int64_t n, const int *list, const uns
   // lopsided (one component's far tail can hold most listed pairs), so each
   // column gets the whole cap rather than a 1/g share of it
   const int64_t need = (n + 8 * a.ppw - 1) / (8 * a.ppw);
-  const int64_t cap = 152 * 2 * 4;
+  const int64_t cap = (int64_t)sm_count() * 2 * 4;
   const int64_t bx = need < cap ? need : cap;
   e = cudaMemsetAsync(a.rescue_count, 0, sizeof(unsigned), st);
   if (e != cudaSuccess) return e;
-  estep_list_kernel<float, 3, DENS><<<dim3((unsigned)(bx < 1 ? 1 : bx), g), 256, smem, st>>>(a, list, count, n);
+  const dim3 grid((unsigned)(bx < 1 ? 1 : bx), g);
+  if (a.prio)
+    estep_list_kernel<float, 3, DENS, true><<<grid, 256, smem, st>>>(a, list, count, n);
+  else
+    estep_list_kernel<float, 3, DENS, false><<<grid, 256, smem, st>>>(a, list, count, n);
   e = cudaGetLastError();
   if (e != cudaSuccess) return e;
-  rescue_kernel<3, DENS><<<152 * 4, 256, 0, st>>>(a, c64, chi64);
+  rescue_kernel<3, DENS><<<sm_count() * 4, 256, 0, st>>>(a, c64, chi64);
   return cudaGetLastError();
 }
 
@@ -1466,6 +1523,7 @@ EArgs make_args(const double *Y, int64_t n, int g, int p, const LatticeDev &lat,
   a.triage = (triage && out.logf != nullptr) ? 1 : 0;
   a.tnats = tnats;
   a.prio = prio ? 1 : 0;
+  a.wait_polls = lat.wait_polls;
   a.pi = d_pi;
   a.comp = nullptr;
   a.chi = nullptr;
@@ -1477,10 +1535,11 @@ cudaError_t launch_estep_list(const double *Y, int64_t n, int g, int p, int r, c
                               const float *chi32, EstepOut out, bool density_only, int e2_mode,
                               const int *list, const unsigned *count, unsigned long long *rescue_list,
                               unsigned *rescue_count, int *d_status, cudaStream_t st, int triage,
-                              const double *d_pi, float tnats) {
+                              const double *d_pi, float tnats, int prio) {
   if (n <= 0) return cudaSuccess;
   if (r != 3) return cudaErrorInvalidValue;
-  EArgs a = make_args(Y, n, g, p, lat, out, e2_mode, rescue_list, rescue_count, d_status, triage, d_pi, tnats);
+  EArgs a = make_args(Y, n, g, p, lat, out, e2_mode, rescue_list, rescue_count, d_status, triage, d_pi, tnats,
+                      prio);
   a.comp = c32;
   a.chi = chi32;
   return density_only ? launch_list_r3<true>(a, g, n, list, count, c64, chi64, st)
@@ -1506,7 +1565,7 @@ cudaError_t launch_estep(int precision, const double *Y, int64_t n, int g, int p
     // about sixteen waves of two resident CTAs per SM (8 warps each), so the
     // last wave's imbalance stays small; 1..32 pairs per warp (measured best
     // near 8 on the p=4, r=4, g=3, n=100000 workload)
-    const int64_t target_ctas = 152 * 2 * 16;
+    const int64_t target_ctas = (int64_t)sm_count() * 2 * 16;
     int64_t ppw = ((int64_t)g * n) / (target_ctas * 8);
     pairs_per_warp = (int)(ppw < 1 ? 1 : (ppw > 32 ? 32 : ppw));
   }

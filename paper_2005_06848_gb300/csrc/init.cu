@@ -252,7 +252,7 @@ int group_sums_width(int mode, int p) { return mode == 0 ? p + 1 : p * (p + 1) /
 
 int group_sums_nblocks(int64_t n) {
   const int64_t ntiles = (n + IT - 1) / IT;
-  const int64_t cap = 152 * 2;
+  const int64_t cap = (int64_t)sm_count() * 2;
   return (int)(ntiles < cap ? (ntiles > 0 ? ntiles : 1) : cap);
 }
 

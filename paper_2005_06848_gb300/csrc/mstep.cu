@@ -753,7 +753,7 @@ cudaError_t launch_finalize_batched(const BatchDev &b, int p, int r, const doubl
 
 int posterior_nblocks(int64_t n) {
   const int64_t ntiles = (n + TJ - 1) / TJ;
-  const int64_t cap = 152 * 4;
+  const int64_t cap = (int64_t)sm_count() * 4;
   return (int)(ntiles < cap ? (ntiles > 0 ? ntiles : 1) : cap);
 }
 
@@ -794,6 +794,22 @@ cudaError_t launch_posterior(int precision, const PosteriorArgs &a, cudaStream_t
 cudaError_t launch_reduce_ll(const double *ll_partials, int nblocks, double *ll_out, double *trace,
                              int *iter, cudaStream_t st) {
   reduce_ll_kernel<<<1, 256, 0, st>>>(ll_partials, nblocks, ll_out, trace, iter);
+  return cudaGetLastError();
+}
+
+namespace {
+__global__ void sum_partials_kernel(const double *partials, int nb, int gK, double *out) {
+  const int e = blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= gK) return;
+  double s = 0.0;
+  for (int b = 0; b < nb; ++b) s += partials[(int64_t)b * gK + e];
+  out[e] = s;
+}
+}  // namespace
+
+cudaError_t launch_sum_partials(const double *partials, int nblocks, int gK, double *out, cudaStream_t st) {
+  if (gK <= 0) return cudaSuccess;
+  sum_partials_kernel<<<(gK + 127) / 128, 128, 0, st>>>(partials, nblocks, gK, out);
   return cudaGetLastError();
 }
 

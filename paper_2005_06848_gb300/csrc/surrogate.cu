@@ -6,7 +6,8 @@
 //                 triangle (11, 12, 13, 22, 23, 33)
 // Network 7 -> 128 -> 128 -> 128 -> 10 with GELU (tanh form) after the hidden
 // layers; BF16 weights and activations, FP32 accumulation on the tensor cores
-// (mma.sync m16n8k16), FP32 master weights updated by Adam.  Inputs are
+// (inference and the E-step: tcgen05 MMAs with accumulators in tensor memory;
+// training GEMMs: mma.sync m16n8k16), FP32 master weights updated by Adam.  Inputs are
 // normalised as c and log m mapped from their ranges onto [-1, 1] and R/0.9.
 // The network predicts log(-log P), the first moments and the covariance
 // (second moments minus the products of the first moments), standardised by
@@ -36,6 +37,7 @@
 #include "cfust_internal.cuh"
 #include "normal_f32.cuh"
 #include "special.cuh"
+#include "tcgen05.cuh"
 
 namespace cfust {
 namespace sg {
@@ -506,102 +508,9 @@ __global__ void __launch_bounds__(256) label_kernel(const float *x, float *y, in
   yb[9] = EXX[2][2];
 }
 
-// ---------------------------------------------------------------------------
-// Fused surrogate E-step.  A CTA holds the whole network in shared memory
-// (weights transposed to [out][in] for the B fragments); each of its 16 warps
-// independently takes tiles of 8 (i, j) pairs = 16 network rows (pass A and
-// pass B of every pair; 16 pairs and pass A only for the density) and carries
-// them through the four layers in registers: the accumulator fragments of a
-// layer are, pair by pair of n-tiles, exactly the A fragments of the next
-// layer's m16n8k16 MMAs, so activations never leave the warp and the loop has
-// no block barrier.  Per-warp shared scratch holds only the inputs and the
-// outputs of the tile.
-// ---------------------------------------------------------------------------
-constexpr int HP = H + 8, XP = DINP + 8, OP = DOUTP + 1;
-constexpr int WARPS = 16, WROWS = 16;
-
-struct InferWeights {
-  bf16 W1t[H * XP];
-  bf16 W2t[H * HP];
-  bf16 W3t[H * HP];
-  bf16 W4t[DOUTP * HP];
-  float bias[3 * H + DOUTP];
-  float norm[2 * DOUT];
-};
-struct WarpScratch {
-  bf16 X[WROWS * XP];
-  float O[WROWS * OP];
-  float logt[WROWS], nud[WROWS], q[3 * WROWS], cmax[WROWS];
-  int kind[WROWS];
-};
-constexpr size_t INFER_SMEM = sizeof(InferWeights) + WARPS * sizeof(WarpScratch);
-static_assert(sizeof(InferWeights) % 16 == 0, "scratch blocks must stay 16-byte aligned");
-static_assert(sizeof(WarpScratch) % 16 == 0, "scratch blocks must stay 16-byte aligned");
-
-__device__ __forceinline__ uint32_t ld32(const bf16 *p) { return *reinterpret_cast<const uint32_t *>(p); }
-
-// Four 8x8 bf16 matrices from shared memory in one instruction; lane l gives
-// the address of row (l & 7) of matrix (l >> 3) (16-byte aligned) and receives
-// row l / 4, columns 2 (l % 4) and 2 (l % 4) + 1 of each matrix.  With the
-// weights stored [out][in], matrices (n-tile, k 0..7), (n-tile, k 8..15) are
-// exactly the two B registers of an m16n8k16 MMA for that n-tile.
-__device__ __forceinline__ void ldsm_x4(uint32_t (&r)[4], const bf16 *p) {
-  const unsigned a = (unsigned)__cvta_generic_to_shared(p);
-  asm volatile("ldmatrix.sync.aligned.m8n8.x4.shared.b16 {%0, %1, %2, %3}, [%4];\n"
-               : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3])
-               : "r"(a));
-}
-
 __device__ __forceinline__ uint32_t pack_bf16x2(float lo, float hi) {
   const __nv_bfloat162 v = __floats2bfloat162_rn(lo, hi);
   return *reinterpret_cast<const uint32_t *>(&v);
-}
-
-// One hidden layer for the warp's 16 rows: out = GELU(in Wt^T + bias), with
-// `in` as KT k-tiles of A fragments and `out` as the 8 k-tiles (128 columns)
-// of the next layer's A fragments.  Computed in two halves of 64 columns to
-// bound the live accumulators.
-template <int KT>
-__device__ __forceinline__ void dense_gelu(const uint32_t (&in)[KT][4], const bf16 *Wt, int wp, const float *bias,
-                                           uint32_t (&out)[8][4], int gid, int tig) {
-#pragma unroll
-  for (int half = 0; half < 2; ++half) {
-    float acc[8][4];
-#pragma unroll
-    for (int nt = 0; nt < 8; ++nt)
-#pragma unroll
-      for (int c = 0; c < 4; ++c) acc[nt][c] = 0.f;
-    // this lane's ldmatrix row: n-tile nt + (l >> 4), row l & 7, k half (l >> 3) & 1
-    const int lane = (gid << 2) | tig;
-    const bf16 *wl = Wt + (((lane >> 4) * 8 + (lane & 7)) * wp + ((lane >> 3) & 1) * 8);
-#pragma unroll
-    for (int kt = 0; kt < KT; ++kt)
-#pragma unroll
-      for (int nt = 0; nt < 8; nt += 2) {
-        uint32_t b4[4];
-        ldsm_x4(b4, wl + (half * 8 + nt) * 8 * wp + kt * 16);
-        const uint32_t b0[2] = {b4[0], b4[1]}, b1[2] = {b4[2], b4[3]};
-        mma_bf16(acc[nt], in[kt], b0);
-        mma_bf16(acc[nt + 1], in[kt], b1);
-      }
-    // columns 16 q .. 16 q + 15 (n-tiles 2q and 2q + 1) form k-tile q of the
-    // next layer: (row gid | gid + 8) x (k 2 tig, 2 tig + 1 | + 8); each
-    // register pair holds two adjacent columns, evaluated as one FP32x2 pair
-#pragma unroll
-    for (int nt = 0; nt < 8; nt += 2) {
-      const int q = half * 4 + nt / 2;
-      const int col0 = (half * 8 + nt) * 8 + tig * 2, col1 = col0 + 8;
-      const float2 b0 = make_float2(bias[col0], bias[col0 + 1]), b1 = make_float2(bias[col1], bias[col1 + 1]);
-      const float2 g0 = gelu_x2(__fadd2_rn(make_float2(acc[nt][0], acc[nt][1]), b0));
-      const float2 g1 = gelu_x2(__fadd2_rn(make_float2(acc[nt][2], acc[nt][3]), b0));
-      const float2 g2 = gelu_x2(__fadd2_rn(make_float2(acc[nt + 1][0], acc[nt + 1][1]), b1));
-      const float2 g3 = gelu_x2(__fadd2_rn(make_float2(acc[nt + 1][2], acc[nt + 1][3]), b1));
-      out[q][0] = pack_bf16x2(g0.x, g0.y);
-      out[q][1] = pack_bf16x2(g1.x, g1.y);
-      out[q][2] = pack_bf16x2(g2.x, g2.y);
-      out[q][3] = pack_bf16x2(g3.x, g3.y);
-    }
-  }
 }
 
 // Nearest-structure PSD repair of a predicted 3x3 covariance (upper order
@@ -699,223 +608,447 @@ __device__ __forceinline__ RowProblem row_problem(const CompT<float> &c, const d
   return rp;
 }
 
-template <bool DENS>
-__global__ void __launch_bounds__(WARPS * 32, 1)
-    surrogate_estep_kernel(SurrogateDev sd, const double *Y, int64_t n, int g, int p,
-                           const CompT<float> *__restrict__ comp, EstepOut out, int *fb_list, unsigned *fb_count) {
-  extern __shared__ __align__(128) unsigned char smem[];
-  InferWeights &Wsm = *reinterpret_cast<InferWeights *>(smem);
-  const int tid = threadIdx.x;
-  {
-    const bf16 *W1 = static_cast<const bf16 *>(sd.W1), *W2 = static_cast<const bf16 *>(sd.W2);
-    const bf16 *W3 = static_cast<const bf16 *>(sd.W3), *W4 = static_cast<const bf16 *>(sd.W4);
-    for (int e = tid; e < DINP * H; e += blockDim.x) {
-      const int k = e / H, o = e % H;
-      Wsm.W1t[o * XP + k] = W1[e];
-    }
-    for (int e = tid; e < H * H; e += blockDim.x) {
-      const int k = e / H, o = e % H;
-      Wsm.W2t[o * HP + k] = W2[e];
-      Wsm.W3t[o * HP + k] = W3[e];
-    }
-    for (int e = tid; e < H * DOUTP; e += blockDim.x) {
-      const int k = e / DOUTP, o = e % DOUTP;
-      Wsm.W4t[o * HP + k] = W4[e];
-    }
-    for (int e = tid; e < H; e += blockDim.x) {
-      Wsm.bias[e] = sd.b1[e];
-      Wsm.bias[H + e] = sd.b2[e];
-      Wsm.bias[2 * H + e] = sd.b3[e];
-    }
-    if (tid < DOUTP) Wsm.bias[3 * H + tid] = sd.b4[tid];
-    if (tid < 2 * DOUT) Wsm.norm[tid] = sd.norm[tid];
-  }
-  __syncthreads();  // the only block barrier: the warps are independent from here
-
-  const int warp = tid >> 5, lane = tid & 31, gid = lane >> 2, tig = lane & 3;
-  WarpScratch &S = *reinterpret_cast<WarpScratch *>(smem + sizeof(InferWeights) + warp * sizeof(WarpScratch));
-  constexpr int PPT = DENS ? WROWS : WROWS / 2;  // pairs per warp tile
-  const int64_t tpc = (n + PPT - 1) / PPT;
-  const int64_t ntiles = tpc * g;
+// The network's normalised input of a row (the clamped point c and log m
+// mapped from their ranges onto [-1, 1], R / 0.9), before its BF16 rounding.
+__device__ __forceinline__ void network_input(const RowProblem &rp, float (&u)[DIN]) {
   const float logm_mid = (float)(LOGM_LO + LOGM_HI), logm_scale = (float)(2.0 / (LOGM_HI - LOGM_LO));
   const float cs = 2.f / (C_HI - C_LO), cm = C_LO + C_HI;
+  u[0] = (2.f * rp.c[0] - cm) * 0.5f * cs;
+  u[1] = (2.f * rp.c[1] - cm) * 0.5f * cs;
+  u[2] = (2.f * rp.c[2] - cm) * 0.5f * cs;
+  u[3] = rp.R[0] / RHO_MAX;
+  u[4] = rp.R[1] / RHO_MAX;
+  u[5] = rp.R[2] / RHO_MAX;
+  u[6] = (2.f * rp.logm - logm_mid) * (0.5f * logm_scale);
+}
 
-  for (int64_t tile = (int64_t)blockIdx.x * WARPS + warp; tile < ntiles; tile += (int64_t)gridDim.x * WARPS) {
-    const int i = (int)(tile / tpc);
-    const int64_t j0 = (tile % tpc) * PPT;
-    const CompT<float> &c = comp[i];
-    // prep: lanes 0..15 are the tile's rows
-    bool push = false;
-    int64_t push_j = 0;
-    if (lane < WROWS) {
-      const int row = lane;
-      const int pair = DENS ? row : row >> 1, pass = DENS ? 0 : (row & 1);
-      const int64_t j = j0 + pair;
-      bf16 *xr = S.X + row * XP;
-      if (j < n) {
-        const RowProblem rp = row_problem(c, Y, p, j, pass);
-        const float u[DIN] = {(2.f * rp.c[0] - cm) * 0.5f * cs, (2.f * rp.c[1] - cm) * 0.5f * cs,
-                              (2.f * rp.c[2] - cm) * 0.5f * cs, rp.R[0] / RHO_MAX, rp.R[1] / RHO_MAX,
-                              rp.R[2] / RHO_MAX, (2.f * rp.logm - logm_mid) * (0.5f * logm_scale)};
+// Every pair's two network inputs exactly as the surrogate E-step hands them
+// to the tensor cores (BF16-rounded, returned as floats): x_out[(i n + j) 2 +
+// pass][7], and the pair's domain class kind[i n + j] (2 in the domain, 1 the
+// point clamped into the box, 0 outside).
+__global__ void inputs_kernel(const double *Y, int64_t n, int g, int p, const CompT<float> *comp, float *x_out,
+                              int *kind) {
+  const int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (k >= 2 * (int64_t)g * n) return;
+  const int64_t ij = k >> 1;
+  const int pass = (int)(k & 1), i = (int)(ij / n);
+  const int64_t j = ij % n;
+  const RowProblem rp = row_problem(comp[i], Y, p, j, pass);
+  float u[DIN];
+  network_input(rp, u);
 #pragma unroll
-        for (int t = 0; t < DINP; t += 2)
-          *reinterpret_cast<__nv_bfloat162 *>(xr + t) =
-              __floats2bfloat162_rn(t < DIN ? u[t] : 0.f, t + 1 < DIN ? u[t + 1] : 0.f);
-        if (pass == 0) {
-          S.logt[pair] = rp.logt;
-          S.nud[pair] = rp.nud;
-          S.q[3 * pair] = rp.q[0];
-          S.q[3 * pair + 1] = rp.q[1];
-          S.q[3 * pair + 2] = rp.q[2];
-          S.kind[pair] = rp.kind;
-          S.cmax[pair] = rp.cmaxA;
-          push = (rp.kind != 2);
-          push_j = j;
-        }
-      } else {
+  for (int t = 0; t < DIN; ++t) x_out[k * DIN + t] = __bfloat162float(__float2bfloat16_rn(u[t]));
+  if (pass == 0) kind[ij] = rp.kind;
+}
+
+// ---------------------------------------------------------------------------
+// The network on the fifth-generation tensor cores (tcgen05).
+//
+// A CTA of four warpgroups (512 threads, one CTA per SM) holds the BF16
+// weights in shared memory in the UMMA K-major layout (W_l as [out][in]: the
+// B operand).  Each warpgroup owns a 32 KB activation tile (128 rows x 128
+// BF16, the A operand) and 128 columns of tensor memory (its FP32
+// accumulator, row t in lane t).  Thread t of a warpgroup is network row t
+// throughout: it writes its input row, and after each layer's MMAs (issued by
+// the warpgroup's first thread, completion signalled on the warpgroup's
+// mbarrier) reads its accumulator row from tensor memory, adds the bias,
+// applies GELU on FP32 pairs and writes the BF16 activations back into the
+// tile as the next layer's A operand.  The four warpgroups run independently,
+// so one's GELU epilogue overlaps the others' MMAs.
+// ---------------------------------------------------------------------------
+namespace tcn {
+constexpr int WG = 4;                                    // warpgroups per CTA
+constexpr int ROWS = 128;                                // rows per warpgroup tile (MMA M)
+constexpr uint32_t OFF_W4 = 0;                           // [16 out][128 in]
+constexpr uint32_t OFF_W1 = OFF_W4 + DOUTP * H * 2;      // [128 out][16 in]
+constexpr uint32_t OFF_W2 = OFF_W1 + H * DINP * 2;       // [128 out][128 in]
+constexpr uint32_t OFF_W3 = OFF_W2 + H * H * 2;
+constexpr uint32_t OFF_ACT = OFF_W3 + H * H * 2;         // per-warpgroup activation tiles
+constexpr uint32_t ACT_BYTES = ROWS * H * 2;
+constexpr uint32_t OFF_BIAS = OFF_ACT + WG * ACT_BYTES;  // b1, b2, b3 [128], b4 [16]
+constexpr uint32_t OFF_NORM = OFF_BIAS + (3 * H + DOUTP) * 4;
+constexpr uint32_t OFF_BAR = OFF_NORM + 2 * DOUT * 4;    // one mbarrier per warpgroup
+constexpr uint32_t OFF_TSLOT = OFF_BAR + WG * 8;         // tensor-memory address
+constexpr uint32_t SMEM = OFF_TSLOT + 16;
+constexpr uint32_t TMEM_COLS = WG * 128;
+constexpr uint32_t SBO_K16 = (DINP / 8) * 128, SBO_K128 = (H / 8) * 128;
+constexpr uint32_t IDESC_HID = tc::idesc_bf16_f32(ROWS, H), IDESC_OUT = tc::idesc_bf16_f32(ROWS, DOUTP);
+constexpr int WAIT_POLLS = 1 << 22;
+static_assert(OFF_BAR % 8 == 0, "mbarriers need 8-byte alignment");
+static_assert(SMEM <= 227 * 1024, "shared memory of one CTA");
+// every descriptor of a misread layout would still address this CTA's own
+// shared memory: the largest reach of a 128 x 128 tile is 32 KB from its start
+static_assert(OFF_W4 + ROWS * H * 2 <= SMEM && OFF_ACT + WG * ACT_BYTES <= SMEM, "operand reach");
+
+struct Ctx {
+  unsigned char *smem;
+  uint32_t sbase;    // shared address of smem
+  uint32_t act;      // shared address of this warpgroup's activation tile
+  uint32_t tmem_d;   // this warpgroup's accumulator (lane 0, its first column)
+  uint32_t tmem_t;   // the same with this thread's warp's lane quarter
+  uint64_t *bar;
+  uint32_t bar_id;   // named barrier of this warpgroup (1..4)
+  int row;           // 0..127
+};
+
+// Copies the packed BF16 weights into the UMMA layout and the biases and
+// target normalisation into shared memory (whole CTA).
+__device__ void stage_network(const SurrogateDev &sd, unsigned char *smem) {
+  const bf16 *W1 = static_cast<const bf16 *>(sd.W1), *W2 = static_cast<const bf16 *>(sd.W2);
+  const bf16 *W3 = static_cast<const bf16 *>(sd.W3), *W4 = static_cast<const bf16 *>(sd.W4);
+  for (int e = threadIdx.x; e < DINP * H; e += blockDim.x) {
+    const int k = e / H, o = e % H;
+    *reinterpret_cast<bf16 *>(smem + OFF_W1 + tc::kmajor_offset(o, k, DINP)) = W1[e];
+  }
+  for (int e = threadIdx.x; e < H * H; e += blockDim.x) {
+    const int k = e / H, o = e % H;
+    *reinterpret_cast<bf16 *>(smem + OFF_W2 + tc::kmajor_offset(o, k, H)) = W2[e];
+    *reinterpret_cast<bf16 *>(smem + OFF_W3 + tc::kmajor_offset(o, k, H)) = W3[e];
+  }
+  for (int e = threadIdx.x; e < H * DOUTP; e += blockDim.x) {
+    const int k = e / DOUTP, o = e % DOUTP;
+    *reinterpret_cast<bf16 *>(smem + OFF_W4 + tc::kmajor_offset(o, k, H)) = W4[e];
+  }
+  float *bias = reinterpret_cast<float *>(smem + OFF_BIAS);
+  for (int e = threadIdx.x; e < H; e += blockDim.x) {
+    bias[e] = sd.b1[e];
+    bias[H + e] = sd.b2[e];
+    bias[2 * H + e] = sd.b3[e];
+  }
+  if (threadIdx.x < DOUTP) bias[3 * H + threadIdx.x] = sd.b4[threadIdx.x];
+  if (threadIdx.x < 2 * DOUT) reinterpret_cast<float *>(smem + OFF_NORM)[threadIdx.x] = sd.norm[threadIdx.x];
+}
+
+// CTA set-up: network staged, mbarriers initialised, 512 tensor-memory
+// columns allocated by warp 0; returns this thread's view.
+__device__ Ctx setup(const SurrogateDev &sd, unsigned char *smem) {
+  stage_network(sd, smem);
+  uint64_t *bars = reinterpret_cast<uint64_t *>(smem + OFF_BAR);
+  uint32_t *slot = reinterpret_cast<uint32_t *>(smem + OFF_TSLOT);
+  if (threadIdx.x < WG) tc::mbar_init1(bars + threadIdx.x);
+  if (threadIdx.x < 32) {
+    tc::tmem_alloc(slot, TMEM_COLS);
+    tc::tmem_relinquish();
+  }
+  tc::fence_proxy_async_smem();
+  tc::fence_before_sync();
+  __syncthreads();
+  tc::fence_after_sync();
+  Ctx c;
+  const int wg = threadIdx.x >> 7;
+  c.smem = smem;
+  c.sbase = tc::smem_u32(smem);
+  c.row = threadIdx.x & 127;
+  c.act = c.sbase + OFF_ACT + wg * ACT_BYTES;
+  c.tmem_d = *slot + wg * 128;
+  c.tmem_t = c.tmem_d + ((uint32_t)((c.row >> 5) * 32) << 16);
+  c.bar = bars + wg;
+  c.bar_id = 1 + wg;
+  return c;
+}
+
+// Barrier of the warpgroup that also ORs a flag over its threads (one
+// instruction), so a give-up decision is the warpgroup's, never one thread's.
+__device__ __forceinline__ bool sync_or(uint32_t id, bool flag) {
+  uint32_t out;
+  asm volatile(
+      "{\n .reg .pred pi, po;\n setp.ne.u32 pi, %1, 0;\n bar.red.or.pred po, %2, 128, pi;\n"
+      " selp.u32 %0, 1, 0, po;\n}\n"
+      : "=r"(out)
+      : "r"((uint32_t)flag), "r"(id)
+      : "memory");
+  return out != 0;
+}
+
+// This thread's input row (7 normalised values, zero padded to 16) as BF16
+// into the activation tile, in the K = 16 layout of layer 1.
+__device__ __forceinline__ void write_input(const Ctx &c, const float (&u)[DIN]) {
+  uint32_t w[8];
 #pragma unroll
-        for (int t = 0; t < DINP; t += 2)
-          *reinterpret_cast<__nv_bfloat162 *>(xr + t) = __floats2bfloat162_rn(0.f, 0.f);
-        if (pass == 0) S.kind[pair] = -1;
-      }
+  for (int q = 0; q < 8; ++q)
+    w[q] = pack_bf16x2(2 * q < DIN ? u[2 * q] : 0.f, 2 * q + 1 < DIN ? u[2 * q + 1] : 0.f);
+  tc::st_shared_v4(c.act + tc::kmajor_offset(c.row, 0, DINP), w[0], w[1], w[2], w[3]);
+  tc::st_shared_v4(c.act + tc::kmajor_offset(c.row, 8, DINP), w[4], w[5], w[6], w[7]);
+}
+
+// One layer's MMAs by the warpgroup's first thread: D = A W^T over `ksteps`
+// slices of 16, then a completion arrive on the warpgroup's mbarrier.
+__device__ __forceinline__ void issue(const Ctx &c, uint32_t w_off, uint32_t a_sbo, uint32_t b_sbo, int ksteps,
+                                      uint32_t idesc) {
+  if (c.row != 0) return;
+  tc::fence_after_sync();
+  const uint32_t wb = c.sbase + w_off;
+  for (int ks = 0; ks < ksteps; ++ks)
+    tc::mma_bf16(c.tmem_d, tc::smem_desc(c.act + ks * 256, 128, a_sbo), tc::smem_desc(wb + ks * 256, 128, b_sbo),
+                 idesc, ks > 0 ? 1u : 0u);
+  tc::mma_commit(c.bar);
+}
+
+// Bounded wait for the layer's MMAs; false (this thread gave up) after the bound.
+__device__ __forceinline__ bool wait_mma(const Ctx &c, uint32_t &phase) {
+  const bool ok = tc::mbar_wait(c.bar, phase, WAIT_POLLS);
+  phase ^= 1u;
+  tc::fence_after_sync();
+  return ok;
+}
+
+// Hidden-layer epilogue of this thread's row: accumulator + bias, GELU, BF16,
+// stored as the next layer's A operand (K = 128 layout), 32 columns at a time.
+__device__ __forceinline__ void hidden_epilogue(const Ctx &c, const float *bias) {
+#pragma unroll 1
+  for (int cc = 0; cc < H / 32; ++cc) {
+    uint32_t v[32];
+    tc::tmem_ld32(c.tmem_t + cc * 32, v);
+    tc::tmem_wait_ld();
+    uint32_t w[16];
+    const float2 *b2 = reinterpret_cast<const float2 *>(bias + cc * 32);
+#pragma unroll
+    for (int q = 0; q < 16; ++q) {
+      const float2 z = __fadd2_rn(make_float2(__uint_as_float(v[2 * q]), __uint_as_float(v[2 * q + 1])), b2[q]);
+      const float2 gz = gelu_x2(z);
+      w[q] = pack_bf16x2(gz.x, gz.y);
     }
+#pragma unroll
+    for (int u = 0; u < 4; ++u)
+      tc::st_shared_v4(c.act + tc::kmajor_offset(c.row, cc * 32 + 8 * u, H), w[4 * u], w[4 * u + 1], w[4 * u + 2],
+                       w[4 * u + 3]);
+  }
+}
+
+// The whole network for the warpgroup's tile (every thread's input row
+// already written): o receives this thread's 16 output columns (10 used,
+// bias added, still standardised).  Returns false, uniformly over the
+// warpgroup, when a completion wait gave up (then *gave_up is set).
+__device__ bool forward(const Ctx &c, uint32_t &phase, float (&o)[DOUTP], bool &gave_up) {
+  const float *bias = reinterpret_cast<const float *>(c.smem + OFF_BIAS);
+  bool bad = false;
+  tc::fence_proxy_async_smem();
+  tc::fence_before_sync();
+  // a wait given up in the previous tile ends the warpgroup's work here
+  if (sync_or(c.bar_id, gave_up)) {
+    gave_up = true;
+    return false;
+  }
+  issue(c, OFF_W1, SBO_K16, SBO_K16, DINP / 16, IDESC_HID);
+#pragma unroll 1
+  for (int layer = 0; layer < 3; ++layer) {
+    bad = !wait_mma(c, phase) || bad;
+    hidden_epilogue(c, bias + layer * H);
+    tc::fence_proxy_async_smem();
+    tc::fence_before_sync();
+    if (sync_or(c.bar_id, bad)) {
+      gave_up = true;
+      return false;
+    }
+    if (layer < 2)
+      issue(c, layer == 0 ? OFF_W2 : OFF_W3, SBO_K128, SBO_K128, H / 16, IDESC_HID);
+    else
+      issue(c, OFF_W4, SBO_K128, SBO_K128, H / 16, IDESC_OUT);
+  }
+  bad = !wait_mma(c, phase) || bad;
+  uint32_t v[16];
+  tc::tmem_ld16(c.tmem_t, v);
+  tc::tmem_wait_ld();
+#pragma unroll
+  for (int k = 0; k < DOUTP; ++k) o[k] = __uint_as_float(v[k]) + bias[3 * H + k];
+  // the next tile's first barrier orders these reads before its MMAs
+  tc::fence_before_sync();
+  if (bad) gave_up = true;
+  return true;
+}
+
+// CTA tear-down: every warpgroup done with tensor memory, warp 0 frees it.
+// A warpgroup that gave up first lets its last MMAs finish (bounded).
+__device__ void teardown(const Ctx &c, uint32_t phase, bool gave_up, int *status) {
+  if (sync_or(c.bar_id, gave_up) && c.row == 0) {
+    tc::mbar_wait(c.bar, phase ^ 1u, WAIT_POLLS);
+    if (status) atomicOr(status, ERR_TIMEOUT);
+  }
+  tc::fence_before_sync();
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    tc::fence_after_sync();
+    tc::tmem_dealloc(*reinterpret_cast<const uint32_t *>(c.smem + OFF_TSLOT) , TMEM_COLS);
+  }
+}
+
+}  // namespace tcn
+
+// Network prediction of raw problems x [B][7] -> outputs y [B][10]
+// (de-normalised, moments form) on the tensor cores.
+__global__ void __launch_bounds__(tcn::WG * 128, 1)
+    predict_tc_kernel(SurrogateDev sd, const float *x, float *y, int64_t B, int *status) {
+  extern __shared__ __align__(1024) unsigned char smem[];
+  const tcn::Ctx c = tcn::setup(sd, smem);
+  const int wg = threadIdx.x >> 7;
+  const float *norm = reinterpret_cast<const float *>(smem + tcn::OFF_NORM);
+  const int64_t ntiles = (B + tcn::ROWS - 1) / tcn::ROWS;
+  uint32_t phase = 0;
+  bool gave_up = false;
+  for (int64_t tile = (int64_t)blockIdx.x * tcn::WG + wg; tile < ntiles; tile += (int64_t)gridDim.x * tcn::WG) {
+    const int64_t b = tile * tcn::ROWS + c.row;
+    float u[DIN];
+    if (b < B) {
+      normalise_input(x + b * DIN, u);
+    } else {
+#pragma unroll
+      for (int t = 0; t < DIN; ++t) u[t] = 0.f;
+    }
+    tcn::write_input(c, u);
+    float o[DOUTP];
+    if (!tcn::forward(c, phase, o, gave_up)) break;
+    if (b < B) {
+      float t[DOUT];
+#pragma unroll
+      for (int k = 0; k < DOUT; ++k) t[k] = fmaf(o[k], norm[DOUT + k], norm[k]);
+      from_net(t, y + b * DOUT);
+    }
+  }
+  tcn::teardown(c, phase, gave_up, status);
+}
+
+// Fused surrogate E-step on the tensor cores.  A warpgroup tile is 64 pairs
+// of one component as 128 network rows: row 2k is pair k's pass A (dof
+// nu + p), row 2k + 1 its pass B (nu + p + 2), so a pair's two rows sit in
+// adjacent lanes of one warp; for the density alone a tile is 128 pairs, one
+// row each (pass A).  Each thread prepares its row's standardised problem
+// (FP32 prologue), runs the network, and the pair's two threads form log f
+// and e1..e4 from the two output rows (the even thread log f, e1, e2, e3;
+// the odd thread e4).  Pairs outside the training domain are appended to the
+// lattice rule's list (one atomic per warp).
+template <bool DENS>
+__global__ void __launch_bounds__(tcn::WG * 128, 1)
+    surrogate_estep_tc_kernel(SurrogateDev sd, const double *Y, int64_t n, int g, int p,
+                              const CompT<float> *__restrict__ comp, EstepOut out, int *fb_list, unsigned *fb_count,
+                              int *status) {
+  extern __shared__ __align__(1024) unsigned char smem[];
+  const tcn::Ctx c = tcn::setup(sd, smem);
+  const int wg = threadIdx.x >> 7, lane = threadIdx.x & 31;
+  const float *mean = reinterpret_cast<const float *>(smem + tcn::OFF_NORM), *sdv = mean + DOUT;
+  constexpr int PPT = DENS ? tcn::ROWS : tcn::ROWS / 2;  // pairs per tile
+  const int64_t tpc = (n + PPT - 1) / PPT;
+  const int64_t ntiles = tpc * g;
+  const int pair = DENS ? c.row : c.row >> 1, pass = DENS ? 0 : (c.row & 1);
+  uint32_t phase = 0;
+  bool gave_up = false;
+  for (int64_t tile = (int64_t)blockIdx.x * tcn::WG + wg; tile < ntiles; tile += (int64_t)gridDim.x * tcn::WG) {
+    const int i = (int)(tile / tpc);
+    const int64_t j = (tile % tpc) * PPT + pair;
+    const CompT<float> &cp = comp[i];
+    const bool valid = j < n;
+    RowProblem rp;
+    float u[DIN];
+    if (valid) {
+      rp = row_problem(cp, Y, p, j, pass);
+      network_input(rp, u);
+    } else {
+      rp.kind = -1;
+#pragma unroll
+      for (int t = 0; t < DIN; ++t) u[t] = 0.f;
+    }
+    tcn::write_input(c, u);
     // pairs outside the domain go to the lattice rule's list: one atomic per warp
+    const bool push = valid && pass == 0 && rp.kind != 2;
     const unsigned pm = __ballot_sync(0xffffffffu, push);
     if (pm) {
       unsigned base = 0;
       if (lane == 0) base = atomicAdd(fb_count + i, (unsigned)__popc(pm));
       base = __shfl_sync(0xffffffffu, base, 0);
-      if (push) fb_list[(int64_t)i * n + base + __popc(pm & ((1u << lane) - 1u))] = (int)push_j;
+      if (push) fb_list[(int64_t)i * n + base + __popc(pm & ((1u << lane) - 1u))] = (int)j;
     }
-    __syncwarp();
+    float o[DOUTP];
+    if (!tcn::forward(c, phase, o, gave_up)) break;
 
-    // layer 1: A fragment of the 16 x 16 (zero-padded) input tile
-    uint32_t a0[1][4];
-    {
-      const bf16 *r0 = S.X + gid * XP + tig * 2;
-      a0[0][0] = ld32(r0);
-      a0[0][1] = ld32(r0 + 8 * XP);
-      a0[0][2] = ld32(r0 + 8);
-      a0[0][3] = ld32(r0 + 8 * XP + 8);
-    }
-    uint32_t h1[8][4], h2[8][4];
-    dense_gelu<1>(a0, Wsm.W1t, XP, Wsm.bias, h1, gid, tig);
-    dense_gelu<8>(h1, Wsm.W2t, HP, Wsm.bias + H, h2, gid, tig);
-    dense_gelu<8>(h2, Wsm.W3t, HP, Wsm.bias + 2 * H, h1, gid, tig);
-    {
-      // output layer: 16 rows x 16 columns (10 used)
-      float o[2][4];
+    const int64_t ij = (int64_t)i * n + j;
+    // this row's log T (pass A: T_A, pass B: T_B) and standardised first moments
+    const float logT = -__expf(fmaf(o[0], sdv[0], mean[0]));
+    float EX[3];
 #pragma unroll
-      for (int a = 0; a < 2; ++a)
-#pragma unroll
-        for (int b = 0; b < 4; ++b) o[a][b] = 0.f;
-      const int lane = (gid << 2) | tig;
-      const bf16 *wl = Wsm.W4t + (((lane >> 4) * 8 + (lane & 7)) * HP + ((lane >> 3) & 1) * 8);
-#pragma unroll
-      for (int kt = 0; kt < 8; ++kt) {
-        uint32_t b4[4];
-        ldsm_x4(b4, wl + kt * 16);
-        const uint32_t b0[2] = {b4[0], b4[1]}, b1[2] = {b4[2], b4[3]};
-        mma_bf16(o[0], h1[kt], b0);
-        mma_bf16(o[1], h1[kt], b1);
+    for (int t = 0; t < 3; ++t) EX[t] = fmaf(o[1 + t], sdv[1 + t], mean[1 + t]);
+    if (DENS) {
+      if (valid) {
+        float *lf = static_cast<float *>(out.logf);
+        if (rp.kind == 2) lf[ij] = rp.logt + logT;
+        if (rp.kind == 0) lf[ij] = INFINITY;
+        if (rp.kind == 1) {
+          // the lattice rule's triage bound: log T is decreasing in every c_t,
+          // so the network at the box-clamped point plus a margin bounds it;
+          // and P(X > c) <= P(X_t > c_t) <= (m + c_t^2) f_m(c_t) / ((m - 1) c_t)
+          // for c_t > 0 (f_m the t_m density), tightest at pass A's largest coordinate
+          float ub = logT + UB_MARGIN;
+          const float cmx = rp.cmaxA, m = cp.fmA;
+          if (cmx > 0.f && m > 1.f) {
+            const float lnorm = lgammaf(0.5f * (m + 1.f)) - lgammaf(0.5f * m) - 0.5f * logf(m * 3.14159265f);
+            const float lb =
+                logf((m + cmx * cmx) / ((m - 1.f) * cmx)) + lnorm - 0.5f * (m + 1.f) * log1pf(cmx * cmx / m);
+            ub = fminf(ub, lb + 1e-3f);
+          }
+          lf[ij] = rp.logt + ub;
+        }
       }
-#pragma unroll
-      for (int nt = 0; nt < 2; ++nt) {
-        const int col = nt * 8 + tig * 2;
-        const float b0 = Wsm.bias[3 * H + col], b1 = Wsm.bias[3 * H + col + 1];
-        S.O[gid * OP + col] = o[nt][0] + b0;
-        S.O[gid * OP + col + 1] = o[nt][1] + b1;
-        S.O[(gid + 8) * OP + col] = o[nt][2] + b0;
-        S.O[(gid + 8) * OP + col + 1] = o[nt][3] + b1;
-      }
+      continue;
     }
-    __syncwarp();
-
-    // epilogue: one lane per pair for the density; four lanes per pair for
-    // the full E-step (part 0: log f, e1, e2; part 1: e3; parts 2, 3: e4)
-    constexpr int PARTS = DENS ? 1 : 4;
-    if (lane < PPT * PARTS) {
-      const int pair = lane / PARTS, part = lane % PARTS;
-      const int64_t j = j0 + pair;
-      const int kind = (j < n) ? S.kind[pair] : -1;
-      const int64_t ij = (int64_t)i * n + j;
-      const float *mean = Wsm.norm, *sdv = Wsm.norm + DOUT;
-      const float *oA = S.O + (DENS ? pair : 2 * pair) * OP;
-      const float logTA = -__expf(fmaf(oA[0], sdv[0], mean[0]));
-      // pairs left to the lattice rule carry an upper bound of log f for its
-      // triage: log T is decreasing in every c_t, so the network's value at
-      // the box-clamped point plus a margin bounds it; none without a domain
-      if (kind == 1 && part == 0) {
-        // and P(X > c) <= P(X_t > c_t) <= (m + c_t^2) f_m(c_t) / ((m - 1) c_t)
-        // for c_t > 0, f_m the t_m density (from d/dx[(m + x^2) f_m(x)] =
-        // -(m - 1) x f_m(x)); the bound decreases in c_t, so the largest
-        // coordinate of pass A's point gives the tightest one
+    // the pair's other row: pass A's log T for the odd thread, pass B's log T
+    // and first moments for the even one
+    const float logT_o = __shfl_xor_sync(0xffffffffu, logT, 1);
+    float EX_o[3];
+#pragma unroll
+    for (int t = 0; t < 3; ++t) EX_o[t] = __shfl_xor_sync(0xffffffffu, EX[t], 1);
+    if (!valid) continue;
+    const float logTA = pass ? logT_o : logT, logTB = pass ? logT : logT_o;
+    const float *EXB = pass ? EX : EX_o;
+    if (pass == 0) {
+      float *lf = static_cast<float *>(out.logf);
+      if (rp.kind == 1) {
         float ub = logTA + UB_MARGIN;
-        const float cmx = S.cmax[pair], m = c.fmA;
+        const float cmx = rp.cmaxA, m = cp.fmA;
         if (cmx > 0.f && m > 1.f) {
           const float lnorm = lgammaf(0.5f * (m + 1.f)) - lgammaf(0.5f * m) - 0.5f * logf(m * 3.14159265f);
-          const float lb = logf((m + cmx * cmx) / ((m - 1.f) * cmx)) + lnorm - 0.5f * (m + 1.f) * log1pf(cmx * cmx / m);
+          const float lb =
+              logf((m + cmx * cmx) / ((m - 1.f) * cmx)) + lnorm - 0.5f * (m + 1.f) * log1pf(cmx * cmx / m);
           ub = fminf(ub, lb + 1e-3f);
         }
-        static_cast<float *>(out.logf)[ij] = S.logt[pair] + ub;
+        lf[ij] = rp.logt + ub;
       }
-      if (kind == 0 && part == 0) static_cast<float *>(out.logf)[ij] = INFINITY;
-      if (kind == 2) {
-        if (part == 0) static_cast<float *>(out.logf)[ij] = S.logt[pair] + logTA;
-        if (!DENS) {
-          const float *oB = oA + OP;
-          const float logTB = -__expf(fmaf(oB[0], sdv[0], mean[0]));
-          const float nud = S.nud[pair];
-          const float mA = c.fmA, mB = c.fmB;
-          const float e1 = mA / nud * __expf(logTB - logTA);
-          if (part == 0) {
-            static_cast<float *>(out.e1)[ij] = e1;
-            static_cast<float *>(out.e2)[ij] = e1 - (logf(0.5f * nud) + mA / nud - c.fpsiA);
-          } else {
-            const float sig = sqrtf(nud / mB);
-            // E[X] and E[X X^T] of pass B in the Lambda basis: D^{1/2} (.) D^{1/2}
-            const float L00 = c.L[0], L10 = c.L[RMAX], L11 = c.L[RMAX + 1];
-            const float L20 = c.L[2 * RMAX], L21 = c.L[2 * RMAX + 1], L22 = c.L[2 * RMAX + 2];
-            const float sD[3] = {fabsf(L00), sqrtf(fmaf(L10, L10, L11 * L11)),
-                                 sqrtf(fmaf(L20, L20, fmaf(L21, L21, L22 * L22)))};
-            const float *qp = S.q + 3 * pair;
-            float LEV[3], EXs[3];
-#pragma unroll
-            for (int t = 0; t < 3; ++t) {
-              EXs[t] = fmaf(oB[1 + t], sdv[1 + t], mean[1 + t]);
-              LEV[t] = sD[t] * EXs[t];
-            }
-            if (part == 1) {
-#pragma unroll
-              for (int t = 0; t < 3; ++t)
-                static_cast<float *>(out.e3)[((int64_t)i * 3 + t) * n + j] = e1 * fmaf(sig, LEV[t], qp[t]);
-            } else {
-              // e4 in lower-triangle order (0,0) (1,0) (1,1) | (2,0) (2,1) (2,2)
-              // (part 2 | part 3); the network's covariance comes in upper
-              // order 00 01 02 11 12 22
-              constexpr int UP[3][3] = {{0, 1, 2}, {1, 3, 4}, {2, 4, 5}};
-              float cv[6];
-#pragma unroll
-              for (int u = 0; u < 6; ++u) cv[u] = fmaf(oB[4 + u], sdv[4 + u], mean[4 + u]);
-              psd_repair3(cv);
-#pragma unroll
-              for (int t = 0; t < 3; ++t)
-#pragma unroll
-                for (int h = 0; h <= t; ++h) {
-                  if ((t == 2) != (part == 3)) continue;
-                  const int u = UP[t][h];
-                  // the network gives the covariance; E[X'_h X'_t] = cov + E[X'_h] E[X'_t]
-                  const float Sth = sD[t] * sD[h] * fmaf(EXs[h], EXs[t], cv[u]);
-                  const float exx = qp[t] * qp[h] + sig * (qp[t] * LEV[h] + LEV[t] * qp[h]) + sig * sig * Sth;
-                  static_cast<float *>(out.e4)[((int64_t)i * 6 + t * (t + 1) / 2 + h) * n + j] = e1 * exx;
-                }
-            }
-          }
-        }
-      }
+      if (rp.kind == 0) lf[ij] = INFINITY;
     }
-    __syncwarp();  // the scratch is reused by the next tile
+    if (rp.kind != 2) continue;
+    const float nud = rp.nud, mA = cp.fmA, mB = cp.fmB;
+    const float e1 = mA / nud * __expf(logTB - logTA);
+    const float sig = sqrtf(nud / mB);
+    // E[X] and E[X X^T] of pass B in the Lambda basis: D^{1/2} (.) D^{1/2}
+    const float L00 = cp.L[0], L10 = cp.L[RMAX], L11 = cp.L[RMAX + 1];
+    const float L20 = cp.L[2 * RMAX], L21 = cp.L[2 * RMAX + 1], L22 = cp.L[2 * RMAX + 2];
+    const float sD[3] = {fabsf(L00), sqrtf(fmaf(L10, L10, L11 * L11)), sqrtf(fmaf(L20, L20, fmaf(L21, L21, L22 * L22)))};
+    float LEV[3];
+#pragma unroll
+    for (int t = 0; t < 3; ++t) LEV[t] = sD[t] * EXB[t];
+    if (pass == 0) {
+      static_cast<float *>(out.logf)[ij] = rp.logt + logTA;
+      static_cast<float *>(out.e1)[ij] = e1;
+      static_cast<float *>(out.e2)[ij] = e1 - (logf(0.5f * nud) + mA / nud - cp.fpsiA);
+#pragma unroll
+      for (int t = 0; t < 3; ++t)
+        static_cast<float *>(out.e3)[((int64_t)i * 3 + t) * n + j] = e1 * fmaf(sig, LEV[t], rp.q[t]);
+    } else {
+      // e4 in lower-triangle order from the network's covariance (upper order
+      // 00 01 02 11 12 22): E[X'_h X'_t] = cov + E[X'_h] E[X'_t]
+      constexpr int UP[3][3] = {{0, 1, 2}, {1, 3, 4}, {2, 4, 5}};
+      float cv[6];
+#pragma unroll
+      for (int q = 0; q < 6; ++q) cv[q] = fmaf(o[4 + q], sdv[4 + q], mean[4 + q]);
+      psd_repair3(cv);
+#pragma unroll
+      for (int t = 0; t < 3; ++t)
+#pragma unroll
+        for (int h = 0; h <= t; ++h) {
+          const float Sth = sD[t] * sD[h] * fmaf(EXB[h], EXB[t], cv[UP[t][h]]);
+          const float exx = rp.q[t] * rp.q[h] + sig * (rp.q[t] * LEV[h] + LEV[t] * rp.q[h]) + sig * sig * Sth;
+          static_cast<float *>(out.e4)[((int64_t)i * 6 + t * (t + 1) / 2 + h) * n + j] = e1 * exx;
+        }
+    }
   }
+  tcn::teardown(c, phase, gave_up, status);
 }
 
 // The standardised problems (network inputs of pass A and pass B) of every
@@ -958,29 +1091,36 @@ cudaError_t launch_surrogate_problems(const double *Y, int64_t n, int g, int p, 
   return cudaGetLastError();
 }
 
+cudaError_t launch_surrogate_inputs(const double *Y, int64_t n, int g, int p, const CompT<float> *c32, float *x_out,
+                                    int *kind, cudaStream_t st) {
+  const int64_t m = 2 * (int64_t)g * n;
+  if (m <= 0) return cudaSuccess;
+  sg::inputs_kernel<<<(unsigned)((m + 255) / 256), 256, 0, st>>>(Y, n, g, p, c32, x_out, kind);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_surrogate_estep(const SurrogateDev &sd, const double *Y, int64_t n, int g, int p,
                                    const CompT<float> *c32, EstepOut out, bool density_only, int *fb_list,
-                                   unsigned *fb_count, cudaStream_t st) {
+                                   unsigned *fb_count, int *status, cudaStream_t st) {
   cudaError_t e = cudaMemsetAsync(fb_count, 0, sizeof(unsigned) * g, st);
   if (e != cudaSuccess || n <= 0) return e;
-  const int smem = (int)sg::INFER_SMEM;
-  const int64_t ppt = density_only ? sg::WROWS : sg::WROWS / 2;
+  const int smem = (int)sg::tcn::SMEM;
+  const int64_t ppt = density_only ? sg::tcn::ROWS : sg::tcn::ROWS / 2;
   const int64_t ntiles = (n + ppt - 1) / ppt * g;
-  int dev = 0, sms = 152;
-  cudaGetDevice(&dev);
-  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  int64_t blocks = (ntiles + sg::WARPS - 1) / sg::WARPS;
+  const int sms = sm_count();
+  int64_t blocks = (ntiles + sg::tcn::WG - 1) / sg::tcn::WG;
   if (blocks > sms) blocks = sms;
   if (density_only) {
-    e = cudaFuncSetAttribute(sg::surrogate_estep_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    e = cudaFuncSetAttribute(sg::surrogate_estep_tc_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     if (e != cudaSuccess) return e;
-    sg::surrogate_estep_kernel<true><<<(unsigned)blocks, sg::WARPS * 32, smem, st>>>(sd, Y, n, g, p, c32, out,
-                                                                                     fb_list, fb_count);
+    sg::surrogate_estep_tc_kernel<true><<<(unsigned)blocks, sg::tcn::WG * 128, smem, st>>>(sd, Y, n, g, p, c32, out,
+                                                                                           fb_list, fb_count, status);
   } else {
-    e = cudaFuncSetAttribute(sg::surrogate_estep_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    e = cudaFuncSetAttribute(sg::surrogate_estep_tc_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             smem);
     if (e != cudaSuccess) return e;
-    sg::surrogate_estep_kernel<false><<<(unsigned)blocks, sg::WARPS * 32, smem, st>>>(sd, Y, n, g, p, c32, out,
-                                                                                      fb_list, fb_count);
+    sg::surrogate_estep_tc_kernel<false><<<(unsigned)blocks, sg::tcn::WG * 128, smem, st>>>(
+        sd, Y, n, g, p, c32, out, fb_list, fb_count, status);
   }
   return cudaGetLastError();
 }
@@ -1008,6 +1148,7 @@ struct cfust_surrogate {
   float *part = nullptr;
   int64_t part_len = 0;
   double *loss_part = nullptr;
+  int *d_status = nullptr;            // error bits of the network kernels
   int adam_t = 0;
 };
 
@@ -1314,6 +1455,8 @@ cfust_status cfust_surrogate_create(cfust_surrogate **out, uint64_t seed, const 
   CR(cudaMalloc(&s->b3, sizeof(float) * H));
   CR(cudaMalloc(&s->b4, sizeof(float) * DOUTP));
   CR(cudaMalloc(&s->loss_part, sizeof(double) * 256));
+  CR(cudaMalloc(&s->d_status, sizeof(int)));
+  CR(cudaMemsetAsync(s->d_status, 0, sizeof(int), s->stream));
   CR(cudaMemsetAsync(s->mom, 0, sizeof(float) * NPARAM, s->stream));
   CR(cudaMemsetAsync(s->vel, 0, sizeof(float) * NPARAM, s->stream));
   // initial weights: N(0, 1/fan_in), zero biases; unit target normalisation
@@ -1348,7 +1491,7 @@ cfust_status cfust_surrogate_destroy(cfust_surrogate *s) {
   if (!s) return CFUST_OK;
   void *bufs[] = {s->tab, s->theta, s->mom, s->vel, s->grad, s->norm, s->W1, s->W2, s->W3, s->W4, s->b1, s->b2, s->b3,
                   s->b4, s->x0, s->Z1, s->H1, s->Z2, s->H2, s->Z3, s->H3, s->out, s->dz4, s->dz3, s->dz2, s->dz1,
-                  s->part, s->loss_part};
+                  s->part, s->loss_part, s->d_status};
   for (void *p : bufs)
     if (p) cudaFree(p);
   delete s;
@@ -1370,12 +1513,19 @@ cfust_status cfust_surrogate_label(cfust_surrogate *s, const float *x, float *y,
 cfust_status cfust_surrogate_predict(cfust_surrogate *s, const float *x, float *y, int64_t B) {
   if (!s || !x || !y || B < 0 || B > MAX_ROWS) return sg_fail(s, CFUST_EINVAL, "bad arguments (0 <= B <= 2^30)");
   if (B == 0) return CFUST_OK;
-  cfust_status st = prep(s, x, B);
-  if (st != CFUST_OK) return st;
-  if ((st = forward(s, B)) != CFUST_OK) return st;
-  denorm_kernel<<<(unsigned)((B + 255) / 256), 256, 0, s->stream>>>(s->out, s->norm, y, B);
+  // the inference network on the tensor cores (tcgen05, accumulators in tensor memory)
+  const int64_t ntiles = (B + tcn::ROWS - 1) / tcn::ROWS;
+  int64_t blocks = (ntiles + tcn::WG - 1) / tcn::WG;
+  if (blocks > sm_count()) blocks = sm_count();
+  SG_CUDA(s, cudaFuncSetAttribute(predict_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tcn::SMEM));
+  SG_CUDA(s, cudaMemsetAsync(s->d_status, 0, sizeof(int), s->stream));
+  predict_tc_kernel<<<(unsigned)blocks, tcn::WG * 128, tcn::SMEM, s->stream>>>(surrogate_dev(s), x, y, B,
+                                                                               s->d_status);
   SG_CUDA(s, cudaGetLastError());
+  int bits = 0;
+  SG_CUDA(s, cudaMemcpyAsync(&bits, s->d_status, sizeof(int), cudaMemcpyDeviceToHost, s->stream));
   SG_CUDA(s, cudaStreamSynchronize(s->stream));
+  if (bits & ERR_TIMEOUT) return sg_fail(s, CFUST_ETIMEOUT, "a bounded tensor-core completion wait ran out");
   return CFUST_OK;
 }
 

@@ -157,3 +157,52 @@ def test_multistart_keeps_the_best_burned_in_start():
     c3 = binding.Context(lat, precision=binding.CFUST_FP32, max_iter=2)
     best0, _, _, _, _ = c3.cfust_fit_multistart(Yd, starts, burn_in=0)
     assert best0 == O.select_start([c3.cfust_loglik(Yd, st) for st in starts])
+
+
+def _oracle_fit_prioritised(Y, P, U, iters):
+    """The oracle's EM with variable prioritisation in every E-step."""
+    n = Y.shape[0]
+    params, trace = P.copy(), []
+    for _ in range(iters):
+        E = O.estep(Y, params, U, prioritise=True)
+        trace.append(E["loglik"])
+        params = O.mstep_update(O.mstep_sums(Y, E["tau"], E["e1"], E["e2"], E["e3"], E["e4"]), params, n)
+    trace.append(O.loglik(Y, params, U, prioritise=True))
+    return params, np.array(trace)
+
+
+def test_batched_prioritised_matches_oracle_fp64():
+    """Variable prioritisation in the persistent batched sweep: two fits, two
+    EM iterations in double precision against the oracle's prioritised EM."""
+    torch = _torch()
+    Ys, truths, inits = synth.batched_workload(2, seed0=7, n_lo=800, n_hi=1500, g_hi=3)
+    lat = synth.make_lattice(256, 4, 3)
+    U = O.lattice_points(lat.n, lat.z, lat.shift)
+    with binding.Context(lat, precision=binding.CFUST_FP64, max_iter=2, prioritise=True) as ctx:
+        bp, btr, st = ctx.cfust_fit_batched([torch.from_numpy(Y).cuda() for Y in Ys], inits)
+    assert all(s_ == 0 for s_ in st)
+    for f in range(2):
+        ref, ref_tr = _oracle_fit_prioritised(Ys[f], inits[f], U, 2)
+        assert np.allclose(btr[f], ref_tr, rtol=1e-10, atol=0)
+        for a, b in zip(bp[f].as_arrays(), ref.as_arrays()):
+            assert np.allclose(a, b, rtol=1e-8, atol=1e-10)
+
+
+@pytest.mark.parametrize("precision", [binding.CFUST_FP64, binding.CFUST_FP32])
+def test_batched_prioritised_equals_single_prioritised_fits(precision):
+    """The prioritised batched sweep reproduces the same fits run one at a
+    time with prioritisation (same per-pair arithmetic)."""
+    torch = _torch()
+    Ys, truths, inits = _small_batch()
+    lat = synth.make_lattice(256, 4, 0)
+    Yd = [torch.from_numpy(Y).cuda() for Y in Ys]
+    iters = 3
+    with binding.Context(lat, precision=precision, max_iter=iters, prioritise=True) as ctx:
+        bp, btr, st = ctx.cfust_fit_batched(Yd, inits)
+    assert all(s == 0 for s in st)
+    for f, (Y, P0) in enumerate(zip(Yd, inits)):
+        with binding.Context(lat, precision=precision, max_iter=iters, prioritise=True) as ctx:
+            sp, str_, _ = ctx.cfust_fit(Y, P0)
+        assert np.allclose(btr[f], str_, rtol=1e-12, atol=0), f
+        for a, b in zip(bp[f].as_arrays(), sp.as_arrays()):
+            assert np.allclose(a, b, rtol=1e-12, atol=1e-14), f
