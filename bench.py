@@ -14,10 +14,10 @@ flushed (a 256 MiB write) between timed steps.  Throughput is E-step pairs
 second are reported beside it.
 
 Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
-For N > 1, launch under torch.distributed.run: every rank fits its own
-independent synthetic problem (seed = rank) with no collective on the data
-path (weak scaling); timing is bracketed by barriers and the max over ranks
-is reported.
+For N > 1, launch under torch.distributed.run: the ranks run one fit whose
+observations are split into contiguous shards (100000 rows per rank, weak
+scaling), with one all-reduce of the M-step sums per EM iteration; timing is
+bracketed by barriers and the max over ranks is reported.
 """
 from __future__ import annotations
 
@@ -352,6 +352,25 @@ def fp32_error_vs_oracle(ref, lat, stream):
     }
 
 
+def fp64_mode_rate(Y, init, lat, stream, rows=20000):
+    """The library's double-precision parity mode on the same workload: one
+    E-step (every sweep in FP64) of `rows` observations x all components,
+    event-timed after a warm-up call."""
+    import torch
+    from paper_2005_06848_gb300 import binding
+    Yd = torch.from_numpy(np.ascontiguousarray(Y[:rows])).cuda()
+    with binding.Context(lat, precision=binding.CFUST_FP64, stream=stream) as ctx:
+        ctx.cfust_estep(Yd, init)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        ctx.cfust_estep(Yd, init)
+        e1.record(stream)
+        e1.synchronize()
+        ms = e0.elapsed_time(e1)
+    return {"value": rows * init.g / (ms / 1e3), "unit": UNIT, "ms": ms,
+            "sample": f"{rows} observations x {init.g} components, one E-step, every sweep in FP64"}
+
+
 def _oracle_estep_block(args):
     """One spawned worker: the oracle's E-step of rows [j0, j1) of a named
     workload (module-level so a spawned process can import it)."""
@@ -481,17 +500,115 @@ def run_reference(args):
     return 0
 
 
+def run_sharded(args):
+    """N > 1 ranks (torch.distributed.run, one GPU each): one fit of
+    N x 100000 observations of the p=4, r=4, g=3 workload, its rows split
+    into contiguous shards (weak scaling: 100000 rows per rank).  A step is one
+    EM iteration: every rank's E-step and M-step sums on its rows, one NCCL
+    all-reduce of the g K + 1 doubles (sums and log-likelihood), the same
+    update on every rank (Algorithm 2's partial sums, Algorithm 3's combine).
+    Timed with CUDA events per rank, max over ranks; rank 0 prints the line."""
+    import torch
+    import torch.distributed as dist
+    from paper_2005_06848_gb300 import binding, sharded, synth
+
+    ws, rank, local = dist_env()
+    torch.cuda.set_device(local)
+    dist.init_process_group("nccl")
+    n_rank = args.rows or synth.WORKLOADS[WORKLOAD]["n"]
+    n_total = ws * n_rank
+    Y, _, truth, init, lat, meta = synth.workload(WORKLOAD, seed=0, n=n_total)
+    g, p, r = meta["g"], meta["p"], meta["r"]
+    j0, j1 = sharded.shard_rows(n_total, ws, rank)
+    Yh = torch.from_numpy(np.ascontiguousarray(Y[j0:j1])).pin_memory()
+    Yd = Yh.cuda()
+    stream = torch.cuda.current_stream()
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
+    red = sharded.torch_allreduce(torch.device("cuda", local))
+    P = init
+    ctx = binding.Context(lat, precision=binding.CFUST_FP32, timing=True, stream=stream)
+    for _ in range(args.warmup):
+        flush.zero_()
+        P, _ = sharded.em_iteration(ctx, Yd, P, n_total, red)
+    torch.cuda.synchronize()
+    dist.barrier()
+    sampler = ClockSampler(torch.cuda.current_device()) if rank == 0 else None
+    if sampler:
+        sampler.start()
+        time.sleep(0.4)
+    ms, sweep, trace = [], [], []
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    for _ in range(args.steps):
+        flush.zero_()
+        ev0.record(stream)
+        P, ll = sharded.em_iteration(ctx, Yd, P, n_total, red)
+        ev1.record(stream)
+        ev1.synchronize()
+        ms.append(ev0.elapsed_time(ev1))
+        sweep.append(ctx.cfust_last_sweep_ms())
+        trace.append(ll)
+    torch.cuda.synchronize()
+    dist.barrier()
+    clocks = sampler.stop() if sampler else None
+    pairs_rank = (j1 - j0) * g
+    total_ms, value, iters_per_s = aggregate_ranks(float(sum(ms)), pairs_rank, args.steps, "cuda")
+    # end to end: the shard copied from pinned host memory each step, the
+    # log-likelihood back on the host (the all-reduced vector), wall clock
+    Ye = torch.empty_like(Yd)
+    torch.cuda.synchronize()
+    dist.barrier()
+    t0 = time.perf_counter()
+    for _ in range(3):
+        Ye.copy_(Yh, non_blocking=True)
+        P, ll = sharded.em_iteration(ctx, Ye, P, n_total, red)
+    torch.cuda.synchronize()
+    e2e_s = torch.tensor([time.perf_counter() - t0], dtype=torch.float64, device="cuda")
+    dist.all_reduce(e2e_s, op=dist.ReduceOp.MAX)
+    ctx.close()
+    peaks = load_peaks() or {}
+    sm_max = peaks.get("sm_max_mhz", 2070.0)
+    sweep_ms = float(np.mean(sweep))
+    flops = pairs_rank * lat.n * sweep_flops_per_point(r)
+    achieved = flops / (sweep_ms / 1e3) / 1e12
+    peak = peak_fp32_tflops(sm_max, sm_count())
+    K = 3 + p + r + p * r + r * (r + 1) // 2 + p * (p + 1) // 2
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic (one seeded CFUST mixture draw, rows split over the ranks)",
+            "config": {"workload": WORKLOAD, "n_per_rank": n_rank, "n_total": n_total, "g": g, "p": p, "r": r,
+                       "lattice_points": lat.n,
+                       "parallelism": f"observation-sharded single fit over {ws} ranks: one all-reduce of "
+                                      f"{g * K + 1} doubles per EM iteration",
+                       "step": "one EM iteration of the whole fit", "l2": "flushed between timed steps"},
+            "em_iters_per_s": iters_per_s,
+            "loglik_last": trace[-1],
+            "gpu_launches": 8 * args.steps,
+            "roofline": {"bound": "alu", "kernel": "estep_kernel<float,4>", "achieved": achieved, "peak": peak,
+                         "unit": "TFLOP/s", "frac": achieved / peak, "traffic": None,
+                         "sweep_ms_mean": sweep_ms, "flops_per_point": sweep_flops_per_point(r)},
+            "sm_count": sm_count(),
+            "clocks": clocks,
+            "e2e": {"value": ws * pairs_rank * 3 / float(e2e_s.item()), "unit": UNIT,
+                    "h2d_bytes_per_step": int(Yh.numel() * 8), "d2h_bytes_per_step": int(8 * (g * K + 1)),
+                    "path": "shard copied from pinned host memory each step; sharded.em_iteration "
+                            "(cfust_estep, cfust_mstep_sums, all-reduce, cfust_mstep_apply)"},
+        }
+        print(json.dumps(line), flush=True)
+    dist.destroy_process_group()
+    return 0
+
+
 def run_ours(args):
     import torch
     from paper_2005_06848_gb300 import binding, synth
 
     ws, rank, local = dist_env()
     if ws > 1:
-        import torch.distributed as dist
-        torch.cuda.set_device(local)
-        dist.init_process_group("nccl")
-    else:
-        torch.cuda.set_device(0)
+        return run_sharded(args)
+    torch.cuda.set_device(0)
     dev = torch.cuda.current_device()
 
     Y, _, truth, init, lat, meta = synth.workload(WORKLOAD, seed=rank, n=args.rows or None)
@@ -628,6 +745,8 @@ def run_ours(args):
         line["fp32_error_vs_oracle"] = fp32_error_vs_oracle(ref, lat, stream)
         if ws == 1:
             line["cpu_baseline_all_cores"] = cpu_baseline_all_cores()
+    if ws == 1 and not args.no_cpu_baseline:
+        line["fp64_mode"] = fp64_mode_rate(Y, init, lat, stream)
     if ws == 1 and not args.no_extras:
         # the metric's comparisons on the other synthetic workloads, each
         # measured in this same run: batched fits, the learned form against
@@ -721,7 +840,31 @@ def _loglik_ms(torch, ctx, Yd, P, reps=3):
     return ll, best
 
 
-def _timed_em(torch, ctx, Yd, P, steps, warmup, flush):
+def _timed_first_iteration(torch, ctx, Yd, P, reps, flush):
+    """The first EM iteration from P, repeated: every repetition restarts the
+    stepwise fit at P (cfust_fit_begin, which keeps the captured graph) and
+    times one iteration with CUDA events, L2 flushed before it.  Returns the
+    times (ms) and the sweep kernel's."""
+    stream = torch.cuda.current_stream()
+    ms, kern = [], []
+    for k in range(reps + 2):
+        ctx.cfust_fit_begin(Yd, P)
+        flush.zero_()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        ctx.cfust_fit_step(1)
+        e1.record(stream)
+        e1.synchronize()
+        if k >= 2:  # the first two build buffers and the graph
+            ms.append(e0.elapsed_time(e1))
+            kern.append(ctx.cfust_last_sweep_ms())
+        ctx.cfust_fit_end()
+    return ms, kern
+
+
+def _timed_em(torch, ctx, Yd, P, steps, warmup, flush, fallback=None):
+    """Event-timed EM iterations; with `fallback` (a list) also each timed
+    step's count of pairs the surrogate left to the lattice rule."""
     stream = torch.cuda.current_stream()
     ctx.cfust_fit_begin(Yd, P)
     for _ in range(warmup):
@@ -738,6 +881,8 @@ def _timed_em(torch, ctx, Yd, P, steps, warmup, flush):
         e1.synchronize()
         ms.append(e0.elapsed_time(e1))
         kern.append(ctx.cfust_last_sweep_ms())
+        if fallback is not None:
+            fallback.append(int(ctx.cfust_last_fallback()))
     params, trace, done = ctx.cfust_fit_end()
     return ms, kern, params
 
@@ -832,18 +977,24 @@ def surrogate_line(args, steps, warmup):
     sampler = ClockSampler(torch.cuda.current_device())
     sampler.start()
     time.sleep(0.4)
-    ms_s, kern_s, _ = _timed_em(torch, ctx_s, Yd, init, steps, warmup, flush)
+    # the first EM iteration from the start, where the accuracies were judged
+    ms_s, kern_s = _timed_first_iteration(torch, ctx_s, Yd, init, steps, flush)
     ctx_p = binding.Context(synth.make_lattice(n_eq, 4, seed=0), precision=binding.CFUST_FP32,
                             max_iter=warmup + steps + 1, use_graph=True, timing=True, triage_nats=tn)
-    ms_p, kern_p, _ = _timed_em(torch, ctx_p, Yd, init, steps, warmup, flush)
-    ctx_p.close()
+    ms_p, kern_p = _timed_first_iteration(torch, ctx_p, Yd, init, steps, flush)
     ms_q = None
     if n_eq_p is not None:
         ctx_q = binding.Context(synth.make_lattice(n_eq_p, 4, seed=0), precision=binding.CFUST_FP32,
                                 max_iter=warmup + steps + 1, use_graph=True, timing=True,
                                 triage_nats=tn, prioritise=True)
-        ms_q, _, _ = _timed_em(torch, ctx_q, Yd, init, steps, warmup, flush)
+        ms_q, _ = _timed_first_iteration(torch, ctx_q, Yd, init, steps, flush)
         ctx_q.close()
+    # and consecutive iterations as a fit runs on from it: the parameters move,
+    # and with them the share of pairs the network's domain covers
+    fb_steps = []
+    ms_run, _, P_s = _timed_em(torch, ctx_s, Yd, init, steps, warmup, flush, fb_steps)
+    ms_run_p, _, _ = _timed_em(torch, ctx_p, Yd, init, steps, warmup, flush)
+    ctx_p.close()
     clocks = sampler.stop()
 
     # end to end through the public API with the surrogate attached
@@ -889,7 +1040,7 @@ def surrogate_line(args, steps, warmup):
                                 "final_loss": float(trace[-1])},
                    "fallback_lattice_points": args.sg_fallback_n,
                    "triage_nats": tn,
-                   "step": "one EM iteration (CUDA graph replay) from the same start",
+                   "step": "the first EM iteration from the start (CUDA graph replay), repeated",
                    "l2": "flushed between timed steps"},
         "em_iters_per_s": 1.0 / step_s,
         "loglik_error_vs_65536_point_rule": ({"surrogate": l_sur - l_judge, "plain_by_points": rms,
@@ -905,6 +1056,15 @@ def surrogate_line(args, steps, warmup):
             "ms_per_step": float(np.mean(ms_q)), "value": pairs / (float(np.mean(ms_q)) / 1e3),
             "speedup_of_surrogate": float(np.mean(ms_q)) / 1e3 / step_s} if ms_q is not None else None),
         "fallback_pairs": int(fallback), "fallback_fraction": fallback / pairs,
+        # the timed steps run on from the start: pairs left to the lattice rule
+        # in each, and the dof the fit reached (the network's domain ends at
+        # nu + p + 2 = 30)
+        "consecutive_iterations": {
+            "note": f"{warmup} untimed then {steps} timed EM iterations run on from the start",
+            "surrogate_ms_per_step": float(np.mean(ms_run)), "plain_ms_per_step": float(np.mean(ms_run_p)),
+            "speedup": float(np.mean(ms_run_p)) / float(np.mean(ms_run)),
+            "fallback_pairs_per_timed_step": fb_steps,
+            "nu_after": [float(v) for v in P_s.nu]},
         # per EM iteration: precompute, network kernel, list sweep, rescue,
         # posterior/sums, log-likelihood reduce, finalize
         "gpu_launches": 7 * steps,

@@ -6,8 +6,8 @@
 //                 triangle (11, 12, 13, 22, 23, 33)
 // Network 7 -> 128 -> 128 -> 128 -> 10 with GELU (tanh form) after the hidden
 // layers; BF16 weights and activations, FP32 accumulation on the tensor cores
-// (inference and the E-step: tcgen05 MMAs with accumulators in tensor memory;
-// training GEMMs: mma.sync m16n8k16), FP32 master weights updated by Adam.  Inputs are
+// (tcgen05 MMAs with accumulators in tensor memory, in the fused E-step,
+// prediction and the training GEMMs), FP32 master weights updated by Adam.  Inputs are
 // normalised as c and log m mapped from their ranges onto [-1, 1] and R/0.9.
 // The network predicts log(-log P), the first moments and the covariance
 // (second moments minus the products of the first moments), standardised by
@@ -61,9 +61,9 @@ constexpr int OFF_W1 = 0, OFF_B1 = OFF_W1 + DIN * H, OFF_W2 = OFF_B1 + H, OFF_B2
 using bf16 = __nv_bfloat16;
 
 // ---------------------------------------------------------------------------
-// BF16 tensor-core GEMM, C[M x N] = A[M x K] B[K x N], FP32 accumulation.
-// A(m, k) = transA ? A[k lda + m] : A[m lda + k];  B(k, n) likewise.
-// Tile 128 x 128 x 32, 8 warps as 4 x 2, warp tile 32 x 64.
+// BF16 tensor-core GEMM of the training passes, C[M x N] = A[M x K] B[K x N],
+// FP32 accumulation.  A(m, k) = transA ? A[k lda + m] : A[m lda + k];  B(k, n)
+// likewise.  Tile 128 x 128, K in slices of 32 (kernel below).
 // ---------------------------------------------------------------------------
 // Operand layouts must keep the contiguous index 16-byte aligned: lda, ldb
 // and the untransposed K multiples of 8 (every use here: 16 or 128).
@@ -83,7 +83,7 @@ struct Gemm {
   const bf16 *Zprev;    // mode 2
 };
 
-constexpr int BM = 128, BN = 128, BK = 32, PITCH = BK + 8;
+constexpr int BM = 128, BN = 128, BK = 32;
 
 // GELU in its tanh form, the tanh from the hardware approximation
 // (tanh.approx.f32, relative error about 2^-11, below the BF16 rounding of
@@ -108,138 +108,190 @@ __device__ __forceinline__ float2 gelu_x2(float2 z) {
   const float2 hz = __fmul2_rn(z, make_float2(0.5f, 0.5f));
   return __ffma2_rn(hz, make_float2(tanh_approx(arg.x), tanh_approx(arg.y)), hz);
 }
+__device__ __forceinline__ uint32_t pack_bf16x2(float lo, float hi) {
+  const __nv_bfloat162 v = __floats2bfloat162_rn(lo, hi);
+  return *reinterpret_cast<const uint32_t *>(&v);
+}
+
 __device__ __forceinline__ float gelu_grad_f(float z) {
   const float t = tanh_approx(z * fmaf(z * z, GELU_AK, GELU_K));
   return 0.5f * (1.0f + t) + 0.5f * z * (1.0f - t * t) * fmaf(3.0f * GELU_AK, z * z, GELU_K);
 }
 
-__device__ __forceinline__ void mma_bf16(float (&d)[4], const uint32_t (&a)[4], const uint32_t (&b)[2]) {
-  asm volatile(
-      "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
-      "{%0,%1,%2,%3};\n"
-      : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
-      : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b[0]), "r"(b[1]));
+// The GEMM on the tcgen05 tensor cores.  A CTA of 256 threads owns one
+// 128 x 128 output tile of one K range (split-K over blockIdx.z); K advances in
+// slices of 32 staged in shared memory in the UMMA K-major layout (both
+// operands K-major: A as [m][k], B as [n][k]), double-buffered so the loads of
+// slice s + 1 overlap the MMAs of slice s; thread 0 issues two MMAs (K = 16)
+// per slice into a 128 x 128 FP32 accumulator in tensor memory, each slice's
+// completion arriving on its buffer's mbarrier.  The epilogue reads the
+// accumulator with tcgen05.ld: warp w takes lanes 32 (w % 4) .. + 31 (rows) and
+// columns 64 (w / 4) .. + 63.
+constexpr uint32_t GT_TILE = BM * BK * 2;   // bytes of one operand slice
+constexpr uint32_t GT_SBO = (BK / 8) * 128;
+constexpr uint32_t GT_IDESC = tc::idesc_bf16_f32(BM, BN);
+
+__device__ __forceinline__ void gemm_load_slice(const Gemm &g, unsigned char *As, unsigned char *Bs, int m0, int n0,
+                                                int k0, int kb1, int tid) {
+  const bf16 zero = __float2bfloat16(0.f);
+  if (!g.transA) {
+    for (int v = tid; v < BM * (BK / 8); v += 256) {
+      const int mm = v / (BK / 8), kk = (v % (BK / 8)) * 8;
+      const int m = m0 + mm, k = k0 + kk;
+      uint4 val = make_uint4(0u, 0u, 0u, 0u);
+      if (m < g.M && k + 8 <= kb1) val = *reinterpret_cast<const uint4 *>(g.A + (int64_t)m * g.lda + k);
+      *reinterpret_cast<uint4 *>(As + tc::kmajor_offset(mm, kk, BK)) = val;
+    }
+  } else {
+    for (int v = tid; v < BK * (BM / 8); v += 256) {
+      const int kk = v / (BM / 8), mm = (v % (BM / 8)) * 8;
+      const int m = m0 + mm, k = k0 + kk;
+      bf16 e[8];
+      if (k < kb1 && m + 8 <= g.M) {
+        *reinterpret_cast<uint4 *>(e) = *reinterpret_cast<const uint4 *>(g.A + (int64_t)k * g.lda + m);
+      } else {
+#pragma unroll
+        for (int q = 0; q < 8; ++q) e[q] = (k < kb1 && m + q < g.M) ? g.A[(int64_t)k * g.lda + m + q] : zero;
+      }
+#pragma unroll
+      for (int q = 0; q < 8; ++q) *reinterpret_cast<bf16 *>(As + tc::kmajor_offset(mm + q, kk, BK)) = e[q];
+    }
+  }
+  if (!g.transB) {
+    for (int v = tid; v < BK * (BN / 8); v += 256) {
+      const int kk = v / (BN / 8), nn = (v % (BN / 8)) * 8;
+      const int n = n0 + nn, k = k0 + kk;
+      bf16 e[8];
+      if (k < kb1 && n + 8 <= g.N) {
+        *reinterpret_cast<uint4 *>(e) = *reinterpret_cast<const uint4 *>(g.B + (int64_t)k * g.ldb + n);
+      } else {
+#pragma unroll
+        for (int q = 0; q < 8; ++q) e[q] = (k < kb1 && n + q < g.N) ? g.B[(int64_t)k * g.ldb + n + q] : zero;
+      }
+#pragma unroll
+      for (int q = 0; q < 8; ++q) *reinterpret_cast<bf16 *>(Bs + tc::kmajor_offset(nn + q, kk, BK)) = e[q];
+    }
+  } else {
+    for (int v = tid; v < BN * (BK / 8); v += 256) {
+      const int nn = v / (BK / 8), kk = (v % (BK / 8)) * 8;
+      const int n = n0 + nn, k = k0 + kk;
+      uint4 val = make_uint4(0u, 0u, 0u, 0u);
+      if (n < g.N && k + 8 <= kb1) val = *reinterpret_cast<const uint4 *>(g.B + (int64_t)n * g.ldb + k);
+      *reinterpret_cast<uint4 *>(Bs + tc::kmajor_offset(nn, kk, BK)) = val;
+    }
+  }
 }
 
-__global__ void __launch_bounds__(256) gemm_kernel(Gemm g) {
-  __shared__ __align__(16) bf16 As[BM * PITCH];
-  __shared__ __align__(16) bf16 Bs[BN * PITCH];
-  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  const int wm = warp >> 1, wn = warp & 1;
-  const int gid = lane >> 2, tig = lane & 3;
+__global__ void __launch_bounds__(256) gemm_kernel(Gemm g, int *status) {
+  // [stage][A | B] slices, then two mbarriers and the tensor-memory address
+  __shared__ __align__(1024) unsigned char sm[2 * 2 * GT_TILE];
+  __shared__ __align__(8) uint64_t bars[2];
+  __shared__ uint32_t tslot;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int m0 = blockIdx.x * BM, n0 = blockIdx.y * BN;
   const int kb0 = blockIdx.z * g.k_chunk;
   const int kb1 = min(g.K, kb0 + g.k_chunk);
-  float acc[2][8][4];
-#pragma unroll
-  for (int a = 0; a < 2; ++a)
-#pragma unroll
-    for (int b = 0; b < 8; ++b)
-#pragma unroll
-      for (int c = 0; c < 4; ++c) acc[a][b][c] = 0.f;
-  const bf16 zero = __float2bfloat16(0.f);
-  for (int k0 = kb0; k0 < kb1; k0 += BK) {
-    // A tile -> As[m][k] and B tile -> Bs[n][k], 16-byte global loads along
-    // the contiguous index (8 BF16), zeros outside the matrix
-    if (!g.transA) {
-      for (int v = tid; v < BM * (BK / 8); v += 256) {
-        const int mm = v / (BK / 8), kk = (v % (BK / 8)) * 8;
-        const int m = m0 + mm, k = k0 + kk;
-        uint4 val = make_uint4(0u, 0u, 0u, 0u);
-        if (m < g.M && k + 8 <= kb1) val = *reinterpret_cast<const uint4 *>(g.A + (int64_t)m * g.lda + k);
-        *reinterpret_cast<uint4 *>(&As[mm * PITCH + kk]) = val;
-      }
-    } else {
-      for (int v = tid; v < BK * (BM / 8); v += 256) {
-        const int kk = v / (BM / 8), mm = (v % (BM / 8)) * 8;
-        const int m = m0 + mm, k = k0 + kk;
-        bf16 e[8];
-        if (k < kb1 && m + 8 <= g.M) {
-          *reinterpret_cast<uint4 *>(e) = *reinterpret_cast<const uint4 *>(g.A + (int64_t)k * g.lda + m);
-        } else {
-#pragma unroll
-          for (int q = 0; q < 8; ++q) e[q] = (k < kb1 && m + q < g.M) ? g.A[(int64_t)k * g.lda + m + q] : zero;
-        }
-#pragma unroll
-        for (int q = 0; q < 8; ++q) As[(mm + q) * PITCH + kk] = e[q];
-      }
-    }
-    if (!g.transB) {
-      for (int v = tid; v < BK * (BN / 8); v += 256) {
-        const int kk = v / (BN / 8), nn = (v % (BN / 8)) * 8;
-        const int n = n0 + nn, k = k0 + kk;
-        bf16 e[8];
-        if (k < kb1 && n + 8 <= g.N) {
-          *reinterpret_cast<uint4 *>(e) = *reinterpret_cast<const uint4 *>(g.B + (int64_t)k * g.ldb + n);
-        } else {
-#pragma unroll
-          for (int q = 0; q < 8; ++q) e[q] = (k < kb1 && n + q < g.N) ? g.B[(int64_t)k * g.ldb + n + q] : zero;
-        }
-#pragma unroll
-        for (int q = 0; q < 8; ++q) Bs[(nn + q) * PITCH + kk] = e[q];
-      }
-    } else {
-      for (int v = tid; v < BN * (BK / 8); v += 256) {
-        const int nn = v / (BK / 8), kk = (v % (BK / 8)) * 8;
-        const int n = n0 + nn, k = k0 + kk;
-        uint4 val = make_uint4(0u, 0u, 0u, 0u);
-        if (n < g.N && k + 8 <= kb1) val = *reinterpret_cast<const uint4 *>(g.B + (int64_t)n * g.ldb + k);
-        *reinterpret_cast<uint4 *>(&Bs[nn * PITCH + kk]) = val;
-      }
-    }
-    __syncthreads();
-#pragma unroll
-    for (int ks = 0; ks < BK; ks += 16) {
-      uint32_t af[2][4], bfr[8][2];
-#pragma unroll
-      for (int mi = 0; mi < 2; ++mi) {
-        const int rb = wm * 32 + mi * 16;
-        af[mi][0] = *reinterpret_cast<const uint32_t *>(&As[(rb + gid) * PITCH + ks + tig * 2]);
-        af[mi][1] = *reinterpret_cast<const uint32_t *>(&As[(rb + gid + 8) * PITCH + ks + tig * 2]);
-        af[mi][2] = *reinterpret_cast<const uint32_t *>(&As[(rb + gid) * PITCH + ks + 8 + tig * 2]);
-        af[mi][3] = *reinterpret_cast<const uint32_t *>(&As[(rb + gid + 8) * PITCH + ks + 8 + tig * 2]);
-      }
-#pragma unroll
-      for (int nj = 0; nj < 8; ++nj) {
-        const int nb = wn * 64 + nj * 8;
-        bfr[nj][0] = *reinterpret_cast<const uint32_t *>(&Bs[(nb + gid) * PITCH + ks + tig * 2]);
-        bfr[nj][1] = *reinterpret_cast<const uint32_t *>(&Bs[(nb + gid) * PITCH + ks + 8 + tig * 2]);
-      }
-#pragma unroll
-      for (int mi = 0; mi < 2; ++mi)
-#pragma unroll
-        for (int nj = 0; nj < 8; ++nj) mma_bf16(acc[mi][nj], af[mi], bfr[nj]);
-    }
-    __syncthreads();
+  if (tid < 2) tc::mbar_init1(bars + tid);
+  if (warp == 0) {
+    tc::tmem_alloc(&tslot, 128);
+    tc::tmem_relinquish();
   }
+  if (kb0 < kb1) gemm_load_slice(g, sm, sm + GT_TILE, m0, n0, kb0, kb1, tid);
+  const uint32_t sbase = tc::smem_u32(sm);
+  uint32_t ph[2] = {0u, 0u};
+  bool bad = false;
+  int it = 0;
+  for (int k0 = kb0; k0 < kb1; k0 += BK, ++it) {
+    const int s = it & 1;
+    tc::fence_proxy_async_smem();
+    tc::fence_before_sync();
+    __syncthreads();
+    if (tid == 0) {
+      tc::fence_after_sync();
+      const uint32_t a = sbase + s * 2 * GT_TILE, b = a + GT_TILE;
 #pragma unroll
-  for (int mi = 0; mi < 2; ++mi)
-#pragma unroll
-    for (int nj = 0; nj < 8; ++nj)
-#pragma unroll
-      for (int c = 0; c < 4; ++c) {
-        const int m = m0 + wm * 32 + mi * 16 + gid + ((c >= 2) ? 8 : 0);
-        const int n = n0 + wn * 64 + nj * 8 + tig * 2 + (c & 1);
-        if (m >= g.M || n >= g.N) continue;
-        const float v = acc[mi][nj][c];
-        if (g.mode == 0) {
-          g.C[(int64_t)blockIdx.z * g.M * g.N + (int64_t)m * g.ldc + n] = v;
-        } else if (g.mode == 1) {
-          const float z = v + g.bias[n];
-          g.Zout[(int64_t)m * g.ldo + n] = __float2bfloat16(z);
-          g.Hout[(int64_t)m * g.ldo + n] = __float2bfloat16(gelu_f(z));
-        } else if (g.mode == 2) {
-          const float zp = __bfloat162float(g.Zprev[(int64_t)m * g.ldo + n]);
-          g.Hout[(int64_t)m * g.ldo + n] = __float2bfloat16(v * gelu_grad_f(zp));
-        } else {
-          g.C[(int64_t)m * g.ldc + n] = v + g.bias[n];
-        }
+      for (int ks = 0; ks < BK / 16; ++ks)
+        tc::mma_bf16(tslot, tc::smem_desc(a + ks * 256, 128, GT_SBO), tc::smem_desc(b + ks * 256, 128, GT_SBO),
+                     GT_IDESC, (k0 > kb0 || ks > 0) ? 1u : 0u);
+      tc::mma_commit(bars + s);
+    }
+    if (k0 + BK < kb1) {
+      // the other buffer was read by the previous slice's MMAs: wait for them
+      if (it >= 1) {
+        bad = !tc::mbar_wait(bars + (s ^ 1), ph[s ^ 1], 1 << 22) || bad;
+        ph[s ^ 1] ^= 1u;
       }
+      gemm_load_slice(g, sm + (s ^ 1) * 2 * GT_TILE, sm + (s ^ 1) * 2 * GT_TILE + GT_TILE, m0, n0, k0 + BK, kb1,
+                      tid);
+    }
+  }
+  // the last slice's MMAs (in order after every earlier one)
+  if (it > 0) bad = !tc::mbar_wait(bars + ((it - 1) & 1), ph[(it - 1) & 1], 1 << 22) || bad;
+  tc::fence_before_sync();
+  __syncthreads();  // also publishes the tensor-memory address when K was empty
+  tc::fence_after_sync();
+  if (bad && status) atomicOr(status, ERR_TIMEOUT);
+  // epilogue: this thread's row, 64 columns in two loads of 32, written 8
+  // columns (16 bytes of BF16, 32 of FP32) at a time where the whole group
+  // lies inside the matrix (every output here has rows of 16 or 128 values)
+  const int row = (warp & 3) * 32 + lane, m = m0 + row;
+  const uint32_t taddr = tslot + ((uint32_t)((warp & 3) * 32) << 16) + (warp >> 2) * 64;
+#pragma unroll 1
+  for (int half = 0; half < 2; ++half) {
+    uint32_t v[32];
+    tc::tmem_ld32(taddr + half * 32, v);
+    tc::tmem_wait_ld(v);
+    if (m >= g.M) continue;
+    const int nb = n0 + (warp >> 2) * 64 + half * 32;
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const int n = nb + 8 * q;
+      if (n >= g.N) continue;
+      float val[8];
+#pragma unroll
+      for (int c = 0; c < 8; ++c) val[c] = it > 0 ? __uint_as_float(v[8 * q + c]) : 0.f;
+      if (g.mode == 0 || g.mode == 3) {
+        float *dst = g.C + (g.mode == 0 ? (int64_t)blockIdx.z * g.M * g.N : 0) + (int64_t)m * g.ldc + n;
+        if (g.mode == 3)
+#pragma unroll
+          for (int c = 0; c < 8; ++c) val[c] += g.bias[n + c];
+        reinterpret_cast<float4 *>(dst)[0] = make_float4(val[0], val[1], val[2], val[3]);
+        reinterpret_cast<float4 *>(dst)[1] = make_float4(val[4], val[5], val[6], val[7]);
+      } else if (g.mode == 1) {
+        uint32_t zw[4], hw[4];
+#pragma unroll
+        for (int c = 0; c < 4; ++c) {
+          const float z0 = val[2 * c] + g.bias[n + 2 * c], z1 = val[2 * c + 1] + g.bias[n + 2 * c + 1];
+          zw[c] = pack_bf16x2(z0, z1);
+          hw[c] = pack_bf16x2(gelu_f(z0), gelu_f(z1));
+        }
+        *reinterpret_cast<uint4 *>(g.Zout + (int64_t)m * g.ldo + n) = make_uint4(zw[0], zw[1], zw[2], zw[3]);
+        *reinterpret_cast<uint4 *>(g.Hout + (int64_t)m * g.ldo + n) = make_uint4(hw[0], hw[1], hw[2], hw[3]);
+      } else {
+        const uint4 zp4 = *reinterpret_cast<const uint4 *>(g.Zprev + (int64_t)m * g.ldo + n);
+        const bf16 *zp = reinterpret_cast<const bf16 *>(&zp4);
+        uint32_t hw[4];
+#pragma unroll
+        for (int c = 0; c < 4; ++c)
+          hw[c] = pack_bf16x2(val[2 * c] * gelu_grad_f(__bfloat162float(zp[2 * c])),
+                              val[2 * c + 1] * gelu_grad_f(__bfloat162float(zp[2 * c + 1])));
+        *reinterpret_cast<uint4 *>(g.Hout + (int64_t)m * g.ldo + n) = make_uint4(hw[0], hw[1], hw[2], hw[3]);
+      }
+    }
+  }
+  tc::fence_before_sync();
+  __syncthreads();
+  if (warp == 0) {
+    tc::fence_after_sync();
+    tc::tmem_dealloc(tslot, 128);
+  }
 }
 
-cudaError_t gemm(const Gemm &g, int splits, cudaStream_t st) {
+cudaError_t gemm(const Gemm &g, int splits, cudaStream_t st, int *status) {
+  // the epilogue writes groups of 8 columns: row lengths must be multiples of 8
+  if (g.N % 8 != 0 || (g.mode == 0 || g.mode == 3 ? g.ldc : g.ldo) % 8 != 0) return cudaErrorInvalidValue;
   dim3 grid((g.M + BM - 1) / BM, (g.N + BN - 1) / BN, splits);
-  gemm_kernel<<<grid, 256, 0, st>>>(g);
+  gemm_kernel<<<grid, 256, 0, st>>>(g, status);
   return cudaGetLastError();
 }
 
@@ -508,29 +560,29 @@ __global__ void __launch_bounds__(256) label_kernel(const float *x, float *y, in
   yb[9] = EXX[2][2];
 }
 
-__device__ __forceinline__ uint32_t pack_bf16x2(float lo, float hi) {
-  const __nv_bfloat162 v = __floats2bfloat162_rn(lo, hi);
-  return *reinterpret_cast<const uint32_t *>(&v);
-}
-
-// Nearest-structure PSD repair of a predicted 3x3 covariance (upper order
-// 00 01 02 11 12 22): LDL^T with every pivot floored at PSD_FLOOR, rebuilt.
-// A positive definite input comes back unchanged up to rounding; a
-// prediction that is not keeps e4 positive semi-definite, as the exact
-// conditional moments are.
-constexpr float PSD_FLOOR = 1e-6f;
+// Positive-definite repair of a predicted 3x3 covariance (upper order 00 01
+// 02 11 12 22), keeping its diagonal: variances floored at PSD_FLOOR, each
+// first-row correlation clamped to |rho| <= PSD_RHO, and the last factor of the
+// LDL^T decomposition shrunk where needed so that every pivot keeps at least
+// 1 - PSD_RHO^2 of its variance.  Every entry stays within the (floored)
+// variances, a well-conditioned positive definite input comes back unchanged up
+// to rounding, and e4 stays positive definite like the exact conditional
+// moments.  Continuous in the prediction.
+constexpr float PSD_FLOOR = 1e-6f, PSD_RHO = 0.999f;
 __device__ __forceinline__ void psd_repair3(float *v) {
-  const float d0 = fmaxf(v[0], PSD_FLOOR);
-  const float l10 = v[1] / d0, l20 = v[2] / d0;
-  const float d1 = fmaxf(v[3] - l10 * l10 * d0, PSD_FLOOR);
-  const float l21 = (v[4] - l20 * l10 * d0) / d1;
-  const float d2 = fmaxf(v[5] - l20 * l20 * d0 - l21 * l21 * d1, PSD_FLOOR);
+  const float d0 = fmaxf(v[0], PSD_FLOOR), d1 = fmaxf(v[3], PSD_FLOOR), d2 = fmaxf(v[5], PSD_FLOOR);
+  const float m01 = PSD_RHO * sqrtf(d0 * d1), m02 = PSD_RHO * sqrtf(d0 * d2);
+  const float c01 = fminf(fmaxf(v[1], -m01), m01), c02 = fminf(fmaxf(v[2], -m02), m02);
+  const float l10 = c01 / d0, l20 = c02 / d0;
+  const float p1 = d1 - l10 * c01;  // >= (1 - PSD_RHO^2) d1
+  const float lmax = sqrtf(fmaxf(PSD_RHO * PSD_RHO * d2 - l20 * c02, 0.f) / p1);
+  const float l21 = fminf(fmaxf((v[4] - l20 * c01) / p1, -lmax), lmax);
   v[0] = d0;
-  v[1] = l10 * d0;
-  v[2] = l20 * d0;
-  v[3] = fmaf(l10 * l10, d0, d1);
-  v[4] = fmaf(l20 * l10, d0, l21 * d1);
-  v[5] = fmaf(l20 * l20, d0, fmaf(l21 * l21, d1, d2));
+  v[1] = c01;
+  v[2] = c02;
+  v[3] = d1;
+  v[4] = fmaf(l20, c01, l21 * p1);
+  v[5] = d2;
 }
 
 // Standardised problem of one network row: pair (i, j), pass 0 (dof nu + p,
@@ -693,21 +745,40 @@ struct Ctx {
 
 // Copies the packed BF16 weights into the UMMA layout and the biases and
 // target normalisation into shared memory (whole CTA).
+// Two rewrites of the network for the tensor cores.  Layer 1's FP32 bias
+// enters the MMA as three BF16 terms (b = hi + mid + lo to FP32 precision) in
+// W1's input rows 7, 8, 9 (zero pads of the packed weights), fed by constant
+// ones in the input: the accumulator equals the unfolded one up to FP32
+// rounding.  The hidden activations are stored as 2 GELU(z) = z (1 + t) with
+// W2, W3, W4 halved: scalings by powers of two are exact in BF16 and in the
+// FP32 products, so this one changes nothing.
+constexpr int BIAS_TERMS = 3;
+static_assert(DIN + BIAS_TERMS <= DINP, "the bias terms need padded input columns");
+__device__ __forceinline__ bf16 bias_term(float b, int k) {
+  const bf16 hi = __float2bfloat16(b);
+  const float r1 = b - __bfloat162float(hi);
+  const bf16 mid = __float2bfloat16(r1);
+  if (k == 0) return hi;
+  if (k == 1) return mid;
+  return __float2bfloat16(r1 - __bfloat162float(mid));
+}
 __device__ void stage_network(const SurrogateDev &sd, unsigned char *smem) {
   const bf16 *W1 = static_cast<const bf16 *>(sd.W1), *W2 = static_cast<const bf16 *>(sd.W2);
   const bf16 *W3 = static_cast<const bf16 *>(sd.W3), *W4 = static_cast<const bf16 *>(sd.W4);
+  const bf16 half = __float2bfloat16(0.5f);
   for (int e = threadIdx.x; e < DINP * H; e += blockDim.x) {
     const int k = e / H, o = e % H;
-    *reinterpret_cast<bf16 *>(smem + OFF_W1 + tc::kmajor_offset(o, k, DINP)) = W1[e];
+    const bf16 w = (k >= DIN && k < DIN + BIAS_TERMS) ? bias_term(sd.b1[o], k - DIN) : W1[e];
+    *reinterpret_cast<bf16 *>(smem + OFF_W1 + tc::kmajor_offset(o, k, DINP)) = w;
   }
   for (int e = threadIdx.x; e < H * H; e += blockDim.x) {
     const int k = e / H, o = e % H;
-    *reinterpret_cast<bf16 *>(smem + OFF_W2 + tc::kmajor_offset(o, k, H)) = W2[e];
-    *reinterpret_cast<bf16 *>(smem + OFF_W3 + tc::kmajor_offset(o, k, H)) = W3[e];
+    *reinterpret_cast<bf16 *>(smem + OFF_W2 + tc::kmajor_offset(o, k, H)) = __hmul(W2[e], half);
+    *reinterpret_cast<bf16 *>(smem + OFF_W3 + tc::kmajor_offset(o, k, H)) = __hmul(W3[e], half);
   }
   for (int e = threadIdx.x; e < H * DOUTP; e += blockDim.x) {
     const int k = e / DOUTP, o = e % DOUTP;
-    *reinterpret_cast<bf16 *>(smem + OFF_W4 + tc::kmajor_offset(o, k, H)) = W4[e];
+    *reinterpret_cast<bf16 *>(smem + OFF_W4 + tc::kmajor_offset(o, k, H)) = __hmul(W4[e], half);
   }
   float *bias = reinterpret_cast<float *>(smem + OFF_BIAS);
   for (int e = threadIdx.x; e < H; e += blockDim.x) {
@@ -764,9 +835,10 @@ __device__ __forceinline__ bool sync_or(uint32_t id, bool flag) {
 // into the activation tile, in the K = 16 layout of layer 1.
 __device__ __forceinline__ void write_input(const Ctx &c, const float (&u)[DIN]) {
   uint32_t w[8];
+  // columns DIN .. DIN + 2 are the constant ones that carry layer 1's bias
+  const auto col = [&](int k) { return k < DIN ? u[k] : (k < DIN + BIAS_TERMS ? 1.f : 0.f); };
 #pragma unroll
-  for (int q = 0; q < 8; ++q)
-    w[q] = pack_bf16x2(2 * q < DIN ? u[2 * q] : 0.f, 2 * q + 1 < DIN ? u[2 * q + 1] : 0.f);
+  for (int q = 0; q < 8; ++q) w[q] = pack_bf16x2(col(2 * q), col(2 * q + 1));
   tc::st_shared_v4(c.act + tc::kmajor_offset(c.row, 0, DINP), w[0], w[1], w[2], w[3]);
   tc::st_shared_v4(c.act + tc::kmajor_offset(c.row, 8, DINP), w[4], w[5], w[6], w[7]);
 }
@@ -792,26 +864,40 @@ __device__ __forceinline__ bool wait_mma(const Ctx &c, uint32_t &phase) {
   return ok;
 }
 
-// Hidden-layer epilogue of this thread's row: accumulator + bias, GELU, BF16,
-// stored as the next layer's A operand (K = 128 layout), 32 columns at a time.
+// z (1 + tanh(z (k + a k z^2))) = 2 GELU(z) on FP32 pairs, the same operations
+// in the same order as gelu_x2 without its final halving (see stage_network).
+__device__ __forceinline__ float2 gelu2_x2(float2 z) {
+  const float2 arg = __fmul2_rn(z, __ffma2_rn(__fmul2_rn(z, z), make_float2(GELU_AK, GELU_AK),
+                                              make_float2(GELU_K, GELU_K)));
+  return __ffma2_rn(z, make_float2(tanh_approx(arg.x), tanh_approx(arg.y)), z);
+}
+
+// Hidden-layer epilogue of this thread's row: accumulator (+ bias for layers
+// 2 and 3; layer 1's is in the MMA), 2 GELU, BF16, stored as the next layer's A
+// operand (K = 128 layout).  16 columns at a time, the load of the next 16
+// in flight while these are evaluated.
+template <bool BIAS>
 __device__ __forceinline__ void hidden_epilogue(const Ctx &c, const float *bias) {
-#pragma unroll 1
-  for (int cc = 0; cc < H / 32; ++cc) {
-    uint32_t v[32];
-    tc::tmem_ld32(c.tmem_t + cc * 32, v);
-    tc::tmem_wait_ld();
-    uint32_t w[16];
-    const float2 *b2 = reinterpret_cast<const float2 *>(bias + cc * 32);
+  uint32_t va[16], vb[16];
+  tc::tmem_ld16(c.tmem_t, va);
+  tc::tmem_wait_ld(va);
 #pragma unroll
-    for (int q = 0; q < 16; ++q) {
-      const float2 z = __fadd2_rn(make_float2(__uint_as_float(v[2 * q]), __uint_as_float(v[2 * q + 1])), b2[q]);
-      const float2 gz = gelu_x2(z);
+  for (int cc = 0; cc < H / 16; ++cc) {
+    uint32_t(&cur)[16] = (cc & 1) ? vb : va;
+    uint32_t(&nxt)[16] = (cc & 1) ? va : vb;
+    if (cc + 1 < H / 16) tc::tmem_ld16(c.tmem_t + (cc + 1) * 16, nxt);
+    uint32_t w[8];
+    const float2 *b2 = reinterpret_cast<const float2 *>(bias + cc * 16);
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+      float2 z = make_float2(__uint_as_float(cur[2 * q]), __uint_as_float(cur[2 * q + 1]));
+      if (BIAS) z = __fadd2_rn(z, b2[q]);
+      const float2 gz = gelu2_x2(z);
       w[q] = pack_bf16x2(gz.x, gz.y);
     }
-#pragma unroll
-    for (int u = 0; u < 4; ++u)
-      tc::st_shared_v4(c.act + tc::kmajor_offset(c.row, cc * 32 + 8 * u, H), w[4 * u], w[4 * u + 1], w[4 * u + 2],
-                       w[4 * u + 3]);
+    tc::st_shared_v4(c.act + tc::kmajor_offset(c.row, cc * 16, H), w[0], w[1], w[2], w[3]);
+    tc::st_shared_v4(c.act + tc::kmajor_offset(c.row, cc * 16 + 8, H), w[4], w[5], w[6], w[7]);
+    if (cc + 1 < H / 16) tc::tmem_wait_ld(nxt);
   }
 }
 
@@ -833,7 +919,10 @@ __device__ bool forward(const Ctx &c, uint32_t &phase, float (&o)[DOUTP], bool &
 #pragma unroll 1
   for (int layer = 0; layer < 3; ++layer) {
     bad = !wait_mma(c, phase) || bad;
-    hidden_epilogue(c, bias + layer * H);
+    if (layer == 0)
+      hidden_epilogue<false>(c, bias);
+    else
+      hidden_epilogue<true>(c, bias + layer * H);
     tc::fence_proxy_async_smem();
     tc::fence_before_sync();
     if (sync_or(c.bar_id, bad)) {
@@ -848,7 +937,7 @@ __device__ bool forward(const Ctx &c, uint32_t &phase, float (&o)[DOUTP], bool &
   bad = !wait_mma(c, phase) || bad;
   uint32_t v[16];
   tc::tmem_ld16(c.tmem_t, v);
-  tc::tmem_wait_ld();
+  tc::tmem_wait_ld(v);
 #pragma unroll
   for (int k = 0; k < DOUTP; ++k) o[k] = __uint_as_float(v[k]) + bias[3 * H + k];
   // the next tile's first barrier orders these reads before its MMAs
@@ -936,6 +1025,13 @@ __global__ void __launch_bounds__(tcn::WG * 128, 1)
     const int64_t j = (tile % tpc) * PPT + pair;
     const CompT<float> &cp = comp[i];
     const bool valid = j < n;
+    {
+      // this row's observation in the warpgroup's next tile, brought into L1
+      // while this tile runs through the network
+      const int64_t nt = tile + (int64_t)gridDim.x * tcn::WG;
+      const int64_t jn = (nt % tpc) * PPT + pair;
+      if (nt < ntiles && jn < n) tc::prefetch_l1(Y + jn * p);
+    }
     RowProblem rp;
     float u[DIN];
     if (valid) {
@@ -1231,14 +1327,14 @@ Gemm fwd_layer(const bf16 *A, int K, const bf16 *W, int N, const float *bias, bf
 
 // forward pass of rows [0, B) from the packed inputs x0; network output in s->out
 cfust_status forward(cfust_surrogate *s, int64_t B) {
-  SG_CUDA(s, gemm(fwd_layer(s->x0, DINP, s->W1, H, s->b1, s->Z1, s->H1, B), 1, s->stream));
-  SG_CUDA(s, gemm(fwd_layer(s->H1, H, s->W2, H, s->b2, s->Z2, s->H2, B), 1, s->stream));
-  SG_CUDA(s, gemm(fwd_layer(s->H2, H, s->W3, H, s->b3, s->Z3, s->H3, B), 1, s->stream));
+  SG_CUDA(s, gemm(fwd_layer(s->x0, DINP, s->W1, H, s->b1, s->Z1, s->H1, B), 1, s->stream, s->d_status));
+  SG_CUDA(s, gemm(fwd_layer(s->H1, H, s->W2, H, s->b2, s->Z2, s->H2, B), 1, s->stream, s->d_status));
+  SG_CUDA(s, gemm(fwd_layer(s->H2, H, s->W3, H, s->b3, s->Z3, s->H3, B), 1, s->stream, s->d_status));
   Gemm g = fwd_layer(s->H3, H, s->W4, DOUTP, s->b4, nullptr, nullptr, B);
   g.mode = 3;
   g.C = s->out;
   g.ldc = DOUTP;
-  SG_CUDA(s, gemm(g, 1, s->stream));
+  SG_CUDA(s, gemm(g, 1, s->stream, s->d_status));
   return CFUST_OK;
 }
 
@@ -1269,7 +1365,7 @@ cfust_status weight_grad(cfust_surrogate *s, const bf16 *Hin, int kin, int kin_r
   g.mode = 0;
   g.C = s->part;
   g.ldc = nout;
-  SG_CUDA(s, gemm(g, S, s->stream));
+  SG_CUDA(s, gemm(g, S, s->stream, s->d_status));
   const int cnt = kin_real * nout_real;
   reduce_partials_kernel<<<(cnt + 255) / 256, 256, 0, s->stream>>>(s->part, S, kin, nout, kin_real, nout_real,
                                                                    s->grad, off);
@@ -1295,7 +1391,7 @@ cfust_status back_layer(cfust_surrogate *s, const bf16 *dZ, int nout, const bf16
   g.Hout = dZprev;
   g.ldo = kin;
   g.Zprev = Zprev;
-  return gemm(g, 1, s->stream) == cudaSuccess ? CFUST_OK : sg_fail(s, CFUST_ECUDA, "gemm (backward)");
+  return gemm(g, 1, s->stream, s->d_status) == cudaSuccess ? CFUST_OK : sg_fail(s, CFUST_ECUDA, "gemm (backward)");
 }
 
 // loss and full gradient (into s->grad) of rows [0, B) with raw targets y

@@ -144,15 +144,21 @@ def _standardised(Y, params, i):
     return d, q, log_tp, sD, xA, xB, inside, edge
 
 
-def _psd_repair(v, floor=1e-6):
+def _psd_repair(v, floor=1e-6, rho=0.999):
+    """The E-step's repair of a predicted covariance (upper order 00 01 02 11
+    12 22), in double: diagonal floored, first-row correlations clamped to
+    |rho|, the last LDL^T factor shrunk so every pivot keeps 1 - rho^2 of its
+    variance, diagonal kept."""
     v = np.asarray(v, dtype=np.float64)
-    d0 = np.maximum(v[:, 0], floor)
-    l10, l20 = v[:, 1] / d0, v[:, 2] / d0
-    d1 = np.maximum(v[:, 3] - l10 * l10 * d0, floor)
-    l21 = (v[:, 4] - l20 * l10 * d0) / d1
-    d2 = np.maximum(v[:, 5] - l20 * l20 * d0 - l21 * l21 * d1, floor)
-    return np.column_stack([d0, l10 * d0, l20 * d0, l10 * l10 * d0 + d1, l20 * l10 * d0 + l21 * d1,
-                            l20 * l20 * d0 + l21 * l21 * d1 + d2])
+    d0, d1, d2 = (np.maximum(v[:, k], floor) for k in (0, 3, 5))
+    m01, m02 = rho * np.sqrt(d0 * d1), rho * np.sqrt(d0 * d2)
+    c01 = np.clip(v[:, 1], -m01, m01)
+    c02 = np.clip(v[:, 2], -m02, m02)
+    l10, l20 = c01 / d0, c02 / d0
+    p1 = d1 - l10 * c01
+    lmax = np.sqrt(np.maximum(rho * rho * d2 - l20 * c02, 0.0) / p1)
+    l21 = np.clip((v[:, 4] - l20 * c01) / p1, -lmax, lmax)
+    return np.column_stack([d0, c01, c02, d1, l20 * c01 + l21 * p1, d2])
 
 
 # Largest error of the BF16 tensor-core network in its normalised output units
