@@ -30,6 +30,25 @@ int sm_count() {
   return sms;
 }
 
+cudaError_t raise_smem_limit(const void *func, size_t bytes) {
+  if (bytes <= 48 * 1024) return cudaSuccess;
+  static std::mutex m;
+  static std::vector<std::pair<std::pair<int, const void *>, size_t>> raised;
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) dev = -1;
+  std::lock_guard<std::mutex> lock(m);
+  for (auto &e : raised)
+    if (e.first.first == dev && e.first.second == func) {
+      if (bytes <= e.second) return cudaSuccess;
+      const cudaError_t err = cudaFuncSetAttribute(func, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+      if (err == cudaSuccess) e.second = bytes;
+      return err;
+    }
+  const cudaError_t err = cudaFuncSetAttribute(func, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+  if (err == cudaSuccess) raised.push_back({{dev, func}, bytes});
+  return err;
+}
+
 }  // namespace cfust
 
 struct cfust_ctx {

@@ -14,6 +14,13 @@ constexpr int PMAX = CFUST_PMAX;
 // queried once per device ordinal and cached).  Persistent grids and block caps
 // are sized from it.
 int sm_count();
+
+// Raises the dynamic shared-memory limit of a kernel on the current device to
+// at least `bytes` (never lowers it; nothing to do up to the default 48 KB).
+// A limit that went down after a launch was captured into a CUDA graph could
+// leave the graph's launch above it, so every kernel of this library sets its
+// limit through here.
+cudaError_t raise_smem_limit(const void *func, size_t bytes);
 constexpr int RMAX = CFUST_RMAX;
 constexpr int WARP = 32;
 

@@ -1160,10 +1160,8 @@ cudaError_t launch_r(EArgs a, int g, int64_t n, cudaStream_t st, bool fp32,
   // the prioritised sweep is its own instantiation (r >= 2), so the default
   // one carries none of its registers
   const bool prio = a.prio && R >= 2;
-  cudaError_t e = prio ? cudaFuncSetAttribute(estep_kernel<T, R, DENS, (R >= 2)>,
-                                              cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)
-                       : cudaFuncSetAttribute(estep_kernel<T, R, DENS, false>,
-                                              cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  cudaError_t e = prio ? raise_smem_limit((const void *)estep_kernel<T, R, DENS, (R >= 2)>, smem)
+                       : raise_smem_limit((const void *)estep_kernel<T, R, DENS, false>, smem);
   if (e != cudaSuccess) return e;
   const int64_t per_cta = (int64_t)a.ppw * 8;
   const int64_t bx = (n + per_cta - 1) / per_cta;
@@ -1337,10 +1335,8 @@ cudaError_t launch_batched_r(EArgs a, const BatchDev &b, const SweepItem *items,
   const bool prio = a.prio && R >= 2;
   const size_t smem = (a.staged ? align16(tab_bytes) : 0) + align16(sizeof(CompT<T>)) +
                       align16(sizeof(PairedConsts)) + 16 + (prio ? 8 * sizeof(PairedConsts) : 0);
-  cudaError_t e = prio ? cudaFuncSetAttribute(estep_batched_kernel<T, R, DENS, (R >= 2)>,
-                                              cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)
-                       : cudaFuncSetAttribute(estep_batched_kernel<T, R, DENS, false>,
-                                              cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  cudaError_t e = prio ? raise_smem_limit((const void *)estep_batched_kernel<T, R, DENS, (R >= 2)>, smem)
+                       : raise_smem_limit((const void *)estep_batched_kernel<T, R, DENS, false>, smem);
   if (e != cudaSuccess) return e;
   if ((e = cudaMemsetAsync(counter, 0, sizeof(unsigned), st)) != cudaSuccess) return e;
   if (fp32 && (e = cudaMemsetAsync(a.rescue_count, 0, sizeof(unsigned), st)) != cudaSuccess) return e;
@@ -1468,10 +1464,8 @@ cudaError_t launch_list_r3(EArgs a, int g, int64_t n, const int *list, const uns
   a.staged = tab_bytes <= 160u * 1024u ? 1 : 0;
   const size_t smem = (a.staged ? align16(tab_bytes) : 0) + align16(sizeof(CompT<float>)) +
                       align16(sizeof(PairedConsts)) + 16 + (a.prio ? 8 * sizeof(PairedConsts) : 0);
-  cudaError_t e = a.prio ? cudaFuncSetAttribute(estep_list_kernel<float, 3, DENS, true>,
-                                                cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)
-                         : cudaFuncSetAttribute(estep_list_kernel<float, 3, DENS, false>,
-                                                cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  cudaError_t e = a.prio ? raise_smem_limit((const void *)estep_list_kernel<float, 3, DENS, true>, smem)
+                         : raise_smem_limit((const void *)estep_list_kernel<float, 3, DENS, false>, smem);
   if (e != cudaSuccess) return e;
   // 16 listed pairs per warp chunk: their FP64 prologues and triage tests run
   // lane-parallel, which matters at the small lattices this path serves

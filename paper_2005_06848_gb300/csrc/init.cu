@@ -262,11 +262,11 @@ cudaError_t launch_group_sums(int mode, const double *Y, int64_t n, int p, int g
   const size_t smem = group_sums_smem(mode, p, g);
   cudaError_t e;
   if (mode == 0) {
-    e = cudaFuncSetAttribute(group_sums_kernel<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    e = raise_smem_limit((const void *)group_sums_kernel<0>, (size_t)((int)smem));
     if (e != cudaSuccess) return e;
     group_sums_kernel<0><<<nblk, IT, smem, st>>>(Y, n, p, g, labels, cm, assign, first, partials, changed, status);
   } else {
-    e = cudaFuncSetAttribute(group_sums_kernel<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    e = raise_smem_limit((const void *)group_sums_kernel<1>, (size_t)((int)smem));
     if (e != cudaSuccess) return e;
     group_sums_kernel<1><<<nblk, IT, smem, st>>>(Y, n, p, g, labels, cm, 0, 0, partials, changed, status);
   }

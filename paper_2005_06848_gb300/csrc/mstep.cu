@@ -68,6 +68,12 @@ __device__ __forceinline__ float2 df_mul(float2 x, float2 y) {
   e = __fmaf_rn(x.y, y.x, e);
   return make_float2(p, e);
 }
+// a + b exactly as an unevaluated pair (Knuth's two-sum)
+__device__ __forceinline__ float2 two_sum(float a, float b) {
+  const float s = __fadd_rn(a, b);
+  const float bp = __fsub_rn(s, a);
+  return make_float2(s, __fadd_rn(__fsub_rn(a, __fsub_rn(s, bp)), __fsub_rn(b, bp)));
+}
 // hi + lo += v.x + v.y (two-sum on the leading parts, the rests added to lo)
 __device__ __forceinline__ void df_acc(float &hi, float &lo, float2 v) {
   const float s = __fadd_rn(hi, v.x);
@@ -84,12 +90,13 @@ __device__ __forceinline__ void df_acc(float &hi, float &lo, float2 v) {
 // tau, e1..e4 and the double-precision observations (y split into two
 // floats), summed within a 64-observation tile with two-sum compensation
 // (about 2^-42 of the sum of |terms| per tile) and across tiles in double:
-// double-precision sums of the same inputs up to ~1e-13.  Native double
-// precision keeps log pi_i + log f_ij, its maximum and the differences (the
-// log-sum-exp's exponents), and l_j = max + log s_j with its sum over the
-// observations; the exponentials and tau are single precision (tau to 1e-7
-// relative, the level of the single-precision log f_ij it comes from), and
-// so is log s_j (s_j in [1, g]: 1e-7 absolute).
+// double-precision sums of the same inputs up to ~1e-13.  log pi_i + log f_ij
+// is formed exactly as a float pair (two-sum), its maximum and the
+// differences (the log-sum-exp's exponents) from the pairs, and
+// l_j = max + log s_j and its sum over the observations in native double;
+// the exponentials and tau are single precision (tau to ~1e-7 relative, the
+// level of the single-precision log f_ij it comes from), and so is log s_j
+// (s_j in [1, g]: 1e-7 absolute).
 __device__ __forceinline__ void posterior_block_f32(const PosteriorArgs &a, int c0, int c1, int blk, int nblk,
                                                     unsigned char *smem_raw) {
   const int p = a.p, r = a.r, g = a.g;
@@ -113,9 +120,15 @@ __device__ __forceinline__ void posterior_block_f32(const PosteriorArgs &a, int 
   int own_w[MAXOWN], own_y1[MAXOWN], own_y2[MAXOWN], own_c[MAXOWN];
   double acc[MAXOWN];
   const int E = a.want_sums ? gc * K : 0;
+  // With few sum entries (a small mixture), S adjacent threads share one
+  // entry: each sums every S-th row of the tile, and the S partial sums are
+  // merged by shuffles in a fixed order, so more of the block's threads work
+  // on the tile's column sums.  S = 1 keeps one entry per thread.
+  const int S = (E > 0 && 4 * E <= THREADS) ? 4 : ((E > 0 && 2 * E <= THREADS) ? 2 : 1);
+  const int split = threadIdx.x % S;
 #pragma unroll
   for (int k = 0; k < MAXOWN; ++k) {
-    const int e = threadIdx.x + k * THREADS;
+    const int e = (S > 1) ? (k == 0 ? (int)threadIdx.x / S : E) : (int)threadIdx.x + k * THREADS;
     acc[k] = 0.0;
     own_c[k] = -1;
     own_w[k] = 0;
@@ -129,8 +142,15 @@ __device__ __forceinline__ void posterior_block_f32(const PosteriorArgs &a, int 
   int bad = 0;
   const int64_t ntiles = (n + TJ - 1) / TJ;
   const bool first_chunk = (c0 == 0);
-  __shared__ double lpi[CFUST_GMAX];
-  for (int i = threadIdx.x; i < g; i += THREADS) lpi[i] = log(a.pi[i]);
+  // log pi_i as a float pair (hi + lo to double precision), so that the
+  // log-sum-exp's exponents log pi_i + log f_ij - max are formed on the
+  // single-precision pipe
+  __shared__ float2 lpi2[CFUST_GMAX];
+  for (int i = threadIdx.x; i < g; i += THREADS) {
+    const double l = log(a.pi[i]);
+    const float hi = (float)l;
+    lpi2[i] = make_float2(hi, (float)(l - (double)hi));
+  }
   __syncthreads();
 
   for (int64_t tile = blk; tile < ntiles; tile += nblk) {
@@ -146,9 +166,16 @@ __device__ __forceinline__ void posterior_block_f32(const PosteriorArgs &a, int 
       const int jj = threadIdx.x;
       const int64_t j = j0 + jj;
       if (lfp != nullptr) {
-        double mx = -INFINITY;
-        for (int i = 0; i < g; ++i) mx = fmax(mx, lpi[i] + (double)lfp[(int64_t)i * n + j]);
-        if (!isfinite(mx)) {
+        // a_i = log pi_i + log f_ij as a float pair (exact sum of the float
+        // log f and the pair of log pi); the shift is the largest a_i
+        float2 mx = make_float2(-INFINITY, 0.0f);
+        for (int i = 0; i < g; ++i) {
+          const float lf = lfp[(int64_t)i * n + j];
+          float2 ai = two_sum(lpi2[i].x, lf);
+          ai.y = __fadd_rn(ai.y, lpi2[i].y);
+          if (ai.x > mx.x || (ai.x == mx.x && ai.y > mx.y)) mx = ai;
+        }
+        if (!isfinite(mx.x)) {
           // no component gives the observation a positive density: flagged,
           // and its weights are zero so that the sums stay defined
           bad = 1;
@@ -159,14 +186,21 @@ __device__ __forceinline__ void posterior_block_f32(const PosteriorArgs &a, int 
         } else {
           float s = 0.0f;
           for (int i = 0; i < g; ++i) {
-            const float ex = expf((float)(lpi[i] + (double)lfp[(int64_t)i * n + j] - mx));
+            const float lf = lfp[(int64_t)i * n + j];
+            float2 ai = two_sum(lpi2[i].x, lf);
+            ai.y = __fadd_rn(ai.y, lpi2[i].y);
+            // the exponent a_i - max (exact leading difference where the two
+            // are within a factor two, else rounded: 2^-24 of an exponent
+            // whose exponential is then below e^-1 of the largest)
+            const float dx = __fadd_rn(__fsub_rn(ai.x, mx.x), __fsub_rn(ai.y, mx.y));
+            const float ex = (ai.x == -INFINITY) ? 0.0f : expf(dx);
             s = __fadd_rn(s, ex);
             if (a.want_sums && i >= c0 && i < c1) ws[((i - c0) * TJ + jj) * WR] = make_float2(ex, 0.0f);
             if (tau_out != nullptr && first_chunk) tau_out[(int64_t)i * n + j] = ex;
           }
           // s is in [1, g]: its single-precision logarithm is good to 1e-7
-          // absolute, below the error of the log f_ij it sums
-          const double lse = mx + (double)logf(s);
+          // absolute, below the error of the log f_ij it sums; l_j in double
+          const double lse = (double)mx.x + (double)mx.y + (double)logf(s);
           if (!isfinite(lse)) bad = 1;
           llacc += lse;
           const float inv = 1.0f / s;
@@ -203,35 +237,43 @@ __device__ __forceinline__ void posterior_block_f32(const PosteriorArgs &a, int 
       __syncthreads();
 #pragma unroll
       for (int k = 0; k < MAXOWN; ++k) {
+        // two compensated chains (rows jj and jj + S) for instruction-level
+        // parallelism, merged by a further two-sum; this thread's rows are
+        // split, split + S, ...
+        float h0 = 0.0f, l0 = 0.0f, h1 = 0.0f, l1 = 0.0f;
         if (own_c[k] >= 0) {
           const float2 *col = ws + own_c[k] * TJ * WR + own_w[k];
           const int y1 = own_y1[k], y2 = own_y2[k];
-          // two compensated chains (even and odd rows) for instruction-level
-          // parallelism, merged by a further two-sum
-          float h0 = 0.0f, l0 = 0.0f, h1 = 0.0f, l1 = 0.0f;
-          int jj = 0;
+          int jj = split;
           if (y1 < 0) {
-            for (; jj + 2 <= nt; jj += 2) {
+            for (; jj + S < nt; jj += 2 * S) {
               df_acc(h0, l0, col[jj * WR]);
-              df_acc(h1, l1, col[(jj + 1) * WR]);
+              df_acc(h1, l1, col[(jj + S) * WR]);
             }
             if (jj < nt) df_acc(h0, l0, col[jj * WR]);
           } else if (y2 < 0) {
-            for (; jj + 2 <= nt; jj += 2) {
+            for (; jj + S < nt; jj += 2 * S) {
               df_acc(h0, l0, df_mul(col[jj * WR], ys[jj * p + y1]));
-              df_acc(h1, l1, df_mul(col[(jj + 1) * WR], ys[(jj + 1) * p + y1]));
+              df_acc(h1, l1, df_mul(col[(jj + S) * WR], ys[(jj + S) * p + y1]));
             }
             if (jj < nt) df_acc(h0, l0, df_mul(col[jj * WR], ys[jj * p + y1]));
           } else {
-            for (; jj + 2 <= nt; jj += 2) {
+            for (; jj + S < nt; jj += 2 * S) {
               df_acc(h0, l0, df_mul(df_mul(col[jj * WR], ys[jj * p + y1]), ys[jj * p + y2]));
-              df_acc(h1, l1, df_mul(df_mul(col[(jj + 1) * WR], ys[(jj + 1) * p + y1]), ys[(jj + 1) * p + y2]));
+              df_acc(h1, l1, df_mul(df_mul(col[(jj + S) * WR], ys[(jj + S) * p + y1]), ys[(jj + S) * p + y2]));
             }
             if (jj < nt) df_acc(h0, l0, df_mul(df_mul(col[jj * WR], ys[jj * p + y1]), ys[jj * p + y2]));
           }
           df_acc(h0, l0, make_float2(h1, l1));
-          acc[k] += (double)h0 + (double)l0;
         }
+        if (S > 1 && k == 0) {
+          // the entry's S partial sums, from adjacent lanes, in a fixed order
+          for (int o = 1; o < S; o <<= 1) {
+            const float h2 = __shfl_xor_sync(0xffffffffu, h0, o), l2 = __shfl_xor_sync(0xffffffffu, l0, o);
+            df_acc(h0, l0, make_float2(h2, l2));
+          }
+        }
+        if (own_c[k] >= 0 && split == 0) acc[k] += (double)h0 + (double)l0;
       }
     }
     __syncthreads();
@@ -239,10 +281,16 @@ __device__ __forceinline__ void posterior_block_f32(const PosteriorArgs &a, int 
 
   if (a.want_sums) {
     double *dst = a.partials + (int64_t)blk * g * K;
+    if (S > 1) {
+      // the first thread of each group of S holds its entry's total
+      const int e = (int)threadIdx.x / S;
+      if (split == 0 && e < E) dst[(int64_t)c0 * K + e] = acc[0];
+    } else {
 #pragma unroll
-    for (int k = 0; k < MAXOWN; ++k) {
-      const int e = threadIdx.x + k * THREADS;
-      if (e < E) dst[(int64_t)c0 * K + e] = acc[k];
+      for (int k = 0; k < MAXOWN; ++k) {
+        const int e = threadIdx.x + k * THREADS;
+        if (e < E) dst[(int64_t)c0 * K + e] = acc[k];
+      }
     }
   }
   if (a.want_ll && first_chunk) {
@@ -721,14 +769,12 @@ cudaError_t launch_posterior_batched(int precision, const BatchDev &b, int p, in
   if (smem > 200 * 1024) return cudaErrorInvalidValue;
   cudaError_t e;
   if (precision == CFUST_FP64) {
-    e = cudaFuncSetAttribute(posterior_batched_kernel<double>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)smem);
+    e = raise_smem_limit((const void *)posterior_batched_kernel<double>, (size_t)((int)smem));
     if (e != cudaSuccess) return e;
     posterior_batched_kernel<double><<<nblocks, THREADS, smem, st>>>(b, p, r, blocks, partials, ll_partials,
                                                                      want_sums);
   } else {
-    e = cudaFuncSetAttribute(posterior_batched_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)smem);
+    e = raise_smem_limit((const void *)posterior_batched_kernel<float>, (size_t)((int)smem));
     if (e != cudaSuccess) return e;
     posterior_batched_kernel<float><<<nblocks, THREADS, smem, st>>>(b, p, r, blocks, partials, ll_partials,
                                                                     want_sums);
@@ -774,13 +820,11 @@ cudaError_t launch_posterior(int precision, const PosteriorArgs &a, cudaStream_t
     const size_t smem = a.want_sums ? ((size_t)TJ * a.p + (size_t)(c1 - c0) * TJ * WR) * 8 : 16;
     cudaError_t e;
     if (precision == CFUST_FP64) {
-      e = cudaFuncSetAttribute(posterior_kernel<double>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                               (int)smem);
+      e = raise_smem_limit((const void *)posterior_kernel<double>, (size_t)((int)smem));
       if (e != cudaSuccess) return e;
       posterior_kernel<double><<<a.nblocks, THREADS, smem, st>>>(a, c0, c1);
     } else {
-      e = cudaFuncSetAttribute(posterior_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                               (int)smem);
+      e = raise_smem_limit((const void *)posterior_kernel<float>, (size_t)((int)smem));
       if (e != cudaSuccess) return e;
       posterior_kernel<float><<<a.nblocks, THREADS, smem, st>>>(a, c0, c1);
     }

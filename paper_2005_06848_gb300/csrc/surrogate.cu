@@ -1207,13 +1207,12 @@ cudaError_t launch_surrogate_estep(const SurrogateDev &sd, const double *Y, int6
   int64_t blocks = (ntiles + sg::tcn::WG - 1) / sg::tcn::WG;
   if (blocks > sms) blocks = sms;
   if (density_only) {
-    e = cudaFuncSetAttribute(sg::surrogate_estep_tc_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    e = raise_smem_limit((const void *)sg::surrogate_estep_tc_kernel<true>, (size_t)(smem));
     if (e != cudaSuccess) return e;
     sg::surrogate_estep_tc_kernel<true><<<(unsigned)blocks, sg::tcn::WG * 128, smem, st>>>(sd, Y, n, g, p, c32, out,
                                                                                            fb_list, fb_count, status);
   } else {
-    e = cudaFuncSetAttribute(sg::surrogate_estep_tc_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             smem);
+    e = raise_smem_limit((const void *)sg::surrogate_estep_tc_kernel<false>, (size_t)(smem));
     if (e != cudaSuccess) return e;
     sg::surrogate_estep_tc_kernel<false><<<(unsigned)blocks, sg::tcn::WG * 128, smem, st>>>(
         sd, Y, n, g, p, c32, out, fb_list, fb_count, status);
@@ -1613,7 +1612,7 @@ cfust_status cfust_surrogate_predict(cfust_surrogate *s, const float *x, float *
   const int64_t ntiles = (B + tcn::ROWS - 1) / tcn::ROWS;
   int64_t blocks = (ntiles + tcn::WG - 1) / tcn::WG;
   if (blocks > sm_count()) blocks = sm_count();
-  SG_CUDA(s, cudaFuncSetAttribute(predict_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tcn::SMEM));
+  SG_CUDA(s, raise_smem_limit((const void *)predict_tc_kernel, (size_t)((int)tcn::SMEM)));
   SG_CUDA(s, cudaMemsetAsync(s->d_status, 0, sizeof(int), s->stream));
   predict_tc_kernel<<<(unsigned)blocks, tcn::WG * 128, tcn::SMEM, s->stream>>>(surrogate_dev(s), x, y, B,
                                                                                s->d_status);

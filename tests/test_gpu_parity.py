@@ -271,9 +271,13 @@ def test_mstep_matches_oracle_fp64():
         _cmp(name, a, b, 1e-10)
 
 
-def test_mstep_matches_oracle_fp32():
+@pytest.mark.parametrize("workload", ["cfust_p4r4g3_n100000_N4096", "cfust_p3r3g4_n1000000_N2048",
+                                      "cfust_p2r2g2_n2000_N1024"])
+def test_mstep_matches_oracle_fp32(workload):
     """Single-precision-mode M-step (CFUST_FP32) against the oracle's FP64
-    M-step on the same single-precision tau and e1..e4.
+    M-step on the same single-precision tau and e1..e4.  The three mixtures
+    have 141, 120 and 34 sum entries: one, two and four threads share an
+    entry's column sums in the kernel.
 
     The kernel forms every product tau e y exactly (two-product, y split
     into two floats) and sums them in double-float within a 64-observation
@@ -285,7 +289,7 @@ def test_mstep_matches_oracle_fp32():
     (2000 = 31 x 64 + 16).
     """
     torch = _torch()
-    Y, truth, init, lat = _problem("cfust_p4r4g3_n100000_N4096", 2000, 1024)
+    Y, truth, init, lat = _problem(workload, 2000, 1024)
     R = _oracle_estep(Y, init, lat)
     r = init.r
     f32 = lambda a: np.ascontiguousarray(a, dtype=np.float32)
