@@ -120,6 +120,18 @@ typedef struct {
                              give up with CFUST_ETIMEOUT; k > 0 sets that bound, -1 makes the wait give
                              up at once.  On giving up a block first lets its copy land (bounded by the
                              default), then returns: no fault, no hang, the context stays usable. */
+  int fused;              /* 1: cfust_fit (and cfust_fit_begin/step/end) and cfust_loglik run each E-step
+                             and the M-step sums of Section 3.2 (Algorithm 2's per-block partial sums) as
+                             one kernel: a CTA takes a tile of observations through all g components,
+                             keeps log f_ij and e1..e4 in shared memory only, forms tau (Eq. 4), l_j
+                             (Eq. 3) and every sum entry, and writes per-block partials that the M-step
+                             (Algorithm 3) combines.  Nothing of size g x n is allocated or moved: the
+                             fit holds Y and the partial sums only.  Same rule and per-pair arithmetic as
+                             the unfused path (results agree to summation order; pairs needing the
+                             double-precision rescue are recomputed by the tile's CTA).  cfust_estep,
+                             cfust_mstep*, cfust_fit_batched and the explicit E-step outputs keep the
+                             unfused kernels; a fit or log-likelihood with a surrogate attached and
+                             fused = 1 fails with CFUST_EINVAL. */
 } cfust_opts;
 
 typedef struct cfust_ctx cfust_ctx;

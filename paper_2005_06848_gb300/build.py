@@ -19,14 +19,14 @@ INCLUDE = os.path.join(ROOT, "include")
 LIBDIR = os.path.join(PKG, "_lib")
 LIB = os.path.join(LIBDIR, "libcfust.so")
 
-SOURCES = ["api.cu", "precompute.cu", "estep.cu", "mstep.cu", "surrogate.cu", "init.cu"]
-HEADERS = ["cfust_internal.cuh", "special.cuh", "normal_f32.cuh", "normal_f32_coeffs.cuh", "tcgen05.cuh"]
+SOURCES = ["api.cu", "precompute.cu", "estep.cu", "fused.cu", "mstep.cu", "surrogate.cu", "init.cu"]
+HEADERS = ["cfust_internal.cuh", "sweep.cuh", "sums.cuh", "special.cuh", "normal_f32.cuh", "normal_f32_coeffs.cuh", "tcgen05.cuh"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr",
          "-I", INCLUDE, "-I", CSRC]
 # the sweep unit instantiates some seventy kernels: let nvcc optimise them in
 # parallel over the host cores (each kernel is compiled on its own either way)
-PER_SOURCE = {"estep.cu": ["--split-compile=0"]}
+PER_SOURCE = {"estep.cu": ["--split-compile=0"], "fused.cu": ["--split-compile=0"]}
 
 
 def nvcc() -> str:

@@ -31,21 +31,27 @@ int sm_count() {
 }
 
 cudaError_t raise_smem_limit(const void *func, size_t bytes) {
-  if (bytes <= 48 * 1024) return cudaSuccess;
+  // the limit a launch may use without the opt-in is 48 KB less the
+  // function's static shared memory: read it (cudaFuncGetAttributes) the first
+  // time a function is seen on a device, then only ever raise it
   static std::mutex m;
-  static std::vector<std::pair<std::pair<int, const void *>, size_t>> raised;
+  static std::vector<std::pair<std::pair<int, const void *>, size_t>> limits;
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess) dev = -1;
   std::lock_guard<std::mutex> lock(m);
-  for (auto &e : raised)
-    if (e.first.first == dev && e.first.second == func) {
-      if (bytes <= e.second) return cudaSuccess;
-      const cudaError_t err = cudaFuncSetAttribute(func, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
-      if (err == cudaSuccess) e.second = bytes;
-      return err;
-    }
+  std::pair<std::pair<int, const void *>, size_t> *ent = nullptr;
+  for (auto &e : limits)
+    if (e.first.first == dev && e.first.second == func) ent = &e;
+  if (!ent) {
+    cudaFuncAttributes fa;
+    const cudaError_t err = cudaFuncGetAttributes(&fa, func);
+    if (err != cudaSuccess) return err;
+    limits.push_back({{dev, func}, (size_t)(fa.maxDynamicSharedSizeBytes > 0 ? fa.maxDynamicSharedSizeBytes : 0)});
+    ent = &limits.back();
+  }
+  if (bytes <= ent->second) return cudaSuccess;
   const cudaError_t err = cudaFuncSetAttribute(func, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
-  if (err == cudaSuccess) raised.push_back({{dev, func}, bytes});
+  if (err == cudaSuccess) ent->second = bytes;
   return err;
 }
 
@@ -180,7 +186,9 @@ void drop_graph(cfust_ctx *c) {
 }
 
 // (Re)allocate every device buffer for shapes (g, p, r) and n observations.
-cfust_status ensure(cfust_ctx *c, int g, int p, int r, int64_t n) {
+// `pairs` = false leaves out the g x n per-pair buffers (the fused path's
+// fits and log-likelihoods never touch them).
+cfust_status ensure(cfust_ctx *c, int g, int p, int r, int64_t n, bool pairs = true) {
   const int N = c->lat.n;
   if (g != c->g || p != c->p || r != c->r) {
     drop_graph(c);
@@ -203,14 +211,15 @@ cfust_status ensure(cfust_ctx *c, int g, int p, int r, int64_t n) {
     CF_CUDA(c, cudaMalloc(&c->d_ll, sizeof(double)));
     CF_CUDA(c, cudaMemset(c->d_rescue_cnt, 0, sizeof(unsigned)));
   }
-  const int nb = posterior_nblocks(n);
+  int nb = posterior_nblocks(n);
+  if (c->opts.fused && fused_max_blocks() > nb) nb = fused_max_blocks();
   if (nb > c->nb_cap) {
     drop_graph(c);
     CF_CUDA(c, realloc_dev(&c->d_partials, sizeof(double) * (size_t)nb * g * sums_width(p, r)));
     CF_CUDA(c, realloc_dev(&c->d_llpart, sizeof(double) * (size_t)nb));
     c->nb_cap = nb;
   }
-  if (n > c->n_cap) {
+  if (pairs && n > c->n_cap) {
     drop_graph(c);
     const size_t es = elem_size(c);
     const size_t gn = (size_t)g * (size_t)n;
@@ -403,11 +412,35 @@ cfust_status run_estep(cfust_ctx *c, const double *Y, int64_t n, EstepOut o, boo
   return CFUST_OK;
 }
 
+// The fused E-step + sums launch (density_only: the log-likelihood partials
+// only); *nb receives the number of partial rows it writes.
+cfust_status enqueue_fused(cfust_ctx *c, const double *Y, int64_t n, bool density_only, cudaStream_t st,
+                           SweepTiming tm, int *nb) {
+  if (c->sur)
+    return fail(c, CFUST_EINVAL, "the fused pass covers the lattice rule: detach the surrogate or set fused = 0");
+  const double *pi = param_view(c->d_params, c->g, c->p, c->r).pi;
+  CF_CUDA(c, launch_fused(c->opts.precision, Y, n, c->g, c->p, c->r, c->lat, c->d_c64, c->d_c32, c->d_chi64,
+                          c->d_chi32, density_only, c->opts.e2_mode, c->d_status, c->d_rescue_cnt,
+                          c->opts.pairs_per_warp, c->d_partials, c->d_llpart, pi, (float)c->opts.triage_nats,
+                          c->opts.prioritise, st, tm, nb));
+  return CFUST_OK;
+}
+
 // One EM iteration on the stream: E-step at the device parameters (yielding
 // their log-likelihood into trace[iter]), then the M-step in place.
 cfust_status enqueue_iteration(cfust_ctx *c, const double *Y, int64_t n, cudaStream_t st) {
   CF_CUDA(c, launch_precompute(c->d_params, c->g, c->p, c->r, c->lat, c->d_c64, c->d_c32, c->d_chi64,
                                c->d_chi32, c->d_status, st));
+  if (c->opts.fused) {
+    // one kernel for the E-step and the sums; the timing events bracket it
+    int nb = 0;
+    cfust_status s = enqueue_fused(c, Y, n, false, st, sweep_timing(c, st == c->cap_stream), &nb);
+    if (s != CFUST_OK) return s;
+    CF_CUDA(c, launch_reduce_ll(c->d_llpart, nb, c->d_ll, c->d_trace, c->d_status + 1, st));
+    CF_CUDA(c, launch_mstep_finalize(c->d_partials, nb, c->g, c->p, c->r, n, nu_lo(c), nu_hi(c), c->d_params,
+                                     c->d_status, st));
+    return CFUST_OK;
+  }
   cfust_status s = run_estep(c, Y, n, ctx_out(c), false, st, sweep_timing(c, st == c->cap_stream), 1);
   if (s != CFUST_OK) return s;
   PosteriorArgs a = post_args(c, Y, n);
@@ -437,6 +470,13 @@ cfust_status enqueue_iteration(cfust_ctx *c, const double *Y, int64_t n, cudaStr
 cfust_status enqueue_loglik(cfust_ctx *c, const double *Y, int64_t n, double *trace) {
   CF_CUDA(c, launch_precompute(c->d_params, c->g, c->p, c->r, c->lat, c->d_c64, c->d_c32, c->d_chi64,
                                c->d_chi32, c->d_status, c->stream));
+  if (c->opts.fused) {
+    int nb = 0;
+    cfust_status s = enqueue_fused(c, Y, n, true, c->stream, sweep_timing(c, false), &nb);
+    if (s != CFUST_OK) return s;
+    CF_CUDA(c, launch_reduce_ll(c->d_llpart, nb, c->d_ll, trace, c->d_status + 1, c->stream));
+    return CFUST_OK;
+  }
   EstepOut o{};
   o.logf = c->d_logf;
   cfust_status s = run_estep(c, Y, n, o, true, c->stream, sweep_timing(c, false), 1);
@@ -499,6 +539,10 @@ cfust_status cfust_create(cfust_ctx **out, const cfust_opts *o, void *cuda_strea
   }
   if (o->test_wait_polls < -1) {
     g_create_error = "test_wait_polls must be -1, 0 or positive";
+    return CFUST_EINVAL;
+  }
+  if (o->fused != 0 && o->fused != 1) {
+    g_create_error = "fused must be 0 or 1";
     return CFUST_EINVAL;
   }
   cfust_ctx *c = new cfust_ctx();
@@ -696,7 +740,7 @@ cfust_status cfust_loglik(cfust_ctx *c, const double *Y, int64_t n, const cfust_
   if (s != CFUST_OK) return s;
   if (!loglik) return fail(c, CFUST_EINVAL, "loglik is NULL");
   DeviceGuard dg(c->device);
-  if ((s = ensure(c, P->g, P->p, P->r, n)) != CFUST_OK) return s;
+  if ((s = ensure(c, P->g, P->p, P->r, n, !c->opts.fused)) != CFUST_OK) return s;
   if ((s = upload_params(c, P)) != CFUST_OK) return s;
   CF_CUDA(c, cudaMemsetAsync(c->d_status, 0, 2 * sizeof(int), c->stream));
   if ((s = enqueue_loglik(c, Y, n, nullptr)) != CFUST_OK) return s;
@@ -813,7 +857,7 @@ cfust_status cfust_fit_begin(cfust_ctx *c, const double *Y, int64_t n, const cfu
   cfust_status s = check_common(c, Y, n, P);
   if (s != CFUST_OK) return s;
   DeviceGuard dg(c->device);
-  if ((s = ensure(c, P->g, P->p, P->r, n)) != CFUST_OK) return s;
+  if ((s = ensure(c, P->g, P->p, P->r, n, !c->opts.fused)) != CFUST_OK) return s;
   const int K = c->opts.max_iter;
   if (K + 1 > c->trace_cap) {
     CF_CUDA(c, realloc_dev(&c->d_trace, sizeof(double) * (K + 1)));

@@ -16,7 +16,8 @@ constexpr int PMAX = CFUST_PMAX;
 int sm_count();
 
 // Raises the dynamic shared-memory limit of a kernel on the current device to
-// at least `bytes` (never lowers it; nothing to do up to the default 48 KB).
+// at least `bytes` (never lowers it; nothing to do up to the default, which is
+// 48 KB less the function's static shared memory).
 // A limit that went down after a launch was captured into a CUDA graph could
 // leave the graph's launch above it, so every kernel of this library sets its
 // limit through here.
@@ -216,6 +217,18 @@ struct PosteriorArgs {
 };
 cudaError_t launch_posterior(int precision, const PosteriorArgs &a, cudaStream_t st);
 int posterior_nblocks(int64_t n);
+
+// Fused E-step + M-step sums (fused.cu): every observation through all g
+// components per tile of observations, the per-pair outputs in shared memory
+// only; writes the partial sums [*nblocks][g][K] and the log-likelihood
+// partials [*nblocks] that the M-step finalize and reduce_ll read (only the
+// log-likelihood partials when density_only).  *nblocks <= fused_max_blocks().
+int fused_max_blocks();
+cudaError_t launch_fused(int precision, const double *Y, int64_t n, int g, int p, int r, const LatticeDev &lat,
+                         const CompT<double> *c64, const CompT<float> *c32, const double *chi64, const float *chi32,
+                         bool density_only, int e2_mode, int *d_status, unsigned *rescue_count, int pairs_per_warp,
+                         double *partials, double *ll_partials, const double *d_pi, float tnats, int prio,
+                         cudaStream_t st, SweepTiming tm, int *nblocks);
 
 // Sum the per-block log-likelihood partials in a fixed order: *ll_out = sum,
 // and when trace != NULL also trace[*iter] = sum and ++*iter.

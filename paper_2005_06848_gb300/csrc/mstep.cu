@@ -18,6 +18,7 @@
 
 #include "cfust_internal.cuh"
 #include "special.cuh"
+#include "sums.cuh"
 
 namespace cfust {
 
@@ -26,62 +27,6 @@ namespace {
 constexpr int TJ = 64;       // observations per tile
 constexpr int MAXOWN = 8;    // sum entries per thread
 constexpr int THREADS = 256;
-
-__device__ inline void entry_desc(int ent, int p, int r, int *w, int *y1, int *y2) {
-  const int rp = r * (r + 1) / 2;
-  *y1 = -1;
-  *y2 = -1;
-  if (ent == 0) { *w = 0; return; }                 // S1
-  if (ent == 1) { *w = 1; return; }                 // S2
-  ent -= 2;
-  if (ent < p) { *w = 1; *y1 = ent; return; }       // S3[a]
-  ent -= p;
-  if (ent < r) { *w = 2 + ent; return; }            // S4[t]
-  ent -= r;
-  if (ent < p * r) { *w = 2 + ent % r; *y1 = ent / r; return; }  // S5[a][t]
-  ent -= p * r;
-  if (ent < rp) { *w = 2 + r + ent; return; }       // S6 packed
-  ent -= rp;
-  if (ent < p * (p + 1) / 2) {                      // S7 packed (a, b), b <= a
-    int a = 0;
-    while ((a + 1) * (a + 2) / 2 <= ent) ++a;
-    *w = 1;
-    *y1 = a;
-    *y2 = ent - a * (a + 1) / 2;
-    return;
-  }
-  *w = 2 + r + rp;                                  // S8
-}
-
-// Double-float numbers (hi + lo, two floats): products formed exactly by
-// Dekker's two-product (hi = fl(a b), lo = fma(a, b, -hi) is the exact rest),
-// cross terms of a double-float product in single precision (their own error
-// is of order 2^-48 of the product).
-__device__ __forceinline__ float2 two_prod(float a, float b) {
-  const float p = __fmul_rn(a, b);
-  return make_float2(p, __fmaf_rn(a, b, -p));
-}
-__device__ __forceinline__ float2 df_mul(float2 x, float2 y) {
-  const float p = __fmul_rn(x.x, y.x);
-  float e = __fmaf_rn(x.x, y.x, -p);
-  e = __fmaf_rn(x.x, y.y, e);
-  e = __fmaf_rn(x.y, y.x, e);
-  return make_float2(p, e);
-}
-// a + b exactly as an unevaluated pair (Knuth's two-sum)
-__device__ __forceinline__ float2 two_sum(float a, float b) {
-  const float s = __fadd_rn(a, b);
-  const float bp = __fsub_rn(s, a);
-  return make_float2(s, __fadd_rn(__fsub_rn(a, __fsub_rn(s, bp)), __fsub_rn(b, bp)));
-}
-// hi + lo += v.x + v.y (two-sum on the leading parts, the rests added to lo)
-__device__ __forceinline__ void df_acc(float &hi, float &lo, float2 v) {
-  const float s = __fadd_rn(hi, v.x);
-  const float bp = __fsub_rn(s, hi);
-  const float err = __fadd_rn(__fsub_rn(hi, __fsub_rn(s, bp)), __fsub_rn(v.x, bp));
-  hi = s;
-  lo = __fadd_rn(lo, __fadd_rn(err, v.y));
-}
 
 // Single-precision E-step outputs (CFUST_FP32).  Double-precision work costs
 // 64 times single-precision work on this GPU, so the double-precision parts

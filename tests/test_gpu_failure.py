@@ -57,3 +57,26 @@ def test_wait_polls_option_is_validated():
     with binding.Context(lat, precision=binding.CFUST_FP64, test_wait_polls=1 << 20) as ctx:
         got = ctx.cfust_loglik(torch.from_numpy(Y).cuda(), init)
     assert np.isfinite(got)
+
+
+@pytest.mark.parametrize("precision", [binding.CFUST_FP64, binding.CFUST_FP32])
+def test_fused_staging_wait_gives_up_with_etimeout(precision):
+    """The fused E-step + sums kernel stages its components through the same
+    bounded wait: with no polls allowed each CTA lets its copy land and
+    returns, the call reports CFUST_ETIMEOUT, and a normal fused context on
+    the same device then matches the oracle."""
+    torch = _torch()
+    Y, _, truth, init, _, meta = synth.workload("cfust_p3r3g4_n1000000_N2048", n=600)
+    lat = synth.make_lattice(256, meta["r"] + 1, 0)
+    Yd = torch.from_numpy(Y).cuda()
+    with binding.Context(lat, precision=precision, max_iter=2, test_wait_polls=-1, fused=True) as ctx:
+        for call in (lambda: ctx.cfust_loglik(Yd, init), lambda: ctx.cfust_fit(Yd, init)):
+            with pytest.raises(binding.CfustError) as ei:
+                call()
+            assert ei.value.status == -5, str(ei.value)
+    torch.cuda.synchronize()
+    with binding.Context(lat, precision=precision, fused=True) as ctx:
+        got = ctx.cfust_loglik(Yd, init)
+    ref = O.loglik(Y, init, O.lattice_points(lat.n, lat.z, lat.shift))
+    tol = 1e-10 if precision == binding.CFUST_FP64 else 1e-6
+    assert abs(got - ref) <= tol * abs(ref)
