@@ -457,6 +457,8 @@ def large_line(args, steps, warmup):
     clocks = sampler.stop()
     ctx.close()
     pairs = n * g
+    fused = fused_comparison(torch, binding, Yd, init, lat, steps, warmup, flush, float(np.mean(ms)), params,
+                             pairs, peak_fp32_tflops((load_peaks() or {}).get("sm_max_mhz", 2070.0), sm_count()), r)
     step_s = float(np.mean(ms)) / 1e3
     sweep_ms = float(np.mean(kern))
     peaks = load_peaks() or {}
@@ -479,6 +481,7 @@ def large_line(args, steps, warmup):
                    "sample": f"first {rows} of {n} observations x {g} components, E-step, one spawned "
                              f"process per core, {wall:.1f} s wall"},
         "fp32_error_vs_oracle": err,
+        "fused": fused,
         "surrogate": "not applicable: the learned form covers r = 3 and this workload has r = 4",
         "clocks": clocks,
         "gpu_launches": 6 * steps,
@@ -647,7 +650,7 @@ def run_ours(args):
     total_iters = args.warmup + args.steps
 
     ctx = binding.Context(lat, precision=binding.CFUST_FP32, max_iter=total_iters, use_graph=True,
-                          timing=True, stream=stream)
+                          timing=True, stream=stream, fused=args.fused)
     ctx.cfust_fit_begin(Yd, init)
     for _ in range(args.warmup):
         flush.zero_()
@@ -672,7 +675,8 @@ def run_ours(args):
         ev1.synchronize()
         step_ms.append(ev0.elapsed_time(ev1))
         sweep_ms.append(ctx.cfust_last_sweep_ms())
-        mstep_ms.append(ctx.cfust_last_mstep_ms())
+        if not args.fused:
+            mstep_ms.append(ctx.cfust_last_mstep_ms())
     torch.cuda.synchronize()
     if ws > 1:
         torch.distributed.barrier()
@@ -705,7 +709,7 @@ def run_ours(args):
         Ye.copy_(Yh)
         e2e_steps = max(3, min(args.steps, 10))
         ctx2 = binding.Context(lat, precision=binding.CFUST_FP32, max_iter=2 + e2e_steps, use_graph=True,
-                               stream=stream)
+                               stream=stream, fused=args.fused)
         ctx2.cfust_fit_begin(Ye, init)
         for _ in range(2):
             Ye.copy_(Yh, non_blocking=True)
@@ -743,8 +747,8 @@ def run_ours(args):
         "rescued_pairs_last_estep": rescued,
         "loglik_first_last": [float(trace[0]), float(trace[-1])],
         "gpu_launches": 6 * args.steps,
-        "roofline": {"bound": "alu", "kernel": "estep_kernel<float,4>", "achieved": achieved,
-                     "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak, "traffic": sweep_traffic_bytes(),
+        "roofline": {"bound": "alu", "kernel": "fused_em_kernel<float,4>" if args.fused else "estep_kernel<float,4>",
+                     "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak, "traffic": sweep_traffic_bytes(),
                      "peak_source": f"FP32 FMA peak {sms} SMs x 128 lanes x 2 x {sm_max:.0f} MHz "
                                     "(derived from unit counts and the maximum SM clock)",
                      "sweep_ms_mean": mean_sweep_ms,
@@ -764,7 +768,11 @@ def run_ours(args):
         # outputs read once (log f, e1, e2, e3, e4 in float) + Y once (double)
         # + the per-block partial sums written once; the kernel is bound by
         # its double-precision-accurate arithmetic, not by these bytes
-        "mstep": mstep_roofline(n, g, p, r, float(np.mean(mstep_ms)), peaks, sms),
+        "mstep": mstep_roofline(n, g, p, r, float(np.mean(mstep_ms)), peaks, sms) if mstep_ms else None,
+        # the fused E-step + M-step-sums pass on the same fit
+        "fused": fused_comparison(torch, binding, Yd, init, lat, args.steps, args.warmup, flush,
+                                  total_ms / args.steps, params, pairs_per_step, peak, r)
+        if ws == 1 and not args.fused and not args.no_extras else None,
         "clocks": clocks,
         "e2e": e2e,
     }
@@ -888,6 +896,56 @@ def _timed_first_iteration(torch, ctx, Yd, P, reps, flush):
             kern.append(ctx.cfust_last_sweep_ms())
         ctx.cfust_fit_end()
     return ms, kern
+
+
+def _fit_memory(torch, binding, Yd, P, lat, fused):
+    """Device memory a single-precision fit context takes for this problem
+    (free memory before and after cfust_fit_begin)."""
+    torch.cuda.synchronize()
+    ctx = binding.Context(lat, precision=binding.CFUST_FP32, max_iter=1, use_graph=False, fused=fused)
+    free0 = torch.cuda.mem_get_info()[0]
+    ctx.cfust_fit_begin(Yd, P)
+    torch.cuda.synchronize()
+    held = free0 - torch.cuda.mem_get_info()[0]
+    ctx.close()
+    return int(held)
+
+
+def fused_comparison(torch, binding, Yd, P, lat, steps, warmup, flush, unfused_ms, unfused_params, pairs, peak, r):
+    """The fused E-step + M-step-sums pass (one kernel per iteration, per-pair
+    outputs in shared memory only) on the same fit as the unfused line: time
+    per EM iteration, the fused kernel against the FP32 peak (the same
+    454-flop-per-point count: the sums are O(1) per observation), the device
+    memory each form's fit holds, and how far the two fits differ after the
+    same iterations from the same start (summation order only)."""
+    ctx = binding.Context(lat, precision=binding.CFUST_FP32, max_iter=warmup + steps + 1, use_graph=True,
+                          timing=True, fused=True)
+    ms, kern, params = _timed_em(torch, ctx, Yd, P, steps, warmup, flush)
+    ctx.close()
+    step_ms = float(np.mean(ms))
+    kern_ms = float(np.mean(kern))
+    flops = pairs * lat.n * sweep_flops_per_point(r)
+    achieved = flops / (kern_ms / 1e3) / 1e12
+    diffs = []
+    for a, b in zip(params.as_arrays(), unfused_params.as_arrays()):
+        a = np.asarray(a, dtype=np.float64)
+        b = np.asarray(b, dtype=np.float64)
+        fin = np.isfinite(b)
+        if fin.any():
+            scale = max(float(np.max(np.abs(b[fin]))), 1e-300)
+            diffs.append(float(np.max(np.abs(a[fin] - b[fin]))) / scale)
+    return {
+        "ms_per_step": step_ms, "value": pairs / (step_ms / 1e3), "unit": UNIT,
+        "em_iters_per_s": 1e3 / step_ms, "unfused_ms_per_step": unfused_ms,
+        "speed_vs_unfused": unfused_ms / step_ms,
+        "kernel": "fused_em_kernel<float,%d>" % r, "kernel_ms_mean": kern_ms,
+        "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak},
+        "fit_device_bytes": {"fused": _fit_memory(torch, binding, Yd, P, lat, True),
+                             "unfused": _fit_memory(torch, binding, Yd, P, lat, False)},
+        "params_max_rel_diff_vs_unfused": max(diffs) if diffs else None,
+        "step": "one EM iteration (CUDA graph replay): precompute, the fused kernel, log-likelihood "
+                "reduction, M-step finalize",
+    }
 
 
 def _timed_em(torch, ctx, Yd, P, steps, warmup, flush, fallback=None):
@@ -1133,6 +1191,8 @@ def main(argv=None):
                     help="triage margin T (nats) of the surrogate and plain contexts: a listed or rescued "
                          "pair with tau provably below exp(-T) is dropped, moving l by at most exp(-T)")
     ap.add_argument("--nfits", type=int, default=256)
+    ap.add_argument("--fused", action="store_true",
+                    help="time the default workload with the fused E-step + M-step-sums kernel (cfust_opts.fused)")
     ap.add_argument("--rows", type=int, default=0,
                     help="observations of the single-fit workload (0: the workload's 100000); for small "
                          "profiling captures only, the bench line is quoted at the default")
