@@ -242,72 +242,6 @@ __device__ __forceinline__ double fused_lse(T *lf, int g, int tj, int jj, const 
 // Single precision: tau times the weight as an exact product (two-product),
 // times y's float pairs (double-float), two compensated chains merged by a
 // two-sum; double: the posterior kernel's four interleaved chains.
-struct TileCols {
-  int kind;  // 0: tau; 1: tau col; 2: tau (col - col1)
-  const void *col, *col1;
-  int y1, y2;
-};
-
-template <typename T>
-__device__ __forceinline__ TileCols tile_cols(const T *out, int g, int tj, int p, int r, int K, int e) {
-  const int rp = r * (r + 1) / 2;
-  const int i = e / K;
-  int w, y1, y2;
-  entry_desc(e % K, p, r, &w, &y1, &y2);
-  const T *e1 = out + (size_t)g * tj, *e2 = out + (size_t)2 * g * tj, *e3 = out + (size_t)3 * g * tj;
-  const T *e4 = e3 + (size_t)g * r * tj;
-  TileCols c;
-  c.y1 = y1;
-  c.y2 = y2;
-  c.col1 = nullptr;
-  c.col = nullptr;
-  if (w == 0) {
-    c.kind = 0;
-  } else if (w == 1) {
-    c.kind = 1;
-    c.col = e1 + (size_t)i * tj;
-  } else if (w < 2 + r) {
-    c.kind = 1;
-    c.col = e3 + ((size_t)i * r + (w - 2)) * tj;
-  } else if (w < 2 + r + rp) {
-    c.kind = 1;
-    c.col = e4 + ((size_t)i * rp + (w - 2 - r)) * tj;
-  } else {
-    c.kind = 2;
-    c.col = e2 + (size_t)i * tj;
-    c.col1 = e1 + (size_t)i * tj;
-  }
-  return c;
-}
-
-__device__ __forceinline__ float2 tile_term_f32(const TileCols &c, float t, int jj, const float2 *ys, int p) {
-  float2 v;
-  if (c.kind == 0) {
-    v = make_float2(t, 0.0f);
-  } else if (c.kind == 1) {
-    v = two_prod(t, reinterpret_cast<const float *>(c.col)[jj]);
-  } else {
-    // e2 - e1 as an exact float pair (two-sum), then times tau
-    const float v2 = reinterpret_cast<const float *>(c.col)[jj];
-    const float v1 = reinterpret_cast<const float *>(c.col1)[jj];
-    const float d = __fsub_rn(v2, v1);
-    const float bp = __fsub_rn(d, v2);
-    const float dlo = __fadd_rn(__fsub_rn(v2, __fsub_rn(d, bp)), __fsub_rn(-v1, bp));
-    v = two_prod(t, d);
-    v.y = __fmaf_rn(t, dlo, v.y);
-  }
-  if (c.y1 >= 0) v = df_mul(v, ys[jj * p + c.y1]);
-  if (c.y2 >= 0) v = df_mul(v, ys[jj * p + c.y2]);
-  return v;
-}
-
-__device__ __forceinline__ double tile_term_f64(const TileCols &c, double t, int jj) {
-  if (c.kind == 0) return t;
-  const double *col = reinterpret_cast<const double *>(c.col);
-  if (c.kind == 1) return t * col[jj];
-  return t * (col[jj] - reinterpret_cast<const double *>(c.col1)[jj]);
-}
-
 // Adds the tile's sums to the CTA's partial row (`first`: the row starts here).
 template <typename T>
 __device__ __forceinline__ void fused_tile_sums(const T *out, const void *ys_raw, int g, int tj, int p, int r, int K,

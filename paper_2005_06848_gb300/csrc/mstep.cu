@@ -42,47 +42,115 @@ constexpr int THREADS = 256;
 // the exponentials and tau are single precision (tau to ~1e-7 relative, the
 // level of the single-precision log f_ij it comes from), and so is log s_j
 // (s_j in [1, g]: 1e-7 absolute).
+//
+// Each tile's rows (log f of every component or the given tau, e1..e4 of
+// the block's components, y) are staged in shared memory by asynchronous
+// copies issued one tile ahead into the other of two buffers, so the loads of
+// tile t + 1 are in flight while tile t is summed.
+
+__device__ __forceinline__ void cp_async4(void *dst, const void *src) {
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"((unsigned)__cvta_generic_to_shared(dst)),
+               "l"(src)
+               : "memory");
+}
+__device__ __forceinline__ void cp_async8(void *dst, const void *src) {
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"((unsigned)__cvta_generic_to_shared(dst)),
+               "l"(src)
+               : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_prev() { asm volatile("cp.async.wait_group 1;" ::: "memory"); }
+
+// One staging buffer of the single-precision kernel, in floats: tau rows of
+// the block's gc components (written from log f, or copied from the given
+// tau), then their e1, e2, e3 (r rows each), e4 (r(r+1)/2 rows each), all of
+// TJ values (the row layout tile_cols reads); then log f of all g components
+// when given; then y as TJ x p doubles.  Two buffers, then y's float pairs.
+struct PostTile {
+  int lf, y, size;
+};
+
+__host__ __device__ inline PostTile post_tile(int g, int gc, int p, int r, bool sums, bool have_lf) {
+  const int rp = r * (r + 1) / 2;
+  PostTile t;
+  int off = gc * TJ;
+  if (sums) off += gc * TJ * (2 + r + rp);
+  t.lf = off;
+  if (have_lf) off += g * TJ;
+  off = (off + 1) & ~1;
+  t.y = off;
+  if (sums) off += TJ * p * 2;
+  t.size = (off + 3) & ~3;
+  return t;
+}
+
+__host__ __device__ inline size_t post_smem_f32(int g, int gc, int p, int r, bool sums, bool have_lf) {
+  return (size_t)2 * post_tile(g, gc, p, r, sums, have_lf).size * 4 + (sums ? (size_t)TJ * p * 8 : 0);
+}
+
+// Issues the asynchronous copies of tile [j0, j0 + nt) into `buf`.
+__device__ __forceinline__ void post_issue(const PosteriorArgs &a, int c0, int gc, int64_t j0, int nt, float *buf,
+                                           const PostTile &L) {
+  const int g = a.g, p = a.p, r = a.r, rp = r * (r + 1) / 2;
+  const int64_t n = a.n;
+  if (a.logf != nullptr) {
+    const float *lf = reinterpret_cast<const float *>(a.logf);
+    for (int idx = threadIdx.x; idx < g * nt; idx += THREADS) {
+      const int row = idx / nt, jj = idx - row * nt;
+      cp_async4(buf + L.lf + row * TJ + jj, lf + (int64_t)row * n + j0 + jj);
+    }
+  } else if (a.want_sums) {
+    const float *ti = reinterpret_cast<const float *>(a.tau_in);
+    for (int idx = threadIdx.x; idx < gc * nt; idx += THREADS) {
+      const int row = idx / nt, jj = idx - row * nt;
+      cp_async4(buf + row * TJ + jj, ti + (int64_t)(c0 + row) * n + j0 + jj);
+    }
+  }
+  if (!a.want_sums) return;
+  const float *e1 = reinterpret_cast<const float *>(a.e1), *e2 = reinterpret_cast<const float *>(a.e2);
+  const float *e3 = reinterpret_cast<const float *>(a.e3), *e4 = reinterpret_cast<const float *>(a.e4);
+  const int nr = gc * (2 + r + rp);
+  for (int idx = threadIdx.x; idx < nr * nt; idx += THREADS) {
+    const int row = idx / nt, jj = idx - row * nt;
+    const float *src;
+    if (row < gc)
+      src = e1 + (int64_t)(c0 + row) * n;
+    else if (row < 2 * gc)
+      src = e2 + (int64_t)(c0 + row - gc) * n;
+    else if (row < 2 * gc + gc * r)
+      src = e3 + (int64_t)(c0 * r + row - 2 * gc) * n;
+    else
+      src = e4 + (int64_t)(c0 * rp + row - 2 * gc - gc * r) * n;
+    cp_async4(buf + (gc + row) * TJ + jj, src + j0 + jj);
+  }
+  const double *yt = a.Y + j0 * a.p;
+  for (int idx = threadIdx.x; idx < nt * p; idx += THREADS) cp_async8(buf + L.y + 2 * idx, yt + idx);
+}
+
 __device__ __forceinline__ void posterior_block_f32(const PosteriorArgs &a, int c0, int c1, int blk, int nblk,
                                                     unsigned char *smem_raw) {
   const int p = a.p, r = a.r, g = a.g;
-  const int rp = r * (r + 1) / 2;
   const int K = sums_width(p, r);
-  const int WR = 3 + r + rp;
   const int gc = c1 - c0;
   const int64_t n = a.n;
-  float2 *ys = reinterpret_cast<float2 *>(smem_raw);  // [TJ][p] (hi, lo) of y
-  float2 *ws = ys + TJ * p;                           // [gc][TJ][WR] exact products
+  const bool have_lf = a.logf != nullptr;
+  const PostTile L = post_tile(g, gc, p, r, a.want_sums, have_lf);
+  float *bufs = reinterpret_cast<float *>(smem_raw);
+  float2 *ys = reinterpret_cast<float2 *>(bufs + 2 * L.size);  // [TJ][p] (hi, lo) of y
   __shared__ double red[THREADS];
-
-  const float *lfp = reinterpret_cast<const float *>(a.logf);
-  const float *tau_in = reinterpret_cast<const float *>(a.tau_in);
-  const float *e1 = reinterpret_cast<const float *>(a.e1);
-  const float *e2 = reinterpret_cast<const float *>(a.e2);
-  const float *e3 = reinterpret_cast<const float *>(a.e3);
-  const float *e4 = reinterpret_cast<const float *>(a.e4);
   float *tau_out = reinterpret_cast<float *>(a.tau_out);
 
-  int own_w[MAXOWN], own_y1[MAXOWN], own_y2[MAXOWN], own_c[MAXOWN];
   double acc[MAXOWN];
+#pragma unroll
+  for (int k = 0; k < MAXOWN; ++k) acc[k] = 0.0;
   const int E = a.want_sums ? gc * K : 0;
   // With few sum entries (a small mixture), S adjacent threads share one
   // entry: each sums every S-th row of the tile, and the S partial sums are
   // merged by shuffles in a fixed order, so more of the block's threads work
-  // on the tile's column sums.  S = 1 keeps one entry per thread.
+  // on the tile's column sums.  S = 1 keeps one entry per thread and step.
   const int S = (E > 0 && 4 * E <= THREADS) ? 4 : ((E > 0 && 2 * E <= THREADS) ? 2 : 1);
   const int split = threadIdx.x % S;
-#pragma unroll
-  for (int k = 0; k < MAXOWN; ++k) {
-    const int e = (S > 1) ? (k == 0 ? (int)threadIdx.x / S : E) : (int)threadIdx.x + k * THREADS;
-    acc[k] = 0.0;
-    own_c[k] = -1;
-    own_w[k] = 0;
-    own_y1[k] = own_y2[k] = -1;
-    if (e < E) {
-      own_c[k] = e / K;
-      entry_desc(e % K, p, r, &own_w[k], &own_y1[k], &own_y2[k]);
-    }
-  }
+  const int per = THREADS / S;
   double llacc = 0.0;
   int bad = 0;
   const int64_t ntiles = (n + TJ - 1) / TJ;
@@ -96,146 +164,117 @@ __device__ __forceinline__ void posterior_block_f32(const PosteriorArgs &a, int 
     const float hi = (float)l;
     lpi2[i] = make_float2(hi, (float)(l - (double)hi));
   }
-  __syncthreads();
+  if (blk < ntiles) {
+    const int64_t j0 = (int64_t)blk * TJ;
+    post_issue(a, c0, gc, j0, (int)((n - j0) < TJ ? (n - j0) : TJ), bufs, L);
+  }
+  cp_async_commit();
 
-  for (int64_t tile = blk; tile < ntiles; tile += nblk) {
+  int it = 0;
+  for (int64_t tile = blk; tile < ntiles; tile += nblk, ++it) {
     const int64_t j0 = tile * TJ;
     const int nt = (int)((n - j0) < TJ ? (n - j0) : TJ);
-    if (a.want_sums)
-      for (int idx = threadIdx.x; idx < nt * p; idx += THREADS) {
-        const double y = a.Y[j0 * p + idx];
-        const float yh = (float)y;
-        ys[idx] = make_float2(yh, (float)(y - (double)yh));
-      }
-    if (threadIdx.x < nt) {
+    float *buf = bufs + (it & 1) * L.size;
+    const int64_t next = tile + nblk;
+    if (next < ntiles) {
+      const int64_t jn = next * TJ;
+      post_issue(a, c0, gc, jn, (int)((n - jn) < TJ ? (n - jn) : TJ), bufs + ((it + 1) & 1) * L.size, L);
+    }
+    cp_async_commit();
+    cp_async_wait_prev();  // this thread's copies of the current tile have landed
+    __syncthreads();       // and everyone's
+    if (have_lf && (int)threadIdx.x < nt) {
       const int jj = threadIdx.x;
       const int64_t j = j0 + jj;
-      if (lfp != nullptr) {
-        // a_i = log pi_i + log f_ij as a float pair (exact sum of the float
-        // log f and the pair of log pi); the shift is the largest a_i
-        float2 mx = make_float2(-INFINITY, 0.0f);
+      const float *lf = buf + L.lf;
+      // a_i = log pi_i + log f_ij as a float pair (exact sum of the float
+      // log f and the pair of log pi); the shift is the largest a_i
+      float2 mx = make_float2(-INFINITY, 0.0f);
+      for (int i = 0; i < g; ++i) {
+        float2 ai = two_sum(lpi2[i].x, lf[i * TJ + jj]);
+        ai.y = __fadd_rn(ai.y, lpi2[i].y);
+        if (ai.x > mx.x || (ai.x == mx.x && ai.y > mx.y)) mx = ai;
+      }
+      if (!isfinite(mx.x)) {
+        // no component gives the observation a positive density: flagged,
+        // and its weights are zero so that the sums stay defined
+        bad = 1;
+        if (a.want_sums)
+          for (int i = c0; i < c1; ++i) buf[(i - c0) * TJ + jj] = 0.0f;
+        if (tau_out != nullptr && first_chunk)
+          for (int i = 0; i < g; ++i) tau_out[(int64_t)i * n + j] = 0.0f;
+      } else {
+        float s = 0.0f;
         for (int i = 0; i < g; ++i) {
-          const float lf = lfp[(int64_t)i * n + j];
-          float2 ai = two_sum(lpi2[i].x, lf);
+          float2 ai = two_sum(lpi2[i].x, lf[i * TJ + jj]);
           ai.y = __fadd_rn(ai.y, lpi2[i].y);
-          if (ai.x > mx.x || (ai.x == mx.x && ai.y > mx.y)) mx = ai;
+          // the exponent a_i - max (exact leading difference where the two
+          // are within a factor two, else rounded: 2^-24 of an exponent
+          // whose exponential is then below e^-1 of the largest)
+          const float dx = __fadd_rn(__fsub_rn(ai.x, mx.x), __fsub_rn(ai.y, mx.y));
+          s = __fadd_rn(s, (ai.x == -INFINITY) ? 0.0f : expf(dx));
         }
-        if (!isfinite(mx.x)) {
-          // no component gives the observation a positive density: flagged,
-          // and its weights are zero so that the sums stay defined
-          bad = 1;
-          if (a.want_sums)
-            for (int i = c0; i < c1; ++i) ws[((i - c0) * TJ + jj) * WR] = make_float2(0.0f, 0.0f);
-          if (tau_out != nullptr && first_chunk)
-            for (int i = 0; i < g; ++i) tau_out[(int64_t)i * n + j] = 0.0f;
-        } else {
-          float s = 0.0f;
-          for (int i = 0; i < g; ++i) {
-            const float lf = lfp[(int64_t)i * n + j];
-            float2 ai = two_sum(lpi2[i].x, lf);
-            ai.y = __fadd_rn(ai.y, lpi2[i].y);
-            // the exponent a_i - max (exact leading difference where the two
-            // are within a factor two, else rounded: 2^-24 of an exponent
-            // whose exponential is then below e^-1 of the largest)
-            const float dx = __fadd_rn(__fsub_rn(ai.x, mx.x), __fsub_rn(ai.y, mx.y));
-            const float ex = (ai.x == -INFINITY) ? 0.0f : expf(dx);
-            s = __fadd_rn(s, ex);
-            if (a.want_sums && i >= c0 && i < c1) ws[((i - c0) * TJ + jj) * WR] = make_float2(ex, 0.0f);
-            if (tau_out != nullptr && first_chunk) tau_out[(int64_t)i * n + j] = ex;
-          }
-          // s is in [1, g]: its single-precision logarithm is good to 1e-7
-          // absolute, below the error of the log f_ij it sums; l_j in double
-          const double lse = (double)mx.x + (double)mx.y + (double)logf(s);
-          if (!isfinite(lse)) bad = 1;
-          llacc += lse;
-          const float inv = 1.0f / s;
-          if (a.want_sums)
-            for (int i = c0; i < c1; ++i) ws[((i - c0) * TJ + jj) * WR].x *= inv;
-          if (tau_out != nullptr && first_chunk)
-            for (int i = 0; i < g; ++i) tau_out[(int64_t)i * n + j] *= inv;
+        // s is in [1, g]: its single-precision logarithm is good to 1e-7
+        // absolute, below the error of the log f_ij it sums; l_j in double
+        const double lse = (double)mx.x + (double)mx.y + (double)logf(s);
+        if (!isfinite(lse)) bad = 1;
+        llacc += lse;
+        const float inv = 1.0f / s;
+        for (int i = 0; i < g; ++i) {
+          float2 ai = two_sum(lpi2[i].x, lf[i * TJ + jj]);
+          ai.y = __fadd_rn(ai.y, lpi2[i].y);
+          const float dx = __fadd_rn(__fsub_rn(ai.x, mx.x), __fsub_rn(ai.y, mx.y));
+          const float t = ((ai.x == -INFINITY) ? 0.0f : expf(dx)) * inv;
+          if (a.want_sums && i >= c0 && i < c1) buf[(i - c0) * TJ + jj] = t;
+          if (tau_out != nullptr && first_chunk) tau_out[(int64_t)i * n + j] = t;
         }
-      } else if (a.want_sums) {
-        for (int i = c0; i < c1; ++i) ws[((i - c0) * TJ + jj) * WR] = make_float2(tau_in[(int64_t)i * n + j], 0.0f);
       }
     }
-    __syncthreads();
     if (a.want_sums) {
-      for (int idx = threadIdx.x; idx < gc * nt; idx += THREADS) {
-        const int ic = idx / nt, jj = idx % nt;
-        const int i = c0 + ic;
-        const int64_t j = j0 + jj;
-        float2 *row = ws + (ic * TJ + jj) * WR;
-        const float t = row[0].x;
-        const float v1 = e1[(int64_t)i * n + j];
-        row[1] = two_prod(t, v1);
-        for (int q = 0; q < r; ++q) row[2 + q] = two_prod(t, e3[((int64_t)i * r + q) * n + j]);
-        for (int q = 0; q < rp; ++q) row[2 + r + q] = two_prod(t, e4[((int64_t)i * rp + q) * n + j]);
-        // e2 - e1 as an exact float pair (two-sum), then times tau
-        const float v2 = e2[(int64_t)i * n + j];
-        const float d = __fsub_rn(v2, v1);
-        const float bp = __fsub_rn(d, v2);
-        const float dlo = __fadd_rn(__fsub_rn(v2, __fsub_rn(d, bp)), __fsub_rn(-v1, bp));
-        float2 pd = two_prod(t, d);
-        pd.y = __fmaf_rn(t, dlo, pd.y);
-        row[2 + r + rp] = pd;
+      const double *yb = reinterpret_cast<const double *>(buf + L.y);
+      for (int idx = threadIdx.x; idx < nt * p; idx += THREADS) {
+        const double y = yb[idx];
+        const float yh = (float)y;
+        ys[idx] = make_float2(yh, (float)(y - (double)yh));
       }
       __syncthreads();
 #pragma unroll
       for (int k = 0; k < MAXOWN; ++k) {
+        const int e0 = k * per;
+        if (e0 >= E) continue;  // uniform over the block
+        const int e = e0 + (int)threadIdx.x / S;
         // two compensated chains (rows jj and jj + S) for instruction-level
         // parallelism, merged by a further two-sum; this thread's rows are
         // split, split + S, ...
         float h0 = 0.0f, l0 = 0.0f, h1 = 0.0f, l1 = 0.0f;
-        if (own_c[k] >= 0) {
-          const float2 *col = ws + own_c[k] * TJ * WR + own_w[k];
-          const int y1 = own_y1[k], y2 = own_y2[k];
+        if (e < E) {
+          const TileCols c = tile_cols<float>(buf, gc, TJ, p, r, K, e);
+          const float *ti = buf + (e / K) * TJ;
           int jj = split;
-          if (y1 < 0) {
-            for (; jj + S < nt; jj += 2 * S) {
-              df_acc(h0, l0, col[jj * WR]);
-              df_acc(h1, l1, col[(jj + S) * WR]);
-            }
-            if (jj < nt) df_acc(h0, l0, col[jj * WR]);
-          } else if (y2 < 0) {
-            for (; jj + S < nt; jj += 2 * S) {
-              df_acc(h0, l0, df_mul(col[jj * WR], ys[jj * p + y1]));
-              df_acc(h1, l1, df_mul(col[(jj + S) * WR], ys[(jj + S) * p + y1]));
-            }
-            if (jj < nt) df_acc(h0, l0, df_mul(col[jj * WR], ys[jj * p + y1]));
-          } else {
-            for (; jj + S < nt; jj += 2 * S) {
-              df_acc(h0, l0, df_mul(df_mul(col[jj * WR], ys[jj * p + y1]), ys[jj * p + y2]));
-              df_acc(h1, l1, df_mul(df_mul(col[(jj + S) * WR], ys[(jj + S) * p + y1]), ys[(jj + S) * p + y2]));
-            }
-            if (jj < nt) df_acc(h0, l0, df_mul(df_mul(col[jj * WR], ys[jj * p + y1]), ys[jj * p + y2]));
+          for (; jj + S < nt; jj += 2 * S) {
+            df_acc(h0, l0, tile_term_f32(c, ti[jj], jj, ys, p));
+            df_acc(h1, l1, tile_term_f32(c, ti[jj + S], jj + S, ys, p));
           }
+          if (jj < nt) df_acc(h0, l0, tile_term_f32(c, ti[jj], jj, ys, p));
           df_acc(h0, l0, make_float2(h1, l1));
         }
-        if (S > 1 && k == 0) {
-          // the entry's S partial sums, from adjacent lanes, in a fixed order
-          for (int o = 1; o < S; o <<= 1) {
-            const float h2 = __shfl_xor_sync(0xffffffffu, h0, o), l2 = __shfl_xor_sync(0xffffffffu, l0, o);
-            df_acc(h0, l0, make_float2(h2, l2));
-          }
+        // the entry's S partial sums, from adjacent lanes, in a fixed order
+        for (int o = 1; o < S; o <<= 1) {
+          const float h2 = __shfl_xor_sync(0xffffffffu, h0, o), l2 = __shfl_xor_sync(0xffffffffu, l0, o);
+          df_acc(h0, l0, make_float2(h2, l2));
         }
-        if (own_c[k] >= 0 && split == 0) acc[k] += (double)h0 + (double)l0;
+        if (e < E && split == 0) acc[k] += (double)h0 + (double)l0;
       }
     }
-    __syncthreads();
+    __syncthreads();  // this buffer is refilled two tiles on
   }
 
   if (a.want_sums) {
     double *dst = a.partials + (int64_t)blk * g * K;
-    if (S > 1) {
-      // the first thread of each group of S holds its entry's total
-      const int e = (int)threadIdx.x / S;
-      if (split == 0 && e < E) dst[(int64_t)c0 * K + e] = acc[0];
-    } else {
 #pragma unroll
-      for (int k = 0; k < MAXOWN; ++k) {
-        const int e = threadIdx.x + k * THREADS;
-        if (e < E) dst[(int64_t)c0 * K + e] = acc[k];
-      }
+    for (int k = 0; k < MAXOWN; ++k) {
+      const int e = k * per + (int)threadIdx.x / S;
+      if (k * per < E && e < E && split == 0) dst[(int64_t)c0 * K + e] = acc[k];
     }
   }
   if (a.want_ll && first_chunk) {
@@ -710,7 +749,11 @@ cudaError_t launch_posterior_batched(int precision, const BatchDev &b, int p, in
   const int WR = 3 + r + r * (r + 1) / 2;
   const int K = sums_width(p, r);
   if (want_sums && g_max * K > MAXOWN * THREADS) return cudaErrorInvalidValue;
-  const size_t smem = want_sums ? ((size_t)TJ * p + (size_t)g_max * TJ * WR) * 8 : 16;
+  // every fit's block takes all its components in one pass (the log f rows of
+  // all of them are staged in single precision): sized for the largest g
+  const size_t smem = precision == CFUST_FP64
+                          ? (want_sums ? ((size_t)TJ * p + (size_t)g_max * TJ * WR) * 8 : 16)
+                          : post_smem_f32(g_max, g_max, p, r, want_sums, true);
   if (smem > 200 * 1024) return cudaErrorInvalidValue;
   cudaError_t e;
   if (precision == CFUST_FP64) {
@@ -751,25 +794,32 @@ int posterior_nblocks(int64_t n) {
 cudaError_t launch_posterior(int precision, const PosteriorArgs &a, cudaStream_t st) {
   const int K = sums_width(a.p, a.r);
   const int WR = 3 + a.r + a.r * (a.r + 1) / 2;
+  const bool f32 = precision != CFUST_FP64;
+  const bool have_lf = a.logf != nullptr;
   // components per launch: bounded by the per-thread entries and by shared memory
   int gc = a.g;
   if (a.want_sums) {
     const int by_entries = (MAXOWN * THREADS) / K;
-    const int by_smem = (int)((96 * 1024 - (size_t)TJ * a.p * 8) / ((size_t)TJ * WR * 8));
     gc = a.g < by_entries ? a.g : by_entries;
-    gc = gc < by_smem ? gc : by_smem;
+    if (f32) {
+      while (gc > 1 && post_smem_f32(a.g, gc, a.p, a.r, true, have_lf) > 200u * 1024u) --gc;
+    } else {
+      const int by_smem = (int)((96 * 1024 - (size_t)TJ * a.p * 8) / ((size_t)TJ * WR * 8));
+      gc = gc < by_smem ? gc : by_smem;
+    }
     if (gc < 1) return cudaErrorInvalidValue;
   }
   for (int c0 = 0; c0 < a.g; c0 += gc) {
     const int c1 = (c0 + gc < a.g) ? c0 + gc : a.g;
-    const size_t smem = a.want_sums ? ((size_t)TJ * a.p + (size_t)(c1 - c0) * TJ * WR) * 8 : 16;
     cudaError_t e;
-    if (precision == CFUST_FP64) {
-      e = raise_smem_limit((const void *)posterior_kernel<double>, (size_t)((int)smem));
+    if (!f32) {
+      const size_t smem = a.want_sums ? ((size_t)TJ * a.p + (size_t)(c1 - c0) * TJ * WR) * 8 : 16;
+      e = raise_smem_limit((const void *)posterior_kernel<double>, smem);
       if (e != cudaSuccess) return e;
       posterior_kernel<double><<<a.nblocks, THREADS, smem, st>>>(a, c0, c1);
     } else {
-      e = raise_smem_limit((const void *)posterior_kernel<float>, (size_t)((int)smem));
+      const size_t smem = post_smem_f32(a.g, c1 - c0, a.p, a.r, a.want_sums, have_lf);
+      e = raise_smem_limit((const void *)posterior_kernel<float>, smem);
       if (e != cudaSuccess) return e;
       posterior_kernel<float><<<a.nblocks, THREADS, smem, st>>>(a, c0, c1);
     }
