@@ -64,8 +64,12 @@ __device__ __forceinline__ void cp_async_wait_prev() { asm volatile("cp.async.wa
 // One staging buffer of the single-precision kernel, in floats: tau rows of
 // the block's gc components (written from log f, or copied from the given
 // tau), then their e1, e2, e3 (r rows each), e4 (r(r+1)/2 rows each), all of
-// TJ values (the row layout tile_cols reads); then log f of all g components
-// when given; then y as TJ x p doubles.  Two buffers, then y's float pairs.
+// TJP values (the row layout tile_cols reads; TJP = TJ + 1 so that the lanes
+// of a warp reading one observation of different rows hit different banks);
+// then log f of all g components when given; then y as TJ x p doubles.  Two
+// buffers, then y's float pairs.
+constexpr int TJP = TJ + 1;
+
 struct PostTile {
   int lf, y, size;
 };
@@ -73,10 +77,10 @@ struct PostTile {
 __host__ __device__ inline PostTile post_tile(int g, int gc, int p, int r, bool sums, bool have_lf) {
   const int rp = r * (r + 1) / 2;
   PostTile t;
-  int off = gc * TJ;
-  if (sums) off += gc * TJ * (2 + r + rp);
+  int off = gc * TJP;
+  if (sums) off += gc * TJP * (2 + r + rp);
   t.lf = off;
-  if (have_lf) off += g * TJ;
+  if (have_lf) off += g * TJP;
   off = (off + 1) & ~1;
   t.y = off;
   if (sums) off += TJ * p * 2;
@@ -97,13 +101,13 @@ __device__ __forceinline__ void post_issue(const PosteriorArgs &a, int c0, int g
     const float *lf = reinterpret_cast<const float *>(a.logf);
     for (int idx = threadIdx.x; idx < g * nt; idx += THREADS) {
       const int row = idx / nt, jj = idx - row * nt;
-      cp_async4(buf + L.lf + row * TJ + jj, lf + (int64_t)row * n + j0 + jj);
+      cp_async4(buf + L.lf + row * TJP + jj, lf + (int64_t)row * n + j0 + jj);
     }
   } else if (a.want_sums) {
     const float *ti = reinterpret_cast<const float *>(a.tau_in);
     for (int idx = threadIdx.x; idx < gc * nt; idx += THREADS) {
       const int row = idx / nt, jj = idx - row * nt;
-      cp_async4(buf + row * TJ + jj, ti + (int64_t)(c0 + row) * n + j0 + jj);
+      cp_async4(buf + row * TJP + jj, ti + (int64_t)(c0 + row) * n + j0 + jj);
     }
   }
   if (!a.want_sums) return;
@@ -121,7 +125,7 @@ __device__ __forceinline__ void post_issue(const PosteriorArgs &a, int c0, int g
       src = e3 + (int64_t)(c0 * r + row - 2 * gc) * n;
     else
       src = e4 + (int64_t)(c0 * rp + row - 2 * gc - gc * r) * n;
-    cp_async4(buf + (gc + row) * TJ + jj, src + j0 + jj);
+    cp_async4(buf + (gc + row) * TJP + jj, src + j0 + jj);
   }
   const double *yt = a.Y + j0 * a.p;
   for (int idx = threadIdx.x; idx < nt * p; idx += THREADS) cp_async8(buf + L.y + 2 * idx, yt + idx);
@@ -191,7 +195,7 @@ __device__ __forceinline__ void posterior_block_f32(const PosteriorArgs &a, int 
       // log f and the pair of log pi); the shift is the largest a_i
       float2 mx = make_float2(-INFINITY, 0.0f);
       for (int i = 0; i < g; ++i) {
-        float2 ai = two_sum(lpi2[i].x, lf[i * TJ + jj]);
+        float2 ai = two_sum(lpi2[i].x, lf[i * TJP + jj]);
         ai.y = __fadd_rn(ai.y, lpi2[i].y);
         if (ai.x > mx.x || (ai.x == mx.x && ai.y > mx.y)) mx = ai;
       }
@@ -200,13 +204,13 @@ __device__ __forceinline__ void posterior_block_f32(const PosteriorArgs &a, int 
         // and its weights are zero so that the sums stay defined
         bad = 1;
         if (a.want_sums)
-          for (int i = c0; i < c1; ++i) buf[(i - c0) * TJ + jj] = 0.0f;
+          for (int i = c0; i < c1; ++i) buf[(i - c0) * TJP + jj] = 0.0f;
         if (tau_out != nullptr && first_chunk)
           for (int i = 0; i < g; ++i) tau_out[(int64_t)i * n + j] = 0.0f;
       } else {
         float s = 0.0f;
         for (int i = 0; i < g; ++i) {
-          float2 ai = two_sum(lpi2[i].x, lf[i * TJ + jj]);
+          float2 ai = two_sum(lpi2[i].x, lf[i * TJP + jj]);
           ai.y = __fadd_rn(ai.y, lpi2[i].y);
           // the exponent a_i - max (exact leading difference where the two
           // are within a factor two, else rounded: 2^-24 of an exponent
@@ -221,11 +225,11 @@ __device__ __forceinline__ void posterior_block_f32(const PosteriorArgs &a, int 
         llacc += lse;
         const float inv = 1.0f / s;
         for (int i = 0; i < g; ++i) {
-          float2 ai = two_sum(lpi2[i].x, lf[i * TJ + jj]);
+          float2 ai = two_sum(lpi2[i].x, lf[i * TJP + jj]);
           ai.y = __fadd_rn(ai.y, lpi2[i].y);
           const float dx = __fadd_rn(__fsub_rn(ai.x, mx.x), __fsub_rn(ai.y, mx.y));
           const float t = ((ai.x == -INFINITY) ? 0.0f : expf(dx)) * inv;
-          if (a.want_sums && i >= c0 && i < c1) buf[(i - c0) * TJ + jj] = t;
+          if (a.want_sums && i >= c0 && i < c1) buf[(i - c0) * TJP + jj] = t;
           if (tau_out != nullptr && first_chunk) tau_out[(int64_t)i * n + j] = t;
         }
       }
@@ -248,8 +252,8 @@ __device__ __forceinline__ void posterior_block_f32(const PosteriorArgs &a, int 
         // split, split + S, ...
         float h0 = 0.0f, l0 = 0.0f, h1 = 0.0f, l1 = 0.0f;
         if (e < E) {
-          const TileCols c = tile_cols<float>(buf, gc, TJ, p, r, K, e);
-          const float *ti = buf + (e / K) * TJ;
+          const TileCols c = tile_cols<float>(buf, gc, TJP, p, r, K, e);
+          const float *ti = buf + (e / K) * TJP;
           int jj = split;
           for (; jj + S < nt; jj += 2 * S) {
             df_acc(h0, l0, tile_term_f32(c, ti[jj], jj, ys, p));
