@@ -1020,17 +1020,31 @@ __global__ void __launch_bounds__(tcn::WG * 128, 1)
   const int pair = DENS ? c.row : c.row >> 1, pass = DENS ? 0 : (c.row & 1);
   uint32_t phase = 0;
   bool gave_up = false;
-  for (int64_t tile = (int64_t)blockIdx.x * tcn::WG + wg; tile < ntiles; tile += (int64_t)gridDim.x * tcn::WG) {
-    const int i = (int)(tile / tpc);
-    const int64_t j = (tile % tpc) * PPT + pair;
+  // the tile's component i and its place tr among that component's tiles,
+  // advanced by additions (one 64-bit division per thread, before the loop)
+  const int64_t stride = (int64_t)gridDim.x * tcn::WG;
+  const int64_t tile0 = (int64_t)blockIdx.x * tcn::WG + wg;
+  int i = (int)(tile0 / tpc);
+  int64_t tr = tile0 - (int64_t)i * tpc;
+  const auto advance = [&](int &ci, int64_t &ct) {
+    ct += stride;
+    while (ct >= tpc) {
+      ct -= tpc;
+      ++ci;
+    }
+  };
+  for (int64_t tile = tile0; tile < ntiles; tile += stride, advance(i, tr)) {
+    const int64_t j = tr * PPT + pair;
     const CompT<float> &cp = comp[i];
     const bool valid = j < n;
     {
       // this row's observation in the warpgroup's next tile, brought into L1
       // while this tile runs through the network
-      const int64_t nt = tile + (int64_t)gridDim.x * tcn::WG;
-      const int64_t jn = (nt % tpc) * PPT + pair;
-      if (nt < ntiles && jn < n) tc::prefetch_l1(Y + jn * p);
+      int in = i;
+      int64_t trn = tr;
+      advance(in, trn);
+      const int64_t jn = trn * PPT + pair;
+      if (tile + stride < ntiles && jn < n) tc::prefetch_l1(Y + jn * p);
     }
     RowProblem rp;
     float u[DIN];
