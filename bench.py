@@ -806,6 +806,52 @@ def run_batched(args):
     return 0
 
 
+def _oracle_loglik_block(args):
+    """One spawned worker: the oracle's log-likelihood of a block of rows of
+    one fit (rows, parameters and lattice passed in)."""
+    Y, P, lat_n, lat_z, lat_shift = args
+    from oracle import cfust_oracle as O
+    U = O.lattice_points(lat_n, lat_z, lat_shift)
+    t0 = time.perf_counter()
+    ll = O.loglik(Y, P, U)
+    return float(ll), time.perf_counter() - t0
+
+
+def batched_oracle_check(Ys, inits, traces, lat, nfits=4):
+    """The batched workload's oracle comparison: the oracle's log-likelihood
+    at the starting parameters of the `nfits` smallest fits (all their rows,
+    spread over every host core in a spawn-context pool) against the first
+    entry of the same fits' traces from the batched path (FP32 bar 1e-6
+    relative)."""
+    import multiprocessing as mp
+    order = sorted(range(len(Ys)), key=lambda f: Ys[f].shape[0])[:nfits]
+    cores = os.cpu_count() or 1
+    per = max(1, cores // len(order))
+    jobs, owner = [], []
+    for f in order:
+        n = Ys[f].shape[0]
+        edges = [n * q // per for q in range(per + 1)]
+        for q in range(per):
+            if edges[q + 1] > edges[q]:
+                jobs.append((np.ascontiguousarray(Ys[f][edges[q]:edges[q + 1]]), inits[f], int(lat.n),
+                             np.asarray(lat.z), np.asarray(lat.shift)))
+                owner.append(f)
+    ctx = mp.get_context("spawn")
+    t0 = time.perf_counter()
+    with ctx.Pool(min(cores, len(jobs))) as pool:
+        res = pool.map_async(_oracle_loglik_block, jobs).get(timeout=900)
+    wall = time.perf_counter() - t0
+    ref = {f: 0.0 for f in order}
+    for f, (ll, _) in zip(owner, res):
+        ref[f] += ll
+    per_fit = [{"fit": f, "n": int(Ys[f].shape[0]), "g": int(inits[f].g), "oracle": ref[f],
+                "gpu": float(traces[f][0]), "rel_err": abs(float(traces[f][0]) - ref[f]) / abs(ref[f])}
+               for f in order]
+    return {"what": f"log-likelihood at the starting parameters of the {len(order)} smallest fits, every row",
+            "max_rel_err": max(x["rel_err"] for x in per_fit), "bar": 1e-6, "fits": per_fit,
+            "oracle_wall_s": wall, "cores": min(cores, len(jobs))}
+
+
 def batched_line(args, steps, warmup):
     """Batched-fits workload (its own JSON line with --workload batched, and a
     key of the default line): 256
@@ -859,6 +905,10 @@ def batched_line(args, steps, warmup):
         "clocks": clocks,
         "fits_failed": int(sum(1 for s in st if s != 0)),
     }
+    try:
+        line["oracle_check"] = batched_oracle_check(Ys, inits, traces, lat)
+    except Exception as exc:  # reported, not hidden
+        line["oracle_check"] = {"error": f"{type(exc).__name__}: {exc}"[:300]}
     return line
 
 
