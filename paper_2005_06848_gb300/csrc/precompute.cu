@@ -45,7 +45,9 @@ __device__ inline double lattice_coord(int k, int z, int n, double shift) {
 
 // Component i of one fit (parameter block `params`): chi tables chi64/chi32
 // ([2][N] each, this component's rows) by the threads of blocks bx = 0..nbx-1,
-// and the factorisations into *o / *f by thread 0 of block 0.
+// and the factorisations into *o / *f by thread 0 of block nbx (a block of
+// its own, so that the serial double-precision factorisation runs beside the
+// tables' quantiles rather than after one of them).
 __device__ void precompute_component(const double *params, int g, int p, int r, int i, const LatticeDev &lat,
                                      CompT<double> *o_out, CompT<float> *f_out, double *t64, float *t32,
                                      int *status, int bx, int nbx) {
@@ -54,7 +56,7 @@ __device__ void precompute_component(const double *params, int g, int p, int r, 
   const int N = lat.n;
 
   // chi-scale tables: [2][N], one quantile per thread (pass A rows, then pass B)
-  for (int kk = bx * blockDim.x + threadIdx.x; kk < 2 * N; kk += nbx * blockDim.x) {
+  for (int kk = bx * blockDim.x + threadIdx.x; bx < nbx && kk < 2 * N; kk += nbx * blockDim.x) {
     const int k = kk < N ? kk : kk - N;
     const double u0 = lattice_coord(k, lat.z[0], N, lat.shift[0]);
     const double m = nu + p + (kk < N ? 0.0 : 2.0);
@@ -64,7 +66,7 @@ __device__ void precompute_component(const double *params, int g, int p, int r, 
     t32[kk] = (float)sc;
   }
 
-  if (bx != 0 || threadIdx.x != 0) return;
+  if (bx != nbx || threadIdx.x != 0) return;
 
   const double *mu = pv.mu + (int64_t)i * p;
   const double *Sig = pv.Sigma + (int64_t)i * p * p;
@@ -171,7 +173,7 @@ __global__ void precompute_kernel(const double *params, int g, int p, int r, Lat
                                   float *chi32, int *status) {
   const int i = blockIdx.y;
   precompute_component(params, g, p, r, i, lat, c64 + i, c32 + i, chi64 + (int64_t)i * 2 * lat.n,
-                       chi32 + (int64_t)i * 2 * lat.n, status, blockIdx.x, gridDim.x);
+                       chi32 + (int64_t)i * 2 * lat.n, status, blockIdx.x, gridDim.x - 1);
 }
 
 __global__ void precompute_batched_kernel(BatchDev b, int p, int r, LatticeDev lat, CompT<double> *c64,
@@ -181,7 +183,7 @@ __global__ void precompute_batched_kernel(BatchDev b, int p, int r, LatticeDev l
   const FitDesc fd = b.fits[cr.fit];
   precompute_component(b.params + fd.param_off, fd.g, p, r, cr.i, lat, c64 + gc, c32 + gc,
                        chi64 + (int64_t)gc * 2 * lat.n, chi32 + (int64_t)gc * 2 * lat.n, b.fit_status + cr.fit,
-                       blockIdx.x, gridDim.x);
+                       blockIdx.x, gridDim.x - 1);
 }
 
 }  // namespace
@@ -192,7 +194,8 @@ cudaError_t launch_precompute_batched(const BatchDev &b, int p, int r, const Lat
   const int threads = 64;
   int bx = (2 * lat.n + threads - 1) / threads;
   if (bx < 1) bx = 1;
-  precompute_batched_kernel<<<dim3(bx, b.G), threads, 0, st>>>(b, p, r, lat, c64, c32, chi64, chi32);
+  // bx table blocks and one factorisation block per component
+  precompute_batched_kernel<<<dim3(bx + 1, b.G), threads, 0, st>>>(b, p, r, lat, c64, c32, chi64, chi32);
   return cudaGetLastError();
 }
 
@@ -202,7 +205,7 @@ cudaError_t launch_precompute(const double *d_params, int g, int p, int r, const
   const int threads = 64;
   int bx = (2 * lat.n + threads - 1) / threads;
   if (bx < 1) bx = 1;
-  dim3 grid(bx, g);
+  dim3 grid(bx + 1, g);  // bx table blocks and one factorisation block per component
   precompute_kernel<<<grid, threads, 0, st>>>(d_params, g, p, r, lat, c64, c32, chi64, chi32,
                                               d_status);
   return cudaGetLastError();
