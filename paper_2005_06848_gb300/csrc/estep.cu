@@ -167,38 +167,53 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? CFUST_ESTEP_MINB : 1)
   }
 }
 
-// Triage and log-domain recomputation of one queued pair by the whole CTA.
+// The triage of a queued pair (single precision): with the log f of every
+// component of observation j in place, final values or pending bounds, a pair
+// whose bound log pi_i + ub_ij trails the best final value by tnats has
+// tau_ij < exp(-tnats) and is dropped instead of recomputed.  Pending bounds
+// of the observation's other pairs do not count towards the best (they are
+// upper bounds), and the decisions are all taken before any rescue writes.
+__device__ __forceinline__ bool triage_drops(const FitView &fv, int i, int64_t j, float tnats) {
+  const float *lf = reinterpret_cast<const float *>(fv.out.logf);
+  double best = -INFINITY;
+  for (int h = 0; h < fv.g; ++h) best = fmax(best, log(fv.pi[h]) + (double)lf[(int64_t)h * fv.n + j]);
+  const double mine = log(fv.pi[i]) + pending_bound_decode(lf[(int64_t)i * fv.n + j]);
+  return isfinite(best) && mine < best - (double)tnats;
+}
+
+constexpr unsigned long long RESCUE_DROP = 1ull << 63;  // marks a queued pair the triage dropped
+
+__global__ void rescue_triage_kernel(EArgs a) {
+  const unsigned cnt = *a.rescue_count;
+  const FitView fv = fit_view(a);
+  for (unsigned w = blockIdx.x * blockDim.x + threadIdx.x; w < cnt; w += gridDim.x * blockDim.x) {
+    const unsigned long long id = a.rescue_list[w];
+    if (triage_drops(fv, static_cast<int>(id >> 32), static_cast<int64_t>(id & 0xffffffffull), a.tnats))
+      a.rescue_list[w] = id | RESCUE_DROP;
+  }
+}
+
+// Log-domain recomputation of one queued pair by the whole CTA, or, when the
+// triage dropped it, log f = -inf and zero expectations.
 template <int R, bool DENS>
 __device__ void rescue_one(const EArgs &a, const FitView &fv, const CompT<double> &comp, const double *tab,
-                           int i, int64_t j, double *sm, Prologue<R> &spr, int &skip) {
-  if (threadIdx.x == 0) {
-    skip = 0;
-    if (a.triage) {
-      // tau_ij < exp(-tnats) when log pi_i + ub_ij trails the best component by tnats
-      const float *lf = reinterpret_cast<const float *>(fv.out.logf);
-      double best = -INFINITY;
-      for (int h = 0; h < fv.g; ++h) best = fmax(best, log(fv.pi[h]) + (double)lf[(int64_t)h * fv.n + j]);
-      const double mine = log(fv.pi[i]) + (double)lf[(int64_t)i * fv.n + j];
-      if (isfinite(best) && mine < best - (double)a.tnats) {
-        skip = 1;
-        const int64_t ij = (int64_t)i * fv.n + j;
-        const int RP = R * (R + 1) / 2;
-        store<float>(fv.out.logf, ij, -INFINITY);
-        if (!DENS) {
-          store<float>(fv.out.e1, ij, 0.0);
-          store<float>(fv.out.e2, ij, 0.0);
-          for (int t = 0; t < R; ++t) store<float>(fv.out.e3, ((int64_t)i * R + t) * fv.n + j, 0.0);
-          for (int t = 0; t < RP; ++t) store<float>(fv.out.e4, ((int64_t)i * RP + t) * fv.n + j, 0.0);
-        }
+                           int i, int64_t j, bool dropped, double *sm, Prologue<R> &spr) {
+  if (dropped) {
+    if (threadIdx.x == 0) {
+      const int64_t ij = (int64_t)i * fv.n + j;
+      const int RP = R * (R + 1) / 2;
+      store<float>(fv.out.logf, ij, -INFINITY);
+      if (!DENS) {
+        store<float>(fv.out.e1, ij, 0.0);
+        store<float>(fv.out.e2, ij, 0.0);
+        for (int t = 0; t < R; ++t) store<float>(fv.out.e3, ((int64_t)i * R + t) * fv.n + j, 0.0);
+        for (int t = 0; t < RP; ++t) store<float>(fv.out.e4, ((int64_t)i * RP + t) * fv.n + j, 0.0);
       }
     }
-    if (!skip) spr = prologue<double, R>(a, fv, comp, j);
+    return;  // uniform over the block
   }
+  if (threadIdx.x == 0) spr = prologue<double, R>(a, fv, comp, j);
   __syncthreads();
-  if (skip) {
-    __syncthreads();
-    return;
-  }
   const Prologue<R> pr = spr;
   pair_sweep_log_cta<R, DENS>(a, fv, comp, pr, tab, tab + a.N, i, j, sm);
 }
@@ -209,14 +224,13 @@ __global__ void __launch_bounds__(256) rescue_kernel(EArgs a, const CompT<double
   constexpr int NV = 3 + R + R * (R + 1) / 2;
   __shared__ double sm[8 * (2 + NV)];
   __shared__ Prologue<R> spr;
-  __shared__ int skip;
   const unsigned cnt = *a.rescue_count;
   const FitView fv = fit_view(a);
   for (unsigned w = blockIdx.x; w < cnt; w += gridDim.x) {
     const unsigned long long id = a.rescue_list[w];
-    const int i = static_cast<int>(id >> 32);
+    const int i = static_cast<int>((id & ~RESCUE_DROP) >> 32);
     const int64_t j = static_cast<int64_t>(id & 0xffffffffull);
-    rescue_one<R, DENS>(a, fv, comp[i], chi + (int64_t)i * 2 * a.N, i, j, sm, spr, skip);
+    rescue_one<R, DENS>(a, fv, comp[i], chi + (int64_t)i * 2 * a.N, i, j, (id & RESCUE_DROP) != 0, sm, spr);
   }
 }
 
@@ -257,6 +271,11 @@ cudaError_t launch_r(EArgs a, int g, int64_t n, cudaStream_t st, bool fp32,
     if (e != cudaSuccess) return e;
   }
   if (!fp32) return e;
+  if (a.triage) {
+    rescue_triage_kernel<<<sm_count() * 2, 256, 0, st>>>(a);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+  }
   rescue_kernel<R, DENS><<<sm_count() * 4, 256, 0, st>>>(a, c64, chi64);
   return cudaGetLastError();
 }
@@ -377,22 +396,35 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? CFUST_ESTEP_MINB : 1)
   }
 }
 
+// The triage of the batch's queued pairs (see rescue_triage_kernel).
+__global__ void rescue_triage_batched_kernel(EArgs a, BatchDev b, int r) {
+  const unsigned cnt = *a.rescue_count;
+  for (unsigned w = blockIdx.x * blockDim.x + threadIdx.x; w < cnt; w += gridDim.x * blockDim.x) {
+    const unsigned long long id = a.rescue_list[w];
+    const int gc = static_cast<int>(id >> 32);
+    const CompRef cr = b.comps[gc];
+    const FitDesc fd = b.fits[cr.fit];
+    const FitView fv = batch_view<float>(b, fd, a.p, r);
+    if (triage_drops(fv, cr.i, static_cast<int64_t>(id & 0xffffffffull), a.tnats))
+      a.rescue_list[w] = id | RESCUE_DROP;
+  }
+}
+
 template <int R, bool DENS>
 __global__ void __launch_bounds__(256) rescue_batched_kernel(EArgs a, BatchDev b, const CompT<double> *comp,
                                                               const double *chi) {
   constexpr int NV = 3 + R + R * (R + 1) / 2;
   __shared__ double sm[8 * (2 + NV)];
   __shared__ Prologue<R> spr;
-  __shared__ int skip;
   const unsigned cnt = *a.rescue_count;
   for (unsigned w = blockIdx.x; w < cnt; w += gridDim.x) {
     const unsigned long long id = a.rescue_list[w];
-    const int gc = static_cast<int>(id >> 32);
+    const int gc = static_cast<int>((id & ~RESCUE_DROP) >> 32);
     const int64_t j = static_cast<int64_t>(id & 0xffffffffull);
     const CompRef cr = b.comps[gc];
     const FitDesc fd = b.fits[cr.fit];
     const FitView fv = batch_view<float>(b, fd, a.p, R);
-    rescue_one<R, DENS>(a, fv, comp[gc], chi + (int64_t)gc * 2 * a.N, cr.i, j, sm, spr, skip);
+    rescue_one<R, DENS>(a, fv, comp[gc], chi + (int64_t)gc * 2 * a.N, cr.i, j, (id & RESCUE_DROP) != 0, sm, spr);
   }
 }
 
@@ -420,6 +452,11 @@ cudaError_t launch_batched_r(EArgs a, const BatchDev &b, const SweepItem *items,
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
   if (tm.stop && (e = cudaEventRecordWithFlags(tm.stop, st, evflag)) != cudaSuccess) return e;
   if (!fp32) return cudaSuccess;
+  if (a.triage) {
+    rescue_triage_batched_kernel<<<sm_count() * 2, 256, 0, st>>>(a, b, R);
+    const cudaError_t et = cudaGetLastError();
+    if (et != cudaSuccess) return et;
+  }
   rescue_batched_kernel<R, DENS><<<sm_count() * 4, 256, 0, st>>>(a, b, c64, chi64);
   return cudaGetLastError();
 }
@@ -557,6 +594,11 @@ cudaError_t launch_list_r3(EArgs a, int g, int64_t n, const int *list, const uns
     estep_list_kernel<float, 3, DENS, false><<<grid, 256, smem, st>>>(a, list, count, n);
   e = cudaGetLastError();
   if (e != cudaSuccess) return e;
+  if (a.triage) {
+    rescue_triage_kernel<<<sm_count() * 2, 256, 0, st>>>(a);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+  }
   rescue_kernel<3, DENS><<<sm_count() * 4, 256, 0, st>>>(a, c64, chi64);
   return cudaGetLastError();
 }

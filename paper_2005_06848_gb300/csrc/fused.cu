@@ -152,7 +152,7 @@ __device__ __noinline__ void fused_rescue(const EArgs &a, const FusedArgs &f, co
           double best = -INFINITY;
           for (int h = 0; h < g; ++h)
             if (!flag[h * tj + jj]) best = fmax(best, log(fv.pi[h]) + (double)lf[h * tj + jj]);
-          const double mine = log(fv.pi[i]) + (double)lf[i * tj + jj];
+          const double mine = log(fv.pi[i]) + pending_bound_decode(lf[i * tj + jj]);
           if (isfinite(best) && mine < best - (double)a.tnats) {
             *skip = 1;
             const int64_t ij = (int64_t)i * tj + jj;

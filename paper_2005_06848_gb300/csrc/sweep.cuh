@@ -309,6 +309,26 @@ __device__ __forceinline__ double lat_sf(const EArgs &a, int t) { return a.sfrac
 __device__ __forceinline__ double lat_two_sf(const EArgs &a, int t) { return 2.0 * a.sfrac[t]; }
 __device__ __forceinline__ double lat_step2(const EArgs &a, int t) { return (double)(2 * a.step[t]); }
 
+// A pair left to the double-precision rescue keeps an upper bound of its
+// log f in its log f slot until the rescue, stored as a quiet NaN whose
+// payload is the bound (ceil(8 ub) + 2^21 in 22 bits: eighths of a nat over
+// +-262144 nats; a bound below that range is stored as its lower end, still
+// an upper bound; the top payload means +inf).  A maximum over an
+// observation's log f values (fmax) skips it, so a triage compares with final
+// values only, and the pair's own test decodes its bound.
+__device__ __forceinline__ float pending_bound_encode(double ub) {
+  unsigned payload = 0x3FFFFFu;
+  if (ub < 262143.0) {
+    const double c = ceil(ub * 8.0) + 2097152.0;
+    payload = c > 0.0 ? (unsigned)c : 0u;
+  }
+  return __uint_as_float(0x7FC00000u | payload);
+}
+__device__ __forceinline__ double pending_bound_decode(float v) {
+  const unsigned payload = __float_as_uint(v) & 0x3FFFFFu;
+  return payload == 0x3FFFFFu ? INFINITY : ((double)payload - 2097152.0) * 0.125;
+}
+
 // Per-pair prologue in double precision: z = A (y - mu), d = z^T z, q = B z and
 // the log of the t_p factor with the constant c0 of Eq. 2.
 template <int R>
@@ -595,10 +615,12 @@ __device__ __forceinline__ bool pair_sweep(const EArgs &a, const FitView &fv, co
       // upper bound of log f for the triage: the float sum misses only point
       // weights that fell below the float range, so T <= max(S_A / N, 1e-37) up
       // to rounding; one nat of margin; +inf when the sum is not finite
-      if (a.triage && fv.out.logf != nullptr && lane == 0) {
-        const double sa = (double)SA / (double)N;
-        const double ub = isfinite(sa) ? pr.logt + log(fmax(sa, 1e-37)) + 1.0 : INFINITY;
-        store<OT>(fv.out.logf, ij, ub);
+      if constexpr (sizeof(OT) == 4) {
+        if (a.triage && fv.out.logf != nullptr && lane == 0) {
+          const double sa = (double)SA / (double)N;
+          const double ub = isfinite(sa) ? pr.logt + log(fmax(sa, 1e-37)) + 1.0 : INFINITY;
+          reinterpret_cast<float *>(fv.out.logf)[ij] = pending_bound_encode(ub);
+        }
       }
       return true;
     }

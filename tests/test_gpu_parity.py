@@ -521,3 +521,41 @@ def test_stepwise_fit_equals_fit_and_triage_keeps_loglik():
     U = O.lattice_points(lat.n, lat.z, lat.shift)
     ref = O.loglik(Y, init, U)
     assert abs(t1[0] - ref) <= 1e-6 * abs(ref)
+
+
+def _two_underflowing_components():
+    """A p=1, r=1, g=2 mixture with both components near the normal limit and
+    skewed downwards, its own draws plus four rows at y = 17.5 .. 19: there
+    both pairs' single-precision lattice sums underflow, component 0
+    outweighs component 1 by 256 to 296 nats under the 512-point rule, and yet
+    component 0's pending density bound trails component 1's by about 30.5
+    nats (both bounds sit at log t + log 1e-37 + 1, and component 1 has the
+    larger log t)."""
+    P = synth.Params(pi=np.array([0.5, 0.5]), mu=np.array([[1.400927034064857], [-0.4946095065202325]]),
+                     Sigma=np.array([[[0.5344986830086018 ** 2]], [[0.4538790293528015 ** 2]]]),
+                     Delta=np.array([[[-1.299385364828229]], [[-2.706859290038734]]]), nu=np.array([200.0, 200.0]))
+    Y, _ = synth.sample_cfust(P, 300, np.random.default_rng(7))
+    Y = np.ascontiguousarray(np.vstack([Y, np.array([[17.5], [18.0], [18.5], [19.0]])]))
+    return Y, P, synth.make_lattice(512, 2, 0)
+
+
+@pytest.mark.parametrize("fused", [False, True])
+def test_triage_compares_with_final_values_only(fused):
+    """The triage of pairs left to the double-precision rescue drops a pair
+    only against another component's FINAL log f: another pending pair's
+    bound is an upper bound (here it would wrongly drop the component that
+    carries the far rows).  The FP32 log-likelihood, with the triage on,
+    against the oracle to 1e-6 relative (-1599.7): a wrong drop of component
+    0 at a far row would move it by more than 250 nats."""
+    torch = _torch()
+    Y, P, lat = _two_underflowing_components()
+    ref = O.loglik(Y, P, O.lattice_points(lat.n, lat.z, lat.shift))
+    Yd = torch.from_numpy(Y).cuda()
+    with binding.Context(lat, precision=binding.CFUST_FP32, fused=fused, max_iter=1) as ctx:
+        got = ctx.cfust_loglik(Yd, P)
+        rescued = ctx.cfust_last_rescued()
+        _, trace, _ = ctx.cfust_fit(Yd, P)
+    print("rescued pairs", rescued)
+    assert rescued >= 8, rescued
+    assert abs(got - ref) <= 1e-6 * abs(ref), (got, ref)
+    assert abs(trace[0] - ref) <= 1e-6 * abs(ref), (trace[0], ref)
