@@ -182,7 +182,7 @@ def mstep_roofline(n, g, p, r, ms, peaks, sms):
             "algorithmic_bytes": int(nbytes), "achieved": gbs, "unit": "GB/s",
             "peak": hbm, "frac": (gbs / hbm) if hbm else None,
             "peak_source": "measured copy bandwidth (MEASURED_PEAKS.json)" if hbm else None,
-            "fused": "not built: per-pair outputs stay in L2 at this size (20 MB)"}
+            "fused": "the fused pass (cfust_opts.fused) folds these sums into the sweep kernel: the line's fused key"}
 
 
 def load_peaks():
