@@ -357,8 +357,8 @@ cfust_status cfust_normal_f32(const float *x, float *out, int64_t n, int which, 
  * each) plus the parameters must fit; larger problems (e.g. g = 64, p = 16,
  * r = 6) return CFUST_EINVAL with a message naming the limit.
  * The first call on a device looks up the array's device address with
- * cudaGetSymbolAddress (with that device current); make that first call
- * before any stream capture.  All calls share the array: calls that overlap
+ * cudaGetSymbolAddress (with that device current).  All calls share the
+ * array: calls that overlap
  * on the GPU (different streams, or different host threads) race and must be
  * serialised by the caller.  No cudaMalloc, cudaFree or allocating library
  * routine is called.
