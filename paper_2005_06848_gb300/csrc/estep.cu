@@ -54,7 +54,7 @@ __device__ __forceinline__ void sweep_warp_pairs(const EArgs &a, const FitView &
     PrioLane<R, T> pp;
     if constexpr (PRIO) pp = shfl_prio<R, T>(pmine, b);
     const int64_t j = jw0 + b;
-    const bool need = pair_sweep<T, T, R, DENS, PRIO>(a, fv, c, pr, tA, tB, i, j, lane, check, pcs, wpc, &pp);
+    const bool need = pair_sweep<T, T, R, DENS, PRIO, 2>(a, fv, c, pr, tA, tB, i, j, lane, check, pcs, wpc, &pp);
     if (need && lane == 0) {
       const unsigned slot = atomicAdd(a.rescue_count, 1u);
       a.rescue_list[slot] = pair_id(qi, j);
@@ -158,7 +158,7 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? CFUST_ESTEP_MINB : 1)
       PrioLane<R, T> pp;
       if constexpr (PRIO) pp = shfl_prio<R, T>(pmine, b);
       const int64_t j = __shfl_sync(0xffffffffu, myj, b);
-      const bool need = pair_sweep<T, T, R, DENS, PRIO>(a, fv, *cs, pr, tA, tB, i, j, lane, check, pcs, wpc, &pp);
+      const bool need = pair_sweep<T, T, R, DENS, PRIO, 2>(a, fv, *cs, pr, tA, tB, i, j, lane, check, pcs, wpc, &pp);
       if (need && lane == 0) {
         const unsigned slot = atomicAdd(a.rescue_count, 1u);
         a.rescue_list[slot] = pair_id(i, j);

@@ -154,6 +154,33 @@ __device__ __forceinline__ float2 neg_quantile_x2(float um, float u, float2 p, f
   return make_float2(lx ? -zq.x : zq.x, ly ? -zq.y : zq.y);
 }
 
+// One lane of neg_quantile_x2: the same coefficients and the same operations in
+// the same order (a packed FP32x2 operation rounds each half as its scalar
+// counterpart does), so the result equals that lane's bit for bit.  For a
+// draw only one pass of the pair needs.
+__device__ __forceinline__ float neg_quantile_x1(float um, float u, float p, float q) {
+  const float x = um * p;
+  const float c = fmaf(um, q, u);  // 1 - x
+  const bool lx = x <= 0.5f;
+  const float xs = lx ? fmaxf(x, 1.17549435e-38f) : c;
+  const float prod = xs * fmaf(xs, -4.0f, 4.0f);
+  const float l = __log2f(prod);
+  const float tc = fmaf(l, -0.69314718056f, -nf32::Q_W0F);
+  float pc = nf32::kPairs.p0[6].x;
+#pragma unroll
+  for (int k = 5; k >= 0; --k) pc = fmaf(pc, tc, nf32::kPairs.p0[k].x);
+  const float rn = rsqrtf(-l);
+  const float tt = fmaf(rn, 1.20112240879f, -nf32::Q_U3);
+  float pt = nf32::kPairs.p3[9].x;
+#pragma unroll
+  for (int k = 8; k >= 0; --k) pt = fmaf(pt, tt, nf32::kPairs.p3[k].x);
+  pt = pt * (l * rn);
+  const float P = l > -7.21347520444f ? pc : pt;
+  const float v = fmaf(2.82842712475f, xs, -1.41421356237f);
+  const float zq = v * P;
+  return lx ? -zq : zq;
+}
+
 // z = -Phi^{-1}(x) for x = um * p, given also u = 1 - um and q = 1 - p; when
 // x > 1/2 the quantile is taken of 1 - x = u + um q, which keeps full relative
 // precision where x itself is within rounding of 1.

@@ -379,7 +379,7 @@ __device__ __forceinline__ Prologue<R> shfl_prologue(const Prologue<R> &mine, in
 // One (i, j) pair on one warp, its prologue given.  Returns true (uniformly
 // over the warp) when `check` is set and the single-precision sweep needs the
 // double rescue; in that case nothing is written.
-template <typename T, typename OT, int R, bool DENS, bool PRIO = false>
+template <typename T, typename OT, int R, bool DENS, bool PRIO = false, int PTS = 1>
 __device__ __forceinline__ bool pair_sweep(const EArgs &a, const FitView &fv, const CompT<T> &c,
                                            const Prologue<R> &pr,
                                            const T *__restrict__ tA, const T *__restrict__ tB,
@@ -482,6 +482,13 @@ __device__ __forceinline__ bool pair_sweep(const EArgs &a, const FitView &fv, co
 #pragma unroll
   for (int t = 0; t < RP; ++t) M2[t] = T(0);
 
+  // paired sweeps up to r = 4 keep two lattice points in flight per lane:
+  // their dependency chains (a point's conditional draws are sequential in t)
+  // interleave, and each lane's sums still take the points in the same order.
+  // Larger r and the prioritised form would spill at the register cap.
+  constexpr int kPoints = (PAIRED && !PRIO && R <= 4) ? PTS : 1;
+  float2 SAB = make_float2(0.0f, 0.0f);  // paired sweeps: (SA, SB) side by side
+#pragma unroll kPoints
   for (int k = lane; k < N; k += WARP) {
     // 1 - u_t = |2 m - N + 2 sfrac| / N and u_t = 2 min(m + sfrac, N - m - sfrac) / N,
     // each formed from an exact integer and the fraction so the small side stays exact;
@@ -519,7 +526,7 @@ __device__ __forceinline__ bool pair_sweep(const EArgs &a, const FitView &fv, co
     if constexpr (PAIRED) {
       // passes A and B side by side in FP32x2: .x is pass A, .y pass B
       const float2 s2 = make_float2(tA[k], tB[k]);
-      float2 w2 = make_float2(1.0f, 1.0f);
+      float2 w2;
       float2 z2[R];
 #pragma unroll
       for (int t = 0; t < R; ++t) {
@@ -528,12 +535,15 @@ __device__ __forceinline__ bool pair_sweep(const EArgs &a, const FitView &fv, co
         for (int h = 0; h < t; ++h) acc2 = __ffma2_rn(pcu->nL[t * (t + 1) / 2 + h], z2[h], acc2);
         float2 p2, q2;
         phi_upper_pq_x2(acc2, p2, q2);
-        w2 = __fmul2_rn(w2, p2);
-        z2[t] = neg_quantile_x2(um[t], uu[t], p2, q2);
+        w2 = (t == 0) ? p2 : __fmul2_rn(w2, p2);
+        // the last draw feeds pass B's moments only: pass A's half is not formed
+        if (t + 1 < R)
+          z2[t] = neg_quantile_x2(um[t], uu[t], p2, q2);
+        else
+          z2[t] = make_float2(0.0f, neg_quantile_x1(um[t], uu[t], p2.y, q2.y));
       }
-      SA += w2.x;
+      SAB = __fadd2_rn(SAB, w2);
       if (e2lat) SL += w2.x * (logmA + T(2) * M::lg(s2.x));
-      SB += w2.y;
       const float isB = __fdividef(1.0f, s2.y);
 #pragma unroll
       for (int t = 0; t < R; ++t) {
@@ -587,6 +597,10 @@ __device__ __forceinline__ bool pair_sweep(const EArgs &a, const FitView &fv, co
       }
   }
 
+  if constexpr (PAIRED) {
+    SA = SAB.x;
+    SB = SAB.y;
+  }
   SA = warp_sum(SA);
   if (e2lat) SL = warp_sum(SL);
   if (!DENS) {
