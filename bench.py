@@ -85,7 +85,7 @@ def sweep_profile():
         with open(os.path.join(ROOT, "profiles", "estep_kernel_p4r4g3_n100000_N4096.json")) as f:
             rec = json.load(f)
         h = hashlib.sha256()
-        for name in ("estep.cu", "normal_f32.cuh", "normal_f32_coeffs.cuh", "cfust_internal.cuh"):
+        for name in ("estep.cu", "sweep.cuh", "normal_f32.cuh", "normal_f32_coeffs.cuh", "cfust_internal.cuh"):
             with open(os.path.join(ROOT, "paper_2005_06848_gb300", "csrc", name), "rb") as f:
                 h.update(f.read())
         if h.hexdigest() != rec["source_sha256"]:

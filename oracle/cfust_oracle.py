@@ -31,6 +31,11 @@ What it computes, and where each step comes from:
   variables over a shifted rank-1 (Korobov) lattice with the baker's
   transform; the t law is handled as a normal divided by an independent
   chi scale, coordinate 0 of the lattice drawing the chi-square quantile.
+* Opt-in (``shared``): pass B estimated on pass A's lattice points.  The
+  chi-square densities satisfy chi2_{m+2}(x) = chi2_m(x) x / m, so pass B's
+  integrals are pass A's integrand weighted by x / (nu+p) at pass A's points
+  (sov_pass_shared): the same T_B and truncated moments, half the normal
+  evaluations of two separate passes.
 * The M-step: the paper's Algorithm 3 updates each component from the
   E-step's partial sums (Section 3.2's "eight partial sums").  The eight sums
   and the conditional-maximisation updates are derived by maximising the
@@ -95,6 +100,23 @@ def chi_scale(u0: np.ndarray, m: float) -> np.ndarray:
     return np.sqrt(2.0 * x / m)
 
 
+def _sov_chain(a, L, U, s):
+    """Point weights w [P, N] and conditional draws z [P, N, r] of the
+    separation-of-variables chain (the loop of sov_pass, below)."""
+    P, r = a.shape
+    N = U.shape[0]
+    zs = np.zeros((P, N, r))
+    w = np.ones((P, N))
+    for t in range(r):
+        cond = np.einsum("h,pnh->pn", L[t, :t], zs[:, :, :t]) if t > 0 else 0.0
+        lim = (a[:, t, None] * s[None, :] - cond) / L[t, t]
+        pt = special.ndtr(-lim)
+        w = w * pt
+        arg = np.maximum((1.0 - U[None, :, t + 1]) * pt, TINY64)
+        zs[:, :, t] = -special.ndtri(arg)
+    return w, zs
+
+
 def sov_pass(a: np.ndarray, L: np.ndarray, m: float, U: np.ndarray,
              moments: bool, logchi: bool = False, s: np.ndarray | None = None):
     """Genz separation-of-variables estimate of P(L V > a), V ~ t_r(0, I, m).
@@ -114,19 +136,10 @@ def sov_pass(a: np.ndarray, L: np.ndarray, m: float, U: np.ndarray,
     Returns T [P]; with ``moments`` also EV [P, r], EVV [P, r, r]; with
     ``logchi`` also E[log chi^2_m] under the weights [P].
     """
-    P, r = a.shape
     N = U.shape[0]
     if s is None:
         s = chi_scale(U[:, 0], m)                            # [N]
-    zs = np.zeros((P, N, r))
-    w = np.ones((P, N))
-    for t in range(r):
-        cond = np.einsum("h,pnh->pn", L[t, :t], zs[:, :, :t]) if t > 0 else 0.0
-        lim = (a[:, t, None] * s[None, :] - cond) / L[t, t]
-        pt = special.ndtr(-lim)
-        w = w * pt
-        arg = np.maximum((1.0 - U[None, :, t + 1]) * pt, TINY64)
-        zs[:, :, t] = -special.ndtri(arg)
+    w, zs = _sov_chain(a, L, U, s)
     T = w.sum(axis=1) / N
     out = [T]
     if moments:
@@ -192,10 +205,45 @@ def prioritised_order(a, Lam):
     return np.argsort(-c, axis=1, kind="stable")
 
 
-def _passes(aA, aB, L, Lam, mA, mB, U, sA, sB, logchi, density_only, prioritise):
+def sov_pass_shared(aA, L, mA, mB, U, sA, logchi=False):
+    """Pass A and pass B from one set of lattice points (``shared`` reading).
+
+    Pass B's law differs from pass A's only in the chi variable: V = Z / s with
+    s^2 = x / m and x ~ chi^2_{m_B} instead of chi^2_{m_A}, m_B = m_A + 2.  The
+    chi-square densities satisfy chi2_{m+2}(x) = chi2_m(x) x / m, and pass B's
+    scaled limit a_B sqrt(x / m_B) = -q sqrt(x / (nu + d)) is pass A's
+    a_A sqrt(x / m_A) at the same x.  So pass B is pass A's integrand at pass
+    A's points (x = m_A s_A^2 from lattice coordinate 0) with the extra weight
+    x / m_A = s_A^2 and V = z / s_B, s_B = sqrt(x / m_B) = s_A sqrt(m_A / m_B):
+        T_B = mean(w s_A^2),
+        E[V] = sum w s_A^2 V / sum w s_A^2,  E[V V^T] likewise,
+    the same integrals as sov_pass at dof m_B, estimated on pass A's draws.  In
+    the skew-normal limit (m_A = m_B = inf, s_A = 1) the weight is 1 and V = z.
+    Returns T_A, E[log chi^2_{m_A}] (with ``logchi``, else None), T_B, E[V], E[V V^T].
+    """
+    N = U.shape[0]
+    w, zs = _sov_chain(aA, L, U, sA)
+    TA = w.sum(axis=1) / N
+    el = None
+    if logchi:
+        with np.errstate(invalid="ignore", divide="ignore"):
+            el = (w @ np.log(mA * sA * sA)) / w.sum(axis=1)
+    ratio = 1.0 if math.isinf(mA) else math.sqrt(mA / mB)
+    wb = w * (sA * sA)[None, :]
+    v = zs / (sA * ratio)[None, :, None]
+    W = wb.sum(axis=1)
+    TB = W / N
+    with np.errstate(invalid="ignore", divide="ignore"):
+        EV = np.einsum("pn,pnr->pr", wb, v) / W[:, None]
+        EVV = np.einsum("pn,pnr,pns->prs", wb, v, v) / W[:, None, None]
+    return TA, el, TB, EV, EVV
+
+
+def _passes(aA, aB, L, Lam, mA, mB, U, sA, sB, logchi, density_only, prioritise, shared=False):
     """Pass A (T_A, optionally E[log chi^2]) and pass B (T_B, L E[V], L E[V V^T] L^T)
     of the pairs of one chunk, in natural or prioritised variable order; the
-    moments come back in the natural order of X = L V."""
+    moments come back in the natural order of X = L V.  With ``shared`` pass B
+    is estimated on pass A's lattice points (sov_pass_shared)."""
     P, r = aA.shape
     perms = prioritised_order(aA, Lam) if (prioritise and r > 1) else np.tile(np.arange(r), (P, 1))
     TA = np.empty(P); EL = np.empty(P) if logchi else None
@@ -203,13 +251,19 @@ def _passes(aA, aB, L, Lam, mA, mB, U, sA, sB, logchi, density_only, prioritise)
     for perm in np.unique(perms, axis=0):
         idx = np.nonzero((perms == perm).all(axis=1))[0]
         Lp = L if np.array_equal(perm, np.arange(r)) else np.linalg.cholesky(Lam[np.ix_(perm, perm)])
-        if logchi:
-            TA[idx], EL[idx] = sov_pass(aA[idx][:, perm], Lp, mA, U, moments=False, logchi=True, s=sA)
+        if shared and not density_only:
+            ta, el, tb, EV, EVV = sov_pass_shared(aA[idx][:, perm], Lp, mA, mB, U, sA, logchi)
+            TA[idx] = ta
+            if logchi:
+                EL[idx] = el
         else:
-            TA[idx] = sov_pass(aA[idx][:, perm], Lp, mA, U, moments=False, s=sA)
-        if density_only:
-            continue
-        tb, EV, EVV = sov_pass(aB[idx][:, perm], Lp, mB, U, moments=True, s=sB)
+            if logchi:
+                TA[idx], EL[idx] = sov_pass(aA[idx][:, perm], Lp, mA, U, moments=False, logchi=True, s=sA)
+            else:
+                TA[idx] = sov_pass(aA[idx][:, perm], Lp, mA, U, moments=False, s=sA)
+            if density_only:
+                continue
+            tb, EV, EVV = sov_pass(aB[idx][:, perm], Lp, mB, U, moments=True, s=sB)
         TB[idx] = tb
         # X_perm = Lp V: scatter its moments back to the natural coordinates
         lev = EV @ Lp.T
@@ -220,7 +274,7 @@ def _passes(aA, aB, L, Lam, mA, mB, U, sA, sB, logchi, density_only, prioritise)
 
 
 def estep_component(Y, mu, Sigma, Delta, nu, U, e2_mode=0, density_only=False,
-                    chunk=None, prioritise=False):
+                    chunk=None, prioritise=False, shared=False):
     """log f_i(y_j) and e1..e4 for every observation j of one component i.
 
     Returns dict with logf [n], and unless ``density_only``: e1 [n], e2 [n],
@@ -233,6 +287,7 @@ def estep_component(Y, mu, Sigma, Delta, nu, U, e2_mode=0, density_only=False,
     set to 0, their weight tau being 0.  ``prioritise``
     integrates each pair's variables in the order of ``prioritised_order``
     (pass B's limits are a positive multiple of pass A's: the same order).
+    ``shared`` estimates pass B on pass A's lattice points (sov_pass_shared).
     """
     n, p = Y.shape
     r = Delta.shape[1]
@@ -256,7 +311,7 @@ def estep_component(Y, mu, Sigma, Delta, nu, U, e2_mode=0, density_only=False,
         aB = -qq * _dof_ratio(mB, nu, dd)[:, None]
         logchi = (e2_mode == 1 and not density_only)
         TA, elogchi, TB, LEV, LEVVL = _passes(aA, aB, L, Lam, mA, mB, U, sA, sB, logchi, density_only,
-                                              prioritise)
+                                              prioritise, shared)
         with np.errstate(divide="ignore"):
             # a probability below the smallest normal double counts as
             # underflowed (reading: subnormal values carry too few bits to
@@ -332,7 +387,7 @@ def posterior(logf: np.ndarray, pi: np.ndarray):
     return tau, float(lse.sum()), lse
 
 
-def estep(Y, params, lattice_U, e2_mode=0, prioritise=False):
+def estep(Y, params, lattice_U, e2_mode=0, prioritise=False, shared=False):
     """E-step of Section 2 for all (i, j): log f_ij, tau_ij, e1..e4 and l(Psi).
 
     ``params`` has arrays pi[g], mu[g,p], Sigma[g,p,p], Delta[g,p,r], nu[g].
@@ -341,7 +396,8 @@ def estep(Y, params, lattice_U, e2_mode=0, prioritise=False):
     """
     g = params.pi.shape[0]
     comps = [estep_component(Y, params.mu[i], params.Sigma[i], params.Delta[i],
-                             params.nu[i], lattice_U, e2_mode=e2_mode, prioritise=prioritise)
+                             params.nu[i], lattice_U, e2_mode=e2_mode, prioritise=prioritise,
+                             shared=shared)
              for i in range(g)]
     out = {k: np.stack([c[k] for c in comps]) for k in comps[0]}
     tau, ll, _ = posterior(out["logf"], params.pi)
@@ -462,7 +518,7 @@ def q_function(Y, tau, e1, e2, e3, e4, params, i):
 
 
 def fit(Y, params0, lattice_U, iters, e2_mode=0, nu_min=1.0, nu_max=200.0,
-        fix_delta=False):
+        fix_delta=False, shared=False):
     """EM (Section 2 outline; Algorithms 2 and 3) for a fixed number of iterations.
 
     The E-step at Psi^(k) also yields l(Psi^(k)) (Algorithm 2 computes the
@@ -474,7 +530,7 @@ def fit(Y, params0, lattice_U, iters, e2_mode=0, nu_min=1.0, nu_max=200.0,
     params = params0.copy()
     trace = []
     for _ in range(iters):
-        E = estep(Y, params, lattice_U, e2_mode)
+        E = estep(Y, params, lattice_U, e2_mode, shared=shared)
         trace.append(E["loglik"])
         sums = mstep_sums(Y, E["tau"], E["e1"], E["e2"], E["e3"], E["e4"])
         params = mstep_update(sums, params, n, nu_min, nu_max, fix_delta)

@@ -556,3 +556,82 @@ def test_prioritised_rule_is_more_accurate_per_point():
             est = np.array([O.sov_pass(a[None, perm], Lp, math.inf, _U(1024, 3, s), False)[0] for s in range(4)])
             errs[prio] = float(np.max(np.abs(est - ref)) / ref)
         assert errs[True] < 1e-6 and errs[False] > 1e-2, (a, errs)
+
+
+# --------------------------------------------------------------------------- pass B on pass A's points
+
+@pytest.mark.parametrize("m", [5.0, 6.3, 12.5])
+def test_shared_points_r1_match_univariate_t_closed_forms_at_dof_plus_two(m):
+    """r = 1: pass B estimated on pass A's points (weight x/m_A) is the t law at
+    dof m + 2 truncated at its own limit a_B = a_A sqrt((m+2)/m): scipy's t
+    survival function and the closed-form truncated moments at dof m + 2."""
+    aA = np.array([[-1.5], [-0.3], [0.0], [0.7], [1.6]])
+    l = 0.8
+    mB = m + 2.0
+    cB = aA[:, 0] * math.sqrt(mB / m) / l
+    S0, E1, E2 = _t_trunc_closed(cB, mB)
+    U = _U(1 << 14, 2, 3)
+    TA, _, TB, EV, EVV = O.sov_pass_shared(aA, np.array([[l]]), m, mB, U, O.chi_scale(U[:, 0], m))
+    assert np.allclose(TA, stats.t.sf(aA[:, 0] / l, m), rtol=2e-5)
+    assert np.allclose(TB, S0, rtol=2e-5)
+    assert np.allclose(EV[:, 0], E1, rtol=2e-3)
+    assert np.allclose(EVV[:, 0, 0], E2, rtol=1e-2)
+
+
+def test_shared_points_agree_with_the_separate_pass_b_at_high_n():
+    """r = 3, general Lambda: the two estimators of pass B (its own chi-square
+    quantile at dof m + 2, or pass A's points with the density ratio x/m) are
+    different rules for the same integrals, so at 65536 points they agree to
+    the rules' error on pairs whose probability is not in the far tail."""
+    rng = np.random.default_rng(5)
+    A = rng.standard_normal((3, 3))
+    Lam = A @ A.T / 3 + 0.6 * np.eye(3)
+    dinv = 1 / np.sqrt(np.diag(Lam))
+    Lam = Lam * dinv[:, None] * dinv[None, :]
+    L = np.linalg.cholesky(Lam)
+    m = 7.5
+    aA = rng.uniform(-1.5, 0.8, (12, 3))
+    aB = aA * math.sqrt((m + 2) / m)
+    U = _U(1 << 16, 4, 2)
+    TA, _, TB, EV, EVV = O.sov_pass_shared(aA, L, m, m + 2, U, O.chi_scale(U[:, 0], m))
+    TB2, EV2, EVV2 = O.sov_pass(aB, L, m + 2, U, True)
+    assert np.all(TB2 > 1e-2)
+    assert np.allclose(TB, TB2, rtol=2e-4)
+    assert np.allclose(EV, EV2, rtol=0, atol=2e-3)
+    assert np.allclose(EVV, EVV2, rtol=0, atol=5e-3)
+    # and pass A is the plain pass at dof m
+    assert np.array_equal(TA, O.sov_pass(aA, L, m, U, False))
+
+
+def test_shared_points_skew_normal_limit_is_the_separate_passes():
+    """nu = inf: the chi scale is 1 and both passes take the limits -q, so the
+    weight x/m is 1 and the shared estimate is the separate one bit for bit."""
+    rng = np.random.default_rng(13)
+    mu, Sigma, Delta = _sn_case(rng, 3, 2)
+    Y = mu + rng.standard_normal((25, 3)) * 1.5
+    U = _U(1024, 3, 4)
+    a = O.estep_component(Y, mu, Sigma, Delta, math.inf, U)
+    b = O.estep_component(Y, mu, Sigma, Delta, math.inf, U, shared=True)
+    for k in ("logf", "e1", "e2", "e3", "e4"):
+        assert np.array_equal(a[k], b[k]), k
+
+
+def test_estep_shared_points_match_brute_force_monte_carlo():
+    """The E-step with pass B on pass A's points against self-normalised
+    importance sampling of Section 2's latent structure (as the natural rule)."""
+    rng = np.random.default_rng(11)
+    p, r = 2, 2
+    mu = np.array([0.3, -0.4])
+    Sigma = np.array([[1.0, 0.4], [0.4, 0.8]])
+    Delta = np.array([[1.2, -0.5], [0.7, 1.5]])
+    nu = 6.0
+    Ys = np.array([[1.5, 1.0], [-0.5, 0.2], [2.5, 3.0]])
+    U = _U(1 << 14, r + 1, 9)
+    out = O.estep_component(Ys, mu, Sigma, Delta, nu, U, e2_mode=1, shared=True)
+    for j, y in enumerate(Ys):
+        f, fse, e1, e2, e3, e4 = _mc_posterior(y, mu, Sigma, Delta, nu, 1_500_000, rng)
+        assert abs(math.exp(out["logf"][j]) - f) < 5 * fse + 2e-4 * f
+        assert abs(out["e1"][j] - e1[0][0]) < 5 * e1[1][0] + 1e-3
+        assert abs(out["e2"][j] - e2[0][0]) < 5 * e2[1][0] + 2e-3
+        assert np.all(np.abs(out["e3"][j] - e3[0]) < 5 * e3[1] + 2e-3)
+        assert np.all(np.abs(out["e4"][j].ravel() - e4[0]) < 5 * e4[1] + 5e-3)
