@@ -60,10 +60,15 @@ PHI_FLOPS = 24
 PHIINV_FLOPS = 30
 
 
-def sweep_flops_per_point(r: int, density_only: bool = False) -> int:
-    """Flop-equivalents of one lattice point of one pair (both passes, or pass A alone)."""
+def sweep_flops_per_point(r: int, density_only: bool = False, shared: bool = False) -> int:
+    """Flop-equivalents of one lattice point of one pair (both passes, or pass A alone).
+    With pass B on pass A's points (shared_points) one conditional chain serves
+    both passes: r Phi, r Phi^-1 (every draw feeds pass B's moments), r(r-1)/2
+    conditional-limit FMAs and the same r + r(r+1)/2 moment FMAs."""
     if density_only:
         return r * PHI_FLOPS + (r - 1) * PHIINV_FLOPS + r * (r - 1)
+    if shared:
+        return r * PHI_FLOPS + r * PHIINV_FLOPS + r * (r - 1) + 2 * (r + r * (r + 1) // 2)
     return 2 * r * PHI_FLOPS + (2 * r - 1) * PHIINV_FLOPS + 2 * r * (r - 1) + 2 * (r + r * (r + 1) // 2)
 
 
@@ -650,7 +655,7 @@ def run_ours(args):
     total_iters = args.warmup + args.steps
 
     ctx = binding.Context(lat, precision=binding.CFUST_FP32, max_iter=total_iters, use_graph=True,
-                          timing=True, stream=stream, fused=args.fused)
+                          timing=True, stream=stream, fused=args.fused, shared_points=args.shared)
     ctx.cfust_fit_begin(Yd, init)
     for _ in range(args.warmup):
         flush.zero_()
@@ -691,13 +696,13 @@ def run_ours(args):
 
     # roofline of the sweep kernel (the E-step's dominant kernel)
     mean_sweep_ms = float(np.mean(sweep_ms))
-    flops = pairs_per_step * lat.n * sweep_flops_per_point(r)
+    flops = pairs_per_step * lat.n * sweep_flops_per_point(r, shared=args.shared)
     achieved = flops / (mean_sweep_ms / 1e3) / 1e12
     peaks = load_peaks()
     sm_max = (peaks or {}).get("sm_max_mhz", 2070.0)
     sms = sm_count()
     peak = peak_fp32_tflops(sm_max, sms)
-    prof = sweep_profile() or {}
+    prof = (sweep_profile() or {}) if not (args.shared or args.fused) else {}
 
     # end-to-end through the public API: every step copies Y from pinned host
     # memory into the bound device buffer, runs one EM iteration, and reads the
@@ -709,7 +714,7 @@ def run_ours(args):
         Ye.copy_(Yh)
         e2e_steps = max(3, min(args.steps, 10))
         ctx2 = binding.Context(lat, precision=binding.CFUST_FP32, max_iter=2 + e2e_steps, use_graph=True,
-                               stream=stream, fused=args.fused)
+                               stream=stream, fused=args.fused, shared_points=args.shared)
         ctx2.cfust_fit_begin(Ye, init)
         for _ in range(2):
             Ye.copy_(Yh, non_blocking=True)
@@ -742,20 +747,24 @@ def run_ours(args):
         "config": {"workload": WORKLOAD, "n": n, "g": g, "p": p, "r": r, "lattice_points": lat.n,
                    "precision": "FP32 lattice sweeps; FP64 prologue, factorisations, log-likelihood, M-step",
                    "step": "one EM iteration (CUDA graph replay)", "l2": "flushed between timed steps",
+                   "pass_b": "on pass A's lattice points" if args.shared else "its own lattice sweep",
                    "parallelism": f"independent fits, {ws} rank(s)"},
         "em_iters_per_s": iters_per_s,
         "rescued_pairs_last_estep": rescued,
         "loglik_first_last": [float(trace[0]), float(trace[-1])],
         "gpu_launches": 6 * args.steps,
         "roofline": {"bound": "alu", "kernel": "fused_em_kernel<float,4>" if args.fused else "estep_kernel<float,4>",
-                     "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak, "traffic": sweep_traffic_bytes(),
+                     "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
+                     "traffic": None if (args.shared or args.fused) else sweep_traffic_bytes(),
                      "peak_source": f"FP32 FMA peak {sms} SMs x 128 lanes x 2 x {sm_max:.0f} MHz "
                                     "(derived from unit counts and the maximum SM clock)",
                      "sweep_ms_mean": mean_sweep_ms,
                      "flops_per_launch": flops,
-                     "flops_per_point": sweep_flops_per_point(r),
-                     "count": f"per point: 2r Phi x {PHI_FLOPS} + (2r-1) Phi^-1 x {PHIINV_FLOPS} "
-                              "+ r(r-1) conditional FMAs + (r + r(r+1)/2) moment FMAs, FMA = 2 flops",
+                     "flops_per_point": sweep_flops_per_point(r, shared=args.shared),
+                     "count": (f"per point: r Phi x {PHI_FLOPS} + r Phi^-1 x {PHIINV_FLOPS} + r(r-1)/2 "
+                               "conditional FMAs + (r + r(r+1)/2) moment FMAs, FMA = 2 flops" if args.shared else
+                               f"per point: 2r Phi x {PHI_FLOPS} + (2r-1) Phi^-1 x {PHIINV_FLOPS} "
+                               "+ r(r-1) conditional FMAs + (r + r(r+1)/2) moment FMAs, FMA = 2 flops"),
                      "ncu": {k: prof[k] for k in ("fma_pipe_pct", "xu_pipe_pct", "issue_active_pct",
                                                   "fp32_flop_eq_per_point", "xu_inst_per_point")
                              if k in prof} or None},
@@ -773,6 +782,10 @@ def run_ours(args):
         "fused": fused_comparison(torch, binding, Yd, init, lat, args.steps, args.warmup, flush,
                                   total_ms / args.steps, params, pairs_per_step, peak, r)
         if ws == 1 and not args.fused and not args.no_extras else None,
+        # pass B on pass A's lattice points on the same fit
+        "shared_points": shared_comparison(torch, binding, synth, Yd, init, lat, args.steps, args.warmup, flush,
+                                           total_ms / args.steps, params, pairs_per_step, peak, r, stream)
+        if ws == 1 and not args.fused and not args.shared and not args.no_extras else None,
         "clocks": clocks,
         "e2e": e2e,
     }
@@ -959,6 +972,65 @@ def _fit_memory(torch, binding, Yd, P, lat, fused):
     held = free0 - torch.cuda.mem_get_info()[0]
     ctx.close()
     return int(held)
+
+
+def shared_comparison(torch, binding, synth, Yd, P, lat, steps, warmup, flush, two_pass_ms, two_pass_params,
+                      pairs, peak, r, stream):
+    """Pass B on pass A's lattice points (cfust_opts.shared_points) on the
+    same fit as the two-pass line: time per EM iteration, the sweep kernel
+    against the FP32 peak (the shared rule's own count), how far the fitted
+    parameters are from the two-pass fit after the same iterations, and the
+    accuracy of both rules' E-step outputs against the 65536-point two-pass rule
+    in prioritised order (l is pass A's and identical; e1 and e3 tau-weighted
+    relative RMS over the pairs)."""
+    ctx = binding.Context(lat, precision=binding.CFUST_FP32, max_iter=warmup + steps + 1, use_graph=True,
+                          timing=True, shared_points=True)
+    ms, kern, params = _timed_em(torch, ctx, Yd, P, steps, warmup, flush)
+    ctx.close()
+    step_ms = float(np.mean(ms))
+    kern_ms = float(np.mean(kern))
+    flops = pairs * lat.n * sweep_flops_per_point(r, shared=True)
+    achieved = flops / (kern_ms / 1e3) / 1e12
+    errs = {}
+    with binding.Context(synth.make_lattice(1 << 16, r + 1, 0), precision=binding.CFUST_FP32, prioritise=True,
+                         stream=stream) as cj:
+        J = cj.cfust_estep(Yd, P)
+    tau = J["tau"].double()
+
+    def rel_rms(a, b):
+        d = (a.double() - b.double()) / b.double().abs().clamp_min(1e-3)
+        d = torch.where(torch.isfinite(d), d, torch.zeros_like(d))
+        w = tau if d.dim() == 2 else tau[:, None, :]
+        return float((w * d * d).sum() / w.expand_as(d).sum()) ** 0.5
+    for shared in (False, True):
+        with binding.Context(lat, precision=binding.CFUST_FP32, shared_points=shared, stream=stream) as c:
+            E = c.cfust_estep(Yd, P)
+            errs["shared" if shared else "two_pass"] = {
+                "loglik_error": float(E["loglik"] - J["loglik"]),
+                "e1_rel_rms_tau_weighted": rel_rms(E["e1"], J["e1"]),
+                "e3_rel_rms_tau_weighted": rel_rms(E["e3"], J["e3"])}
+    return {
+        "ms_per_step": step_ms, "value": pairs / (step_ms / 1e3), "unit": UNIT,
+        "em_iters_per_s": 1e3 / step_ms, "two_pass_ms_per_step": two_pass_ms,
+        "speed_vs_two_pass": two_pass_ms / step_ms,
+        "kernel": "estep_kernel<float,%d,shared points>" % r, "kernel_ms_mean": kern_ms,
+        "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
+                     "flops_per_point": sweep_flops_per_point(r, shared=True)},
+        "params_max_rel_diff_vs_two_pass": _max_rel_diff(params, two_pass_params),
+        "accuracy": {"judge": "65536-point lattice, two passes, prioritised order, FP32", **errs},
+    }
+
+
+def _max_rel_diff(a_params, b_params):
+    diffs = []
+    for a, b in zip(a_params.as_arrays(), b_params.as_arrays()):
+        a = np.asarray(a, dtype=np.float64)
+        b = np.asarray(b, dtype=np.float64)
+        fin = np.isfinite(b)
+        if fin.any():
+            scale = max(float(np.max(np.abs(b[fin]))), 1e-300)
+            diffs.append(float(np.max(np.abs(a[fin] - b[fin]))) / scale)
+    return max(diffs) if diffs else None
 
 
 def fused_comparison(torch, binding, Yd, P, lat, steps, warmup, flush, unfused_ms, unfused_params, pairs, peak, r):
@@ -1241,6 +1313,8 @@ def main(argv=None):
                     help="triage margin T (nats) of the surrogate and plain contexts: a listed or rescued "
                          "pair with tau provably below exp(-T) is dropped, moving l by at most exp(-T)")
     ap.add_argument("--nfits", type=int, default=256)
+    ap.add_argument("--shared", action="store_true",
+                    help="time the default workload with pass B on pass A's lattice points (cfust_opts.shared_points)")
     ap.add_argument("--fused", action="store_true",
                     help="time the default workload with the fused E-step + M-step-sums kernel (cfust_opts.fused)")
     ap.add_argument("--rows", type=int, default=0,

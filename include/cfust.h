@@ -132,6 +132,17 @@ typedef struct {
                              cfust_mstep*, cfust_fit_batched and the explicit E-step outputs keep the
                              unfused kernels; a fit or log-likelihood with a surrogate attached and
                              fused = 1 fails with CFUST_EINVAL. */
+  int shared_points;      /* 1: pass B (T_B and the truncated moments at dof nu+p+2 that give e1, e3, e4)
+                             is estimated on pass A's lattice points.  The two laws differ only in the
+                             chi-square variable x, and chi2_{nu+p+2}(x) = chi2_{nu+p}(x) x / (nu+p): at
+                             pass A's x of a point pass B's scaled limits equal pass A's, so pass A's
+                             conditional draws serve both, pass B with the extra weight x / (nu+p).  The
+                             same integrals with one conditional chain per point instead of two (about
+                             half the normal-function work); log f and l are pass A's, unchanged, and
+                             e1..e4 move within the rule's error.  0 keeps the two separate sweeps.
+                             Taken by cfust_estep, cfust_loglik and the single-fit paths in both
+                             precisions; prioritise = 1 or fused = 1 with it fail at cfust_create, and
+                             a surrogate or cfust_fit_batched with it fail with CFUST_EINVAL. */
 } cfust_opts;
 
 typedef struct cfust_ctx cfust_ctx;

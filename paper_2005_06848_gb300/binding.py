@@ -57,7 +57,7 @@ class cfust_opts(ctypes.Structure):
                 ("max_iter", ctypes.c_int), ("tol", ctypes.c_double), ("use_graph", ctypes.c_int),
                 ("timing", ctypes.c_int), ("pairs_per_warp", ctypes.c_int), ("autotune", ctypes.c_int),
                 ("triage_nats", ctypes.c_double), ("prioritise", ctypes.c_int),
-                ("test_wait_polls", ctypes.c_int), ("fused", ctypes.c_int)]
+                ("test_wait_polls", ctypes.c_int), ("fused", ctypes.c_int), ("shared_points", ctypes.c_int)]
 
 
 _LIB = None
@@ -189,7 +189,8 @@ class Context:
 
     def __init__(self, lattice, precision=CFUST_FP32, e2_mode=0, nu_min=0.0, nu_max=0.0,
                  max_iter=0, tol=0.0, use_graph=True, timing=False, pairs_per_warp=0, autotune=False,
-                 stream=None, triage_nats=0.0, prioritise=False, test_wait_polls=0, fused=False):
+                 stream=None, triage_nats=0.0, prioritise=False, test_wait_polls=0, fused=False,
+                 shared_points=False):
         import torch
         self.lib = load()
         self._z = np.ascontiguousarray(lattice.z, dtype=np.int64)
@@ -200,7 +201,8 @@ class Context:
         self.opts = cfust_opts(int(precision), lat, int(e2_mode), float(nu_min), float(nu_max),
                                int(max_iter), float(tol), 1 if use_graph else 0, 1 if timing else 0,
                                int(pairs_per_warp), 1 if autotune else 0, float(triage_nats),
-                               1 if prioritise else 0, int(test_wait_polls), 1 if fused else 0)
+                               1 if prioritise else 0, int(test_wait_polls), 1 if fused else 0,
+                               1 if shared_points else 0)
         self.precision = int(precision)
         self.stream = stream if stream is not None else torch.cuda.current_stream()
         self.lattice_n = int(lattice.n)

@@ -395,9 +395,11 @@ cfust_status run_estep(cfust_ctx *c, const double *Y, int64_t n, EstepOut o, boo
     CF_CUDA(c, launch_estep(c->opts.precision, Y, n, c->g, c->p, c->r, c->lat, c->d_c64, c->d_c32,
                             c->d_chi64, c->d_chi32, o, density_only, c->opts.e2_mode, c->d_rescue,
                             c->d_rescue_cnt, c->d_status, c->opts.pairs_per_warp, st, tm, triage, pi,
-                            (float)c->opts.triage_nats, c->opts.prioritise));
+                            (float)c->opts.triage_nats, c->opts.prioritise, c->opts.shared_points));
     return CFUST_OK;
   }
+  if (c->opts.shared_points)
+    return fail(c, CFUST_EINVAL, "shared_points covers the lattice rule alone: detach the surrogate");
   if (c->opts.precision != CFUST_FP32 || c->opts.e2_mode != 0 || c->r != 3)
     return fail(c, CFUST_EINVAL, "the surrogate E-step needs CFUST_FP32, e2_mode 0 and r = 3");
   const unsigned evflag = tm.capturing ? cudaEventRecordExternal : cudaEventRecordDefault;
@@ -543,6 +545,14 @@ cfust_status cfust_create(cfust_ctx **out, const cfust_opts *o, void *cuda_strea
   }
   if (o->fused != 0 && o->fused != 1) {
     g_create_error = "fused must be 0 or 1";
+    return CFUST_EINVAL;
+  }
+  if (o->shared_points != 0 && o->shared_points != 1) {
+    g_create_error = "shared_points must be 0 or 1";
+    return CFUST_EINVAL;
+  }
+  if (o->shared_points && (o->prioritise || o->fused)) {
+    g_create_error = "shared_points runs the natural order in the unfused sweep: prioritise and fused must be 0";
     return CFUST_EINVAL;
   }
   cfust_ctx *c = new cfust_ctx();
@@ -1128,6 +1138,7 @@ extern "C" cfust_status cfust_fit_batched(cfust_ctx *c, int nfits, const double 
                                          cfust_params *P, double *trace_out, int *fit_status_out) {
   if (!c) return CFUST_EINVAL;
   if (nfits < 1 || !Y || !n || !P) return fail(c, CFUST_EINVAL, "nfits >= 1 with Y, n and params required");
+  if (c->opts.shared_points) return fail(c, CFUST_EINVAL, "batched fits take the two-pass rule: shared_points must be 0");
   DeviceGuard dg(c->device);
   const int p = P[0].p, r = P[0].r;
   for (int f = 0; f < nfits; ++f) {

@@ -149,7 +149,8 @@ cudaError_t launch_estep(int precision, const double *Y, int64_t n, int g, int p
                          const double *chi64, const float *chi32, EstepOut out, bool density_only,
                          int e2_mode, unsigned long long *rescue_list, unsigned *rescue_count, int *d_status,
                          int pairs_per_warp, cudaStream_t st, SweepTiming tm = SweepTiming(),
-                         int triage = 0, const double *d_pi = nullptr, float tnats = 30.f, int prio = 0);
+                         int triage = 0, const double *d_pi = nullptr, float tnats = 30.f, int prio = 0,
+                         int shared = 0);
 
 // FP32 lattice sweep (r = 3 only) of the observations listed per component:
 // list[i * n + k], k < count[i] (device counts), followed by the rescue pass.

@@ -35,7 +35,7 @@ namespace {
 // computes the double prologue of the b-th observation, then the warp sweeps
 // them one at a time.  `qi` is the component index recorded for queued pairs
 // (the fit's own index, or the global one in a batch).
-template <typename T, int R, bool DENS, bool PRIO = false>
+template <typename T, int R, bool DENS, bool PRIO = false, bool SHR = false>
 __device__ __forceinline__ void sweep_warp_pairs(const EArgs &a, const FitView &fv, const CompT<T> &c,
                                                  const PairedConsts *pcs, const T *tA, const T *tB,
                                                  int i, int qi, int64_t jw0, int ppw, PairedConsts *wpc) {
@@ -54,7 +54,8 @@ __device__ __forceinline__ void sweep_warp_pairs(const EArgs &a, const FitView &
     PrioLane<R, T> pp;
     if constexpr (PRIO) pp = shfl_prio<R, T>(pmine, b);
     const int64_t j = jw0 + b;
-    const bool need = pair_sweep<T, T, R, DENS, PRIO, 2>(a, fv, c, pr, tA, tB, i, j, lane, check, pcs, wpc, &pp);
+    const bool need = pair_sweep<T, T, R, DENS, PRIO, 2, SHR>(a, fv, c, pr, tA, tB, i, j, lane, check, pcs, wpc,
+                                                              &pp);
     if (need && lane == 0) {
       const unsigned slot = atomicAdd(a.rescue_count, 1u);
       a.rescue_list[slot] = pair_id(qi, j);
@@ -62,7 +63,7 @@ __device__ __forceinline__ void sweep_warp_pairs(const EArgs &a, const FitView &
   }
 }
 
-template <typename T, int R, bool DENS, bool PRIO>
+template <typename T, int R, bool DENS, bool PRIO, bool SHR = false>
 __global__ void __launch_bounds__(256, sizeof(T) == 4 ? CFUST_ESTEP_MINB : 1) estep_kernel(EArgs a) {
   extern __shared__ __align__(128) unsigned char smem[];
   const int i = blockIdx.y;
@@ -79,7 +80,7 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? CFUST_ESTEP_MINB : 1) es
     wpc = reinterpret_cast<PairedConsts *>(smem + align16(tab_bytes) + align16(sizeof(CompT<T>)) +
                                            align16(sizeof(PairedConsts)) + 16) + warp;
   }
-  sweep_warp_pairs<T, R, DENS, PRIO>(a, fit_view(a), *cs, pcs, tA, tB, i, i, jw0, a.ppw, wpc);
+  sweep_warp_pairs<T, R, DENS, PRIO, SHR>(a, fit_view(a), *cs, pcs, tA, tB, i, i, jw0, a.ppw, wpc);
 }
 
 // Triage of a listed pair (single precision outputs): with log f of every
@@ -195,7 +196,7 @@ __global__ void rescue_triage_kernel(EArgs a) {
 
 // Log-domain recomputation of one queued pair by the whole CTA, or, when the
 // triage dropped it, log f = -inf and zero expectations.
-template <int R, bool DENS>
+template <int R, bool DENS, bool SHR = false>
 __device__ void rescue_one(const EArgs &a, const FitView &fv, const CompT<double> &comp, const double *tab,
                            int i, int64_t j, bool dropped, double *sm, Prologue<R> &spr) {
   if (dropped) {
@@ -215,10 +216,10 @@ __device__ void rescue_one(const EArgs &a, const FitView &fv, const CompT<double
   if (threadIdx.x == 0) spr = prologue<double, R>(a, fv, comp, j);
   __syncthreads();
   const Prologue<R> pr = spr;
-  pair_sweep_log_cta<R, DENS>(a, fv, comp, pr, tab, tab + a.N, i, j, sm);
+  pair_sweep_log_cta<R, DENS, SHR>(a, fv, comp, pr, tab, tab + a.N, i, j, sm);
 }
 
-template <int R, bool DENS>
+template <int R, bool DENS, bool SHR = false>
 __global__ void __launch_bounds__(256) rescue_kernel(EArgs a, const CompT<double> *comp,
                                                       const double *chi) {
   constexpr int NV = 3 + R + R * (R + 1) / 2;
@@ -230,7 +231,8 @@ __global__ void __launch_bounds__(256) rescue_kernel(EArgs a, const CompT<double
     const unsigned long long id = a.rescue_list[w];
     const int i = static_cast<int>((id & ~RESCUE_DROP) >> 32);
     const int64_t j = static_cast<int64_t>(id & 0xffffffffull);
-    rescue_one<R, DENS>(a, fv, comp[i], chi + (int64_t)i * 2 * a.N, i, j, (id & RESCUE_DROP) != 0, sm, spr);
+    rescue_one<R, DENS, SHR>(a, fv, comp[i], chi + (int64_t)i * 2 * a.N, i, j, (id & RESCUE_DROP) != 0, sm,
+                             spr);
   }
 }
 
@@ -244,8 +246,11 @@ cudaError_t launch_r(EArgs a, int g, int64_t n, cudaStream_t st, bool fp32,
   // the prioritised sweep is its own instantiation (r >= 2), so the default
   // one carries none of its registers
   const bool prio = a.prio && R >= 2;
-  cudaError_t e = prio ? raise_smem_limit((const void *)estep_kernel<T, R, DENS, (R >= 2)>, smem)
-                       : raise_smem_limit((const void *)estep_kernel<T, R, DENS, false>, smem);
+  // pass B on pass A's points: its own instantiation (full sweeps, natural order)
+  const bool shr = a.shr && !DENS && !prio;
+  cudaError_t e = prio  ? raise_smem_limit((const void *)estep_kernel<T, R, DENS, (R >= 2)>, smem)
+                  : shr ? raise_smem_limit((const void *)estep_kernel<T, R, DENS, false, !DENS>, smem)
+                        : raise_smem_limit((const void *)estep_kernel<T, R, DENS, false>, smem);
   if (e != cudaSuccess) return e;
   const int64_t per_cta = (int64_t)a.ppw * 8;
   const int64_t bx = (n + per_cta - 1) / per_cta;
@@ -262,6 +267,8 @@ cudaError_t launch_r(EArgs a, int g, int64_t n, cudaStream_t st, bool fp32,
   }
   if (prio)
     estep_kernel<T, R, DENS, (R >= 2)><<<grid, 256, smem, st>>>(a);
+  else if (shr)
+    estep_kernel<T, R, DENS, false, !DENS><<<grid, 256, smem, st>>>(a);
   else
     estep_kernel<T, R, DENS, false><<<grid, 256, smem, st>>>(a);
   e = cudaGetLastError();
@@ -276,7 +283,10 @@ cudaError_t launch_r(EArgs a, int g, int64_t n, cudaStream_t st, bool fp32,
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
   }
-  rescue_kernel<R, DENS><<<sm_count() * 4, 256, 0, st>>>(a, c64, chi64);
+  if (shr)
+    rescue_kernel<R, DENS, !DENS><<<sm_count() * 4, 256, 0, st>>>(a, c64, chi64);
+  else
+    rescue_kernel<R, DENS><<<sm_count() * 4, 256, 0, st>>>(a, c64, chi64);
   return cudaGetLastError();
 }
 
@@ -530,6 +540,7 @@ cudaError_t launch_estep_batched(int precision, const BatchDev &b, int p, int r,
   a.triage = triage ? 1 : 0;
   a.tnats = 30.f;
   a.prio = prio ? 1 : 0;
+  a.shr = 0;
   a.wait_polls = lat.wait_polls;
   if (precision == CFUST_FP64) {
     a.comp = c64;
@@ -605,7 +616,7 @@ cudaError_t launch_list_r3(EArgs a, int g, int64_t n, const int *list, const uns
 
 EArgs make_args(const double *Y, int64_t n, int g, int p, const LatticeDev &lat, EstepOut out, int e2_mode,
                 unsigned long long *rescue_list, unsigned *rescue_count, int *d_status, int triage,
-                const double *d_pi, float tnats, int prio = 0) {
+                const double *d_pi, float tnats, int prio = 0, int shared = 0) {
   EArgs a;
   a.Y = Y;
   a.n = n;
@@ -629,6 +640,7 @@ EArgs make_args(const double *Y, int64_t n, int g, int p, const LatticeDev &lat,
   a.triage = (triage && out.logf != nullptr) ? 1 : 0;
   a.tnats = tnats;
   a.prio = prio ? 1 : 0;
+  a.shr = shared ? 1 : 0;
   a.wait_polls = lat.wait_polls;
   a.pi = d_pi;
   a.comp = nullptr;
@@ -663,10 +675,10 @@ cudaError_t launch_estep(int precision, const double *Y, int64_t n, int g, int p
                          const double *chi64, const float *chi32, EstepOut out, bool density_only,
                          int e2_mode, unsigned long long *rescue_list, unsigned *rescue_count, int *d_status,
                          int pairs_per_warp, cudaStream_t st, SweepTiming tm, int triage,
-                         const double *d_pi, float tnats, int prio) {
+                         const double *d_pi, float tnats, int prio, int shared) {
   if (n <= 0) return cudaSuccess;
   EArgs a = make_args(Y, n, g, p, lat, out, e2_mode, rescue_list, rescue_count, d_status, triage, d_pi, tnats,
-                      prio);
+                      prio, shared);
   if (pairs_per_warp <= 0) {
     // about sixteen waves of two resident CTAs per SM (8 warps each), so the
     // last wave's imbalance stays small; 1..32 pairs per warp (measured best

@@ -603,6 +603,7 @@ cudaError_t launch_fused(int precision, const double *Y, int64_t n, int g, int p
   a.pi = d_pi;
   a.tnats = tnats;
   a.prio = prio ? 1 : 0;
+  a.shr = 0;
   a.wait_polls = lat.wait_polls;
   FusedArgs f{};
   f.c64 = c64;

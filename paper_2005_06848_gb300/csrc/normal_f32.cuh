@@ -133,9 +133,10 @@ __device__ __forceinline__ void phi_upper_pq_x2(float2 y, float2 &p, float2 &q) 
 
 // Paired, branch-free neg_quantile_f32: central piece below w = 5, single
 // tail piece P = sqrt(w) T(1/sqrt(w)) above.
-__device__ __forceinline__ float2 neg_quantile_x2(float um, float u, float2 p, float2 q) {
-  const float2 x = __fmul2_rn(f2(um), p);
-  const float2 c = __ffma2_rn(f2(um), q, f2(u));  // 1 - x
+// um and u may differ between the halves (two lattice points side by side).
+__device__ __forceinline__ float2 neg_quantile_x2v(float2 um, float2 u, float2 p, float2 q) {
+  const float2 x = __fmul2_rn(um, p);
+  const float2 c = __ffma2_rn(um, q, u);  // 1 - x
   const bool lx = x.x <= 0.5f, ly = x.y <= 0.5f;
   const float2 xs = make_float2(lx ? fmaxf(x.x, 1.17549435e-38f) : c.x, ly ? fmaxf(x.y, 1.17549435e-38f) : c.y);
   const float2 prod = __fmul2_rn(xs, __ffma2_rn(xs, f2(-4.0f), f2(4.0f)));  // 4 x (1 - x), exactly
@@ -152,6 +153,11 @@ __device__ __forceinline__ float2 neg_quantile_x2(float um, float u, float2 p, f
   const float2 v = __ffma2_rn(f2(2.82842712475f), xs, f2(-1.41421356237f));  // sqrt(2) (2x - 1)
   const float2 zq = __fmul2_rn(v, P);
   return make_float2(lx ? -zq.x : zq.x, ly ? -zq.y : zq.y);
+}
+
+// The same with one lattice point's (1 - u, u) for both halves (passes A and B).
+__device__ __forceinline__ float2 neg_quantile_x2(float um, float u, float2 p, float2 q) {
+  return neg_quantile_x2v(f2(um), f2(u), p, q);
 }
 
 // One lane of neg_quantile_x2: the same coefficients and the same operations in

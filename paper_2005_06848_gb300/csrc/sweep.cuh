@@ -103,6 +103,7 @@ struct EArgs {
   const double *pi;    // device [g], read by the triage
   float tnats;         // the triage's margin: tau_ij < exp(-tnats) counts as negligible
   int prio;            // 1: variable prioritisation (every sweep and its rescue)
+  int shr;             // 1: pass B estimated on pass A's lattice points (see pair_sweep)
   int wait_polls;      // polls of the staging wait before it gives up (LatticeDev::wait_polls)
 };
 
@@ -379,7 +380,88 @@ __device__ __forceinline__ Prologue<R> shfl_prologue(const Prologue<R> &mine, in
 // One (i, j) pair on one warp, its prologue given.  Returns true (uniformly
 // over the warp) when `check` is set and the single-precision sweep needs the
 // double rescue; in that case nothing is written.
-template <typename T, typename OT, int R, bool DENS, bool PRIO = false, int PTS = 1>
+// Single-precision sums of one pair with pass B on pass A's lattice points.
+// Pass B's law differs from pass A's only in the chi variable (dof m_B = m_A + 2
+// for m_A = nu + p), and chi2_{m+2}(x) = chi2_m(x) x / m: with x = m_A s^2 at
+// pass A's chi scale s of a point, pass B's scaled limit equals pass A's, so
+// pass B takes pass A's weight w and draws z with the extra weight s^2, and
+// V = z / (s c), c = sqrt(m_A / m_B).  Returned: SA = sum w, SB = sum w s^2,
+// M1 = sum w s z (= c sum w_B V), M2 = sum w z z^T (= c^2 sum w_B V V^T), SL
+// (e2_mode 1) = sum w (log m_A + 2 log s).  Each lane takes the points k and
+// k + 32 side by side in FP32x2 operations (.x and .y); a second point past
+// N repeats the first and gets weight 0.
+template <int R>
+__device__ __forceinline__ void shared_point_sums(const EArgs &a, int lane, const float *__restrict__ tA,
+                                                  const float2 (&ab2)[R], const PairedConsts *pcu, bool e2lat,
+                                                  float logmA, float &SA, float &SB, float &SL, float (&M1)[R],
+                                                  float (&M2)[R * (R + 1) / 2]) {
+  constexpr int RP = R * (R + 1) / 2;
+  constexpr int US = uniform_stride(R);
+  const int N = a.N;
+  float2 sa2 = make_float2(0.f, 0.f), sb2 = make_float2(0.f, 0.f);
+  float2 m1[R], m2[RP];
+#pragma unroll
+  for (int t = 0; t < R; ++t) m1[t] = make_float2(0.f, 0.f);
+#pragma unroll
+  for (int t = 0; t < RP; ++t) m2[t] = make_float2(0.f, 0.f);
+  float sl = 0.f;
+  for (int k = lane; k < N; k += 2 * WARP) {
+    const bool two = k + WARP < N;
+    const int k2 = two ? k + WARP : k;
+    const float4 *ra = reinterpret_cast<const float4 *>(a.utab) + (size_t)k * (US / 4);
+    const float4 *rb = reinterpret_cast<const float4 *>(a.utab) + (size_t)k2 * (US / 4);
+    float va[US], vb[US];
+#pragma unroll
+    for (int q4 = 0; q4 < US / 4; ++q4) {
+      const float4 fa = __ldg(ra + q4), fb = __ldg(rb + q4);
+      va[4 * q4] = fa.x;
+      va[4 * q4 + 1] = fa.y;
+      va[4 * q4 + 2] = fa.z;
+      va[4 * q4 + 3] = fa.w;
+      vb[4 * q4] = fb.x;
+      vb[4 * q4 + 1] = fb.y;
+      vb[4 * q4 + 2] = fb.z;
+      vb[4 * q4 + 3] = fb.w;
+    }
+    const float2 s2 = make_float2(tA[k], tA[k2]);
+    float2 w2;
+    float2 z2[R];
+#pragma unroll
+    for (int t = 0; t < R; ++t) {
+      float2 acc2 = __fmul2_rn(ab2[t], s2);
+#pragma unroll
+      for (int h = 0; h < t; ++h) acc2 = __ffma2_rn(pcu->nL[t * (t + 1) / 2 + h], z2[h], acc2);
+      float2 p2, q2;
+      phi_upper_pq_x2(acc2, p2, q2);
+      w2 = (t == 0) ? p2 : __fmul2_rn(w2, p2);
+      z2[t] = neg_quantile_x2v(make_float2(va[t], vb[t]), make_float2(va[R + t], vb[R + t]), p2, q2);
+    }
+    if (!two) w2.y = 0.0f;
+    sa2 = __fadd2_rn(sa2, w2);
+    if (e2lat) sl += w2.x * (logmA + 2.0f * logf(s2.x)) + w2.y * (logmA + 2.0f * logf(s2.y));
+    const float2 ws = __fmul2_rn(w2, s2);
+    sb2 = __ffma2_rn(ws, s2, sb2);
+#pragma unroll
+    for (int t = 0; t < R; ++t) {
+      m1[t] = __ffma2_rn(ws, z2[t], m1[t]);
+      const float2 u = __fmul2_rn(w2, z2[t]);
+#pragma unroll
+      for (int h = 0; h <= t; ++h) m2[t * (t + 1) / 2 + h] = __ffma2_rn(u, z2[h], m2[t * (t + 1) / 2 + h]);
+    }
+  }
+  SA = sa2.x + sa2.y;
+  SB = sb2.x + sb2.y;
+  SL = sl;
+#pragma unroll
+  for (int t = 0; t < R; ++t) M1[t] = m1[t].x + m1[t].y;
+#pragma unroll
+  for (int t = 0; t < RP; ++t) M2[t] = m2[t].x + m2[t].y;
+}
+
+// With SHR, pass B is estimated on pass A's lattice points (shared_point_sums;
+// the double-precision sweep does the same per point): one conditional chain
+// per point instead of two.
+template <typename T, typename OT, int R, bool DENS, bool PRIO = false, int PTS = 1, bool SHR = false>
 __device__ __forceinline__ bool pair_sweep(const EArgs &a, const FitView &fv, const CompT<T> &c,
                                            const Prologue<R> &pr,
                                            const T *__restrict__ tA, const T *__restrict__ tB,
@@ -488,6 +570,15 @@ __device__ __forceinline__ bool pair_sweep(const EArgs &a, const FitView &fv, co
   // Larger r and the prioritised form would spill at the register cap.
   constexpr int kPoints = (PAIRED && !PRIO && R <= 4) ? PTS : 1;
   float2 SAB = make_float2(0.0f, 0.0f);  // paired sweeps: (SA, SB) side by side
+  if constexpr (PAIRED && SHR) {
+    float2 abs2[R];
+#pragma unroll
+    for (int t = 0; t < R; ++t) abs2[t] = make_float2(ab2[t].x, ab2[t].x);
+    float sa, sb, sl;
+    shared_point_sums<R>(a, lane, tA, abs2, pcu, e2lat, logmA, sa, sb, sl, M1, M2);
+    SAB = make_float2(sa, sb);
+    SL = sl;
+  } else {
 #pragma unroll kPoints
   for (int k = lane; k < N; k += WARP) {
     // 1 - u_t = |2 m - N + 2 sfrac| / N and u_t = 2 min(m + sfrac, N - m - sfrac) / N,
@@ -565,11 +656,22 @@ __device__ __forceinline__ bool pair_sweep(const EArgs &a, const FitView &fv, co
         T pt, qt;
         M::upper_pq(acc * Li[t], pt, qt);
         wA *= pt;
-        if (t + 1 < R) zA[t] = M::neg_quantile(um[t], uu[t], pt, qt);
+        if (SHR || t + 1 < R) zA[t] = M::neg_quantile(um[t], uu[t], pt, qt);
       }
       SA += wA;
       if (e2lat) SL += wA * (logmA + T(2) * M::lg(sA));
-      if (!DENS) {
+      if constexpr (SHR && !DENS) {
+        // pass B on pass A's point: weight w s^2, sums as shared_point_sums
+        const T ws = wA * sA;
+        SB += ws * sA;
+#pragma unroll
+        for (int t = 0; t < R; ++t) {
+          M1[t] += ws * zA[t];
+          const T u = wA * zA[t];
+#pragma unroll
+          for (int h = 0; h <= t; ++h) M2[t * (t + 1) / 2 + h] += u * zA[h];
+        }
+      } else if (!DENS) {
         // pass B: the e1 numerator and the truncated moments
         const T sB = tB[k];
         const T isB = T(1) / sB;
@@ -596,6 +698,7 @@ __device__ __forceinline__ bool pair_sweep(const EArgs &a, const FitView &fv, co
       }
       }
   }
+  }
 
   if constexpr (PAIRED) {
     SA = SAB.x;
@@ -610,6 +713,14 @@ __device__ __forceinline__ bool pair_sweep(const EArgs &a, const FitView &fv, co
 #pragma unroll
     for (int t = 0; t < RP; ++t) M2[t] = warp_sum(M2[t]);
   }
+  if constexpr (SHR && !DENS) {
+    // sum w s z = c sum w_B V and sum w z z^T = c^2 sum w_B V V^T, c = sqrt(m_A / m_B)
+    const T ic = nrm ? T(1) : M::sq(mBT / mAT);
+#pragma unroll
+    for (int t = 0; t < R; ++t) M1[t] *= ic;
+#pragma unroll
+    for (int t = 0; t < RP; ++t) M2[t] *= ic * ic;
+  }
 
   // double precision: a probability below the smallest normal double counts
   // as underflowed (log f = -inf, expectations 0); a single-precision sum that
@@ -622,7 +733,12 @@ __device__ __forceinline__ bool pair_sweep(const EArgs &a, const FitView &fv, co
   const int64_t ij = (int64_t)i * n + j;
   if (check) {
     const T thr = T(1e-20) * static_cast<T>(N);
-    const bool densok = (SA >= thr) && isfinite(logf);
+    // pass B on pass A's points: pass B's sum no longer falls first for pairs
+    // far in the tails, whose single-precision log f degrades with the size
+    // of their conditional limits, so pass A's own threshold is raised to
+    // 1e-15 N (the pairs the separate pass B sends to the rescue lie below it)
+    const T thrA = SHR ? T(1e-15) * static_cast<T>(N) : thr;
+    const bool densok = (SA >= thrA) && isfinite(logf);
     bool need = !densok;
     if (!DENS) need = need || !(SB >= thr);
     if (need) {
@@ -810,7 +926,7 @@ __device__ __forceinline__ void lse_add(double &m, float &s, double lw, float &s
 // (limits and log weights in double arithmetic, every transcendental in float)
 // and accumulated against a running maximum, per lane, warp and CTA, so nothing
 // underflows.  `sm` is shared scratch of at least 8 * (4 + 3 + R + R(R+1)/2) words.
-template <int R, bool DENS>
+template <int R, bool DENS, bool SHR = false>
 __device__ void pair_sweep_log_cta(const EArgs &a, const FitView &fv, const CompT<double> &c,
                                    const Prologue<R> &pr,
                                    const double *__restrict__ tA, const double *__restrict__ tB, int i,
@@ -822,6 +938,7 @@ __device__ void pair_sweep_log_cta(const EArgs &a, const FitView &fv, const Comp
   const bool nrm = isinf(c.nu);  // the skew-normal limit: scale 1, e1 = 1, e2 = 0
   const double nud64 = c.nu + pr.d;
   const double fA = nrm ? 1.0 : sqrt(c.mA / nud64), fB = nrm ? 1.0 : sqrt(c.mB / nud64);
+  const double cshr = nrm ? 1.0 : sqrt(c.mA / c.mB);  // c of pass B on pass A's points
   double aA[R], aB[R], Lc[RP], Li[R], qv[R];
   int ord[R];
 #pragma unroll
@@ -899,17 +1016,24 @@ __device__ void pair_sweep_log_cta(const EArgs &a, const FitView &fv, const Comp
     lse_add(mA, v[0], lw, so, wn);
     if (e2lat) v[1] = fmaf(v[1], so, wn * (float)(c.logmA + 2.0 * (double)logf((float)sA)));
     if (!DENS) {
-      const double sB = tB[k];
-      const float isB = (float)(1.0 / sB);
       double lwb = 0.0;
+      float isB;
+      if constexpr (SHR) {
+        // pass B on this point of pass A: weight s_A^2, V = z / (s_A c)
+        lwb = lw + 2.0 * (double)logf((float)sA);
+        isB = (float)(1.0 / (sA * cshr));
+      } else {
+        const double sB = tB[k];
+        isB = (float)(1.0 / sB);
 #pragma unroll
-      for (int t = 0; t < R; ++t) {
-        double acc = aB[t] * sB;
+        for (int t = 0; t < R; ++t) {
+          double acc = aB[t] * sB;
 #pragma unroll
-        for (int h = 0; h < t; ++h) acc -= Lc[t * (t + 1) / 2 + h] * (double)z[h];
-        double lp;
-        rescue_dim(acc * Li[t], um[t], uu[t], lp, z[t]);
-        lwb += lp;
+          for (int h = 0; h < t; ++h) acc -= Lc[t * (t + 1) / 2 + h] * (double)z[h];
+          double lp;
+          rescue_dim(acc * Li[t], um[t], uu[t], lp, z[t]);
+          lwb += lp;
+        }
       }
       lse_add(mB, v[2], lwb, so, wn);
 #pragma unroll
