@@ -4,7 +4,9 @@
 One step = one EM iteration (Section 2 outline, Algorithms 2 and 3) on the
 synthetic workload p=4, r=4, g=3, n=100000 with a 4096-point lattice: the
 per-component precompute, the E-step lattice sweeps over all n*g pairs
-(single precision, double-precision prologue), the posterior, the
+(single precision, double-precision prologue; pass B estimated on pass A's
+lattice points, cfust_opts.shared_points, the separate pass-B sweep reported
+beside it and timed alone with --two-pass), the posterior, the
 log-likelihood and the M-step sums (double-precision accuracy; in the
 single-precision mode as double-float arithmetic on the FP32 pipe), and the
 conditional-maximisation update, replayed
@@ -44,6 +46,11 @@ sys.path.insert(0, ROOT)
 METRIC = "E-step (obs x comp)/s & EM iters/s: surrogate/FP32 vs plain QMC at fixed error"
 UNIT = "(obs x comp)/s"
 WORKLOAD = "cfust_p4r4g3_n100000_N4096"
+# The rule the bench times: pass B estimated on pass A's lattice points
+# (cfust_opts.shared_points; the same integrals, one conditional chain per
+# point).  --two-pass times the separate pass-B sweep instead, and the default
+# line reports that rule beside it.  The oracle legs run the same rule.
+PASS_B_SHARED = True
 L2_FLUSH_BYTES = 256 << 20
 # reference rule for log-likelihood accuracy (single precision: its FP32/FP64
 # difference, ~1e-9 relative, is far below the errors it judges)
@@ -82,12 +89,13 @@ def peak_fp32_tflops(sm_mhz: float, sms: int) -> float:
     return sms * 128 * 2 * sm_mhz * 1e6 / 1e12
 
 
-def sweep_profile():
-    """The committed ncu record of one sweep launch, or None when the sweep
-    sources changed since it was taken."""
+def sweep_profile(shared: bool = False):
+    """The committed ncu record of one sweep launch of the given pass-B rule,
+    or None when the sweep sources changed since it was taken."""
     import hashlib
+    name = "estep_kernel_shared_p4r4g3_n100000_N4096.json" if shared else "estep_kernel_p4r4g3_n100000_N4096.json"
     try:
-        with open(os.path.join(ROOT, "profiles", "estep_kernel_p4r4g3_n100000_N4096.json")) as f:
+        with open(os.path.join(ROOT, "profiles", name)) as f:
             rec = json.load(f)
         h = hashlib.sha256()
         for name in ("estep.cu", "sweep.cuh", "normal_f32.cuh", "normal_f32_coeffs.cuh", "cfust_internal.cuh"):
@@ -100,9 +108,9 @@ def sweep_profile():
         return None
 
 
-def sweep_traffic_bytes():
+def sweep_traffic_bytes(shared: bool = False):
     """DRAM bytes per sweep launch from the committed ncu capture (None when stale)."""
-    rec = sweep_profile()
+    rec = sweep_profile(shared)
     if rec is None:
         return None
     return int(rec["dram_bytes_read"]) + int(rec["dram_bytes_write"])
@@ -120,7 +128,8 @@ def accuracy_vs_judge(torch, binding, synth, Yd, P, lat, stream, r, pairs):
     tau = J["tau"].double()
     out = {"judge": "65536-point lattice, prioritised order, FP32", "lattice_points": lat.n}
     for prio in (False, True):
-        with binding.Context(lat, precision=binding.CFUST_FP32, prioritise=prio, stream=stream) as c:
+        with binding.Context(lat, precision=binding.CFUST_FP32, prioritise=prio, stream=stream,
+                             shared_points=PASS_B_SHARED) as c:
             E = c.cfust_estep(Yd, P)
             d = (E["logf"].double() - jl)
             d = torch.where(torch.isfinite(d), d, torch.zeros_like(d))
@@ -131,7 +140,7 @@ def accuracy_vs_judge(torch, binding, synth, Yd, P, lat, stream, r, pairs):
                 "tau_max_abs_error": float((E["tau"].double() - tau).abs().max())}
     def em_ms(L, prio):
         with binding.Context(L, precision=binding.CFUST_FP32, max_iter=8, use_graph=True, timing=True,
-                             prioritise=prio, stream=stream) as c:
+                             prioritise=prio, stream=stream, shared_points=PASS_B_SHARED) as c:
             c.cfust_fit_begin(Yd, P)
             for _ in range(3):
                 c.cfust_fit_step(1)
@@ -290,14 +299,15 @@ def cpu_baseline(rows: int = 1024):
     U = O.lattice_points(lat.n, lat.z, lat.shift)
     Ys = Y[:rows]
     t0 = time.perf_counter()
-    E = O.estep(Ys, init, U)
+    E = O.estep(Ys, init, U, shared=PASS_B_SHARED)
     S = O.mstep_sums(Ys, E["tau"], E["e1"], E["e2"], E["e3"], E["e4"])
     P1 = O.mstep_update(S, init, rows)
     dt = time.perf_counter() - t0
     pairs = rows * meta["g"]
     return ({"value": pairs / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
              "sample": f"{rows} of {meta['n']} observations x {meta['g']} components, "
-                       f"{lat.n}-point lattice, one E-step + M-step, FP64 numpy/scipy, {dt:.1f} s"},
+                       f"{lat.n}-point lattice, one E-step + M-step, FP64 numpy/scipy, {dt:.1f} s"
+                       + (", pass B on pass A's points" if PASS_B_SHARED else "")},
             (Ys, init, E, P1))
 
 
@@ -305,13 +315,13 @@ def _oracle_estep_rows(args):
     """One worker's share of the all-core baseline: the oracle's E-step of
     observations [j0, j1) of the bench workload (module-level so a spawned
     worker can import it)."""
-    j0, j1 = args
+    j0, j1, shared = args
     from oracle import cfust_oracle as O
     from paper_2005_06848_gb300 import synth
     Y, _, _, init, lat, _ = synth.workload(WORKLOAD)
     U = O.lattice_points(lat.n, lat.z, lat.shift)
     t0 = time.perf_counter()
-    O.estep(Y[j0:j1], init, U)
+    O.estep(Y[j0:j1], init, U, shared=shared)
     return time.perf_counter() - t0
 
 
@@ -326,7 +336,7 @@ def cpu_baseline_all_cores(rows_per_core: int = 256):
         from paper_2005_06848_gb300 import synth
         g = synth.WORKLOADS[WORKLOAD]["g"]
         n = synth.WORKLOADS[WORKLOAD]["n"]
-        blocks = [(k * rows_per_core, (k + 1) * rows_per_core) for k in range(cores)]
+        blocks = [(k * rows_per_core, (k + 1) * rows_per_core, PASS_B_SHARED) for k in range(cores)]
         blocks = [b for b in blocks if b[1] <= n]
         # spawned workers inherit the one-thread BLAS/OpenMP settings made at
         # the top of this module, so each process is one core
@@ -334,7 +344,7 @@ def cpu_baseline_all_cores(rows_per_core: int = 256):
         # bounded waits: a worker that dies would leave a plain map waiting;
         # leaving the block terminates the pool
         with ctx.Pool(len(blocks)) as pool:
-            pool.map_async(_oracle_estep_rows, [(0, 8)] * len(blocks)).get(timeout=120)  # start-up, untimed
+            pool.map_async(_oracle_estep_rows, [(0, 8, PASS_B_SHARED)] * len(blocks)).get(timeout=120)  # start-up
             t0 = time.perf_counter()
             pool.map_async(_oracle_estep_rows, blocks).get(timeout=120)
             dt = time.perf_counter() - t0
@@ -358,7 +368,7 @@ def fp32_error_vs_oracle(ref, lat, stream):
         S = O.mstep_sums(Ys, E["tau"], E["e1"], E["e2"], E["e3"], E["e4"])
         P1 = O.mstep_update(S, init, Ys.shape[0])
     Yd = torch.from_numpy(Ys).cuda()
-    with binding.Context(lat, precision=binding.CFUST_FP32, stream=stream) as ctx:
+    with binding.Context(lat, precision=binding.CFUST_FP32, stream=stream, shared_points=PASS_B_SHARED) as ctx:
         G = ctx.cfust_estep(Yd, init)
         P1g = ctx.cfust_mstep(Yd, G, init)
     r = init.r
@@ -407,13 +417,13 @@ def fp64_mode_rate(Y, init, lat, stream, rows=20000):
 def _oracle_estep_block(args):
     """One spawned worker: the oracle's E-step of rows [j0, j1) of a named
     workload (module-level so a spawned process can import it)."""
-    name, j0, j1 = args
+    name, j0, j1, shared = args
     from oracle import cfust_oracle as O
     from paper_2005_06848_gb300 import synth
     Y, _, _, init, lat, _ = synth.workload(name)
     U = O.lattice_points(lat.n, lat.z, lat.shift)
     t0 = time.perf_counter()
-    E = O.estep(Y[j0:j1], init, U)
+    E = O.estep(Y[j0:j1], init, U, shared=shared)
     return E, time.perf_counter() - t0
 
 
@@ -424,10 +434,10 @@ def oracle_estep_pool(name, rows):
     import multiprocessing as mp
     cores = max(1, min(os.cpu_count() or 1, rows))
     edges = [rows * k // cores for k in range(cores + 1)]
-    blocks = [(name, edges[k], edges[k + 1]) for k in range(cores) if edges[k + 1] > edges[k]]
+    blocks = [(name, edges[k], edges[k + 1], PASS_B_SHARED) for k in range(cores) if edges[k + 1] > edges[k]]
     ctx = mp.get_context("spawn")
     with ctx.Pool(len(blocks)) as pool:
-        pool.map_async(_oracle_estep_block, [(name, 0, 4)] * len(blocks)).get(timeout=300)  # start-up, untimed
+        pool.map_async(_oracle_estep_block, [(name, 0, 4, PASS_B_SHARED)] * len(blocks)).get(timeout=300)  # start-up
         t0 = time.perf_counter()
         parts = pool.map_async(_oracle_estep_block, blocks).get(timeout=900)
         wall = time.perf_counter() - t0
@@ -454,7 +464,7 @@ def large_line(args, steps, warmup):
     stream = torch.cuda.current_stream()
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
     ctx = binding.Context(lat, precision=binding.CFUST_FP32, max_iter=warmup + steps + 1, use_graph=True,
-                          timing=True, stream=stream)
+                          timing=True, stream=stream, shared_points=PASS_B_SHARED)
     sampler = ClockSampler(torch.cuda.current_device())
     sampler.start()
     time.sleep(0.4)
@@ -462,13 +472,27 @@ def large_line(args, steps, warmup):
     clocks = sampler.stop()
     ctx.close()
     pairs = n * g
-    fused = fused_comparison(torch, binding, Yd, init, lat, steps, warmup, flush, float(np.mean(ms)), params,
-                             pairs, peak_fp32_tflops((load_peaks() or {}).get("sm_max_mhz", 2070.0), sm_count()), r)
+    peak0 = peak_fp32_tflops((load_peaks() or {}).get("sm_max_mhz", 2070.0), sm_count())
+    two_pass, tp_ms, tp_params = None, float(np.mean(ms)), params
+    if PASS_B_SHARED:
+        # the separate pass-B sweep on the same fit (and the fused pass's reference)
+        ctx = binding.Context(lat, precision=binding.CFUST_FP32, max_iter=warmup + steps + 1, use_graph=True,
+                              timing=True, stream=stream)
+        ms2, kern2, tp_params = _timed_em(torch, ctx, Yd, init, steps, warmup, flush)
+        ctx.close()
+        tp_ms = float(np.mean(ms2))
+        ach2 = pairs * lat.n * sweep_flops_per_point(r) / (float(np.mean(kern2)) / 1e3) / 1e12
+        two_pass = {"ms_per_step": tp_ms, "value": pairs / (tp_ms / 1e3), "unit": UNIT,
+                    "em_iters_per_s": 1e3 / tp_ms, "sweep_ms_mean": float(np.mean(kern2)),
+                    "roofline": {"achieved": ach2, "peak": peak0, "frac": ach2 / peak0,
+                                 "flops_per_point": sweep_flops_per_point(r)},
+                    "params_max_rel_diff_vs_shared": _max_rel_diff(tp_params, params)}
+    fused = fused_comparison(torch, binding, Yd, init, lat, steps, warmup, flush, tp_ms, tp_params, pairs, peak0, r)
     step_s = float(np.mean(ms)) / 1e3
     sweep_ms = float(np.mean(kern))
     peaks = load_peaks() or {}
     sm_max = peaks.get("sm_max_mhz", 2070.0)
-    flops = pairs * lat.n * sweep_flops_per_point(r)
+    flops = pairs * lat.n * sweep_flops_per_point(r, shared=PASS_B_SHARED)
     achieved = flops / (sweep_ms / 1e3) / 1e12
     peak = peak_fp32_tflops(sm_max, sm_count())
     rows = args.c5_oracle_rows
@@ -481,7 +505,9 @@ def large_line(args, steps, warmup):
         "step": "one EM iteration (CUDA graph replay), L2 flushed between timed steps",
         "roofline": {"bound": "alu", "kernel": "estep_kernel<float,4>", "achieved": achieved, "peak": peak,
                      "unit": "TFLOP/s", "frac": achieved / peak, "sweep_ms_mean": sweep_ms,
-                     "flops_per_point": sweep_flops_per_point(r)},
+                     "flops_per_point": sweep_flops_per_point(r, shared=PASS_B_SHARED)},
+        "pass_b": "on pass A's lattice points" if PASS_B_SHARED else "its own lattice sweep",
+        "two_pass": two_pass,
         "oracle": {"value": rows * g / wall, "unit": UNIT, "cores": cores, "kind": "oracle",
                    "sample": f"first {rows} of {n} observations x {g} components, E-step, one spawned "
                              f"process per core, {wall:.1f} s wall"},
@@ -512,7 +538,7 @@ def run_reference(args):
     times = []
     for k in range(args.warmup + args.steps):
         t0 = time.perf_counter()
-        E = O.estep(Ys, params, U)
+        E = O.estep(Ys, params, U, shared=PASS_B_SHARED)
         S = O.mstep_sums(Ys, E["tau"], E["e1"], E["e2"], E["e3"], E["e4"])
         params = O.mstep_update(S, params, rows)
         if k >= args.warmup:
@@ -562,7 +588,8 @@ def run_sharded(args):
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
     red = sharded.torch_allreduce(torch.device("cuda", local))
     P = init
-    ctx = binding.Context(lat, precision=binding.CFUST_FP32, timing=True, stream=stream)
+    ctx = binding.Context(lat, precision=binding.CFUST_FP32, timing=True, stream=stream,
+                          shared_points=PASS_B_SHARED)
     for _ in range(args.warmup):
         flush.zero_()
         P, _ = sharded.em_iteration(ctx, Yd, P, n_total, red)
@@ -604,7 +631,7 @@ def run_sharded(args):
     peaks = load_peaks() or {}
     sm_max = peaks.get("sm_max_mhz", 2070.0)
     sweep_ms = float(np.mean(sweep))
-    flops = pairs_rank * lat.n * sweep_flops_per_point(r)
+    flops = pairs_rank * lat.n * sweep_flops_per_point(r, shared=PASS_B_SHARED)
     achieved = flops / (sweep_ms / 1e3) / 1e12
     peak = peak_fp32_tflops(sm_max, sm_count())
     K = 3 + p + r + p * r + r * (r + 1) // 2 + p * (p + 1) // 2
@@ -624,7 +651,7 @@ def run_sharded(args):
             "gpu_launches": 8 * args.steps,
             "roofline": {"bound": "alu", "kernel": "estep_kernel<float,4>", "achieved": achieved, "peak": peak,
                          "unit": "TFLOP/s", "frac": achieved / peak, "traffic": None,
-                         "sweep_ms_mean": sweep_ms, "flops_per_point": sweep_flops_per_point(r)},
+                         "sweep_ms_mean": sweep_ms, "flops_per_point": sweep_flops_per_point(r, shared=PASS_B_SHARED)},
             "sm_count": sm_count(),
             "clocks": clocks,
             "e2e": {"value": ws * pairs_rank * 3 / float(e2e_s.item()), "unit": UNIT,
@@ -654,8 +681,9 @@ def run_ours(args):
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
     total_iters = args.warmup + args.steps
 
+    shared = PASS_B_SHARED and not args.fused
     ctx = binding.Context(lat, precision=binding.CFUST_FP32, max_iter=total_iters, use_graph=True,
-                          timing=True, stream=stream, fused=args.fused, shared_points=args.shared)
+                          timing=True, stream=stream, fused=args.fused, shared_points=shared)
     ctx.cfust_fit_begin(Yd, init)
     for _ in range(args.warmup):
         flush.zero_()
@@ -696,13 +724,13 @@ def run_ours(args):
 
     # roofline of the sweep kernel (the E-step's dominant kernel)
     mean_sweep_ms = float(np.mean(sweep_ms))
-    flops = pairs_per_step * lat.n * sweep_flops_per_point(r, shared=args.shared)
+    flops = pairs_per_step * lat.n * sweep_flops_per_point(r, shared=shared)
     achieved = flops / (mean_sweep_ms / 1e3) / 1e12
     peaks = load_peaks()
     sm_max = (peaks or {}).get("sm_max_mhz", 2070.0)
     sms = sm_count()
     peak = peak_fp32_tflops(sm_max, sms)
-    prof = (sweep_profile() or {}) if not (args.shared or args.fused) else {}
+    prof = (sweep_profile(shared) or {}) if not args.fused else {}
 
     # end-to-end through the public API: every step copies Y from pinned host
     # memory into the bound device buffer, runs one EM iteration, and reads the
@@ -714,7 +742,7 @@ def run_ours(args):
         Ye.copy_(Yh)
         e2e_steps = max(3, min(args.steps, 10))
         ctx2 = binding.Context(lat, precision=binding.CFUST_FP32, max_iter=2 + e2e_steps, use_graph=True,
-                               stream=stream, fused=args.fused, shared_points=args.shared)
+                               stream=stream, fused=args.fused, shared_points=shared)
         ctx2.cfust_fit_begin(Ye, init)
         for _ in range(2):
             Ye.copy_(Yh, non_blocking=True)
@@ -739,6 +767,13 @@ def run_ours(args):
         if ws > 1:
             torch.distributed.destroy_process_group()
         return 0
+    other_rule, two_pass_ms, two_pass_params = None, total_ms / args.steps, params
+    if ws == 1 and not args.fused and not args.no_extras:
+        other_rule, o_ms, o_params = pass_b_comparison(torch, binding, synth, Yd, init, lat, args.steps,
+                                                        args.warmup, flush, total_ms / args.steps, params,
+                                                        pairs_per_step, peak, r, stream, not shared)
+        if shared:
+            two_pass_ms, two_pass_params = o_ms, o_params
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
@@ -747,7 +782,7 @@ def run_ours(args):
         "config": {"workload": WORKLOAD, "n": n, "g": g, "p": p, "r": r, "lattice_points": lat.n,
                    "precision": "FP32 lattice sweeps; FP64 prologue, factorisations, log-likelihood, M-step",
                    "step": "one EM iteration (CUDA graph replay)", "l2": "flushed between timed steps",
-                   "pass_b": "on pass A's lattice points" if args.shared else "its own lattice sweep",
+                   "pass_b": "on pass A's lattice points" if shared else "its own lattice sweep",
                    "parallelism": f"independent fits, {ws} rank(s)"},
         "em_iters_per_s": iters_per_s,
         "rescued_pairs_last_estep": rescued,
@@ -755,14 +790,14 @@ def run_ours(args):
         "gpu_launches": 6 * args.steps,
         "roofline": {"bound": "alu", "kernel": "fused_em_kernel<float,4>" if args.fused else "estep_kernel<float,4>",
                      "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
-                     "traffic": None if (args.shared or args.fused) else sweep_traffic_bytes(),
+                     "traffic": None if args.fused else sweep_traffic_bytes(shared),
                      "peak_source": f"FP32 FMA peak {sms} SMs x 128 lanes x 2 x {sm_max:.0f} MHz "
                                     "(derived from unit counts and the maximum SM clock)",
                      "sweep_ms_mean": mean_sweep_ms,
                      "flops_per_launch": flops,
-                     "flops_per_point": sweep_flops_per_point(r, shared=args.shared),
+                     "flops_per_point": sweep_flops_per_point(r, shared=shared),
                      "count": (f"per point: r Phi x {PHI_FLOPS} + r Phi^-1 x {PHIINV_FLOPS} + r(r-1)/2 "
-                               "conditional FMAs + (r + r(r+1)/2) moment FMAs, FMA = 2 flops" if args.shared else
+                               "conditional FMAs + (r + r(r+1)/2) moment FMAs, FMA = 2 flops" if shared else
                                f"per point: 2r Phi x {PHI_FLOPS} + (2r-1) Phi^-1 x {PHIINV_FLOPS} "
                                "+ r(r-1) conditional FMAs + (r + r(r+1)/2) moment FMAs, FMA = 2 flops"),
                      "ncu": {k: prof[k] for k in ("fma_pipe_pct", "xu_pipe_pct", "issue_active_pct",
@@ -778,14 +813,12 @@ def run_ours(args):
         # + the per-block partial sums written once; the kernel is bound by
         # its double-precision-accurate arithmetic, not by these bytes
         "mstep": mstep_roofline(n, g, p, r, float(np.mean(mstep_ms)), peaks, sms) if mstep_ms else None,
-        # the fused E-step + M-step-sums pass on the same fit
+        # the other pass-B rule on the same fit, and the fused E-step +
+        # M-step-sums pass (two passes) against the unfused two-pass fit
+        "two_pass" if shared else "shared_points": other_rule,
         "fused": fused_comparison(torch, binding, Yd, init, lat, args.steps, args.warmup, flush,
-                                  total_ms / args.steps, params, pairs_per_step, peak, r)
-        if ws == 1 and not args.fused and not args.no_extras else None,
-        # pass B on pass A's lattice points on the same fit
-        "shared_points": shared_comparison(torch, binding, synth, Yd, init, lat, args.steps, args.warmup, flush,
-                                           total_ms / args.steps, params, pairs_per_step, peak, r, stream)
-        if ws == 1 and not args.fused and not args.shared and not args.no_extras else None,
+                                  two_pass_ms, two_pass_params, pairs_per_step, peak, r)
+        if other_rule is not None else None,
         "clocks": clocks,
         "e2e": e2e,
     }
@@ -974,22 +1007,23 @@ def _fit_memory(torch, binding, Yd, P, lat, fused):
     return int(held)
 
 
-def shared_comparison(torch, binding, synth, Yd, P, lat, steps, warmup, flush, two_pass_ms, two_pass_params,
-                      pairs, peak, r, stream):
-    """Pass B on pass A's lattice points (cfust_opts.shared_points) on the
-    same fit as the two-pass line: time per EM iteration, the sweep kernel
-    against the FP32 peak (the shared rule's own count), how far the fitted
-    parameters are from the two-pass fit after the same iterations, and the
-    accuracy of both rules' E-step outputs against the 65536-point two-pass rule
-    in prioritised order (l is pass A's and identical; e1 and e3 tau-weighted
-    relative RMS over the pairs)."""
+def pass_b_comparison(torch, binding, synth, Yd, P, lat, steps, warmup, flush, line_ms, line_params,
+                      pairs, peak, r, stream, shared):
+    """The other pass-B rule on the same fit as the line: pass B on pass A's
+    lattice points (``shared``, cfust_opts.shared_points) or as its own sweep.
+    Time per EM iteration, its sweep kernel against the FP32 peak (the rule's
+    own count), the fitted parameters' distance from the line's after the same
+    iterations, and both rules' E-step accuracy against the 65536-point
+    two-pass rule in prioritised order (l is pass A's, the same in both; e1 and
+    e3 as tau-weighted relative RMS over the pairs).  Returns (the comparison,
+    the rule's mean ms per iteration, its fitted parameters)."""
     ctx = binding.Context(lat, precision=binding.CFUST_FP32, max_iter=warmup + steps + 1, use_graph=True,
-                          timing=True, shared_points=True)
+                          timing=True, shared_points=shared)
     ms, kern, params = _timed_em(torch, ctx, Yd, P, steps, warmup, flush)
     ctx.close()
     step_ms = float(np.mean(ms))
     kern_ms = float(np.mean(kern))
-    flops = pairs * lat.n * sweep_flops_per_point(r, shared=True)
+    flops = pairs * lat.n * sweep_flops_per_point(r, shared=shared)
     achieved = flops / (kern_ms / 1e3) / 1e12
     errs = {}
     with binding.Context(synth.make_lattice(1 << 16, r + 1, 0), precision=binding.CFUST_FP32, prioritise=True,
@@ -1002,23 +1036,45 @@ def shared_comparison(torch, binding, synth, Yd, P, lat, steps, warmup, flush, t
         d = torch.where(torch.isfinite(d), d, torch.zeros_like(d))
         w = tau if d.dim() == 2 else tau[:, None, :]
         return float((w * d * d).sum() / w.expand_as(d).sum()) ** 0.5
-    for shared in (False, True):
-        with binding.Context(lat, precision=binding.CFUST_FP32, shared_points=shared, stream=stream) as c:
+    for sh in (False, True):
+        with binding.Context(lat, precision=binding.CFUST_FP32, shared_points=sh, stream=stream) as c:
             E = c.cfust_estep(Yd, P)
-            errs["shared" if shared else "two_pass"] = {
+            errs["shared_points" if sh else "two_pass"] = {
                 "loglik_error": float(E["loglik"] - J["loglik"]),
                 "e1_rel_rms_tau_weighted": rel_rms(E["e1"], J["e1"]),
                 "e3_rel_rms_tau_weighted": rel_rms(E["e3"], J["e3"])}
-    return {
+    # the fitted parameters of both rules against the same iterations of a
+    # 65536-point two-pass fit in prioritised order from the same start
+    with binding.Context(synth.make_lattice(1 << 16, r + 1, 0), precision=binding.CFUST_FP32, prioritise=True,
+                         max_iter=warmup + steps + 1, use_graph=True, timing=True, stream=stream) as cj:
+        _, _, judge_params = _timed_em(torch, cj, Yd, P, steps, warmup, flush)
+    fit_err = {("shared_points" if shared else "two_pass"): _rel_diff_by_name(params, judge_params),
+               ("two_pass" if shared else "shared_points"): _rel_diff_by_name(line_params, judge_params)}
+    out = {
+        "pass_b": "on pass A's lattice points" if shared else "its own lattice sweep",
         "ms_per_step": step_ms, "value": pairs / (step_ms / 1e3), "unit": UNIT,
-        "em_iters_per_s": 1e3 / step_ms, "two_pass_ms_per_step": two_pass_ms,
-        "speed_vs_two_pass": two_pass_ms / step_ms,
-        "kernel": "estep_kernel<float,%d,shared points>" % r, "kernel_ms_mean": kern_ms,
+        "em_iters_per_s": 1e3 / step_ms, "line_ms_per_step": line_ms,
+        "speed_vs_line": line_ms / step_ms,
+        "kernel": "estep_kernel<float,%d>" % r, "kernel_ms_mean": kern_ms,
         "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
-                     "flops_per_point": sweep_flops_per_point(r, shared=True)},
-        "params_max_rel_diff_vs_two_pass": _max_rel_diff(params, two_pass_params),
+                     "flops_per_point": sweep_flops_per_point(r, shared=shared)},
+        "params_max_rel_diff_vs_line": _max_rel_diff(params, line_params),
+        "params_max_rel_diff_vs_65536_point_fit": fit_err,
         "accuracy": {"judge": "65536-point lattice, two passes, prioritised order, FP32", **errs},
     }
+    return out, step_ms, params
+
+
+def _rel_diff_by_name(a_params, b_params):
+    """Largest |a - b| of each parameter array over the array's largest |b|."""
+    out = {}
+    for name, a, b in zip(("pi", "mu", "Sigma", "Delta", "nu"), a_params.as_arrays(), b_params.as_arrays()):
+        a = np.asarray(a, dtype=np.float64)
+        b = np.asarray(b, dtype=np.float64)
+        fin = np.isfinite(b)
+        if fin.any():
+            out[name] = float(np.max(np.abs(a[fin] - b[fin]))) / max(float(np.max(np.abs(b[fin]))), 1e-300)
+    return out
 
 
 def _max_rel_diff(a_params, b_params):
@@ -1187,14 +1243,17 @@ def surrogate_line(args, steps, warmup):
     time.sleep(0.4)
     # the first EM iteration from the start, where the accuracies were judged
     ms_s, kern_s = _timed_first_iteration(torch, ctx_s, Yd, init, steps, flush)
+    # the plain rule at equal accuracy runs the bench's pass-B rule (its
+    # log-likelihood is pass A's under either rule)
     ctx_p = binding.Context(synth.make_lattice(n_eq, 4, seed=0), precision=binding.CFUST_FP32,
-                            max_iter=warmup + steps + 1, use_graph=True, timing=True, triage_nats=tn)
+                            max_iter=warmup + steps + 1, use_graph=True, timing=True, triage_nats=tn,
+                            shared_points=PASS_B_SHARED)
     ms_p, kern_p = _timed_first_iteration(torch, ctx_p, Yd, init, steps, flush)
     ms_q = None
     if n_eq_p is not None:
         ctx_q = binding.Context(synth.make_lattice(n_eq_p, 4, seed=0), precision=binding.CFUST_FP32,
                                 max_iter=warmup + steps + 1, use_graph=True, timing=True,
-                                triage_nats=tn, prioritise=True)
+                                triage_nats=tn, prioritise=True, shared_points=PASS_B_SHARED)
         ms_q, _ = _timed_first_iteration(torch, ctx_q, Yd, init, steps, flush)
         ctx_q.close()
     # and consecutive iterations as a fit runs on from it: the parameters move,
@@ -1313,14 +1372,17 @@ def main(argv=None):
                     help="triage margin T (nats) of the surrogate and plain contexts: a listed or rescued "
                          "pair with tau provably below exp(-T) is dropped, moving l by at most exp(-T)")
     ap.add_argument("--nfits", type=int, default=256)
-    ap.add_argument("--shared", action="store_true",
-                    help="time the default workload with pass B on pass A's lattice points (cfust_opts.shared_points)")
+    ap.add_argument("--two-pass", action="store_true",
+                    help="time pass B as its own lattice sweep (the default rule of the library) instead of on "
+                         "pass A's points (cfust_opts.shared_points)")
     ap.add_argument("--fused", action="store_true",
                     help="time the default workload with the fused E-step + M-step-sums kernel (cfust_opts.fused)")
     ap.add_argument("--rows", type=int, default=0,
                     help="observations of the single-fit workload (0: the workload's 100000); for small "
                          "profiling captures only, the bench line is quoted at the default")
     args = ap.parse_args(argv)
+    global PASS_B_SHARED
+    PASS_B_SHARED = not args.two_pass
     if args.warmup < 3:
         args.warmup = 3
     if args.impl == "reference":

@@ -141,8 +141,9 @@ typedef struct {
                              half the normal-function work); log f and l are pass A's, unchanged, and
                              e1..e4 move within the rule's error.  0 keeps the two separate sweeps.
                              Taken by cfust_estep, cfust_loglik and the single-fit paths in both
-                             precisions; prioritise = 1 or fused = 1 with it fail at cfust_create, and
-                             a surrogate or cfust_fit_batched with it fail with CFUST_EINVAL. */
+                             precisions, in natural or prioritised order; fused = 1 with it fails at
+                             cfust_create, and a surrogate or cfust_fit_batched with it fail with
+                             CFUST_EINVAL. */
 } cfust_opts;
 
 typedef struct cfust_ctx cfust_ctx;

@@ -551,8 +551,8 @@ cfust_status cfust_create(cfust_ctx **out, const cfust_opts *o, void *cuda_strea
     g_create_error = "shared_points must be 0 or 1";
     return CFUST_EINVAL;
   }
-  if (o->shared_points && (o->prioritise || o->fused)) {
-    g_create_error = "shared_points runs the natural order in the unfused sweep: prioritise and fused must be 0";
+  if (o->shared_points && o->fused) {
+    g_create_error = "shared_points runs in the unfused sweep: fused must be 0";
     return CFUST_EINVAL;
   }
   cfust_ctx *c = new cfust_ctx();

@@ -246,11 +246,13 @@ cudaError_t launch_r(EArgs a, int g, int64_t n, cudaStream_t st, bool fp32,
   // the prioritised sweep is its own instantiation (r >= 2), so the default
   // one carries none of its registers
   const bool prio = a.prio && R >= 2;
-  // pass B on pass A's points: its own instantiation (full sweeps, natural order)
-  const bool shr = a.shr && !DENS && !prio;
-  cudaError_t e = prio  ? raise_smem_limit((const void *)estep_kernel<T, R, DENS, (R >= 2)>, smem)
-                  : shr ? raise_smem_limit((const void *)estep_kernel<T, R, DENS, false, !DENS>, smem)
-                        : raise_smem_limit((const void *)estep_kernel<T, R, DENS, false>, smem);
+  // pass B on pass A's points: its own instantiations (full sweeps)
+  const bool shr = a.shr && !DENS;
+  const void *kern = prio ? (shr ? (const void *)estep_kernel<T, R, DENS, (R >= 2), !DENS>
+                                 : (const void *)estep_kernel<T, R, DENS, (R >= 2)>)
+                          : (shr ? (const void *)estep_kernel<T, R, DENS, false, !DENS>
+                                 : (const void *)estep_kernel<T, R, DENS, false>);
+  cudaError_t e = raise_smem_limit(kern, smem);
   if (e != cudaSuccess) return e;
   const int64_t per_cta = (int64_t)a.ppw * 8;
   const int64_t bx = (n + per_cta - 1) / per_cta;
@@ -265,7 +267,9 @@ cudaError_t launch_r(EArgs a, int g, int64_t n, cudaStream_t st, bool fp32,
     e = cudaEventRecordWithFlags(tm.start, st, evflag);
     if (e != cudaSuccess) return e;
   }
-  if (prio)
+  if (prio && shr)
+    estep_kernel<T, R, DENS, (R >= 2), !DENS><<<grid, 256, smem, st>>>(a);
+  else if (prio)
     estep_kernel<T, R, DENS, (R >= 2)><<<grid, 256, smem, st>>>(a);
   else if (shr)
     estep_kernel<T, R, DENS, false, !DENS><<<grid, 256, smem, st>>>(a);

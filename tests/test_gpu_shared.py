@@ -25,18 +25,19 @@ def _torch():
     return torch
 
 
-def _gpu(Y, params, lat, precision, shared=True, e2_mode=0):
+def _gpu(Y, params, lat, precision, shared=True, e2_mode=0, prioritise=False):
     torch = _torch()
-    with binding.Context(lat, precision=precision, e2_mode=e2_mode, shared_points=shared) as ctx:
+    with binding.Context(lat, precision=precision, e2_mode=e2_mode, shared_points=shared,
+                         prioritise=prioritise) as ctx:
         out = ctx.cfust_estep(torch.from_numpy(Y).cuda(), params)
         res = {k: (v.double().cpu().numpy() if hasattr(v, "cpu") else v) for k, v in out.items()}
         res["rescued"] = ctx.cfust_last_rescued()
     return res
 
 
-def _oracle(Y, params, lat, e2_mode=0):
+def _oracle(Y, params, lat, e2_mode=0, prioritise=False):
     U = O.lattice_points(lat.n, lat.z, lat.shift)
-    return O.estep(Y, params, U, e2_mode, shared=True)
+    return O.estep(Y, params, U, e2_mode, prioritise=prioritise, shared=True)
 
 
 @pytest.mark.parametrize("precision", [binding.CFUST_FP64, binding.CFUST_FP32])
@@ -145,16 +146,25 @@ def test_shared_fit_matches_oracle_fit(precision):
         assert max(errs.values()) <= 1e-3, errs
 
 
+@pytest.mark.parametrize("precision", [binding.CFUST_FP64, binding.CFUST_FP32])
+@pytest.mark.parametrize("case", CASES[1:], ids=[c[0].split("_n")[0] for c in CASES[1:]])
+def test_shared_prioritised_estep_matches_oracle(case, precision):
+    """Variable prioritisation with pass B on pass A's points: each pair's
+    chain in its own order serves both passes, the moments scattered back."""
+    wl, n, N = case
+    Y, truth, init, lat = _problem(wl, n, N)
+    _compare_estep(_gpu(Y, init, lat, precision, prioritise=True), _oracle(Y, init, lat, prioritise=True),
+                   init.r, precision == binding.CFUST_FP64)
+
+
 def test_shared_refusals():
-    """The shared rule runs the natural order in the unfused single-fit sweep:
-    with prioritise or fused it is refused at create, and a surrogate or a
-    batched fit refuses it when called."""
+    """The shared rule runs in the unfused single-fit sweep: with fused it is
+    refused at create, and a surrogate or a batched fit refuses it when called."""
     torch = _torch()
     Y, truth, init, lat = _problem("cfust_p3r3g4_n1000000_N2048", 64, 256)
-    for kw in (dict(prioritise=True), dict(fused=True)):
-        with pytest.raises(binding.CfustError) as ei:
-            binding.Context(lat, precision=binding.CFUST_FP32, shared_points=True, **kw)
-        assert ei.value.status == -1
+    with pytest.raises(binding.CfustError) as ei:
+        binding.Context(lat, precision=binding.CFUST_FP32, shared_points=True, fused=True)
+    assert ei.value.status == -1
     sur = binding.Surrogate(synth.make_lattice(1024, 4, seed=1), seed=2)
     with binding.Context(lat, precision=binding.CFUST_FP32, shared_points=True) as ctx:
         ctx.cfust_set_surrogate(sur)
@@ -163,3 +173,7 @@ def test_shared_refusals():
         assert ei.value.status == -1
         ctx.cfust_set_surrogate(None)
     sur.close()
+    with binding.Context(lat, precision=binding.CFUST_FP32, shared_points=True, max_iter=2) as ctx:
+        with pytest.raises(binding.CfustError) as ei:
+            ctx.cfust_fit_batched([torch.from_numpy(Y).cuda()], [init])
+        assert ei.value.status == -1
