@@ -916,10 +916,12 @@ def batched_line(args, steps, warmup):
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
     # warm-up call: autotune, buffers, graph capture
     with binding.Context(lat, precision=binding.CFUST_FP32, max_iter=warmup, autotune=True,
+                         shared_points=PASS_B_SHARED,
                          stream=stream) as ctx:
         ctx.cfust_fit_batched(Yd, inits)
         ppw, cps = ctx.cfust_batched_shape()
     ctx = binding.Context(lat, precision=binding.CFUST_FP32, max_iter=steps, pairs_per_warp=ppw,
+                          shared_points=PASS_B_SHARED,
                           stream=stream)
     ctx.cfust_fit_batched(Yd, inits)            # buffers + graph for this iteration count
     flush.zero_()
@@ -1216,6 +1218,7 @@ def surrogate_line(args, steps, warmup):
 
     tn = args.sg_triage
     ctx_s = binding.Context(synth.make_lattice(args.sg_fallback_n, 4, seed=0), precision=binding.CFUST_FP32,
+                            shared_points=PASS_B_SHARED,
                             max_iter=warmup + steps + 1, use_graph=True, timing=True, triage_nats=tn)
     ctx_s.cfust_set_surrogate(sur)
     l_sur, _ = _loglik_ms(torch, ctx_s, Yd, init)
@@ -1269,6 +1272,7 @@ def surrogate_line(args, steps, warmup):
     Ye = torch.empty_like(Yd)
     Ye.copy_(Yh)
     ctx_e = binding.Context(synth.make_lattice(args.sg_fallback_n, 4, seed=0), precision=binding.CFUST_FP32,
+                            shared_points=PASS_B_SHARED,
                             max_iter=12, use_graph=True, triage_nats=tn)
     ctx_e.cfust_set_surrogate(sur)
     ctx_e.cfust_fit_begin(Ye, init)

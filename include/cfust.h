@@ -140,10 +140,10 @@ typedef struct {
                              same integrals with one conditional chain per point instead of two (about
                              half the normal-function work); log f and l are pass A's, unchanged, and
                              e1..e4 move within the rule's error.  0 keeps the two separate sweeps.
-                             Taken by cfust_estep, cfust_loglik and the single-fit paths in both
-                             precisions, in natural or prioritised order; fused = 1 with it fails at
-                             cfust_create, and a surrogate or cfust_fit_batched with it fail with
-                             CFUST_EINVAL. */
+                             Taken by every lattice sweep in both precisions and either variable order:
+                             cfust_estep, cfust_loglik, the single and batched fits, and the pairs a
+                             surrogate leaves to the lattice rule.  The fused pass keeps the two
+                             sweeps: fused = 1 with it fails at cfust_create. */
 } cfust_opts;
 
 typedef struct cfust_ctx cfust_ctx;

@@ -398,8 +398,6 @@ cfust_status run_estep(cfust_ctx *c, const double *Y, int64_t n, EstepOut o, boo
                             (float)c->opts.triage_nats, c->opts.prioritise, c->opts.shared_points));
     return CFUST_OK;
   }
-  if (c->opts.shared_points)
-    return fail(c, CFUST_EINVAL, "shared_points covers the lattice rule alone: detach the surrogate");
   if (c->opts.precision != CFUST_FP32 || c->opts.e2_mode != 0 || c->r != 3)
     return fail(c, CFUST_EINVAL, "the surrogate E-step needs CFUST_FP32, e2_mode 0 and r = 3");
   const unsigned evflag = tm.capturing ? cudaEventRecordExternal : cudaEventRecordDefault;
@@ -410,7 +408,7 @@ cfust_status run_estep(cfust_ctx *c, const double *Y, int64_t n, EstepOut o, boo
   CF_CUDA(c, launch_estep_list(Y, n, c->g, c->p, c->r, c->lat, c->d_c64, c->d_c32, c->d_chi64, c->d_chi32, o,
                                density_only, c->opts.e2_mode, c->d_fb, c->d_fb_cnt, c->d_rescue,
                                c->d_rescue_cnt, c->d_status, st, triage, pi, (float)c->opts.triage_nats,
-                               c->opts.prioritise));
+                               c->opts.prioritise, c->opts.shared_points));
   return CFUST_OK;
 }
 
@@ -1068,7 +1066,8 @@ cfust_status enqueue_batch_estep(cfust_ctx *c, cudaStream_t st, bool density_onl
   CF_CUDA(c, launch_estep_batched(c->opts.precision, d, b.p, b.r, c->lat, b.c64, b.c32, b.chi64, b.chi32,
                                   b.d_items, b.nitems, b.counter, density_only, c->opts.e2_mode, b.ppw, b.cps,
                                   b.rescue, b.rescue_cnt, b.status, 1, st,
-                                  sweep_timing(c, st == c->cap_stream), c->opts.prioritise));
+                                  sweep_timing(c, st == c->cap_stream), c->opts.prioritise,
+                                  c->opts.shared_points));
   return CFUST_OK;
 }
 
@@ -1106,7 +1105,7 @@ cfust_status autotune_batch(cfust_ctx *c) {
         CF_CUDA(c, launch_estep_batched(c->opts.precision, d, b.p, b.r, c->lat, b.c64, b.c32, b.chi64, b.chi32,
                                         b.d_items, b.nitems, b.counter, false, c->opts.e2_mode, ppw, cps,
                                         b.rescue, b.rescue_cnt, b.status, 1, c->stream, SweepTiming(),
-                                        c->opts.prioritise));
+                                        c->opts.prioritise, c->opts.shared_points));
         CF_CUDA(c, cudaEventRecord(e1, c->stream));
         CF_CUDA(c, cudaEventSynchronize(e1));
         CF_CUDA(c, cudaEventElapsedTime(&ms, e0, e1));
@@ -1138,7 +1137,6 @@ extern "C" cfust_status cfust_fit_batched(cfust_ctx *c, int nfits, const double 
                                          cfust_params *P, double *trace_out, int *fit_status_out) {
   if (!c) return CFUST_EINVAL;
   if (nfits < 1 || !Y || !n || !P) return fail(c, CFUST_EINVAL, "nfits >= 1 with Y, n and params required");
-  if (c->opts.shared_points) return fail(c, CFUST_EINVAL, "batched fits take the two-pass rule: shared_points must be 0");
   DeviceGuard dg(c->device);
   const int p = P[0].p, r = P[0].r;
   for (int f = 0; f < nfits; ++f) {

@@ -160,7 +160,7 @@ cudaError_t launch_estep_list(const double *Y, int64_t n, int g, int p, int r, c
                               const float *chi32, EstepOut out, bool density_only, int e2_mode,
                               const int *list, const unsigned *count, unsigned long long *rescue_list,
                               unsigned *rescue_count, int *d_status, cudaStream_t st, int triage,
-                              const double *d_pi, float tnats = 30.f, int prio = 0);
+                              const double *d_pi, float tnats = 30.f, int prio = 0, int shared = 0);
 
 // Device view of a trained surrogate network (owned by cfust_surrogate):
 // packed BF16 weights W1 [16][128], W2, W3 [128][128], W4 [128][16] (input x
@@ -293,7 +293,7 @@ cudaError_t launch_estep_batched(int precision, const BatchDev &b, int p, int r,
                                  unsigned *item_counter, bool density_only, int e2_mode, int ppw,
                                  int ctas_per_sm, unsigned long long *rescue_list, unsigned *rescue_count,
                                  int *d_status, int triage, cudaStream_t st, SweepTiming tm = SweepTiming(),
-                                 int prio = 0);
+                                 int prio = 0, int shared = 0);
 
 cudaError_t launch_posterior_batched(int precision, const BatchDev &b, int p, int r, const BlockRef *blocks,
                                      int nblocks, double *partials, double *ll_partials, bool want_sums,

@@ -114,7 +114,7 @@ __device__ bool triage_listed(const FitView &fv, int i, int64_t j, float tnats) 
 // The same sweep over an explicit list of observations per component:
 // list[i * stride + k] for k < count[i] (the pairs a surrogate E-step leaves
 // to the lattice rule).  Warps stride over the list in chunks of ppw.
-template <typename T, int R, bool DENS, bool PRIO = false>
+template <typename T, int R, bool DENS, bool PRIO = false, bool SHR = false>
 __global__ void __launch_bounds__(256, sizeof(T) == 4 ? CFUST_ESTEP_MINB : 1)
     estep_list_kernel(EArgs a, const int *list, const unsigned *count, int64_t stride) {
   extern __shared__ __align__(128) unsigned char smem[];
@@ -159,7 +159,8 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? CFUST_ESTEP_MINB : 1)
       PrioLane<R, T> pp;
       if constexpr (PRIO) pp = shfl_prio<R, T>(pmine, b);
       const int64_t j = __shfl_sync(0xffffffffu, myj, b);
-      const bool need = pair_sweep<T, T, R, DENS, PRIO, 2>(a, fv, *cs, pr, tA, tB, i, j, lane, check, pcs, wpc, &pp);
+      const bool need = pair_sweep<T, T, R, DENS, PRIO, 2, SHR>(a, fv, *cs, pr, tA, tB, i, j, lane, check, pcs, wpc,
+                                                                &pp);
       if (need && lane == 0) {
         const unsigned slot = atomicAdd(a.rescue_count, 1u);
         a.rescue_list[slot] = pair_id(i, j);
@@ -335,7 +336,7 @@ __device__ __forceinline__ FitView batch_view(const BatchDev &b, const FitDesc &
 // constants copied only when the component changes from the CTA's previous
 // item.  Items are ordered component by component, so a CTA mostly stays on
 // one component.  A lost copy ends the whole CTA with ERR_TIMEOUT.
-template <typename T, int R, bool DENS, bool PRIO = false>
+template <typename T, int R, bool DENS, bool PRIO = false, bool SHR = false>
 __global__ void __launch_bounds__(256, sizeof(T) == 4 ? CFUST_ESTEP_MINB : 1)
     estep_batched_kernel(EArgs a, BatchDev b, const SweepItem *items, int nitems, unsigned *counter) {
   extern __shared__ __align__(128) unsigned char smem[];
@@ -405,7 +406,7 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? CFUST_ESTEP_MINB : 1)
     PairedConsts *wpc = nullptr;
     if constexpr (PRIO)
       wpc = reinterpret_cast<PairedConsts *>(reinterpret_cast<unsigned char *>(bar) + 16) + warp;
-    sweep_warp_pairs<T, R, DENS, PRIO>(a, fv, *cs, pcs, tA, tB, cr.i, item.gc, jw0, a.ppw, wpc);
+    sweep_warp_pairs<T, R, DENS, PRIO, SHR>(a, fv, *cs, pcs, tA, tB, cr.i, item.gc, jw0, a.ppw, wpc);
     __syncthreads();
   }
 }
@@ -424,7 +425,7 @@ __global__ void rescue_triage_batched_kernel(EArgs a, BatchDev b, int r) {
   }
 }
 
-template <int R, bool DENS>
+template <int R, bool DENS, bool SHR = false>
 __global__ void __launch_bounds__(256) rescue_batched_kernel(EArgs a, BatchDev b, const CompT<double> *comp,
                                                               const double *chi) {
   constexpr int NV = 3 + R + R * (R + 1) / 2;
@@ -438,7 +439,8 @@ __global__ void __launch_bounds__(256) rescue_batched_kernel(EArgs a, BatchDev b
     const CompRef cr = b.comps[gc];
     const FitDesc fd = b.fits[cr.fit];
     const FitView fv = batch_view<float>(b, fd, a.p, R);
-    rescue_one<R, DENS>(a, fv, comp[gc], chi + (int64_t)gc * 2 * a.N, cr.i, j, (id & RESCUE_DROP) != 0, sm, spr);
+    rescue_one<R, DENS, SHR>(a, fv, comp[gc], chi + (int64_t)gc * 2 * a.N, cr.i, j, (id & RESCUE_DROP) != 0, sm,
+                             spr);
   }
 }
 
@@ -451,16 +453,24 @@ cudaError_t launch_batched_r(EArgs a, const BatchDev &b, const SweepItem *items,
   const bool prio = a.prio && R >= 2;
   const size_t smem = (a.staged ? align16(tab_bytes) : 0) + align16(sizeof(CompT<T>)) +
                       align16(sizeof(PairedConsts)) + 16 + (prio ? 8 * sizeof(PairedConsts) : 0);
-  cudaError_t e = prio ? raise_smem_limit((const void *)estep_batched_kernel<T, R, DENS, (R >= 2)>, smem)
-                       : raise_smem_limit((const void *)estep_batched_kernel<T, R, DENS, false>, smem);
+  const bool shr = a.shr && !DENS;
+  const void *kern = prio ? (shr ? (const void *)estep_batched_kernel<T, R, DENS, (R >= 2), !DENS>
+                                 : (const void *)estep_batched_kernel<T, R, DENS, (R >= 2)>)
+                          : (shr ? (const void *)estep_batched_kernel<T, R, DENS, false, !DENS>
+                                 : (const void *)estep_batched_kernel<T, R, DENS, false>);
+  cudaError_t e = raise_smem_limit(kern, smem);
   if (e != cudaSuccess) return e;
   if ((e = cudaMemsetAsync(counter, 0, sizeof(unsigned), st)) != cudaSuccess) return e;
   if (fp32 && (e = cudaMemsetAsync(a.rescue_count, 0, sizeof(unsigned), st)) != cudaSuccess) return e;
   const unsigned evflag = tm.capturing ? cudaEventRecordExternal : cudaEventRecordDefault;
   if (tm.start && (e = cudaEventRecordWithFlags(tm.start, st, evflag)) != cudaSuccess) return e;
   const unsigned grid = (unsigned)(sm_count() * (ctas_per_sm > 0 ? ctas_per_sm : 2));
-  if (prio)
+  if (prio && shr)
+    estep_batched_kernel<T, R, DENS, (R >= 2), !DENS><<<grid, 256, smem, st>>>(a, b, items, nitems, counter);
+  else if (prio)
     estep_batched_kernel<T, R, DENS, (R >= 2)><<<grid, 256, smem, st>>>(a, b, items, nitems, counter);
+  else if (shr)
+    estep_batched_kernel<T, R, DENS, false, !DENS><<<grid, 256, smem, st>>>(a, b, items, nitems, counter);
   else
     estep_batched_kernel<T, R, DENS, false><<<grid, 256, smem, st>>>(a, b, items, nitems, counter);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
@@ -471,7 +481,10 @@ cudaError_t launch_batched_r(EArgs a, const BatchDev &b, const SweepItem *items,
     const cudaError_t et = cudaGetLastError();
     if (et != cudaSuccess) return et;
   }
-  rescue_batched_kernel<R, DENS><<<sm_count() * 4, 256, 0, st>>>(a, b, c64, chi64);
+  if (shr)
+    rescue_batched_kernel<R, DENS, !DENS><<<sm_count() * 4, 256, 0, st>>>(a, b, c64, chi64);
+  else
+    rescue_batched_kernel<R, DENS><<<sm_count() * 4, 256, 0, st>>>(a, b, c64, chi64);
   return cudaGetLastError();
 }
 
@@ -521,7 +534,8 @@ cudaError_t launch_estep_batched(int precision, const BatchDev &b, int p, int r,
                                  const float *chi32, const SweepItem *items, int nitems,
                                  unsigned *item_counter, bool density_only, int e2_mode, int ppw,
                                  int ctas_per_sm, unsigned long long *rescue_list, unsigned *rescue_count,
-                                 int *d_status, int triage, cudaStream_t st, SweepTiming tm, int prio) {
+                                 int *d_status, int triage, cudaStream_t st, SweepTiming tm, int prio,
+                                 int shared) {
   if (nitems <= 0) return cudaSuccess;
   EArgs a{};
   a.Y = nullptr;
@@ -544,7 +558,7 @@ cudaError_t launch_estep_batched(int precision, const BatchDev &b, int p, int r,
   a.triage = triage ? 1 : 0;
   a.tnats = 30.f;
   a.prio = prio ? 1 : 0;
-  a.shr = 0;
+  a.shr = shared ? 1 : 0;
   a.wait_polls = lat.wait_polls;
   if (precision == CFUST_FP64) {
     a.comp = c64;
@@ -586,8 +600,12 @@ cudaError_t launch_list_r3(EArgs a, int g, int64_t n, const int *list, const uns
   a.staged = tab_bytes <= 160u * 1024u ? 1 : 0;
   const size_t smem = (a.staged ? align16(tab_bytes) : 0) + align16(sizeof(CompT<float>)) +
                       align16(sizeof(PairedConsts)) + 16 + (a.prio ? 8 * sizeof(PairedConsts) : 0);
-  cudaError_t e = a.prio ? raise_smem_limit((const void *)estep_list_kernel<float, 3, DENS, true>, smem)
-                         : raise_smem_limit((const void *)estep_list_kernel<float, 3, DENS, false>, smem);
+  const bool shr = a.shr && !DENS;
+  const void *kern = a.prio ? (shr ? (const void *)estep_list_kernel<float, 3, DENS, true, !DENS>
+                                   : (const void *)estep_list_kernel<float, 3, DENS, true>)
+                            : (shr ? (const void *)estep_list_kernel<float, 3, DENS, false, !DENS>
+                                   : (const void *)estep_list_kernel<float, 3, DENS, false>);
+  cudaError_t e = raise_smem_limit(kern, smem);
   if (e != cudaSuccess) return e;
   // 16 listed pairs per warp chunk: their FP64 prologues and triage tests run
   // lane-parallel, which matters at the small lattices this path serves
@@ -603,8 +621,12 @@ cudaError_t launch_list_r3(EArgs a, int g, int64_t n, const int *list, const uns
   e = cudaMemsetAsync(a.rescue_count, 0, sizeof(unsigned), st);
   if (e != cudaSuccess) return e;
   const dim3 grid((unsigned)(bx < 1 ? 1 : bx), g);
-  if (a.prio)
+  if (a.prio && shr)
+    estep_list_kernel<float, 3, DENS, true, !DENS><<<grid, 256, smem, st>>>(a, list, count, n);
+  else if (a.prio)
     estep_list_kernel<float, 3, DENS, true><<<grid, 256, smem, st>>>(a, list, count, n);
+  else if (shr)
+    estep_list_kernel<float, 3, DENS, false, !DENS><<<grid, 256, smem, st>>>(a, list, count, n);
   else
     estep_list_kernel<float, 3, DENS, false><<<grid, 256, smem, st>>>(a, list, count, n);
   e = cudaGetLastError();
@@ -614,7 +636,10 @@ cudaError_t launch_list_r3(EArgs a, int g, int64_t n, const int *list, const uns
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
   }
-  rescue_kernel<3, DENS><<<sm_count() * 4, 256, 0, st>>>(a, c64, chi64);
+  if (shr)
+    rescue_kernel<3, DENS, !DENS><<<sm_count() * 4, 256, 0, st>>>(a, c64, chi64);
+  else
+    rescue_kernel<3, DENS><<<sm_count() * 4, 256, 0, st>>>(a, c64, chi64);
   return cudaGetLastError();
 }
 
@@ -657,11 +682,11 @@ cudaError_t launch_estep_list(const double *Y, int64_t n, int g, int p, int r, c
                               const float *chi32, EstepOut out, bool density_only, int e2_mode,
                               const int *list, const unsigned *count, unsigned long long *rescue_list,
                               unsigned *rescue_count, int *d_status, cudaStream_t st, int triage,
-                              const double *d_pi, float tnats, int prio) {
+                              const double *d_pi, float tnats, int prio, int shared) {
   if (n <= 0) return cudaSuccess;
   if (r != 3) return cudaErrorInvalidValue;
   EArgs a = make_args(Y, n, g, p, lat, out, e2_mode, rescue_list, rescue_count, d_status, triage, d_pi, tnats,
-                      prio);
+                      prio, shared);
   a.comp = c32;
   a.chi = chi32;
   return density_only ? launch_list_r3<true>(a, g, n, list, count, c64, chi64, st)

@@ -157,23 +157,85 @@ def test_shared_prioritised_estep_matches_oracle(case, precision):
                    init.r, precision == binding.CFUST_FP64)
 
 
-def test_shared_refusals():
-    """The shared rule runs in the unfused single-fit sweep: with fused it is
-    refused at create, and a surrogate or a batched fit refuses it when called."""
-    torch = _torch()
+def test_shared_refusal_with_the_fused_pass():
+    """The fused pass keeps the two sweeps: shared_points with fused = 1 is
+    refused at create."""
+    _torch()
     Y, truth, init, lat = _problem("cfust_p3r3g4_n1000000_N2048", 64, 256)
     with pytest.raises(binding.CfustError) as ei:
         binding.Context(lat, precision=binding.CFUST_FP32, shared_points=True, fused=True)
     assert ei.value.status == -1
-    sur = binding.Surrogate(synth.make_lattice(1024, 4, seed=1), seed=2)
-    with binding.Context(lat, precision=binding.CFUST_FP32, shared_points=True) as ctx:
-        ctx.cfust_set_surrogate(sur)
-        with pytest.raises(binding.CfustError) as ei:
-            ctx.cfust_loglik(torch.from_numpy(Y).cuda(), init)
-        assert ei.value.status == -1
-        ctx.cfust_set_surrogate(None)
-    sur.close()
-    with binding.Context(lat, precision=binding.CFUST_FP32, shared_points=True, max_iter=2) as ctx:
-        with pytest.raises(binding.CfustError) as ei:
-            ctx.cfust_fit_batched([torch.from_numpy(Y).cuda()], [init])
-        assert ei.value.status == -1
+
+
+@pytest.mark.parametrize("prioritise", [False, True])
+def test_shared_batched_fits_match_oracle_fp64(prioritise):
+    """Two fits in one persistent launch per iteration with the shared rule:
+    the trace and the fitted parameters against the oracle's fits."""
+    torch = _torch()
+    Ys, truths, inits = synth.batched_workload(2, seed0=7, n_lo=800, n_hi=1500, g_hi=3)
+    lat = synth.make_lattice(256, 4, 3)
+    U = O.lattice_points(lat.n, lat.z, lat.shift)
+    with binding.Context(lat, precision=binding.CFUST_FP64, max_iter=2, shared_points=True,
+                         prioritise=prioritise) as ctx:
+        bp, btr, st = ctx.cfust_fit_batched([torch.from_numpy(Y).cuda() for Y in Ys], inits)
+    assert all(v == 0 for v in st)
+    for f in range(2):
+        if prioritise:
+            # the oracle's fit takes the natural order: run its E- and M-steps by hand
+            P = inits[f].copy()
+            tr = []
+            for _ in range(2):
+                E = O.estep(Ys[f], P, U, prioritise=True, shared=True)
+                tr.append(E["loglik"])
+                P = O.mstep_update(O.mstep_sums(Ys[f], E["tau"], E["e1"], E["e2"], E["e3"], E["e4"]), P,
+                                   Ys[f].shape[0])
+            tr.append(O.loglik(Ys[f], P, U, prioritise=True))
+            ref, ref_tr = P, np.array(tr)
+        else:
+            ref, ref_tr = O.fit(Ys[f], inits[f], U, 2, shared=True)
+        assert np.allclose(btr[f], ref_tr, rtol=1e-10, atol=0)
+        for a, b in zip(bp[f].as_arrays(), ref.as_arrays()):
+            assert np.allclose(a, b, rtol=1e-8, atol=1e-10)
+
+
+def test_shared_batched_equals_single_fits_fp32():
+    """The batched sweep and the single-fit sweep take the same shared rule:
+    the same fits agree to their summation order."""
+    torch = _torch()
+    Ys, truths, inits = synth.batched_workload(5, seed0=40, n_lo=60, n_hi=1500)
+    lat = synth.make_lattice(256, 4, 0)
+    Yd = [torch.from_numpy(Y).cuda() for Y in Ys]
+    with binding.Context(lat, precision=binding.CFUST_FP32, max_iter=3, shared_points=True) as ctx:
+        bp, btr, st = ctx.cfust_fit_batched(Yd, inits)
+    for f, (Y, P0) in enumerate(zip(Yd, inits)):
+        with binding.Context(lat, precision=binding.CFUST_FP32, max_iter=3, shared_points=True) as ctx:
+            sp, str_, _ = ctx.cfust_fit(Y, P0)
+        assert np.allclose(btr[f], str_, rtol=1e-12, atol=0), f
+        for a, b in zip(bp[f].as_arrays(), sp.as_arrays()):
+            assert np.allclose(a, b, rtol=1e-12, atol=1e-14), f
+
+
+@pytest.mark.parametrize("prioritise", [False, True])
+def test_shared_fallback_pairs_equal_the_shared_lattice_estep(prioritise):
+    """With a surrogate attached and the shared rule, the pairs the network
+    leaves to the lattice rule are bit-identical to the plain shared E-step's."""
+    torch = _torch()
+    s = binding.Surrogate(synth.make_lattice(8192, 4, seed=11), seed=6)
+    s.cfust_surrogate_train(1 << 16, 1, batch=4096, lr=3e-3, seed=2)
+    Y, _, truth, init, _, _ = synth.workload("cfust_p3r3g4_n1000000_N2048", n=2000, seed=0)
+    Yd = torch.tensor(Y, dtype=torch.float64, device="cuda")
+    lat = synth.make_lattice(512, 4, seed=0)
+    with binding.Context(lat, precision=binding.CFUST_FP32, prioritise=prioritise, shared_points=True) as plain, \
+            binding.Context(lat, precision=binding.CFUST_FP32, prioritise=prioritise, shared_points=True) as sur:
+        sur.cfust_set_surrogate(s)
+        Ep = plain.cfust_estep(Yd, init)
+        Es = sur.cfust_estep(Yd, init)
+        _, kind = sur.cfust_surrogate_inputs(Yd, init)
+    s.close()
+    out = kind.cpu().numpy() != 2
+    assert out.sum() > 100
+    for k in ("logf", "e1", "e2", "e3", "e4"):
+        a = Es[k].cpu().numpy()
+        b = Ep[k].cpu().numpy()
+        for i in range(init.g):
+            assert np.array_equal(a[i][..., out[i]], b[i][..., out[i]]), (i, k)
