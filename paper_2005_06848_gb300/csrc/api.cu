@@ -600,13 +600,14 @@ cfust_status cfust_create(cfust_ctx **out, const cfust_opts *o, void *cuda_strea
   {
     const int r = L.dim - 1;
     float *tab = nullptr;
-    if (cudaMalloc(&tab, sizeof(float) * (size_t)L.n * uniform_stride(r)) != cudaSuccess) {
+    if (cudaMalloc(&tab, sizeof(float) * (size_t)uniform_table_floats(L.n, r)) != cudaSuccess) {
       g_create_error = "cudaMalloc of the lattice table failed";
       cfust_destroy(c);
       return CFUST_ENOMEM;
     }
     c->d_utab = tab;
     c->lat.utab = tab;
+    c->lat.utab2 = tab + (size_t)L.n * uniform_stride(r);
     if (launch_uniform_table(c->lat, r, tab, c->stream) != cudaSuccess ||
         cudaStreamSynchronize(c->stream) != cudaSuccess) {
       g_create_error = "building the lattice table failed";

@@ -113,13 +113,26 @@ struct LatticeDev {
   // row k = [1 - u_1 .. 1 - u_r, u_1 .. u_r, padding] with a row stride of
   // uniform_stride(r) floats (device memory; built by launch_uniform_table)
   const float *utab = nullptr;
+  // the same values in the order of the shared-points sweep, which takes the
+  // points k and k + 32 side by side: for k = 64 b + l (l < 32), entry
+  // (b, l) holds, for each of the uniform_stride(r) columns c, the pair
+  // (row k [c], row k + 32 [c]) (row k again where k + 32 >= n); entries for
+  // ceil(n / 64) blocks, right after the row table in the same allocation
+  const float *utab2 = nullptr;
 };
 
 __host__ __device__ constexpr int uniform_stride(int r) { return ((2 * r + 3) / 4) * 4; }
 
-// Fill the uniform table of `lat` for r normal coordinates into tab
-// [lat.n][uniform_stride(r)], with the same single-precision arithmetic as the
-// sweep used to form them per point.
+// Floats of the two uniform tables of an n-point lattice for r normal
+// coordinates (the row table, then the pair-interleaved one).
+__host__ __device__ constexpr int64_t uniform_table_floats(int n, int r) {
+  return ((int64_t)n + ((int64_t)n + 63) / 64 * 64) * uniform_stride(r);
+}
+
+// Fill the uniform tables of `lat` for r normal coordinates into tab (row
+// table [lat.n][uniform_stride(r)], then the pair-interleaved table, see
+// LatticeDev::utab2; uniform_table_floats(lat.n, r) floats), with the same
+// single-precision arithmetic as the sweep used to form them per point.
 cudaError_t launch_uniform_table(const LatticeDev &lat, int r, float *tab, cudaStream_t st);
 
 // Precompute: factorisations, constants and chi-scale tables for every component.

@@ -550,6 +550,7 @@ cudaError_t launch_estep_batched(int precision, const BatchDev &b, int p, int r,
     a.sfrac[t] = lat.sfrac[t];
   }
   a.utab = lat.utab;
+  a.utab2 = lat.utab2;
   a.e2_mode = e2_mode;
   a.ppw = ppw < 1 ? 1 : (ppw > 32 ? 32 : ppw);
   a.rescue_list = rescue_list;
@@ -574,23 +575,38 @@ cudaError_t launch_estep_batched(int precision, const BatchDev &b, int p, int r,
              : dispatch_batched<float, false>(r, a, b, items, nitems, item_counter, ctas_per_sm, st, true, c64, chi64, tm);
 }
 
+// One thread per slot k of the padded lattice (ceil(n / 64) * 64 slots): the
+// row of point k (k < n) and its place in the pair-interleaved table, where a
+// second point past n repeats the first of its pair.
 __global__ void uniform_table_kernel(LatticeDev lat, int r, int us, float *tab) {
   const int k = blockIdx.x * blockDim.x + threadIdx.x;
   const int N = lat.n;
-  if (k >= N) return;
+  const int npad = (N + 63) / 64 * 64;
+  if (k >= npad) return;
+  const int src = k < N ? k : (k - 32 < N ? k - 32 : N - 1);
   const float fN = (float)N, invN = 1.0f / fN;
   const float umin = 1.1102230246251565e-16f, umax = 1.0f - 5.9604644775390625e-08f;
   float *row = tab + (int64_t)k * us;
+  float *pair = tab + (int64_t)N * us + ((int64_t)(k >> 6) * 32 + (k & 31)) * 2 * us + ((k >> 5) & 1);
   for (int t = 0; t < r; ++t) {
-    const int m = (int)(((int64_t)k * lat.z[t + 1] + lat.sint[t + 1]) % N);
+    const int m = (int)(((int64_t)src * lat.z[t + 1] + lat.sint[t + 1]) % N);
     const float fm = (float)(2 * m - N);
     const float sf = (float)lat.sfrac[t + 1], two_sf = (float)(2.0 * lat.sfrac[t + 1]);
     const float mm = 0.5f * (fm + fN);
     const float lo = mm + sf, hi = (fN - mm) - sf;
-    row[t] = fminf(fmaxf(fabsf(fm + two_sf) * invN, umin), umax);
-    row[r + t] = fmaxf(2.0f * fminf(lo, hi) * invN, umin);
+    const float um = fminf(fmaxf(fabsf(fm + two_sf) * invN, umin), umax);
+    const float uu = fmaxf(2.0f * fminf(lo, hi) * invN, umin);
+    if (k < N) {
+      row[t] = um;
+      row[r + t] = uu;
+    }
+    pair[2 * t] = um;
+    pair[2 * (r + t)] = uu;
   }
-  for (int t = 2 * r; t < us; ++t) row[t] = 0.0f;
+  for (int t = 2 * r; t < us; ++t) {
+    if (k < N) row[t] = 0.0f;
+    pair[2 * t] = 0.0f;
+  }
 }
 
 template <bool DENS>
@@ -660,6 +676,7 @@ EArgs make_args(const double *Y, int64_t n, int g, int p, const LatticeDev &lat,
   }
   a.out = out;
   a.utab = lat.utab;
+  a.utab2 = lat.utab2;
   a.e2_mode = e2_mode;
   a.ppw = 1;
   a.staged = 1;
@@ -695,7 +712,8 @@ cudaError_t launch_estep_list(const double *Y, int64_t n, int g, int p, int r, c
 
 cudaError_t launch_uniform_table(const LatticeDev &lat, int r, float *tab, cudaStream_t st) {
   if (lat.n <= 0 || r < 1 || r > RMAX) return cudaErrorInvalidValue;
-  uniform_table_kernel<<<(lat.n + 255) / 256, 256, 0, st>>>(lat, r, uniform_stride(r), tab);
+  const int npad = (lat.n + 63) / 64 * 64;
+  uniform_table_kernel<<<(npad + 255) / 256, 256, 0, st>>>(lat, r, uniform_stride(r), tab);
   return cudaGetLastError();
 }
 

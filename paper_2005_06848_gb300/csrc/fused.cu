@@ -593,6 +593,7 @@ cudaError_t launch_fused(int precision, const double *Y, int64_t n, int g, int p
     a.sfrac[t] = lat.sfrac[t];
   }
   a.utab = lat.utab;
+  a.utab2 = lat.utab2;
   a.e2_mode = e2_mode;
   a.ppw = 1;
   a.staged = 1;

@@ -90,6 +90,7 @@ struct EArgs {
   int sint[RMAX + 1];
   double sfrac[RMAX + 1];
   const float *utab; // lattice uniforms, [N][uniform_stride(r)] (single precision sweeps)
+  const float *utab2; // the same, pair-interleaved for the shared-points sweep (LatticeDev::utab2)
   const void *comp;  // CompT<T>[g]
   const void *chi;   // T[g][2][N]
   EstepOut out;
@@ -408,20 +409,15 @@ __device__ __forceinline__ void shared_point_sums(const EArgs &a, int lane, cons
   for (int k = lane; k < N; k += 2 * WARP) {
     const bool two = k + WARP < N;
     const int k2 = two ? k + WARP : k;
-    const float4 *ra = reinterpret_cast<const float4 *>(a.utab) + (size_t)k * (US / 4);
-    const float4 *rb = reinterpret_cast<const float4 *>(a.utab) + (size_t)k2 * (US / 4);
-    float va[US], vb[US];
+    // the uniforms of points k and k + 32 as (k, k + 32) pairs, column by
+    // column: entry (k / 64, lane) of the pair-interleaved table
+    const float4 *rp = reinterpret_cast<const float4 *>(a.utab2) + (size_t)((k >> 6) * WARP + lane) * (US / 2);
+    float2 v2[US];
 #pragma unroll
-    for (int q4 = 0; q4 < US / 4; ++q4) {
-      const float4 fa = __ldg(ra + q4), fb = __ldg(rb + q4);
-      va[4 * q4] = fa.x;
-      va[4 * q4 + 1] = fa.y;
-      va[4 * q4 + 2] = fa.z;
-      va[4 * q4 + 3] = fa.w;
-      vb[4 * q4] = fb.x;
-      vb[4 * q4 + 1] = fb.y;
-      vb[4 * q4 + 2] = fb.z;
-      vb[4 * q4 + 3] = fb.w;
+    for (int q4 = 0; q4 < US / 2; ++q4) {
+      const float4 f = __ldg(rp + q4);
+      v2[2 * q4] = make_float2(f.x, f.y);
+      v2[2 * q4 + 1] = make_float2(f.z, f.w);
     }
     const float2 s2 = make_float2(tA[k], tA[k2]);
     float2 w2;
@@ -434,7 +430,7 @@ __device__ __forceinline__ void shared_point_sums(const EArgs &a, int lane, cons
       float2 p2, q2;
       phi_upper_pq_x2(acc2, p2, q2);
       w2 = (t == 0) ? p2 : __fmul2_rn(w2, p2);
-      z2[t] = neg_quantile_x2v(make_float2(va[t], vb[t]), make_float2(va[R + t], vb[R + t]), p2, q2);
+      z2[t] = neg_quantile_x2v(v2[t], v2[R + t], p2, q2);
     }
     if (!two) w2.y = 0.0f;
     sa2 = __fadd2_rn(sa2, w2);

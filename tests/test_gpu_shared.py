@@ -239,3 +239,24 @@ def test_shared_fallback_pairs_equal_the_shared_lattice_estep(prioritise):
         b = Ep[k].cpu().numpy()
         for i in range(init.g):
             assert np.array_equal(a[i][..., out[i]], b[i][..., out[i]]), (i, k)
+
+
+def test_shared_repeat_fits_are_bitwise_identical_fp32():
+    """Fixed-order sums everywhere: the same shared-rule fit twice (the bench
+    workload's first 20000 rows, 8 EM iterations, rescued pairs included)
+    gives the same trace and parameters bit for bit, as does the E-step."""
+    torch = _torch()
+    Y, truth, init, lat = _problem("cfust_p4r4g3_n100000_N4096", 20000, 4096)
+    Yd = torch.from_numpy(Y).cuda()
+    runs = []
+    for _ in range(2):
+        with binding.Context(lat, precision=binding.CFUST_FP32, max_iter=8, shared_points=True) as ctx:
+            runs.append(ctx.cfust_fit(Yd, init))
+    (pa, ta, _), (pb, tb, _) = runs
+    assert np.array_equal(ta, tb)
+    for a, b in zip(pa.as_arrays(), pb.as_arrays()):
+        assert np.array_equal(a, b)
+    a = _gpu(Y, init, lat, binding.CFUST_FP32)
+    b = _gpu(Y, init, lat, binding.CFUST_FP32)
+    for k in ("logf", "tau", "e1", "e2", "e3", "e4"):
+        assert np.array_equal(a[k], b[k]), k
