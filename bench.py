@@ -801,7 +801,8 @@ def run_ours(args):
                                f"per point: 2r Phi x {PHI_FLOPS} + (2r-1) Phi^-1 x {PHIINV_FLOPS} "
                                "+ r(r-1) conditional FMAs + (r + r(r+1)/2) moment FMAs, FMA = 2 flops"),
                      "ncu": {k: prof[k] for k in ("fma_pipe_pct", "xu_pipe_pct", "issue_active_pct",
-                                                  "fp32_flop_eq_per_point", "xu_inst_per_point")
+                                                  "fp32_flop_eq_per_point", "xu_inst_per_point",
+                                                  "thread_inst_per_point")
                              if k in prof} or None},
         "sm_count": sms,
         # accuracy of the timed rule against a 65536-point prioritised rule
