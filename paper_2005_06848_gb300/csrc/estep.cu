@@ -10,7 +10,9 @@
 //   lim_t = (a_t s - sum_{h<t} L_th z_h) / L_tt,  p_t = Phi(-lim_t),
 //   z_t = -Phi^{-1}(max((1 - u_t) p_t, tiny)),   weight w = prod_t p_t,  V = z / s,
 // s the chi scale of the point (a per-component table).  Both passes share
-// the lattice point and run interleaved in one sweep.  The per-pair outputs
+// the lattice point and run interleaved in one sweep; with shared_points,
+// pass B is instead estimated on pass A's draws with the weight s^2 (the
+// chi-square density ratio x / (nu+p), x = (nu+p) s^2).  The per-pair outputs
 // are the E-step expectations of the latent gamma W and truncated normal U:
 //   e1 = (nu+p)/(nu+d) T_B/T_A,  sigma = sqrt((nu+d)/(nu+p+2)),
 //   e3 = e1 (q + sigma L E[V]),
