@@ -141,9 +141,8 @@ typedef struct {
                              half the normal-function work); log f and l are pass A's, unchanged, and
                              e1..e4 move within the rule's error.  0 keeps the two separate sweeps.
                              Taken by every lattice sweep in both precisions and either variable order:
-                             cfust_estep, cfust_loglik, the single and batched fits, and the pairs a
-                             surrogate leaves to the lattice rule.  The fused pass keeps the two
-                             sweeps: fused = 1 with it fails at cfust_create. */
+                             cfust_estep, cfust_loglik, the single and batched fits, the fused pass, and
+                             the pairs a surrogate leaves to the lattice rule. */
 } cfust_opts;
 
 typedef struct cfust_ctx cfust_ctx;

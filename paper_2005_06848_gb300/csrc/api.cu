@@ -422,7 +422,7 @@ cfust_status enqueue_fused(cfust_ctx *c, const double *Y, int64_t n, bool densit
   CF_CUDA(c, launch_fused(c->opts.precision, Y, n, c->g, c->p, c->r, c->lat, c->d_c64, c->d_c32, c->d_chi64,
                           c->d_chi32, density_only, c->opts.e2_mode, c->d_status, c->d_rescue_cnt,
                           c->opts.pairs_per_warp, c->d_partials, c->d_llpart, pi, (float)c->opts.triage_nats,
-                          c->opts.prioritise, st, tm, nb));
+                          c->opts.prioritise, c->opts.shared_points, st, tm, nb));
   return CFUST_OK;
 }
 
@@ -547,10 +547,6 @@ cfust_status cfust_create(cfust_ctx **out, const cfust_opts *o, void *cuda_strea
   }
   if (o->shared_points != 0 && o->shared_points != 1) {
     g_create_error = "shared_points must be 0 or 1";
-    return CFUST_EINVAL;
-  }
-  if (o->shared_points && o->fused) {
-    g_create_error = "shared_points runs in the unfused sweep: fused must be 0";
     return CFUST_EINVAL;
   }
   cfust_ctx *c = new cfust_ctx();

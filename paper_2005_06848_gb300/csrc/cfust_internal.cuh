@@ -242,7 +242,7 @@ cudaError_t launch_fused(int precision, const double *Y, int64_t n, int g, int p
                          const CompT<double> *c64, const CompT<float> *c32, const double *chi64, const float *chi32,
                          bool density_only, int e2_mode, int *d_status, unsigned *rescue_count, int pairs_per_warp,
                          double *partials, double *ll_partials, const double *d_pi, float tnats, int prio,
-                         cudaStream_t st, SweepTiming tm, int *nblocks);
+                         int shared, cudaStream_t st, SweepTiming tm, int *nblocks);
 
 // Sum the per-block log-likelihood partials in a fixed order: *ll_out = sum,
 // and when trace != NULL also trace[*iter] = sum and ++*iter.

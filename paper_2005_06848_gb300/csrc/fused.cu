@@ -136,7 +136,7 @@ __device__ __forceinline__ bool fused_stage(const EArgs &a, int c0, int c1, bool
 // the best FINAL value of the observation (pairs still flagged do not count:
 // their bounds are upper bounds), so a pair is dropped only when some
 // component is known to outweigh it by exp(tnats).
-template <int R, bool DENS>
+template <int R, bool DENS, bool SHR>
 __device__ __noinline__ void fused_rescue(const EArgs &a, const FusedArgs &f, const FitView &fv, unsigned char *flag,
                                           int nt, int tj, double *sm, Prologue<R> *spr, int *skip) {
   constexpr int RP = R * (R + 1) / 2;
@@ -170,7 +170,7 @@ __device__ __noinline__ void fused_rescue(const EArgs &a, const FusedArgs &f, co
       __syncthreads();
       if (!*skip) {
         const double *tab = f.chi64 + (int64_t)i * 2 * a.N;
-        pair_sweep_log_cta<R, DENS>(a, fv, f.c64[i], *spr, tab, tab + a.N, i, jj, sm);
+        pair_sweep_log_cta<R, DENS, SHR>(a, fv, f.c64[i], *spr, tab, tab + a.N, i, jj, sm);
       }
       if (threadIdx.x == 0) flag[i * tj + jj] = 0;
       __syncthreads();
@@ -317,7 +317,7 @@ __device__ __forceinline__ void fused_tile_sums(const T *out, const void *ys_raw
 // without waiting for the other warps; lane k ppw + b first computes the
 // double prologue of (component c0 + k, observation b) ((c1 - c0) ppw <= 32),
 // and the pairs needing the rescue are recorded.
-template <typename T, int R, bool DENS, bool PRIO>
+template <typename T, int R, bool DENS, bool PRIO, bool SHR>
 __device__ __forceinline__ void fused_sweep_group(const EArgs &a, const FitView &fv, const PairedConsts *pcs,
                                                   PairedConsts *wpc, const T *tab, int tab_stride, int c0, int c1,
                                                   int nt, unsigned char *flag) {
@@ -342,14 +342,14 @@ __device__ __forceinline__ void fused_sweep_group(const EArgs &a, const FitView 
       const Prologue<R> pr = shfl_prologue<R>(mine, src);
       PrioLane<R, T> pp;
       if constexpr (PRIO) pp = shfl_prio<R, T>(pmine, src);
-      const bool need = pair_sweep<T, T, R, DENS, PRIO>(a, fv, cs[i], pr, tA, tA + a.N, i, jw0 + b, lane,
-                                                        sizeof(T) == 4, pcs + (i - c0), wpc, &pp);
+      const bool need = pair_sweep<T, T, R, DENS, PRIO, 1, SHR>(a, fv, cs[i], pr, tA, tA + a.N, i, jw0 + b,
+                                                                lane, sizeof(T) == 4, pcs + (i - c0), wpc, &pp);
       if (lane == 0) flag[i * tj + jw0 + b] = need ? 1 : 0;
     }
   }
 }
 
-template <typename T, int R, bool DENS, bool PRIO>
+template <typename T, int R, bool DENS, bool PRIO, bool SHR = false>
 __global__ void __launch_bounds__(FT, sizeof(T) == 4 ? CFUST_ESTEP_MINB : 1) fused_em_kernel(EArgs a, FusedArgs f) {
   extern __shared__ __align__(128) unsigned char smem[];
   constexpr int RP = R * (R + 1) / 2;
@@ -418,11 +418,11 @@ __global__ void __launch_bounds__(FT, sizeof(T) == 4 ? CFUST_ESTEP_MINB : 1) fus
         ++stage;
       }
       const T *tab = staged ? stab : reinterpret_cast<const T *>(a.chi) + (int64_t)c0 * 2 * a.N;
-      fused_sweep_group<T, R, DENS, PRIO>(a, s_fv, FUSED_PCS, FUSED_WPC, tab, staged ? (int)f.tab_stride : 2 * a.N,
+      fused_sweep_group<T, R, DENS, PRIO, SHR>(a, s_fv, FUSED_PCS, FUSED_WPC, tab, staged ? (int)f.tab_stride : 2 * a.N,
                                           c0, c1, nt, FUSED_FLAG);
     }
     __syncthreads();
-    if constexpr (sizeof(T) == 4) fused_rescue<R, DENS>(a, f, s_fv, FUSED_FLAG, nt, tj, s_rsm, &s_pr, &s_skip);
+    if constexpr (sizeof(T) == 4) fused_rescue<R, DENS, SHR>(a, f, s_fv, FUSED_FLAG, nt, tj, s_rsm, &s_pr, &s_skip);
     if ((int)threadIdx.x < nt) {
       int bad = 0;
       s_red[threadIdx.x] += fused_lse<T, !DENS>(FUSED_OUT, g, tj, threadIdx.x, s_lpi, bad);
@@ -502,12 +502,12 @@ bool fused_plan(int N, int g, int p, int64_t n, int ppw_req, FusedPlan *pl) {
   return false;
 }
 
-template <typename T, int R, bool DENS, bool PRIO>
+template <typename T, int R, bool DENS, bool PRIO, bool SHR = false>
 cudaError_t fused_launch(EArgs a, FusedArgs f, int64_t n, int ppw_req, cudaStream_t st, SweepTiming tm,
                          int *nblocks) {
   FusedPlan pl;
   if (!fused_plan<T, R, DENS, PRIO>(a.N, a.g, a.p, n, ppw_req, &pl)) return cudaErrorInvalidValue;
-  const void *kern = (const void *)fused_em_kernel<T, R, DENS, PRIO>;
+  const void *kern = (const void *)fused_em_kernel<T, R, DENS, PRIO, SHR>;
   cudaError_t e = raise_smem_limit(kern, pl.smem);
   if (e != cudaSuccess) return e;
   int occ = 0;
@@ -544,21 +544,28 @@ cudaError_t fused_launch(EArgs a, FusedArgs f, int64_t n, int ppw_req, cudaStrea
     e = cudaEventRecordWithFlags(tm.start, st, evflag);
     if (e != cudaSuccess) return e;
   }
-  fused_em_kernel<T, R, DENS, PRIO><<<(unsigned)nb, FT, pl.smem, st>>>(a, f);
+  fused_em_kernel<T, R, DENS, PRIO, SHR><<<(unsigned)nb, FT, pl.smem, st>>>(a, f);
   e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   if (tm.stop) e = cudaEventRecordWithFlags(tm.stop, st, evflag);
   return e;
 }
 
+// pass B on pass A's points (shr) has its own instantiations for full sweeps
 template <typename T, bool DENS>
-cudaError_t fused_dispatch(int r, bool prio, EArgs a, FusedArgs f, int64_t n, int ppw, cudaStream_t st,
+cudaError_t fused_dispatch(int r, bool prio, bool shr, EArgs a, FusedArgs f, int64_t n, int ppw, cudaStream_t st,
                            SweepTiming tm, int *nb) {
+  shr = shr && !DENS;
   switch (r) {
-    case 1: return fused_launch<T, 1, DENS, false>(a, f, n, ppw, st, tm, nb);
-#define CFUST_FUSED_R(R)                                                   \
-  case R:                                                                  \
-    return prio ? fused_launch<T, R, DENS, true>(a, f, n, ppw, st, tm, nb) \
+    case 1:
+      return shr ? fused_launch<T, 1, DENS, false, !DENS>(a, f, n, ppw, st, tm, nb)
+                 : fused_launch<T, 1, DENS, false>(a, f, n, ppw, st, tm, nb);
+#define CFUST_FUSED_R(R)                                                                  \
+  case R:                                                                                 \
+    if (shr)                                                                              \
+      return prio ? fused_launch<T, R, DENS, true, !DENS>(a, f, n, ppw, st, tm, nb)       \
+                  : fused_launch<T, R, DENS, false, !DENS>(a, f, n, ppw, st, tm, nb);     \
+    return prio ? fused_launch<T, R, DENS, true>(a, f, n, ppw, st, tm, nb)                \
                 : fused_launch<T, R, DENS, false>(a, f, n, ppw, st, tm, nb);
     CFUST_FUSED_R(2)
     CFUST_FUSED_R(3)
@@ -578,7 +585,7 @@ cudaError_t launch_fused(int precision, const double *Y, int64_t n, int g, int p
                          const CompT<double> *c64, const CompT<float> *c32, const double *chi64, const float *chi32,
                          bool density_only, int e2_mode, int *d_status, unsigned *rescue_count, int pairs_per_warp,
                          double *partials, double *ll_partials, const double *d_pi, float tnats, int prio,
-                         cudaStream_t st, SweepTiming tm, int *nblocks) {
+                         int shared, cudaStream_t st, SweepTiming tm, int *nblocks) {
   if (n <= 0 || g < 1 || g > CFUST_GMAX || r < 1 || r > RMAX) return cudaErrorInvalidValue;
   EArgs a{};
   a.Y = Y;
@@ -604,7 +611,7 @@ cudaError_t launch_fused(int precision, const double *Y, int64_t n, int g, int p
   a.pi = d_pi;
   a.tnats = tnats;
   a.prio = prio ? 1 : 0;
-  a.shr = 0;
+  a.shr = shared ? 1 : 0;
   a.wait_polls = lat.wait_polls;
   FusedArgs f{};
   f.c64 = c64;
@@ -613,17 +620,17 @@ cudaError_t launch_fused(int precision, const double *Y, int64_t n, int g, int p
   f.ll_partials = ll_partials;
   f.r = r;
   f.K = sums_width(p, r);
-  const bool pr = prio != 0;
+  const bool pr = prio != 0, sh = shared != 0;
   if (precision == CFUST_FP64) {
     a.comp = c64;
     a.chi = chi64;
-    return density_only ? fused_dispatch<double, true>(r, pr, a, f, n, pairs_per_warp, st, tm, nblocks)
-                        : fused_dispatch<double, false>(r, pr, a, f, n, pairs_per_warp, st, tm, nblocks);
+    return density_only ? fused_dispatch<double, true>(r, pr, sh, a, f, n, pairs_per_warp, st, tm, nblocks)
+                        : fused_dispatch<double, false>(r, pr, sh, a, f, n, pairs_per_warp, st, tm, nblocks);
   }
   a.comp = c32;
   a.chi = chi32;
-  return density_only ? fused_dispatch<float, true>(r, pr, a, f, n, pairs_per_warp, st, tm, nblocks)
-                      : fused_dispatch<float, false>(r, pr, a, f, n, pairs_per_warp, st, tm, nblocks);
+  return density_only ? fused_dispatch<float, true>(r, pr, sh, a, f, n, pairs_per_warp, st, tm, nblocks)
+                      : fused_dispatch<float, false>(r, pr, sh, a, f, n, pairs_per_warp, st, tm, nblocks);
 }
 
 }  // namespace cfust

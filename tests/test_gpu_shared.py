@@ -157,14 +157,31 @@ def test_shared_prioritised_estep_matches_oracle(case, precision):
                    init.r, precision == binding.CFUST_FP64)
 
 
-def test_shared_refusal_with_the_fused_pass():
-    """The fused pass keeps the two sweeps: shared_points with fused = 1 is
-    refused at create."""
-    _torch()
-    Y, truth, init, lat = _problem("cfust_p3r3g4_n1000000_N2048", 64, 256)
-    with pytest.raises(binding.CfustError) as ei:
-        binding.Context(lat, precision=binding.CFUST_FP32, shared_points=True, fused=True)
-    assert ei.value.status == -1
+@pytest.mark.parametrize("precision", [binding.CFUST_FP64, binding.CFUST_FP32])
+@pytest.mark.parametrize("case", [("cfust_p4r4g3_n100000_N4096", 1003, 1024, False),
+                                  ("cfust_p3r3g4_n1000000_N2048", 777, 512, True),
+                                  ("cfust_p8r4g6_n1000000_N8192", 301, 1024, False)],
+                         ids=["p4r4g3", "p3r3g4-prio", "p8r4g6"])
+def test_shared_fused_fit_agrees_with_unfused(case, precision):
+    """The fused E-step + sums pass with the shared rule against the unfused
+    shared fit: the same per-pair arithmetic, sums in another order."""
+    torch = _torch()
+    wl, n, N, prio = case
+    Y, truth, init, lat = _problem(wl, n, N)
+    out = []
+    for fused in (False, True):
+        with binding.Context(lat, precision=precision, max_iter=3, fused=fused, prioritise=prio,
+                             shared_points=True) as ctx:
+            got, trace, done = ctx.cfust_fit(torch.from_numpy(Y).cuda(), init)
+        assert done == 3
+        out.append((got, trace))
+    (a, ta), (b, tb) = out
+    assert abs(tb[0] - ta[0]) <= 1e-12 * abs(ta[0]), (ta[0], tb[0])
+    assert np.all(np.abs(tb - ta) <= 1e-9 * np.abs(ta)), (ta, tb)
+    errs = parameter_errors(b.as_arrays(), a.as_arrays())
+    bar = 1e-9 if precision == binding.CFUST_FP64 else 1e-6
+    for name, e in errs.items():
+        assert e <= bar, f"{name}: fused vs unfused relative difference {e:.3g}"
 
 
 @pytest.mark.parametrize("prioritise", [False, True])
