@@ -487,7 +487,8 @@ def large_line(args, steps, warmup):
                     "roofline": {"achieved": ach2, "peak": peak0, "frac": ach2 / peak0,
                                  "flops_per_point": sweep_flops_per_point(r)},
                     "params_max_rel_diff_vs_shared": _max_rel_diff(tp_params, params)}
-    fused = fused_comparison(torch, binding, Yd, init, lat, steps, warmup, flush, tp_ms, tp_params, pairs, peak0, r)
+    fused = fused_comparison(torch, binding, Yd, init, lat, steps, warmup, flush, float(np.mean(ms)), params, pairs,
+                             peak0, r)
     step_s = float(np.mean(ms)) / 1e3
     sweep_ms = float(np.mean(kern))
     peaks = load_peaks() or {}
@@ -681,7 +682,7 @@ def run_ours(args):
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
     total_iters = args.warmup + args.steps
 
-    shared = PASS_B_SHARED and not args.fused
+    shared = PASS_B_SHARED
     ctx = binding.Context(lat, precision=binding.CFUST_FP32, max_iter=total_iters, use_graph=True,
                           timing=True, stream=stream, fused=args.fused, shared_points=shared)
     ctx.cfust_fit_begin(Yd, init)
@@ -767,13 +768,11 @@ def run_ours(args):
         if ws > 1:
             torch.distributed.destroy_process_group()
         return 0
-    other_rule, two_pass_ms, two_pass_params = None, total_ms / args.steps, params
+    other_rule = None
     if ws == 1 and not args.fused and not args.no_extras:
-        other_rule, o_ms, o_params = pass_b_comparison(torch, binding, synth, Yd, init, lat, args.steps,
-                                                        args.warmup, flush, total_ms / args.steps, params,
-                                                        pairs_per_step, peak, r, stream, not shared)
-        if shared:
-            two_pass_ms, two_pass_params = o_ms, o_params
+        other_rule, _, _ = pass_b_comparison(torch, binding, synth, Yd, init, lat, args.steps, args.warmup, flush,
+                                             total_ms / args.steps, params, pairs_per_step, peak, r, stream,
+                                             not shared)
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
@@ -815,10 +814,10 @@ def run_ours(args):
         # its double-precision-accurate arithmetic, not by these bytes
         "mstep": mstep_roofline(n, g, p, r, float(np.mean(mstep_ms)), peaks, sms) if mstep_ms else None,
         # the other pass-B rule on the same fit, and the fused E-step +
-        # M-step-sums pass (two passes) against the unfused two-pass fit
+        # M-step-sums pass with the line's rule against the line's fit
         "two_pass" if shared else "shared_points": other_rule,
         "fused": fused_comparison(torch, binding, Yd, init, lat, args.steps, args.warmup, flush,
-                                  two_pass_ms, two_pass_params, pairs_per_step, peak, r)
+                                  total_ms / args.steps, params, pairs_per_step, peak, r)
         if other_rule is not None else None,
         "clocks": clocks,
         "e2e": e2e,
@@ -1094,18 +1093,18 @@ def _max_rel_diff(a_params, b_params):
 
 def fused_comparison(torch, binding, Yd, P, lat, steps, warmup, flush, unfused_ms, unfused_params, pairs, peak, r):
     """The fused E-step + M-step-sums pass (one kernel per iteration, per-pair
-    outputs in shared memory only) on the same fit as the unfused line: time
-    per EM iteration, the fused kernel against the FP32 peak (the same
-    454-flop-per-point count: the sums are O(1) per observation), the device
-    memory each form's fit holds, and how far the two fits differ after the
-    same iterations from the same start (summation order only)."""
+    outputs in shared memory only) with the bench's pass-B rule on the same
+    fit as the unfused line: time per EM iteration, the fused kernel against
+    the FP32 peak (the rule's count: the sums are O(1) per observation), the
+    device memory each form's fit holds, and how far the two fits differ after
+    the same iterations from the same start (summation order only)."""
     ctx = binding.Context(lat, precision=binding.CFUST_FP32, max_iter=warmup + steps + 1, use_graph=True,
-                          timing=True, fused=True)
+                          timing=True, fused=True, shared_points=PASS_B_SHARED)
     ms, kern, params = _timed_em(torch, ctx, Yd, P, steps, warmup, flush)
     ctx.close()
     step_ms = float(np.mean(ms))
     kern_ms = float(np.mean(kern))
-    flops = pairs * lat.n * sweep_flops_per_point(r)
+    flops = pairs * lat.n * sweep_flops_per_point(r, shared=PASS_B_SHARED)
     achieved = flops / (kern_ms / 1e3) / 1e12
     diffs = []
     for a, b in zip(params.as_arrays(), unfused_params.as_arrays()):
