@@ -380,9 +380,6 @@ __device__ __forceinline__ Prologue<R> shfl_prologue(const Prologue<R> &mine, in
   return o;
 }
 
-// One (i, j) pair on one warp, its prologue given.  Returns true (uniformly
-// over the warp) when `check` is set and the single-precision sweep needs the
-// double rescue; in that case nothing is written.
 // Single-precision sums of one pair with pass B on pass A's lattice points.
 // Pass B's law differs from pass A's only in the chi variable (dof m_B = m_A + 2
 // for m_A = nu + p), and chi2_{m+2}(x) = chi2_m(x) x / m: with x = m_A s^2 at
@@ -456,9 +453,13 @@ __device__ __forceinline__ void shared_point_sums(const EArgs &a, int lane, cons
   for (int t = 0; t < RP; ++t) M2[t] = m2[t].x + m2[t].y;
 }
 
-// With SHR, pass B is estimated on pass A's lattice points (shared_point_sums;
-// the double-precision sweep does the same per point): one conditional chain
-// per point instead of two.
+// One (i, j) pair on one warp, its prologue given.  Returns true (uniformly
+// over the warp) when `check` is set and the single-precision sweep needs the
+// double rescue; in that case nothing is written.  With SHR, pass B is
+// estimated on pass A's lattice points (shared_point_sums; the
+// double-precision sweep does the same per point): one conditional chain per
+// point instead of two.  PTS > 1 lets the paired two-pass loop keep two
+// lattice points in flight.
 template <typename T, typename OT, int R, bool DENS, bool PRIO = false, int PTS = 1, bool SHR = false>
 __device__ __forceinline__ bool pair_sweep(const EArgs &a, const FitView &fv, const CompT<T> &c,
                                            const Prologue<R> &pr,
