@@ -516,7 +516,7 @@ def large_line(args, steps, warmup):
         "fused": fused,
         "surrogate": "not applicable: the learned form covers r = 3 and this workload has r = 4",
         "clocks": clocks,
-        "gpu_launches": 6 * steps,
+        "gpu_launches": 7 * steps,
     }
 
 
@@ -786,7 +786,10 @@ def run_ours(args):
         "em_iters_per_s": iters_per_s,
         "rescued_pairs_last_estep": rescued,
         "loglik_first_last": [float(trace[0]), float(trace[-1])],
-        "gpu_launches": 6 * args.steps,
+        # per EM iteration: precompute, sweep, rescue triage, rescue,
+        # posterior/sums, log-likelihood reduce, finalize (the fused pass:
+        # precompute, fused kernel, reduce, finalize)
+        "gpu_launches": (4 if args.fused else 7) * args.steps,
         "roofline": {"bound": "alu", "kernel": "fused_em_kernel<float,4>" if args.fused else "estep_kernel<float,4>",
                      "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
                      "traffic": None if args.fused else sweep_traffic_bytes(shared),
@@ -947,9 +950,10 @@ def batched_line(args, steps, warmup):
                    "step": "one EM iteration of every fit; the timed call adds one final density sweep",
                    "l2": "inputs larger than L2"},
         "fit_iters_per_s": args.nfits * steps / (ms / 1e3),
-        # per iteration: precompute, persistent sweep, rescue, posterior/sums,
-        # log-likelihood reduce, finalize; then one density pass (five kernels)
-        "gpu_launches": 6 * steps + 5,
+        # per iteration: precompute, persistent sweep, rescue triage, rescue,
+        # posterior/sums, log-likelihood reduce, finalize; then one density
+        # pass (five kernels)
+        "gpu_launches": 7 * steps + 5,
         "clocks": clocks,
         "fits_failed": int(sum(1 for s in st if s != 0)),
     }
@@ -1336,9 +1340,9 @@ def surrogate_line(args, steps, warmup):
             "speedup": float(np.mean(ms_run_p)) / float(np.mean(ms_run)),
             "fallback_pairs_per_timed_step": fb_steps,
             "nu_after": [float(v) for v in P_s.nu]},
-        # per EM iteration: precompute, network kernel, list sweep, rescue,
-        # posterior/sums, log-likelihood reduce, finalize
-        "gpu_launches": 7 * steps,
+        # per EM iteration: precompute, network kernel, list sweep, rescue
+        # triage, rescue, posterior/sums, log-likelihood reduce, finalize
+        "gpu_launches": 8 * steps,
         "roofline": {"bound": "tensor", "kernel": "surrogate_estep_kernel<false>", "achieved": achieved,
                      "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak, "traffic": None,
                      "peak_source": "measured cuBLAS bf16 (MEASURED_PEAKS.json)" if peaks else "fallback 1.7 PFLOP/s",
