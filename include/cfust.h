@@ -132,8 +132,9 @@ typedef struct {
                              cfust_mstep*, cfust_fit_batched and the explicit E-step outputs keep the
                              unfused kernels; a fit or log-likelihood with a surrogate attached and
                              fused = 1 fails with CFUST_EINVAL. */
-  int shared_points;      /* 1: pass B (T_B and the truncated moments at dof nu+p+2 that give e1, e3, e4)
-                             is estimated on pass A's lattice points.  The two laws differ only in the
+  int shared_points;      /* 1: pass B (T_B and the truncated moments at dof nu+p+2 that give e1, e3, e4,
+                             the E-step expectations of Section 2's latent gamma and truncated normal
+                             variables) is estimated on pass A's lattice points.  The two laws differ only in the
                              chi-square variable x, and chi2_{nu+p+2}(x) = chi2_{nu+p}(x) x / (nu+p): at
                              pass A's x of a point pass B's scaled limits equal pass A's, so pass A's
                              conditional draws serve both, pass B with the extra weight x / (nu+p).  The
